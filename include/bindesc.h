@@ -1,0 +1,219 @@
+/*
+ * bindesc.h -- C ABI of the GB300 (sm_103a) library for the BAD and HashSIFT
+ * binary descriptors and brute-force Hamming matching of
+ *   I. Suarez, J. M. Buenaposada, L. Baumela, "Revisiting Binary Local Image
+ *   Description for Resource Limited Devices", IEEE RA-L 2021.
+ *
+ * The calls follow the paper's statement of the problem: an image, keypoints
+ * (x, y, scale, angle) and learned descriptor parameters give packed binary
+ * descriptors (Sec. III-A, Eq. 1 stumps h = +1 iff f <= theta; Sec. III-B,
+ * D = sgn(B [f; 1])); two descriptor sets give nearest / second-nearest
+ * matches (Sec. IV-C, Sec. IV-F pipeline table).
+ *
+ * Conventions shared by every call
+ *  - Only plain pointers and sizes cross this boundary.  Pointers named
+ *    "host" are CPU memory; every other data pointer is CUDA device memory
+ *    owned by the caller, which must stay valid until the work completes.
+ *  - Work is enqueued asynchronously on the context's stream; the caller
+ *    synchronises (or calls bd_sync_status) before reading results.
+ *  - Every call returns a bd_status; nothing is thrown across the ABI.  On an
+ *    error nothing has been enqueued and bd_last_error() says why.
+ *  - Descriptors are packed little-endian bit vectors: bit k of a descriptor
+ *    is bit (k % 32) of 32-bit word k / 32; bit value 1 is the paper's +1.
+ *  - Images are 8-bit grayscale, row-major with a row pitch in bytes;
+ *    1 <= w, h <= 32767 and 255*w*h < 2^32.
+ *  - A keypoint is valid iff its four fields are finite, |x|,|y| <= 2^20,
+ *    0 < scale <= 1024 and |angle| <= 2^20.  Pixel centres sit at integer
+ *    coordinates, angles are radians, the image y axis points down.  An
+ *    invalid keypoint gets an all-zero descriptor and raises
+ *    BD_FLAG_INVALID_KEYPOINT in the device status word.
+ */
+#ifndef BINDESC_H
+#define BINDESC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum bd_status {
+    BD_OK = 0,
+    BD_ERR_INVALID = 1,      /* bad argument; nothing was enqueued */
+    BD_ERR_CUDA = 2,         /* a CUDA call failed */
+    BD_ERR_NOMEM = 3,        /* device memory could not be allocated */
+    BD_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    BD_ERR_DEVICE_CHECK = 5, /* a kernel flagged its input (see the flags) */
+    BD_ERR_UNSUPPORTED = 6   /* device or feature not supported by this build */
+} bd_status;
+
+/* Bits of the device status word returned by bd_sync_status. */
+#define BD_FLAG_INVALID_KEYPOINT 0x1u
+#define BD_FLAG_TIMEOUT 0x2u
+
+/* Keypoint: pixel position, scale (1 = the 32x32 patch frame covers 32 px)
+ * and orientation in radians. */
+typedef struct bd_keypoint {
+    float x, y, scale, angle;
+} bd_keypoint;
+
+/* One query's result: train index of the nearest neighbour (-1 if the train
+ * set is empty), its Hamming distance d1, the second-smallest distance d2
+ * (nbits+1 when there is no second entry) and the ratio-test verdict. */
+typedef struct bd_match_result {
+    int32_t idx;
+    uint16_t d1;
+    uint16_t d2;
+    uint8_t accept;
+    uint8_t pad[3];
+} bd_match_result;
+
+typedef struct bd_ctx bd_ctx;
+typedef struct bd_bad_params bd_bad_params;
+typedef struct bd_hs_params bd_hs_params;
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+
+/* Creates a context on CUDA device `device` that enqueues on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  The context owns a small
+ * status block and a growable scratch area on that device.  Requires an
+ * sm_103 device; otherwise BD_ERR_UNSUPPORTED. */
+bd_status bd_create(int device, void *stream, bd_ctx **out);
+
+/* Releases the context and its device memory (synchronising its stream). */
+void bd_destroy(bd_ctx *ctx);
+
+/* Switches the stream later calls enqueue on. */
+bd_status bd_set_stream(bd_ctx *ctx, void *stream);
+
+/* Message of the last failed call on this context (static storage owned by
+ * the context; valid until the next call). */
+const char *bd_last_error(const bd_ctx *ctx);
+
+/* Synchronises the context's stream, returns the device status flags
+ * (BD_FLAG_*) raised since the last call in *flags (may be NULL) and clears
+ * them.  Returns BD_ERR_TIMEOUT if BD_FLAG_TIMEOUT was raised,
+ * BD_ERR_DEVICE_CHECK if any other flag was, else BD_OK. */
+bd_status bd_sync_status(bd_ctx *ctx, uint32_t *flags);
+
+/* Number of HashSIFT bits re-evaluated in FP32 since the last reset
+ * (synchronises the stream).  reset != 0 zeroes the counter afterwards. */
+bd_status bd_rescued_count(bd_ctx *ctx, uint64_t *count, int reset);
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t bd_kernel_launches(void);
+
+/* Grows the scratch area to at least `bytes` now, so that later calls of
+ * that size allocate nothing (needed before capturing them in a CUDA graph). */
+bd_status bd_reserve(bd_ctx *ctx, size_t bytes);
+
+/* Scratch bytes the calls below need for the given sizes (host-side query). */
+size_t bd_scratch_bytes_bad(int w, int h);
+size_t bd_scratch_bytes_hashsift(int n);
+size_t bd_scratch_bytes_match(int nq, int nt, int nbits);
+
+/* ------------------------------------------------------------------------ */
+/* BAD parameters (Sec. III-A)                                               */
+
+/* Learned BAD parameters, copied from host memory and owned by the handle.
+ *  nbits        256 or 512 (K weak descriptors).
+ *  centres      host, nbits x 2 x 2 uint8: box centre (x, y) of box 1 and 2
+ *               of pair k in the 32x32 patch frame (values 0..31; the frame
+ *               centre is (16,16)).
+ *  sides        host, nbits uint8 box sides s (1..64); both boxes of a pair
+ *               share s (Sec. III-A: "two boxes of size s").
+ *  thr_num      host, nbits int32; threshold theta_k = thr_num[k] / thr_den.
+ *  thr_den      > 0 (1 for integer thresholds; 10 for the 0.1 grid of
+ *               Sec. III-A, Alg. 2 discussion).
+ *  n_angle_bins 1..64 orientation bins (32 in the benchmarks).
+ *  level_scales host, n_levels strictly increasing pyramid scales in
+ *               (0, 32]; a keypoint uses the level whose geometric-mean
+ *               neighbourhood contains its scale.
+ * The library builds, on the host, an integer table of every box's rotated
+ * and scaled corner offsets per (level, angle bin) and uploads it. */
+bd_status bd_bad_params_create(bd_ctx *ctx, int nbits, const uint8_t *centres,
+                               const uint8_t *sides, const int32_t *thr_num, int32_t thr_den,
+                               int n_angle_bins, const float *level_scales, int n_levels,
+                               bd_bad_params **out);
+void bd_bad_params_destroy(bd_bad_params *p);
+
+/* Copies the host-side table out (for checking): for each level l, angle
+ * bin b and bit k, offsets[((l*NB + b)*nbits + k)*4 + {0..3}] = centre offset
+ * (dx1, dy1, dx2, dy2) of the two boxes from the keypoint's pixel, and
+ * sides_out[l*nbits + k] = scaled side.  Buffers are host memory of
+ * n_levels*NB*nbits*4 and n_levels*nbits int32. */
+bd_status bd_bad_params_table(const bd_bad_params *p, int32_t *offsets, int32_t *sides_out);
+
+/* ------------------------------------------------------------------------ */
+/* HashSIFT parameters (Sec. III-B)                                          */
+
+#define BD_HS_FP32 0        /* projection on CUDA cores in FP32 */
+#define BD_HS_BF16_RESCUE 1 /* tcgen05 BF16 x BF16 -> FP32, FP32 re-check near 0 */
+
+/* Learned hash B = [W^T | b], copied from host memory.
+ *  nbits     256 or 512.
+ *  W         host, 128 x nbits float, row-major (W[i*nbits + k]).
+ *  bias      host, nbits float (the last column of B).
+ *  spacing   patch pixel step in units of the keypoint scale (> 0, <= 16).
+ *  precision BD_HS_FP32 or BD_HS_BF16_RESCUE.
+ *  band      BF16 mode: bits whose BF16 margin |W_k.f + b_k| is below the
+ *            band are recomputed in FP32.  band < 0 selects the per-bit bound
+ *            (2^-7 + 2^-16 + 129*2^-23 + 2e-4) * ||W_k||_2, which covers the
+ *            BF16 rounding of f and W for unit-norm f; band >= 0 is used as
+ *            given for every bit. */
+bd_status bd_hs_params_create(bd_ctx *ctx, int nbits, const float *W, const float *bias,
+                              float spacing, int precision, float band, bd_hs_params **out);
+void bd_hs_params_destroy(bd_hs_params *p);
+
+/* ------------------------------------------------------------------------ */
+/* Work                                                                      */
+
+/* Integral image (Sec. III-A): ii[y*ii_stride + x] = sum of img over
+ * [0,y) x [0,x), for 0 <= y <= h, 0 <= x <= w; ii_stride >= w+1 entries. */
+bd_status bd_integral(bd_ctx *ctx, const uint8_t *img, int w, int h, int pitch, uint32_t *ii,
+                      int ii_stride);
+
+/* BAD descriptors (Sec. III-A) of n keypoints: out is n x nbits/32 words.
+ * Builds the integral image in scratch, then one warp per keypoint gathers
+ * the box sums of every pair and packs the stump outputs. */
+bd_status bd_bad_describe(bd_ctx *ctx, const bd_bad_params *p, const uint8_t *img, int w, int h,
+                          int pitch, const bd_keypoint *kps, int n, uint32_t *out);
+
+/* 32x32 FP32 patches of n keypoints (Sec. III-A/III-B: patches normalised to
+ * 32x32): patches is n x 1024 floats, pixel (i, j) at [i*32 + j], sampled
+ * bilinearly (clamp to edge) at (x,y) + scale*spacing*R(angle)(j-15.5, i-15.5). */
+bd_status bd_hashsift_warp(bd_ctx *ctx, const bd_hs_params *p, const uint8_t *img, int w, int h,
+                           int pitch, const bd_keypoint *kps, int n, float *patches);
+
+/* L2-normalised 128-bin gradient-orientation histograms (Sec. III-B, "SIFT
+ * features") of n FP32 patches (n x 1024): hist is n x 128 floats, index
+ * (cell_row*4 + cell_col)*8 + orientation_bin. */
+bd_status bd_hashsift_hist(bd_ctx *ctx, const float *patches, int n, float *hist);
+
+/* Hash bits D = sgn(W^T f + b) (Sec. III-B) of n FP32 histograms (n x 128):
+ * out is n x nbits/32 words.  Uses the precision chosen in p. */
+bd_status bd_hashsift_project(bd_ctx *ctx, const bd_hs_params *p, const float *hist, int n,
+                              uint32_t *out);
+
+/* Whole HashSIFT descriptor of n keypoints: warp + histogram fused in one
+ * kernel, then the projection.  hist_out (n x 128 floats) may be NULL. */
+bd_status bd_hashsift_describe(bd_ctx *ctx, const bd_hs_params *p, const uint8_t *img, int w,
+                               int h, int pitch, const bd_keypoint *kps, int n, uint32_t *out,
+                               float *hist_out);
+
+/* Brute-force Hamming matching (Sec. IV-C nearest neighbour): for each of the
+ * nq query descriptors, the nearest train descriptor (lowest index among
+ * equal distances), its distance d1, the second-smallest distance d2 over
+ * the remaining train entries, and accept = ratio_den*d1 < ratio_num*d2.
+ * q: nq x nbits/32 words; t: nt x nbits/32 words; out: nq entries.
+ * nbits 256 or 512; 0 <= nt < 2^22; 0 < ratio_num <= ratio_den. */
+bd_status bd_match(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt, int nbits,
+                   int ratio_num, int ratio_den, bd_match_result *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BINDESC_H */

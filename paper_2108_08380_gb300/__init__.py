@@ -1,0 +1,333 @@
+"""GB300 (sm_103a) BAD / HashSIFT binary descriptors and Hamming matching.
+
+Python binding of ``libbindesc.so`` (declared in ``include/bindesc.h``).  The
+``bd_*`` functions here carry the C names and only marshal arguments; every
+step of the computation runs in the library's CUDA kernels.  PyTorch serves
+for device memory and streams: tensors are passed by ``data_ptr()`` and work
+is enqueued on ``torch.cuda.current_stream()`` unless a context says otherwise.
+
+There is no CPU fallback: if the library is missing or the device is not an
+sm_103 GPU, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbindesc.so")
+
+BD_OK = 0
+BD_ERR_INVALID = 1
+BD_ERR_CUDA = 2
+BD_ERR_NOMEM = 3
+BD_ERR_TIMEOUT = 4
+BD_ERR_DEVICE_CHECK = 5
+BD_ERR_UNSUPPORTED = 6
+BD_FLAG_INVALID_KEYPOINT = 0x1
+BD_FLAG_TIMEOUT = 0x2
+BD_HS_FP32 = 0
+BD_HS_BF16_RESCUE = 1
+
+_STATUS_NAMES = {0: "BD_OK", 1: "BD_ERR_INVALID", 2: "BD_ERR_CUDA", 3: "BD_ERR_NOMEM",
+                 4: "BD_ERR_TIMEOUT", 5: "BD_ERR_DEVICE_CHECK", 6: "BD_ERR_UNSUPPORTED"}
+
+# (name, restype, argtypes) of every exported call; include/bindesc.h is the reference.
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_F = ctypes.c_float
+_SZ = ctypes.c_size_t
+_SIGS = [
+    ("bd_create", _I, [_I, _P, ctypes.POINTER(_P)]),
+    ("bd_destroy", None, [_P]),
+    ("bd_set_stream", _I, [_P, _P]),
+    ("bd_last_error", ctypes.c_char_p, [_P]),
+    ("bd_sync_status", _I, [_P, ctypes.POINTER(ctypes.c_uint32)]),
+    ("bd_rescued_count", _I, [_P, ctypes.POINTER(ctypes.c_uint64), _I]),
+    ("bd_kernel_launches", ctypes.c_uint64, []),
+    ("bd_reserve", _I, [_P, _SZ]),
+    ("bd_scratch_bytes_bad", _SZ, [_I, _I]),
+    ("bd_scratch_bytes_hashsift", _SZ, [_I]),
+    ("bd_scratch_bytes_match", _SZ, [_I, _I, _I]),
+    ("bd_bad_params_create", _I, [_P, _I, _P, _P, _P, ctypes.c_int32, _I, _P, _I, ctypes.POINTER(_P)]),
+    ("bd_bad_params_destroy", None, [_P]),
+    ("bd_bad_params_table", _I, [_P, _P, _P]),
+    ("bd_hs_params_create", _I, [_P, _I, _P, _P, _F, _I, _F, ctypes.POINTER(_P)]),
+    ("bd_hs_params_destroy", None, [_P]),
+    ("bd_integral", _I, [_P, _P, _I, _I, _I, _P, _I]),
+    ("bd_bad_describe", _I, [_P, _P, _P, _I, _I, _I, _P, _I, _P]),
+    ("bd_hashsift_warp", _I, [_P, _P, _P, _I, _I, _I, _P, _I, _P]),
+    ("bd_hashsift_hist", _I, [_P, _P, _I, _P]),
+    ("bd_hashsift_project", _I, [_P, _P, _P, _I, _P]),
+    ("bd_hashsift_describe", _I, [_P, _P, _P, _I, _I, _I, _P, _I, _P, _P]),
+    ("bd_match", _I, [_P, _P, _I, _P, _I, _I, _I, _I, _P]),
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class BindescError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(
+                    f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                    "g.build()'` (or paper_2108_08380_gb300/build.py); there is no CPU fallback")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, res, args in _SIGS:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(lib().bd_kernel_launches())
+
+
+def exported_names():
+    return [s[0] for s in _SIGS]
+
+
+# --------------------------------------------------------------------------
+# raw C calls under their C names (pointers and sizes only)
+# --------------------------------------------------------------------------
+
+def _fwd(name):
+    def call(*args):
+        return getattr(lib(), name)(*args)
+    call.__name__ = name
+    call.__doc__ = f"Direct call of {name} (see include/bindesc.h)."
+    return call
+
+
+for _name, _r, _a in _SIGS:
+    globals()[_name] = _fwd(_name)
+
+
+# --------------------------------------------------------------------------
+# torch conveniences
+# --------------------------------------------------------------------------
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(None)
+
+
+def _np_ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Context:
+    """Owns a bd_ctx on one CUDA device; calls enqueue on the current torch stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self._torch = torch
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        st = lib().bd_create(self.device, ctypes.c_void_p(s), ctypes.byref(h))
+        if st != BD_OK:
+            raise BindescError(st, "bd_create failed (an sm_103 GPU is required)")
+        self.handle = h
+        self._explicit_stream = stream is not None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().bd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != BD_OK:
+            msg = lib().bd_last_error(self.handle)
+            raise BindescError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def _stream(self):
+        if not self._explicit_stream:
+            s = self._torch.cuda.current_stream(self.device).cuda_stream
+            lib().bd_set_stream(self.handle, ctypes.c_void_p(s))
+
+    # ---- status ---------------------------------------------------------
+    def sync_status(self) -> int:
+        f = ctypes.c_uint32(0)
+        st = lib().bd_sync_status(self.handle, ctypes.byref(f))
+        if st not in (BD_OK, BD_ERR_DEVICE_CHECK, BD_ERR_TIMEOUT):
+            self._check(st, "bd_sync_status")
+        return int(f.value)
+
+    def rescued_count(self, reset: bool = False) -> int:
+        c = ctypes.c_uint64(0)
+        self._check(lib().bd_rescued_count(self.handle, ctypes.byref(c), int(reset)), "bd_rescued_count")
+        return int(c.value)
+
+    def reserve(self, nbytes: int):
+        self._check(lib().bd_reserve(self.handle, int(nbytes)), "bd_reserve")
+
+    # ---- parameters -----------------------------------------------------
+    def bad_params(self, p) -> "BadParamsHandle":
+        return BadParamsHandle(self, p)
+
+    def hs_params(self, p, precision: int = BD_HS_BF16_RESCUE, band: float = -1.0) -> "HsParamsHandle":
+        return HsParamsHandle(self, p, precision, band)
+
+    # ---- work -----------------------------------------------------------
+    def integral(self, img, out=None):
+        torch = self._torch
+        h, w = img.shape
+        if out is None:
+            out = torch.empty((h + 1, w + 1), dtype=torch.int32, device=img.device)
+        self._stream()
+        self._check(lib().bd_integral(self.handle, _ptr(img), w, h, img.stride(0), _ptr(out),
+                                      out.stride(0)), "bd_integral")
+        return out
+
+    def bad_describe(self, params, img, kps, out=None):
+        torch = self._torch
+        h, w = img.shape
+        n = kps.shape[0]
+        if out is None:
+            out = torch.empty((n, params.nbits // 32), dtype=torch.int32, device=img.device)
+        self._stream()
+        self._check(lib().bd_bad_describe(self.handle, params.handle, _ptr(img), w, h, img.stride(0),
+                                          _ptr(kps), n, _ptr(out)), "bd_bad_describe")
+        return out
+
+    def hashsift_warp(self, params, img, kps, out=None):
+        torch = self._torch
+        h, w = img.shape
+        n = kps.shape[0]
+        if out is None:
+            out = torch.empty((n, 32, 32), dtype=torch.float32, device=img.device)
+        self._stream()
+        self._check(lib().bd_hashsift_warp(self.handle, params.handle, _ptr(img), w, h, img.stride(0),
+                                           _ptr(kps), n, _ptr(out)), "bd_hashsift_warp")
+        return out
+
+    def hashsift_hist(self, patches, out=None):
+        torch = self._torch
+        n = patches.shape[0]
+        if out is None:
+            out = torch.empty((n, 128), dtype=torch.float32, device=patches.device)
+        self._stream()
+        self._check(lib().bd_hashsift_hist(self.handle, _ptr(patches), n, _ptr(out)), "bd_hashsift_hist")
+        return out
+
+    def hashsift_project(self, params, hist, out=None):
+        torch = self._torch
+        n = hist.shape[0]
+        if out is None:
+            out = torch.empty((n, params.nbits // 32), dtype=torch.int32, device=hist.device)
+        self._stream()
+        self._check(lib().bd_hashsift_project(self.handle, params.handle, _ptr(hist), n, _ptr(out)),
+                    "bd_hashsift_project")
+        return out
+
+    def hashsift_describe(self, params, img, kps, out=None, hist_out=None):
+        torch = self._torch
+        h, w = img.shape
+        n = kps.shape[0]
+        if out is None:
+            out = torch.empty((n, params.nbits // 32), dtype=torch.int32, device=img.device)
+        self._stream()
+        self._check(lib().bd_hashsift_describe(self.handle, params.handle, _ptr(img), w, h,
+                                               img.stride(0), _ptr(kps), n, _ptr(out),
+                                               _ptr(hist_out)), "bd_hashsift_describe")
+        return out
+
+    def match(self, q, t, nbits: int, ratio_num: int = 4, ratio_den: int = 5, out=None):
+        """Returns an int32 [nq, 3] tensor viewing bd_match_result records:
+        column 0 = idx, column 1 = d1 | d2 << 16, column 2 = accept."""
+        torch = self._torch
+        nq, nt = q.shape[0], t.shape[0]
+        if out is None:
+            out = torch.empty((nq, 3), dtype=torch.int32, device=q.device)
+        self._stream()
+        self._check(lib().bd_match(self.handle, _ptr(q), nq, _ptr(t), nt, nbits, ratio_num, ratio_den,
+                                   _ptr(out)), "bd_match")
+        return out
+
+
+def unpack_matches(m):
+    """(idx, d1, d2, accept) numpy arrays from the int32 [nq, 3] result of Context.match."""
+    import numpy as np
+    a = m.cpu().numpy() if hasattr(m, "cpu") else np.asarray(m)
+    a = a.view(np.uint32)
+    return (a[:, 0].view(np.int32).copy(), (a[:, 1] & 0xFFFF).astype(np.int32),
+            (a[:, 1] >> 16).astype(np.int32), (a[:, 2] & 0xFF).astype(np.uint8))
+
+
+class BadParamsHandle:
+    def __init__(self, ctx: Context, p):
+        import numpy as np
+        self.ctx = ctx
+        self.nbits = int(p.nbits)
+        self.nbins = int(p.n_angle_bins)
+        self.nlevels = int(len(p.level_scales))
+        self._keep = [np.ascontiguousarray(p.centres, dtype=np.uint8),
+                      np.ascontiguousarray(p.sides, dtype=np.uint8),
+                      np.ascontiguousarray(p.thr_num, dtype=np.int32),
+                      np.ascontiguousarray(p.level_scales, dtype=np.float32)]
+        c, s, t, ls = self._keep
+        h = ctypes.c_void_p()
+        st = lib().bd_bad_params_create(ctx.handle, self.nbits, _np_ptr(c), _np_ptr(s), _np_ptr(t),
+                                        int(p.thr_den), self.nbins, _np_ptr(ls), self.nlevels,
+                                        ctypes.byref(h))
+        ctx._check(st, "bd_bad_params_create")
+        self.handle = h
+
+    def table(self):
+        import numpy as np
+        off = np.empty((self.nlevels, self.nbins, self.nbits, 2, 2), dtype=np.int32)
+        sides = np.empty((self.nlevels, self.nbits), dtype=np.int32)
+        st = lib().bd_bad_params_table(self.handle, _np_ptr(off), _np_ptr(sides))
+        if st != BD_OK:
+            raise BindescError(st, "bd_bad_params_table")
+        return off, sides
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().bd_bad_params_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+class HsParamsHandle:
+    def __init__(self, ctx: Context, p, precision: int, band: float):
+        import numpy as np
+        self.ctx = ctx
+        self.nbits = int(p.nbits)
+        W = np.ascontiguousarray(p.W, dtype=np.float32)
+        b = np.ascontiguousarray(p.b, dtype=np.float32)
+        h = ctypes.c_void_p()
+        st = lib().bd_hs_params_create(ctx.handle, self.nbits, _np_ptr(W), _np_ptr(b), float(p.spacing),
+                                       int(precision), float(band), ctypes.byref(h))
+        ctx._check(st, "bd_hs_params_create")
+        self.handle = h
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().bd_hs_params_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass

@@ -1,0 +1,302 @@
+// Internal declarations of the sm_103a descriptor library (not part of the ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/bindesc.h"
+
+// ---------------------------------------------------------------------------
+// limits and constants
+// ---------------------------------------------------------------------------
+namespace bd {
+
+constexpr int kPatch = 32;          // patch side (Sec. III-A: 32x32 patches)
+constexpr int kHistDim = 128;       // 4x4 cells x 8 orientation bins
+constexpr int kMaxImageSide = 32767;
+constexpr int kMaxAngleBins = 64;
+constexpr int kMaxLevels = 16;
+constexpr int kMatchIdxBits = 22;   // train index bits in a packed (distance, index) key
+constexpr uint32_t kMatchIdxMask = (1u << kMatchIdxBits) - 1u;
+// bounded spin-waits: iterations before a kernel gives up and raises BD_FLAG_TIMEOUT
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+// integral-image tiling
+constexpr int kIiTileRows = 32;
+constexpr int kIiTileCols = 128;
+
+// device status block: [0] flags (uint32 in a u64 slot), [1] rescued-bit counter
+struct DeviceStatus {
+    unsigned long long flags;
+    unsigned long long rescued;
+};
+
+}  // namespace bd
+
+// ---------------------------------------------------------------------------
+// host-side objects behind the opaque ABI handles
+// ---------------------------------------------------------------------------
+struct bd_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    bd::DeviceStatus *status = nullptr;  // device
+    void *scratch = nullptr;             // device, grows on demand
+    size_t scratch_bytes = 0;
+    std::string err;
+};
+
+struct bd_bad_params {
+    bd_ctx *ctx = nullptr;
+    int nbits = 0, nbins = 0, nlevels = 0;
+    int32_t thr_den = 1;
+    float angle_scale = 0.f;  // float(NB / (2 pi)), applied in IEEE single precision
+    float level_mid[bd::kMaxLevels] = {};  // float(sqrt(s_l s_{l+1}))
+    // host copies (for bd_bad_params_table)
+    int32_t *h_offsets = nullptr;  // [L][NB][K][4] centre offsets
+    int32_t *h_sides = nullptr;    // [L][K]
+    // device tables
+    short4 *d_corner = nullptr;    // [L][NB][K] top-left corner offsets (x1,y1,x2,y2)
+    int2 *d_side_thr = nullptr;    // [L][K] (scaled side, integer threshold on sum1-sum2)
+};
+
+struct bd_hs_params {
+    bd_ctx *ctx = nullptr;
+    int nbits = 0;
+    int precision = BD_HS_FP32;
+    float spacing = 1.f;
+    float *d_W = nullptr;           // [128][K] FP32 (row-major, as given)
+    float *d_Wt = nullptr;          // [K][128] FP32 (per-bit rows, for the FP32 re-check)
+    __nv_bfloat16 *d_Wt16 = nullptr;  // [K][128] BF16 (tensor-core B operand, K-major)
+    float *d_bias = nullptr;        // [K]
+    float *d_band = nullptr;        // [K] rescue band per bit
+    CUtensorMap tmap_w;             // TMA map of d_Wt16, box 64 x 256
+    bool tmap_ok = false;
+};
+
+// ---------------------------------------------------------------------------
+// helpers shared by the .cu files
+// ---------------------------------------------------------------------------
+namespace bd {
+
+bd_status set_err(bd_ctx *ctx, bd_status s, const char *fmt, ...);
+bd_status cuda_err(bd_ctx *ctx, cudaError_t e, const char *what);
+bd_status ensure_scratch(bd_ctx *ctx, size_t bytes);
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// process-wide count of kernels this library has launched (bd_kernel_launches)
+void note_launches(int k);
+
+// TMA descriptor encoding through the driver entry point (no -lcuda needed).
+bool encode_tmap_2d_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
+                         uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer);
+
+// ---------------------------------------------------------------------------
+// kernel launchers (each returns cudaGetLastError() of its launch)
+// ---------------------------------------------------------------------------
+struct IntegralScratch {
+    uint32_t *colsum;   // [nty][w]
+    uint32_t *rowsum;   // [h][ntx]
+    uint32_t *tiletot;  // [nty][ntx]
+};
+size_t integral_scratch_bytes(int w, int h);
+IntegralScratch integral_scratch_carve(void *base, int w, int h);
+cudaError_t launch_integral(const uint8_t *img, int w, int h, int pitch, uint32_t *ii,
+                            int ii_stride, const IntegralScratch &s, cudaStream_t st);
+
+cudaError_t launch_bad_gather(const bd_bad_params *p, const uint32_t *ii, int ii_stride, int w,
+                              int h, const bd_keypoint *kps, int n, uint32_t *out,
+                              DeviceStatus *status, cudaStream_t st);
+
+cudaError_t launch_hs_warp(const bd_hs_params *p, const uint8_t *img, int w, int h, int pitch,
+                           const bd_keypoint *kps, int n, float *patches, DeviceStatus *status,
+                           cudaStream_t st, int sm_count);
+cudaError_t launch_hs_hist_patches(const float *patches, int n, float *hist,
+                                   __nv_bfloat16 *hist16, cudaStream_t st, int sm_count);
+cudaError_t launch_hs_hist_image(const bd_hs_params *p, const uint8_t *img, int w, int h, int pitch,
+                                 const bd_keypoint *kps, int n, float *hist,
+                                 __nv_bfloat16 *hist16, DeviceStatus *status, cudaStream_t st,
+                                 int sm_count);
+cudaError_t launch_hs_to_bf16(const float *hist, int n, __nv_bfloat16 *hist16, cudaStream_t st);
+cudaError_t launch_hs_proj_fp32(const bd_hs_params *p, const float *hist, int n, uint32_t *out,
+                                cudaStream_t st, const bd_keypoint *kps);
+cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const CUtensorMap &tmap_hist,
+                              const float *hist, int n, uint32_t *out, DeviceStatus *status,
+                              cudaStream_t st, const bd_keypoint *kps);
+
+size_t match_scratch_bytes(int nq, int nt, int nbits, int sm_count);
+cudaError_t launch_match(const uint32_t *q, int nq, const uint32_t *t, int nt, int nbits,
+                         int ratio_num, int ratio_den, bd_match_result *out, void *scratch,
+                         int sm_count, cudaStream_t st);
+
+}  // namespace bd
+
+// ---------------------------------------------------------------------------
+// device-side PTX helpers (sm_100 family: mbarrier, TMA, tcgen05)
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace bd {
+namespace dev {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void raise_flag(DeviceStatus *st, unsigned long long f)
+{
+    if (st)
+        atomicOr(&st->flags, f);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase with the given parity; gives up after kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity))
+            return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *map, int c0, int c1,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *smem_slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(smem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor for a K-major operand stored in the 128-byte
+// swizzled layout TMA writes (rows of 128 B, 8-row groups 1024 B apart).
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                    // leading byte offset (unused when swizzled)
+    d |= (uint64_t)(1024u >> 4) << 32;         // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::f16 with BF16 A and B, FP32 accumulator,
+// both operands K-major, M x N tile.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16_f32(int M, int N)
+{
+    return (1u << 4)                       // D format: F32
+           | (1u << 7)                     // A format: BF16
+           | (1u << 10)                    // B format: BF16
+           | ((uint32_t)(N >> 3) << 17)    // N / 8
+           | ((uint32_t)(M >> 4) << 24);   // M / 16
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit TMEM columns: thread t of the warp gets
+// lane (warp's lane base + t), columns [col, col+32).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Keypoint validity and quantisation, in IEEE single precision with explicit
+// round-to-nearest intrinsics so no multiply-add is contracted.
+__device__ __forceinline__ bool kp_valid(const bd_keypoint &k)
+{
+    const float lim = 1048576.0f;
+    if (!isfinite(k.x) || !isfinite(k.y) || !isfinite(k.scale) || !isfinite(k.angle))
+        return false;
+    if (fabsf(k.x) > lim || fabsf(k.y) > lim || fabsf(k.angle) > lim)
+        return false;
+    return k.scale > 0.0f && k.scale <= 1024.0f;
+}
+
+__device__ __forceinline__ int round_coord(float v) { return (int)floorf(__fadd_rn(v, 0.5f)); }
+
+}  // namespace dev
+}  // namespace bd
+#endif

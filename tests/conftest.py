@@ -17,3 +17,16 @@ def pytest_configure(config):
 def oracle_lib():
     import oracle
     return oracle.lib()
+
+
+@pytest.fixture(scope="session")
+def gpu_ctx():
+    """A bd_ctx on cuda:0 (GPU tests only)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2108_08380_gb300 as bd
+    ctx = bd.Context(0)
+    yield ctx
+    torch.cuda.synchronize()
+    ctx.close()

@@ -1,0 +1,98 @@
+"""GPU parity of brute-force Hamming matching with fused top-2 and ratio test
+against the CPU oracle: bit-exact index, distances and verdict (Sec. IV-C)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+
+
+def _rand_desc(rng, n, K):
+    return rng.integers(0, 2 ** 32, size=(n, K // 32), dtype=np.uint64).astype(np.uint32)
+
+
+def _noisy(rng, d, K, flips):
+    """Copies of descriptors with `flips` random bits flipped each."""
+    out = d.copy()
+    bits = np.unpackbits(out.view(np.uint8), axis=1, bitorder="little")
+    for i in range(bits.shape[0]):
+        bits[i, rng.choice(K, size=flips, replace=False)] ^= 1
+    return np.packbits(bits, axis=1, bitorder="little").view(np.uint32)
+
+
+def _check(ctx, q, t, K, rnum=4, rden=5, rows=None):
+    import paper_2108_08380_gb300 as bd
+    m = ctx.match(_dev(q), _dev(t), K, rnum, rden)
+    idx, d1, d2, acc = bd.unpack_matches(m)
+    if rows is None:
+        rows = np.arange(q.shape[0])
+    ri, r1, r2, ra = oracle.match(q[rows], t, K, rnum, rden)
+    assert np.array_equal(idx[rows], ri)
+    assert np.array_equal(d1[rows], r1)
+    assert np.array_equal(d2[rows], r2)
+    assert np.array_equal(acc[rows], ra)
+    return idx, d1, d2, acc
+
+
+@pytest.mark.parametrize("K,nq,nt", [(256, 1000, 1000), (512, 1000, 1000), (256, 333, 777),
+                                     (512, 129, 4099), (256, 5000, 3), (256, 1, 1), (512, 7, 0),
+                                     (256, 300, 1), (512, 2, 2)])
+def test_match_random_exact(gpu_ctx, K, nq, nt):
+    rng = np.random.default_rng(K + 31 * nq + nt)
+    t = _rand_desc(rng, nt, K)
+    q = _rand_desc(rng, nq, K)
+    if nt:
+        pick = rng.integers(0, nt, size=nq)
+        q[: nq // 2] = _noisy(rng, t[pick[: nq // 2]], K, K // 8)
+    _check(gpu_ctx, q, t, K)
+
+
+def test_match_ties_lowest_index(gpu_ctx):
+    K = 256
+    rng = np.random.default_rng(3)
+    base = _rand_desc(rng, 50, K)
+    t = np.concatenate([base, base, base[::-1]])  # every entry three times
+    q = _noisy(rng, base, K, 3)
+    idx, d1, d2, acc = _check(gpu_ctx, q, t, K)
+    assert np.all(d1 == d2) and not acc.any()
+    assert np.all(idx < 50)
+
+
+def test_match_bad_descriptors_of_noisy_pair(gpu_ctx):
+    """Plain workload: BAD-256 of image A against image B = A + N(0,5)."""
+    wl = synth.plain_workload(1000)
+    qa, _ = oracle.bad_describe(wl.img_a, wl.kps_a, wl.bad)
+    tb, _ = oracle.bad_describe(wl.img_b, wl.kps_b, wl.bad)
+    idx, d1, d2, acc = _check(gpu_ctx, qa, tb, 256)
+    assert (idx == np.arange(1000)).mean() > 0.5  # most keypoints find themselves
+
+
+@pytest.mark.parametrize("K", [256, 512])
+def test_match_full_size_sampled(gpu_ctx, K):
+    """20000 x 20000 in the launch configuration of the large workload; a
+    seeded sample of 400 queries checked against the oracle."""
+    rng = np.random.default_rng(K)
+    n = 20000
+    t = _rand_desc(rng, n, K)
+    perm = rng.permutation(n)
+    q = _noisy(rng, t[perm], K, K // 10)
+    rows = np.sort(rng.choice(n, size=400, replace=False))
+    idx, d1, d2, acc = _check(gpu_ctx, q, t, K, rows=rows)
+    assert np.array_equal(idx[rows], perm[rows])
+
+
+def test_match_rejects_bad_arguments(gpu_ctx):
+    import paper_2108_08380_gb300 as bd
+    rng = np.random.default_rng(0)
+    q = _dev(_rand_desc(rng, 4, 256))
+    with pytest.raises(bd.BindescError):
+        gpu_ctx.match(q, q, 300)
+    with pytest.raises(bd.BindescError):
+        gpu_ctx.match(q, q, 256, 6, 5)
