@@ -193,12 +193,14 @@ bd_status bd_hashsift_warp(bd_ctx *ctx, const bd_hs_params *p, const uint8_t *im
 bd_status bd_hashsift_hist(bd_ctx *ctx, const float *patches, int n, float *hist);
 
 /* Hash bits D = sgn(W^T f + b) (Sec. III-B) of n FP32 histograms (n x 128):
- * out is n x nbits/32 words.  Uses the precision chosen in p. */
+ * out is n x nbits/32 words.  Uses the precision chosen in p; the BF16 path
+ * needs hist 16-byte aligned. */
 bd_status bd_hashsift_project(bd_ctx *ctx, const bd_hs_params *p, const float *hist, int n,
                               uint32_t *out);
 
 /* Whole HashSIFT descriptor of n keypoints: warp + histogram fused in one
- * kernel, then the projection.  hist_out (n x 128 floats) may be NULL. */
+ * kernel, then the projection.  hist_out (n x 128 floats, 16-byte aligned)
+ * may be NULL. */
 bd_status bd_hashsift_describe(bd_ctx *ctx, const bd_hs_params *p, const uint8_t *img, int w,
                                int h, int pitch, const bd_keypoint *kps, int n, uint32_t *out,
                                float *hist_out);
@@ -207,7 +209,8 @@ bd_status bd_hashsift_describe(bd_ctx *ctx, const bd_hs_params *p, const uint8_t
  * nq query descriptors, the nearest train descriptor (lowest index among
  * equal distances), its distance d1, the second-smallest distance d2 over
  * the remaining train entries, and accept = ratio_den*d1 < ratio_num*d2.
- * q: nq x nbits/32 words; t: nt x nbits/32 words; out: nq entries.
+ * q: nq x nbits/32 words; t: nt x nbits/32 words (both 16-byte aligned);
+ * out: nq entries (4-byte aligned).
  * nbits 256 or 512; 0 <= nt < 2^22; 0 < ratio_num <= ratio_den. */
 bd_status bd_match(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt, int nbits,
                    int ratio_num, int ratio_den, bd_match_result *out);

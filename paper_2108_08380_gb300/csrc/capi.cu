@@ -585,6 +585,8 @@ bd_status bd_hashsift_project(bd_ctx *ctx, const bd_hs_params *p, const float *h
     if (n == 0)
         return BD_OK;
     __nv_bfloat16 *h16 = nullptr;
+    if (p->precision == BD_HS_BF16_RESCUE && ((uintptr_t)hist & 15))
+        return set_err(ctx, BD_ERR_INVALID, "bd_hashsift_project: hist must be 16-byte aligned");
     if (p->precision == BD_HS_BF16_RESCUE) {
         bd_status s = ensure_scratch(ctx, align_up((size_t)n * 256, 256));
         if (s != BD_OK)
@@ -601,6 +603,8 @@ bd_status bd_hashsift_describe(bd_ctx *ctx, const bd_hs_params *p, const uint8_t
     BD_GUARD(ctx);
     if (!p || !img || !image_ok(w, h, pitch) || n < 0 || (n > 0 && (!kps || !out)))
         return set_err(ctx, BD_ERR_INVALID, "bd_hashsift_describe: bad arguments");
+    if (hist_out && ((uintptr_t)hist_out & 15))
+        return set_err(ctx, BD_ERR_INVALID, "bd_hashsift_describe: hist_out must be 16-byte aligned");
     if (n == 0)
         return BD_OK;
     bd_status s = ensure_scratch(ctx, bd_scratch_bytes_hashsift(n));
@@ -621,8 +625,9 @@ bd_status bd_match(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, in
                    int ratio_num, int ratio_den, bd_match_result *out)
 {
     BD_GUARD(ctx);
-    if (((uintptr_t)q & 15) || ((uintptr_t)t & 15))
-        return set_err(ctx, BD_ERR_INVALID, "bd_match: descriptor arrays must be 16-byte aligned");
+    if (((uintptr_t)q & 15) || ((uintptr_t)t & 15) || ((uintptr_t)out & 3))
+        return set_err(ctx, BD_ERR_INVALID,
+                       "bd_match: descriptor arrays must be 16-byte and out 4-byte aligned");
     if ((nbits != 256 && nbits != 512) || nq < 0 || nt < 0 || nt > (int)kMatchIdxMask ||
         ratio_den <= 0 || ratio_num <= 0 || ratio_num > ratio_den || (nq > 0 && (!q || !out)) ||
         (nt > 0 && !t))

@@ -148,10 +148,10 @@ __global__ void __launch_bounds__(128) hs_proj_tc_kernel(
         if (t == 0 && rescued)
             atomicAdd(&status->rescued, rescued);
         if (kp < n) {
-            uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)kp * (K / 32) + n0 / 32);
-            const uint4 *src = reinterpret_cast<const uint4 *>(out_tile + row * 8);
-            dst[0] = src[0];
-            dst[1] = src[1];
+            uint32_t *dst = out + (size_t)kp * (K / 32) + n0 / 32;
+#pragma unroll
+            for (int c = 0; c < BN / 32; ++c)
+                dst[c] = out_tile[row * 8 + c];
         }
     } else if (t == 0) {
         dev::raise_flag(status, BD_FLAG_TIMEOUT);
