@@ -150,7 +150,7 @@ bd_status bd_bad_params_table(const bd_bad_params *p, int32_t *offsets, int32_t 
 /* HashSIFT parameters (Sec. III-B)                                          */
 
 #define BD_HS_FP32 0        /* projection on CUDA cores in FP32 */
-#define BD_HS_BF16_RESCUE 1 /* tcgen05 BF16 x BF16 -> FP32, FP32 re-check near 0 */
+#define BD_HS_BF16_RESCUE 1 /* tcgen05 BF16 x BF16 -> FP32 (split head/tail), FP32 re-check near 0 */
 
 /* Learned hash B = [W^T | b], copied from host memory.
  *  nbits     256 or 512.
@@ -158,11 +158,14 @@ bd_status bd_bad_params_table(const bd_bad_params *p, int32_t *offsets, int32_t 
  *  bias      host, nbits float (the last column of B).
  *  spacing   patch pixel step in units of the keypoint scale (> 0, <= 16).
  *  precision BD_HS_FP32 or BD_HS_BF16_RESCUE.
- *  band      BF16 mode: bits whose BF16 margin |W_k.f + b_k| is below the
- *            band are recomputed in FP32.  band < 0 selects the per-bit bound
- *            (2^-7 + 2^-16 + 129*2^-23 + 2e-4) * ||W_k||_2, which covers the
- *            BF16 rounding of f and W for unit-norm f; band >= 0 is used as
- *            given for every bit. */
+ *  band      BF16 mode: f and W are split into BF16 head + tail and the
+ *            tensor cores accumulate f_hi W_hi + f_lo W_hi + f_hi W_lo in FP32;
+ *            bits whose margin |W_k.f + b_k| falls below the band are
+ *            recomputed in FP32 exactly as the FP32 mode computes them.
+ *            band < 0 selects the per-bit bound 2^-13 * ||W_k||_2, which covers
+ *            the split's rounding and both FP32 accumulations for unit-norm f,
+ *            so the two modes give identical bits; band >= 0 is used as given
+ *            for every bit (a smaller band may differ from FP32 mode). */
 bd_status bd_hs_params_create(bd_ctx *ctx, int nbits, const float *W, const float *bias,
                               float spacing, int precision, float band, bd_hs_params **out);
 void bd_hs_params_destroy(bd_hs_params *p);

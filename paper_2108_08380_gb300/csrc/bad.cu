@@ -24,7 +24,7 @@ __device__ __forceinline__ uint32_t box_sum(const uint32_t *__restrict__ ii, int
 }
 
 template <int NW>
-__global__ void __launch_bounds__(256) bad_gather_kernel(
+__global__ void __launch_bounds__(256, 2) bad_gather_kernel(
     const short4 *__restrict__ corner, const int2 *__restrict__ side_thr, int nbins, int nlevels,
     float angle_scale, LevelMids mids, const uint32_t *__restrict__ ii, int stride, int w, int h,
     const bd_keypoint *__restrict__ kps, int n, uint32_t *__restrict__ out, DeviceStatus *status)
@@ -53,17 +53,27 @@ __global__ void __launch_bounds__(256) bad_gather_kernel(
         const short4 *tab = corner + ((size_t)l * nbins + b) * K;
         const int2 *st = side_thr + (size_t)l * K;
         uint32_t mine = 0;
-#pragma unroll 4
-        for (int j = 0; j < NW; ++j) {
-            const int k = j * 32 + lane;
-            const short4 c = __ldg(tab + k);
-            const int2 s = __ldg(st + k);
-            const uint32_t s1 = box_sum(ii, stride, w, h, ix + c.x, iy + c.y, s.x);
-            const uint32_t s2 = box_sum(ii, stride, w, h, ix + c.z, iy + c.w, s.x);
-            const bool bit = ((int)s1 - (int)s2) <= s.y;
-            const uint32_t word = __ballot_sync(0xffffffffu, bit);
-            if (lane == j)
-                mine = word;
+        // all of a group's table reads first, then all its gathers: the warp keeps
+        // 8 * 8 independent loads in flight instead of walking the bits in series
+        constexpr int G = NW < 8 ? NW : 8;
+#pragma unroll 1
+        for (int j0 = 0; j0 < NW; j0 += G) {
+            short4 c[G];
+            int2 s[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                c[g] = __ldg(tab + (j0 + g) * 32 + lane);
+                s[g] = __ldg(st + (j0 + g) * 32 + lane);
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const uint32_t s1 = box_sum(ii, stride, w, h, ix + c[g].x, iy + c[g].y, s[g].x);
+                const uint32_t s2 = box_sum(ii, stride, w, h, ix + c[g].z, iy + c[g].w, s[g].x);
+                const bool bit = ((int)s1 - (int)s2) <= s[g].y;
+                const uint32_t word = __ballot_sync(0xffffffffu, bit);
+                if (lane == j0 + g)
+                    mine = word;
+            }
         }
         if (lane < NW)
             out[(size_t)i * NW + lane] = mine;

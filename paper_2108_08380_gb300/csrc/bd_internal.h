@@ -71,10 +71,12 @@ struct bd_hs_params {
     float spacing = 1.f;
     float *d_W = nullptr;           // [128][K] FP32 (row-major, as given)
     float *d_Wt = nullptr;          // [K][128] FP32 (per-bit rows, for the FP32 re-check)
-    __nv_bfloat16 *d_Wt16 = nullptr;  // [K][128] BF16 (tensor-core B operand, K-major)
+    __nv_bfloat16 *d_Wt16_hi = nullptr;  // [K][128] BF16 head of W^T (tensor-core B operand, K-major)
+    __nv_bfloat16 *d_Wt16_lo = nullptr;  // [K][128] BF16 tail: W - hi rounded to BF16
+    bool w_has_lo = false;               // false when W is exactly BF16
     float *d_bias = nullptr;        // [K]
     float *d_band = nullptr;        // [K] rescue band per bit
-    CUtensorMap tmap_w;             // TMA map of d_Wt16, box 64 x 256
+    CUtensorMap tmap_w_hi, tmap_w_lo;  // TMA maps of the two BF16 parts, box 64 x 128
     bool tmap_ok = false;
 };
 
@@ -116,6 +118,7 @@ cudaError_t launch_bad_gather(const bd_bad_params *p, const uint32_t *ii, int ii
 cudaError_t launch_hs_warp(const bd_hs_params *p, const uint8_t *img, int w, int h, int pitch,
                            const bd_keypoint *kps, int n, float *patches, DeviceStatus *status,
                            cudaStream_t st, int sm_count);
+// hist16 (nullable) receives the BF16 head [n][128] followed by the BF16 tail [n][128]
 cudaError_t launch_hs_hist_patches(const float *patches, int n, float *hist,
                                    __nv_bfloat16 *hist16, cudaStream_t st, int sm_count);
 cudaError_t launch_hs_hist_image(const bd_hs_params *p, const uint8_t *img, int w, int h, int pitch,
@@ -125,9 +128,9 @@ cudaError_t launch_hs_hist_image(const bd_hs_params *p, const uint8_t *img, int 
 cudaError_t launch_hs_to_bf16(const float *hist, int n, __nv_bfloat16 *hist16, cudaStream_t st);
 cudaError_t launch_hs_proj_fp32(const bd_hs_params *p, const float *hist, int n, uint32_t *out,
                                 cudaStream_t st, const bd_keypoint *kps);
-cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const CUtensorMap &tmap_hist,
-                              const float *hist, int n, uint32_t *out, DeviceStatus *status,
-                              cudaStream_t st, const bd_keypoint *kps);
+cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const CUtensorMap &tm_hi,
+                              const CUtensorMap &tm_lo, const float *hist, int n, uint32_t *out,
+                              DeviceStatus *status, cudaStream_t st, const bd_keypoint *kps);
 
 size_t match_scratch_bytes(int nq, int nt, int nbits, int sm_count);
 cudaError_t launch_match(const uint32_t *q, int nq, const uint32_t *t, int nt, int nbits,

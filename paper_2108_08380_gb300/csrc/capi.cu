@@ -262,7 +262,7 @@ size_t bd_scratch_bytes_hashsift(int n)
 {
     if (n < 0)
         return 0;
-    return align_up((size_t)n * kHistDim * 4, 256) + align_up((size_t)n * kHistDim * 2, 256);
+    return align_up((size_t)n * kHistDim * 4, 256) + align_up((size_t)n * kHistDim * 4, 256);
 }
 
 size_t bd_scratch_bytes_match(int nq, int nt, int nbits)
@@ -436,35 +436,47 @@ bd_status bd_hs_params_create(bd_ctx *ctx, int nbits, const float *W, const floa
     p->precision = precision;
     p->spacing = spacing;
     std::vector<float> Wt((size_t)K * 128), bnd(K);
-    std::vector<__nv_bfloat16> Wt16((size_t)K * 128);
+    std::vector<__nv_bfloat16> Whi((size_t)K * 128), Wlo((size_t)K * 128);
+    bool has_lo = false;
     for (int k = 0; k < K; ++k) {
         double nn = 0.0;
         for (int i = 0; i < 128; ++i) {
             const float v = W[(size_t)i * K + k];
             Wt[(size_t)k * 128 + i] = v;
-            Wt16[(size_t)k * 128 + i] = __float2bfloat16_rn(v);
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+            Whi[(size_t)k * 128 + i] = hi;
+            Wlo[(size_t)k * 128 + i] = lo;
+            has_lo = has_lo || __bfloat162float(lo) != 0.0f;
             nn += (double)v * (double)v;
         }
-        // |m_bf16 - m_fp32| <= (2u + u^2 + 129*2^-23)||W_k|| ||f|| with u = 2^-8 and
-        // ||f|| = 1, plus 2e-4||W_k|| for the FP32 histogram's own error.
-        const double c = ldexp(1.0, -7) + ldexp(1.0, -16) + 129.0 * ldexp(1.0, -23) + 2e-4;
+        // With x = hi + lo + d, |d| <= 2^-16 |x| (two BF16 roundings), the three
+        // products hi*hi + lo*hi + hi*lo miss |W||f| by at most 3*2^-16 + O(2^-24);
+        // FP32 accumulation of 384 products adds <= 384*2^-24, the FP32 path's own
+        // 128-term rounding <= 128*2^-24.  All of it, times ||W_k||_2 ||f||_2
+        // (||f|| = 1), stays below 2^-13 ||W_k||_2.
+        const double c = ldexp(1.0, -13);
         bnd[k] = band < 0.f ? (float)(c * sqrt(nn)) : band;
     }
+    p->w_has_lo = has_lo;
     cudaError_t e = cudaMalloc(&p->d_W, sizeof(float) * 128 * K);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_Wt, sizeof(float) * 128 * K);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_Wt16, sizeof(__nv_bfloat16) * 128 * K);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_Wt16_hi, sizeof(__nv_bfloat16) * 128 * K);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_Wt16_lo, sizeof(__nv_bfloat16) * 128 * K);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_bias, sizeof(float) * K);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_band, sizeof(float) * K);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_W, W, sizeof(float) * 128 * K, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_Wt, Wt.data(), sizeof(float) * 128 * K, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(p->d_Wt16, Wt16.data(), sizeof(__nv_bfloat16) * 128 * K, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_Wt16_hi, Whi.data(), sizeof(__nv_bfloat16) * 128 * K, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_Wt16_lo, Wlo.data(), sizeof(__nv_bfloat16) * 128 * K, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_bias, bias, sizeof(float) * K, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_band, bnd.data(), sizeof(float) * K, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         bd_hs_params_destroy(p);
         return cuda_err(ctx, e, "bd_hs_params_create: upload");
     }
-    p->tmap_ok = encode_tmap_2d_bf16(&p->tmap_w, p->d_Wt16, 128, (uint64_t)K, 256, 64, 256);
+    p->tmap_ok = encode_tmap_2d_bf16(&p->tmap_w_hi, p->d_Wt16_hi, 128, (uint64_t)K, 256, 64, 128) &&
+                 encode_tmap_2d_bf16(&p->tmap_w_lo, p->d_Wt16_lo, 128, (uint64_t)K, 256, 64, 128);
     if (precision == BD_HS_BF16_RESCUE && !p->tmap_ok) {
         bd_hs_params_destroy(p);
         return set_err(ctx, BD_ERR_UNSUPPORTED, "cannot encode the TMA descriptor of W");
@@ -480,7 +492,8 @@ void bd_hs_params_destroy(bd_hs_params *p)
     DeviceGuard g(p->ctx->device);
     if (p->d_W) cudaFree(p->d_W);
     if (p->d_Wt) cudaFree(p->d_Wt);
-    if (p->d_Wt16) cudaFree(p->d_Wt16);
+    if (p->d_Wt16_hi) cudaFree(p->d_Wt16_hi);
+    if (p->d_Wt16_lo) cudaFree(p->d_Wt16_lo);
     if (p->d_bias) cudaFree(p->d_bias);
     if (p->d_band) cudaFree(p->d_band);
     delete p;
@@ -568,10 +581,11 @@ static bd_status project(bd_ctx *ctx, const bd_hs_params *p, const float *hist,
     }
     if (need_convert)
         BD_LAUNCH(ctx, launch_hs_to_bf16(hist, n, hist16, ctx->stream), "BF16 conversion kernel");
-    CUtensorMap tm;
-    if (!encode_tmap_2d_bf16(&tm, hist16, 128, (uint64_t)n, 256, 64, 128))
-        return set_err(ctx, BD_ERR_CUDA, "cannot encode the TMA descriptor of the histograms");
-    BD_LAUNCH(ctx, launch_hs_proj_tc(p, tm, hist, n, out, ctx->status, ctx->stream, kps),
+    CUtensorMap tm_hi, tm_lo;
+    if (!encode_tmap_2d_bf16(&tm_hi, hist16, 128, (uint64_t)n, 256, 64, 128) ||
+        !encode_tmap_2d_bf16(&tm_lo, hist16 + (size_t)n * kHistDim, 128, (uint64_t)n, 256, 64, 128))
+        return set_err(ctx, BD_ERR_CUDA, "cannot encode the TMA descriptors of the histograms");
+    BD_LAUNCH(ctx, launch_hs_proj_tc(p, tm_hi, tm_lo, hist, n, out, ctx->status, ctx->stream, kps),
               "tcgen05 projection kernel");
     return BD_OK;
 }
@@ -588,7 +602,7 @@ bd_status bd_hashsift_project(bd_ctx *ctx, const bd_hs_params *p, const float *h
     if (p->precision == BD_HS_BF16_RESCUE && ((uintptr_t)hist & 15))
         return set_err(ctx, BD_ERR_INVALID, "bd_hashsift_project: hist must be 16-byte aligned");
     if (p->precision == BD_HS_BF16_RESCUE) {
-        bd_status s = ensure_scratch(ctx, align_up((size_t)n * 256, 256));
+        bd_status s = ensure_scratch(ctx, align_up((size_t)n * 512, 256));
         if (s != BD_OK)
             return s;
         h16 = (__nv_bfloat16 *)ctx->scratch;

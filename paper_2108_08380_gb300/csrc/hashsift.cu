@@ -126,7 +126,7 @@ __device__ __forceinline__ void vote(HistSmem &S, const HistLane &L, int t)
 
 // Sum of the cell's 8 private columns for bin t%8, L2 norm, output.
 __device__ __forceinline__ void finish(HistSmem &S, int t, bool valid, float *__restrict__ hist,
-                                       __nv_bfloat16 *__restrict__ hist16, size_t kp)
+                                       __nv_bfloat16 *__restrict__ hist16, size_t kp, size_t nkp)
 {
     const int cell = t >> 3, b = t & 7;
     float H = 0.0f;
@@ -144,8 +144,11 @@ __device__ __forceinline__ void finish(HistSmem &S, int t, bool valid, float *__
     const float nrm = sqrtf(tot);
     const float h = (valid && nrm > 0.0f) ? H / nrm : 0.0f;
     hist[kp * kHistDim + t] = h;
-    if (hist16)
-        hist16[kp * kHistDim + t] = __float2bfloat16_rn(h);
+    if (hist16) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(h);
+        hist16[kp * kHistDim + t] = hi;
+        hist16[(nkp + kp) * kHistDim + t] = __float2bfloat16_rn(h - __bfloat162float(hi));
+    }
 }
 
 __global__ void __launch_bounds__(NT) hs_hist_image_kernel(
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(NT) hs_hist_image_kernel(
         if (valid)
             vote(S, L, t);
         __syncthreads();
-        finish(S, t, valid, hist, hist16, (size_t)k);
+        finish(S, t, valid, hist, hist16, (size_t)k, (size_t)n);
     }
 }
 
@@ -200,7 +203,7 @@ __global__ void __launch_bounds__(NT) hs_hist_patch_kernel(const float *__restri
         __syncthreads();
         vote(S, L, t);
         __syncthreads();
-        finish(S, t, true, hist, hist16, (size_t)k);
+        finish(S, t, true, hist, hist16, (size_t)k, (size_t)n);
     }
 }
 
@@ -234,8 +237,12 @@ __global__ void hs_to_bf16_kernel(const float *__restrict__ src, size_t count,
                                   __nv_bfloat16 *__restrict__ dst)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
-         i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = __float2bfloat16_rn(src[i]);
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float v = src[i];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        dst[i] = hi;
+        dst[count + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -91,12 +91,15 @@ __global__ void __launch_bounds__(TC) ii_final_kernel(const uint8_t *__restrict_
 
     // column sums of all bands above this one
     uint32_t v = 0;
-    if (x < w)
+    if (x < w) {
+#pragma unroll 8
         for (int a = 0; a < ty; ++a)
             v += __ldg(colsum + (size_t)a * w + x);
+    }
     // total of the tiles above-left
     uint32_t g = 0;
     const int nab = ty * tx;
+#pragma unroll 4
     for (int i = t; i < nab; i += TC)
         g += __ldg(tiletot + (size_t)(i / tx) * ntx + (i % tx));
     g = warp_sum(g);
@@ -110,9 +113,11 @@ __global__ void __launch_bounds__(TC) ii_final_kernel(const uint8_t *__restrict_
     if (wp == 0) {
         uint32_t r = 0;
         const int y = y0 + lane;
-        if (y < h)
+        if (y < h) {
+#pragma unroll 8
             for (int a = 0; a < tx; ++a)
                 r += __ldg(rowsum + (size_t)y * ntx + a);
+        }
         R[lane] = r;
     }
     __syncthreads();

@@ -99,6 +99,7 @@ __global__ void match_merge_kernel(const uint2 *__restrict__ partial, int nq, in
     if (qi >= nq)
         return;
     uint2 a = partial[qi];
+#pragma unroll 8
     for (int s = 1; s < S; ++s) {
         const uint2 b = partial[(size_t)s * nq + qi];
         const uint32_t k1 = min(a.x, b.x);
@@ -111,9 +112,9 @@ __global__ void match_merge_kernel(const uint2 *__restrict__ partial, int nq, in
 void plan(int nq, int nt, int sm_count, int &S, int &chunk)
 {
     const int qblocks = (nq + QB - 1) / QB;
-    const int target = 4 * sm_count;
+    const int target = 8 * sm_count;
     S = (target + qblocks - 1) / qblocks;
-    const int max_split = (nt + 63) / 64;
+    const int max_split = (nt + 31) / 32;
     if (S > max_split)
         S = max_split;
     if (S < 1)

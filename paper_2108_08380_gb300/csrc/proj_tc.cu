@@ -2,16 +2,21 @@
 // cores: the projection is a dense 128-deep contraction, so it runs as
 // tcgen05.mma kind::f16 with BF16 operands and an FP32 accumulator in TMEM.
 //
-// CTA = 128 threads, tile = 128 keypoints x 256 bits.
-//  - thread 0 loads the two operand tiles with TMA (128-byte swizzle, two
-//    64-wide K chunks each), then issues 8 MMAs of K = 16 and commits them to
-//    an mbarrier;
-//  - each warp reads its 32 TMEM lanes (= keypoints) back 32 columns at a
-//    time, adds the FP32 bias and takes the sign;
-//  - every bit whose BF16 margin lies inside the band |m| < band_k is queued
-//    and recomputed from the FP32 histogram and FP32 W (same accumulation
-//    order as the FP32 projection kernel, so the two paths agree bit for bit
-//    whenever the band bounds the BF16 error).
+// Precision: f and W are each split into a BF16 head and a BF16 tail
+// (x = hi + lo + O(2^-16 |x|)); three MMAs accumulate f_hi W_hi + f_lo W_hi +
+// f_hi W_lo in FP32 (the third is skipped when W is exactly BF16).  The
+// margin is then within ~8e-5 ||W_k|| of the exact one, so only bits with
+// |m| below the band (default 2^-13 ||W_k||_2) are queued and recomputed from
+// the FP32 histogram and FP32 W, in the FP32 projection kernel's order: the
+// result equals the FP32 path bit for bit.
+//
+// CTA = 128 threads, tile = 128 keypoints x 128 bits, K = 128 in two 64-wide
+// phases through one 64 KB shared-memory stage (three CTAs fit on an SM):
+//  - thread 0 loads the phase's four operand tiles with TMA (128-byte
+//    swizzle) and issues 4 x (2 or 3) MMAs of K = 16, committed to an mbarrier;
+//  - each warp then reads its 32 TMEM lanes (= keypoints) back, 32 columns at
+//    a time, adds the FP32 bias, takes the sign, queues the band bits, and the
+//    CTA re-evaluates the queue in FP32.
 // Waits on mbarriers are bounded; on a timeout the CTA raises
 // BD_FLAG_TIMEOUT, waits once more for its MMAs, frees TMEM and returns.
 #include "bd_internal.h"
@@ -20,14 +25,16 @@ namespace bd {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BN = 256;
-constexpr int A_CHUNK = BM * 128;       // bytes of one 64-wide BF16 K chunk of A
-constexpr int B_CHUNK = BN * 128;       // ... of B
-constexpr int TILE_BYTES = 2 * A_CHUNK + 2 * B_CHUNK;  // 98304
-constexpr int SMEM_BYTES = TILE_BYTES + 1024;           // + alignment slack
+constexpr int BN = 128;
+constexpr int TILE = BM * 128;             // bytes of one 64-wide BF16 K chunk of a 128-row operand
+constexpr int STAGE_BYTES = 4 * TILE;      // A_hi, A_lo, B_hi, B_lo
+constexpr int SMEM_BYTES = STAGE_BYTES + 1024;
+constexpr int RB = 28;                     // FP32 re-checks staged per round (1 KB each)
+static_assert(2048 + 2 * BM * BN + RB * 1024 <= STAGE_BYTES, "epilogue does not fit the stage");
 
 __global__ void __launch_bounds__(128) hs_proj_tc_kernel(
-    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+    const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int w_has_lo,
     const float *__restrict__ hist32, const float *__restrict__ Wt32,
     const float *__restrict__ bias, const float *__restrict__ band,
     const bd_keypoint *__restrict__ kps, int n, int K, uint32_t *__restrict__ out,
@@ -36,12 +43,11 @@ __global__ void __launch_bounds__(128) hs_proj_tc_kernel(
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *sA = smem;
-    uint8_t *sB = smem + 2 * A_CHUNK;
-    __shared__ uint64_t bar_tma, bar_mma;
+    uint8_t *sAh = smem, *sAl = smem + TILE, *sBh = smem + 2 * TILE, *sBl = smem + 3 * TILE;
+    __shared__ uint64_t bar_tma, bar_mma0, bar_mma1;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
-    __shared__ int list_n[BN / 32];
+    __shared__ int list_n;
     __shared__ float bias_s[BN], band_s[BN];
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -49,15 +55,16 @@ __global__ void __launch_bounds__(128) hs_proj_tc_kernel(
 
     if (t == 0) {
         dev::mbar_init(&bar_tma, 1);
-        dev::mbar_init(&bar_mma, 1);
+        dev::mbar_init(&bar_mma0, 1);
+        dev::mbar_init(&bar_mma1, 1);
         dev::fence_mbar_init();
         abort_flag = 0;
     }
-    if (t < BN / 32)
-        list_n[t] = 0;
-    for (int c = t; c < BN; c += 128) {
-        bias_s[c] = __ldg(bias + n0 + c);
-        band_s[c] = __ldg(band + n0 + c);
+    if (t == 0)
+        list_n = 0;
+    if (t < BN) {
+        bias_s[t] = __ldg(bias + n0 + t);
+        band_s[t] = __ldg(band + n0 + t);
     }
     if (warp == 0)
         dev::tmem_alloc(&tmem_slot, BN);
@@ -66,44 +73,58 @@ __global__ void __launch_bounds__(128) hs_proj_tc_kernel(
     dev::tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    bool issued = false;
+    int issued = 0;  // commits issued (thread 0)
     if (t == 0) {
-        dev::mbar_arrive_expect_tx(&bar_tma, TILE_BYTES);
-        dev::tma_load_2d(sA, &tmA, 0, m0, &bar_tma);
-        dev::tma_load_2d(sA + A_CHUNK, &tmA, 64, m0, &bar_tma);
-        dev::tma_load_2d(sB, &tmB, 0, n0, &bar_tma);
-        dev::tma_load_2d(sB + B_CHUNK, &tmB, 64, n0, &bar_tma);
-        if (!dev::mbar_wait_bounded(&bar_tma, 0)) {
-            abort_flag = 1;
-        } else {
-            dev::tc_fence_after();
-            const uint32_t idesc = dev::umma_idesc_bf16_f32(BM, BN);
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                const int chunk = kk >> 2, sub = kk & 3;
-                const uint64_t a = dev::umma_desc_sw128(dev::smem_u32(sA + chunk * A_CHUNK + sub * 32));
-                const uint64_t b = dev::umma_desc_sw128(dev::smem_u32(sB + chunk * B_CHUNK + sub * 32));
-                dev::umma_bf16(tmem, a, b, idesc, kk > 0 ? 1u : 0u);
+        const uint32_t idesc = dev::umma_idesc_bf16_f32(BM, BN);
+        bool ok = true;
+        for (int p = 0; p < 2 && ok; ++p) {
+            if (p == 1 && !dev::mbar_wait_bounded(&bar_mma0, 0)) {  // stage free again
+                ok = false;
+                break;
             }
-            dev::umma_commit(&bar_mma);
-            issued = true;
+            dev::mbar_arrive_expect_tx(&bar_tma, STAGE_BYTES);
+            dev::tma_load_2d(sAh, &tmAh, 64 * p, m0, &bar_tma);
+            dev::tma_load_2d(sAl, &tmAl, 64 * p, m0, &bar_tma);
+            dev::tma_load_2d(sBh, &tmBh, 64 * p, n0, &bar_tma);
+            dev::tma_load_2d(sBl, &tmBl, 64 * p, n0, &bar_tma);
+            if (!dev::mbar_wait_bounded(&bar_tma, (uint32_t)p)) {
+                ok = false;
+                break;
+            }
+            dev::tc_fence_after();
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const uint64_t ah = dev::umma_desc_sw128(dev::smem_u32(sAh + s * 32));
+                const uint64_t al = dev::umma_desc_sw128(dev::smem_u32(sAl + s * 32));
+                const uint64_t bh = dev::umma_desc_sw128(dev::smem_u32(sBh + s * 32));
+                const uint64_t bl = dev::umma_desc_sw128(dev::smem_u32(sBl + s * 32));
+                dev::umma_bf16(tmem, ah, bh, idesc, (p | s) ? 1u : 0u);
+                dev::umma_bf16(tmem, al, bh, idesc, 1u);
+                if (w_has_lo)
+                    dev::umma_bf16(tmem, ah, bl, idesc, 1u);
+            }
+            dev::umma_commit(p == 0 ? &bar_mma0 : &bar_mma1);
+            ++issued;
         }
+        if (!ok)
+            abort_flag = 1;
     }
     __syncthreads();
     bool ok = abort_flag == 0;
     if (ok)
-        ok = dev::mbar_wait_bounded(&bar_mma, 0);
+        ok = dev::mbar_wait_bounded(&bar_mma1, 0);
     ok = __syncthreads_and(ok) != 0;
     dev::tc_fence_after();
 
     if (ok) {
-        // operand tiles are dead now: reuse them for the output tile and the rescue queue
-        uint32_t *out_tile = reinterpret_cast<uint32_t *>(sA);             // [128][8]
-        uint16_t *queue = reinterpret_cast<uint16_t *>(sA + BM * 8 * 4);   // <= 128*32 entries
+        // The operand stage is dead now.  It holds the output tile, the queue of
+        // band bits and a staging area for the rows the FP32 re-check reads.
+        uint32_t *out_tile = reinterpret_cast<uint32_t *>(smem);                 // [128][BN/32], 2 KB
+        uint16_t *queue = reinterpret_cast<uint16_t *>(smem + 2048);             // <= 128*BN entries, 32 KB
+        float4 *stage = reinterpret_cast<float4 *>(smem + 2048 + 2 * BM * BN);    // RB x (f row, W row)
         const int row = warp * 32 + lane;
         const int kp = m0 + row;
         const bool valid = kp < n && (kps == nullptr || dev::kp_valid(kps[kp]));
-        unsigned long long rescued = 0;
 #pragma unroll 1
         for (int c = 0; c < BN / 32; ++c) {
             uint32_t r[32];
@@ -114,49 +135,64 @@ __global__ void __launch_bounds__(128) hs_proj_tc_kernel(
                 const float m = __uint_as_float(r[j]) + bias_s[c * 32 + j];
                 word |= (m > 0.0f) ? (1u << j) : 0u;
                 if (valid && fabsf(m) < band_s[c * 32 + j]) {
-                    const int q = atomicAdd(&list_n[c], 1);
-                    queue[q] = (uint16_t)((row << 5) | j);
+                    const int q = atomicAdd(&list_n, 1);
+                    queue[q] = (uint16_t)((row << 7) | (c * 32 + j));
                 }
             }
-            out_tile[row * 8 + c] = valid ? word : 0u;
+            out_tile[row * (BN / 32) + c] = valid ? word : 0u;
+        }
+        __syncthreads();
+        // FP32 re-check of the queued bits, RB at a time: the CTA first copies
+        // every needed histogram row and W row into shared memory (one round
+        // trip), then thread e recomputes entry e in the FP32 kernel's order.
+        const int total = list_n;
+#pragma unroll 1
+        for (int base = 0; base < total; base += RB) {
+            const int cnt = min(RB, total - base);
+            for (int v = t; v < cnt * 64; v += 128) {
+                const int e = v >> 6, part = v & 63;
+                const int ent = queue[base + e];
+                const float4 *src = part < 32
+                    ? reinterpret_cast<const float4 *>(hist32 + (size_t)(m0 + (ent >> 7)) * kHistDim) + part
+                    : reinterpret_cast<const float4 *>(Wt32 + (size_t)(n0 + (ent & 127)) * kHistDim) + (part - 32);
+                stage[v] = __ldg(src);
+            }
             __syncthreads();
-            const int cnt = list_n[c];
-            for (int e = t; e < cnt; e += 128) {
-                const int ent = queue[e];
-                const int rr = ent >> 5, jj = ent & 31;
-                const int col = n0 + c * 32 + jj;
-                const float4 *hv = reinterpret_cast<const float4 *>(hist32 + (size_t)(m0 + rr) * kHistDim);
-                const float4 *wv = reinterpret_cast<const float4 *>(Wt32 + (size_t)col * kHistDim);
+            if (t < cnt) {
+                const int ent = queue[base + t];
+                const int rr = ent >> 7, cc = ent & 127;
+                const float4 *hv = stage + t * 64, *wv = stage + t * 64 + 32;
                 float acc = 0.0f;
 #pragma unroll 8
                 for (int i = 0; i < kHistDim / 4; ++i) {
-                    const float4 a = __ldg(hv + i), b = __ldg(wv + i);
+                    const float4 a = hv[i], b = wv[i];
                     acc = fmaf(a.x, b.x, acc);
                     acc = fmaf(a.y, b.y, acc);
                     acc = fmaf(a.z, b.z, acc);
                     acc = fmaf(a.w, b.w, acc);
                 }
-                const float m32 = acc + bias_s[c * 32 + jj];
+                const float m32 = acc + bias_s[cc];
                 if (m32 > 0.0f)
-                    atomicOr(&out_tile[rr * 8 + c], 1u << jj);
+                    atomicOr(&out_tile[rr * (BN / 32) + (cc >> 5)], 1u << (cc & 31));
                 else
-                    atomicAnd(&out_tile[rr * 8 + c], ~(1u << jj));
+                    atomicAnd(&out_tile[rr * (BN / 32) + (cc >> 5)], ~(1u << (cc & 31)));
             }
-            rescued += (unsigned long long)cnt;
             __syncthreads();
         }
-        if (t == 0 && rescued)
-            atomicAdd(&status->rescued, rescued);
+        if (t == 0 && total)
+            atomicAdd(&status->rescued, (unsigned long long)total);
         if (kp < n) {
             uint32_t *dst = out + (size_t)kp * (K / 32) + n0 / 32;
 #pragma unroll
             for (int c = 0; c < BN / 32; ++c)
-                dst[c] = out_tile[row * 8 + c];
+                dst[c] = out_tile[row * (BN / 32) + c];
         }
     } else if (t == 0) {
         dev::raise_flag(status, BD_FLAG_TIMEOUT);
-        if (issued)
-            dev::mbar_wait_bounded(&bar_mma, 0);  // let issued MMAs drain before freeing TMEM
+        if (issued >= 1)
+            dev::mbar_wait_bounded(&bar_mma0, 0);  // let issued MMAs drain before freeing TMEM
+        if (issued >= 2)
+            dev::mbar_wait_bounded(&bar_mma1, 0);
     }
     dev::tc_fence_before();
     __syncthreads();
@@ -166,9 +202,9 @@ __global__ void __launch_bounds__(128) hs_proj_tc_kernel(
 
 }  // namespace
 
-cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const CUtensorMap &tmap_hist,
-                              const float *hist, int n, uint32_t *out, DeviceStatus *status,
-                              cudaStream_t st, const bd_keypoint *kps)
+cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const CUtensorMap &tm_hi,
+                              const CUtensorMap &tm_lo, const float *hist, int n, uint32_t *out,
+                              DeviceStatus *status, cudaStream_t st, const bd_keypoint *kps)
 {
     static bool configured = false;
     if (!configured) {
@@ -179,9 +215,9 @@ cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const CUtensorMap &tmap_his
         configured = true;
     }
     dim3 grid((n + BM - 1) / BM, p->nbits / BN);
-    hs_proj_tc_kernel<<<grid, 128, SMEM_BYTES, st>>>(tmap_hist, p->tmap_w, hist, p->d_Wt,
-                                                     p->d_bias, p->d_band, kps, n, p->nbits, out,
-                                                     status);
+    hs_proj_tc_kernel<<<grid, 128, SMEM_BYTES, st>>>(tm_hi, tm_lo, p->tmap_w_hi, p->tmap_w_lo,
+                                                     p->w_has_lo ? 1 : 0, hist, p->d_Wt, p->d_bias,
+                                                     p->d_band, kps, n, p->nbits, out, status);
     note_launches(1);
     return cudaGetLastError();
 }
