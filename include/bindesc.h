@@ -218,6 +218,41 @@ bd_status bd_hashsift_describe(bd_ctx *ctx, const bd_hs_params *p, const uint8_t
 bd_status bd_match(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt, int nbits,
                    int ratio_num, int ratio_den, bd_match_result *out);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free variant (the paper has no counterpart: this is a          */
+/* deployment aid of this library)                                           */
+
+/* Bytes of the static device area bd_bad_describe_noalloc works in. */
+#define BD_BAD_NOALLOC_SCRATCH_BYTES ((size_t)9 << 20)
+
+/* BAD descriptors like bd_bad_describe, for callers that cannot call
+ * cudaMalloc: code that enqueues work while a stream capture in global mode
+ * is active (cudaMalloc is an error there), processes whose device memory is
+ * all owned by another allocator, and real-time loops that cannot take the
+ * implicit synchronisation of cudaMalloc/cudaFree.  The call allocates
+ * nothing: the integral image and its tile carries live in a file-scope
+ * static device array of BD_BAD_NOALLOC_SCRATCH_BYTES (held by every GPU
+ * that loads the library until the process exits).  Parameters come from
+ * bd_bad_params_create, done once at set-up.
+ *  - Same arguments and outputs as bd_bad_describe, plus the cudaStream_t to
+ *    enqueue on (NULL = legacy default stream); the parameters' device must be
+ *    the current device.
+ *  - Images whose table needs more than BD_BAD_NOALLOC_SCRATCH_BYTES
+ *    ((h+1)(w+1) 4-byte entries plus carries; about 2.3 megapixels, e.g.
+ *    1920x1088) are rejected with BD_ERR_INVALID and a message in the
+ *    parameters' context; nothing is enqueued then.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current) and caches it; make
+ *    that first call before any stream capture.
+ *  - Every call on a device shares the one array, which keeps the last call's
+ *    contents (each call overwrites all it reads); calls that overlap on the
+ *    GPU (other streams, or graph nodes not ordered after each other) race.
+ *  - Invalid keypoints get all-zero descriptors but raise no status flag:
+ *    the call has no context status word. */
+bd_status bd_bad_describe_noalloc(const bd_bad_params *p, const uint8_t *img, int w, int h,
+                                  int pitch, const bd_keypoint *kps, int n, uint32_t *out,
+                                  void *stream);
+
 #ifdef __cplusplus
 }
 #endif

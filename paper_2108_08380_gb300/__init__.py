@@ -62,6 +62,7 @@ _SIGS = [
     ("bd_hashsift_project", _I, [_P, _P, _P, _I, _P]),
     ("bd_hashsift_describe", _I, [_P, _P, _P, _I, _I, _I, _P, _I, _P, _P]),
     ("bd_match", _I, [_P, _P, _I, _P, _I, _I, _I, _I, _P]),
+    ("bd_bad_describe_noalloc", _I, [_P, _P, _I, _I, _I, _P, _I, _P, _P]),
 ]
 
 _lock = threading.Lock()
