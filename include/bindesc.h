@@ -219,6 +219,55 @@ bd_status bd_match(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, in
                    int ratio_num, int ratio_den, bd_match_result *out);
 
 /* ------------------------------------------------------------------------ */
+/* Batched description (many images in one persistent launch)               */
+
+typedef struct bd_batch bd_batch;
+
+/* Launch shape of the batched kernel (picked by bd_batch_autotune).
+ *  bad_kp_per_item  keypoints per BAD work item (multiple of 4, 4..256)
+ *  ctas_per_sm      resident CTAs per SM of the persistent grid (0 = the most
+ *                   that fit)
+ *  hs_first         1: HashSIFT items are queued before the integral pass-2
+ *                   tiles and BAD items; 0: after them. */
+typedef struct bd_batch_config {
+    int bad_kp_per_item;
+    int ctas_per_sm;
+    int hs_first;
+} bd_batch_config;
+
+/* Plans the description of n_img images with BAD and/or HashSIFT (either
+ * params may be NULL, not both).  w, h, pitch: host arrays of n_img image
+ * sizes; kp_offsets: host array of n_img+1 non-decreasing keypoint offsets
+ * (keypoints of image i are kps[kp_offsets[i] .. kp_offsets[i+1])).  The
+ * plan allocates, once, the integral tables of all images, their carries,
+ * the histograms and the work-queue counters. */
+bd_status bd_batch_create(bd_ctx *ctx, const bd_bad_params *bad, const bd_hs_params *hs,
+                          int n_img, const int *w, const int *h, const int *pitch,
+                          const int *kp_offsets, bd_batch **out);
+void bd_batch_destroy(bd_batch *b);
+bd_status bd_batch_set_config(bd_batch *b, const bd_batch_config *cfg);
+bd_status bd_batch_get_config(const bd_batch *b, bd_batch_config *cfg);
+
+/* Describes the whole batch: one persistent kernel builds every integral
+ * image and computes every BAD descriptor and HashSIFT histogram from one
+ * work queue, then the projection kernel hashes all histograms.
+ *  imgs     host array of n_img device pointers to the images
+ *  kps      device, all keypoints (kp_offsets[n_img] of them)
+ *  bad_out  device, n x bad_nbits/32 words, or NULL to skip BAD
+ *  hs_out   device, n x hs_nbits/32 words, or NULL to skip HashSIFT
+ *  use_graph != 0: the launches are captured once into a CUDA graph (per set
+ *           of pointers) and replayed on later calls. */
+bd_status bd_describe_batch(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs,
+                            const bd_keypoint *kps, uint32_t *bad_out, uint32_t *hs_out,
+                            int use_graph);
+
+/* Times every candidate launch shape (reps launches each, CUDA events on the
+ * context's stream), keeps the fastest in the plan and returns it. */
+bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs,
+                            const bd_keypoint *kps, uint32_t *bad_out, uint32_t *hs_out,
+                            int reps, bd_batch_config *best, float *best_ms);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free variant (the paper has no counterpart: this is a          */
 /* deployment aid of this library)                                           */
 

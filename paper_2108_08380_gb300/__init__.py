@@ -62,6 +62,12 @@ _SIGS = [
     ("bd_hashsift_project", _I, [_P, _P, _P, _I, _P]),
     ("bd_hashsift_describe", _I, [_P, _P, _P, _I, _I, _I, _P, _I, _P, _P]),
     ("bd_match", _I, [_P, _P, _I, _P, _I, _I, _I, _I, _P]),
+    ("bd_batch_create", _I, [_P, _P, _P, _I, _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    ("bd_batch_destroy", None, [_P]),
+    ("bd_batch_set_config", _I, [_P, _P]),
+    ("bd_batch_get_config", _I, [_P, _P]),
+    ("bd_describe_batch", _I, [_P, _P, _P, _P, _P, _P, _I]),
+    ("bd_batch_autotune", _I, [_P, _P, _P, _P, _P, _P, _I, _P, ctypes.POINTER(_F)]),
     ("bd_bad_describe_noalloc", _I, [_P, _P, _I, _I, _I, _P, _I, _P, _P]),
 ]
 
@@ -189,6 +195,11 @@ class Context:
     def hs_params(self, p, precision: int = BD_HS_BF16_RESCUE, band: float = -1.0) -> "HsParamsHandle":
         return HsParamsHandle(self, p, precision, band)
 
+    def batch(self, bad, hs, images, kp_offsets) -> "Batch":
+        """Plan for a list of uint8 device images (bad / hs params handles or None)."""
+        return Batch(self, bad, hs, [(int(t.shape[1]), int(t.shape[0])) for t in images],
+                     [int(t.stride(0)) for t in images], kp_offsets)
+
     # ---- work -----------------------------------------------------------
     def integral(self, img, out=None):
         torch = self._torch
@@ -264,6 +275,76 @@ class Context:
         self._check(lib().bd_match(self.handle, _ptr(q), nq, _ptr(t), nt, nbits, ratio_num, ratio_den,
                                    _ptr(out)), "bd_match")
         return out
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("bad_kp_per_item", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("hs_first", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"bad_kp_per_item": self.bad_kp_per_item, "ctas_per_sm": self.ctas_per_sm,
+                "hs_first": self.hs_first}
+
+
+class Batch:
+    """A bd_batch plan: many images described by one persistent launch."""
+
+    def __init__(self, ctx: Context, bad, hs, sizes, pitches, kp_offsets):
+        import numpy as np
+        self.ctx = ctx
+        self.bad, self.hs = bad, hs
+        self.n_img = len(sizes)
+        w = np.ascontiguousarray([s[0] for s in sizes], dtype=np.int32)
+        h = np.ascontiguousarray([s[1] for s in sizes], dtype=np.int32)
+        p = np.ascontiguousarray(pitches, dtype=np.int32)
+        o = np.ascontiguousarray(kp_offsets, dtype=np.int32)
+        self._keep = (w, h, p, o)
+        self.n_kp = int(o[-1])
+        hd = ctypes.c_void_p()
+        st = lib().bd_batch_create(ctx.handle, bad.handle if bad else None, hs.handle if hs else None,
+                                   self.n_img, _np_ptr(w), _np_ptr(h), _np_ptr(p), _np_ptr(o),
+                                   ctypes.byref(hd))
+        ctx._check(st, "bd_batch_create")
+        self.handle = hd
+
+    def _ptrs(self, imgs):
+        arr = (ctypes.c_void_p * self.n_img)(*[t.data_ptr() for t in imgs])
+        return arr
+
+    def describe(self, imgs, kps, bad_out=None, hs_out=None, graph: bool = False):
+        self.ctx._stream()
+        arr = self._ptrs(imgs)
+        st = lib().bd_describe_batch(self.ctx.handle, self.handle, ctypes.cast(arr, ctypes.c_void_p),
+                                     _ptr(kps), _ptr(bad_out), _ptr(hs_out), int(graph))
+        self.ctx._check(st, "bd_describe_batch")
+
+    def set_config(self, bad_kp_per_item: int, ctas_per_sm: int, hs_first: int):
+        c = BatchConfig(bad_kp_per_item, ctas_per_sm, hs_first)
+        self.ctx._check(lib().bd_batch_set_config(self.handle, ctypes.byref(c)), "bd_batch_set_config")
+
+    def config(self) -> dict:
+        c = BatchConfig()
+        self.ctx._check(lib().bd_batch_get_config(self.handle, ctypes.byref(c)), "bd_batch_get_config")
+        return c.as_dict()
+
+    def autotune(self, imgs, kps, bad_out=None, hs_out=None, reps: int = 3):
+        self.ctx._stream()
+        arr = self._ptrs(imgs)
+        c = BatchConfig()
+        ms = ctypes.c_float(0)
+        st = lib().bd_batch_autotune(self.ctx.handle, self.handle, ctypes.cast(arr, ctypes.c_void_p),
+                                     _ptr(kps), _ptr(bad_out), _ptr(hs_out), int(reps),
+                                     ctypes.byref(c), ctypes.byref(ms))
+        self.ctx._check(st, "bd_batch_autotune")
+        return c.as_dict(), float(ms.value)
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().bd_batch_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
 
 
 def unpack_matches(m):

@@ -1,0 +1,571 @@
+// Batched description of many images of uneven size and keypoint count in one
+// persistent launch (plus the tensor-core projection), replayable from a
+// captured CUDA graph, with launch shapes picked by an autotuner.
+//
+// The persistent kernel runs one CTA of 128 threads per resident slot and
+// claims work items from an atomic counter, in this order (or with the
+// HashSIFT items last, a tunable):
+//   [integral pass-1 tiles of all images]
+//   [HashSIFT keypoints]                       (no dependency)
+//   [integral pass-2 tiles of all images]      (wait: the image's pass-1 tiles)
+//   [BAD keypoint groups, per image]           (wait: the image's pass-2 tiles)
+// Every wait is on items with smaller indices, already claimed by resident
+// CTAs that never wait on later items, so the queue always drains.  Waits are
+// bounded by the GPU timer; on expiry the CTA raises BD_FLAG_TIMEOUT and
+// skips the item.
+#include <string.h>
+
+#include <vector>
+
+#include "bad_dev.cuh"
+#include "hashsift_dev.cuh"
+#include "integral_dev.cuh"
+
+namespace bd {
+
+struct BatchImageDev {
+    int w, h, pitch, ntx, nty;
+    int tile_begin;          // first pass-1/pass-2 tile of this image
+    int kp_begin, kp_end;    // keypoints of this image
+    int bad_item_begin;      // first BAD item of this image
+    size_t ii_off;           // integral table offset (entries)
+    size_t cs_off, rs_off, tt_off;  // carry offsets (entries)
+};
+
+struct BatchKernelArgs {
+    const BatchImageDev *imgs;
+    const uint8_t *const *img_ptr;
+    int n_img, n_tiles, n_kp, n_bad_items, bad_per_item;
+    int hs_items;            // n_kp if HashSIFT is on, else 0
+    int hs_first;
+    uint32_t *ii, *carry;
+    unsigned int *work, *stats_done, *final_done;
+    dev::BadTables bad;
+    int bad_nw;
+    uint32_t *bad_out;
+    float spacing;
+    float *hist;
+    __nv_bfloat16 *hist16;
+    const bd_keypoint *kps;
+    DeviceStatus *status;
+};
+
+namespace {
+
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// thread 0 waits until *ctr >= target (bounded); the CTA learns the outcome.
+__device__ __forceinline__ bool cta_wait_count(const unsigned int *ctr, unsigned int target,
+                                               int *flag_s, DeviceStatus *status)
+{
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (atomicAdd(const_cast<unsigned int *>(ctr), 0u) < target) {
+            const unsigned long long t0 = gtimer();
+            while (atomicAdd(const_cast<unsigned int *>(ctr), 0u) < target) {
+                __nanosleep(200);
+                if (gtimer() - t0 > kWaitNs) {
+                    ok = 0;
+                    dev::raise_flag(status, BD_FLAG_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        *flag_s = ok;
+    }
+    __syncthreads();
+    return *flag_s != 0;
+}
+
+__device__ __forceinline__ int find_image(const BatchImageDev *imgs, int n_img, int key, int which)
+{
+    // largest i with begin(i) <= key; which: 0 tiles, 1 keypoints, 2 BAD items
+    int lo = 0, hi = n_img - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int b = which == 0 ? imgs[mid].tile_begin
+                                 : (which == 1 ? imgs[mid].kp_begin : imgs[mid].bad_item_begin);
+        if (b <= key)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int NW>
+__global__ void __launch_bounds__(128, 4) batch_persistent_kernel(BatchKernelArgs A)
+{
+    __shared__ union {
+        dev::IiStatsSmem s;
+        dev::IiFinalSmem f;
+        dev::HistSmem h;
+    } U;
+    __shared__ unsigned int item_s;
+    __shared__ int flag_s;
+    const int t = threadIdx.x;
+    const dev::HistLane L = dev::hist_lane(t);
+
+    // item ranges
+    const int e_stats = A.n_tiles;
+    const int n_hs = A.hs_items;
+    const int b_hs = A.hs_first ? e_stats : e_stats + A.n_tiles + A.n_bad_items;
+    const int b_final = A.hs_first ? e_stats + n_hs : e_stats;
+    const int b_bad = b_final + A.n_tiles;
+    const int total = 2 * A.n_tiles + n_hs + A.n_bad_items;
+
+    for (;;) {
+        if (t == 0)
+            item_s = atomicAdd(A.work, 1u);
+        __syncthreads();
+        const int item = (int)item_s;
+        __syncthreads();
+        if (item >= total)
+            break;
+        if (item < e_stats) {
+            const int im = find_image(A.imgs, A.n_img, item, 0);
+            const BatchImageDev &I = A.imgs[im];
+            const int tl = item - I.tile_begin;
+            dev::ii_stats_tile(U.s, A.img_ptr[im], I.w, I.h, I.pitch, A.carry + I.cs_off,
+                               A.carry + I.rs_off, A.carry + I.tt_off, I.ntx, tl % I.ntx, tl / I.ntx);
+            __syncthreads();
+            if (t == 0) {
+                __threadfence();
+                atomicAdd(A.stats_done + im, 1u);
+            }
+        } else if (item >= b_hs && item < b_hs + n_hs) {
+            const int k = item - b_hs;
+            const int im = find_image(A.imgs, A.n_img, k, 1);
+            const BatchImageDev &I = A.imgs[im];
+            dev::hs_hist_one(U.h, L, A.img_ptr[im], I.w, I.h, I.pitch, A.kps[k], A.spacing, A.hist,
+                             A.hist16, (size_t)k, (size_t)A.n_kp, A.status);
+            __syncthreads();
+        } else if (item >= b_final && item < b_final + A.n_tiles) {
+            const int tile = item - b_final;
+            const int im = find_image(A.imgs, A.n_img, tile, 0);
+            const BatchImageDev &I = A.imgs[im];
+            if (cta_wait_count(A.stats_done + im, (unsigned)(I.ntx * I.nty), &flag_s, A.status)) {
+                const int tl = tile - I.tile_begin;
+                dev::ii_final_tile(U.f, A.img_ptr[im], I.w, I.h, I.pitch, A.carry + I.cs_off,
+                                   A.carry + I.rs_off, A.carry + I.tt_off, I.ntx, A.ii + I.ii_off,
+                                   I.w + 1, tl % I.ntx, tl / I.ntx);
+            }
+            __syncthreads();
+            if (t == 0) {
+                __threadfence();
+                atomicAdd(A.final_done + im, 1u);
+            }
+        } else if (item >= b_bad && item < b_bad + A.n_bad_items) {
+            const int bi = item - b_bad;
+            const int im = find_image(A.imgs, A.n_img, bi, 2);
+            const BatchImageDev &I = A.imgs[im];
+            if (cta_wait_count(A.final_done + im, (unsigned)(I.ntx * I.nty), &flag_s, A.status)) {
+                const int k0 = I.kp_begin + (bi - I.bad_item_begin) * A.bad_per_item;
+                const int k1 = min(I.kp_end, k0 + A.bad_per_item);
+                for (int k = k0 + (t >> 5); k < k1; k += 4)
+                    dev::bad_describe_warp<NW, false>(A.bad, A.ii + I.ii_off, I.w + 1, I.w, I.h,
+                                                      A.kps[k], A.bad_out + (size_t)k * NW,
+                                                      A.status);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace
+}  // namespace bd
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+using namespace bd;
+
+struct bd_batch {
+    bd_ctx *ctx = nullptr;
+    const bd_bad_params *bad = nullptr;
+    const bd_hs_params *hs = nullptr;
+    int n_img = 0, n_tiles = 0, n_kp = 0, n_bad_items = 0;
+    std::vector<BatchImageDev> imgs;
+    BatchImageDev *d_imgs = nullptr;
+    const uint8_t **d_ptrs = nullptr;
+    std::vector<const uint8_t *> last_ptrs;
+    uint32_t *d_ii = nullptr, *d_carry = nullptr;
+    unsigned int *d_counters = nullptr;  // [work][stats_done n_img][final_done n_img]
+    float *d_hist = nullptr;
+    __nv_bfloat16 *d_hist16 = nullptr;
+    CUtensorMap tm_hi, tm_lo;
+    bd_batch_config cfg = {8, 0, 1};
+    int max_ctas_per_sm = 0;
+    // graph replay
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<const void *> gkey;
+    int graph_kernels = 0;
+};
+
+namespace {
+
+bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_t *bad_out,
+                       uint32_t *hs_out, cudaStream_t st, int *kernels)
+{
+    const size_t cbytes = sizeof(unsigned int) * (1 + 2 * (size_t)b->n_img);
+    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, cbytes, st);
+    if (e != cudaSuccess)
+        return cuda_err(ctx, e, "bd_describe_batch: counter reset");
+    BatchKernelArgs A;
+    memset(&A, 0, sizeof(A));
+    A.imgs = b->d_imgs;
+    A.img_ptr = b->d_ptrs;
+    A.n_img = b->n_img;
+    A.n_tiles = (b->bad && bad_out) ? b->n_tiles : 0;
+    A.n_kp = b->n_kp;
+    A.bad_per_item = b->cfg.bad_kp_per_item;
+    A.n_bad_items = (b->bad && bad_out) ? b->n_bad_items : 0;
+    A.hs_items = (b->hs && hs_out) ? b->n_kp : 0;
+    A.hs_first = b->cfg.hs_first;
+    A.ii = b->d_ii;
+    A.carry = b->d_carry;
+    A.work = b->d_counters;
+    A.stats_done = b->d_counters + 1;
+    A.final_done = b->d_counters + 1 + b->n_img;
+    if (b->bad)
+        A.bad = dev::bad_tables(b->bad);
+    A.bad_nw = b->bad ? b->bad->nbits / 32 : 8;
+    A.bad_out = bad_out;
+    A.spacing = b->hs ? b->hs->spacing : 1.f;
+    A.hist = b->d_hist;
+    A.hist16 = (b->hs && b->hs->precision == BD_HS_BF16_RESCUE) ? b->d_hist16 : nullptr;
+    A.kps = kps;
+    A.status = ctx->status;
+    int per_sm = b->cfg.ctas_per_sm > 0 ? b->cfg.ctas_per_sm : b->max_ctas_per_sm;
+    if (per_sm > b->max_ctas_per_sm)
+        per_sm = b->max_ctas_per_sm;
+    const int grid = per_sm * ctx->sm_count;
+    if (A.bad_nw == 16)
+        batch_persistent_kernel<16><<<grid, 128, 0, st>>>(A);
+    else
+        batch_persistent_kernel<8><<<grid, 128, 0, st>>>(A);
+    note_launches(1);
+    int nk = 1;
+    e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_err(ctx, e, "bd_describe_batch: persistent kernel");
+    if (A.hs_items) {
+        const bd_hs_params *p = b->hs;
+        if (p->precision == BD_HS_FP32)
+            e = launch_hs_proj_fp32(p, b->d_hist, b->n_kp, hs_out, st, kps);
+        else
+            e = launch_hs_proj_tc(p, b->tm_hi, b->tm_lo, b->d_hist, b->n_kp, hs_out, ctx->status, st,
+                                  kps);
+        ++nk;
+        if (e != cudaSuccess)
+            return cuda_err(ctx, e, "bd_describe_batch: projection kernel");
+    }
+    if (kernels)
+        *kernels = nk;
+    return BD_OK;
+}
+
+bd_status upload_ptrs(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs)
+{
+    bool same = b->last_ptrs.size() == (size_t)b->n_img;
+    for (int i = 0; same && i < b->n_img; ++i)
+        same = b->last_ptrs[i] == imgs[i];
+    if (same)
+        return BD_OK;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);  // earlier launches may still read the table
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_ptrs, imgs, sizeof(void *) * b->n_img, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess)
+        return cuda_err(ctx, e, "bd_describe_batch: image table upload");
+    b->last_ptrs.assign(imgs, imgs + b->n_img);
+    return BD_OK;
+}
+
+void drop_graph(bd_batch *b)
+{
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    b->gkey.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+bd_status bd_batch_create(bd_ctx *ctx, const bd_bad_params *bad, const bd_hs_params *hs, int n_img,
+                          const int *w, const int *h, const int *pitch, const int *kp_offsets,
+                          bd_batch **out)
+{
+    if (!ctx || !out)
+        return BD_ERR_INVALID;
+    *out = nullptr;
+    if ((!bad && !hs) || n_img < 1 || n_img > 65536 || !w || !h || !pitch || !kp_offsets)
+        return set_err(ctx, BD_ERR_INVALID, "bd_batch_create: bad arguments");
+    if (kp_offsets[0] != 0)
+        return set_err(ctx, BD_ERR_INVALID, "bd_batch_create: kp_offsets[0] must be 0");
+    bd_batch *b = new bd_batch();
+    b->ctx = ctx;
+    b->bad = bad;
+    b->hs = hs;
+    b->n_img = n_img;
+    size_t ii_total = 0, carry_total = 0;
+    int tiles = 0, bad_items = 0;
+    for (int i = 0; i < n_img; ++i) {
+        if (w[i] < 1 || h[i] < 1 || w[i] > kMaxImageSide || h[i] > kMaxImageSide || pitch[i] < w[i] ||
+            255.0 * (double)w[i] * (double)h[i] >= 4294967296.0 || kp_offsets[i + 1] < kp_offsets[i]) {
+            delete b;
+            return set_err(ctx, BD_ERR_INVALID, "bd_batch_create: image %d has bad size or keypoints", i);
+        }
+        BatchImageDev I;
+        I.w = w[i];
+        I.h = h[i];
+        I.pitch = pitch[i];
+        I.ntx = (w[i] + kIiTileCols - 1) / kIiTileCols;
+        I.nty = (h[i] + kIiTileRows - 1) / kIiTileRows;
+        I.tile_begin = tiles;
+        tiles += I.ntx * I.nty;
+        I.kp_begin = kp_offsets[i];
+        I.kp_end = kp_offsets[i + 1];
+        I.bad_item_begin = bad_items;
+        I.ii_off = ii_total;
+        ii_total += align_up((size_t)(h[i] + 1) * (w[i] + 1), 64);
+        I.cs_off = carry_total;
+        carry_total += align_up((size_t)I.nty * w[i], 64);
+        I.rs_off = carry_total;
+        carry_total += align_up((size_t)h[i] * I.ntx, 64);
+        I.tt_off = carry_total;
+        carry_total += align_up((size_t)I.nty * I.ntx, 64);
+        b->imgs.push_back(I);
+    }
+    b->n_tiles = tiles;
+    b->n_kp = kp_offsets[n_img];
+    b->cfg.bad_kp_per_item = 8;
+    for (int i = 0; i < n_img; ++i) {
+        b->imgs[i].bad_item_begin = bad_items;
+        bad_items += (b->imgs[i].kp_end - b->imgs[i].kp_begin + 7) / 8;
+    }
+    b->n_bad_items = bad_items;
+    cudaError_t e = cudaSuccess;
+    {
+        int prev = -1;
+        cudaGetDevice(&prev);
+        if (prev != ctx->device)
+            cudaSetDevice(ctx->device);
+        e = cudaMalloc(&b->d_imgs, sizeof(BatchImageDev) * n_img);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_ptrs, sizeof(void *) * n_img);
+        if (e == cudaSuccess && bad) e = cudaMalloc(&b->d_ii, sizeof(uint32_t) * ii_total);
+        if (e == cudaSuccess && bad) e = cudaMalloc(&b->d_carry, sizeof(uint32_t) * carry_total);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(unsigned int) * (1 + 2 * (size_t)n_img));
+        if (e == cudaSuccess && hs) e = cudaMalloc(&b->d_hist, sizeof(float) * kHistDim * (size_t)(b->n_kp > 0 ? b->n_kp : 1));
+        if (e == cudaSuccess && hs) e = cudaMalloc(&b->d_hist16, sizeof(__nv_bfloat16) * 2 * kHistDim * (size_t)(b->n_kp > 0 ? b->n_kp : 1));
+        if (e == cudaSuccess) e = cudaMemcpy(b->d_imgs, b->imgs.data(), sizeof(BatchImageDev) * n_img, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+        int occ8 = 0, occ16 = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ8, batch_persistent_kernel<8>, 128, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16, batch_persistent_kernel<16>, 128, 0);
+        b->max_ctas_per_sm = occ8 < occ16 ? occ8 : occ16;
+        if (prev >= 0 && prev != ctx->device)
+            cudaSetDevice(prev);
+    }
+    if (e != cudaSuccess) {
+        bd_batch_destroy(b);
+        return cuda_err(ctx, e, "bd_batch_create");
+    }
+    if (hs && hs->precision == BD_HS_BF16_RESCUE && b->n_kp > 0) {
+        if (!encode_tmap_2d_bf16(&b->tm_hi, b->d_hist16, 128, (uint64_t)b->n_kp, 256, 64, 128) ||
+            !encode_tmap_2d_bf16(&b->tm_lo, b->d_hist16 + (size_t)b->n_kp * kHistDim, 128,
+                                 (uint64_t)b->n_kp, 256, 64, 128)) {
+            bd_batch_destroy(b);
+            return set_err(ctx, BD_ERR_CUDA, "bd_batch_create: TMA descriptors");
+        }
+    }
+    *out = b;
+    return BD_OK;
+}
+
+void bd_batch_destroy(bd_batch *b)
+{
+    if (!b)
+        return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->ctx->device)
+        cudaSetDevice(b->ctx->device);
+    cudaStreamSynchronize(b->ctx->stream);
+    drop_graph(b);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->d_imgs) cudaFree(b->d_imgs);
+    if (b->d_ptrs) cudaFree(b->d_ptrs);
+    if (b->d_ii) cudaFree(b->d_ii);
+    if (b->d_carry) cudaFree(b->d_carry);
+    if (b->d_counters) cudaFree(b->d_counters);
+    if (b->d_hist) cudaFree(b->d_hist);
+    if (b->d_hist16) cudaFree(b->d_hist16);
+    if (prev >= 0 && prev != b->ctx->device)
+        cudaSetDevice(prev);
+    delete b;
+}
+
+bd_status bd_batch_set_config(bd_batch *b, const bd_batch_config *cfg)
+{
+    if (!b || !cfg)
+        return BD_ERR_INVALID;
+    if (cfg->bad_kp_per_item < 4 || cfg->bad_kp_per_item > 256 || (cfg->bad_kp_per_item & 3) ||
+        cfg->ctas_per_sm < 0 || (cfg->hs_first != 0 && cfg->hs_first != 1))
+        return set_err(b->ctx, BD_ERR_INVALID, "bd_batch_set_config: bad configuration");
+    b->cfg = *cfg;
+    int items = 0;
+    for (int i = 0; i < b->n_img; ++i) {
+        b->imgs[i].bad_item_begin = items;
+        items += (b->imgs[i].kp_end - b->imgs[i].kp_begin + cfg->bad_kp_per_item - 1) / cfg->bad_kp_per_item;
+    }
+    b->n_bad_items = items;
+    cudaError_t e = cudaStreamSynchronize(b->ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_imgs, b->imgs.data(), sizeof(BatchImageDev) * b->n_img, cudaMemcpyHostToDevice);
+    drop_graph(b);
+    return e == cudaSuccess ? BD_OK : cuda_err(b->ctx, e, "bd_batch_set_config");
+}
+
+bd_status bd_batch_get_config(const bd_batch *b, bd_batch_config *cfg)
+{
+    if (!b || !cfg)
+        return BD_ERR_INVALID;
+    *cfg = b->cfg;
+    if (cfg->ctas_per_sm == 0)
+        cfg->ctas_per_sm = b->max_ctas_per_sm;
+    return BD_OK;
+}
+
+bd_status bd_describe_batch(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs,
+                            const bd_keypoint *kps, uint32_t *bad_out, uint32_t *hs_out,
+                            int use_graph)
+{
+    if (!ctx || !b || b->ctx != ctx || !imgs)
+        return BD_ERR_INVALID;
+    if ((b->n_kp > 0 && !kps) || (!bad_out && !hs_out) || (bad_out && !b->bad) || (hs_out && !b->hs))
+        return set_err(ctx, BD_ERR_INVALID, "bd_describe_batch: bad arguments");
+    for (int i = 0; i < b->n_img; ++i)
+        if (!imgs[i])
+            return set_err(ctx, BD_ERR_INVALID, "bd_describe_batch: image %d is NULL", i);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device)
+        cudaSetDevice(ctx->device);
+    struct Restore {
+        int p, d;
+        ~Restore()
+        {
+            if (p >= 0 && p != d)
+                cudaSetDevice(p);
+        }
+    } restore{prev, ctx->device};
+    bd_status s = upload_ptrs(ctx, b, imgs);
+    if (s != BD_OK)
+        return s;
+    if (!use_graph)
+        return batch_launch(ctx, b, kps, bad_out, hs_out, ctx->stream, nullptr);
+
+    std::vector<const void *> key(imgs, imgs + b->n_img);
+    key.push_back(kps);
+    key.push_back(bad_out);
+    key.push_back(hs_out);
+    if (!b->gexec || key != b->gkey) {
+        drop_graph(b);
+        cudaGraph_t g = nullptr;
+        const uint64_t before = bd_kernel_launches();
+        cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess)
+            return cuda_err(ctx, e, "bd_describe_batch: begin capture");
+        int nk = 0;
+        s = batch_launch(ctx, b, kps, bad_out, hs_out, b->cap_stream, &nk);
+        e = cudaStreamEndCapture(b->cap_stream, &g);
+        note_launches(-(int)(bd_kernel_launches() - before));
+        if (s != BD_OK) {
+            if (g)
+                cudaGraphDestroy(g);
+            return s;
+        }
+        if (e == cudaSuccess)
+            e = cudaGraphInstantiate(&b->gexec, g, 0);
+        if (g)
+            cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            b->gexec = nullptr;
+            return cuda_err(ctx, e, "bd_describe_batch: graph capture");
+        }
+        b->gkey = key;
+        b->graph_kernels = nk;
+    }
+    cudaError_t e = cudaGraphLaunch(b->gexec, ctx->stream);
+    if (e != cudaSuccess)
+        return cuda_err(ctx, e, "bd_describe_batch: graph launch");
+    note_launches(b->graph_kernels);
+    return BD_OK;
+}
+
+bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs,
+                            const bd_keypoint *kps, uint32_t *bad_out, uint32_t *hs_out, int reps,
+                            bd_batch_config *best, float *best_ms)
+{
+    if (!ctx || !b || reps < 1)
+        return BD_ERR_INVALID;
+    const int items[] = {4, 8, 16, 32};
+    std::vector<int> per_sm;
+    for (int c : {1, 2, 3, 4, 6, 8, 12, 16})
+        if (c <= b->max_ctas_per_sm)
+            per_sm.push_back(c);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    bd_batch_config win = b->cfg;
+    float win_ms = 1e30f;
+    for (int hs_first = 0; hs_first < 2; ++hs_first) {
+        for (int it : items) {
+            for (int c : per_sm) {
+                bd_batch_config cfg = {it, c, hs_first};
+                bd_status s = bd_batch_set_config(b, &cfg);
+                if (s == BD_OK)
+                    s = bd_describe_batch(ctx, b, imgs, kps, bad_out, hs_out, 0);  // warm-up
+                if (s != BD_OK) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return s;
+                }
+                cudaEventRecord(e0, ctx->stream);
+                for (int r = 0; r < reps; ++r)
+                    bd_describe_batch(ctx, b, imgs, kps, bad_out, hs_out, 0);
+                cudaEventRecord(e1, ctx->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= reps;
+                if (ms < win_ms) {
+                    win_ms = ms;
+                    win = cfg;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    bd_status s = bd_batch_set_config(b, &win);
+    if (best)
+        *best = win;
+    if (best_ms)
+        *best_ms = win_ms;
+    return s;
+}
+
+}  // extern "C"

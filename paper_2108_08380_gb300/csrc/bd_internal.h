@@ -128,6 +128,8 @@ cudaError_t launch_hs_hist_image(const bd_hs_params *p, const uint8_t *img, int 
 cudaError_t launch_hs_to_bf16(const float *hist, int n, __nv_bfloat16 *hist16, cudaStream_t st);
 cudaError_t launch_hs_proj_fp32(const bd_hs_params *p, const float *hist, int n, uint32_t *out,
                                 cudaStream_t st, const bd_keypoint *kps);
+// raises the projection kernel's dynamic shared-memory limit (per device, at set-up)
+cudaError_t prepare_hs_proj_tc();
 cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const CUtensorMap &tm_hi,
                               const CUtensorMap &tm_lo, const float *hist, int n, uint32_t *out,
                               DeviceStatus *status, cudaStream_t st, const bd_keypoint *kps);

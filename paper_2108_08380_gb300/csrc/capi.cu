@@ -481,6 +481,11 @@ bd_status bd_hs_params_create(bd_ctx *ctx, int nbits, const float *W, const floa
         bd_hs_params_destroy(p);
         return set_err(ctx, BD_ERR_UNSUPPORTED, "cannot encode the TMA descriptor of W");
     }
+    e = prepare_hs_proj_tc();
+    if (e != cudaSuccess) {
+        bd_hs_params_destroy(p);
+        return cuda_err(ctx, e, "bd_hs_params_create: projection kernel attribute");
+    }
     *out = p;
     return BD_OK;
 }

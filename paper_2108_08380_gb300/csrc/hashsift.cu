@@ -1,155 +1,18 @@
-// HashSIFT feature extraction (Sec. III-B) on CUDA cores, FP32:
-//  - the 32x32 patch, sampled bilinearly around the keypoint (Sec. III-A/IV-F:
-//    HashSIFT describes a normalised 32x32 patch, not an image pyramid);
-//  - the SIFT-style histogram: central-difference gradients, 8 orientation
-//    bins with linear voting between neighbours, 4x4 cells of 8x8 pixels, a
-//    sigma = 16 Gaussian weight about the patch centre, L2 normalisation;
-//  - the plain FP32 projection D = sgn(W^T f + b) used as the reference GPU
-//    path (the tensor-core projection lives in proj_tc.cu).
-//
-// One CTA of 128 threads describes one keypoint at a time (grid-stride).
-// Thread t owns cell t/8 and pixel row t%8 of that cell: its 8 pixels vote
-// into a thread-private 8-bin histogram in shared memory laid out [bin][thread]
-// (conflict-free), and thread t then sums bin t%8 of cell t/8 over the cell's
-// 8 threads.  No atomics are needed.
-#include "bd_internal.h"
+// HashSIFT extraction kernels over the keypoints of one image (Sec. III-B):
+// patch warp, fused warp + histogram, histogram of given patches (one CTA of
+// 128 threads per keypoint, grid-stride; routines in hashsift_dev.cuh), and
+// the plain FP32 projection D = sgn(W^T f + b) used as the reference GPU path
+// (the tensor-core projection lives in proj_tc.cu).
+
+#include "hashsift_dev.cuh"
 
 namespace bd {
 namespace {
 
-constexpr int NT = 128;          // threads per CTA
-constexpr int PS = kPatch;       // 32
-constexpr int PSP = kPatch + 1;  // padded smem row
-
-struct Frame {
-    int ix, iy;
-    float fx, fy, A, B;  // A = scale*spacing*cos(angle), B = scale*spacing*sin(angle)
-};
-
-__device__ __forceinline__ Frame make_frame(const bd_keypoint &kp, float spacing)
-{
-    Frame f;
-    f.ix = dev::round_coord(kp.x);
-    f.iy = dev::round_coord(kp.y);
-    f.fx = kp.x - (float)f.ix;  // exact: both operands are within a factor of 2
-    f.fy = kp.y - (float)f.iy;
-    float s, c;
-    sincosf(kp.angle, &s, &c);
-    const float sg = kp.scale * spacing;
-    f.A = sg * c;
-    f.B = sg * s;
-    return f;
-}
-
-// Bilinear sample (clamp-to-edge taps) of patch pixel (i, j): the offset from
-// the rounded keypoint is kept small so FP32 keeps ~1e-6 px of precision.
-__device__ __forceinline__ float sample(const uint8_t *__restrict__ img, int w, int h, int pitch,
-                                        const Frame &f, int i, int j)
-{
-    const float u = (float)j - 15.5f, v = (float)i - 15.5f;
-    const float ox = fmaf(f.A, u, fmaf(-f.B, v, f.fx));
-    const float oy = fmaf(f.B, u, fmaf(f.A, v, f.fy));
-    const float flx = floorf(ox), fly = floorf(oy);
-    const float ax = ox - flx, ay = oy - fly;
-    const int x0 = f.ix + (int)flx, y0 = f.iy + (int)fly;
-    const int xa = min(max(x0, 0), w - 1), xb = min(max(x0 + 1, 0), w - 1);
-    const int ya = min(max(y0, 0), h - 1), yb = min(max(y0 + 1, 0), h - 1);
-    const uint8_t *ra = img + (size_t)ya * pitch;
-    const uint8_t *rb = img + (size_t)yb * pitch;
-    const float i00 = (float)__ldg(ra + xa), i01 = (float)__ldg(ra + xb);
-    const float i10 = (float)__ldg(rb + xa), i11 = (float)__ldg(rb + xb);
-    const float top = fmaf(ax, i01 - i00, i00);
-    const float bot = fmaf(ax, i11 - i10, i10);
-    return fmaf(ay, bot - top, top);
-}
-
-struct HistSmem {
-    float P[PS][PSP];
-    float priv[8][NT];
-    float wss[NT / 32];
-    int valid;
-};
-
-// Per-thread constants of the histogram mapping: pixel row i, first column j0
-// and the separable Gaussian weights gi * gj[q] (Sec. III-B; sigma = 16).
-struct HistLane {
-    int i, j0;
-    float g[8];
-};
-
-__device__ __forceinline__ HistLane hist_lane(int t)
-{
-    HistLane L;
-    const int cell = t >> 3;
-    L.i = (cell >> 2) * 8 + (t & 7);
-    L.j0 = (cell & 3) * 8;
-    const float di = (float)L.i - 15.5f;
-    const float gi = expf(-di * di * (1.0f / 512.0f));
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const float dj = (float)(L.j0 + q) - 15.5f;
-        L.g[q] = gi * expf(-dj * dj * (1.0f / 512.0f));
-    }
-    return L;
-}
-
-// Votes of this thread's 8 pixels into its private histogram column.
-__device__ __forceinline__ void vote(HistSmem &S, const HistLane &L, int t)
-{
-    const int i = L.i;
-    const int iu = max(i - 1, 0), id = min(i + 1, PS - 1);
-    float left = S.P[i][max(L.j0 - 1, 0)];
-    float mid = S.P[i][L.j0];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int j = L.j0 + q;
-        const float right = S.P[i][min(j + 1, PS - 1)];
-        const float gx = 0.5f * (right - left);
-        const float gy = 0.5f * (S.P[id][j] - S.P[iu][j]);
-        left = mid;
-        mid = right;
-        const float m = sqrtf(gx * gx + gy * gy);
-        float phi = atan2f(gy, gx);
-        if (phi < 0.0f)
-            phi += 6.28318530717958647692f;
-        const float tt = phi * 1.27323954473516268615f;  // 8 / (2 pi)
-        const float fl = floorf(tt);
-        const float w1 = tt - fl;
-        const int b0 = ((int)fl) & 7;
-        const int b1 = (b0 + 1) & 7;
-        const float gm = L.g[q] * m;
-        const float v1 = gm * w1;
-        S.priv[b0][t] += gm - v1;
-        S.priv[b1][t] += v1;
-    }
-}
-
-// Sum of the cell's 8 private columns for bin t%8, L2 norm, output.
-__device__ __forceinline__ void finish(HistSmem &S, int t, bool valid, float *__restrict__ hist,
-                                       __nv_bfloat16 *__restrict__ hist16, size_t kp, size_t nkp)
-{
-    const int cell = t >> 3, b = t & 7;
-    float H = 0.0f;
-#pragma unroll
-    for (int s = 0; s < 8; ++s)
-        H += S.priv[b][cell * 8 + ((s + b) & 7)];
-    float ss = H * H;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if ((t & 31) == 0)
-        S.wss[t >> 5] = ss;
-    __syncthreads();
-    const float tot = S.wss[0] + S.wss[1] + S.wss[2] + S.wss[3];
-    const float nrm = sqrtf(tot);
-    const float h = (valid && nrm > 0.0f) ? H / nrm : 0.0f;
-    hist[kp * kHistDim + t] = h;
-    if (hist16) {
-        const __nv_bfloat16 hi = __float2bfloat16_rn(h);
-        hist16[kp * kHistDim + t] = hi;
-        hist16[(nkp + kp) * kHistDim + t] = __float2bfloat16_rn(h - __bfloat162float(hi));
-    }
-}
+using dev::HistLane;
+using dev::HistSmem;
+using dev::NT;
+using dev::PS;
 
 __global__ void __launch_bounds__(NT) hs_hist_image_kernel(
     const uint8_t *__restrict__ img, int w, int h, int pitch, const bd_keypoint *__restrict__ kps,
@@ -157,30 +20,10 @@ __global__ void __launch_bounds__(NT) hs_hist_image_kernel(
     DeviceStatus *status)
 {
     __shared__ HistSmem S;
-    const int t = threadIdx.x;
-    const HistLane L = hist_lane(t);
-    for (int k = blockIdx.x; k < n; k += gridDim.x) {
-        const bd_keypoint kp = kps[k];
-        const bool valid = dev::kp_valid(kp);
-        if (valid) {
-            const Frame f = make_frame(kp, spacing);
-#pragma unroll
-            for (int r = 0; r < PS * PS / NT; ++r) {
-                const int p = t + r * NT;
-                S.P[p >> 5][p & 31] = sample(img, w, h, pitch, f, p >> 5, p & 31);
-            }
-        } else if (t == 0) {
-            dev::raise_flag(status, BD_FLAG_INVALID_KEYPOINT);
-        }
-#pragma unroll
-        for (int b = 0; b < 8; ++b)
-            S.priv[b][t] = 0.0f;
-        __syncthreads();
-        if (valid)
-            vote(S, L, t);
-        __syncthreads();
-        finish(S, t, valid, hist, hist16, (size_t)k, (size_t)n);
-    }
+    const HistLane L = dev::hist_lane(threadIdx.x);
+    for (int k = blockIdx.x; k < n; k += gridDim.x)
+        dev::hs_hist_one(S, L, img, w, h, pitch, kps[k], spacing, hist, hist16, (size_t)k,
+                         (size_t)n, status);
 }
 
 __global__ void __launch_bounds__(NT) hs_hist_patch_kernel(const float *__restrict__ patches,
@@ -189,7 +32,7 @@ __global__ void __launch_bounds__(NT) hs_hist_patch_kernel(const float *__restri
 {
     __shared__ HistSmem S;
     const int t = threadIdx.x;
-    const HistLane L = hist_lane(t);
+    const HistLane L = dev::hist_lane(t);
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const float *src = patches + (size_t)k * PS * PS;
 #pragma unroll
@@ -201,9 +44,9 @@ __global__ void __launch_bounds__(NT) hs_hist_patch_kernel(const float *__restri
         for (int b = 0; b < 8; ++b)
             S.priv[b][t] = 0.0f;
         __syncthreads();
-        vote(S, L, t);
+        dev::vote(S, L, t);
         __syncthreads();
-        finish(S, t, true, hist, hist16, (size_t)k, (size_t)n);
+        dev::hist_finish(S, t, true, hist, hist16, (size_t)k, (size_t)n);
     }
 }
 
@@ -224,11 +67,11 @@ __global__ void __launch_bounds__(NT) hs_warp_kernel(const uint8_t *__restrict__
                 dev::raise_flag(status, BD_FLAG_INVALID_KEYPOINT);
             continue;
         }
-        const Frame f = make_frame(kp, spacing);
+        const dev::Frame f = dev::make_frame(kp, spacing);
 #pragma unroll
         for (int r = 0; r < PS * PS / NT; ++r) {
             const int p = t + r * NT;
-            dst[p] = sample(img, w, h, pitch, f, p >> 5, p & 31);
+            dst[p] = dev::sample(img, w, h, pitch, f, p >> 5, p & 31);
         }
     }
 }

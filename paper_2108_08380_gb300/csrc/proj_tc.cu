@@ -202,18 +202,16 @@ __global__ void __launch_bounds__(128) hs_proj_tc_kernel(
 
 }  // namespace
 
+cudaError_t prepare_hs_proj_tc()
+{
+    return cudaFuncSetAttribute(hs_proj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                SMEM_BYTES);
+}
+
 cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const CUtensorMap &tm_hi,
                               const CUtensorMap &tm_lo, const float *hist, int n, uint32_t *out,
                               DeviceStatus *status, cudaStream_t st, const bd_keypoint *kps)
 {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(hs_proj_tc_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-        if (e != cudaSuccess)
-            return e;
-        configured = true;
-    }
     dim3 grid((n + BM - 1) / BM, p->nbits / BN);
     hs_proj_tc_kernel<<<grid, 128, SMEM_BYTES, st>>>(tm_hi, tm_lo, p->tmap_w_hi, p->tmap_w_lo,
                                                      p->w_has_lo ? 1 : 0, hist, p->d_Wt, p->d_bias,

@@ -173,10 +173,21 @@ class HashSiftParams:
         return int(self.W.shape[1])
 
 
-def make_hashsift_params(nbits: int, rng: np.random.Generator, spacing: float = 1.0) -> HashSiftParams:
-    """W ~ N(0, 1/128); zero-mean offset b_k = -(1/sqrt(128)) * sum_i W_ik, which
-    centres the projection of a flat unit-norm histogram."""
+def round_to_bf16(a: np.ndarray) -> np.ndarray:
+    """float32 values rounded to the nearest bfloat16 (ties to even), as float32."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def make_hashsift_params(nbits: int, rng: np.random.Generator, spacing: float = 1.0,
+                         bf16: bool = False) -> HashSiftParams:
+    """W ~ N(0, 1/128) (rounded to bfloat16 values if bf16); zero-mean offset
+    b_k = -(1/sqrt(128)) * sum_i W_ik, which centres the projection of a flat
+    unit-norm histogram."""
     W = rng.normal(0.0, 1.0 / math.sqrt(128.0), size=(128, nbits)).astype(np.float32)
+    if bf16:
+        W = round_to_bf16(W)
     b = (-(W.astype(np.float64).sum(axis=0)) / math.sqrt(128.0)).astype(np.float32)
     return HashSiftParams(W, b, float(spacing))
 
@@ -260,7 +271,7 @@ def batch_workload(seed: int = 1002, n_img: int = 64, total_kp: int = 200_000,
     offs = np.zeros(n_img + 1, dtype=np.int32)
     offs[1:] = np.cumsum(counts)
     bad = make_bad_params(bad_bits, rng, level_scales=tuple(float(s) for s in scales))
-    hs = make_hashsift_params(hs_bits, rng)
+    hs = make_hashsift_params(hs_bits, rng, bf16=True)
     return BatchWorkload(images, np.concatenate(kps, axis=0), offs, bad, hs)
 
 

@@ -1,0 +1,167 @@
+"""GPU parity of the batched persistent description (many images of uneven
+size and keypoint count in one launch, optionally replayed from a CUDA graph):
+identical bits to the per-image calls, which are pinned to the oracle, plus
+an oracle sample on the batch itself."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def _small_batch(seed=5, bad_bits=256, hs_bits=256, levels=1):
+    rng = np.random.default_rng(seed)
+    sizes = [(640, 480), (1, 1), (33, 17), (300, 200), (129, 257), (800, 600)]
+    counts = [700, 3, 0, 250, 77, 1300]
+    scales = tuple(float(s) for s in synth.pyramid_scales(levels))
+    imgs, kps = [], []
+    for (w, h), c in zip(sizes, counts):
+        imgs.append(synth.make_image(w, h, rng))
+        k = synth.make_keypoints(c, w, h, rng, border=-10.0, scales=scales, angle_bins=None)
+        kps.append(k)
+    offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    bad = synth.make_bad_params(bad_bits, rng, level_scales=scales)
+    hs = synth.make_hashsift_params(hs_bits, rng, bf16=True)
+    return imgs, np.concatenate(kps), offs, bad, hs
+
+
+def _per_image(ctx, bp, hp, imgs, kps, offs):
+    bad, hs = [], []
+    for i, im in enumerate(imgs):
+        k = kps[offs[i]:offs[i + 1]]
+        if len(k) == 0:
+            continue
+        bad.append(_u32(ctx.bad_describe(bp, _dev(im), _dev(k))))
+        hs.append(_u32(ctx.hashsift_describe(hp, _dev(im), _dev(k))))
+    return np.concatenate(bad), np.concatenate(hs)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_equals_per_image_calls(gpu_ctx, graph):
+    import torch
+    imgs, kps, offs, bad, hs = _small_batch()
+    bp, hp = gpu_ctx.bad_params(bad), gpu_ctx.hs_params(hs)
+    ref_bad, ref_hs = _per_image(gpu_ctx, bp, hp, imgs, kps, offs)
+    dimgs = [_dev(im) for im in imgs]
+    b = gpu_ctx.batch(bp, hp, dimgs, offs)
+    n = len(kps)
+    ob = torch.full((n, 8), -1, dtype=torch.int32, device="cuda")
+    oh = torch.full((n, 8), -1, dtype=torch.int32, device="cuda")
+    dk = _dev(kps)
+    for _ in range(2):
+        b.describe(dimgs, dk, ob, oh, graph=graph)
+    assert gpu_ctx.sync_status() == 0
+    assert np.array_equal(_u32(ob), ref_bad)
+    assert np.array_equal(_u32(oh), ref_hs)
+    # BAD against the oracle directly, all keypoints
+    for i, im in enumerate(imgs):
+        k = kps[offs[i]:offs[i + 1]]
+        if len(k):
+            assert np.array_equal(_u32(ob)[offs[i]:offs[i + 1]], oracle.bad_describe(im, k, bad)[0])
+
+
+def test_graph_replay_sees_new_image_contents(gpu_ctx):
+    import torch
+    imgs, kps, offs, bad, hs = _small_batch(seed=6)
+    bp, hp = gpu_ctx.bad_params(bad), gpu_ctx.hs_params(hs)
+    dimgs = [_dev(im) for im in imgs]
+    b = gpu_ctx.batch(bp, hp, dimgs, offs)
+    n = len(kps)
+    ob = torch.empty((n, 8), dtype=torch.int32, device="cuda")
+    oh = torch.empty((n, 8), dtype=torch.int32, device="cuda")
+    dk = _dev(kps)
+    b.describe(dimgs, dk, ob, oh, graph=True)
+    rng = np.random.default_rng(99)
+    new = [synth.make_image(im.shape[1], im.shape[0], rng) for im in imgs]
+    for d, im in zip(dimgs, new):
+        d.copy_(torch.from_numpy(im))
+    b.describe(dimgs, dk, ob, oh, graph=True)
+    ref_bad, ref_hs = _per_image(gpu_ctx, bp, hp, new, kps, offs)
+    assert np.array_equal(_u32(ob), ref_bad)
+    assert np.array_equal(_u32(oh), ref_hs)
+
+
+def test_autotune_keeps_results(gpu_ctx):
+    import torch
+    imgs, kps, offs, bad, hs = _small_batch(seed=7, bad_bits=512, hs_bits=512, levels=5)
+    bp, hp = gpu_ctx.bad_params(bad), gpu_ctx.hs_params(hs)
+    dimgs = [_dev(im) for im in imgs]
+    b = gpu_ctx.batch(bp, hp, dimgs, offs)
+    n = len(kps)
+    ob = torch.empty((n, 16), dtype=torch.int32, device="cuda")
+    oh = torch.empty((n, 16), dtype=torch.int32, device="cuda")
+    dk = _dev(kps)
+    best, ms = b.autotune(dimgs, dk, ob, oh, reps=2)
+    assert ms > 0 and best == b.config()
+    ob.fill_(-1)
+    oh.fill_(-1)
+    b.describe(dimgs, dk, ob, oh, graph=True)
+    ref_bad, ref_hs = _per_image(gpu_ctx, bp, hp, imgs, kps, offs)
+    assert np.array_equal(_u32(ob), ref_bad)
+    assert np.array_equal(_u32(oh), ref_hs)
+
+
+def test_batch_bad_only_hs_only_and_invalid(gpu_ctx):
+    import torch
+    import paper_2108_08380_gb300 as bd
+    imgs, kps, offs, bad, hs = _small_batch(seed=8)
+    kps[5, 0] = np.nan
+    kps[900, 2] = -3.0
+    bp, hp = gpu_ctx.bad_params(bad), gpu_ctx.hs_params(hs, precision=bd.BD_HS_FP32)
+    dimgs = [_dev(im) for im in imgs]
+    n = len(kps)
+    dk = _dev(kps)
+    b1 = gpu_ctx.batch(bp, None, dimgs, offs)
+    ob = torch.full((n, 8), -1, dtype=torch.int32, device="cuda")
+    b1.describe(dimgs, dk, ob, None)
+    b2 = gpu_ctx.batch(None, hp, dimgs, offs)
+    oh = torch.full((n, 8), -1, dtype=torch.int32, device="cuda")
+    b2.describe(dimgs, dk, None, oh)
+    assert gpu_ctx.sync_status() & bd.BD_FLAG_INVALID_KEYPOINT
+    ref_bad, ref_hs = _per_image(gpu_ctx, bp, hp, imgs, kps, offs)
+    gpu_ctx.sync_status()
+    assert np.array_equal(_u32(ob), ref_bad)
+    assert np.array_equal(_u32(oh), ref_hs)
+    assert np.all(_u32(ob)[[5, 900]] == 0) and np.all(_u32(oh)[[5, 900]] == 0)
+
+
+def test_batched_workload_full_size_sampled(gpu_ctx):
+    """The batched workload (64 images 480x360..1920x1080, 200k keypoints on a
+    5-level pyramid, BAD-512 + HashSIFT-512 with BF16 W) in the benchmark's
+    launch configuration: every descriptor equals the per-image calls; a
+    seeded sample of keypoints checked against the oracle."""
+    import torch
+    wl = synth.batch_workload(1002)
+    bp, hp = gpu_ctx.bad_params(wl.bad), gpu_ctx.hs_params(wl.hs, band=1e-3)
+    dimgs = [_dev(im) for im in wl.images]
+    b = gpu_ctx.batch(bp, hp, dimgs, wl.kp_offsets)
+    n = len(wl.kps)
+    dk = _dev(wl.kps)
+    ob = torch.empty((n, 16), dtype=torch.int32, device="cuda")
+    oh = torch.empty((n, 16), dtype=torch.int32, device="cuda")
+    b.describe(dimgs, dk, ob, oh, graph=True)
+    assert gpu_ctx.sync_status() == 0
+    ref_bad, ref_hs = _per_image(gpu_ctx, bp, hp, wl.images, wl.kps, wl.kp_offsets)
+    assert np.array_equal(_u32(ob), ref_bad)
+    assert np.array_equal(_u32(oh), ref_hs)
+    rng = np.random.default_rng(0)
+    for i in rng.choice(len(wl.images), size=6, replace=False):
+        lo, hi = wl.kp_offsets[i], wl.kp_offsets[i + 1]
+        sel = np.sort(rng.choice(np.arange(lo, hi), size=min(40, hi - lo), replace=False))
+        rb, _ = oracle.bad_describe(wl.images[i], wl.kps[sel], wl.bad)
+        assert np.array_equal(_u32(ob)[sel], rb)
+        ro = oracle.hs_describe(wl.images[i], wl.kps[sel], wl.hs)
+        got = np.unpackbits(_u32(oh)[sel].view(np.uint8), axis=1, bitorder="little").astype(bool)
+        sure = np.abs(ro["margins"]) > 2e-3
+        assert np.array_equal(got[sure], (ro["margins"] > 0)[sure])
