@@ -48,77 +48,124 @@ def load_peaks():
 # ---------------------------------------------------------------------------
 
 class Workload:
-    """Host-side inputs of one step and their device copies."""
+    """Host-side inputs of one step, their device copies and the step's ABI calls."""
 
     def __init__(self, name: str):
         import synth
         self.name = name
+        self.match = True
         if name == "plain":
             wl = synth.plain_workload(1000)  # 640x480, 1000 keypoints, BAD-256, HashSIFT-256
-            self.config = {"workload": "plain image pair 640x480, 1000 keypoints, BAD-256 + "
-                                       "HashSIFT-256 (BF16+rescue), 1000x1000 top-2/ratio 0.8 "
-                                       "match per descriptor",
+            self.images = [wl.img_a, wl.img_b]
+            self.kps = np.concatenate([wl.kps_a, wl.kps_b])
+            self.offsets = np.array([0, len(wl.kps_a), 2 * len(wl.kps_a)], np.int32)
+            self.band = -1.0
+            self.config = {"workload": "plain image pair 640x480 (B = A + N(0,5)), 1000 keypoints "
+                                       "each, BAD-256 + HashSIFT-256 (BF16+rescue), 1000x1000 "
+                                       "top-2/ratio 0.8 match per descriptor",
                            "images": "2 x 640x480 uint8", "keypoints_per_image": 1000,
                            "bad_bits": 256, "hashsift_bits": 256, "angle_bins": 32}
         elif name == "large":
             wl = synth.large_pair_workload(1004)  # 2 x 3840x2160, 20000 kps, BAD-256, HashSIFT-512
+            self.images = [wl.img_a, wl.img_b]
+            self.kps = np.concatenate([wl.kps_a, wl.kps_b])
+            self.offsets = np.array([0, len(wl.kps_a), 2 * len(wl.kps_a)], np.int32)
+            self.band = -1.0
             self.config = {"workload": "large image pair 3840x2160 (B = homography + noise), "
                                        "20000 keypoints each, BAD-256 + HashSIFT-512 (BF16+rescue), "
                                        "20000x20000 top-2/ratio 0.8 match per descriptor",
                            "images": "2 x 3840x2160 uint8", "keypoints_per_image": 20000,
                            "bad_bits": 256, "hashsift_bits": 512, "angle_bins": 32}
+        elif name == "batch":
+            wl = synth.batch_workload(1002)  # 64 images, 200k kps, BAD-512, HashSIFT-512 (BF16 W)
+            self.images = wl.images
+            self.kps = wl.kps
+            self.offsets = wl.kp_offsets
+            self.band = 1e-3
+            self.match = False
+            self.config = {"workload": "64 images 480x360..1920x1080, 200000 keypoints (log-uniform "
+                                       "500-8000 per image), 5-level 1.2 pyramid, BAD-512 + "
+                                       "HashSIFT-512 (BF16 W, rescue band 1e-3), one persistent "
+                                       "launch in a CUDA graph, autotuned",
+                           "images": "64 uint8", "keypoints": 200000, "bad_bits": 512,
+                           "hashsift_bits": 512, "angle_bins": 32}
         else:
             raise SystemExit(f"unknown workload {name}")
         self.wl = wl
-        self.n = int(wl.kps_a.shape[0])
+        self.n = int(self.kps.shape[0])
         self.bad_bits = wl.bad.nbits
         self.hs_bits = wl.hs.nbits
-        self.descriptors_per_step = 4 * self.n
-        self.pairs_per_step = 2 * self.n * self.n
+        self.descriptors_per_step = 2 * self.n
+        if self.match:
+            na = int(self.offsets[1])
+            self.pairs_per_step = 2 * na * (self.n - na)
+        else:
+            self.pairs_per_step = 0
 
     # ---- GPU -----------------------------------------------------------
-    def to_device(self, ctx):
+    def to_device(self, ctx, autotune=True):
         import torch
         import paper_2108_08380_gb300 as bd
-        wl = self.wl
         dev = "cuda"
-        self.img = [torch.from_numpy(wl.img_a).to(dev), torch.from_numpy(wl.img_b).to(dev)]
-        self.kps = [torch.from_numpy(wl.kps_a).to(dev), torch.from_numpy(wl.kps_b).to(dev)]
-        self.bp = ctx.bad_params(wl.bad)
-        self.hp = ctx.hs_params(wl.hs, precision=bd.BD_HS_BF16_RESCUE)
+        self.dimg = [torch.from_numpy(im).to(dev) for im in self.images]
+        self.dkps = torch.from_numpy(self.kps).to(dev)
+        self.bp = ctx.bad_params(self.wl.bad)
+        self.hp = ctx.hs_params(self.wl.hs, precision=bd.BD_HS_BF16_RESCUE, band=self.band)
         n = self.n
         i32 = torch.int32
-        self.bad = [torch.empty((n, self.bad_bits // 32), dtype=i32, device=dev) for _ in range(2)]
-        self.hs = [torch.empty((n, self.hs_bits // 32), dtype=i32, device=dev) for _ in range(2)]
-        self.m_bad = torch.empty((n, 3), dtype=i32, device=dev)
-        self.m_hs = torch.empty((n, 3), dtype=i32, device=dev)
+        self.bad = torch.empty((n, self.bad_bits // 32), dtype=i32, device=dev)
+        self.hs = torch.empty((n, self.hs_bits // 32), dtype=i32, device=dev)
+        self.plan = ctx.batch(self.bp, self.hp, self.dimg, self.offsets)
+        self.tuned = None
+        if autotune:
+            self.tuned, _ = self.plan.autotune(self.dimg, self.dkps, self.bad, self.hs, reps=3)
+        if self.match:
+            na = int(self.offsets[1])
+            self.m_bad = torch.empty((na, 3), dtype=i32, device=dev)
+            self.m_hs = torch.empty((na, 3), dtype=i32, device=dev)
 
     def stages(self, ctx):
         """(label, callable) of the ABI calls of one step, in order."""
-        return [
-            ("bad_describe_A", lambda: ctx.bad_describe(self.bp, self.img[0], self.kps[0], out=self.bad[0])),
-            ("bad_describe_B", lambda: ctx.bad_describe(self.bp, self.img[1], self.kps[1], out=self.bad[1])),
-            ("hashsift_describe_A", lambda: ctx.hashsift_describe(self.hp, self.img[0], self.kps[0], out=self.hs[0])),
-            ("hashsift_describe_B", lambda: ctx.hashsift_describe(self.hp, self.img[1], self.kps[1], out=self.hs[1])),
-            ("match_bad", lambda: ctx.match(self.bad[0], self.bad[1], self.bad_bits, 4, 5, out=self.m_bad)),
-            ("match_hashsift", lambda: ctx.match(self.hs[0], self.hs[1], self.hs_bits, 4, 5, out=self.m_hs)),
-        ]
+        st = [("describe_batch", lambda: self.plan.describe(self.dimg, self.dkps, self.bad, self.hs,
+                                                            graph=True))]
+        if self.match:
+            na = int(self.offsets[1])
+            st += [
+                ("match_bad", lambda: ctx.match(self.bad[:na], self.bad[na:], self.bad_bits, 4, 5,
+                                                out=self.m_bad)),
+                ("match_hashsift", lambda: ctx.match(self.hs[:na], self.hs[na:], self.hs_bits, 4, 5,
+                                                     out=self.m_hs)),
+            ]
+        return st
+
+    def outputs(self):
+        return [self.bad, self.hs] + ([self.m_bad, self.m_hs] if self.match else [])
 
     # ---- CPU oracle ----------------------------------------------------
     def oracle_step(self, sample_kp: int):
-        """The oracle on the first `sample_kp` keypoints of both images (all
+        """The oracle on the first `sample_kp` keypoints of each image (all
         stages); returns the descriptors and pairs it covered."""
         import oracle
         wl = self.wl
-        s = min(sample_kp, self.n)
-        ka, kb = wl.kps_a[:s], wl.kps_b[:s]
-        da, _ = oracle.bad_describe(wl.img_a, ka, wl.bad)
-        db, _ = oracle.bad_describe(wl.img_b, kb, wl.bad)
-        ha = oracle.hs_describe(wl.img_a, ka, wl.hs)["bits"]
-        hb = oracle.hs_describe(wl.img_b, kb, wl.hs)["bits"]
-        oracle.match(da, db, self.bad_bits)
-        oracle.match(ha, hb, self.hs_bits)
-        return 4 * s, 2 * s * s
+        nd = npairs = 0
+        descs = []
+        for i, im in enumerate(self.images):
+            lo, hi = int(self.offsets[i]), int(self.offsets[i + 1])
+            k = self.kps[lo:min(hi, lo + sample_kp)]
+            if len(k) == 0:
+                continue
+            d, _ = oracle.bad_describe(im, k, wl.bad)
+            h = oracle.hs_describe(im, k, wl.hs)["bits"]
+            descs.append((d, h))
+            nd += 2 * len(k)
+            if not self.match and nd >= 4 * sample_kp:
+                break
+        if self.match and len(descs) == 2:
+            (da, ha), (db, hb) = descs
+            oracle.match(da, db, self.bad_bits)
+            oracle.match(ha, hb, self.hs_bits)
+            npairs = 2 * len(da) * len(db)
+        return nd, npairs
 
 
 # ---------------------------------------------------------------------------
@@ -223,7 +270,7 @@ def run_reference(args):
 
 def cpu_baseline(wl, budget_s: float):
     """The oracle, as it stands, on host cores: steps of a bounded keypoint sample."""
-    sample = min(wl.n, 250 if wl.name == "plain" else 120)
+    sample = {"plain": 250, "large": 120, "batch": 60}[wl.name]
     wl.oracle_step(4)
     t0 = time.perf_counter()
     nd = npairs = steps = 0
@@ -254,8 +301,9 @@ def run_ours(args):
         pg = dist
 
     ctx = bd.Context(local)
+    ctx.trace(True)  # kernel-level CUDA events inside every call (graph replays included)
     wl = Workload(args.workload)
-    wl.to_device(ctx)
+    wl.to_device(ctx, autotune=not args.no_autotune)
     stages = wl.stages(ctx)
     n_launch0 = bd.kernel_launches()
 
@@ -276,15 +324,29 @@ def run_ours(args):
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
+    ctx.rescued_count(reset=True)
     launches_before = bd.kernel_launches()
+    kernel_ms = []  # per step: {stage/kernel: ms}
     t_wall0 = time.time()
     for s in range(K):
         flush.fill_(float(s))               # evict the previous step's data from L2
         torch.cuda._sleep(200_000)          # let the host enqueue the whole step first
+        ctx.trace_reset()
         ev[s][0].record()
-        for j, (_, fn) in enumerate(stages):
+        for j, (lab, fn) in enumerate(stages):
             fn()
             ev[s][j + 1].record()
+        step_k = {}
+        # marks arrive in call order; attribute each kernel to its call
+        names = [lab for lab, _ in stages]
+        call = 0  # the first call's own start mark opens the list
+        for kname, kms in ctx.trace_read_raw():
+            if kname == "begin":
+                call += 1
+                continue
+            key = f"{names[min(call, len(names) - 1)]}/{kname}"
+            step_k[key] = step_k.get(key, 0.0) + kms
+        kernel_ms.append(step_k)
     torch.cuda.synchronize()
     t_wall1 = time.time()
     launches = bd.kernel_launches() - launches_before
@@ -305,12 +367,17 @@ def run_ours(args):
     assert ctx.sync_status() == 0, "device flags raised during the timed steps"
 
     # ---- end to end through the public API with pinned host buffers ----
+    ctx.trace(False)
+    ctx.trace_reset()
+    rescued = ctx.rescued_count(reset=True)
     e2e = measure_e2e(ctx, wl, stages, max(3, min(K, 50)))
 
     if rank != 0:
         return
     per_stage = {lab: float(stage_ms[:, j].mean()) for j, (lab, _) in enumerate(stages)}
-    roof = roofline(wl, per_stage, stage_ms, args)
+    keys = sorted({k for d in kernel_ms for k in d})
+    per_kernel = {k: float(np.mean([d.get(k, 0.0) for d in kernel_ms])) for k in keys}
+    roof = roofline(wl, per_kernel, clocks)
     value = world * wl.descriptors_per_step / (ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "descriptors/s", "n_gpus": world, "steps": K,
@@ -321,6 +388,9 @@ def run_ours(args):
                        parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
         "matches_per_s": world * wl.pairs_per_step / (ms * 1e-3),
         "stage_ms": per_stage,
+        "kernel_ms": per_kernel,
+        "hashsift_rescued_bits_per_step": rescued / K,
+        "batch_config": wl.tuned,
         "roofline": roof,
         "clocks": clocks,
         "e2e": e2e,
@@ -334,14 +404,14 @@ def run_ours(args):
 
 
 def measure_e2e(ctx, wl, stages, steps):
-    """Same step through the API with host buffers: H2D of both images and
-    keypoint sets from pinned memory, the step, D2H of all descriptors and
+    """Same step through the API with host buffers: H2D of every image and of
+    the keypoints from pinned memory, the step, D2H of all descriptors and
     match records, inside the timed region."""
     import torch
-    host_in = [torch.from_numpy(wl.wl.img_a).pin_memory(), torch.from_numpy(wl.wl.img_b).pin_memory(),
-               torch.from_numpy(wl.wl.kps_a).pin_memory(), torch.from_numpy(wl.wl.kps_b).pin_memory()]
-    dev_in = [wl.img[0], wl.img[1], wl.kps[0], wl.kps[1]]
-    dev_out = [wl.bad[0], wl.bad[1], wl.hs[0], wl.hs[1], wl.m_bad, wl.m_hs]
+    host_in = [torch.from_numpy(im).pin_memory() for im in wl.images] + \
+        [torch.from_numpy(wl.kps).pin_memory()]
+    dev_in = list(wl.dimg) + [wl.dkps]
+    dev_out = wl.outputs()
     host_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in dev_out]
     bi = sum(t.numel() * t.element_size() for t in host_in)
     bo = sum(t.numel() * t.element_size() for t in host_out)
@@ -363,35 +433,47 @@ def measure_e2e(ctx, wl, stages, steps):
             "ms_per_step": ms, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
 
 
-def roofline(wl, per_stage, stage_ms, args):
-    """Roofline of the dominant call of the step (roofline table)."""
+def roofline(wl, per_kernel, clocks):
+    """Roofline of the dominant kernel of the step (largest mean time per step).
+    Algorithmic work per launch and the bound of each kernel are listed in
+    the design doc (roofline table)."""
     peaks, kind = load_peaks()
-    lab = max(per_stage, key=per_stage.get)
-    t = per_stage[lab] * 1e-3
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    n = wl.n
-    if lab.startswith("match"):
-        K = wl.bad_bits if lab == "match_bad" else wl.hs_bits
-        popc = n * n * (K // 32)
-        peak = 152 * 16 * sm_mhz * 1e6 / 1e12  # Tpopc/s: 152 SMs x 16 POPC/clk
-        achieved = popc / t / 1e12
-        return {"bound": "alu", "kernel": lab, "achieved": achieved, "peak": peak,
-                "unit": "Tpopc/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"derived: 152 SMs x 16 POPC/clk x {sm_mhz:.0f} MHz"}
-    if lab.startswith("hashsift"):
-        flops = 2.0 * 128 * wl.hs_bits * n
+    key = max(per_kernel, key=per_kernel.get)
+    t = per_kernel[key] * 1e-3
+    stage, kname = key.split("/")
+    sm_mhz = float(clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0))
+    na = int(wl.offsets[1]) if wl.match else 0
+    nb = wl.n - na
+    out = {"kernel": key, "ms": per_kernel[key], "sm_mhz_used": sm_mhz}
+    if kname == "match_top2":
+        K = wl.bad_bits if stage == "match_bad" else wl.hs_bits
+        popc = na * nb * (K // 32)
+        peak = 152 * 16 * sm_mhz * 1e6 / 1e12
+        ach = popc / t / 1e12
+        out.update(bound="alu", achieved=ach, peak=peak, unit="Tpopc/s", frac=ach / peak,
+                   traffic=None, peak_source=f"derived: 152 SMs x 16 POPC/clk x {sm_mhz:.0f} MHz")
+    elif kname == "hs_proj_tc":
+        flops = 2.0 * 128 * wl.hs_bits * wl.n
         peak = float(peaks["bf16_tflops"])
-        achieved = flops / t / 1e12
-        return {"bound": "tensor", "kernel": lab, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"{kind} bf16 burst"}
-    # BAD: integral (5 B/px) + descriptor output, HBM
-    px = wl.wl.img_a.size
-    byts = 5.0 * px + n * (wl.bad_bits // 8) + 16 * n
-    peak = float(peaks["hbm_gbs"])
-    achieved = byts / t / 1e9
-    return {"bound": "hbm", "kernel": lab, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "peak_source": f"{kind} HBM copy"}
+        ach = flops / t / 1e12
+        out.update(bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                   traffic=None, peak_source=f"{kind} bf16 burst (MEASURED_PEAKS.json)")
+    else:
+        # batch_persistent: histogram arithmetic dominates; FP32 lane-ops of the
+        # histogram (HS_OPS_PER_PIXEL per patch pixel) against 152 SMs x 128 lanes
+        ops = HS_OPS_PER_PIXEL * 1024.0 * wl.n
+        peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+        ach = ops / t / 1e12
+        out.update(bound="alu", achieved=ach, peak=peak, unit="Tops/s", frac=ach / peak,
+                   traffic=None,
+                   peak_source=f"derived: 152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz")
+    return out
+
+
+# FP32/SFU operations one patch pixel of the HashSIFT histogram needs (DESIGN.md):
+# sample position 4, tap split 4, bilinear 6, gradient 4, magnitude 3, orientation
+# (atan2 as 1), bin split 3, Gaussian weight 1, two votes 4.
+HS_OPS_PER_PIXEL = 30
 
 
 def main():
@@ -400,8 +482,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["plain", "large"], default="plain")
+    ap.add_argument("--workload", choices=["plain", "large", "batch"], default="plain")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-sample-kp", type=int, default=250)
     args = ap.parse_args()

@@ -105,6 +105,17 @@ bd_status bd_rescued_count(bd_ctx *ctx, uint64_t *count, int reset);
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t bd_kernel_launches(void);
 
+/* Tracing: with tracing on, every call records a CUDA event on its stream
+ * when it starts and after each kernel it launches (a graph captured while
+ * tracing is on records them at each replay).  bd_trace_read synchronises on
+ * the last event and returns, for up to max consecutive mark pairs since the
+ * last bd_trace_reset, the elapsed ms and the name of the kernel that ended
+ * at the later mark ("begin" for the gap before a call).  Returns the number
+ * of intervals written, or -1 on error. */
+bd_status bd_trace_enable(bd_ctx *ctx, int on);
+bd_status bd_trace_reset(bd_ctx *ctx);
+int bd_trace_read(bd_ctx *ctx, int max, float *ms, const char **labels);
+
 /* Grows the scratch area to at least `bytes` now, so that later calls of
  * that size allocate nothing (needed before capturing them in a CUDA graph). */
 bd_status bd_reserve(bd_ctx *ctx, size_t bytes);

@@ -46,6 +46,9 @@ _SIGS = [
     ("bd_sync_status", _I, [_P, ctypes.POINTER(ctypes.c_uint32)]),
     ("bd_rescued_count", _I, [_P, ctypes.POINTER(ctypes.c_uint64), _I]),
     ("bd_kernel_launches", ctypes.c_uint64, []),
+    ("bd_trace_enable", _I, [_P, _I]),
+    ("bd_trace_reset", _I, [_P]),
+    ("bd_trace_read", _I, [_P, _I, ctypes.POINTER(_F), ctypes.POINTER(ctypes.c_char_p)]),
     ("bd_reserve", _I, [_P, _SZ]),
     ("bd_scratch_bytes_bad", _SZ, [_I, _I]),
     ("bd_scratch_bytes_hashsift", _SZ, [_I]),
@@ -184,6 +187,30 @@ class Context:
         c = ctypes.c_uint64(0)
         self._check(lib().bd_rescued_count(self.handle, ctypes.byref(c), int(reset)), "bd_rescued_count")
         return int(c.value)
+
+    def trace(self, on: bool = True):
+        self._check(lib().bd_trace_enable(self.handle, int(on)), "bd_trace_enable")
+
+    def trace_reset(self):
+        self._check(lib().bd_trace_reset(self.handle), "bd_trace_reset")
+
+    def trace_read(self, max_marks: int = 256):
+        """[(kernel name, ms)] of the traced kernels since the last reset ('begin' gaps dropped)."""
+        ms = (ctypes.c_float * max_marks)()
+        lab = (ctypes.c_char_p * max_marks)()
+        n = lib().bd_trace_read(self.handle, max_marks, ms, lab)
+        if n < 0:
+            raise BindescError(BD_ERR_CUDA, "bd_trace_read failed")
+        return [(lab[i].decode(), float(ms[i])) for i in range(n) if lab[i] != b"begin"]
+
+    def trace_read_raw(self, max_marks: int = 256):
+        """[(name, ms)] including the 'begin' gaps that separate calls."""
+        ms = (ctypes.c_float * max_marks)()
+        lab = (ctypes.c_char_p * max_marks)()
+        n = lib().bd_trace_read(self.handle, max_marks, ms, lab)
+        if n < 0:
+            raise BindescError(BD_ERR_CUDA, "bd_trace_read failed")
+        return [(lab[i].decode(), float(ms[i])) for i in range(n)]
 
     def reserve(self, nbytes: int):
         self._check(lib().bd_reserve(self.handle, int(nbytes)), "bd_reserve")

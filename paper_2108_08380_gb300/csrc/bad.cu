@@ -34,6 +34,7 @@ cudaError_t launch_bad_gather(const bd_bad_params *p, const uint32_t *ii, int ii
         bad_gather_kernel<8><<<blocks, 256, 0, st>>>(T, ii, ii_stride, w, h, kps, n, out, status);
     else
         bad_gather_kernel<16><<<blocks, 256, 0, st>>>(T, ii, ii_stride, w, h, kps, n, out, status);
+    trace_kernel(st, "bad_gather");
     note_launches(1);
     return cudaGetLastError();
 }

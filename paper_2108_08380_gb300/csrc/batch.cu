@@ -209,6 +209,7 @@ struct bd_batch {
     cudaGraphExec_t gexec = nullptr;
     std::vector<const void *> gkey;
     int graph_kernels = 0;
+    std::vector<TraceMark> gmarks;  // trace events recorded by the graph's nodes
 };
 
 namespace {
@@ -253,6 +254,7 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
         batch_persistent_kernel<16><<<grid, 128, 0, st>>>(A);
     else
         batch_persistent_kernel<8><<<grid, 128, 0, st>>>(A);
+    trace_kernel(st, "batch_persistent");
     note_launches(1);
     int nk = 1;
     e = cudaGetLastError();
@@ -296,6 +298,9 @@ void drop_graph(bd_batch *b)
         cudaGraphExecDestroy(b->gexec);
         b->gexec = nullptr;
     }
+    for (const TraceMark &m : b->gmarks)
+        cudaEventDestroy(m.ev);
+    b->gmarks.clear();
     b->gkey.clear();
 }
 
@@ -474,8 +479,10 @@ bd_status bd_describe_batch(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     bd_status s = upload_ptrs(ctx, b, imgs);
     if (s != BD_OK)
         return s;
-    if (!use_graph)
+    if (!use_graph) {
+        TraceScope scope(ctx, ctx->stream);
         return batch_launch(ctx, b, kps, bad_out, hs_out, ctx->stream, nullptr);
+    }
 
     std::vector<const void *> key(imgs, imgs + b->n_img);
     key.push_back(kps);
@@ -489,7 +496,10 @@ bd_status bd_describe_batch(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
         if (e != cudaSuccess)
             return cuda_err(ctx, e, "bd_describe_batch: begin capture");
         int nk = 0;
-        s = batch_launch(ctx, b, kps, bad_out, hs_out, b->cap_stream, &nk);
+        {
+            TraceScope scope(ctx, b->cap_stream, &b->gmarks);
+            s = batch_launch(ctx, b, kps, bad_out, hs_out, b->cap_stream, &nk);
+        }
         e = cudaStreamEndCapture(b->cap_stream, &g);
         note_launches(-(int)(bd_kernel_launches() - before));
         if (s != BD_OK) {
@@ -512,6 +522,8 @@ bd_status bd_describe_batch(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     if (e != cudaSuccess)
         return cuda_err(ctx, e, "bd_describe_batch: graph launch");
     note_launches(b->graph_kernels);
+    if (ctx->trace)
+        ctx->marks.insert(ctx->marks.end(), b->gmarks.begin(), b->gmarks.end());
     return BD_OK;
 }
 

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/bindesc.h"
 
@@ -40,6 +41,15 @@ struct DeviceStatus {
 // ---------------------------------------------------------------------------
 // host-side objects behind the opaque ABI handles
 // ---------------------------------------------------------------------------
+namespace bd {
+// one recorded CUDA event with the name of the kernel that ended before it
+// ("begin" marks the start of an ABI call)
+struct TraceMark {
+    cudaEvent_t ev;
+    const char *label;
+};
+}  // namespace bd
+
 struct bd_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -48,6 +58,11 @@ struct bd_ctx {
     void *scratch = nullptr;             // device, grows on demand
     size_t scratch_bytes = 0;
     std::string err;
+    // tracing (bd_trace_*)
+    bool trace = false;
+    std::vector<cudaEvent_t> trace_pool;  // events owned by the context
+    size_t trace_next = 0;
+    std::vector<bd::TraceMark> marks;     // marks of the calls since the last reset
 };
 
 struct bd_bad_params {
@@ -93,6 +108,20 @@ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // process-wide count of kernels this library has launched (bd_kernel_launches)
 void note_launches(int k);
+
+// Tracing.  An ABI call opens a TraceScope on its thread; launch helpers call
+// trace_kernel(stream, name) after each kernel.  With tracing on, each mark
+// records a CUDA event on the stream.  Under graph capture the scope writes
+// its marks (events it creates) into `captured` instead, and the owner replays
+// them into the context's mark list at each graph launch.
+struct TraceScope {
+    TraceScope(bd_ctx *ctx, cudaStream_t st, std::vector<TraceMark> *captured = nullptr);
+    ~TraceScope();
+    bd_ctx *ctx;
+    std::vector<TraceMark> *captured;
+    TraceScope *prev;
+};
+void trace_kernel(cudaStream_t st, const char *label);
 
 // TMA descriptor encoding through the driver entry point (no -lcuda needed).
 bool encode_tmap_2d_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,

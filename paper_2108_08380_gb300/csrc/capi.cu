@@ -15,6 +15,52 @@ static std::atomic<unsigned long long> g_launches{0};
 
 void note_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
 
+static thread_local TraceScope *t_scope = nullptr;
+
+static void trace_record(TraceScope *sc, cudaStream_t st, const char *label)
+{
+    bd_ctx *ctx = sc->ctx;
+    if (!ctx || !ctx->trace)
+        return;
+    cudaEvent_t ev = nullptr;
+    if (sc->captured) {
+        // under capture a plain record only orders nodes: record an external event node
+        if (cudaEventCreate(&ev) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        sc->captured->push_back({ev, label});
+        if (cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal) != cudaSuccess)
+            cudaGetLastError();
+        return;
+    } else {
+        if (ctx->trace_next == ctx->trace_pool.size()) {
+            if (cudaEventCreate(&ev) != cudaSuccess)
+                return;
+            ctx->trace_pool.push_back(ev);
+        }
+        ev = ctx->trace_pool[ctx->trace_next++];
+        ctx->marks.push_back({ev, label});
+    }
+    if (cudaEventRecord(ev, st) != cudaSuccess)
+        cudaGetLastError();
+}
+
+TraceScope::TraceScope(bd_ctx *c, cudaStream_t st, std::vector<TraceMark> *cap)
+    : ctx(c), captured(cap), prev(t_scope)
+{
+    t_scope = this;
+    trace_record(this, st, "begin");
+}
+
+TraceScope::~TraceScope() { t_scope = prev; }
+
+void trace_kernel(cudaStream_t st, const char *label)
+{
+    if (t_scope)
+        trace_record(t_scope, st, label);
+}
+
 bd_status set_err(bd_ctx *ctx, bd_status s, const char *fmt, ...)
 {
     if (ctx) {
@@ -183,6 +229,8 @@ void bd_destroy(bd_ctx *ctx)
     {
         DeviceGuard g(ctx->device);
         cudaStreamSynchronize(ctx->stream);
+        for (cudaEvent_t ev : ctx->trace_pool)
+            cudaEventDestroy(ev);
         if (ctx->scratch)
             cudaFree(ctx->scratch);
         if (ctx->status)
@@ -202,6 +250,50 @@ bd_status bd_set_stream(bd_ctx *ctx, void *stream)
 const char *bd_last_error(const bd_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 uint64_t bd_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+bd_status bd_trace_enable(bd_ctx *ctx, int on)
+{
+    if (!ctx)
+        return BD_ERR_INVALID;
+    ctx->trace = on != 0;
+    return BD_OK;
+}
+
+bd_status bd_trace_reset(bd_ctx *ctx)
+{
+    if (!ctx)
+        return BD_ERR_INVALID;
+    ctx->marks.clear();
+    ctx->trace_next = 0;
+    return BD_OK;
+}
+
+int bd_trace_read(bd_ctx *ctx, int max, float *ms, const char **labels)
+{
+    if (!ctx || max < 0)
+        return -1;
+    DeviceGuard g(ctx->device);
+    if (ctx->marks.empty())
+        return 0;
+    if (cudaEventSynchronize(ctx->marks.back().ev) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    int n = 0;
+    for (size_t i = 1; i < ctx->marks.size() && n < max; ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, ctx->marks[i - 1].ev, ctx->marks[i].ev) != cudaSuccess) {
+            cudaGetLastError();  // leave no pending error behind for the next launch check
+            t = -1.f;
+        }
+        if (ms)
+            ms[n] = t;
+        if (labels)
+            labels[n] = ctx->marks[i].label;
+        ++n;
+    }
+    return n;
+}
 
 bd_status bd_sync_status(bd_ctx *ctx, uint32_t *flags)
 {
@@ -517,6 +609,7 @@ bd_status bd_integral(bd_ctx *ctx, const uint8_t *img, int w, int h, int pitch, 
     bd_status s = ensure_scratch(ctx, integral_scratch_bytes(w, h));
     if (s != BD_OK)
         return s;
+    TraceScope scope(ctx, ctx->stream);
     BD_LAUNCH(ctx,
               launch_integral(img, w, h, pitch, ii, ii_stride,
                               integral_scratch_carve(ctx->scratch, w, h), ctx->stream),
@@ -538,6 +631,7 @@ bd_status bd_bad_describe(bd_ctx *ctx, const bd_bad_params *p, const uint8_t *im
     if (s != BD_OK)
         return s;
     uint32_t *ii = (uint32_t *)ctx->scratch;
+    TraceScope scope(ctx, ctx->stream);
     BD_LAUNCH(ctx,
               launch_integral(img, w, h, pitch, ii, stride,
                               integral_scratch_carve((char *)ctx->scratch + ii_bytes, w, h),
@@ -556,6 +650,7 @@ bd_status bd_hashsift_warp(bd_ctx *ctx, const bd_hs_params *p, const uint8_t *im
         return set_err(ctx, BD_ERR_INVALID, "bd_hashsift_warp: bad arguments");
     if (n == 0)
         return BD_OK;
+    TraceScope scope(ctx, ctx->stream);
     BD_LAUNCH(ctx,
               launch_hs_warp(p, img, w, h, pitch, kps, n, patches, ctx->status, ctx->stream,
                              ctx->sm_count),
@@ -570,6 +665,7 @@ bd_status bd_hashsift_hist(bd_ctx *ctx, const float *patches, int n, float *hist
         return set_err(ctx, BD_ERR_INVALID, "bd_hashsift_hist: bad arguments");
     if (n == 0)
         return BD_OK;
+    TraceScope scope(ctx, ctx->stream);
     BD_LAUNCH(ctx, launch_hs_hist_patches(patches, n, hist, nullptr, ctx->stream, ctx->sm_count),
               "histogram kernel");
     return BD_OK;
@@ -612,6 +708,7 @@ bd_status bd_hashsift_project(bd_ctx *ctx, const bd_hs_params *p, const float *h
             return s;
         h16 = (__nv_bfloat16 *)ctx->scratch;
     }
+    TraceScope scope(ctx, ctx->stream);
     return project(ctx, p, hist, h16, true, n, out, nullptr);
 }
 
@@ -633,6 +730,7 @@ bd_status bd_hashsift_describe(bd_ctx *ctx, const bd_hs_params *p, const uint8_t
     __nv_bfloat16 *h16 =
         (__nv_bfloat16 *)((char *)ctx->scratch + align_up((size_t)n * kHistDim * 4, 256));
     const bool tc = p->precision == BD_HS_BF16_RESCUE;
+    TraceScope scope(ctx, ctx->stream);
     BD_LAUNCH(ctx,
               launch_hs_hist_image(p, img, w, h, pitch, kps, n, h32, tc ? h16 : nullptr,
                                    ctx->status, ctx->stream, ctx->sm_count),
@@ -656,6 +754,7 @@ bd_status bd_match(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, in
     bd_status s = ensure_scratch(ctx, match_scratch_bytes(nq, nt, nbits, ctx->sm_count));
     if (s != BD_OK)
         return s;
+    TraceScope scope(ctx, ctx->stream);
     BD_LAUNCH(ctx,
               launch_match(q, nq, t, nt, nbits, ratio_num, ratio_den, out, ctx->scratch,
                            ctx->sm_count, ctx->stream),

@@ -173,6 +173,7 @@ cudaError_t launch_hs_warp(const bd_hs_params *p, const uint8_t *img, int w, int
 {
     hs_warp_kernel<<<grid_for(n, sm_count, 16), NT, 0, st>>>(img, w, h, pitch, kps, n, p->spacing,
                                                              patches, status);
+    trace_kernel(st, "hs_warp");
     note_launches(1);
     return cudaGetLastError();
 }
@@ -181,6 +182,7 @@ cudaError_t launch_hs_hist_patches(const float *patches, int n, float *hist,
                                    __nv_bfloat16 *hist16, cudaStream_t st, int sm_count)
 {
     hs_hist_patch_kernel<<<grid_for(n, sm_count, 12), NT, 0, st>>>(patches, n, hist, hist16);
+    trace_kernel(st, "hs_hist_patch");
     note_launches(1);
     return cudaGetLastError();
 }
@@ -193,6 +195,7 @@ cudaError_t launch_hs_hist_image(const bd_hs_params *p, const uint8_t *img, int 
     hs_hist_image_kernel<<<grid_for(n, sm_count, 12), NT, 0, st>>>(img, w, h, pitch, kps, n,
                                                                    p->spacing, hist, hist16,
                                                                    status);
+    trace_kernel(st, "hs_hist_image");
     note_launches(1);
     return cudaGetLastError();
 }
@@ -204,6 +207,7 @@ cudaError_t launch_hs_to_bf16(const float *hist, int n, __nv_bfloat16 *hist16, c
     if (blocks > 4096)
         blocks = 4096;
     hs_to_bf16_kernel<<<blocks, 256, 0, st>>>(hist, cnt, hist16);
+    trace_kernel(st, "hs_to_bf16");
     note_launches(1);
     return cudaGetLastError();
 }
@@ -214,6 +218,7 @@ cudaError_t launch_hs_proj_fp32(const bd_hs_params *p, const float *hist, int n,
     dim3 grid((n + PBM - 1) / PBM, p->nbits / PBN);
     hs_proj_fp32_kernel<<<grid, 256, 0, st>>>(hist, n, p->d_W, p->nbits, p->d_bias, kps,
                                               reinterpret_cast<uint8_t *>(out));
+    trace_kernel(st, "hs_proj_fp32");
     note_launches(1);
     return cudaGetLastError();
 }

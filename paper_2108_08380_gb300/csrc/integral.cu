@@ -54,8 +54,10 @@ cudaError_t launch_integral(const uint8_t *img, int w, int h, int pitch, uint32_
     const int ntx = (w + dev::IITC - 1) / dev::IITC, nty = (h + dev::IITR - 1) / dev::IITR;
     dim3 grid(ntx, nty);
     ii_stats_kernel<<<grid, dev::IITC, 0, st>>>(img, w, h, pitch, s.colsum, s.rowsum, s.tiletot, ntx);
+    trace_kernel(st, "ii_stats");
     ii_final_kernel<<<grid, dev::IITC, 0, st>>>(img, w, h, pitch, s.colsum, s.rowsum, s.tiletot,
                                                 ntx, ii, ii_stride);
+    trace_kernel(st, "ii_final");
     note_launches(2);
     return cudaGetLastError();
 }

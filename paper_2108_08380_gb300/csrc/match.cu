@@ -151,9 +151,12 @@ cudaError_t launch_match(const uint32_t *q, int nq, const uint32_t *t, int nt, i
     else
         match_top2_kernel<16><<<grid, QB, 0, st>>>(q, nq, t, nt, chunk, nbits, ratio_num,
                                                    ratio_den, partial, out);
-    if (S > 1)
+    trace_kernel(st, "match_top2");
+    if (S > 1) {
         match_merge_kernel<<<(nq + 255) / 256, 256, 0, st>>>(partial, nq, S, nbits, ratio_num,
                                                              ratio_den, out);
+        trace_kernel(st, "match_merge");
+    }
     note_launches(S > 1 ? 2 : 1);
     return cudaGetLastError();
 }

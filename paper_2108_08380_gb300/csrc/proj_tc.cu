@@ -216,6 +216,7 @@ cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const CUtensorMap &tm_hi,
     hs_proj_tc_kernel<<<grid, 128, SMEM_BYTES, st>>>(tm_hi, tm_lo, p->tmap_w_hi, p->tmap_w_lo,
                                                      p->w_has_lo ? 1 : 0, hist, p->d_Wt, p->d_bias,
                                                      p->d_band, kps, n, p->nbits, out, status);
+    trace_kernel(st, "hs_proj_tc");
     note_launches(1);
     return cudaGetLastError();
 }
