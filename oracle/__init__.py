@@ -9,8 +9,9 @@ compiles it with gcc on first use and marshals numpy arrays into it.
 Every function follows a definition of the paper (Suarez et al., RA-L 2021):
 Sec. III-A for the integral image, the box features and the BAD stumps,
 Sec. III-B for the HashSIFT histogram and hash, Sec. IV-C for nearest
-neighbour matching; the readings taken where the paper is silent are listed
-at the top of ``bd_oracle.c``.
+neighbour matching, Eq. 1 / Eq. 3 for the triplet ranking loss of the
+training step (``bd_oracle_train.c``); the readings taken where the paper is
+silent are listed at the top of the two C files.
 """
 from __future__ import annotations
 
@@ -248,3 +249,75 @@ def match(q, t, nbits: int, ratio_num: int = 4, ratio_den: int = 5):
     lib().or_match(_u32p(q), nq, _u32p(t), nt, nbits, ratio_num, ratio_den, _i32p(idx), _i32p(d1),
                    _i32p(d2), _u8p(acc))
     return idx, d1, d2, acc
+
+
+# ---------------------------------------------------------------------------
+# training step (Sec. III-A Eq. 1, Sec. III-B Eq. 3; relaxed tanh responses)
+# ---------------------------------------------------------------------------
+
+def train_step(patches, bad, theta, hs, T=0.1, tau_bad=None, tau_hs=None, w_bad=1.0, w_hs=1.0,
+               fixed_mining=None, want_grads=True, want_r=False):
+    """One FP64 training step on [3, n, 32, 32] patches (anchors, positives,
+    negatives).  bad: BadParams (box geometry; its level 0 is the patch frame),
+    theta: float thresholds [Kb]; hs: HashSiftParams (W, b).  Returns a dict
+    with loss [2] (BAD, HashSIFT), mining [4, n] (nstar_bad, xsel_bad,
+    nstar_hs, xsel_hs) and, if asked, the gradients of w_bad*L_bad + w_hs*L_hs
+    and the relaxed responses."""
+    P = np.ascontiguousarray(patches, dtype=np.float64).reshape(-1, 1024)
+    rows = P.shape[0]
+    n = rows // 3
+    Kb, Kh = bad.nbits, hs.nbits
+    tau_bad = Kb / 2.0 if tau_bad is None else tau_bad
+    tau_hs = Kh / 2.0 if tau_hs is None else tau_hs
+    c = np.ascontiguousarray(bad.centres, dtype=np.uint8)
+    s = np.ascontiguousarray(bad.sides, dtype=np.uint8)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    W = np.ascontiguousarray(hs.W, dtype=np.float64)
+    b = np.ascontiguousarray(hs.b, dtype=np.float64)
+    loss = np.zeros(2)
+    mining = np.zeros((4, n), dtype=np.int32)
+    fm = None if fixed_mining is None else np.ascontiguousarray(fixed_mining, dtype=np.int32)
+    out = dict(loss=loss, mining=mining)
+    dth = dW = db = dP = rb = rh = None
+    if want_grads:
+        dth = np.zeros(Kb)
+        dW = np.zeros((128, Kh))
+        db = np.zeros(Kh)
+        dP = np.zeros((rows, 1024))
+    if want_r:
+        rb = np.zeros((rows, Kb))
+        rh = np.zeros((rows, Kh))
+    null = ctypes.POINTER(ctypes.c_double)()
+    lib().or_train_step(_f64p(P), ctypes.c_int(n), ctypes.c_int(Kb), _u8p(c), _u8p(s), _f64p(th),
+                        ctypes.c_int(Kh), _f64p(W), _f64p(b), ctypes.c_double(T),
+                        ctypes.c_double(tau_bad), ctypes.c_double(tau_hs), ctypes.c_double(w_bad),
+                        ctypes.c_double(w_hs), _i32p(fm) if fm is not None else ctypes.POINTER(ctypes.c_int32)(),
+                        _f64p(loss), _i32p(mining),
+                        _f64p(dth) if dth is not None else null, _f64p(dW) if dW is not None else null,
+                        _f64p(db) if db is not None else null, _f64p(dP) if dP is not None else null,
+                        _f64p(rb) if rb is not None else null, _f64p(rh) if rh is not None else null)
+    if want_grads:
+        out.update(dtheta=dth, dW=dW, db=db, dpatches=dP.reshape(3, n, 32, 32))
+    if want_r:
+        out.update(r_bad=rb, r_hs=rh)
+    return out
+
+
+def train_codes(patches, bad, theta, hs):
+    """Hard codes of all 3n patches: (bits_bad, bits_hs, f_bad, m_hs)."""
+    P = np.ascontiguousarray(patches, dtype=np.float64).reshape(-1, 1024)
+    rows = P.shape[0]
+    n = rows // 3
+    Kb, Kh = bad.nbits, hs.nbits
+    bb = np.zeros((rows, Kb // 32), dtype=np.uint32)
+    bh = np.zeros((rows, Kh // 32), dtype=np.uint32)
+    fb = np.zeros((rows, Kb))
+    mh = np.zeros((rows, Kh))
+    c = np.ascontiguousarray(bad.centres, dtype=np.uint8)
+    s = np.ascontiguousarray(bad.sides, dtype=np.uint8)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    W = np.ascontiguousarray(hs.W, dtype=np.float64)
+    b = np.ascontiguousarray(hs.b, dtype=np.float64)
+    lib().or_train_codes(_f64p(P), ctypes.c_int(n), ctypes.c_int(Kb), _u8p(c), _u8p(s), _f64p(th),
+                         ctypes.c_int(Kh), _f64p(W), _f64p(b), _u32p(bb), _u32p(bh), _f64p(fb), _f64p(mh))
+    return bb, bh, fb, mh
