@@ -279,6 +279,49 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
                             int reps, bd_batch_config *best, float *best_ms);
 
 /* ------------------------------------------------------------------------ */
+/* Differentiable training step (relaxed descriptors, Sec. III-A Eq. 1,      */
+/* Sec. III-B Eq. 3)                                                         */
+
+typedef struct bd_train bd_train;
+
+/* Plans a training step over n triplets of 32x32 FP32 patches.
+ *  bad          BAD parameters: their box centres and sides, read in the
+ *               32x32 patch frame, define the relaxed BAD responses (its
+ *               integer thresholds are not used; theta is an input below).
+ *  hs_bits      256 or 512 HashSIFT bits.
+ *  temperature  T of the relaxations r = tanh(z / T), with z = (theta - f)/255
+ *               for BAD (f a difference of box means, in intensity units) and
+ *               z = W^T h + b for HashSIFT.
+ *  tau_bad, tau_hs  margins of the two triplet ranking losses.
+ * The plan owns the responses, hard codes, histograms and mining of the last
+ * forward call, which the backward call reuses. */
+bd_status bd_train_create(bd_ctx *ctx, const bd_bad_params *bad, int hs_bits, int n,
+                          float temperature, float tau_bad, float tau_hs, bd_train **out);
+void bd_train_destroy(bd_train *tr);
+
+/* Forward: patches [3][n][32][32] FP32 (anchors, positives, negatives);
+ * theta [Kb], W [128][Kh] row-major, b [Kh] FP32.  Hard-negative mining on
+ * the hard codes (S = K - 2 Hamming, Sec. III-A): for anchor i the negative
+ * j != i most similar to a_i or p_i (lowest j on ties); anchor swap uses p_i
+ * when it is the more similar one.  loss (device, 2 floats) receives
+ * L = sum_i [tau - r(a_i).r(p_i) + r(x*_i).r(n*_i)]_+ for BAD and HashSIFT;
+ * mining_out (device, nullable) receives [4][n] int32: n*_bad, swap_bad,
+ * n*_hs, swap_hs; fixed_mining (device, nullable) replaces the mining. */
+bd_status bd_train_forward(bd_ctx *ctx, bd_train *tr, const float *patches, const float *theta,
+                           const float *W, const float *b, const int32_t *fixed_mining,
+                           float *loss, int32_t *mining_out);
+
+/* Backward of grad_loss[0] * L_bad + grad_loss[1] * L_hs (grad_loss: device,
+ * 2 floats) through the last forward's state, mining held fixed.  Writes
+ * dtheta [Kb], dW [128][Kh], db [Kh] and dpatches [3][n][32][32] (device).
+ * Conventions at the non-differentiable points: a pixel with zero gradient
+ * contributes nothing, a zero histogram has zero gradient, an inactive hinge
+ * has zero gradient. */
+bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, const float *W,
+                            const float *grad_loss, float *dtheta, float *dW, float *db,
+                            float *dpatches);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free variant (the paper has no counterpart: this is a          */
 /* deployment aid of this library)                                           */
 

@@ -71,6 +71,10 @@ _SIGS = [
     ("bd_batch_get_config", _I, [_P, _P]),
     ("bd_describe_batch", _I, [_P, _P, _P, _P, _P, _P, _I]),
     ("bd_batch_autotune", _I, [_P, _P, _P, _P, _P, _P, _I, _P, ctypes.POINTER(_F)]),
+    ("bd_train_create", _I, [_P, _P, _I, _I, _F, _F, _F, ctypes.POINTER(_P)]),
+    ("bd_train_destroy", None, [_P]),
+    ("bd_train_forward", _I, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    ("bd_train_backward", _I, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     ("bd_bad_describe_noalloc", _I, [_P, _P, _I, _I, _I, _P, _I, _P, _P]),
 ]
 
@@ -372,6 +376,98 @@ class Batch:
                 self.handle = None
         except Exception:
             pass
+
+
+class TrainStep:
+    """A bd_train plan: relaxed BAD / HashSIFT responses of n triplets of
+    32x32 patches, triplet ranking losses with hard-negative mining and anchor
+    swap, and the hand-written backward."""
+
+    def __init__(self, ctx: Context, bad, hs_bits: int, n: int, temperature: float = 0.1,
+                 tau_bad=None, tau_hs=None):
+        self.ctx, self.bad, self.n = ctx, bad, int(n)
+        self.kb, self.kh = bad.nbits, int(hs_bits)
+        self.tau_bad = self.kb / 2.0 if tau_bad is None else float(tau_bad)
+        self.tau_hs = self.kh / 2.0 if tau_hs is None else float(tau_hs)
+        h = ctypes.c_void_p()
+        st = lib().bd_train_create(ctx.handle, bad.handle, self.kh, self.n, float(temperature),
+                                   self.tau_bad, self.tau_hs, ctypes.byref(h))
+        ctx._check(st, "bd_train_create")
+        self.handle = h
+
+    def forward(self, patches, theta, W, b, fixed_mining=None):
+        """(loss [2] float32 tensor: BAD, HashSIFT; mining [4, n] int32 tensor)."""
+        torch = self.ctx._torch
+        loss = torch.empty(2, dtype=torch.float32, device=patches.device)
+        mining = torch.empty((4, self.n), dtype=torch.int32, device=patches.device)
+        self.ctx._stream()
+        st = lib().bd_train_forward(self.ctx.handle, self.handle, _ptr(patches), _ptr(theta), _ptr(W),
+                                    _ptr(b), _ptr(fixed_mining), _ptr(loss), _ptr(mining))
+        self.ctx._check(st, "bd_train_forward")
+        return loss, mining
+
+    def backward(self, patches, W, grad_loss):
+        """(dpatches, dtheta, dW, db) of grad_loss[0]*L_bad + grad_loss[1]*L_hs."""
+        torch = self.ctx._torch
+        dev = patches.device
+        dth = torch.empty(self.kb, dtype=torch.float32, device=dev)
+        dW = torch.empty((128, self.kh), dtype=torch.float32, device=dev)
+        db = torch.empty(self.kh, dtype=torch.float32, device=dev)
+        dP = torch.empty_like(patches)
+        g = grad_loss.to(device=dev, dtype=torch.float32).contiguous()
+        self.ctx._stream()
+        st = lib().bd_train_backward(self.ctx.handle, self.handle, _ptr(patches), _ptr(W), _ptr(g),
+                                     _ptr(dth), _ptr(dW), _ptr(db), _ptr(dP))
+        self.ctx._check(st, "bd_train_backward")
+        return dP, dth, dW, db
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().bd_train_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def triplet_loss(step: "TrainStep", patches, theta, W, b):
+    """Differentiable [L_bad, L_hs] of the training step (torch.autograd.Function)."""
+    return _TripletLoss.apply(step, patches, theta, W, b)
+
+
+def _make_autograd():
+    import torch
+
+    class TripletLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx_, step, patches, theta, W, b):
+            patches = patches.contiguous()
+            W = W.contiguous()
+            loss, mining = step.forward(patches, theta.contiguous(), W, b.contiguous())
+            ctx_.step = step
+            ctx_.save_for_backward(patches, W)
+            return loss
+
+        @staticmethod
+        def backward(ctx_, grad):
+            patches, W = ctx_.saved_tensors
+            dP, dth, dW, db = ctx_.step.backward(patches, W, grad)
+            return None, dP, dth, dW, db
+
+    return TripletLoss
+
+
+class _Lazy:
+    def __init__(self):
+        self.fn = None
+
+    def apply(self, *args):
+        if self.fn is None:
+            self.fn = _make_autograd()
+        return self.fn.apply(*args)
+
+
+_TripletLoss = _Lazy()
 
 
 def unpack_matches(m):

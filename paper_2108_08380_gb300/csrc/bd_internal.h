@@ -77,6 +77,8 @@ struct bd_bad_params {
     // device tables
     short4 *d_corner = nullptr;    // [L][NB][K] top-left corner offsets (x1,y1,x2,y2)
     int2 *d_side_thr = nullptr;    // [L][K] (scaled side, integer threshold on sum1-sum2)
+    short4 *d_patch_box = nullptr; // [K] top-left corners in the 32x32 patch frame (training)
+    int *d_patch_side = nullptr;   // [K] box sides in the patch frame
 };
 
 struct bd_hs_params {
@@ -149,7 +151,8 @@ cudaError_t launch_hs_warp(const bd_hs_params *p, const uint8_t *img, int w, int
                            cudaStream_t st, int sm_count);
 // hist16 (nullable) receives the BF16 head [n][128] followed by the BF16 tail [n][128]
 cudaError_t launch_hs_hist_patches(const float *patches, int n, float *hist,
-                                   __nv_bfloat16 *hist16, cudaStream_t st, int sm_count);
+                                   __nv_bfloat16 *hist16, cudaStream_t st, int sm_count,
+                                   float *norm_out = nullptr);
 cudaError_t launch_hs_hist_image(const bd_hs_params *p, const uint8_t *img, int w, int h, int pitch,
                                  const bd_keypoint *kps, int n, float *hist,
                                  __nv_bfloat16 *hist16, DeviceStatus *status, cudaStream_t st,
@@ -157,6 +160,10 @@ cudaError_t launch_hs_hist_image(const bd_hs_params *p, const uint8_t *img, int 
 cudaError_t launch_hs_to_bf16(const float *hist, int n, __nv_bfloat16 *hist16, cudaStream_t st);
 cudaError_t launch_hs_proj_fp32(const bd_hs_params *p, const float *hist, int n, uint32_t *out,
                                 cudaStream_t st, const bd_keypoint *kps);
+// FP32 projection with any W [128][K] / bias; relaxed (nullable) gets tanh(m * inv_t)
+cudaError_t launch_hs_proj_fp32_raw(const float *W, const float *bias, int K, const float *hist,
+                                    int n, uint32_t *out, float *relaxed, float inv_t,
+                                    cudaStream_t st);
 // raises the projection kernel's dynamic shared-memory limit (per device, at set-up)
 cudaError_t prepare_hs_proj_tc();
 cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const CUtensorMap &tm_hi,

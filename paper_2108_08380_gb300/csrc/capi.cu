@@ -453,7 +453,23 @@ bd_status bd_bad_params_create(bd_ctx *ctx, int nbits, const uint8_t *centres,
             }
         }
     }
+    std::vector<short4> pbox(nbits);
+    std::vector<int> pside(nbits);
+    for (int k = 0; k < nbits; ++k) {
+        const int s = sides[k];
+        pside[k] = s;
+        pbox[k] = make_short4((short)(centres[k * 4 + 0] - s / 2), (short)(centres[k * 4 + 1] - s / 2),
+                              (short)(centres[k * 4 + 2] - s / 2), (short)(centres[k * 4 + 3] - s / 2));
+    }
     cudaError_t e = cudaMalloc(&p->d_corner, nt * sizeof(short4));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&p->d_patch_box, nbits * sizeof(short4));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&p->d_patch_side, nbits * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->d_patch_box, pbox.data(), nbits * sizeof(short4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->d_patch_side, pside.data(), nbits * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMalloc(&p->d_side_thr, side_thr.size() * sizeof(int2));
     if (e == cudaSuccess)
@@ -479,6 +495,10 @@ void bd_bad_params_destroy(bd_bad_params *p)
             cudaFree(p->d_corner);
         if (p->d_side_thr)
             cudaFree(p->d_side_thr);
+        if (p->d_patch_box)
+            cudaFree(p->d_patch_box);
+        if (p->d_patch_side)
+            cudaFree(p->d_patch_side);
     }
     delete[] p->h_offsets;
     delete[] p->h_sides;

@@ -28,7 +28,8 @@ __global__ void __launch_bounds__(NT) hs_hist_image_kernel(
 
 __global__ void __launch_bounds__(NT) hs_hist_patch_kernel(const float *__restrict__ patches,
                                                            int n, float *__restrict__ hist,
-                                                           __nv_bfloat16 *__restrict__ hist16)
+                                                           __nv_bfloat16 *__restrict__ hist16,
+                                                           float *__restrict__ norm_out)
 {
     __shared__ HistSmem S;
     const int t = threadIdx.x;
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(NT) hs_hist_patch_kernel(const float *__restri
         __syncthreads();
         dev::vote(S, L, t);
         __syncthreads();
-        dev::hist_finish(S, t, true, hist, hist16, (size_t)k, (size_t)n);
+        dev::hist_finish(S, t, true, hist, hist16, (size_t)k, (size_t)n, norm_out);
     }
 }
 
@@ -100,7 +101,9 @@ __global__ void __launch_bounds__(256) hs_proj_fp32_kernel(const float *__restri
                                                            const float *__restrict__ W, int K,
                                                            const float *__restrict__ bias,
                                                            const bd_keypoint *__restrict__ kps,
-                                                           uint8_t *__restrict__ out)
+                                                           uint8_t *__restrict__ out,
+                                                           float *__restrict__ relaxed,
+                                                           float inv_t)
 {
     __shared__ float Hs[PBK][PBM + 4];
     __shared__ float Ws[PBK][PBN];
@@ -156,6 +159,11 @@ __global__ void __launch_bounds__(256) hs_proj_fp32_kernel(const float *__restri
         for (int b = 0; b < 8; ++b)
             byte |= (ok && (acc[a][b] + bv[b]) > 0.0f) ? (1u << b) : 0u;
         out[(size_t)row * (K / 8) + (n0 + tx * 8) / 8] = (uint8_t)byte;
+        if (relaxed) {
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+                relaxed[(size_t)row * K + n0 + tx * 8 + b] = tanhf((acc[a][b] + bv[b]) * inv_t);
+        }
     }
 }
 
@@ -179,9 +187,11 @@ cudaError_t launch_hs_warp(const bd_hs_params *p, const uint8_t *img, int w, int
 }
 
 cudaError_t launch_hs_hist_patches(const float *patches, int n, float *hist,
-                                   __nv_bfloat16 *hist16, cudaStream_t st, int sm_count)
+                                   __nv_bfloat16 *hist16, cudaStream_t st, int sm_count,
+                                   float *norm_out)
 {
-    hs_hist_patch_kernel<<<grid_for(n, sm_count, 12), NT, 0, st>>>(patches, n, hist, hist16);
+    hs_hist_patch_kernel<<<grid_for(n, sm_count, 12), NT, 0, st>>>(patches, n, hist, hist16,
+                                                                   norm_out);
     trace_kernel(st, "hs_hist_patch");
     note_launches(1);
     return cudaGetLastError();
@@ -212,12 +222,24 @@ cudaError_t launch_hs_to_bf16(const float *hist, int n, __nv_bfloat16 *hist16, c
     return cudaGetLastError();
 }
 
+cudaError_t launch_hs_proj_fp32_raw(const float *W, const float *bias, int K, const float *hist,
+                                    int n, uint32_t *out, float *relaxed, float inv_t,
+                                    cudaStream_t st)
+{
+    dim3 grid((n + PBM - 1) / PBM, K / PBN);
+    hs_proj_fp32_kernel<<<grid, 256, 0, st>>>(hist, n, W, K, bias, nullptr,
+                                              reinterpret_cast<uint8_t *>(out), relaxed, inv_t);
+    trace_kernel(st, "hs_proj_fp32_relaxed");
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_hs_proj_fp32(const bd_hs_params *p, const float *hist, int n, uint32_t *out,
                                 cudaStream_t st, const bd_keypoint *kps)
 {
     dim3 grid((n + PBM - 1) / PBM, p->nbits / PBN);
     hs_proj_fp32_kernel<<<grid, 256, 0, st>>>(hist, n, p->d_W, p->nbits, p->d_bias, kps,
-                                              reinterpret_cast<uint8_t *>(out));
+                                              reinterpret_cast<uint8_t *>(out), nullptr, 1.0f);
     trace_kernel(st, "hs_proj_fp32");
     note_launches(1);
     return cudaGetLastError();

@@ -129,7 +129,8 @@ __device__ __forceinline__ void vote(HistSmem &S, const HistLane &L, int t)
 
 // Sum of the cell's 8 private columns for bin t%8, L2 norm, output.
 __device__ __forceinline__ void hist_finish(HistSmem &S, int t, bool valid, float *__restrict__ hist,
-                                       __nv_bfloat16 *__restrict__ hist16, size_t kp, size_t nkp)
+                                       __nv_bfloat16 *__restrict__ hist16, size_t kp, size_t nkp,
+                                       float *__restrict__ norm_out = nullptr)
 {
     const int cell = t >> 3, b = t & 7;
     float H = 0.0f;
@@ -145,6 +146,8 @@ __device__ __forceinline__ void hist_finish(HistSmem &S, int t, bool valid, floa
     __syncthreads();
     const float tot = S.wss[0] + S.wss[1] + S.wss[2] + S.wss[3];
     const float nrm = sqrtf(tot);
+    if (norm_out && t == 0)
+        norm_out[kp] = valid ? nrm : 0.0f;
     const float h = (valid && nrm > 0.0f) ? H / nrm : 0.0f;
     hist[kp * kHistDim + t] = h;
     if (hist16) {

@@ -1,0 +1,715 @@
+// Differentiable training step for BAD and HashSIFT (Sec. III-A Eq. 1 and
+// Sec. III-B Eq. 3) on 32x32 patches, with a hand-written backward.
+//
+// Rows of the patch tensor: [0,n) anchors, [n,2n) positives, [2n,3n) negatives.
+//  forward
+//   - relaxed BAD: per-patch summed-area table in FP64 (so the hard bit
+//     [f <= theta] is decided in double precision), r = tanh((theta - f)/(255 T));
+//   - relaxed HashSIFT: the patch histogram kernel, then the FP32 projection
+//     with r = tanh((W^T h + b)/T) and hard bits [m > 0];
+//   - mining on hard codes: for anchor i the negative j != i with the smallest
+//     min(Hamming(a_i,n_j), Hamming(p_i,n_j)) (= the largest similarity
+//     K - 2 Hamming, Sec. III-A), lowest j on ties; anchor swap keeps p_i when
+//     it is closer to that negative than a_i;
+//   - the hinge loss of each descriptor.
+//  backward (mining held fixed)
+//   - dL/dr from the active hinges (negatives collect with atomics);
+//   - BAD: dtheta column sums, and the box adjoint as a 2-D difference array
+//     per patch (4 corner updates per box, then a 2-D prefix sum);
+//   - HashSIFT: dW = H^T dM and db (split over rows), dh = W dM, the
+//     normalisation adjoint and the histogram adjoint per pixel (recomputed
+//     from the patch), gathered into the patch gradient.
+#include "hashsift_dev.cuh"
+
+using namespace bd;
+
+struct bd_train {
+    bd_ctx *ctx = nullptr;
+    const bd_bad_params *bad = nullptr;
+    int n = 0, rows = 0, kb = 0, kh = 0, splits = 1, chunk = 1;
+    float T = 0.1f, tau_bad = 0.f, tau_hs = 0.f;
+    float *r_bad = nullptr, *r_hs = nullptr, *h = nullptr, *norm = nullptr;
+    uint32_t *bits_bad = nullptr, *bits_hs = nullptr, *partial = nullptr;
+    int32_t *mining = nullptr;  // [4][n]
+    float *dr_bad = nullptr, *dr_hs = nullptr, *Wt = nullptr;
+    double *loss_acc = nullptr;
+};
+
+namespace bd {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int MTT = 256;  // negatives per shared-memory tile (mining)
+
+__device__ __forceinline__ double sat_box(const double (*S)[34], int x0, int y0, int s)
+{
+    const int xa = min(max(x0, 0), 32), xb = min(max(x0 + s, 0), 32);
+    const int ya = min(max(y0, 0), 32), yb = min(max(y0 + s, 0), 32);
+    return S[yb][xb] - S[ya][xb] - S[yb][xa] + S[ya][xa];
+}
+
+template <int NW>
+__global__ void __launch_bounds__(128) train_bad_fwd_kernel(const float *__restrict__ patches, int rows,
+                                                            const short4 *__restrict__ box,
+                                                            const int *__restrict__ side,
+                                                            const float *__restrict__ theta,
+                                                            float inv_scale, float *__restrict__ r,
+                                                            uint32_t *__restrict__ bits)
+{
+    constexpr int K = NW * 32;
+    __shared__ double S[33][34];
+    __shared__ float P[32][33];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const float *p = patches + (size_t)row * 1024;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = t + q * 128;
+            P[e >> 5][e & 31] = __ldg(p + e);
+        }
+        if (t < 33) {
+            S[0][t] = 0.0;
+            S[t][0] = 0.0;
+        }
+        __syncthreads();
+        if (t < 32) {  // row prefix of patch row t
+            double acc = 0.0;
+            for (int x = 0; x < 32; ++x) {
+                acc += (double)P[t][x];
+                S[t + 1][x + 1] = acc;
+            }
+        }
+        __syncthreads();
+        if (t < 32) {  // column prefix of column t + 1
+            double acc = 0.0;
+            for (int y = 1; y <= 32; ++y) {
+                acc += S[y][t + 1];
+                S[y][t + 1] = acc;
+            }
+        }
+        __syncthreads();
+        for (int j = warp; j < NW; j += 4) {
+            const int k = j * 32 + lane;
+            const short4 b = __ldg(box + k);
+            const int s = __ldg(side + k);
+            const double d = sat_box(S, b.x, b.y, s) - sat_box(S, b.z, b.w, s);
+            const double th = (double)__ldg(theta + k);
+            const double s2 = (double)s * (double)s;
+            const bool bit = d <= th * s2;  // f = d / s^2 <= theta
+            const float f = (float)(d / s2);
+            r[(size_t)row * K + k] = tanhf(((float)th - f) * inv_scale);
+            const uint32_t word = __ballot_sync(FULL, bit);
+            if (lane == 0)
+                bits[(size_t)row * NW + j] = word;
+        }
+    }
+}
+
+template <int NW>
+__global__ void __launch_bounds__(128) train_mine_kernel(const uint32_t *__restrict__ bits, int n,
+                                                         int chunk, uint32_t *__restrict__ partial)
+{
+    __shared__ uint4 tile[MTT * NW / 4];
+    const int i = blockIdx.x * 128 + threadIdx.x;
+    const int j0 = blockIdx.y * chunk, j1 = min(n, j0 + chunk);
+    uint32_t qa[NW], qp[NW];
+#pragma unroll
+    for (int v = 0; v < NW; ++v) {
+        qa[v] = i < n ? __ldg(bits + (size_t)i * NW + v) : 0u;
+        qp[v] = i < n ? __ldg(bits + (size_t)(n + i) * NW + v) : 0u;
+    }
+    uint32_t best = 0xffffffffu;
+    const uint32_t *neg = bits + (size_t)2 * n * NW;
+    for (int base = j0; base < j1; base += MTT) {
+        const int cnt = min(MTT, j1 - base);
+        __syncthreads();
+        const uint4 *src = reinterpret_cast<const uint4 *>(neg + (size_t)base * NW);
+        for (int v = threadIdx.x; v < cnt * NW / 4; v += 128)
+            tile[v] = __ldg(src + v);
+        __syncthreads();
+        for (int jj = 0; jj < cnt; ++jj) {
+            uint32_t da = 0, dp = 0;
+#pragma unroll
+            for (int v = 0; v < NW / 4; ++v) {
+                const uint4 x = tile[jj * (NW / 4) + v];
+                da += __popc(qa[4 * v] ^ x.x) + __popc(qa[4 * v + 1] ^ x.y) + __popc(qa[4 * v + 2] ^ x.z) +
+                      __popc(qa[4 * v + 3] ^ x.w);
+                dp += __popc(qp[4 * v] ^ x.x) + __popc(qp[4 * v + 1] ^ x.y) + __popc(qp[4 * v + 2] ^ x.z) +
+                      __popc(qp[4 * v + 3] ^ x.w);
+            }
+            const int j = base + jj;
+            const uint32_t key = (min(da, dp) << 20) | (uint32_t)j;
+            if (j != i || n == 1)
+                best = min(best, key);
+        }
+    }
+    if (i < n)
+        partial[(size_t)blockIdx.y * n + i] = best;
+}
+
+__global__ void train_mine_merge_kernel(const uint32_t *__restrict__ partial, int n, int S,
+                                        const uint32_t *__restrict__ bits, int NW,
+                                        int32_t *__restrict__ nstar, int32_t *__restrict__ xsel)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    uint32_t best = 0xffffffffu;
+    for (int s = 0; s < S; ++s)
+        best = min(best, partial[(size_t)s * n + i]);
+    const int j = (int)(best & 0xfffffu);
+    uint32_t da = 0, dp = 0;
+    for (int v = 0; v < NW; ++v) {
+        const uint32_t nv = bits[(size_t)(2 * n + j) * NW + v];
+        da += __popc(bits[(size_t)i * NW + v] ^ nv);
+        dp += __popc(bits[(size_t)(n + i) * NW + v] ^ nv);
+    }
+    nstar[i] = j;
+    xsel[i] = da <= dp ? 0 : 1;  // S(a,n*) >= S(p,n*) keeps the anchor
+}
+
+// Warp per triplet: hinge term, loss accumulation and (backward) dL/dr.
+template <int K>
+__global__ void __launch_bounds__(256) train_loss_kernel(const float *__restrict__ r, int n,
+                                                         const int32_t *__restrict__ nstar,
+                                                         const int32_t *__restrict__ xsel, float tau,
+                                                         const float *__restrict__ gw,
+                                                         double *__restrict__ loss_acc,
+                                                         float *__restrict__ dr)
+{
+    constexpr int Q = K / 32;
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n)
+        return;
+    const int xs = xsel[i];
+    const int nrow = 2 * n + nstar[i];
+    float ra[Q], rp[Q], rn[Q];
+    float sap = 0.f, sxn = 0.f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int k = q * 32 + lane;
+        ra[q] = r[(size_t)i * K + k];
+        rp[q] = r[(size_t)(n + i) * K + k];
+        rn[q] = r[(size_t)nrow * K + k];
+        sap = fmaf(ra[q], rp[q], sap);
+        sxn = fmaf(xs ? rp[q] : ra[q], rn[q], sxn);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sap += __shfl_xor_sync(FULL, sap, o);
+        sxn += __shfl_xor_sync(FULL, sxn, o);
+    }
+    const float term = tau - sap + sxn;
+    if (loss_acc && lane == 0 && term > 0.f)
+        atomicAdd(loss_acc, (double)term);
+    if (!dr)
+        return;
+    const float w = *gw;
+    const bool on = term > 0.f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int k = q * 32 + lane;
+        const float rx = xs ? rp[q] : ra[q];
+        dr[(size_t)i * K + k] = on ? w * (-rp[q] + (xs ? 0.f : rn[q])) : 0.f;
+        dr[(size_t)(n + i) * K + k] = on ? w * (-ra[q] + (xs ? rn[q] : 0.f)) : 0.f;
+        if (on)
+            atomicAdd(dr + (size_t)nrow * K + k, w * rx);
+    }
+}
+
+__global__ void train_loss_finish_kernel(const double *__restrict__ acc, float *__restrict__ loss)
+{
+    if (threadIdx.x < 2)
+        loss[threadIdx.x] = (float)acc[threadIdx.x];
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) train_bad_bwd_kernel(int rows, const short4 *__restrict__ box,
+                                                            const int *__restrict__ side,
+                                                            const float *__restrict__ r,
+                                                            const float *__restrict__ dr,
+                                                            float inv_scale,
+                                                            float *__restrict__ dtheta,
+                                                            float *__restrict__ dpatches)
+{
+    __shared__ float D[33][33];
+    float dth[K / 128];
+#pragma unroll
+    for (int q = 0; q < K / 128; ++q)
+        dth[q] = 0.f;
+    const int t = threadIdx.x;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        __syncthreads();
+        for (int e = t; e < 33 * 33; e += 128)
+            (&D[0][0])[e] = 0.f;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < K / 128; ++q) {
+            const int k = q * 128 + t;
+            const float rv = r[(size_t)row * K + k];
+            const float dz = dr[(size_t)row * K + k] * (1.f - rv * rv);
+            dth[q] += dz * inv_scale;
+            if (dz == 0.f)
+                continue;
+            const int s = __ldg(side + k);
+            const float g = -dz * inv_scale / (float)(s * s);  // z = (theta - f)/(255 T)
+            const short4 b = __ldg(box + k);
+#pragma unroll
+            for (int bx = 0; bx < 2; ++bx) {
+                const int x0 = bx ? b.z : b.x, y0 = bx ? b.w : b.y;
+                const float sg = bx ? -g : g;
+                const int xa = min(max(x0, 0), 32), xb = min(max(x0 + s, 0), 32);
+                const int ya = min(max(y0, 0), 32), yb = min(max(y0 + s, 0), 32);
+                if (xa < xb && ya < yb) {
+                    atomicAdd(&D[ya][xa], sg);
+                    atomicAdd(&D[ya][xb], -sg);
+                    atomicAdd(&D[yb][xa], -sg);
+                    atomicAdd(&D[yb][xb], sg);
+                }
+            }
+        }
+        __syncthreads();
+        if (t < 32) {  // prefix along x of row t
+            float acc = 0.f;
+            for (int x = 0; x < 32; ++x) {
+                acc += D[t][x];
+                D[t][x] = acc;
+            }
+        }
+        __syncthreads();
+        if (t < 32) {  // prefix along y of column t
+            float acc = 0.f;
+            for (int y = 0; y < 32; ++y) {
+                acc += D[y][t];
+                D[y][t] = acc;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = t + q * 128;
+            dpatches[(size_t)row * 1024 + e] = D[e >> 5][e & 31];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < K / 128; ++q)
+        atomicAdd(dtheta + q * 128 + t, dth[q]);
+}
+
+__global__ void transpose_w_kernel(const float *__restrict__ W, int K, float *__restrict__ Wt)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < 128 * K) {
+        const int q = e / K, k = e % K;
+        Wt[(size_t)k * 128 + q] = W[e];
+    }
+}
+
+// dW = H^T dM and db = colsum(dM), dM = dr (1 - r^2) / T; rows split across CTAs.
+constexpr int DW_ROWS = 1024;
+__global__ void __launch_bounds__(256) train_hs_dw_kernel(int rows, int K, const float *__restrict__ h,
+                                                          const float *__restrict__ r,
+                                                          const float *__restrict__ dr, float inv_t,
+                                                          float *__restrict__ dW,
+                                                          float *__restrict__ db)
+{
+    __shared__ float Hs[32][128 + 4];
+    __shared__ float Ms[32][64];
+    const int t = threadIdx.x;
+    const int tq = t >> 3, tk = t & 7;  // 32 x 8 threads: 4 q x 8 k outputs each
+    const int k0 = blockIdx.y * 64;
+    const int r0 = blockIdx.x * DW_ROWS, r1 = min(rows, r0 + DW_ROWS);
+    float acc[4][8];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            acc[a][b] = 0.f;
+    float dbs = 0.f;
+    for (int base = r0; base < r1; base += 32) {
+        __syncthreads();
+        for (int e = t; e < 32 * 128; e += 256) {
+            const int rr = e >> 7, q = e & 127;
+            Hs[rr][q] = base + rr < r1 ? h[(size_t)(base + rr) * 128 + q] : 0.f;
+        }
+        for (int e = t; e < 32 * 64; e += 256) {
+            const int rr = e >> 6, k = e & 63;
+            float m = 0.f;
+            if (base + rr < r1) {
+                const float rv = r[(size_t)(base + rr) * K + k0 + k];
+                m = dr[(size_t)(base + rr) * K + k0 + k] * (1.f - rv * rv) * inv_t;
+            }
+            Ms[rr][k] = m;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr) {
+            float hv[4], mv[8];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                hv[a] = Hs[rr][tq * 4 + a];
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+                mv[b] = Ms[rr][tk * 8 + b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b)
+                    acc[a][b] = fmaf(hv[a], mv[b], acc[a][b]);
+        }
+        if (t < 64)
+            for (int rr = 0; rr < 32; ++rr)
+                dbs += Ms[rr][t];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            atomicAdd(dW + (size_t)(tq * 4 + a) * K + k0 + tk * 8 + b, acc[a][b]);
+    if (t < 64)
+        atomicAdd(db + k0 + t, dbs);
+}
+
+// Patch gradient of the HashSIFT loss (added to dpatches), one patch per CTA
+// iteration: dh = W dM, the normalisation adjoint, then the histogram adjoint.
+template <int K>
+__global__ void __launch_bounds__(128) train_hs_bwd_kernel(const float *__restrict__ patches,
+                                                           int rows, const float *__restrict__ Wt,
+                                                           const float *__restrict__ h,
+                                                           const float *__restrict__ norm,
+                                                           const float *__restrict__ r,
+                                                           const float *__restrict__ dr,
+                                                           float inv_t,
+                                                           float *__restrict__ dpatches)
+{
+    __shared__ float P[32][33];
+    __shared__ float gxs[32][33], gys[32][33];
+    __shared__ float dm[K];
+    __shared__ float dH[128];
+    __shared__ float red[4];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const dev::HistLane L = dev::hist_lane(t);
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        __syncthreads();
+        for (int k = t; k < K; k += 128) {
+            const float rv = r[(size_t)row * K + k];
+            dm[k] = dr[(size_t)row * K + k] * (1.f - rv * rv) * inv_t;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = t + q * 128;
+            P[e >> 5][e & 31] = __ldg(patches + (size_t)row * 1024 + e);
+        }
+        __syncthreads();
+        // dh_t = sum_k W[t][k] dm[k]
+        float dh = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < K; ++k)
+            dh = fmaf(__ldg(Wt + (size_t)k * 128 + t), dm[k], dh);
+        const float ht = h[(size_t)row * 128 + t];
+        float hd = ht * dh;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            hd += __shfl_xor_sync(FULL, hd, o);
+        if (lane == 0)
+            red[warp] = hd;
+        __syncthreads();
+        hd = red[0] + red[1] + red[2] + red[3];
+        const float nrm = norm[row];
+        dH[t] = nrm > 0.f ? (dh - ht * hd) / nrm : 0.f;
+        __syncthreads();
+        // per-pixel adjoint of the votes: thread t owns one pixel row of one cell
+        const int i = L.i;
+        const int iu = max(i - 1, 0), id = min(i + 1, 31);
+        const int cell = t >> 3;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int j = L.j0 + q;
+            const int jl = max(j - 1, 0), jr = min(j + 1, 31);
+            const float gx = 0.5f * (P[i][jr] - P[i][jl]);
+            const float gy = 0.5f * (P[id][j] - P[iu][j]);
+            const float m2 = gx * gx + gy * gy;
+            float dgx = 0.f, dgy = 0.f;
+            if (m2 > 0.f && nrm > 0.f) {
+                const float m = sqrtf(m2);
+                float phi = atan2f(gy, gx);
+                if (phi < 0.0f)
+                    phi += 6.28318530717958647692f;
+                const float tt = phi * 1.27323954473516268615f;
+                const float fl = floorf(tt);
+                const float w1 = tt - fl;
+                const int b0 = ((int)fl) & 7, b1 = (b0 + 1) & 7;
+                const float d0 = dH[cell * 8 + b0], d1 = dH[cell * 8 + b1];
+                const float g = L.g[q];
+                const float dmag = g * ((1.f - w1) * d0 + w1 * d1);
+                const float dphi = g * m * (d1 - d0) * 1.27323954473516268615f;
+                dgx = dmag * gx / m - dphi * gy / m2;
+                dgy = dmag * gy / m + dphi * gx / m2;
+            }
+            gxs[i][j] = dgx;
+            gys[i][j] = dgy;
+        }
+        __syncthreads();
+        // gather: gx(i,c) reads columns jr(c) (+) and jl(c) (-); gy likewise for rows
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = t + q * 128;
+            const int y = e >> 5, x = e & 31;
+            float v = 0.f;
+            if (x >= 1) v += gxs[y][x - 1];      // jr(x-1) = x
+            if (x == 31) v += gxs[y][31];        // jr(31) = 31
+            if (x <= 30) v -= gxs[y][x + 1];     // jl(x+1) = x
+            if (x == 0) v -= gxs[y][0];          // jl(0) = 0
+            if (y >= 1) v += gys[y - 1][x];
+            if (y == 31) v += gys[31][x];
+            if (y <= 30) v -= gys[y + 1][x];
+            if (y == 0) v -= gys[0][x];
+            dpatches[(size_t)row * 1024 + e] += 0.5f * v;
+        }
+    }
+}
+
+void mine_plan(int n, int sm_count, int &S, int &chunk)
+{
+    const int qb = (n + 127) / 128;
+    S = (8 * sm_count + qb - 1) / qb;
+    const int maxs = (n + 255) / 256;
+    if (S > maxs)
+        S = maxs;
+    if (S < 1)
+        S = 1;
+    chunk = (n + S - 1) / S;
+    S = (n + chunk - 1) / chunk;
+    if (S < 1)
+        S = 1;
+}
+
+int grid_rows(int rows, int sm_count, int per_sm)
+{
+    const long long g = (long long)sm_count * per_sm;
+    return (int)(rows < g ? rows : g);
+}
+
+}  // namespace
+}  // namespace bd
+
+extern "C" {
+
+bd_status bd_train_create(bd_ctx *ctx, const bd_bad_params *bad, int hs_bits, int n,
+                          float temperature, float tau_bad, float tau_hs, bd_train **out)
+{
+    if (!ctx || !out)
+        return BD_ERR_INVALID;
+    *out = nullptr;
+    if (!bad || (hs_bits != 256 && hs_bits != 512) || n < 1 || n > (1 << 20) ||
+        !(temperature > 0.f) || !isfinite(tau_bad) || !isfinite(tau_hs))
+        return set_err(ctx, BD_ERR_INVALID, "bd_train_create: bad arguments");
+    bd_train *tr = new bd_train();
+    tr->ctx = ctx;
+    tr->bad = bad;
+    tr->n = n;
+    tr->rows = 3 * n;
+    tr->kb = bad->nbits;
+    tr->kh = hs_bits;
+    tr->T = temperature;
+    tr->tau_bad = tau_bad;
+    tr->tau_hs = tau_hs;
+    mine_plan(n, ctx->sm_count, tr->splits, tr->chunk);
+    const size_t R = (size_t)tr->rows;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device)
+        cudaSetDevice(ctx->device);
+    cudaError_t e = cudaMalloc(&tr->r_bad, sizeof(float) * R * tr->kb);
+    if (e == cudaSuccess) e = cudaMalloc(&tr->r_hs, sizeof(float) * R * tr->kh);
+    if (e == cudaSuccess) e = cudaMalloc(&tr->h, sizeof(float) * R * 128);
+    if (e == cudaSuccess) e = cudaMalloc(&tr->norm, sizeof(float) * R);
+    if (e == cudaSuccess) e = cudaMalloc(&tr->bits_bad, sizeof(uint32_t) * R * (tr->kb / 32));
+    if (e == cudaSuccess) e = cudaMalloc(&tr->bits_hs, sizeof(uint32_t) * R * (tr->kh / 32));
+    if (e == cudaSuccess) e = cudaMalloc(&tr->partial, sizeof(uint32_t) * (size_t)tr->splits * n);
+    if (e == cudaSuccess) e = cudaMalloc(&tr->mining, sizeof(int32_t) * 4 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&tr->dr_bad, sizeof(float) * R * tr->kb);
+    if (e == cudaSuccess) e = cudaMalloc(&tr->dr_hs, sizeof(float) * R * tr->kh);
+    if (e == cudaSuccess) e = cudaMalloc(&tr->Wt, sizeof(float) * 128 * tr->kh);
+    if (e == cudaSuccess) e = cudaMalloc(&tr->loss_acc, sizeof(double) * 2);
+    if (prev >= 0 && prev != ctx->device)
+        cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        bd_train_destroy(tr);
+        return cuda_err(ctx, e, "bd_train_create");
+    }
+    *out = tr;
+    return BD_OK;
+}
+
+void bd_train_destroy(bd_train *tr)
+{
+    if (!tr)
+        return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != tr->ctx->device)
+        cudaSetDevice(tr->ctx->device);
+    cudaStreamSynchronize(tr->ctx->stream);
+    for (void *p : {(void *)tr->r_bad, (void *)tr->r_hs, (void *)tr->h, (void *)tr->norm,
+                    (void *)tr->bits_bad, (void *)tr->bits_hs, (void *)tr->partial,
+                    (void *)tr->mining, (void *)tr->dr_bad, (void *)tr->dr_hs, (void *)tr->Wt,
+                    (void *)tr->loss_acc})
+        if (p)
+            cudaFree(p);
+    if (prev >= 0 && prev != tr->ctx->device)
+        cudaSetDevice(prev);
+    delete tr;
+}
+
+bd_status bd_train_forward(bd_ctx *ctx, bd_train *tr, const float *patches, const float *theta,
+                           const float *W, const float *b, const int32_t *fixed_mining,
+                           float *loss, int32_t *mining_out)
+{
+    if (!ctx || !tr || tr->ctx != ctx || !patches || !theta || !W || !b || !loss)
+        return BD_ERR_INVALID;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device)
+        cudaSetDevice(ctx->device);
+    cudaStream_t st = ctx->stream;
+    TraceScope scope(ctx, st);
+    const int n = tr->n, rows = tr->rows, sm = ctx->sm_count;
+    const float inv_scale = 1.0f / (255.0f * tr->T);
+    const bd_bad_params *bp = tr->bad;
+    cudaError_t e = cudaSuccess;
+    // relaxed BAD
+    if (tr->kb == 256)
+        train_bad_fwd_kernel<8><<<grid_rows(rows, sm, 16), 128, 0, st>>>(
+            patches, rows, bp->d_patch_box, bp->d_patch_side, theta, inv_scale, tr->r_bad, tr->bits_bad);
+    else
+        train_bad_fwd_kernel<16><<<grid_rows(rows, sm, 16), 128, 0, st>>>(
+            patches, rows, bp->d_patch_box, bp->d_patch_side, theta, inv_scale, tr->r_bad, tr->bits_bad);
+    trace_kernel(st, "train_bad_fwd");
+    // relaxed HashSIFT
+    e = launch_hs_hist_patches(patches, rows, tr->h, nullptr, st, sm, tr->norm);
+    if (e == cudaSuccess)
+        e = launch_hs_proj_fp32_raw(W, b, tr->kh, tr->h, rows, tr->bits_hs, tr->r_hs, 1.0f / tr->T, st);
+    // mining on hard codes, or the given mining
+    if (e == cudaSuccess && fixed_mining) {
+        e = cudaMemcpyAsync(tr->mining, fixed_mining, sizeof(int32_t) * 4 * (size_t)n,
+                            cudaMemcpyDeviceToDevice, st);
+    } else if (e == cudaSuccess) {
+        dim3 grid((n + 127) / 128, tr->splits);
+        for (int d = 0; d < 2; ++d) {
+            const uint32_t *bits = d == 0 ? tr->bits_bad : tr->bits_hs;
+            const int nw = (d == 0 ? tr->kb : tr->kh) / 32;
+            if (nw == 8)
+                train_mine_kernel<8><<<grid, 128, 0, st>>>(bits, n, tr->chunk, tr->partial);
+            else
+                train_mine_kernel<16><<<grid, 128, 0, st>>>(bits, n, tr->chunk, tr->partial);
+            trace_kernel(st, "train_mine");
+            train_mine_merge_kernel<<<(n + 255) / 256, 256, 0, st>>>(
+                tr->partial, n, tr->splits, bits, nw, tr->mining + (size_t)(2 * d) * n,
+                tr->mining + (size_t)(2 * d + 1) * n);
+            trace_kernel(st, "train_mine_merge");
+        }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(tr->loss_acc, 0, sizeof(double) * 2, st);
+    if (e == cudaSuccess) {
+        const int blocks = (n * 32 + 255) / 256;
+        for (int d = 0; d < 2; ++d) {
+            const float *r = d == 0 ? tr->r_bad : tr->r_hs;
+            const int K = d == 0 ? tr->kb : tr->kh;
+            const float tau = d == 0 ? tr->tau_bad : tr->tau_hs;
+            const int32_t *ns = tr->mining + (size_t)(2 * d) * n, *xs = ns + n;
+            if (K == 256)
+                train_loss_kernel<256><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, nullptr, tr->loss_acc + d, nullptr);
+            else
+                train_loss_kernel<512><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, nullptr, tr->loss_acc + d, nullptr);
+            trace_kernel(st, "train_loss");
+        }
+        train_loss_finish_kernel<<<1, 32, 0, st>>>(tr->loss_acc, loss);
+        trace_kernel(st, "train_loss_finish");
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && mining_out)
+        e = cudaMemcpyAsync(mining_out, tr->mining, sizeof(int32_t) * 4 * (size_t)n,
+                            cudaMemcpyDeviceToDevice, st);
+    note_launches(fixed_mining ? 6 : 10);
+    if (prev >= 0 && prev != ctx->device)
+        cudaSetDevice(prev);
+    return e == cudaSuccess ? BD_OK : cuda_err(ctx, e, "bd_train_forward");
+}
+
+bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, const float *W,
+                            const float *grad_loss, float *dtheta, float *dW, float *db,
+                            float *dpatches)
+{
+    if (!ctx || !tr || tr->ctx != ctx || !patches || !W || !grad_loss || !dtheta || !dW || !db ||
+        !dpatches)
+        return BD_ERR_INVALID;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device)
+        cudaSetDevice(ctx->device);
+    cudaStream_t st = ctx->stream;
+    TraceScope scope(ctx, st);
+    const int n = tr->n, rows = tr->rows, sm = ctx->sm_count;
+    const size_t R = (size_t)rows;
+    const float inv_scale = 1.0f / (255.0f * tr->T), inv_t = 1.0f / tr->T;
+    const bd_bad_params *bp = tr->bad;
+    cudaError_t e = cudaSuccess;
+    // dL/dr: negatives' rows collect with atomics, so they start at zero
+    e = cudaMemsetAsync(tr->dr_bad + (size_t)2 * n * tr->kb, 0, sizeof(float) * n * tr->kb, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(tr->dr_hs + (size_t)2 * n * tr->kh, 0, sizeof(float) * n * tr->kh, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(dtheta, 0, sizeof(float) * tr->kb, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(dW, 0, sizeof(float) * 128 * tr->kh, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(db, 0, sizeof(float) * tr->kh, st);
+    if (e == cudaSuccess) {
+        const int blocks = (n * 32 + 255) / 256;
+        for (int d = 0; d < 2; ++d) {
+            const float *r = d == 0 ? tr->r_bad : tr->r_hs;
+            float *drp = d == 0 ? tr->dr_bad : tr->dr_hs;
+            const int K = d == 0 ? tr->kb : tr->kh;
+            const float tau = d == 0 ? tr->tau_bad : tr->tau_hs;
+            const int32_t *ns = tr->mining + (size_t)(2 * d) * n, *xs = ns + n;
+            if (K == 256)
+                train_loss_kernel<256><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, grad_loss + d, nullptr, drp);
+            else
+                train_loss_kernel<512><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, grad_loss + d, nullptr, drp);
+            trace_kernel(st, "train_dr");
+        }
+        // BAD: dtheta and the patch gradient (written, not added)
+        if (tr->kb == 256)
+            train_bad_bwd_kernel<256><<<grid_rows(rows, sm, 12), 128, 0, st>>>(
+                rows, bp->d_patch_box, bp->d_patch_side, tr->r_bad, tr->dr_bad, inv_scale, dtheta, dpatches);
+        else
+            train_bad_bwd_kernel<512><<<grid_rows(rows, sm, 12), 128, 0, st>>>(
+                rows, bp->d_patch_box, bp->d_patch_side, tr->r_bad, tr->dr_bad, inv_scale, dtheta, dpatches);
+        trace_kernel(st, "train_bad_bwd");
+        // HashSIFT: dW, db, then the patch gradient (added)
+        transpose_w_kernel<<<(128 * tr->kh + 255) / 256, 256, 0, st>>>(W, tr->kh, tr->Wt);
+        dim3 g2((rows + DW_ROWS - 1) / DW_ROWS, tr->kh / 64);
+        train_hs_dw_kernel<<<g2, 256, 0, st>>>(rows, tr->kh, tr->h, tr->r_hs, tr->dr_hs, inv_t, dW, db);
+        trace_kernel(st, "train_hs_dw");
+        if (tr->kh == 256)
+            train_hs_bwd_kernel<256><<<grid_rows(rows, sm, 8), 128, 0, st>>>(
+                patches, rows, tr->Wt, tr->h, tr->norm, tr->r_hs, tr->dr_hs, inv_t, dpatches);
+        else
+            train_hs_bwd_kernel<512><<<grid_rows(rows, sm, 8), 128, 0, st>>>(
+                patches, rows, tr->Wt, tr->h, tr->norm, tr->r_hs, tr->dr_hs, inv_t, dpatches);
+        trace_kernel(st, "train_hs_bwd");
+        e = cudaGetLastError();
+    }
+    note_launches(7);
+    (void)R;
+    if (prev >= 0 && prev != ctx->device)
+        cudaSetDevice(prev);
+    return e == cudaSuccess ? BD_OK : cuda_err(ctx, e, "bd_train_backward");
+}
+
+}  // extern "C"
