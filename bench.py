@@ -476,13 +476,57 @@ def roofline(wl, per_kernel, clocks):
 HS_OPS_PER_PIXEL = 30
 
 
+def run_train(args):
+    """Training-step workload: 65536 triplets of 32x32 FP32 patches, relaxed
+    BAD-256 + HashSIFT-256 (T = 0.1), mining with anchor swap, loss, backward."""
+    import torch
+    import paper_2108_08380_gb300 as bd
+    import synth
+    n = 65536
+    rng = np.random.default_rng(1003)
+    P = torch.from_numpy(synth.triplet_workload(1003, n=n).patches).cuda()
+    bad = synth.make_bad_params(256, rng)
+    theta = torch.from_numpy(rng.uniform(-20, 20, size=256).astype(np.float32)).cuda()
+    hs = synth.make_hashsift_params(256, rng)
+    W, b = torch.from_numpy(hs.W).cuda(), torch.from_numpy(hs.b).cuda()
+    ctx = bd.Context(0)
+    ctx.trace(True)
+    step = bd.TrainStep(ctx, ctx.bad_params(bad), 256, n, temperature=0.1)
+    g = torch.ones(2, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        step.forward(P, theta, W, b)
+        step.backward(P, W, g)
+    torch.cuda.synchronize()
+    K = args.steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kern = {}
+    tot = 0.0
+    for _ in range(K):
+        ctx.trace_reset()
+        e0.record()
+        step.forward(P, theta, W, b)
+        step.backward(P, W, g)
+        e1.record()
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+        for name, ms in ctx.trace_read():
+            kern[name] = kern.get(name, 0.0) + ms / K
+    ms = tot / K
+    print(json.dumps({"metric": "training steps (forward + backward) per second", "value": 1e3 / ms,
+                      "unit": "steps/s", "ms_per_step": ms, "triplets_per_s": n * 1e3 / ms,
+                      "steps": K, "config": {"workload": "65536 triplets of 32x32 FP32 patches, "
+                                             "BAD-256 + HashSIFT-256 relaxed at T = 0.1, mining with "
+                                             "anchor swap, full backward"},
+                      "kernel_ms": kern}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["plain", "large", "batch"], default="plain")
+    ap.add_argument("--workload", choices=["plain", "large", "batch", "train"], default="plain")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
@@ -490,6 +534,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "train":
+        run_train(args)
     else:
         run_ours(args)
 

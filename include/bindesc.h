@@ -356,6 +356,17 @@ bd_status bd_bad_describe_noalloc(const bd_bad_params *p, const uint8_t *img, in
                                   int pitch, const bd_keypoint *kps, int n, uint32_t *out,
                                   void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Tensor-core matching                                                      */
+
+/* Same contract and results as bd_match, computed on the tensor cores: the
+ * codes are expanded to +-1 in FP8 E4M3 and the similarity S = h(q)^T h(t)
+ * = nbits - 2 Hamming (Sec. III-A) is accumulated exactly in FP32 by
+ * tcgen05 MMAs, with the top-2 and ratio test fused into the epilogue.
+ * Needs (nq + nt) * nbits bytes of scratch; nq <= 65535 * 128. */
+bd_status bd_match_tc(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt,
+                      int nbits, int ratio_num, int ratio_den, bd_match_result *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -65,6 +65,7 @@ _SIGS = [
     ("bd_hashsift_project", _I, [_P, _P, _P, _I, _P]),
     ("bd_hashsift_describe", _I, [_P, _P, _P, _I, _I, _I, _P, _I, _P, _P]),
     ("bd_match", _I, [_P, _P, _I, _P, _I, _I, _I, _I, _P]),
+    ("bd_match_tc", _I, [_P, _P, _I, _P, _I, _I, _I, _I, _P]),
     ("bd_batch_create", _I, [_P, _P, _P, _I, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     ("bd_batch_destroy", None, [_P]),
     ("bd_batch_set_config", _I, [_P, _P]),
@@ -295,16 +296,19 @@ class Context:
                                                _ptr(hist_out)), "bd_hashsift_describe")
         return out
 
-    def match(self, q, t, nbits: int, ratio_num: int = 4, ratio_den: int = 5, out=None):
+    def match(self, q, t, nbits: int, ratio_num: int = 4, ratio_den: int = 5, out=None,
+              tensor_cores: bool = False):
         """Returns an int32 [nq, 3] tensor viewing bd_match_result records:
-        column 0 = idx, column 1 = d1 | d2 << 16, column 2 = accept."""
+        column 0 = idx, column 1 = d1 | d2 << 16, column 2 = accept.
+        tensor_cores selects bd_match_tc (same results)."""
         torch = self._torch
         nq, nt = q.shape[0], t.shape[0]
         if out is None:
             out = torch.empty((nq, 3), dtype=torch.int32, device=q.device)
         self._stream()
-        self._check(lib().bd_match(self.handle, _ptr(q), nq, _ptr(t), nt, nbits, ratio_num, ratio_den,
-                                   _ptr(out)), "bd_match")
+        fn = lib().bd_match_tc if tensor_cores else lib().bd_match
+        self._check(fn(self.handle, _ptr(q), nq, _ptr(t), nt, nbits, ratio_num, ratio_den, _ptr(out)),
+                    "bd_match_tc" if tensor_cores else "bd_match")
         return out
 
 

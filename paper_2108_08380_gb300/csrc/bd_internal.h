@@ -57,6 +57,8 @@ struct bd_ctx {
     bd::DeviceStatus *status = nullptr;  // device
     void *scratch = nullptr;             // device, grows on demand
     size_t scratch_bytes = 0;
+    unsigned int *arrivals = nullptr;    // device, zeroed per-block arrival counters (matching)
+    int arrivals_cap = 0;
     std::string err;
     // tracing (bd_trace_*)
     bool trace = false;
@@ -128,6 +130,8 @@ void trace_kernel(cudaStream_t st, const char *label);
 // TMA descriptor encoding through the driver entry point (no -lcuda needed).
 bool encode_tmap_2d_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
                          uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer);
+bool encode_tmap_2d_u8(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
+                       uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer);
 
 // ---------------------------------------------------------------------------
 // kernel launchers (each returns cudaGetLastError() of its launch)
@@ -171,9 +175,22 @@ cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const CUtensorMap &tm_hi,
                               DeviceStatus *status, cudaStream_t st, const bd_keypoint *kps);
 
 size_t match_scratch_bytes(int nq, int nt, int nbits, int sm_count);
+// tensor-core matching: scratch for the FP8 codes and split partials
+size_t match_tc_scratch_bytes(int nq, int nt, int nbits, int sm_count);
+int match_tc_query_blocks(int nq);
+cudaError_t launch_match_tc(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt,
+                            int nbits, int ratio_num, int ratio_den, bd_match_result *out,
+                            void *scratch, cudaStream_t st, unsigned int *arrivals);
+// same, returning the raw top-2 keys (distance << 22 | index) per query
+cudaError_t launch_match_tc_keys(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt,
+                                 int nbits, int ratio_num, int ratio_den, bd_match_result *out,
+                                 uint2 *raw_keys, void *scratch, cudaStream_t st,
+                                 unsigned int *arrivals);
+int match_query_blocks(int nq);
+// arrivals: one zero-initialised counter per query block (ctx-owned; each call leaves them zero)
 cudaError_t launch_match(const uint32_t *q, int nq, const uint32_t *t, int nt, int nbits,
                          int ratio_num, int ratio_den, bd_match_result *out, void *scratch,
-                         int sm_count, cudaStream_t st);
+                         int sm_count, cudaStream_t st, unsigned int *arrivals);
 
 }  // namespace bd
 
@@ -296,6 +313,33 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint6
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
+}
+
+// Instruction descriptor: kind::f8f6f4 with E4M3 A and B, FP32 accumulator,
+// both operands K-major, M x N tile.
+__host__ __device__ constexpr uint32_t umma_idesc_e4m3_f32(int M, int N)
+{
+    return (1u << 4)                       // D format: F32
+           | (0u << 7)                     // A format: E4M3
+           | (0u << 10)                    // B format: E4M3
+           | ((uint32_t)(N >> 3) << 17)    // N / 8
+           | ((uint32_t)(M >> 4) << 24);   // M / 16
+}
+
+__device__ __forceinline__ void umma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t *bar)

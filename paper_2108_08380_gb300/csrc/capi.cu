@@ -141,6 +141,22 @@ bool encode_tmap_2d_bf16(CUtensorMap *map, const void *base, uint64_t inner, uin
     return r == CUDA_SUCCESS;
 }
 
+bool encode_tmap_2d_u8(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
+                       uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer)
+{
+    PFN_encodeTiled fn = get_encode_fn();
+    if (!fn)
+        return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {row_bytes};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // Restores the caller's current device on scope exit.
 struct DeviceGuard {
     int prev = -1;
@@ -233,6 +249,8 @@ void bd_destroy(bd_ctx *ctx)
             cudaEventDestroy(ev);
         if (ctx->scratch)
             cudaFree(ctx->scratch);
+        if (ctx->arrivals)
+            cudaFree(ctx->arrivals);
         if (ctx->status)
             cudaFree(ctx->status);
     }
@@ -758,6 +776,52 @@ bd_status bd_hashsift_describe(bd_ctx *ctx, const bd_hs_params *p, const uint8_t
     return project(ctx, p, h32, h16, false, n, out, kps);
 }
 
+static bd_status ensure_arrivals(bd_ctx *ctx, int qblocks)
+{
+    if (qblocks <= ctx->arrivals_cap)
+        return BD_OK;
+    const int cap = qblocks < 4096 ? 4096 : qblocks;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess && ctx->arrivals)
+        e = cudaFree(ctx->arrivals);
+    ctx->arrivals = nullptr;
+    ctx->arrivals_cap = 0;
+    if (e == cudaSuccess)
+        e = cudaMalloc(&ctx->arrivals, sizeof(unsigned int) * cap);
+    if (e == cudaSuccess)
+        e = cudaMemset(ctx->arrivals, 0, sizeof(unsigned int) * cap);
+    if (e != cudaSuccess)
+        return cuda_err(ctx, e, "arrival counters");
+    ctx->arrivals_cap = cap;
+    return BD_OK;
+}
+
+bd_status bd_match_tc(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt, int nbits,
+                      int ratio_num, int ratio_den, bd_match_result *out)
+{
+    BD_GUARD(ctx);
+    if (((uintptr_t)q & 15) || ((uintptr_t)t & 15) || ((uintptr_t)out & 3))
+        return set_err(ctx, BD_ERR_INVALID,
+                       "bd_match_tc: descriptor arrays must be 16-byte and out 4-byte aligned");
+    if ((nbits != 256 && nbits != 512) || nq < 0 || nt < 0 || nt > (int)kMatchIdxMask ||
+        ratio_den <= 0 || ratio_num <= 0 || ratio_num > ratio_den || (nq > 0 && (!q || !out)) ||
+        (nt > 0 && !t) || (nq + 127) / 128 > 65535)
+        return set_err(ctx, BD_ERR_INVALID, "bd_match_tc: bad arguments");
+    if (nq == 0)
+        return BD_OK;
+    bd_status s = ensure_scratch(ctx, match_tc_scratch_bytes(nq, nt, nbits, ctx->sm_count));
+    if (s == BD_OK)
+        s = ensure_arrivals(ctx, match_tc_query_blocks(nq));
+    if (s != BD_OK)
+        return s;
+    TraceScope scope(ctx, ctx->stream);
+    BD_LAUNCH(ctx,
+              launch_match_tc(ctx, q, nq, t, nt, nbits, ratio_num, ratio_den, out, ctx->scratch,
+                              ctx->stream, ctx->arrivals),
+              "tensor-core matching kernels");
+    return BD_OK;
+}
+
 bd_status bd_match(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt, int nbits,
                    int ratio_num, int ratio_den, bd_match_result *out)
 {
@@ -774,11 +838,14 @@ bd_status bd_match(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, in
     bd_status s = ensure_scratch(ctx, match_scratch_bytes(nq, nt, nbits, ctx->sm_count));
     if (s != BD_OK)
         return s;
+    s = ensure_arrivals(ctx, match_query_blocks(nq));
+    if (s != BD_OK)
+        return s;
     TraceScope scope(ctx, ctx->stream);
     BD_LAUNCH(ctx,
               launch_match(q, nq, t, nt, nbits, ratio_num, ratio_den, out, ctx->scratch,
-                           ctx->sm_count, ctx->stream),
-              "matching kernels");
+                           ctx->sm_count, ctx->stream, ctx->arrivals),
+              "matching kernel");
     return BD_OK;
 }
 

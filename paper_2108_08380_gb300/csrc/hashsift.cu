@@ -90,10 +90,11 @@ __global__ void hs_to_bf16_kernel(const float *__restrict__ src, size_t count,
 }
 
 // ---------------------------------------------------------------------------
-// FP32 projection: margins m = W^T f + b accumulated in the order i = 0..127
-// (the tensor-core path's FP32 re-check uses the same order, so both paths
-// give the same bits), bit = m > 0.  Tile: 64 keypoints x 128 bits per CTA,
-// 4 x 8 outputs per thread.
+// FP32 projection: margins m = W^T f + b, bit = m > 0.  The sum runs in four
+// chunks of 32 terms, each a sequential fmaf chain from zero, combined as
+// ((c0 + c1) + c2) + c3 before the bias; the tensor-core path's FP32
+// re-check evaluates the same expression, so both paths give the same bits.
+// Tile: 64 keypoints x 128 bits per CTA, 4 x 8 outputs per thread.
 // ---------------------------------------------------------------------------
 constexpr int PBM = 64, PBN = 128, PBK = 32;
 
@@ -128,6 +129,12 @@ __global__ void __launch_bounds__(256) hs_proj_fp32_kernel(const float *__restri
             Ws[r][c] = __ldg(W + (size_t)(k0 + r) * K + n0 + c);
         }
         __syncthreads();
+        float part[4][8];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+                part[a][b] = 0.0f;
 #pragma unroll 8
         for (int kk = 0; kk < PBK; ++kk) {
             float hv[4], wv[8];
@@ -141,8 +148,13 @@ __global__ void __launch_bounds__(256) hs_proj_fp32_kernel(const float *__restri
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int b = 0; b < 8; ++b)
-                    acc[a][b] = fmaf(hv[a], wv[b], acc[a][b]);
+                    part[a][b] = fmaf(hv[a], wv[b], part[a][b]);
         }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+                acc[a][b] = k0 == 0 ? part[a][b] : acc[a][b] + part[a][b];
     }
     float bv[8];
 #pragma unroll

@@ -7,7 +7,8 @@
 // packed keys (distance << 22 | train index).  Comparing packed keys orders
 // by distance, then by lowest index, so the first key gives the nearest
 // neighbour and the second key's distance is d2.  When the train set is split
-// across CTAs, a second kernel merges the per-slice top-2 pairs.
+// across CTAs, each CTA publishes its per-slice top-2 pairs and the last CTA of
+// a query block (per-block arrival counter, reset by that CTA) merges them.
 #include "bd_internal.h"
 
 namespace bd {
@@ -35,12 +36,14 @@ __device__ __forceinline__ void finalize(uint32_t k1, uint32_t k2, int nbits, in
 }
 
 template <int NW>
-__global__ void __launch_bounds__(QB) match_top2_kernel(const uint32_t *__restrict__ q, int nq,
+__global__ void __launch_bounds__(QB, 8) match_top2_kernel(const uint32_t *__restrict__ q, int nq,
                                                         const uint32_t *__restrict__ t, int nt,
                                                         int chunk, int nbits, int rnum, int rden,
                                                         uint2 *__restrict__ partial,
-                                                        bd_match_result *__restrict__ out)
+                                                        bd_match_result *__restrict__ out,
+                                                        unsigned int *__restrict__ arrivals)
 {
+    __shared__ int last_cta;
     __shared__ uint4 tile[TT * NW / 4];
     const int qi = blockIdx.x * QB + threadIdx.x;
     const int t0 = blockIdx.y * chunk;
@@ -84,27 +87,31 @@ __global__ void __launch_bounds__(QB) match_top2_kernel(const uint32_t *__restri
             top2_push((d << kMatchIdxBits) | (uint32_t)(base + j), k1, k2);
         }
     }
-    if (qi >= nq)
+    if (gridDim.y == 1) {
+        if (qi < nq)
+            finalize(k1, k2, nbits, rnum, rden, out + qi);
         return;
-    if (gridDim.y == 1)
-        finalize(k1, k2, nbits, rnum, rden, out + qi);
-    else
+    }
+    if (qi < nq)
         partial[(size_t)blockIdx.y * nq + qi] = make_uint2(k1, k2);
-}
-
-__global__ void match_merge_kernel(const uint2 *__restrict__ partial, int nq, int S, int nbits,
-                                   int rnum, int rden, bd_match_result *__restrict__ out)
-{
-    const int qi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (qi >= nq)
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int prev = atomicAdd(arrivals + blockIdx.x, 1u);
+        last_cta = prev == gridDim.y - 1;
+        if (last_cta)
+            arrivals[blockIdx.x] = 0u;  // every slice has arrived: ready for the next call
+    }
+    __syncthreads();
+    if (!last_cta || qi >= nq)
         return;
-    uint2 a = partial[qi];
-#pragma unroll 8
-    for (int s = 1; s < S; ++s) {
-        const uint2 b = partial[(size_t)s * nq + qi];
-        const uint32_t k1 = min(a.x, b.x);
-        const uint32_t k2 = min(max(a.x, b.x), min(a.y, b.y));
-        a = make_uint2(k1, k2);
+    __threadfence();
+    uint2 a = __ldcg(partial + qi);
+    for (int s = 1; s < (int)gridDim.y; ++s) {
+        const uint2 b = __ldcg(partial + (size_t)s * nq + qi);
+        const uint32_t m1 = min(a.x, b.x);
+        const uint32_t m2 = min(max(a.x, b.x), min(a.y, b.y));
+        a = make_uint2(m1, m2);
     }
     finalize(a.x, a.y, nbits, rnum, rden, out + qi);
 }
@@ -137,9 +144,11 @@ size_t match_scratch_bytes(int nq, int nt, int nbits, int sm_count)
     return S > 1 ? align_up((size_t)S * nq * sizeof(uint2), 256) : 0;
 }
 
+int match_query_blocks(int nq) { return (nq + QB - 1) / QB; }
+
 cudaError_t launch_match(const uint32_t *q, int nq, const uint32_t *t, int nt, int nbits,
                          int ratio_num, int ratio_den, bd_match_result *out, void *scratch, int sm_count,
-                         cudaStream_t st)
+                         cudaStream_t st, unsigned int *arrivals)
 {
     int S, chunk;
     plan(nq, nt, sm_count, S, chunk);
@@ -147,17 +156,12 @@ cudaError_t launch_match(const uint32_t *q, int nq, const uint32_t *t, int nt, i
     uint2 *partial = (uint2 *)scratch;
     if (nbits == 256)
         match_top2_kernel<8><<<grid, QB, 0, st>>>(q, nq, t, nt, chunk, nbits, ratio_num, ratio_den,
-                                                  partial, out);
+                                                  partial, out, arrivals);
     else
         match_top2_kernel<16><<<grid, QB, 0, st>>>(q, nq, t, nt, chunk, nbits, ratio_num,
-                                                   ratio_den, partial, out);
+                                                   ratio_den, partial, out, arrivals);
     trace_kernel(st, "match_top2");
-    if (S > 1) {
-        match_merge_kernel<<<(nq + 255) / 256, 256, 0, st>>>(partial, nq, S, nbits, ratio_num,
-                                                             ratio_den, out);
-        trace_kernel(st, "match_merge");
-    }
-    note_launches(S > 1 ? 2 : 1);
+    note_launches(1);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,376 @@
+// Exact Hamming matching on the tensor cores.  With +-1 codes h(x) the
+// paper's similarity is S = h(x)^T h(y) = K - 2 Hamming(x, y) (Sec. III-A), a
+// dense contraction: the bits are expanded to FP8 E4M3 +-1 (exact), S is
+// accumulated by tcgen05.mma kind::f8f6f4 in FP32 (exact: |S| <= 512), and the
+// epilogue turns S into the distance (K - S)/2 and keeps a per-query top-2 of
+// packed (distance << 22 | index) keys, exactly like the POPC kernel.
+//
+// CTA = 12 warps, one 128-query tile, a range of 128-row train tiles:
+//  - warp 0 (one lane) loads the query tile once and the train tiles into a
+//    two-stage shared-memory ring with TMA (128-byte swizzle);
+//  - warp 1 (one lane) issues K/32 MMAs per train tile into one of two TMEM
+//    accumulators (128 x 128 FP32 each) and commits them to mbarriers;
+//  - warps 4..11 drain the accumulators: warps w and w+4 share TMEM lane
+//    quadrant w%4 (32 queries) and take 64 columns each, freeing the buffer
+//    for the next MMA before they update their top-2 keys.
+// Train tiles are split across CTAs; partial top-2 pairs are merged by the
+// last CTA of each query block (per-block arrival counter).  Every wait is
+// bounded by the GPU timer; on expiry the CTA raises BD_FLAG_TIMEOUT.
+#include "bd_internal.h"
+
+namespace bd {
+namespace {
+
+constexpr int BM = 128, BN = 128;
+constexpr int NTHREADS = 384;
+constexpr int EPI_WARPS = 8;
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long gtime()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+{
+    if (dev::mbar_try_wait(bar, parity))
+        return true;
+    const unsigned long long t0 = gtime();
+    while (!dev::mbar_try_wait(bar, parity)) {
+        if (*abort_flag || gtime() - t0 > kWaitNs)
+            return false;
+    }
+    return true;
+}
+
+// Packed bits -> one byte per bit: +1.0 (E4M3 0x38) for a set bit, -1.0 (0xB8) otherwise.
+__global__ void expand_pm1_kernel(const uint32_t *__restrict__ bits, size_t words,
+                                  uint4 *__restrict__ out)
+{
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < words;
+         w += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t v = __ldg(bits + w);
+        uint32_t o[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            uint32_t x = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                x |= (((v >> (4 * q + b)) & 1u) ? 0x38u : 0xB8u) << (8 * b);
+            o[q] = x;
+        }
+        out[2 * w] = make_uint4(o[0], o[1], o[2], o[3]);
+        out[2 * w + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+    }
+}
+
+__device__ __forceinline__ void top2_push(uint32_t key, uint32_t &k1, uint32_t &k2)
+{
+    k2 = min(k2, max(k1, key));
+    k1 = min(k1, key);
+}
+
+__device__ __forceinline__ void top2_merge(uint32_t b1, uint32_t b2, uint32_t &k1, uint32_t &k2)
+{
+    const uint32_t m1 = min(k1, b1);
+    const uint32_t m2 = min(max(k1, b1), min(k2, b2));
+    k1 = m1;
+    k2 = m2;
+}
+
+__device__ __forceinline__ void finalize(uint32_t k1, uint32_t k2, int nbits, int rnum, int rden,
+                                         bd_match_result *o)
+{
+    const uint32_t d1 = k1 >> kMatchIdxBits, d2 = k2 >> kMatchIdxBits;
+    const int32_t idx = (d1 > (uint32_t)nbits) ? -1 : (int32_t)(k1 & kMatchIdxMask);
+    const uint32_t acc = ((long long)rden * d1 < (long long)rnum * d2) ? 1u : 0u;
+    uint32_t *w = reinterpret_cast<uint32_t *>(o);
+    w[0] = (uint32_t)idx;
+    w[1] = d1 | (d2 << 16);
+    w[2] = acc;
+}
+
+template <int K>
+__global__ void __launch_bounds__(NTHREADS, 1) match_tc_kernel(
+    const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmT, int nq,
+    int nt, int tiles_per_split, int nbits, int rnum, int rden, uint2 *__restrict__ partial,
+    bd_match_result *__restrict__ out, uint2 *__restrict__ raw_keys,
+    unsigned int *__restrict__ arrivals, DeviceStatus *status)
+{
+    constexpr int CH = K / 128;          // 128-byte K chunks per row
+    constexpr int A_BYTES = BM * K;
+    constexpr int B_BYTES = BN * K;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;
+    uint8_t *sB0 = smem + A_BYTES;
+    __shared__ uint64_t bar_a, bar_bf[2], bar_be[2], bar_tf[2], bar_te[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ int last_cta;
+    __shared__ uint2 half_keys[BM];
+
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int qb = blockIdx.x, split = blockIdx.y;
+    const int ntiles = (nt + BN - 1) / BN;
+    const int tile0 = split * tiles_per_split;
+    const int count = max(0, min(ntiles, tile0 + tiles_per_split) - tile0);
+
+    if (t == 0) {
+        dev::mbar_init(&bar_a, 1);
+        for (int s = 0; s < 2; ++s) {
+            dev::mbar_init(&bar_bf[s], 1);
+            dev::mbar_init(&bar_be[s], 1);
+            dev::mbar_init(&bar_tf[s], 1);
+            dev::mbar_init(&bar_te[s], EPI_WARPS);
+        }
+        dev::fence_mbar_init();
+        abort_flag = 0;
+    }
+    if (warp == 0)
+        dev::tmem_alloc(&tmem_slot, 2 * BN);
+    dev::tc_fence_before();
+    __syncthreads();
+    dev::tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t sentinel = ((uint32_t)(nbits + 1) << kMatchIdxBits) | kMatchIdxMask;
+
+    int issued = 0;  // MMA commits (warp 1)
+    if (warp == 0 && lane == 0 && count > 0) {
+        dev::mbar_arrive_expect_tx(&bar_a, A_BYTES);
+        for (int c = 0; c < CH; ++c)
+            dev::tma_load_2d(sA + c * BM * 128, &tmQ, c * 128, qb * BM, &bar_a);
+        for (int i = 0; i < count; ++i) {
+            const int s = i & 1;
+            if (i >= 2 && !wait_bar(&bar_be[s], ((i >> 1) - 1) & 1, &abort_flag)) {
+                abort_flag = 1;
+                break;
+            }
+            uint8_t *sB = sB0 + s * B_BYTES;
+            dev::mbar_arrive_expect_tx(&bar_bf[s], B_BYTES);
+            for (int c = 0; c < CH; ++c)
+                dev::tma_load_2d(sB + c * BN * 128, &tmT, c * 128, (tile0 + i) * BN, &bar_bf[s]);
+        }
+    } else if (warp == 1 && lane == 0 && count > 0) {
+        const uint32_t idesc = dev::umma_idesc_e4m3_f32(BM, BN);
+        bool ok = wait_bar(&bar_a, 0, &abort_flag);
+        for (int i = 0; ok && i < count; ++i) {
+            const int s = i & 1;
+            ok = wait_bar(&bar_bf[s], (i >> 1) & 1, &abort_flag);
+            if (ok && i >= 2)
+                ok = wait_bar(&bar_te[s], ((i >> 1) - 1) & 1, &abort_flag);
+            if (!ok)
+                break;
+            dev::tc_fence_after();
+            const uint8_t *sB = sB0 + s * B_BYTES;
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint64_t a = dev::umma_desc_sw128(dev::smem_u32(sA + c * BM * 128 + u * 32));
+                    const uint64_t b = dev::umma_desc_sw128(dev::smem_u32(sB + c * BN * 128 + u * 32));
+                    dev::umma_e4m3(tmem + s * BN, a, b, idesc, (c | u) ? 1u : 0u);
+                }
+            dev::umma_commit(&bar_be[s]);
+            dev::umma_commit(&bar_tf[s]);
+            ++issued;
+        }
+        if (!ok)
+            abort_flag = 1;
+    }
+
+    uint32_t k1 = sentinel, k2 = sentinel;
+    const int ew = warp - 4, quad = warp & 3, half = ew >> 2;
+    const int row = quad * 32 + lane;
+    if (warp >= 4) {
+        uint32_t ka1 = sentinel, ka2 = sentinel, kb1 = sentinel, kb2 = sentinel;
+        for (int i = 0; i < count; ++i) {
+            const int s = i & 1;
+            if (!wait_bar(&bar_tf[s], (i >> 1) & 1, &abort_flag)) {
+                abort_flag = 1;
+                break;
+            }
+            dev::tc_fence_after();
+            uint32_t r0[32], r1[32];
+            const uint32_t col = (uint32_t)(s * BN + half * 64);
+            dev::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + col, r0);
+            dev::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + col + 32, r1);
+            dev::tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+                dev::mbar_arrive(&bar_te[s]);
+            const int j0 = (tile0 + i) * BN + half * 64;
+            const int valid = nt - j0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const uint32_t d = (uint32_t)((K - __float2int_rn(__uint_as_float(r0[j]))) >> 1);
+                const uint32_t key = j < valid ? ((d << kMatchIdxBits) | (uint32_t)(j0 + j)) : sentinel;
+                if (j & 1)
+                    top2_push(key, kb1, kb2);
+                else
+                    top2_push(key, ka1, ka2);
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const uint32_t d = (uint32_t)((K - __float2int_rn(__uint_as_float(r1[j]))) >> 1);
+                const uint32_t key =
+                    j + 32 < valid ? ((d << kMatchIdxBits) | (uint32_t)(j0 + 32 + j)) : sentinel;
+                if (j & 1)
+                    top2_push(key, kb1, kb2);
+                else
+                    top2_push(key, ka1, ka2);
+            }
+        }
+        top2_merge(kb1, kb2, ka1, ka2);
+        k1 = ka1;
+        k2 = ka2;
+        if (half == 1)
+            half_keys[row] = make_uint2(k1, k2);
+    }
+    __syncthreads();
+    const bool aborted = abort_flag != 0;
+    const int query = qb * BM + row;
+    const bool owner = warp >= 4 && half == 0;
+    if (owner) {
+        const uint2 o = half_keys[row];
+        top2_merge(o.x, o.y, k1, k2);
+    }
+    if (aborted) {
+        if (t == 0)
+            dev::raise_flag(status, BD_FLAG_TIMEOUT);
+    } else if (gridDim.y == 1) {
+        if (owner && query < nq) {
+            if (raw_keys)
+                raw_keys[query] = make_uint2(k1, k2);
+            else
+                finalize(k1, k2, nbits, rnum, rden, out + query);
+        }
+    } else {
+        if (owner && query < nq)
+            partial[(size_t)split * nq + query] = make_uint2(k1, k2);
+        __threadfence();
+        __syncthreads();
+        if (t == 0) {
+            const unsigned int prev = atomicAdd(arrivals + qb, 1u);
+            last_cta = prev == gridDim.y - 1;
+            if (last_cta)
+                arrivals[qb] = 0u;
+        }
+        __syncthreads();
+        if (last_cta && owner && query < nq) {
+            __threadfence();
+            uint2 a = __ldcg(partial + query);
+            for (int s = 1; s < (int)gridDim.y; ++s) {
+                const uint2 b = __ldcg(partial + (size_t)s * nq + query);
+                top2_merge(b.x, b.y, a.x, a.y);
+            }
+            if (raw_keys)
+                raw_keys[query] = a;
+            else
+                finalize(a.x, a.y, nbits, rnum, rden, out + query);
+        }
+    }
+    if (aborted && warp == 1 && lane == 0) {
+        // let issued MMAs finish before TMEM is released
+        for (int i = 0; i < issued; ++i) {
+            uint64_t *b = &bar_tf[i & 1];
+            const unsigned long long t0 = gtime();
+            while (!dev::mbar_try_wait(b, (i >> 1) & 1) && gtime() - t0 < kWaitNs) {
+            }
+        }
+    }
+    dev::tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        dev::tmem_dealloc(tmem, 2 * BN);
+}
+
+void tc_plan(int nq, int nt, int sm_count, int &S, int &per)
+{
+    const int qb = (nq + BM - 1) / BM;
+    const int ntiles = (nt + BN - 1) / BN;
+    S = (4 * sm_count + qb - 1) / qb;
+    if (S > ntiles)
+        S = ntiles;
+    if (S < 1)
+        S = 1;
+    per = (ntiles + S - 1) / S;
+    if (per < 1)
+        per = 1;
+    S = (ntiles + per - 1) / per;
+    if (S < 1)
+        S = 1;
+}
+
+}  // namespace
+
+int match_tc_query_blocks(int nq) { return (nq + BM - 1) / BM; }
+
+size_t match_tc_scratch_bytes(int nq, int nt, int nbits, int sm_count)
+{
+    int S, per;
+    tc_plan(nq, nt, sm_count, S, per);
+    return align_up((size_t)nq * nbits, 256) + align_up((size_t)(nt > 0 ? nt : 1) * nbits, 256) +
+           (S > 1 ? align_up((size_t)S * nq * sizeof(uint2), 256) : 0);
+}
+
+cudaError_t launch_match_tc_keys(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt,
+                                 int nbits, int ratio_num, int ratio_den, bd_match_result *out,
+                                 uint2 *raw_keys, void *scratch, cudaStream_t st,
+                                 unsigned int *arrivals)
+{
+    const int sm_count = ctx->sm_count;
+    int S, per;
+    tc_plan(nq, nt, sm_count, S, per);
+    uint8_t *qx = (uint8_t *)scratch;
+    uint8_t *tx = qx + align_up((size_t)nq * nbits, 256);
+    uint2 *partial = (uint2 *)(tx + align_up((size_t)(nt > 0 ? nt : 1) * nbits, 256));
+    const size_t qw = (size_t)nq * (nbits / 32), tw = (size_t)nt * (nbits / 32);
+    expand_pm1_kernel<<<(int)((qw + 255) / 256 < 4096 ? (qw + 255) / 256 : 4096), 256, 0, st>>>(
+        q, qw, reinterpret_cast<uint4 *>(qx));
+    if (nt > 0)
+        expand_pm1_kernel<<<(int)((tw + 255) / 256 < 4096 ? (tw + 255) / 256 : 4096), 256, 0, st>>>(
+            t, tw, reinterpret_cast<uint4 *>(tx));
+    trace_kernel(st, "expand_pm1");
+    CUtensorMap tmQ, tmT;
+    if (!encode_tmap_2d_u8(&tmQ, qx, (uint64_t)nbits, (uint64_t)nq, (uint64_t)nbits, 128, 128) ||
+        !encode_tmap_2d_u8(&tmT, tx, (uint64_t)nbits, (uint64_t)(nt > 0 ? nt : 1), (uint64_t)nbits,
+                           128, 128))
+        return cudaErrorInvalidValue;
+    dim3 grid((nq + BM - 1) / BM, S);
+    const size_t smem = (size_t)(BM + 2 * BN) * nbits + 1024;
+    cudaError_t e;
+    if (nbits == 256) {
+        e = cudaFuncSetAttribute(match_tc_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        match_tc_kernel<256><<<grid, NTHREADS, smem, st>>>(tmQ, tmT, nq, nt, per, nbits, ratio_num,
+                                                           ratio_den, partial, out, raw_keys,
+                                                           arrivals, ctx->status);
+    } else {
+        e = cudaFuncSetAttribute(match_tc_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        match_tc_kernel<512><<<grid, NTHREADS, smem, st>>>(tmQ, tmT, nq, nt, per, nbits, ratio_num,
+                                                           ratio_den, partial, out, raw_keys,
+                                                           arrivals, ctx->status);
+    }
+    trace_kernel(st, "match_tc");
+    note_launches(nt > 0 ? 3 : 2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_match_tc(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt,
+                            int nbits, int ratio_num, int ratio_den, bd_match_result *out,
+                            void *scratch, cudaStream_t st, unsigned int *arrivals)
+{
+    return launch_match_tc_keys(ctx, q, nq, t, nt, nbits, ratio_num, ratio_den, out, nullptr,
+                                scratch, st, arrivals);
+}
+
+}  // namespace bd

@@ -10,13 +10,15 @@
 // the FP32 histogram and FP32 W, in the FP32 projection kernel's order: the
 // result equals the FP32 path bit for bit.
 //
-// CTA = 128 threads, tile = 128 keypoints x 128 bits, K = 128 in two 64-wide
-// phases through one 64 KB shared-memory stage (three CTAs fit on an SM):
+// CTA = 256 threads, tile = 128 keypoints x 128 bits, K = 128 in two 64-wide
+// phases through one 64 KB shared-memory stage:
 //  - thread 0 loads the phase's four operand tiles with TMA (128-byte
 //    swizzle) and issues 4 x (2 or 3) MMAs of K = 16, committed to an mbarrier;
-//  - each warp then reads its 32 TMEM lanes (= keypoints) back, 32 columns at
-//    a time, adds the FP32 bias, takes the sign, queues the band bits, and the
-//    CTA re-evaluates the queue in FP32.
+//  - warps w and w+4 read TMEM lane quadrant w%4 (= 32 keypoints), each half
+//    of the columns, add the FP32 bias, take the sign and queue band bits;
+//  - four threads re-evaluate each queued bit in FP32: thread q sums terms
+//    [32q, 32q+32) from zero, and the four partials are combined in the FP32
+//    projection kernel's order.
 // Waits on mbarriers are bounded; on a timeout the CTA raises
 // BD_FLAG_TIMEOUT, waits once more for its MMAs, frees TMEM and returns.
 #include "bd_internal.h"
@@ -29,10 +31,10 @@ constexpr int BN = 128;
 constexpr int TILE = BM * 128;             // bytes of one 64-wide BF16 K chunk of a 128-row operand
 constexpr int STAGE_BYTES = 4 * TILE;      // A_hi, A_lo, B_hi, B_lo
 constexpr int SMEM_BYTES = STAGE_BYTES + 1024;
-constexpr int RB = 28;                     // FP32 re-checks staged per round (1 KB each)
-static_assert(2048 + 2 * BM * BN + RB * 1024 <= STAGE_BYTES, "epilogue does not fit the stage");
+constexpr int NTH = 256;                   // threads per CTA
+static_assert(2048 + 2 * BM * BN <= STAGE_BYTES, "epilogue does not fit the stage");
 
-__global__ void __launch_bounds__(128) hs_proj_tc_kernel(
+__global__ void __launch_bounds__(NTH) hs_proj_tc_kernel(
     const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
     const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int w_has_lo,
     const float *__restrict__ hist32, const float *__restrict__ Wt32,
@@ -51,7 +53,9 @@ __global__ void __launch_bounds__(128) hs_proj_tc_kernel(
     __shared__ float bias_s[BN], band_s[BN];
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    // the bit tiles of one keypoint tile are neighbours in launch order, so they
+    // read the same histogram rows while those are still in L2
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
 
     if (t == 0) {
         dev::mbar_init(&bar_tma, 1);
@@ -66,6 +70,7 @@ __global__ void __launch_bounds__(128) hs_proj_tc_kernel(
         bias_s[t] = __ldg(bias + n0 + t);
         band_s[t] = __ldg(band + n0 + t);
     }
+    static_assert(BN <= NTH, "one thread per bias entry");
     if (warp == 0)
         dev::tmem_alloc(&tmem_slot, BN);
     dev::tc_fence_before();
@@ -82,11 +87,12 @@ __global__ void __launch_bounds__(128) hs_proj_tc_kernel(
                 ok = false;
                 break;
             }
-            dev::mbar_arrive_expect_tx(&bar_tma, STAGE_BYTES);
+            dev::mbar_arrive_expect_tx(&bar_tma, w_has_lo ? STAGE_BYTES : 3 * TILE);
             dev::tma_load_2d(sAh, &tmAh, 64 * p, m0, &bar_tma);
             dev::tma_load_2d(sAl, &tmAl, 64 * p, m0, &bar_tma);
             dev::tma_load_2d(sBh, &tmBh, 64 * p, n0, &bar_tma);
-            dev::tma_load_2d(sBl, &tmBl, 64 * p, n0, &bar_tma);
+            if (w_has_lo)
+                dev::tma_load_2d(sBl, &tmBl, 64 * p, n0, &bar_tma);
             if (!dev::mbar_wait_bounded(&bar_tma, (uint32_t)p)) {
                 ok = false;
                 break;
@@ -117,18 +123,18 @@ __global__ void __launch_bounds__(128) hs_proj_tc_kernel(
     dev::tc_fence_after();
 
     if (ok) {
-        // The operand stage is dead now.  It holds the output tile, the queue of
-        // band bits and a staging area for the rows the FP32 re-check reads.
+        // The operand stage is dead now: it holds the output tile and the queue.
         uint32_t *out_tile = reinterpret_cast<uint32_t *>(smem);                 // [128][BN/32], 2 KB
         uint16_t *queue = reinterpret_cast<uint16_t *>(smem + 2048);             // <= 128*BN entries, 32 KB
-        float4 *stage = reinterpret_cast<float4 *>(smem + 2048 + 2 * BM * BN);    // RB x (f row, W row)
-        const int row = warp * 32 + lane;
+        const int quad = warp & 3, half = warp >> 2;
+        const int row = quad * 32 + lane;
         const int kp = m0 + row;
         const bool valid = kp < n && (kps == nullptr || dev::kp_valid(kps[kp]));
 #pragma unroll 1
-        for (int c = 0; c < BN / 32; ++c) {
+        for (int cc = 0; cc < BN / 64; ++cc) {
+            const int c = half * (BN / 64) + cc;  // 32-column chunk of this warp
             uint32_t r[32];
-            dev::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
+            dev::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32), r);
             uint32_t word = 0;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
@@ -142,50 +148,52 @@ __global__ void __launch_bounds__(128) hs_proj_tc_kernel(
             out_tile[row * (BN / 32) + c] = valid ? word : 0u;
         }
         __syncthreads();
-        // FP32 re-check of the queued bits, RB at a time: the CTA first copies
-        // every needed histogram row and W row into shared memory (one round
-        // trip), then thread e recomputes entry e in the FP32 kernel's order.
+        // FP32 re-check: four threads per queued bit, one 32-term chunk each
         const int total = list_n;
+        const int qq = t & 3;
 #pragma unroll 1
-        for (int base = 0; base < total; base += RB) {
-            const int cnt = min(RB, total - base);
-            for (int v = t; v < cnt * 64; v += 128) {
-                const int e = v >> 6, part = v & 63;
-                const int ent = queue[base + e];
-                const float4 *src = part < 32
-                    ? reinterpret_cast<const float4 *>(hist32 + (size_t)(m0 + (ent >> 7)) * kHistDim) + part
-                    : reinterpret_cast<const float4 *>(Wt32 + (size_t)(n0 + (ent & 127)) * kHistDim) + (part - 32);
-                stage[v] = __ldg(src);
-            }
-            __syncthreads();
-            if (t < cnt) {
-                const int ent = queue[base + t];
-                const int rr = ent >> 7, cc = ent & 127;
-                const float4 *hv = stage + t * 64, *wv = stage + t * 64 + 32;
-                float acc = 0.0f;
-#pragma unroll 8
-                for (int i = 0; i < kHistDim / 4; ++i) {
-                    const float4 a = hv[i], b = wv[i];
-                    acc = fmaf(a.x, b.x, acc);
-                    acc = fmaf(a.y, b.y, acc);
-                    acc = fmaf(a.z, b.z, acc);
-                    acc = fmaf(a.w, b.w, acc);
+        for (int base = 0; base < total; base += NTH / 4) {
+            const int e = base + (t >> 2);
+            const bool act = e < total;
+            const int ent = act ? queue[e] : 0;
+            const int rr = ent >> 7, cc = ent & 127;
+            float part = 0.0f;
+            if (act) {
+                const float4 *hv = reinterpret_cast<const float4 *>(hist32 + (size_t)(m0 + rr) * kHistDim) + 8 * qq;
+                const float4 *wv = reinterpret_cast<const float4 *>(Wt32 + (size_t)(n0 + cc) * kHistDim) + 8 * qq;
+                float4 a[8], b[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    a[i] = __ldg(hv + i);
+                    b[i] = __ldg(wv + i);
                 }
-                const float m32 = acc + bias_s[cc];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    part = fmaf(a[i].x, b[i].x, part);
+                    part = fmaf(a[i].y, b[i].y, part);
+                    part = fmaf(a[i].z, b[i].z, part);
+                    part = fmaf(a[i].w, b[i].w, part);
+                }
+            }
+            const float c1 = __shfl_down_sync(0xffffffffu, part, 1, 4);
+            const float c2 = __shfl_down_sync(0xffffffffu, part, 2, 4);
+            const float c3 = __shfl_down_sync(0xffffffffu, part, 3, 4);
+            if (act && qq == 0) {
+                const float m32 = ((part + c1) + c2) + c3 + bias_s[cc];
                 if (m32 > 0.0f)
                     atomicOr(&out_tile[rr * (BN / 32) + (cc >> 5)], 1u << (cc & 31));
                 else
                     atomicAnd(&out_tile[rr * (BN / 32) + (cc >> 5)], ~(1u << (cc & 31)));
             }
-            __syncthreads();
         }
+        __syncthreads();
         if (t == 0 && total)
             atomicAdd(&status->rescued, (unsigned long long)total);
-        if (kp < n) {
-            uint32_t *dst = out + (size_t)kp * (K / 32) + n0 / 32;
+        if (t < BM && m0 + t < n) {
+            uint32_t *dst = out + (size_t)(m0 + t) * (K / 32) + n0 / 32;
 #pragma unroll
             for (int c = 0; c < BN / 32; ++c)
-                dst[c] = out_tile[row * (BN / 32) + c];
+                dst[c] = out_tile[t * (BN / 32) + c];
         }
     } else if (t == 0) {
         dev::raise_flag(status, BD_FLAG_TIMEOUT);
@@ -212,8 +220,8 @@ cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const CUtensorMap &tm_hi,
                               const CUtensorMap &tm_lo, const float *hist, int n, uint32_t *out,
                               DeviceStatus *status, cudaStream_t st, const bd_keypoint *kps)
 {
-    dim3 grid((n + BM - 1) / BM, p->nbits / BN);
-    hs_proj_tc_kernel<<<grid, 128, SMEM_BYTES, st>>>(tm_hi, tm_lo, p->tmap_w_hi, p->tmap_w_lo,
+    dim3 grid(p->nbits / BN, (n + BM - 1) / BM);
+    hs_proj_tc_kernel<<<grid, NTH, SMEM_BYTES, st>>>(tm_hi, tm_lo, p->tmap_w_hi, p->tmap_w_lo,
                                                      p->w_has_lo ? 1 : 0, hist, p->d_Wt, p->d_bias,
                                                      p->d_band, kps, n, p->nbits, out, status);
     trace_kernel(st, "hs_proj_tc");

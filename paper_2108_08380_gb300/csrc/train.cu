@@ -9,8 +9,9 @@
 //     with r = tanh((W^T h + b)/T) and hard bits [m > 0];
 //   - mining on hard codes: for anchor i the negative j != i with the smallest
 //     min(Hamming(a_i,n_j), Hamming(p_i,n_j)) (= the largest similarity
-//     K - 2 Hamming, Sec. III-A), lowest j on ties; anchor swap keeps p_i when
-//     it is closer to that negative than a_i;
+//     K - 2 Hamming, Sec. III-A), lowest j on ties, from two exact
+//     tensor-core top-2 searches (match_tc.cu); anchor swap keeps p_i when it
+//     is closer to that negative than a_i;
 //   - the hinge loss of each descriptor.
 //  backward (mining held fixed)
 //   - dL/dr from the active hinges (negatives collect with atomics);
@@ -26,20 +27,22 @@ using namespace bd;
 struct bd_train {
     bd_ctx *ctx = nullptr;
     const bd_bad_params *bad = nullptr;
-    int n = 0, rows = 0, kb = 0, kh = 0, splits = 1, chunk = 1;
+    int n = 0, rows = 0, kb = 0, kh = 0;
     float T = 0.1f, tau_bad = 0.f, tau_hs = 0.f;
     float *r_bad = nullptr, *r_hs = nullptr, *h = nullptr, *norm = nullptr;
-    uint32_t *bits_bad = nullptr, *bits_hs = nullptr, *partial = nullptr;
+    uint32_t *bits_bad = nullptr, *bits_hs = nullptr;
     int32_t *mining = nullptr;  // [4][n]
     float *dr_bad = nullptr, *dr_hs = nullptr, *Wt = nullptr;
     double *loss_acc = nullptr;
+    void *tc_scratch = nullptr;       // FP8 codes and partials of the top-2 searches
+    uint2 *keys = nullptr;            // [2][n] top-2 keys (anchors, positives)
+    unsigned int *arrivals = nullptr; // zeroed per-block arrival counters
 };
 
 namespace bd {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int MTT = 256;  // negatives per shared-memory tile (mining)
 
 __device__ __forceinline__ double sat_box(const double (*S)[34], int x0, int y0, int s)
 {
@@ -106,59 +109,24 @@ __global__ void __launch_bounds__(128) train_bad_fwd_kernel(const float *__restr
     }
 }
 
-template <int NW>
-__global__ void __launch_bounds__(128) train_mine_kernel(const uint32_t *__restrict__ bits, int n,
-                                                         int chunk, uint32_t *__restrict__ partial)
-{
-    __shared__ uint4 tile[MTT * NW / 4];
-    const int i = blockIdx.x * 128 + threadIdx.x;
-    const int j0 = blockIdx.y * chunk, j1 = min(n, j0 + chunk);
-    uint32_t qa[NW], qp[NW];
-#pragma unroll
-    for (int v = 0; v < NW; ++v) {
-        qa[v] = i < n ? __ldg(bits + (size_t)i * NW + v) : 0u;
-        qp[v] = i < n ? __ldg(bits + (size_t)(n + i) * NW + v) : 0u;
-    }
-    uint32_t best = 0xffffffffu;
-    const uint32_t *neg = bits + (size_t)2 * n * NW;
-    for (int base = j0; base < j1; base += MTT) {
-        const int cnt = min(MTT, j1 - base);
-        __syncthreads();
-        const uint4 *src = reinterpret_cast<const uint4 *>(neg + (size_t)base * NW);
-        for (int v = threadIdx.x; v < cnt * NW / 4; v += 128)
-            tile[v] = __ldg(src + v);
-        __syncthreads();
-        for (int jj = 0; jj < cnt; ++jj) {
-            uint32_t da = 0, dp = 0;
-#pragma unroll
-            for (int v = 0; v < NW / 4; ++v) {
-                const uint4 x = tile[jj * (NW / 4) + v];
-                da += __popc(qa[4 * v] ^ x.x) + __popc(qa[4 * v + 1] ^ x.y) + __popc(qa[4 * v + 2] ^ x.z) +
-                      __popc(qa[4 * v + 3] ^ x.w);
-                dp += __popc(qp[4 * v] ^ x.x) + __popc(qp[4 * v + 1] ^ x.y) + __popc(qp[4 * v + 2] ^ x.z) +
-                      __popc(qp[4 * v + 3] ^ x.w);
-            }
-            const int j = base + jj;
-            const uint32_t key = (min(da, dp) << 20) | (uint32_t)j;
-            if (j != i || n == 1)
-                best = min(best, key);
-        }
-    }
-    if (i < n)
-        partial[(size_t)blockIdx.y * n + i] = best;
-}
-
-__global__ void train_mine_merge_kernel(const uint32_t *__restrict__ partial, int n, int S,
-                                        const uint32_t *__restrict__ bits, int NW,
-                                        int32_t *__restrict__ nstar, int32_t *__restrict__ xsel)
+// Mining from the two top-2 searches (anchors vs negatives, positives vs
+// negatives, keys = distance << 22 | index): the first key of each pair whose
+// index is not i (any index when n == 1), then the smaller of the two keys.
+// Smaller key = smaller min(Hamming(a_i,n_j), Hamming(p_i,n_j)), lowest j on
+// ties, i.e. the largest similarity K - 2 Hamming (Sec. III-A).
+__global__ void train_mine_combine_kernel(const uint2 *__restrict__ keys_a,
+                                          const uint2 *__restrict__ keys_p, int n,
+                                          const uint32_t *__restrict__ bits, int NW,
+                                          int32_t *__restrict__ nstar, int32_t *__restrict__ xsel)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
         return;
-    uint32_t best = 0xffffffffu;
-    for (int s = 0; s < S; ++s)
-        best = min(best, partial[(size_t)s * n + i]);
-    const int j = (int)(best & 0xfffffu);
+    const uint2 a = keys_a[i], p = keys_p[i];
+    const bool any = n == 1;
+    const uint32_t ca = (any || (int)(a.x & kMatchIdxMask) != i) ? a.x : a.y;
+    const uint32_t cp = (any || (int)(p.x & kMatchIdxMask) != i) ? p.x : p.y;
+    const int j = (int)(min(ca, cp) & kMatchIdxMask);
     uint32_t da = 0, dp = 0;
     for (int v = 0; v < NW; ++v) {
         const uint32_t nv = bits[(size_t)(2 * n + j) * NW + v];
@@ -471,21 +439,6 @@ __global__ void __launch_bounds__(128) train_hs_bwd_kernel(const float *__restri
     }
 }
 
-void mine_plan(int n, int sm_count, int &S, int &chunk)
-{
-    const int qb = (n + 127) / 128;
-    S = (8 * sm_count + qb - 1) / qb;
-    const int maxs = (n + 255) / 256;
-    if (S > maxs)
-        S = maxs;
-    if (S < 1)
-        S = 1;
-    chunk = (n + S - 1) / S;
-    S = (n + chunk - 1) / chunk;
-    if (S < 1)
-        S = 1;
-}
-
 int grid_rows(int rows, int sm_count, int per_sm)
 {
     const long long g = (long long)sm_count * per_sm;
@@ -516,7 +469,6 @@ bd_status bd_train_create(bd_ctx *ctx, const bd_bad_params *bad, int hs_bits, in
     tr->T = temperature;
     tr->tau_bad = tau_bad;
     tr->tau_hs = tau_hs;
-    mine_plan(n, ctx->sm_count, tr->splits, tr->chunk);
     const size_t R = (size_t)tr->rows;
     int prev = -1;
     cudaGetDevice(&prev);
@@ -528,7 +480,11 @@ bd_status bd_train_create(bd_ctx *ctx, const bd_bad_params *bad, int hs_bits, in
     if (e == cudaSuccess) e = cudaMalloc(&tr->norm, sizeof(float) * R);
     if (e == cudaSuccess) e = cudaMalloc(&tr->bits_bad, sizeof(uint32_t) * R * (tr->kb / 32));
     if (e == cudaSuccess) e = cudaMalloc(&tr->bits_hs, sizeof(uint32_t) * R * (tr->kh / 32));
-    if (e == cudaSuccess) e = cudaMalloc(&tr->partial, sizeof(uint32_t) * (size_t)tr->splits * n);
+    const int kmax = tr->kb > tr->kh ? tr->kb : tr->kh;
+    if (e == cudaSuccess) e = cudaMalloc(&tr->tc_scratch, match_tc_scratch_bytes(n, n, kmax, ctx->sm_count));
+    if (e == cudaSuccess) e = cudaMalloc(&tr->keys, sizeof(uint2) * 2 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&tr->arrivals, sizeof(unsigned int) * (size_t)match_tc_query_blocks(n));
+    if (e == cudaSuccess) e = cudaMemset(tr->arrivals, 0, sizeof(unsigned int) * (size_t)match_tc_query_blocks(n));
     if (e == cudaSuccess) e = cudaMalloc(&tr->mining, sizeof(int32_t) * 4 * (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc(&tr->dr_bad, sizeof(float) * R * tr->kb);
     if (e == cudaSuccess) e = cudaMalloc(&tr->dr_hs, sizeof(float) * R * tr->kh);
@@ -554,9 +510,9 @@ void bd_train_destroy(bd_train *tr)
         cudaSetDevice(tr->ctx->device);
     cudaStreamSynchronize(tr->ctx->stream);
     for (void *p : {(void *)tr->r_bad, (void *)tr->r_hs, (void *)tr->h, (void *)tr->norm,
-                    (void *)tr->bits_bad, (void *)tr->bits_hs, (void *)tr->partial,
-                    (void *)tr->mining, (void *)tr->dr_bad, (void *)tr->dr_hs, (void *)tr->Wt,
-                    (void *)tr->loss_acc})
+                    (void *)tr->bits_bad, (void *)tr->bits_hs, (void *)tr->tc_scratch,
+                    (void *)tr->keys, (void *)tr->arrivals, (void *)tr->mining, (void *)tr->dr_bad,
+                    (void *)tr->dr_hs, (void *)tr->Wt, (void *)tr->loss_acc})
         if (p)
             cudaFree(p);
     if (prev >= 0 && prev != tr->ctx->device)
@@ -597,21 +553,24 @@ bd_status bd_train_forward(bd_ctx *ctx, bd_train *tr, const float *patches, cons
         e = cudaMemcpyAsync(tr->mining, fixed_mining, sizeof(int32_t) * 4 * (size_t)n,
                             cudaMemcpyDeviceToDevice, st);
     } else if (e == cudaSuccess) {
-        dim3 grid((n + 127) / 128, tr->splits);
-        for (int d = 0; d < 2; ++d) {
+        for (int d = 0; d < 2 && e == cudaSuccess; ++d) {
             const uint32_t *bits = d == 0 ? tr->bits_bad : tr->bits_hs;
-            const int nw = (d == 0 ? tr->kb : tr->kh) / 32;
-            if (nw == 8)
-                train_mine_kernel<8><<<grid, 128, 0, st>>>(bits, n, tr->chunk, tr->partial);
-            else
-                train_mine_kernel<16><<<grid, 128, 0, st>>>(bits, n, tr->chunk, tr->partial);
-            trace_kernel(st, "train_mine");
-            train_mine_merge_kernel<<<(n + 255) / 256, 256, 0, st>>>(
-                tr->partial, n, tr->splits, bits, nw, tr->mining + (size_t)(2 * d) * n,
-                tr->mining + (size_t)(2 * d + 1) * n);
-            trace_kernel(st, "train_mine_merge");
+            const int K = d == 0 ? tr->kb : tr->kh;
+            const int nw = K / 32;
+            const uint32_t *neg = bits + (size_t)2 * n * nw;
+            e = launch_match_tc_keys(ctx, bits, n, neg, n, K, 1, 1, nullptr, tr->keys, tr->tc_scratch,
+                                     st, tr->arrivals);
+            if (e == cudaSuccess)
+                e = launch_match_tc_keys(ctx, bits + (size_t)n * nw, n, neg, n, K, 1, 1, nullptr,
+                                         tr->keys + n, tr->tc_scratch, st, tr->arrivals);
+            if (e == cudaSuccess) {
+                train_mine_combine_kernel<<<(n + 255) / 256, 256, 0, st>>>(
+                    tr->keys, tr->keys + n, n, bits, nw, tr->mining + (size_t)(2 * d) * n,
+                    tr->mining + (size_t)(2 * d + 1) * n);
+                trace_kernel(st, "train_mine_combine");
+                e = cudaGetLastError();
+            }
         }
-        e = cudaGetLastError();
     }
     if (e == cudaSuccess)
         e = cudaMemsetAsync(tr->loss_acc, 0, sizeof(double) * 2, st);
@@ -635,7 +594,7 @@ bd_status bd_train_forward(bd_ctx *ctx, bd_train *tr, const float *patches, cons
     if (e == cudaSuccess && mining_out)
         e = cudaMemcpyAsync(mining_out, tr->mining, sizeof(int32_t) * 4 * (size_t)n,
                             cudaMemcpyDeviceToDevice, st);
-    note_launches(fixed_mining ? 6 : 10);
+    note_launches(fixed_mining ? 6 : 8);
     if (prev >= 0 && prev != ctx->device)
         cudaSetDevice(prev);
     return e == cudaSuccess ? BD_OK : cuda_err(ctx, e, "bd_train_forward");

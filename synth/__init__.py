@@ -281,19 +281,20 @@ class TripletWorkload:
     patches: np.ndarray
 
 
-def _sample_patch(img: np.ndarray, cx: float, cy: float, A: np.ndarray) -> np.ndarray:
-    """32x32 bilinear crop: p(i,j) = img(c + A @ (j-15.5, i-15.5)), edge-clamped."""
+def _sample_patches(img: np.ndarray, cx, cy, A) -> np.ndarray:
+    """m 32x32 bilinear crops: p(i,j) = img(c + A @ (j-15.5, i-15.5)), edge-clamped.
+    cx, cy: [m]; A: [m, 2, 2]."""
     h, w = img.shape
     jj, ii = np.meshgrid(np.arange(32) - 15.5, np.arange(32) - 15.5)
-    sx = cx + A[0, 0] * jj + A[0, 1] * ii
-    sy = cy + A[1, 0] * jj + A[1, 1] * ii
+    sx = cx[:, None, None] + A[:, 0, 0, None, None] * jj + A[:, 0, 1, None, None] * ii
+    sy = cy[:, None, None] + A[:, 1, 0, None, None] * jj + A[:, 1, 1, None, None] * ii
     x0 = np.floor(sx)
     y0 = np.floor(sy)
     fx = sx - x0
     fy = sy - y0
     x0 = x0.astype(np.int64)
     y0 = y0.astype(np.int64)
-    src = img.astype(np.float64)
+    src = img.astype(np.float32)
 
     def at(yy, xx):
         return src[np.clip(yy, 0, h - 1), np.clip(xx, 0, w - 1)]
@@ -302,22 +303,36 @@ def _sample_patch(img: np.ndarray, cx: float, cy: float, A: np.ndarray) -> np.nd
 
 
 def triplet_workload(seed: int = 1003, n: int = 65536, n_images: int = 4,
-                     w: int = 640, h: int = 480) -> TripletWorkload:
+                     w: int = 640, h: int = 480, chunk: int = 4096) -> "TripletWorkload":
     """Positive = anchor region under rotation U(+-15 deg), scale U[0.9, 1.1],
     plus N(0, 5) noise; negatives = random patches elsewhere."""
     rng = np.random.default_rng(seed)
     imgs = [make_image(w, h, rng) for _ in range(n_images)]
     out = np.empty((3, n, 32, 32), dtype=np.float32)
     eye = np.eye(2)
-    for t in range(n):
-        img = imgs[rng.integers(0, n_images)]
-        cx = rng.uniform(40, w - 40)
-        cy = rng.uniform(40, h - 40)
-        out[0, t] = _sample_patch(img, cx, cy, eye)
-        a = math.radians(rng.uniform(-15, 15))
-        s = rng.uniform(0.9, 1.1)
-        A = s * np.array([[math.cos(a), -math.sin(a)], [math.sin(a), math.cos(a)]])
-        out[1, t] = _sample_patch(img, cx, cy, A) + rng.normal(0.0, 5.0, size=(32, 32))
-        img2 = imgs[rng.integers(0, n_images)]
-        out[2, t] = _sample_patch(img2, rng.uniform(40, w - 40), rng.uniform(40, h - 40), eye)
+    for c0 in range(0, n, chunk):
+        m = min(chunk, n - c0)
+        src = rng.integers(0, n_images, size=m)
+        cx = rng.uniform(40, w - 40, size=m)
+        cy = rng.uniform(40, h - 40, size=m)
+        a = np.radians(rng.uniform(-15, 15, size=m))
+        s = rng.uniform(0.9, 1.1, size=m)
+        A = np.empty((m, 2, 2))
+        A[:, 0, 0] = s * np.cos(a)
+        A[:, 0, 1] = -s * np.sin(a)
+        A[:, 1, 0] = s * np.sin(a)
+        A[:, 1, 1] = s * np.cos(a)
+        noise = rng.normal(0.0, 5.0, size=(m, 32, 32))
+        src2 = rng.integers(0, n_images, size=m)
+        nx = rng.uniform(40, w - 40, size=m)
+        ny = rng.uniform(40, h - 40, size=m)
+        I = np.broadcast_to(eye, (m, 2, 2))
+        for im in range(n_images):
+            sel = np.nonzero(src == im)[0]
+            if len(sel):
+                out[0, c0 + sel] = _sample_patches(imgs[im], cx[sel], cy[sel], I[sel])
+                out[1, c0 + sel] = _sample_patches(imgs[im], cx[sel], cy[sel], A[sel]) + noise[sel]
+            sel2 = np.nonzero(src2 == im)[0]
+            if len(sel2):
+                out[2, c0 + sel2] = _sample_patches(imgs[im], nx[sel2], ny[sel2], I[sel2])
     return TripletWorkload(out)

@@ -1,5 +1,7 @@
 """GPU parity of brute-force Hamming matching with fused top-2 and ratio test
-against the CPU oracle: bit-exact index, distances and verdict (Sec. IV-C)."""
+against the CPU oracle: bit-exact index, distances and verdict (Sec. IV-C).
+Every case runs through both the POPC kernel (bd_match) and the tensor-core
+kernel (bd_match_tc, +-1 codes in FP8, S = K - 2 Hamming)."""
 import numpy as np
 import pytest
 
@@ -27,9 +29,14 @@ def _noisy(rng, d, K, flips):
     return np.packbits(bits, axis=1, bitorder="little").view(np.uint32)
 
 
-def _check(ctx, q, t, K, rnum=4, rden=5, rows=None):
+@pytest.fixture(params=[False, True], ids=["popc", "tensor"])
+def tc(request):
+    return request.param
+
+
+def _check(ctx, q, t, K, rnum=4, rden=5, rows=None, tc=False):
     import paper_2108_08380_gb300 as bd
-    m = ctx.match(_dev(q), _dev(t), K, rnum, rden)
+    m = ctx.match(_dev(q), _dev(t), K, rnum, rden, tensor_cores=tc)
     idx, d1, d2, acc = bd.unpack_matches(m)
     if rows is None:
         rows = np.arange(q.shape[0])
@@ -44,38 +51,38 @@ def _check(ctx, q, t, K, rnum=4, rden=5, rows=None):
 @pytest.mark.parametrize("K,nq,nt", [(256, 1000, 1000), (512, 1000, 1000), (256, 333, 777),
                                      (512, 129, 4099), (256, 5000, 3), (256, 1, 1), (512, 7, 0),
                                      (256, 300, 1), (512, 2, 2)])
-def test_match_random_exact(gpu_ctx, K, nq, nt):
+def test_match_random_exact(gpu_ctx, K, nq, nt, tc):
     rng = np.random.default_rng(K + 31 * nq + nt)
     t = _rand_desc(rng, nt, K)
     q = _rand_desc(rng, nq, K)
     if nt:
         pick = rng.integers(0, nt, size=nq)
         q[: nq // 2] = _noisy(rng, t[pick[: nq // 2]], K, K // 8)
-    _check(gpu_ctx, q, t, K)
+    _check(gpu_ctx, q, t, K, tc=tc)
 
 
-def test_match_ties_lowest_index(gpu_ctx):
+def test_match_ties_lowest_index(gpu_ctx, tc):
     K = 256
     rng = np.random.default_rng(3)
     base = _rand_desc(rng, 50, K)
     t = np.concatenate([base, base, base[::-1]])  # every entry three times
     q = _noisy(rng, base, K, 3)
-    idx, d1, d2, acc = _check(gpu_ctx, q, t, K)
+    idx, d1, d2, acc = _check(gpu_ctx, q, t, K, tc=tc)
     assert np.all(d1 == d2) and not acc.any()
     assert np.all(idx < 50)
 
 
-def test_match_bad_descriptors_of_noisy_pair(gpu_ctx):
+def test_match_bad_descriptors_of_noisy_pair(gpu_ctx, tc):
     """Plain workload: BAD-256 of image A against image B = A + N(0,5)."""
     wl = synth.plain_workload(1000)
     qa, _ = oracle.bad_describe(wl.img_a, wl.kps_a, wl.bad)
     tb, _ = oracle.bad_describe(wl.img_b, wl.kps_b, wl.bad)
-    idx, d1, d2, acc = _check(gpu_ctx, qa, tb, 256)
+    idx, d1, d2, acc = _check(gpu_ctx, qa, tb, 256, tc=tc)
     assert (idx == np.arange(1000)).mean() > 0.5  # most keypoints find themselves
 
 
 @pytest.mark.parametrize("K", [256, 512])
-def test_match_full_size_sampled(gpu_ctx, K):
+def test_match_full_size_sampled(gpu_ctx, K, tc):
     """20000 x 20000 in the launch configuration of the large workload; a
     seeded sample of 400 queries checked against the oracle."""
     rng = np.random.default_rng(K)
@@ -84,7 +91,7 @@ def test_match_full_size_sampled(gpu_ctx, K):
     perm = rng.permutation(n)
     q = _noisy(rng, t[perm], K, K // 10)
     rows = np.sort(rng.choice(n, size=400, replace=False))
-    idx, d1, d2, acc = _check(gpu_ctx, q, t, K, rows=rows)
+    idx, d1, d2, acc = _check(gpu_ctx, q, t, K, rows=rows, tc=tc)
     assert np.array_equal(idx[rows], perm[rows])
 
 
@@ -96,3 +103,16 @@ def test_match_rejects_bad_arguments(gpu_ctx):
         gpu_ctx.match(q, q, 300)
     with pytest.raises(bd.BindescError):
         gpu_ctx.match(q, q, 256, 6, 5)
+
+
+@pytest.mark.parametrize("K", [256, 512])
+def test_tensor_core_and_popc_agree_on_full_size(gpu_ctx, K):
+    """All 20000 queries: the two kernels return identical records."""
+    import torch
+    rng = np.random.default_rng(K + 1)
+    n = 20000
+    t = _rand_desc(rng, n, K)
+    q = _noisy(rng, t[rng.permutation(n)], K, K // 6)
+    a = gpu_ctx.match(_dev(q), _dev(t), K).cpu().numpy()
+    b = gpu_ctx.match(_dev(q), _dev(t), K, tensor_cores=True).cpu().numpy()
+    assert np.array_equal(a, b)
