@@ -50,10 +50,11 @@ def load_peaks():
 class Workload:
     """Host-side inputs of one step, their device copies and the step's ABI calls."""
 
-    def __init__(self, name: str):
+    def __init__(self, name: str, match_kind: str = "tensor"):
         import synth
         self.name = name
         self.match = True
+        self.match_kind = match_kind
         if name == "plain":
             wl = synth.plain_workload(1000)  # 640x480, 1000 keypoints, BAD-256, HashSIFT-256
             self.images = [wl.img_a, wl.img_b]
@@ -99,6 +100,8 @@ class Workload:
         if self.match:
             na = int(self.offsets[1])
             self.pairs_per_step = 2 * na * (self.n - na)
+            if self.match_kind == "auto":
+                self.match_kind = "tensor" if na * (self.n - na) >= (1 << 24) else "popc"
         else:
             self.pairs_per_step = 0
 
@@ -130,11 +133,12 @@ class Workload:
                                                             graph=True))]
         if self.match:
             na = int(self.offsets[1])
+            tc = self.match_kind == "tensor"
             st += [
                 ("match_bad", lambda: ctx.match(self.bad[:na], self.bad[na:], self.bad_bits, 4, 5,
-                                                out=self.m_bad)),
+                                                out=self.m_bad, tensor_cores=tc)),
                 ("match_hashsift", lambda: ctx.match(self.hs[:na], self.hs[na:], self.hs_bits, 4, 5,
-                                                     out=self.m_hs)),
+                                                     out=self.m_hs, tensor_cores=tc)),
             ]
         return st
 
@@ -302,7 +306,7 @@ def run_ours(args):
 
     ctx = bd.Context(local)
     ctx.trace(True)  # kernel-level CUDA events inside every call (graph replays included)
-    wl = Workload(args.workload)
+    wl = Workload(args.workload, args.match)
     wl.to_device(ctx, autotune=not args.no_autotune)
     stages = wl.stages(ctx)
     n_launch0 = bd.kernel_launches()
@@ -385,6 +389,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "u8/int32 (BAD, matching), f32 + bf16 tensor (HashSIFT)",
         "data": "synthetic",
         "config": dict(wl.config, l2="flushed between steps (512 MB write)",
+                       matching=("tensor cores (FP8 +-1, tcgen05)" if wl.match_kind == "tensor"
+                                 else "POPC") if wl.match else None,
                        parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
         "matches_per_s": world * wl.pairs_per_step / (ms * 1e-3),
         "stage_ms": per_stage,
@@ -452,6 +458,14 @@ def roofline(wl, per_kernel, clocks):
         ach = popc / t / 1e12
         out.update(bound="alu", achieved=ach, peak=peak, unit="Tpopc/s", frac=ach / peak,
                    traffic=None, peak_source=f"derived: 152 SMs x 16 POPC/clk x {sm_mhz:.0f} MHz")
+    elif kname == "match_tc":
+        K = wl.bad_bits if stage == "match_bad" else wl.hs_bits
+        flops = 2.0 * na * nb * K
+        peak = 2.0 * float(peaks["bf16_tflops"])
+        ach = flops / t / 1e12
+        out.update(bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                   traffic=None,
+                   peak_source=f"{kind} bf16 burst x 2 (nominal FP8/BF16 dense ratio)")
     elif kname == "hs_proj_tc":
         flops = 2.0 * 128 * wl.hs_bits * wl.n
         peak = float(peaks["bf16_tflops"])
@@ -529,6 +543,9 @@ def main():
     ap.add_argument("--workload", choices=["plain", "large", "batch", "train"], default="plain")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--match", choices=["auto", "tensor", "popc"], default="auto",
+                    help="matching kernel: tensor cores (bd_match_tc), POPC (bd_match), or auto "
+                         "(tensor cores from 2^24 query-train pairs up)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-sample-kp", type=int, default=250)
     args = ap.parse_args()

@@ -82,7 +82,9 @@ typedef struct bd_hs_params bd_hs_params;
  * sm_103 device; otherwise BD_ERR_UNSUPPORTED. */
 bd_status bd_create(int device, void *stream, bd_ctx **out);
 
-/* Releases the context and its device memory (synchronising its stream). */
+/* Releases the context and its device memory (synchronising its stream).
+ * Parameter sets and plans created from the context must be destroyed
+ * first: they refer to it. */
 void bd_destroy(bd_ctx *ctx);
 
 /* Switches the stream later calls enqueue on. */

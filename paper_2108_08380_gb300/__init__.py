@@ -14,6 +14,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbindesc.so")
@@ -158,9 +159,18 @@ class Context:
             raise BindescError(st, "bd_create failed (an sm_103 GPU is required)")
         self.handle = h
         self._explicit_stream = stream is not None
+        self._children = weakref.WeakSet()
+
+    def _adopt(self, child):
+        self._children.add(child)
+        return child
 
     def close(self):
+        """Destroys the context after every parameter set, batch plan and
+        training plan created from it that is still alive."""
         if getattr(self, "handle", None):
+            for child in list(self._children):
+                child.close()
             lib().bd_destroy(self.handle)
             self.handle = None
 
@@ -341,6 +351,12 @@ class Batch:
                                    ctypes.byref(hd))
         ctx._check(st, "bd_batch_create")
         self.handle = hd
+        ctx._adopt(self)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().bd_batch_destroy(self.handle)
+            self.handle = None
 
     def _ptrs(self, imgs):
         arr = (ctypes.c_void_p * self.n_img)(*[t.data_ptr() for t in imgs])
@@ -375,9 +391,7 @@ class Batch:
 
     def __del__(self):
         try:
-            if self.handle:
-                lib().bd_batch_destroy(self.handle)
-                self.handle = None
+            self.close()
         except Exception:
             pass
 
@@ -398,6 +412,12 @@ class TrainStep:
                                    self.tau_bad, self.tau_hs, ctypes.byref(h))
         ctx._check(st, "bd_train_create")
         self.handle = h
+        ctx._adopt(self)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().bd_train_destroy(self.handle)
+            self.handle = None
 
     def forward(self, patches, theta, W, b, fixed_mining=None):
         """(loss [2] float32 tensor: BAD, HashSIFT; mining [4, n] int32 tensor)."""
@@ -427,9 +447,7 @@ class TrainStep:
 
     def __del__(self):
         try:
-            if self.handle:
-                lib().bd_train_destroy(self.handle)
-                self.handle = None
+            self.close()
         except Exception:
             pass
 
@@ -501,6 +519,12 @@ class BadParamsHandle:
                                         ctypes.byref(h))
         ctx._check(st, "bd_bad_params_create")
         self.handle = h
+        ctx._adopt(self)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().bd_bad_params_destroy(self.handle)
+            self.handle = None
 
     def table(self):
         import numpy as np
@@ -513,9 +537,7 @@ class BadParamsHandle:
 
     def __del__(self):
         try:
-            if self.handle:
-                lib().bd_bad_params_destroy(self.handle)
-                self.handle = None
+            self.close()
         except Exception:
             pass
 
@@ -532,11 +554,15 @@ class HsParamsHandle:
                                        int(precision), float(band), ctypes.byref(h))
         ctx._check(st, "bd_hs_params_create")
         self.handle = h
+        ctx._adopt(self)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().bd_hs_params_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:
-            if self.handle:
-                lib().bd_hs_params_destroy(self.handle)
-                self.handle = None
+            self.close()
         except Exception:
             pass

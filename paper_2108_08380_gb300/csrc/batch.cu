@@ -101,8 +101,10 @@ __device__ __forceinline__ int find_image(const BatchImageDev *imgs, int n_img, 
     return lo;
 }
 
-template <int NW>
-__global__ void __launch_bounds__(128, 4) batch_persistent_kernel(BatchKernelArgs A)
+// MINB: resident CTAs per SM the register budget is sized for (4: 128 registers,
+// 6: 80); the autotuner picks the variant through ctas_per_sm.
+template <int NW, int MINB>
+__global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernelArgs A)
 {
     __shared__ union {
         dev::IiStatsSmem s;
@@ -204,6 +206,7 @@ struct bd_batch {
     CUtensorMap tm_hi, tm_lo;
     bd_batch_config cfg = {8, 0, 1};
     int max_ctas_per_sm = 0;
+    int occ4 = 0;  // resident CTAs per SM of the 128-register variant
     // graph replay
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -250,10 +253,18 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     if (per_sm > b->max_ctas_per_sm)
         per_sm = b->max_ctas_per_sm;
     const int grid = per_sm * ctx->sm_count;
-    if (A.bad_nw == 16)
-        batch_persistent_kernel<16><<<grid, 128, 0, st>>>(A);
-    else
-        batch_persistent_kernel<8><<<grid, 128, 0, st>>>(A);
+    const bool wide = per_sm > b->occ4;  // needs the 80-register variant to be resident
+    if (A.bad_nw == 16) {
+        if (wide)
+            batch_persistent_kernel<16, 6><<<grid, 128, 0, st>>>(A);
+        else
+            batch_persistent_kernel<16, 4><<<grid, 128, 0, st>>>(A);
+    } else {
+        if (wide)
+            batch_persistent_kernel<8, 6><<<grid, 128, 0, st>>>(A);
+        else
+            batch_persistent_kernel<8, 4><<<grid, 128, 0, st>>>(A);
+    }
     trace_kernel(st, "batch_persistent");
     note_launches(1);
     int nk = 1;
@@ -376,10 +387,14 @@ bd_status bd_batch_create(bd_ctx *ctx, const bd_bad_params *bad, const bd_hs_par
         if (e == cudaSuccess && hs) e = cudaMalloc(&b->d_hist16, sizeof(__nv_bfloat16) * 2 * kHistDim * (size_t)(b->n_kp > 0 ? b->n_kp : 1));
         if (e == cudaSuccess) e = cudaMemcpy(b->d_imgs, b->imgs.data(), sizeof(BatchImageDev) * n_img, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
-        int occ8 = 0, occ16 = 0;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ8, batch_persistent_kernel<8>, 128, 0);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ16, batch_persistent_kernel<16>, 128, 0);
-        b->max_ctas_per_sm = occ8 < occ16 ? occ8 : occ16;
+        int o[4] = {0, 0, 0, 0};
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[0], batch_persistent_kernel<8, 4>, 128, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[1], batch_persistent_kernel<16, 4>, 128, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[2], batch_persistent_kernel<8, 6>, 128, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], batch_persistent_kernel<16, 6>, 128, 0);
+        b->occ4 = o[0] < o[1] ? o[0] : o[1];
+        const int occ6 = o[2] < o[3] ? o[2] : o[3];
+        b->max_ctas_per_sm = occ6 > b->occ4 ? occ6 : b->occ4;
         if (prev >= 0 && prev != ctx->device)
             cudaSetDevice(prev);
     }

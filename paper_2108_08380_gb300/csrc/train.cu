@@ -402,6 +402,8 @@ __global__ void __launch_bounds__(128) train_hs_bwd_kernel(const float *__restri
             float dgx = 0.f, dgy = 0.f;
             if (m2 > 0.f && nrm > 0.f) {
                 const float m = sqrtf(m2);
+                // the adjoint picks a bin pair from the orientation, so it uses the
+                // closer-to-exact atan2f (the vote itself is continuous in it)
                 float phi = atan2f(gy, gx);
                 if (phi < 0.0f)
                     phi += 6.28318530717958647692f;
