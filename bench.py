@@ -371,9 +371,14 @@ def run_ours(args):
     assert ctx.sync_status() == 0, "device flags raised during the timed steps"
 
     # ---- end to end through the public API with pinned host buffers ----
+    rescued = ctx.rescued_count(reset=True)
+    probes = components = None
+    if not args.no_components:
+        probes = measure_probes(ctx)
+        components = measure_components(ctx, wl, probes)
     ctx.trace(False)
     ctx.trace_reset()
-    rescued = ctx.rescued_count(reset=True)
+    ctx.rescued_count(reset=True)
     e2e = measure_e2e(ctx, wl, stages, max(3, min(K, 50)))
 
     if rank != 0:
@@ -381,7 +386,7 @@ def run_ours(args):
     per_stage = {lab: float(stage_ms[:, j].mean()) for j, (lab, _) in enumerate(stages)}
     keys = sorted({k for d in kernel_ms for k in d})
     per_kernel = {k: float(np.mean([d.get(k, 0.0) for d in kernel_ms])) for k in keys}
-    roof = roofline(wl, per_kernel, clocks)
+    roof = roofline(wl, per_kernel, clocks, probes)
     value = world * wl.descriptors_per_step / (ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "descriptors/s", "n_gpus": world, "steps": K,
@@ -398,6 +403,8 @@ def run_ours(args):
         "hashsift_rescued_bits_per_step": rescued / K,
         "batch_config": wl.tuned,
         "roofline": roof,
+        "probes": probes,
+        "components": components,
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -407,6 +414,135 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# measured path rates (bd_probe) and per-stage kernels against them
+# ---------------------------------------------------------------------------
+
+def _kernel_ms(ctx, fn, reps):
+    """Mean device time per call of each kernel that fn launches (trace events)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    acc = {}
+    for _ in range(reps):
+        ctx.trace_reset()
+        fn()
+        torch.cuda.synchronize()
+        for name, ms in ctx.trace_read():
+            acc[name] = acc.get(name, 0.0) + ms / reps
+    return acc
+
+
+def measure_probes(ctx):
+    """Measured rates of the paths the descriptor kernels lean on (units/s):
+    random 4-byte gathers from L2 (32 MB table) and within BAD-sized 8 KB
+    windows (L1 hits), POPC, FFMA and MUFU instructions."""
+    import torch
+    import paper_2108_08380_gb300 as bd
+    table = torch.randint(0, 1 << 20, (1 << 23,), dtype=torch.int32, device="cuda")
+    cases = {
+        "gather_l2": (bd.BD_PROBE_GATHER, 16, table, 1 << 23),
+        "gather_l1_window_8kb": (bd.BD_PROBE_GATHER, 64, table, 1 << 11),
+        "popc": (bd.BD_PROBE_POPC, 256, None, 0),
+        "ffma": (bd.BD_PROBE_FFMA, 1024, None, 0),
+        "mufu_ex2": (bd.BD_PROBE_MUFU, 256, None, 0),
+    }
+    out = {}
+    for name, (kind, reps, tab, win) in cases.items():
+        best = None
+        for _ in range(4):
+            ctx.trace_reset()
+            units = ctx.probe(kind, reps, tab, win)
+            torch.cuda.synchronize()
+            ms = sum(m for _, m in ctx.trace_read())
+            best = ms if best is None else min(best, ms)
+        out[name] = {"per_s": units / (best * 1e-3), "ms": best, "units": units}
+    del table
+    return out
+
+
+def measure_components(ctx, wl, probes):
+    """Each stage's kernel run on its own over image A of the workload (warm
+    L2, mean of 10 calls), its rate against the measured rate of the path that
+    bounds it; the BF16+rescue projection against the FP32 projection on the
+    same histograms (time and bit disagreements); POPC against tensor-core
+    matching (time and record equality)."""
+    import torch
+    import paper_2108_08380_gb300 as bd
+    reps = 10
+    img = wl.dimg[0]
+    na = int(wl.offsets[1])
+    kps = wl.dkps[:na]
+    h, w = img.shape
+    res = {"scope": f"image A ({w}x{h}, {na} keypoints), warm L2, mean of {reps} calls"}
+
+    # BAD: integral image + gather (Sec. III-A); 8 integral lookups per bit
+    out = torch.empty((na, wl.bad_bits // 32), dtype=torch.int32, device="cuda")
+    k = _kernel_ms(ctx, lambda: ctx.bad_describe(wl.bp, img, kps, out=out), reps)
+    t = k.get("bad_gather", float("nan")) * 1e-3
+    loads = na * wl.bad_bits * 8
+    res["bad_gather"] = {
+        "ms": t * 1e3, "gathers_per_s": loads / t,
+        "frac_of_l2_gather": loads / t / probes["gather_l2"]["per_s"],
+        "frac_of_l1_window_gather": loads / t / probes["gather_l1_window_8kb"]["per_s"],
+        "work": f"{na} kps x {wl.bad_bits} bits x 8 lookups"}
+    ii_ms = sum(v for kk, v in k.items() if kk.startswith("ii_"))
+    res["integral"] = {"ms": ii_ms, "bytes": 6 * w * h,
+                       "gbs": 6 * w * h / (ii_ms * 1e-3) / 1e9,
+                       "work": "1 B read twice + 4 B written per pixel"}
+
+    # HashSIFT: fused warp + histogram, then projection (Sec. III-B)
+    hist = torch.empty((na, 128), dtype=torch.float32, device="cuda")
+    bits_bf = torch.empty((na, wl.hs_bits // 32), dtype=torch.int32, device="cuda")
+    k = _kernel_ms(ctx, lambda: ctx.hashsift_describe(wl.hp, img, kps, out=bits_bf,
+                                                        hist_out=hist), reps)
+    th = sum(v for kk, v in k.items() if kk.startswith("hs_hist")) * 1e-3
+    ops = HS_OPS_PER_PIXEL * 1024.0 * na
+    res["hs_histogram"] = {"ms": th * 1e3, "patches_per_s": na / th,
+                           "frac_of_ffma": ops / th / probes["ffma"]["per_s"],
+                           "work": f"{na} patches x 1024 px x {HS_OPS_PER_PIXEL} FP32 ops"}
+    hp32 = ctx.hs_params(wl.wl.hs, precision=bd.BD_HS_FP32)
+    bits32 = torch.empty_like(bits_bf)
+    ctx.rescued_count(reset=True)
+    k_bf = _kernel_ms(ctx, lambda: ctx.hashsift_project(wl.hp, hist, out=bits_bf), reps)
+    rescued = ctx.rescued_count(reset=True) / (reps + 1)
+    k_32 = _kernel_ms(ctx, lambda: ctx.hashsift_project(hp32, hist, out=bits32), reps)
+    torch.cuda.synchronize()
+    dis = int(np.unpackbits((bits_bf ^ bits32).cpu().numpy().view(np.uint8)).sum())
+    t_bf = sum(k_bf.values())
+    t_32 = sum(k_32.values())
+    flops = 2.0 * 128 * wl.hs_bits * na
+    res["hs_projection"] = {
+        "bf16_rescue_ms": t_bf, "fp32_ms": t_32, "speedup_vs_fp32": t_32 / t_bf,
+        "bit_disagreements": dis, "rescued_bits": rescued,
+        "bf16_kernels": k_bf, "fp32_kernels": k_32,
+        "bf16_tflops": flops / (k_bf.get("hs_proj_tc", t_bf) * 1e-3) / 1e12}
+    hp32.close()
+
+    # matching (Sec. IV-C): POPC kernel and tensor-core kernel, same records
+    if wl.match:
+        q, tr = wl.bad[:na], wl.bad[na:]
+        nb = tr.shape[0]
+        m1 = torch.empty((na, 3), dtype=torch.int32, device="cuda")
+        m2 = torch.empty_like(m1)
+        for lab, K, qq, tt in (("bad", wl.bad_bits, wl.bad[:na], wl.bad[na:]),
+                               ("hashsift", wl.hs_bits, wl.hs[:na], wl.hs[na:])):
+            kp = _kernel_ms(ctx, lambda: ctx.match(qq, tt, K, 4, 5, out=m1), reps)
+            kt = _kernel_ms(ctx, lambda: ctx.match(qq, tt, K, 4, 5, out=m2, tensor_cores=True), reps)
+            torch.cuda.synchronize()
+            tp = sum(kp.values()) * 1e-3
+            tt_ = sum(kt.values()) * 1e-3
+            popc = na * nb * (K // 32)
+            res[f"match_{lab}"] = {
+                "popc_ms": tp * 1e3, "tensor_ms": tt_ * 1e3,
+                "popc_frac_of_popc_probe": popc / tp / probes["popc"]["per_s"],
+                "tensor_fp8_tflops": 2.0 * na * nb * K / tt_ / 1e12,
+                "records_equal": bool(torch.equal(m1, m2)),
+                "pairs_per_s_popc": na * nb / tp, "pairs_per_s_tensor": na * nb / tt_,
+                "work": f"{na} x {nb} pairs x {K // 32} POPC"}
+    return res
 
 
 def measure_e2e(ctx, wl, stages, steps):
@@ -439,10 +575,12 @@ def measure_e2e(ctx, wl, stages, steps):
             "ms_per_step": ms, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
 
 
-def roofline(wl, per_kernel, clocks):
+def roofline(wl, per_kernel, clocks, probes=None):
     """Roofline of the dominant kernel of the step (largest mean time per step).
-    Algorithmic work per launch and the bound of each kernel are listed in
-    the design doc (roofline table)."""
+    Denominators are measured: MEASURED_PEAKS.json for HBM and BF16 tensor
+    throughput, the bd_probe kernels for POPC, FFMA and gather rates (derived
+    from unit counts and the sampled clock only when the probes were skipped).
+    Algorithmic work per launch and each kernel's bound are listed in the design doc."""
     peaks, kind = load_peaks()
     key = max(per_kernel, key=per_kernel.get)
     t = per_kernel[key] * 1e-3
@@ -451,13 +589,18 @@ def roofline(wl, per_kernel, clocks):
     na = int(wl.offsets[1]) if wl.match else 0
     nb = wl.n - na
     out = {"kernel": key, "ms": per_kernel[key], "sm_mhz_used": sm_mhz}
+
+    def probe(name, derived, what):
+        if probes and name in probes:
+            return probes[name]["per_s"], f"measured: bd_probe {name}"
+        return derived, f"derived: {what} x {sm_mhz:.0f} MHz"
+
     if kname == "match_top2":
         K = wl.bad_bits if stage == "match_bad" else wl.hs_bits
         popc = na * nb * (K // 32)
-        peak = 152 * 16 * sm_mhz * 1e6 / 1e12
-        ach = popc / t / 1e12
-        out.update(bound="alu", achieved=ach, peak=peak, unit="Tpopc/s", frac=ach / peak,
-                   traffic=None, peak_source=f"derived: 152 SMs x 16 POPC/clk x {sm_mhz:.0f} MHz")
+        peak, src = probe("popc", 152 * 16 * sm_mhz * 1e6, "152 SMs x 16 POPC/clk")
+        out.update(bound="alu", achieved=popc / t / 1e12, peak=peak / 1e12, unit="Tpopc/s",
+                   frac=popc / t / peak, traffic=None, peak_source=src)
     elif kname == "match_tc":
         K = wl.bad_bits if stage == "match_bad" else wl.hs_bits
         flops = 2.0 * na * nb * K
@@ -473,14 +616,27 @@ def roofline(wl, per_kernel, clocks):
         out.update(bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
                    traffic=None, peak_source=f"{kind} bf16 burst (MEASURED_PEAKS.json)")
     else:
-        # batch_persistent: histogram arithmetic dominates; FP32 lane-ops of the
-        # histogram (HS_OPS_PER_PIXEL per patch pixel) against 152 SMs x 128 lanes
-        ops = HS_OPS_PER_PIXEL * 1024.0 * wl.n
-        peak = 152 * 128 * sm_mhz * 1e6 / 1e12
-        ach = ops / t / 1e12
-        out.update(bound="alu", achieved=ach, peak=peak, unit="Tops/s", frac=ach / peak,
-                   traffic=None,
-                   peak_source=f"derived: 152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz")
+        # batch_persistent: integral images (HBM), BAD gathers and histogram
+        # arithmetic fused in one launch.  Each part's minimum time at its
+        # measured rate; the bound is the largest part, and the sum is the
+        # time the three would take if they could not overlap.
+        px = float(sum(int(im.shape[0]) * int(im.shape[1]) for im in wl.images))
+        g_rate, g_src = probe("gather_l1_window_8kb", 152 * 32 * sm_mhz * 1e6,
+                              "152 SMs x 32 loads/clk")
+        f_rate, f_src = probe("ffma", 152 * 128 * sm_mhz * 1e6, "152 SMs x 128 FP32 lanes")
+        parts = {
+            "gather": (wl.n * wl.bad_bits * 8.0, g_rate, "Gload/s", g_src),
+            "alu": (HS_OPS_PER_PIXEL * 1024.0 * wl.n, f_rate, "Tops/s", f_src),
+            "hbm": (6.0 * px, float(peaks["hbm_gbs"]) * 1e9, "GB/s", f"{kind} HBM copy"),
+        }
+        tmin = {k: v[0] / v[1] for k, v in parts.items()}
+        bound = max(tmin, key=tmin.get)
+        work, rate, unit, src = parts[bound]
+        scale = 1e9 if unit in ("Gload/s", "GB/s") else 1e12
+        out.update(bound=bound, achieved=work / t / scale, peak=rate / scale, unit=unit,
+                   frac=work / t / rate, traffic=None, peak_source=src,
+                   parts_min_ms={k: v * 1e3 for k, v in tmin.items()},
+                   frac_of_parts_sum=sum(tmin.values()) / t)
     return out
 
 
@@ -543,6 +699,8 @@ def main():
     ap.add_argument("--workload", choices=["plain", "large", "batch", "train"], default="plain")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-components", action="store_true",
+                    help="skip the probe kernels and the per-stage component measurements")
     ap.add_argument("--match", choices=["auto", "tensor", "popc"], default="auto",
                     help="matching kernel: tensor cores (bd_match_tc), POPC (bd_match), or auto "
                          "(tensor cores from 2^24 query-train pairs up)")

@@ -369,6 +369,36 @@ bd_status bd_bad_describe_noalloc(const bd_bad_params *p, const uint8_t *img, in
 bd_status bd_match_tc(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt,
                       int nbits, int ratio_num, int ratio_den, bd_match_result *out);
 
+/* ------------------------------------------------------------------------ */
+/* Measurement probes (the paper has no counterpart: they give each kernel's  */
+/* roofline a measured denominator)                                          */
+
+typedef enum {
+    BD_PROBE_GATHER = 0, /* random 4-byte loads, read-only path (BAD stump access) */
+    BD_PROBE_POPC = 1,   /* 32-bit population counts (Hamming matching) */
+    BD_PROBE_FFMA = 2,   /* FP32 fused multiply-adds (histogram arithmetic) */
+    BD_PROBE_MUFU = 3    /* ex2 on the special-function unit */
+} bd_probe_kind;
+
+/* Enqueues one probe kernel on the context's stream, sized to fill every SM
+ * (a multiple of the SM count at full occupancy), and stores in *units the
+ * operations (loads or instructions) it performs; time it with events on the
+ * same stream and divide.
+ *  - BD_PROBE_GATHER: table (device, table_words uint32, contents irrelevant)
+ *    with table_words and window_words powers of two, 32 <= window_words <=
+ *    table_words <= 2^31.  Each warp draws reps windows of window_words
+ *    words; per window every lane loads 64 random words of it, independent
+ *    of each other.  window_words = table_words measures L2 random gathers
+ *    once the table is larger than L1; a window of a few KB measures L1 hits.
+ *  - The other kinds ignore table and window_words; each thread runs
+ *    reps x 64 instructions of the kind in eight independent chains.
+ *  - sink: one device uint32 that the results are added to (keeps the work
+ *    live); its value means nothing.
+ *  - Errors: BD_ERR_INVALID for an unknown kind, reps outside [1, 2^20], a
+ *    null sink or units, or a gather geometry that breaks the rules above. */
+bd_status bd_probe(bd_ctx *ctx, int kind, const uint32_t *table, size_t table_words,
+                   size_t window_words, int reps, uint32_t *sink, uint64_t *units);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,10 @@ BD_FLAG_INVALID_KEYPOINT = 0x1
 BD_FLAG_TIMEOUT = 0x2
 BD_HS_FP32 = 0
 BD_HS_BF16_RESCUE = 1
+BD_PROBE_GATHER = 0
+BD_PROBE_POPC = 1
+BD_PROBE_FFMA = 2
+BD_PROBE_MUFU = 3
 
 _STATUS_NAMES = {0: "BD_OK", 1: "BD_ERR_INVALID", 2: "BD_ERR_CUDA", 3: "BD_ERR_NOMEM",
                  4: "BD_ERR_TIMEOUT", 5: "BD_ERR_DEVICE_CHECK", 6: "BD_ERR_UNSUPPORTED"}
@@ -78,6 +82,8 @@ _SIGS = [
     ("bd_train_forward", _I, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     ("bd_train_backward", _I, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     ("bd_bad_describe_noalloc", _I, [_P, _P, _I, _I, _I, _P, _I, _P, _P]),
+    ("bd_probe", _I, [_P, _I, _P, ctypes.c_size_t, ctypes.c_size_t, _I, _P,
+                      ctypes.POINTER(ctypes.c_uint64)]),
 ]
 
 _lock = threading.Lock()
@@ -320,6 +326,20 @@ class Context:
         self._check(fn(self.handle, _ptr(q), nq, _ptr(t), nt, nbits, ratio_num, ratio_den, _ptr(out)),
                     "bd_match_tc" if tensor_cores else "bd_match")
         return out
+
+
+    def probe(self, kind: int, reps: int, table=None, window_words: int = 0, sink=None) -> int:
+        """Enqueues one bd_probe kernel on the current stream; returns the
+        loads / instructions it performs (time it with events around the call)."""
+        torch = self._torch
+        if sink is None:
+            sink = torch.zeros(1, dtype=torch.int32, device="cuda")
+        units = ctypes.c_uint64(0)
+        tw = table.numel() if table is not None else 0
+        self._stream()
+        self._check(lib().bd_probe(self.handle, kind, _ptr(table), tw, window_words, reps,
+                                   _ptr(sink), ctypes.byref(units)), "bd_probe")
+        return int(units.value)
 
 
 class BatchConfig(ctypes.Structure):

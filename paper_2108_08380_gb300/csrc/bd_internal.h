@@ -186,6 +186,11 @@ cudaError_t launch_match_tc_keys(bd_ctx *ctx, const uint32_t *q, int nq, const u
                                  int nbits, int ratio_num, int ratio_den, bd_match_result *out,
                                  uint2 *raw_keys, void *scratch, cudaStream_t st,
                                  unsigned int *arrivals);
+// measurement probes (bd_probe); bad_args set when the geometry is refused
+cudaError_t launch_probe(int kind, const uint32_t *table, size_t table_words, size_t window_words,
+                         int reps, uint32_t *sink, int sm_count, cudaStream_t st,
+                         unsigned long long *units, bool *bad_args);
+
 int match_query_blocks(int nq);
 // arrivals: one zero-initialised counter per query block (ctx-owned; each call leaves them zero)
 cudaError_t launch_match(const uint32_t *q, int nq, const uint32_t *t, int nt, int nbits,

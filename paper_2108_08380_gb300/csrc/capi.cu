@@ -849,4 +849,23 @@ bd_status bd_match(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, in
     return BD_OK;
 }
 
+bd_status bd_probe(bd_ctx *ctx, int kind, const uint32_t *table, size_t table_words,
+                   size_t window_words, int reps, uint32_t *sink, uint64_t *units)
+{
+    BD_GUARD(ctx);
+    if (!units)
+        return set_err(ctx, BD_ERR_INVALID, "bd_probe: null units");
+    unsigned long long u = 0;
+    bool bad = false;
+    TraceScope scope(ctx, ctx->stream);
+    BD_LAUNCH(ctx,
+              launch_probe(kind, table, table_words, window_words, reps, sink, ctx->sm_count,
+                           ctx->stream, &u, &bad),
+              "probe kernel");
+    if (bad)
+        return set_err(ctx, BD_ERR_INVALID, "bd_probe: bad kind, repetitions or gather geometry");
+    *units = (uint64_t)u;
+    return BD_OK;
+}
+
 }  // extern "C"

@@ -204,24 +204,47 @@ __global__ void __launch_bounds__(NTHREADS, 1) match_tc_kernel(
                 dev::mbar_arrive(&bar_te[s]);
             const int j0 = (tile0 + i) * BN + half * 64;
             const int valid = nt - j0;
+            // Tile-local keys in FP32: f = 256 S - jl (jl < 64) is exact and larger
+            // f means larger S (smaller distance), then smaller jl.  The two best
+            // f of the 64 columns become global integer keys once per tile.
+            float f1 = -INFINITY, f2 = -INFINITY;
+            if (valid >= 64) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const uint32_t d = (uint32_t)((K - __float2int_rn(__uint_as_float(r0[j]))) >> 1);
-                const uint32_t key = j < valid ? ((d << kMatchIdxBits) | (uint32_t)(j0 + j)) : sentinel;
-                if (j & 1)
-                    top2_push(key, kb1, kb2);
-                else
-                    top2_push(key, ka1, ka2);
+                for (int j = 0; j < 32; ++j) {
+                    const float f = fmaf(__uint_as_float(r0[j]), 256.0f, -(float)j);
+                    f2 = fmaxf(f2, fminf(f1, f));
+                    f1 = fmaxf(f1, f);
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float f = fmaf(__uint_as_float(r1[j]), 256.0f, -(float)(32 + j));
+                    f2 = fmaxf(f2, fminf(f1, f));
+                    f1 = fmaxf(f1, f);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float f = j < valid ? fmaf(__uint_as_float(r0[j]), 256.0f, -(float)j) : -INFINITY;
+                    f2 = fmaxf(f2, fminf(f1, f));
+                    f1 = fmaxf(f1, f);
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float f = j + 32 < valid ? fmaf(__uint_as_float(r1[j]), 256.0f, -(float)(32 + j))
+                                                   : -INFINITY;
+                    f2 = fmaxf(f2, fminf(f1, f));
+                    f1 = fmaxf(f1, f);
+                }
             }
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const uint32_t d = (uint32_t)((K - __float2int_rn(__uint_as_float(r1[j]))) >> 1);
-                const uint32_t key =
-                    j + 32 < valid ? ((d << kMatchIdxBits) | (uint32_t)(j0 + 32 + j)) : sentinel;
-                if (j & 1)
-                    top2_push(key, kb1, kb2);
-                else
-                    top2_push(key, ka1, ka2);
+            for (int b = 0; b < 2; ++b) {
+                const float f = b ? f2 : f1;
+                if (f == -INFINITY)
+                    continue;
+                const int S = (int)ceilf(f * (1.0f / 256.0f));  // f = 256 S - jl, 0 <= jl < 64
+                const int jl = 256 * S - (int)f;
+                const uint32_t d = (uint32_t)((K - S) >> 1);
+                top2_push((d << kMatchIdxBits) | (uint32_t)(j0 + jl), ka1, ka2);
             }
         }
         top2_merge(kb1, kb2, ka1, ka2);
