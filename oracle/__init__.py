@@ -251,6 +251,16 @@ def match(q, t, nbits: int, ratio_num: int = 4, ratio_den: int = 5):
     return idx, d1, d2, acc
 
 
+def match_mnn(q, t, nbits: int):
+    """Mutual nearest neighbours: int32 [nq], the partner in t or -1 (Sec. V,
+    Hamming MNN matching; ties to the lowest index on both sides)."""
+    q = np.ascontiguousarray(q, dtype=np.uint32).reshape(-1, nbits // 32)
+    t = np.ascontiguousarray(t, dtype=np.uint32).reshape(-1, nbits // 32)
+    out = np.empty(q.shape[0], dtype=np.int32)
+    lib().or_match_mnn(_u32p(q), q.shape[0], _u32p(t), t.shape[0], nbits, _i32p(out))
+    return out
+
+
 # ---------------------------------------------------------------------------
 # training step (Sec. III-A Eq. 1, Sec. III-B Eq. 3; relaxed tanh responses)
 # ---------------------------------------------------------------------------

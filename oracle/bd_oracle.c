@@ -387,3 +387,35 @@ void or_match(const uint32_t *q, int nq, const uint32_t *t, int nt, int nbits, i
     }
     free(pr);
 }
+
+/* Nearest entry of set b for one descriptor a (lowest index among equal
+ * distances); -1 when b is empty. */
+static int or_nearest(const uint32_t *a, const uint32_t *b, int nb, int nw)
+{
+    int best = -1, bd = 0;
+    for (int j = 0; j < nb; ++j) {
+        const int d = or_hamming(a, b + (size_t)j * nw, nw);
+        if (best < 0 || d < bd) {
+            best = j;
+            bd = d;
+        }
+    }
+    return best;
+}
+
+/* Mutual nearest neighbours (the Hamming MNN matching of the pipeline-timing
+ * experiment, Sec. V): query i and train entry j match iff j is the nearest
+ * train entry of i and i is the nearest query of j, each side breaking ties
+ * to the lowest index.  mnn[i] = j, or -1 when i has no mutual partner. */
+void or_match_mnn(const uint32_t *q, int nq, const uint32_t *t, int nt, int nbits, int32_t *mnn)
+{
+    const int nw = nbits / 32;
+    int *back = (int *)malloc(sizeof(int) * (size_t)(nt > 0 ? nt : 1));
+    for (int j = 0; j < nt; ++j)
+        back[j] = or_nearest(t + (size_t)j * nw, q, nq, nw);
+    for (int i = 0; i < nq; ++i) {
+        const int j = or_nearest(q + (size_t)i * nw, t, nt, nw);
+        mnn[i] = (j >= 0 && back[j] == i) ? j : -1;
+    }
+    free(back);
+}
