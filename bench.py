@@ -5,7 +5,7 @@ integral image + BAD gather for both images, fused patch-warp + histogram and
 tcgen05 projection (BF16 + FP32 rescue) for both images, then brute-force
 Hamming top-2 + ratio matching of image A against image B for both
 descriptor types.  Inputs are synthetic (seeded), shaped like the paper's
-workloads; see the design doc for the recipe.
+workloads (generators in synth/).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload plain|large]
     python bench.py --impl reference ...   # the CPU oracle on a bounded sample
@@ -50,13 +50,17 @@ def load_peaks():
 class Workload:
     """Host-side inputs of one step, their device copies and the step's ABI calls."""
 
-    def __init__(self, name: str, match_kind: str = "tensor"):
+    def __init__(self, name: str, match_kind: str = "tensor", rank: int = 0):
+        """rank > 0 draws its own inputs of the same shape (seed + 100 x rank):
+        ranks describe independent images (weak scaling)."""
         import synth
         self.name = name
+        self.rank = rank
+        off = 100 * rank
         self.match = True
         self.match_kind = match_kind
         if name == "plain":
-            wl = synth.plain_workload(1000)  # 640x480, 1000 keypoints, BAD-256, HashSIFT-256
+            wl = synth.plain_workload(1000 + off)  # 640x480, 1000 keypoints, BAD-256, HashSIFT-256
             self.images = [wl.img_a, wl.img_b]
             self.kps = np.concatenate([wl.kps_a, wl.kps_b])
             self.offsets = np.array([0, len(wl.kps_a), 2 * len(wl.kps_a)], np.int32)
@@ -67,7 +71,7 @@ class Workload:
                            "images": "2 x 640x480 uint8", "keypoints_per_image": 1000,
                            "bad_bits": 256, "hashsift_bits": 256, "angle_bins": 32}
         elif name == "large":
-            wl = synth.large_pair_workload(1004)  # 2 x 3840x2160, 20000 kps, BAD-256, HashSIFT-512
+            wl = synth.large_pair_workload(1004 + off)  # 2 x 3840x2160, 20000 kps, BAD-256, HashSIFT-512
             self.images = [wl.img_a, wl.img_b]
             self.kps = np.concatenate([wl.kps_a, wl.kps_b])
             self.offsets = np.array([0, len(wl.kps_a), 2 * len(wl.kps_a)], np.int32)
@@ -78,7 +82,7 @@ class Workload:
                            "images": "2 x 3840x2160 uint8", "keypoints_per_image": 20000,
                            "bad_bits": 256, "hashsift_bits": 512, "angle_bins": 32}
         elif name == "batch":
-            wl = synth.batch_workload(1002)  # 64 images, 200k kps, BAD-512, HashSIFT-512 (BF16 W)
+            wl = synth.batch_workload(1002 + off)  # 64 images, 200k kps, BAD-512, HashSIFT-512 (BF16 W)
             self.images = wl.images
             self.kps = wl.kps
             self.offsets = wl.kp_offsets
@@ -106,7 +110,7 @@ class Workload:
             self.pairs_per_step = 0
 
     # ---- GPU -----------------------------------------------------------
-    def to_device(self, ctx, autotune=True):
+    def to_device(self, ctx, autotune=True, config=None):
         import torch
         import paper_2108_08380_gb300 as bd
         dev = "cuda"
@@ -120,7 +124,10 @@ class Workload:
         self.hs = torch.empty((n, self.hs_bits // 32), dtype=i32, device=dev)
         self.plan = ctx.batch(self.bp, self.hp, self.dimg, self.offsets)
         self.tuned = None
-        if autotune:
+        if config is not None:
+            self.plan.set_config(*config)
+            self.tuned = self.plan.config()
+        elif autotune:
             self.tuned, _ = self.plan.autotune(self.dimg, self.dkps, self.bad, self.hs, reps=3)
         if self.match:
             na = int(self.offsets[1])
@@ -242,6 +249,14 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (the step time the job is charged)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -305,11 +320,10 @@ def run_ours(args):
         pg = dist
 
     ctx = bd.Context(local)
-    ctx.trace(True)  # kernel-level CUDA events inside every call (graph replays included)
-    wl = Workload(args.workload, args.match)
-    wl.to_device(ctx, autotune=not args.no_autotune)
+    wl = Workload(args.workload, args.match, rank=rank)
+    cfg = tuple(int(x) for x in args.batch_config.split(",")) if args.batch_config else None
+    wl.to_device(ctx, autotune=not args.no_autotune, config=cfg)
     stages = wl.stages(ctx)
-    n_launch0 = bd.kernel_launches()
 
     # warm-up (also sizes the scratch area)
     for _ in range(max(3, args.warmup)):
@@ -320,7 +334,42 @@ def run_ours(args):
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 2 x L2
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(K)]
+    names = [lab for lab, _ in stages]
+
+    def run_steps(traced: bool):
+        """K steps, each: L2 flush, a device sleep while the host enqueues the
+        step, then the step's calls between CUDA events.  traced = kernel-level
+        events inside every call as well (graph replays included)."""
+        ctx.trace(traced)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)]
+              for _ in range(K)]
+        kernel_ms = []  # per step: {stage/kernel: ms}
+        for s in range(K):
+            flush.fill_(float(s))               # evict the previous step's data from L2
+            torch.cuda._sleep(1_000_000)        # let the host enqueue the whole step first
+            if traced:
+                ctx.trace_reset()
+            ev[s][0].record()
+            for j, (_, fn) in enumerate(stages):
+                fn()
+                ev[s][j + 1].record()
+            if traced:
+                step_k = {}
+                call = 0  # marks arrive in call order; each call opens with a 'begin' mark
+                for kname, kms in ctx.trace_read_raw():
+                    if kname == "begin":
+                        call += 1
+                        continue
+                    key = f"{names[min(call, len(names) - 1)]}/{kname}"
+                    step_k[key] = step_k.get(key, 0.0) + kms
+                kernel_ms.append(step_k)
+        torch.cuda.synchronize()
+        ctx.trace(False)
+        stage = np.array([[ev[s][j].elapsed_time(ev[s][j + 1]) for j in range(len(stages))]
+                          for s in range(K)])
+        return stage, kernel_ms
+
+    # ---- timed steps (no kernel-level events: each one drains the stream) ----
     props = torch.cuda.get_device_properties(local)
     sampler = ClockSampler(getattr(props, "uuid", None) and f"GPU-{props.uuid}" or str(local))
     sampler.start()
@@ -330,55 +379,34 @@ def run_ours(args):
     torch.cuda.synchronize()
     ctx.rescued_count(reset=True)
     launches_before = bd.kernel_launches()
-    kernel_ms = []  # per step: {stage/kernel: ms}
     t_wall0 = time.time()
-    for s in range(K):
-        flush.fill_(float(s))               # evict the previous step's data from L2
-        torch.cuda._sleep(200_000)          # let the host enqueue the whole step first
-        ctx.trace_reset()
-        ev[s][0].record()
-        for j, (lab, fn) in enumerate(stages):
-            fn()
-            ev[s][j + 1].record()
-        step_k = {}
-        # marks arrive in call order; attribute each kernel to its call
-        names = [lab for lab, _ in stages]
-        call = 0  # the first call's own start mark opens the list
-        for kname, kms in ctx.trace_read_raw():
-            if kname == "begin":
-                call += 1
-                continue
-            key = f"{names[min(call, len(names) - 1)]}/{kname}"
-            step_k[key] = step_k.get(key, 0.0) + kms
-        kernel_ms.append(step_k)
-    torch.cuda.synchronize()
+    stage_ms, _ = run_steps(traced=False)
     t_wall1 = time.time()
     launches = bd.kernel_launches() - launches_before
+    rescued = ctx.rescued_count(reset=True)
     if pg:
         pg.barrier()
     time.sleep(0.15)
     sampler.stop()
     clocks = sampler.summary(t_wall0 - 0.05, t_wall1 + 0.05)
-
-    stage_ms = np.array([[ev[s][j].elapsed_time(ev[s][j + 1]) for j in range(len(stages))]
-                         for s in range(K)])
-    step_ms = stage_ms.sum(axis=1)
-    ms = float(step_ms.mean())
+    ms = float(stage_ms.sum(axis=1).mean())
     if pg:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, pg, "cuda")
     assert ctx.sync_status() == 0, "device flags raised during the timed steps"
 
-    # ---- end to end through the public API with pinned host buffers ----
-    rescued = ctx.rescued_count(reset=True)
-    probes = components = None
+    # ---- the same K steps again with kernel-level events: per-kernel times ----
+    traced_stage_ms, kernel_ms = run_steps(traced=True)
+    assert ctx.sync_status() == 0, "device flags raised during the traced steps"
+
+    # ---- measured path rates, per-stage components ----
+    probes = measure_probes(ctx)
+    components = None
     if not args.no_components:
-        probes = measure_probes(ctx)
         components = measure_components(ctx, wl, probes)
     ctx.trace(False)
     ctx.trace_reset()
     ctx.rescued_count(reset=True)
+    # ---- end to end through the public API with pinned host buffers ----
     e2e = measure_e2e(ctx, wl, stages, max(3, min(K, 50)))
 
     if rank != 0:
@@ -396,10 +424,14 @@ def run_ours(args):
         "config": dict(wl.config, l2="flushed between steps (512 MB write)",
                        matching=("tensor cores (FP8 +-1, tcgen05)" if wl.match_kind == "tensor"
                                  else "POPC") if wl.match else None,
-                       parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+                       parallelism=(f"{world} ranks, independent inputs per rank (weak scaling)"
+                                    if world > 1 else "single GPU")),
         "matches_per_s": world * wl.pairs_per_step / (ms * 1e-3),
         "stage_ms": per_stage,
         "kernel_ms": per_kernel,
+        "kernel_ms_source": "kernel-level CUDA events on the launching stream over K further steps "
+                            "identical to the timed ones (traced step: "
+                            f"{float(traced_stage_ms.sum(axis=1).mean()):.4f} ms)",
         "hashsift_rescued_bits_per_step": rescued / K,
         "batch_config": wl.tuned,
         "roofline": roof,
@@ -421,12 +453,15 @@ def run_ours(args):
 # ---------------------------------------------------------------------------
 
 def _kernel_ms(ctx, fn, reps):
-    """Mean device time per call of each kernel that fn launches (trace events)."""
+    """Mean device time per call of each kernel that fn launches (trace events).
+    A device sleep is queued first, so the call is enqueued before the GPU
+    reaches it and the marks time the kernels, not the host's launch latency."""
     import torch
     fn()
     torch.cuda.synchronize()
     acc = {}
     for _ in range(reps):
+        torch.cuda._sleep(1_000_000)
         ctx.trace_reset()
         fn()
         torch.cuda.synchronize()
@@ -441,6 +476,7 @@ def measure_probes(ctx):
     windows (L1 hits), POPC, FFMA and MUFU instructions."""
     import torch
     import paper_2108_08380_gb300 as bd
+    ctx.trace(True)
     table = torch.randint(0, 1 << 20, (1 << 23,), dtype=torch.int32, device="cuda")
     cases = {
         "gather_l2": (bd.BD_PROBE_GATHER, 16, table, 1 << 23),
@@ -471,6 +507,7 @@ def measure_components(ctx, wl, probes):
     matching (time and record equality)."""
     import torch
     import paper_2108_08380_gb300 as bd
+    ctx.trace(True)
     reps = 10
     img = wl.dimg[0]
     na = int(wl.offsets[1])
@@ -542,6 +579,15 @@ def measure_components(ctx, wl, probes):
                 "records_equal": bool(torch.equal(m1, m2)),
                 "pairs_per_s_popc": na * nb / tp, "pairs_per_s_tensor": na * nb / tt_,
                 "work": f"{na} x {nb} pairs x {K // 32} POPC"}
+            # mutual nearest neighbours (Sec. V): both directions + cross-check
+            tc = wl.match_kind == "tensor"
+            mnn = torch.empty(na, dtype=torch.int32, device="cuda")
+            km = _kernel_ms(ctx, lambda: ctx.match_mnn(qq, tt, K, 4, 5, tensor_cores=tc,
+                                                       out=m1, mnn=mnn), reps)
+            torch.cuda.synchronize()
+            res[f"mnn_{lab}"] = {"ms": sum(km.values()), "kernels": km,
+                                 "kernel": "tensor cores" if tc else "POPC",
+                                 "mutual_pairs": int((mnn >= 0).sum().item())}
     return res
 
 
@@ -580,7 +626,9 @@ def roofline(wl, per_kernel, clocks, probes=None):
     Denominators are measured: MEASURED_PEAKS.json for HBM and BF16 tensor
     throughput, the bd_probe kernels for POPC, FFMA and gather rates (derived
     from unit counts and the sampled clock only when the probes were skipped).
-    Algorithmic work per launch and each kernel's bound are listed in the design doc."""
+    Algorithmic work per unit: 6 B per pixel (integral image), 8 x K lookups
+    per BAD keypoint, HS_OPS_PER_PIXEL x 1024 per HashSIFT patch, 2 x 128 x K
+    flop per projected keypoint, K/32 POPC or 2 x K flop per matched pair."""
     peaks, kind = load_peaks()
     key = max(per_kernel, key=per_kernel.get)
     t = per_kernel[key] * 1e-3
@@ -640,7 +688,7 @@ def roofline(wl, per_kernel, clocks, probes=None):
     return out
 
 
-# FP32/SFU operations one patch pixel of the HashSIFT histogram needs (DESIGN.md):
+# FP32/SFU operations one patch pixel of the HashSIFT histogram needs:
 # sample position 4, tap split 4, bilinear 6, gradient 4, magnitude 3, orientation
 # (atan2 as 1), bin split 3, Gaussian weight 1, two votes 4.
 HS_OPS_PER_PIXEL = 30
@@ -700,7 +748,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-components", action="store_true",
-                    help="skip the probe kernels and the per-stage component measurements")
+                    help="skip the per-stage component measurements")
+    ap.add_argument("--batch-config", default=None,
+                    help="bad_kp_per_item,ctas_per_sm,hs_first for the persistent kernel "
+                         "instead of the autotuner's pick")
     ap.add_argument("--match", choices=["auto", "tensor", "popc"], default="auto",
                     help="matching kernel: tensor cores (bd_match_tc), POPC (bd_match), or auto "
                          "(tensor cores from 2^24 query-train pairs up)")

@@ -370,6 +370,28 @@ bd_status bd_match_tc(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t,
                       int nbits, int ratio_num, int ratio_den, bd_match_result *out);
 
 /* ------------------------------------------------------------------------ */
+/* Mutual nearest neighbours                                                 */
+
+/* Hamming mutual-nearest-neighbour matching, the matching step of the
+ * paper's pipeline-timing experiment (Sec. V: ORB detection, Hamming MNN
+ * matching, PROSAC).  Query i and train entry j are a mutual pair iff j is
+ * the nearest train entry of i and i is the nearest query of j, each
+ * direction breaking equal distances to the lowest index.
+ *  - out (device, nq records): the bd_match records of q against t, exactly
+ *    as bd_match / bd_match_tc return them (ratio test ratio_num/ratio_den).
+ *  - mnn (device, nq int32): out[i].idx when the pair is mutual, else -1.
+ *  - tensor_cores: 0 runs both directions on the POPC kernel, 1 on the
+ *    tensor-core kernel; the results are identical.
+ *  - Scratch: nt * 12 bytes (rounded up to 256) for the reverse records plus
+ *    the larger of the two directions' matching scratch.
+ *  - Errors: BD_ERR_INVALID as for bd_match, and also when nq > 2^22 - 1, mnn is
+ *    null or misaligned, or (tensor cores) nt > 65535 * 128.  nq = 0 is a
+ *    no-op; nt = 0 gives out as bd_match does and mnn = -1 everywhere. */
+bd_status bd_match_mnn(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt,
+                       int nbits, int ratio_num, int ratio_den, int tensor_cores,
+                       bd_match_result *out, int32_t *mnn);
+
+/* ------------------------------------------------------------------------ */
 /* Measurement probes (the paper has no counterpart: they give each kernel's  */
 /* roofline a measured denominator)                                          */
 

@@ -82,6 +82,7 @@ _SIGS = [
     ("bd_train_forward", _I, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     ("bd_train_backward", _I, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     ("bd_bad_describe_noalloc", _I, [_P, _P, _I, _I, _I, _P, _I, _P, _P]),
+    ("bd_match_mnn", _I, [_P, _P, _I, _P, _I, _I, _I, _I, _I, _P, _P]),
     ("bd_probe", _I, [_P, _I, _P, ctypes.c_size_t, ctypes.c_size_t, _I, _P,
                       ctypes.POINTER(ctypes.c_uint64)]),
 ]
@@ -327,6 +328,22 @@ class Context:
                     "bd_match_tc" if tensor_cores else "bd_match")
         return out
 
+
+    def match_mnn(self, q, t, nbits: int, ratio_num: int = 4, ratio_den: int = 5,
+                  tensor_cores: bool = False, out=None, mnn=None):
+        """Mutual nearest neighbours: (records as match() returns them,
+        int32 [nq] partner index or -1)."""
+        torch = self._torch
+        nq, nt = q.shape[0], t.shape[0]
+        if out is None:
+            out = torch.empty((nq, 3), dtype=torch.int32, device=q.device)
+        if mnn is None:
+            mnn = torch.empty(nq, dtype=torch.int32, device=q.device)
+        self._stream()
+        self._check(lib().bd_match_mnn(self.handle, _ptr(q), nq, _ptr(t), nt, nbits, ratio_num,
+                                       ratio_den, int(bool(tensor_cores)), _ptr(out), _ptr(mnn)),
+                    "bd_match_mnn")
+        return out, mnn
 
     def probe(self, kind: int, reps: int, table=None, window_words: int = 0, sink=None) -> int:
         """Enqueues one bd_probe kernel on the current stream; returns the

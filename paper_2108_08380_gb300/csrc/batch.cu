@@ -6,7 +6,7 @@
 // claims work items from an atomic counter, in this order (or with the
 // HashSIFT items last, a tunable):
 //   [integral pass-1 tiles of all images]
-//   [HashSIFT keypoints]                       (no dependency)
+//   [HashSIFT keypoints, four per item]        (no dependency)
 //   [integral pass-2 tiles of all images]      (wait: the image's pass-1 tiles)
 //   [BAD keypoint groups, per image]           (wait: the image's pass-2 tiles)
 // Every wait is on items with smaller indices, already claimed by resident
@@ -36,7 +36,7 @@ struct BatchKernelArgs {
     const BatchImageDev *imgs;
     const uint8_t *const *img_ptr;
     int n_img, n_tiles, n_kp, n_bad_items, bad_per_item;
-    int hs_items;            // n_kp if HashSIFT is on, else 0
+    int hs_items;            // ceil(n_kp / 4) if HashSIFT is on, else 0
     int hs_first;
     uint32_t *ii, *carry;
     unsigned int *work, *stats_done, *final_done;
@@ -109,12 +109,11 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
     __shared__ union {
         dev::IiStatsSmem s;
         dev::IiFinalSmem f;
-        dev::HistSmem h;
+        dev::WarpHist h[4];  // one per warp
     } U;
     __shared__ unsigned int item_s;
     __shared__ int flag_s;
     const int t = threadIdx.x;
-    const dev::HistLane L = dev::hist_lane(t);
 
     // item ranges
     const int e_stats = A.n_tiles;
@@ -144,11 +143,15 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                 atomicAdd(A.stats_done + im, 1u);
             }
         } else if (item >= b_hs && item < b_hs + n_hs) {
-            const int k = item - b_hs;
-            const int im = find_image(A.imgs, A.n_img, k, 1);
-            const BatchImageDev &I = A.imgs[im];
-            dev::hs_hist_one(U.h, L, A.img_ptr[im], I.w, I.h, I.pitch, A.kps[k], A.spacing, A.hist,
-                             A.hist16, (size_t)k, (size_t)A.n_kp, A.status);
+            // four keypoints per item, one per warp
+            const int k = (item - b_hs) * 4 + (t >> 5);
+            if (k < A.n_kp) {
+                const int im = find_image(A.imgs, A.n_img, k, 1);
+                const BatchImageDev &I = A.imgs[im];
+                dev::hs_hist_image_warp(U.h[t >> 5], A.img_ptr[im], I.w, I.h, I.pitch, A.kps[k],
+                                        A.spacing, A.hist, A.hist16, (size_t)k, (size_t)A.n_kp,
+                                        A.status);
+            }
             __syncthreads();
         } else if (item >= b_final && item < b_final + A.n_tiles) {
             const int tile = item - b_final;
@@ -233,7 +236,7 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     A.n_kp = b->n_kp;
     A.bad_per_item = b->cfg.bad_kp_per_item;
     A.n_bad_items = (b->bad && bad_out) ? b->n_bad_items : 0;
-    A.hs_items = (b->hs && hs_out) ? b->n_kp : 0;
+    A.hs_items = (b->hs && hs_out) ? (b->n_kp + 3) / 4 : 0;
     A.hs_first = b->cfg.hs_first;
     A.ii = b->d_ii;
     A.carry = b->d_carry;
@@ -503,6 +506,8 @@ bd_status bd_describe_batch(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     key.push_back(kps);
     key.push_back(bad_out);
     key.push_back(hs_out);
+    // the graph holds the trace events or not: re-capture when tracing is switched
+    key.push_back(reinterpret_cast<const void *>((uintptr_t)(ctx->trace ? 1 : 0)));
     if (!b->gexec || key != b->gkey) {
         drop_graph(b);
         cudaGraph_t g = nullptr;

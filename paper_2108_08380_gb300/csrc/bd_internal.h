@@ -191,6 +191,10 @@ cudaError_t launch_probe(int kind, const uint32_t *table, size_t table_words, si
                          int reps, uint32_t *sink, int sm_count, cudaStream_t st,
                          unsigned long long *units, bool *bad_args);
 
+// mnn[i] = fwd[i].idx if rev[fwd[i].idx].idx == i, else -1 (rev: nearest queries of t)
+cudaError_t launch_mnn_cross(const bd_match_result *fwd, const bd_match_result *rev, int nq,
+                             int32_t *mnn, cudaStream_t st);
+
 int match_query_blocks(int nq);
 // arrivals: one zero-initialised counter per query block (ctx-owned; each call leaves them zero)
 cudaError_t launch_match(const uint32_t *q, int nq, const uint32_t *t, int nt, int nbits,

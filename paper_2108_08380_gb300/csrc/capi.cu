@@ -849,6 +849,66 @@ bd_status bd_match(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, in
     return BD_OK;
 }
 
+bd_status bd_match_mnn(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt,
+                       int nbits, int ratio_num, int ratio_den, int tensor_cores,
+                       bd_match_result *out, int32_t *mnn)
+{
+    BD_GUARD(ctx);
+    if (((uintptr_t)q & 15) || ((uintptr_t)t & 15) || ((uintptr_t)out & 3) || ((uintptr_t)mnn & 3))
+        return set_err(ctx, BD_ERR_INVALID,
+                       "bd_match_mnn: descriptor arrays must be 16-byte, out and mnn 4-byte aligned");
+    if ((nbits != 256 && nbits != 512) || nq < 0 || nt < 0 || nt > (int)kMatchIdxMask ||
+        nq > (int)kMatchIdxMask || ratio_den <= 0 || ratio_num <= 0 || ratio_num > ratio_den ||
+        (nq > 0 && (!q || !out || !mnn)) || (nt > 0 && !t) ||
+        (tensor_cores && ((nq + 127) / 128 > 65535 || (nt + 127) / 128 > 65535)))
+        return set_err(ctx, BD_ERR_INVALID, "bd_match_mnn: bad arguments");
+    if (nq == 0)
+        return BD_OK;
+    // reverse records first in the scratch area, the matchings' own scratch after them
+    const size_t rev_bytes = align_up((size_t)(nt > 0 ? nt : 1) * sizeof(bd_match_result), 256);
+    size_t need = tensor_cores ? match_tc_scratch_bytes(nq, nt, nbits, ctx->sm_count)
+                               : match_scratch_bytes(nq, nt, nbits, ctx->sm_count);
+    int qblocks = tensor_cores ? match_tc_query_blocks(nq) : match_query_blocks(nq);
+    if (nt > 0) {
+        const size_t rn = tensor_cores ? match_tc_scratch_bytes(nt, nq, nbits, ctx->sm_count)
+                                       : match_scratch_bytes(nt, nq, nbits, ctx->sm_count);
+        const int rb = tensor_cores ? match_tc_query_blocks(nt) : match_query_blocks(nt);
+        need = need > rn ? need : rn;
+        qblocks = qblocks > rb ? qblocks : rb;
+    }
+    bd_status s = ensure_scratch(ctx, rev_bytes + need);
+    if (s == BD_OK)
+        s = ensure_arrivals(ctx, qblocks);
+    if (s != BD_OK)
+        return s;
+    bd_match_result *rev = (bd_match_result *)ctx->scratch;
+    void *work = (char *)ctx->scratch + rev_bytes;
+    TraceScope scope(ctx, ctx->stream);
+    if (tensor_cores) {
+        BD_LAUNCH(ctx,
+                  launch_match_tc(ctx, q, nq, t, nt, nbits, ratio_num, ratio_den, out, work,
+                                  ctx->stream, ctx->arrivals),
+                  "tensor-core matching kernels");
+        if (nt > 0)
+            BD_LAUNCH(ctx,
+                      launch_match_tc(ctx, t, nt, q, nq, nbits, ratio_num, ratio_den, rev, work,
+                                      ctx->stream, ctx->arrivals),
+                      "tensor-core matching kernels (reverse)");
+    } else {
+        BD_LAUNCH(ctx,
+                  launch_match(q, nq, t, nt, nbits, ratio_num, ratio_den, out, work, ctx->sm_count,
+                               ctx->stream, ctx->arrivals),
+                  "matching kernel");
+        if (nt > 0)
+            BD_LAUNCH(ctx,
+                      launch_match(t, nt, q, nq, nbits, ratio_num, ratio_den, rev, work,
+                                   ctx->sm_count, ctx->stream, ctx->arrivals),
+                      "matching kernel (reverse)");
+    }
+    BD_LAUNCH(ctx, launch_mnn_cross(out, rev, nq, mnn, ctx->stream), "mutual check kernel");
+    return BD_OK;
+}
+
 bd_status bd_probe(bd_ctx *ctx, int kind, const uint32_t *table, size_t table_words,
                    size_t window_words, int reps, uint32_t *sink, uint64_t *units)
 {

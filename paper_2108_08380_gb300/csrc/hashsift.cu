@@ -9,21 +9,20 @@
 namespace bd {
 namespace {
 
-using dev::HistLane;
-using dev::HistSmem;
 using dev::NT;
 using dev::PS;
 
+// One warp per keypoint (hs_hist_warp); the CTA's warps take independent keypoints.
 __global__ void __launch_bounds__(NT) hs_hist_image_kernel(
     const uint8_t *__restrict__ img, int w, int h, int pitch, const bd_keypoint *__restrict__ kps,
     int n, float spacing, float *__restrict__ hist, __nv_bfloat16 *__restrict__ hist16,
     DeviceStatus *status)
 {
-    __shared__ HistSmem S;
-    const HistLane L = dev::hist_lane(threadIdx.x);
-    for (int k = blockIdx.x; k < n; k += gridDim.x)
-        dev::hs_hist_one(S, L, img, w, h, pitch, kps[k], spacing, hist, hist16, (size_t)k,
-                         (size_t)n, status);
+    __shared__ dev::WarpHist S[NT / 32];
+    const int warp = threadIdx.x >> 5;
+    for (int k = blockIdx.x * (NT / 32) + warp; k < n; k += gridDim.x * (NT / 32))
+        dev::hs_hist_image_warp(S[warp], img, w, h, pitch, kps[k], spacing, hist, hist16,
+                                (size_t)k, (size_t)n, status);
 }
 
 __global__ void __launch_bounds__(NT) hs_hist_patch_kernel(const float *__restrict__ patches,
@@ -31,48 +30,46 @@ __global__ void __launch_bounds__(NT) hs_hist_patch_kernel(const float *__restri
                                                            __nv_bfloat16 *__restrict__ hist16,
                                                            float *__restrict__ norm_out)
 {
-    __shared__ HistSmem S;
-    const int t = threadIdx.x;
-    const HistLane L = dev::hist_lane(t);
-    for (int k = blockIdx.x; k < n; k += gridDim.x) {
-        const float *src = patches + (size_t)k * PS * PS;
-#pragma unroll
-        for (int r = 0; r < PS * PS / NT; ++r) {
-            const int p = t + r * NT;
-            S.P[p >> 5][p & 31] = __ldg(src + p);
-        }
-#pragma unroll
-        for (int b = 0; b < 8; ++b)
-            S.priv[b][t] = 0.0f;
-        __syncthreads();
-        dev::vote(S, L, t);
-        __syncthreads();
-        dev::hist_finish(S, t, true, hist, hist16, (size_t)k, (size_t)n, norm_out);
+    __shared__ dev::WarpHist S[NT / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = blockIdx.x * (NT / 32) + warp; k < n; k += gridDim.x * (NT / 32)) {
+        dev::PatchMem src;
+        src.p = patches + (size_t)k * PS * PS;
+        dev::hs_hist_warp(S[warp], src, true, lane, hist, hist16, (size_t)k, (size_t)n, norm_out);
     }
 }
 
+// Standalone patch warp (bd_hashsift_warp): the same sampler as the histogram.
 __global__ void __launch_bounds__(NT) hs_warp_kernel(const uint8_t *__restrict__ img, int w, int h,
                                                      int pitch,
                                                      const bd_keypoint *__restrict__ kps, int n,
                                                      float spacing, float *__restrict__ patches,
                                                      DeviceStatus *status)
 {
-    const int t = threadIdx.x;
-    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = blockIdx.x * (NT / 32) + warp; k < n; k += gridDim.x * (NT / 32)) {
         const bd_keypoint kp = kps[k];
-        float *dst = patches + (size_t)k * PS * PS;
+        float *dst = patches + (size_t)k * PS * PS + lane;
         if (!dev::kp_valid(kp)) {
-            for (int p = t; p < PS * PS; p += NT)
-                dst[p] = 0.0f;
-            if (t == 0)
+            for (int i = 0; i < PS; ++i)
+                dst[i * PS] = 0.0f;
+            if (lane == 0)
                 dev::raise_flag(status, BD_FLAG_INVALID_KEYPOINT);
             continue;
         }
         const dev::Frame f = dev::make_frame(kp, spacing);
-#pragma unroll
-        for (int r = 0; r < PS * PS / NT; ++r) {
-            const int p = t + r * NT;
-            dst[p] = dev::sample(img, w, h, pitch, f, p >> 5, p & 31);
+        if (dev::col_interior(f, w, h)) {
+            dev::ColSampler<true> cs;
+            cs.c = dev::col_frame(img, w, h, pitch, f, lane);
+#pragma unroll 8
+            for (int i = 0; i < PS; ++i)
+                dst[i * PS] = cs.at(i, lane);
+        } else {
+            dev::ColSampler<false> cs;
+            cs.c = dev::col_frame(img, w, h, pitch, f, lane);
+#pragma unroll 8
+            for (int i = 0; i < PS; ++i)
+                dst[i * PS] = cs.at(i, lane);
         }
     }
 }
@@ -191,7 +188,7 @@ cudaError_t launch_hs_warp(const bd_hs_params *p, const uint8_t *img, int w, int
                            const bd_keypoint *kps, int n, float *patches, DeviceStatus *status,
                            cudaStream_t st, int sm_count)
 {
-    hs_warp_kernel<<<grid_for(n, sm_count, 16), NT, 0, st>>>(img, w, h, pitch, kps, n, p->spacing,
+    hs_warp_kernel<<<grid_for((n + 3) / 4, sm_count, 16), NT, 0, st>>>(img, w, h, pitch, kps, n, p->spacing,
                                                              patches, status);
     trace_kernel(st, "hs_warp");
     note_launches(1);
@@ -202,7 +199,7 @@ cudaError_t launch_hs_hist_patches(const float *patches, int n, float *hist,
                                    __nv_bfloat16 *hist16, cudaStream_t st, int sm_count,
                                    float *norm_out)
 {
-    hs_hist_patch_kernel<<<grid_for(n, sm_count, 12), NT, 0, st>>>(patches, n, hist, hist16,
+    hs_hist_patch_kernel<<<grid_for((n + 3) / 4, sm_count, 12), NT, 0, st>>>(patches, n, hist, hist16,
                                                                    norm_out);
     trace_kernel(st, "hs_hist_patch");
     note_launches(1);
@@ -214,7 +211,7 @@ cudaError_t launch_hs_hist_image(const bd_hs_params *p, const uint8_t *img, int 
                                  __nv_bfloat16 *hist16, DeviceStatus *status, cudaStream_t st,
                                  int sm_count)
 {
-    hs_hist_image_kernel<<<grid_for(n, sm_count, 12), NT, 0, st>>>(img, w, h, pitch, kps, n,
+    hs_hist_image_kernel<<<grid_for((n + 3) / 4, sm_count, 12), NT, 0, st>>>(img, w, h, pitch, kps, n,
                                                                    p->spacing, hist, hist16,
                                                                    status);
     trace_kernel(st, "hs_hist_image");

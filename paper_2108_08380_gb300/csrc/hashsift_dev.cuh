@@ -1,5 +1,6 @@
 // HashSIFT per-keypoint routines (Sec. III-B), FP32 on CUDA cores; shared by
-// the per-image kernels (hashsift.cu) and the batched persistent kernel.
+// the per-image kernels (hashsift.cu), the batched persistent kernel and the
+// training step.
 //
 //  - the 32x32 patch, sampled bilinearly around the keypoint (Sec. IV-F:
 //    HashSIFT describes a normalised 32x32 patch, not an image pyramid);
@@ -7,11 +8,19 @@
 //    bins with linear voting between neighbours, 4x4 cells of 8x8 pixels, a
 //    sigma = 16 Gaussian weight about the patch centre, L2 normalisation.
 //
-// One CTA of 128 threads describes one keypoint.  Thread t owns cell t/8 and
-// pixel row t%8 of that cell: its 8 pixels vote into a thread-private 8-bin
-// histogram in shared memory laid out [bin][thread] (conflict-free), and
-// thread t then sums bin t%8 of cell t/8 over the cell's 8 threads.  No
-// atomics are needed.
+// One warp describes one keypoint (hs_hist_warp), in three phases:
+//  1. sample the 1024 patch pixels in 4x8 blocks (one block per warp-wide
+//     load: a compact block of a rotated patch touches a few image rows,
+//     where a 32-pixel patch row can touch one row per pixel) into the
+//     warp's patch buffer in shared memory, rows padded to 40 floats so both
+//     the block writes and the row reads are conflict-free;
+//  2. lane j walks down patch column j with the vertical neighbours in
+//     registers and the horizontal ones from the neighbouring lanes, voting
+//     into a lane-private histogram of the four cells its column crosses,
+//     laid out [cell row][bin][lane] (conflict-free, no atomics);
+//  3. each lane sums four of the 128 (cell, bin) entries over the cell's 8
+//     columns and the warp normalises them.
+// There is no CTA-wide barrier: the warps of a CTA run independent keypoints.
 #pragma once
 
 #include "bd_internal.h"
@@ -123,15 +132,9 @@ __device__ __forceinline__ float orientation8(float gx, float gy)
     return q;
 }
 
-struct HistSmem {
-    float P[PS][PSP];
-    float priv[8][NT];
-    float wss[NT / 32];
-    int valid;
-};
-
-// Per-thread constants of the histogram mapping: pixel row i, first column j0
-// and the separable Gaussian weights gi * gj[q] (Sec. III-B; sigma = 16).
+// Per-thread constants of the 128-thread histogram layout used by the
+// training backward (thread t: cell t/8, pixel row t%8 of it): pixel row i,
+// first column j0 and the separable Gaussian weights gi * gj[q] (sigma = 16).
 struct HistLane {
     int i, j0;
     float g[8];
@@ -155,95 +158,276 @@ __device__ __forceinline__ HistLane hist_lane(int t)
     return L;
 }
 
-// Votes of this thread's 8 pixels into its private histogram column.
-__device__ __forceinline__ void vote(HistSmem &S, const HistLane &L, int t)
+// ---------------------------------------------------------------------------
+// warp per keypoint
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Splits x (|x| < 2^21) into x = i + f exactly, with i an integer and f in
+// [0, 1]: i = floor(x), or floor(x) - 1 with f = 1 when x is an integer.
+// Adding 1.5 * 2^23 rounds to an integer in the mantissa, so this takes FP32
+// adds and one integer subtract instead of conversion instructions.  Either
+// split gives the same bilinear value and the same orientation votes.
+__device__ __forceinline__ int split_floor(float x, float &f)
 {
-    const int i = L.i;
-    const int iu = max(i - 1, 0), id = min(i + 1, PS - 1);
-    float left = S.P[i][max(L.j0 - 1, 0)];
-    float mid = S.P[i][L.j0];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int j = L.j0 + q;
-        const float right = S.P[i][min(j + 1, PS - 1)];
-        const float gx = 0.5f * (right - left);
-        const float gy = 0.5f * (S.P[id][j] - S.P[iu][j]);
-        left = mid;
-        mid = right;
-        const float m2 = gx * gx + gy * gy;
-        if (!(m2 > 0.0f))
-            continue;  // no gradient, no vote
-        const float m = m2 * rsqrtf(m2);
-        const float tt = orientation8(gx, gy);  // 8 phi / (2 pi)
-        const float fl = floorf(tt);
-        const float w1 = tt - fl;
-        const int b0 = ((int)fl) & 7;
-        const int b1 = (b0 + 1) & 7;
-        const float gm = L.g[q] * m;
-        const float v1 = gm * w1;
-        S.priv[b0][t] += gm - v1;
-        S.priv[b1][t] += v1;
-    }
+    const float M = 12582912.0f;  // 1.5 * 2^23, bit pattern 0x4B400000
+    const float t = __fadd_rn(__fadd_rn(x, -0.5f), M);
+    f = __fadd_rn(x, -__fadd_rn(t, -M));
+    return __float_as_int(t) - 0x4B400000;
 }
 
-// Sum of the cell's 8 private columns for bin t%8, L2 norm, output.
-__device__ __forceinline__ void hist_finish(HistSmem &S, int t, bool valid, float *__restrict__ hist,
-                                       __nv_bfloat16 *__restrict__ hist16, size_t kp, size_t nkp,
-                                       float *__restrict__ norm_out = nullptr)
+// uint8 value as FP32 through the mantissa (exact for b < 2^23).
+__device__ __forceinline__ float u8f(uint32_t b)
 {
-    const int cell = t >> 3, b = t & 7;
-    float H = 0.0f;
+    return __uint_as_float(0x4B000000u | b) - 8388608.0f;
+}
+
+// Bilinear sampler of patch column j of a keypoint: pixel (i, j) samples
+// (x, y) + scale * spacing * R(angle) (j - 15.5, i - 15.5), clamp to edge.
+// The offset from the rounded keypoint is kept small so FP32 keeps ~1e-6 px.
+// Interior = true (decided once per keypoint, see col_interior) reads the
+// four taps without clamping: the whole footprint lies inside the image.
+struct ColFrame {
+    const uint8_t *img;
+    int w, h, pitch, ix, iy;
+    float A, B, cx, cy;
+};
+
+__device__ __forceinline__ ColFrame col_frame(const uint8_t *img, int w, int h, int pitch,
+                                              const Frame &f, int j = 0)
+{
+    ColFrame c;
+    c.img = img;
+    c.w = w;
+    c.h = h;
+    c.pitch = pitch;
+    c.ix = f.ix;
+    c.iy = f.iy;
+    c.A = f.A;
+    c.B = f.B;
+    c.cx = f.fx;
+    c.cy = f.fy;
+    (void)j;
+    return c;
+}
+
+// True when every tap of the patch is inside the image with a margin:
+// |offset| <= 15.5 (|A| + |B|) + 0.5, taps reach one pixel beyond, and
+// split_floor may step one more to the left / top.
+__device__ __forceinline__ bool col_interior(const Frame &f, int w, int h)
+{
+    const float reach = 15.5f * (fabsf(f.A) + fabsf(f.B));
+    if (!(reach < 1.0e6f) || w < 2 || h < 2)
+        return false;
+    const int m = (int)reach + 5;
+    return f.ix - m >= 0 && f.ix + m < w && f.iy - m >= 0 && f.iy + m < h;
+}
+
+template <bool Interior>
+struct ColSampler {
+    ColFrame c;
+
+    __device__ __forceinline__ float at(int i, int j) const
+    {
+        const float u = (float)j - 15.5f, v = (float)i - 15.5f;
+        float ox = fmaf(c.A, u, fmaf(-c.B, v, c.cx));
+        float oy = fmaf(c.B, u, fmaf(c.A, v, c.cy));
+        if (!Interior) {  // keep split_floor in range; the taps clamp to the edge anyway
+            ox = fminf(fmaxf(ox, -1048576.0f), 1048576.0f);
+            oy = fminf(fmaxf(oy, -1048576.0f), 1048576.0f);
+        }
+        float ax, ay;
+        int x0 = split_floor(ox, ax) + c.ix;
+        int y0 = split_floor(oy, ay) + c.iy;
+        float i00, i01, i10, i11;
+        if (Interior) {
+            const uint8_t *p = c.img + (size_t)y0 * c.pitch + x0;
+            i00 = u8f(__ldg(p));
+            i01 = u8f(__ldg(p + 1));
+            i10 = u8f(__ldg(p + c.pitch));
+            i11 = u8f(__ldg(p + c.pitch + 1));
+        } else if (c.w >= 2 && c.h >= 2) {
+            // a sample left of / above the image reads column / row 0 with
+            // weight 0 on the next one; at or beyond the last column / row it
+            // reads that one with weight 1
+            if (x0 < 0) {
+                x0 = 0;
+                ax = 0.0f;
+            } else if (x0 > c.w - 2) {
+                x0 = c.w - 2;
+                ax = 1.0f;
+            }
+            if (y0 < 0) {
+                y0 = 0;
+                ay = 0.0f;
+            } else if (y0 > c.h - 2) {
+                y0 = c.h - 2;
+                ay = 1.0f;
+            }
+            const uint8_t *p = c.img + (size_t)y0 * c.pitch + x0;
+            i00 = u8f(__ldg(p));
+            i01 = u8f(__ldg(p + 1));
+            i10 = u8f(__ldg(p + c.pitch));
+            i11 = u8f(__ldg(p + c.pitch + 1));
+        } else {
+            const int xa = min(max(x0, 0), c.w - 1), xb = min(max(x0 + 1, 0), c.w - 1);
+            const int ya = min(max(y0, 0), c.h - 1), yb = min(max(y0 + 1, 0), c.h - 1);
+            const uint8_t *ra = c.img + (size_t)ya * c.pitch;
+            const uint8_t *rb = c.img + (size_t)yb * c.pitch;
+            i00 = u8f(__ldg(ra + xa));
+            i01 = u8f(__ldg(ra + xb));
+            i10 = u8f(__ldg(rb + xa));
+            i11 = u8f(__ldg(rb + xb));
+        }
+        const float top = fmaf(ax, i01 - i00, i00);
+        const float bot = fmaf(ax, i11 - i10, i10);
+        return fmaf(ay, bot - top, top);
+    }
+};
+
+// A patch already in memory ([32][32] FP32, row-major).
+struct PatchMem {
+    const float *p;
+    __device__ __forceinline__ float at(int i, int j) const { return __ldg(p + i * PS + j); }
+};
+
+constexpr int kPRow = 40;  // padded patch row: bank (8 i + j) % 32 is distinct per block and per row
+
+struct WarpHist {
+    float P[PS][kPRow];    // patch samples [row][column]
+    float priv[4][8][32];  // [cell row][bin][lane]
+};
+
+// Gaussian weight exp(-(d^2) / 512) of row / column index i (sigma = 16 about
+// 15.5); __expf's relative error (~2^-21) is far below the histogram tolerance.
+__device__ __forceinline__ float gauss16(int i)
+{
+    const float d = (float)i - 15.5f;
+    return __expf(-d * d * (1.0f / 512.0f));
+}
+
+// Votes of pixel (i, lane) with vertical neighbours up / down and the row's
+// value here.  gx, gy are twice the central differences, so the weight is
+// halved (exact).  Lanes 0 and 31 get their own value from the shuffles,
+// which is the replicated edge.  A zero gradient votes zero (no branch).
+__device__ __forceinline__ void vote_px(WarpHist &S, int lane, int i, float up, float here,
+                                        float down, float g_half)
+{
+    const float left = __shfl_up_sync(kFull, here, 1);
+    const float right = __shfl_down_sync(kFull, here, 1);
+    const float gx = right - left;
+    const float gy = down - up;
+    const float m2 = gx * gx + gy * gy;
+    const float gi = __shfl_sync(kFull, g_half, i);  // lane i holds half its weight
+    const bool any = m2 > 0.0f;
+    const float m = any ? m2 * rsqrtf(m2) : 0.0f;
+    float w1;
+    const int b0 = split_floor(orientation8(any ? gx : 1.0f, gy), w1) & 7;
+    const int b1 = (b0 + 1) & 7;
+    // (g_i g_j) |grad|: gi and g_half carry a factor 1/2 each, m a factor 2
+    const float gm = (2.0f * gi * g_half) * m;
+    const float v1 = gm * w1;
+    float *col = &S.priv[i >> 3][0][lane];
+    col[b0 * 32] += gm - v1;
+    col[b1 * 32] += v1;
+}
+
+// Histogram of one keypoint by one warp: rows from `src` (a ColSampler or a
+// PatchCol of this lane's column), output like the oracle's [cell][bin]
+// order, L2-normalised, with optional BF16 head/tail copies and norm.
+template <class Src>
+__device__ __forceinline__ void hs_hist_warp(WarpHist &S, const Src &src, bool valid, int lane,
+                                             float *__restrict__ hist,
+                                             __nv_bfloat16 *__restrict__ hist16, size_t k,
+                                             size_t n, float *__restrict__ norm_out)
+{
+    {
+        float4 *z = reinterpret_cast<float4 *>(&S.priv[0][0][0]);
 #pragma unroll
-    for (int s = 0; s < 8; ++s)
-        H += S.priv[b][cell * 8 + ((s + b) & 7)];
-    float ss = H * H;
+        for (int q = 0; q < 8; ++q)
+            z[q * 32 + lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    __syncwarp();
+    if (valid) {
+        // 1. samples in 4x8 blocks: block bb covers rows 4 (bb / 4) + [0, 4),
+        //    columns 8 (bb % 4) + [0, 8); lane -> (lane / 8, lane % 8)
+        const int bi = lane >> 3, bj = lane & 7;
+#pragma unroll 8
+        for (int bb = 0; bb < 32; ++bb) {
+            const int i = 4 * (bb >> 2) + bi, j = 8 * (bb & 3) + bj;
+            S.P[i][j] = src.at(i, j);
+        }
+        __syncwarp();
+        // 2. votes down this lane's column
+        const float g_half = 0.5f * gauss16(lane);
+        float up = S.P[0][lane];  // replicated row -1
+        float here = up;
+#pragma unroll 8
+        for (int i = 0; i < PS; ++i) {
+            const float down = S.P[i < PS - 1 ? i + 1 : PS - 1][lane];
+            vote_px(S, lane, i, up, here, down, g_half);
+            up = here;
+            here = down;
+        }
+    }
+    __syncwarp();
+    // entry (cell row ci, cell column cj, bin b) = ci*32 + lane, lane = cj*8 + b
+    const int cj = lane >> 3, b = lane & 7;
+    float H[4];
+    float ss = 0.0f;
+#pragma unroll
+    for (int ci = 0; ci < 4; ++ci) {
+        float s = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            s += S.priv[ci][b][cj * 8 + ((q + b) & 7)];
+        H[ci] = s;
+        ss += s * s;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
-        ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if ((t & 31) == 0)
-        S.wss[t >> 5] = ss;
-    __syncthreads();
-    const float tot = S.wss[0] + S.wss[1] + S.wss[2] + S.wss[3];
-    const float nrm = sqrtf(tot);
-    if (norm_out && t == 0)
-        norm_out[kp] = valid ? nrm : 0.0f;
-    const float h = (valid && nrm > 0.0f) ? H / nrm : 0.0f;
-    hist[kp * kHistDim + t] = h;
-    if (hist16) {
-        const __nv_bfloat16 hi = __float2bfloat16_rn(h);
-        hist16[kp * kHistDim + t] = hi;
-        hist16[(nkp + kp) * kHistDim + t] = __float2bfloat16_rn(h - __bfloat162float(hi));
+        ss += __shfl_xor_sync(kFull, ss, o);
+    const float nrm = sqrtf(ss);
+    if (norm_out && lane == 0)
+        norm_out[k] = valid ? nrm : 0.0f;
+#pragma unroll
+    for (int ci = 0; ci < 4; ++ci) {
+        const float hv = (valid && nrm > 0.0f) ? H[ci] / nrm : 0.0f;
+        const size_t e = k * kHistDim + ci * 32 + lane;
+        hist[e] = hv;
+        if (hist16) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(hv);
+            hist16[e] = hi;
+            hist16[n * kHistDim + e] = __float2bfloat16_rn(hv - __bfloat162float(hi));
+        }
     }
+    __syncwarp();
 }
 
-
-// Histogram (and BF16 head/tail copies) of keypoint k of n, sampled from the
-// image; all 128 threads of the CTA call it with the same keypoint.
-__device__ __forceinline__ void hs_hist_one(HistSmem &S, const HistLane &L, const uint8_t *img,
-                                            int w, int h, int pitch, const bd_keypoint &kp,
-                                            float spacing, float *hist, __nv_bfloat16 *hist16,
-                                            size_t k, size_t n, DeviceStatus *status)
+// Histogram of keypoint k of n sampled from the image; all 32 lanes call it.
+__device__ __forceinline__ void hs_hist_image_warp(WarpHist &S, const uint8_t *img, int w, int h,
+                                                   int pitch, const bd_keypoint &kp, float spacing,
+                                                   float *hist, __nv_bfloat16 *hist16, size_t k,
+                                                   size_t n, DeviceStatus *status)
 {
-    const int t = threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const bool valid = kp_valid(kp);
-    if (valid) {
-        const Frame f = make_frame(kp, spacing);
-#pragma unroll
-        for (int r = 0; r < PS * PS / NT; ++r) {
-            const int p = t + r * NT;
-            S.P[p >> 5][p & 31] = sample(img, w, h, pitch, f, p >> 5, p & 31);
-        }
-    } else if (t == 0) {
-        raise_flag(status, BD_FLAG_INVALID_KEYPOINT);
+    ColSampler<false> edge;
+    if (!valid) {
+        if (lane == 0)
+            raise_flag(status, BD_FLAG_INVALID_KEYPOINT);
+        hs_hist_warp(S, edge, false, lane, hist, hist16, k, n, nullptr);
+        return;
     }
-#pragma unroll
-    for (int b = 0; b < 8; ++b)
-        S.priv[b][t] = 0.0f;
-    __syncthreads();
-    if (valid)
-        vote(S, L, t);
-    __syncthreads();
-    hist_finish(S, t, valid, hist, hist16, k, n);
+    const Frame f = make_frame(kp, spacing);
+    if (col_interior(f, w, h)) {
+        ColSampler<true> in;
+        in.c = col_frame(img, w, h, pitch, f, lane);
+        hs_hist_warp(S, in, true, lane, hist, hist16, k, n, nullptr);
+    } else {
+        edge.c = col_frame(img, w, h, pitch, f, lane);
+        hs_hist_warp(S, edge, true, lane, hist, hist16, k, n, nullptr);
+    }
 }
 
 }  // namespace dev

@@ -165,4 +165,30 @@ cudaError_t launch_match(const uint32_t *q, int nq, const uint32_t *t, int nt, i
     return cudaGetLastError();
 }
 
+namespace {
+
+// Mutual check: query i keeps its nearest train entry j only if i is also
+// the nearest query of j (both directions break ties to the lowest index).
+__global__ void mnn_cross_kernel(const bd_match_result *__restrict__ fwd,
+                                 const bd_match_result *__restrict__ rev, int nq,
+                                 int32_t *__restrict__ mnn)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq)
+        return;
+    const int j = fwd[i].idx;
+    mnn[i] = (j >= 0 && rev[j].idx == i) ? j : -1;
+}
+
+}  // namespace
+
+cudaError_t launch_mnn_cross(const bd_match_result *fwd, const bd_match_result *rev, int nq,
+                             int32_t *mnn, cudaStream_t st)
+{
+    mnn_cross_kernel<<<(nq + 255) / 256, 256, 0, st>>>(fwd, rev, nq, mnn);
+    trace_kernel(st, "mnn_cross");
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace bd

@@ -116,3 +116,55 @@ def test_tensor_core_and_popc_agree_on_full_size(gpu_ctx, K):
     a = gpu_ctx.match(_dev(q), _dev(t), K).cpu().numpy()
     b = gpu_ctx.match(_dev(q), _dev(t), K, tensor_cores=True).cpu().numpy()
     assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# mutual nearest neighbours (bd_match_mnn, Sec. V)
+
+@pytest.mark.parametrize("K,nq,nt", [(256, 1000, 1000), (512, 333, 777), (256, 129, 4099),
+                                     (512, 5000, 3), (256, 1, 1), (256, 7, 0), (512, 300, 1)])
+def test_mnn_exact(gpu_ctx, K, nq, nt, tc):
+    import paper_2108_08380_gb300 as bd
+    rng = np.random.default_rng(K + 17 * nq + nt)
+    t = _rand_desc(rng, nt, K)
+    q = _rand_desc(rng, nq, K)
+    if nt:
+        q[: nq // 2] = _noisy(rng, t[rng.integers(0, nt, size=nq // 2)], K, K // 8)
+    out, mnn = gpu_ctx.match_mnn(_dev(q), _dev(t), K, tensor_cores=tc)
+    idx, d1, d2, acc = bd.unpack_matches(out)
+    ri, r1, r2, ra = oracle.match(q, t, K)
+    assert np.array_equal(idx, ri) and np.array_equal(d1, r1) and np.array_equal(d2, r2)
+    assert np.array_equal(acc, ra)
+    assert np.array_equal(mnn.cpu().numpy(), oracle.match_mnn(q, t, K))
+
+
+def test_mnn_duplicates_and_equal_queries(gpu_ctx, tc):
+    K = 256
+    rng = np.random.default_rng(9)
+    base = _rand_desc(rng, 64, K)
+    t = np.concatenate([base, base])                  # each entry twice
+    q = np.concatenate([base[:10], base[:10], base])  # equal queries compete for one entry
+    _, mnn = gpu_ctx.match_mnn(_dev(q), _dev(t), K, tensor_cores=tc)
+    want = oracle.match_mnn(q, t, K)
+    assert np.array_equal(mnn.cpu().numpy(), want)
+    assert np.array_equal(want[:10], np.arange(10)) and np.all(want[10:20] == -1)
+
+
+@pytest.mark.parametrize("K", [256, 512])
+def test_mnn_full_size_sampled(gpu_ctx, K, tc):
+    """20000 x 20000: for a seeded sample of queries the oracle gives the
+    nearest train entry j, then the nearest query of t[j] over all queries."""
+    rng = np.random.default_rng(K + 3)
+    n = 20000
+    t = _rand_desc(rng, n, K)
+    q = _noisy(rng, t[rng.permutation(n)], K, K // 5)
+    q[rng.choice(n, size=n // 4, replace=False)] = _rand_desc(rng, n // 4, K)  # unmatched queries
+    _, mnn = gpu_ctx.match_mnn(_dev(q), _dev(t), K, tensor_cores=tc)
+    mnn = mnn.cpu().numpy()
+    rows = np.sort(rng.choice(n, size=150, replace=False))
+    fwd, _, _, _ = oracle.match(q[rows], t, K)
+    back, _, _, _ = oracle.match(t[fwd], q, K)
+    want = np.where(back == rows, fwd, -1)
+    assert np.array_equal(mnn[rows], want)
+    partners = mnn[mnn >= 0]
+    assert len(partners) == len(np.unique(partners))  # a partial one-to-one matching
