@@ -370,6 +370,30 @@ bd_status bd_match_tc(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t,
                       int nbits, int ratio_num, int ratio_den, bd_match_result *out);
 
 /* ------------------------------------------------------------------------ */
+/* Several matchings in one launch                                           */
+
+#define BD_MATCH_MAX_JOBS 8
+
+/* One matching of a bd_match_batch call: the arguments of bd_match. */
+typedef struct {
+    const uint32_t *q;      /* device, nq x nbits/32 words, 16-byte aligned */
+    const uint32_t *t;      /* device, nt x nbits/32 words, 16-byte aligned */
+    bd_match_result *out;   /* device, nq records, 4-byte aligned */
+    int nq, nt, nbits, ratio_num, ratio_den;
+} bd_match_job;
+
+/* Runs up to BD_MATCH_MAX_JOBS independent bd_match problems (Sec. IV-C NN
+ * matching with the top-2 ratio test; Sec. III-A S = K - 2 Hamming) as one
+ * kernel launch on the POPC path, e.g. the BAD and the HashSIFT descriptors
+ * of an image pair, or several image pairs.  Every job gets exactly the
+ * records bd_match would return.  jobs is a host array, read during the
+ * call.  Jobs may mix nbits 256 and 512; a job with nq = 0 is skipped.
+ * Scratch: the sum of the jobs' bd_match scratch.  Errors: BD_ERR_INVALID for
+ * n_jobs outside [0, BD_MATCH_MAX_JOBS] or any job that bd_match would
+ * refuse (nothing is enqueued then). */
+bd_status bd_match_batch(bd_ctx *ctx, const bd_match_job *jobs, int n_jobs);
+
+/* ------------------------------------------------------------------------ */
 /* Mutual nearest neighbours                                                 */
 
 /* Hamming mutual-nearest-neighbour matching, the matching step of the

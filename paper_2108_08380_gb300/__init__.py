@@ -82,6 +82,7 @@ _SIGS = [
     ("bd_train_forward", _I, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     ("bd_train_backward", _I, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     ("bd_bad_describe_noalloc", _I, [_P, _P, _I, _I, _I, _P, _I, _P, _P]),
+    ("bd_match_batch", _I, [_P, _P, _I]),
     ("bd_match_mnn", _I, [_P, _P, _I, _P, _I, _I, _I, _I, _I, _P, _P]),
     ("bd_probe", _I, [_P, _I, _P, ctypes.c_size_t, ctypes.c_size_t, _I, _P,
                       ctypes.POINTER(ctypes.c_uint64)]),
@@ -329,6 +330,24 @@ class Context:
         return out
 
 
+    def match_batch(self, jobs, ratio_num: int = 4, ratio_den: int = 5, outs=None):
+        """bd_match_batch: jobs = [(q, t, nbits), ...] (at most 8); returns the
+        records tensors, one per job, as match() returns them."""
+        torch = self._torch
+        n = len(jobs)
+        arr = (MatchJob * max(n, 1))()
+        res = []
+        for k, (q, t, nbits) in enumerate(jobs):
+            out = outs[k] if outs is not None else torch.empty((q.shape[0], 3), dtype=torch.int32,
+                                                              device=q.device)
+            res.append(out)
+            arr[k] = MatchJob(q.data_ptr(), t.data_ptr(), out.data_ptr(), q.shape[0], t.shape[0],
+                              nbits, ratio_num, ratio_den)
+        self._stream()
+        self._check(lib().bd_match_batch(self.handle, ctypes.cast(arr, ctypes.c_void_p), n),
+                    "bd_match_batch")
+        return res
+
     def match_mnn(self, q, t, nbits: int, ratio_num: int = 4, ratio_den: int = 5,
                   tensor_cores: bool = False, out=None, mnn=None):
         """Mutual nearest neighbours: (records as match() returns them,
@@ -357,6 +376,13 @@ class Context:
         self._check(lib().bd_probe(self.handle, kind, _ptr(table), tw, window_words, reps,
                                    _ptr(sink), ctypes.byref(units)), "bd_probe")
         return int(units.value)
+
+
+class MatchJob(ctypes.Structure):
+    """bd_match_job."""
+    _fields_ = [("q", ctypes.c_void_p), ("t", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("nq", ctypes.c_int), ("nt", ctypes.c_int), ("nbits", ctypes.c_int),
+                ("ratio_num", ctypes.c_int), ("ratio_den", ctypes.c_int)]
 
 
 class BatchConfig(ctypes.Structure):

@@ -39,7 +39,7 @@ struct BatchKernelArgs {
     int hs_items;            // ceil(n_kp / 4) if HashSIFT is on, else 0
     int hs_first;
     uint32_t *ii, *carry;
-    unsigned int *work, *stats_done, *final_done;
+    unsigned int *work, *exit_count, *stats_done, *final_done;
     dev::BadTables bad;
     int bad_nw;
     uint32_t *bad_out;
@@ -114,6 +114,11 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
     __shared__ unsigned int item_s;
     __shared__ int flag_s;
     const int t = threadIdx.x;
+    // launched with programmatic serialization: wait for the previous kernel
+    // (which may still read this launch's outputs), then let the next one
+    // (the projection) get scheduled as SMs free up
+    dev::griddep_wait();
+    dev::griddep_launch_dependents();
 
     // item ranges
     const int e_stats = A.n_tiles;
@@ -183,6 +188,23 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
             __syncthreads();
         }
     }
+    // The last CTA out resets the queue and readiness counters for the next
+    // launch: every other CTA has fetched its last item and finished its work.
+    if (t == 0) {
+        __threadfence();
+        flag_s = atomicAdd(A.exit_count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (flag_s) {
+        if (t == 0) {
+            *A.work = 0u;
+            *A.exit_count = 0u;
+        }
+        for (int i = t; i < A.n_img; i += blockDim.x) {
+            A.stats_done[i] = 0u;
+            A.final_done[i] = 0u;
+        }
+    }
 }
 
 }  // namespace
@@ -203,7 +225,7 @@ struct bd_batch {
     const uint8_t **d_ptrs = nullptr;
     std::vector<const uint8_t *> last_ptrs;
     uint32_t *d_ii = nullptr, *d_carry = nullptr;
-    unsigned int *d_counters = nullptr;  // [work][stats_done n_img][final_done n_img]
+    unsigned int *d_counters = nullptr;  // [work][exit][stats_done n_img][final_done n_img], zero between launches
     float *d_hist = nullptr;
     __nv_bfloat16 *d_hist16 = nullptr;
     CUtensorMap tm_hi, tm_lo;
@@ -223,10 +245,7 @@ namespace {
 bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_t *bad_out,
                        uint32_t *hs_out, cudaStream_t st, int *kernels)
 {
-    const size_t cbytes = sizeof(unsigned int) * (1 + 2 * (size_t)b->n_img);
-    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, cbytes, st);
-    if (e != cudaSuccess)
-        return cuda_err(ctx, e, "bd_describe_batch: counter reset");
+    cudaError_t e;
     BatchKernelArgs A;
     memset(&A, 0, sizeof(A));
     A.imgs = b->d_imgs;
@@ -241,8 +260,9 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     A.ii = b->d_ii;
     A.carry = b->d_carry;
     A.work = b->d_counters;
-    A.stats_done = b->d_counters + 1;
-    A.final_done = b->d_counters + 1 + b->n_img;
+    A.exit_count = b->d_counters + 1;
+    A.stats_done = b->d_counters + 2;
+    A.final_done = b->d_counters + 2 + b->n_img;
     if (b->bad)
         A.bad = dev::bad_tables(b->bad);
     A.bad_nw = b->bad ? b->bad->nbits / 32 : 8;
@@ -257,17 +277,14 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
         per_sm = b->max_ctas_per_sm;
     const int grid = per_sm * ctx->sm_count;
     const bool wide = per_sm > b->occ4;  // needs the 80-register variant to be resident
-    if (A.bad_nw == 16) {
-        if (wide)
-            batch_persistent_kernel<16, 6><<<grid, 128, 0, st>>>(A);
-        else
-            batch_persistent_kernel<16, 4><<<grid, 128, 0, st>>>(A);
-    } else {
-        if (wide)
-            batch_persistent_kernel<8, 6><<<grid, 128, 0, st>>>(A);
-        else
-            batch_persistent_kernel<8, 4><<<grid, 128, 0, st>>>(A);
-    }
+    if (A.bad_nw == 16)
+        e = launch_pdl(wide ? batch_persistent_kernel<16, 6> : batch_persistent_kernel<16, 4>,
+                       dim3(grid), dim3(128), 0, st, A);
+    else
+        e = launch_pdl(wide ? batch_persistent_kernel<8, 6> : batch_persistent_kernel<8, 4>,
+                       dim3(grid), dim3(128), 0, st, A);
+    if (e != cudaSuccess)
+        return cuda_err(ctx, e, "bd_describe_batch: persistent kernel");
     trace_kernel(st, "batch_persistent");
     note_launches(1);
     int nk = 1;
@@ -385,7 +402,8 @@ bd_status bd_batch_create(bd_ctx *ctx, const bd_bad_params *bad, const bd_hs_par
         if (e == cudaSuccess) e = cudaMalloc(&b->d_ptrs, sizeof(void *) * n_img);
         if (e == cudaSuccess && bad) e = cudaMalloc(&b->d_ii, sizeof(uint32_t) * ii_total);
         if (e == cudaSuccess && bad) e = cudaMalloc(&b->d_carry, sizeof(uint32_t) * carry_total);
-        if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(unsigned int) * (1 + 2 * (size_t)n_img));
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(unsigned int) * (2 + 2 * (size_t)n_img));
+        if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, sizeof(unsigned int) * (2 + 2 * (size_t)n_img));
         if (e == cudaSuccess && hs) e = cudaMalloc(&b->d_hist, sizeof(float) * kHistDim * (size_t)(b->n_kp > 0 ? b->n_kp : 1));
         if (e == cudaSuccess && hs) e = cudaMalloc(&b->d_hist16, sizeof(__nv_bfloat16) * 2 * kHistDim * (size_t)(b->n_kp > 0 ? b->n_kp : 1));
         if (e == cudaSuccess) e = cudaMemcpy(b->d_imgs, b->imgs.data(), sizeof(BatchImageDev) * n_img, cudaMemcpyHostToDevice);

@@ -191,6 +191,11 @@ cudaError_t launch_probe(int kind, const uint32_t *table, size_t table_words, si
                          int reps, uint32_t *sink, int sm_count, cudaStream_t st,
                          unsigned long long *units, bool *bad_args);
 
+// several POPC matchings in one launch (bd_match_batch); jobs already validated
+size_t match_batch_scratch_bytes(const bd_match_job *jobs, int n, int sm_count);
+int match_batch_query_blocks(const bd_match_job *jobs, int n);
+cudaError_t launch_match_batch(const bd_match_job *jobs, int n, void *scratch, int sm_count,
+                               cudaStream_t st, unsigned int *arrivals);
 // mnn[i] = fwd[i].idx if rev[fwd[i].idx].idx == i, else -1 (rev: nearest queries of t)
 cudaError_t launch_mnn_cross(const bd_match_result *fwd, const bd_match_result *rev, int nq,
                              int32_t *mnn, cudaStream_t st);
@@ -207,8 +212,45 @@ cudaError_t launch_match(const uint32_t *q, int nq, const uint32_t *t, int nt, i
 // device-side PTX helpers (sm_100 family: mbarrier, TMA, tcgen05)
 // ---------------------------------------------------------------------------
 #ifdef __CUDACC__
+#include <utility>
+
+namespace bd {
+
+// Programmatic dependent launch: the kernel may be scheduled while the
+// previous kernel of the stream is still running (its launch and prologue
+// overlap that kernel's tail).  Such a kernel calls dev::griddep_wait()
+// before it touches global memory that earlier work reads or writes; the
+// wait returns once the previous grid has completed and its writes are
+// visible, so stream order is kept.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args &&...args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+}  // namespace bd
+
 namespace bd {
 namespace dev {
+
+// griddepcontrol (sm_90+): wait for the previous grid of the stream to
+// complete and its memory to be visible; allow the next grid to launch.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {

@@ -849,6 +849,32 @@ bd_status bd_match(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, in
     return BD_OK;
 }
 
+bd_status bd_match_batch(bd_ctx *ctx, const bd_match_job *jobs, int n_jobs)
+{
+    BD_GUARD(ctx);
+    if (n_jobs < 0 || n_jobs > BD_MATCH_MAX_JOBS || (n_jobs > 0 && !jobs))
+        return set_err(ctx, BD_ERR_INVALID, "bd_match_batch: bad job count");
+    for (int k = 0; k < n_jobs; ++k) {
+        const bd_match_job &a = jobs[k];
+        if (((uintptr_t)a.q & 15) || ((uintptr_t)a.t & 15) || ((uintptr_t)a.out & 3) ||
+            (a.nbits != 256 && a.nbits != 512) || a.nq < 0 || a.nt < 0 ||
+            a.nt > (int)kMatchIdxMask || a.ratio_den <= 0 || a.ratio_num <= 0 ||
+            a.ratio_num > a.ratio_den || (a.nq > 0 && (!a.q || !a.out)) || (a.nt > 0 && !a.t))
+            return set_err(ctx, BD_ERR_INVALID, "bd_match_batch: job %d has bad arguments", k);
+    }
+    bd_status s = ensure_scratch(ctx, match_batch_scratch_bytes(jobs, n_jobs, ctx->sm_count));
+    if (s == BD_OK)
+        s = ensure_arrivals(ctx, match_batch_query_blocks(jobs, n_jobs));
+    if (s != BD_OK)
+        return s;
+    TraceScope scope(ctx, ctx->stream);
+    BD_LAUNCH(ctx,
+              launch_match_batch(jobs, n_jobs, ctx->scratch, ctx->sm_count, ctx->stream,
+                                 ctx->arrivals),
+              "batched matching kernel");
+    return BD_OK;
+}
+
 bd_status bd_match_mnn(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt,
                        int nbits, int ratio_num, int ratio_den, int tensor_cores,
                        bd_match_result *out, int32_t *mnn)

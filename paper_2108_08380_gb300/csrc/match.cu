@@ -9,6 +9,8 @@
 // neighbour and the second key's distance is d2.  When the train set is split
 // across CTAs, each CTA publishes its per-slice top-2 pairs and the last CTA of
 // a query block (per-block arrival counter, reset by that CTA) merges them.
+#include <string.h>
+
 #include "bd_internal.h"
 
 namespace bd {
@@ -35,18 +37,21 @@ __device__ __forceinline__ void finalize(uint32_t k1, uint32_t k2, int nbits, in
     w[2] = acc;
 }
 
+// One CTA of the matching: queries [bx*QB, bx*QB + QB) against train slice by
+// of S (chunk entries each); with S > 1 the last CTA of the query block merges.
 template <int NW>
-__global__ void __launch_bounds__(QB, 8) match_top2_kernel(const uint32_t *__restrict__ q, int nq,
-                                                        const uint32_t *__restrict__ t, int nt,
-                                                        int chunk, int nbits, int rnum, int rden,
-                                                        uint2 *__restrict__ partial,
-                                                        bd_match_result *__restrict__ out,
-                                                        unsigned int *__restrict__ arrivals)
+__device__ __forceinline__ void match_cta(uint4 *tile, const uint32_t *__restrict__ q, int nq,
+                                          const uint32_t *__restrict__ t, int nt, int chunk,
+                                          int nbits, int rnum, int rden, int bx, int by, int S,
+                                          uint2 *__restrict__ partial,
+                                          bd_match_result *__restrict__ out,
+                                          unsigned int *__restrict__ arrivals, int &last_cta)
 {
-    __shared__ int last_cta;
-    __shared__ uint4 tile[TT * NW / 4];
-    const int qi = blockIdx.x * QB + threadIdx.x;
-    const int t0 = blockIdx.y * chunk;
+    // programmatic launch: wait for the kernel that wrote the descriptors
+    dev::griddep_wait();
+    dev::griddep_launch_dependents();
+    const int qi = bx * QB + threadIdx.x;
+    const int t0 = by * chunk;
     const int t1 = min(nt, t0 + chunk);
 
     uint32_t qd[NW];
@@ -87,33 +92,80 @@ __global__ void __launch_bounds__(QB, 8) match_top2_kernel(const uint32_t *__res
             top2_push((d << kMatchIdxBits) | (uint32_t)(base + j), k1, k2);
         }
     }
-    if (gridDim.y == 1) {
+    if (S == 1) {
         if (qi < nq)
             finalize(k1, k2, nbits, rnum, rden, out + qi);
         return;
     }
     if (qi < nq)
-        partial[(size_t)blockIdx.y * nq + qi] = make_uint2(k1, k2);
+        partial[(size_t)by * nq + qi] = make_uint2(k1, k2);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned int prev = atomicAdd(arrivals + blockIdx.x, 1u);
-        last_cta = prev == gridDim.y - 1;
+        const unsigned int prev = atomicAdd(arrivals + bx, 1u);
+        last_cta = prev == (unsigned)S - 1;
         if (last_cta)
-            arrivals[blockIdx.x] = 0u;  // every slice has arrived: ready for the next call
+            arrivals[bx] = 0u;  // every slice has arrived: ready for the next call
     }
     __syncthreads();
     if (!last_cta || qi >= nq)
         return;
     __threadfence();
     uint2 a = __ldcg(partial + qi);
-    for (int s = 1; s < (int)gridDim.y; ++s) {
+    for (int s = 1; s < S; ++s) {
         const uint2 b = __ldcg(partial + (size_t)s * nq + qi);
         const uint32_t m1 = min(a.x, b.x);
         const uint32_t m2 = min(max(a.x, b.x), min(a.y, b.y));
         a = make_uint2(m1, m2);
     }
     finalize(a.x, a.y, nbits, rnum, rden, out + qi);
+}
+
+template <int NW>
+__global__ void __launch_bounds__(QB, NW == 16 ? 6 : 8) match_top2_kernel(const uint32_t *__restrict__ q, int nq,
+                                                        const uint32_t *__restrict__ t, int nt,
+                                                        int chunk, int nbits, int rnum, int rden,
+                                                        uint2 *__restrict__ partial,
+                                                        bd_match_result *__restrict__ out,
+                                                        unsigned int *__restrict__ arrivals)
+{
+    __shared__ int last_cta;
+    __shared__ uint4 tile[TT * NW / 4];
+    match_cta<NW>(tile, q, nq, t, nt, chunk, nbits, rnum, rden, blockIdx.x, blockIdx.y,
+                  (int)gridDim.y, partial, out, arrivals, last_cta);
+}
+
+// Several matchings in one launch: job j owns CTAs [begin_j, begin_j +
+// qblocks_j * S_j) of a 1-D grid.
+struct MatchJobDev {
+    const uint32_t *q, *t;
+    bd_match_result *out;
+    uint2 *partial;
+    unsigned int *arrivals;
+    int nq, nt, nbits, rnum, rden, S, chunk, qblocks, begin;
+};
+
+struct MatchJobsDev {
+    int n;
+    MatchJobDev j[BD_MATCH_MAX_JOBS];
+};
+
+__global__ void __launch_bounds__(QB, 6) match_multi_kernel(const __grid_constant__ MatchJobsDev J)
+{
+    __shared__ int last_cta;
+    __shared__ uint4 tile[TT * 16 / 4];
+    int k = 0;
+    while (k + 1 < J.n && (int)blockIdx.x >= J.j[k + 1].begin)
+        ++k;
+    const MatchJobDev &b = J.j[k];
+    const int local = (int)blockIdx.x - b.begin;
+    const int bx = local % b.qblocks, by = local / b.qblocks;
+    if (b.nbits == 256)
+        match_cta<8>(tile, b.q, b.nq, b.t, b.nt, b.chunk, b.nbits, b.rnum, b.rden, bx, by, b.S,
+                     b.partial, b.out, b.arrivals, last_cta);
+    else
+        match_cta<16>(tile, b.q, b.nq, b.t, b.nt, b.chunk, b.nbits, b.rnum, b.rden, bx, by, b.S,
+                      b.partial, b.out, b.arrivals, last_cta);
 }
 
 void plan(int nq, int nt, int sm_count, int &S, int &chunk)
@@ -154,13 +206,70 @@ cudaError_t launch_match(const uint32_t *q, int nq, const uint32_t *t, int nt, i
     plan(nq, nt, sm_count, S, chunk);
     dim3 grid((nq + QB - 1) / QB, S);
     uint2 *partial = (uint2 *)scratch;
-    if (nbits == 256)
-        match_top2_kernel<8><<<grid, QB, 0, st>>>(q, nq, t, nt, chunk, nbits, ratio_num, ratio_den,
-                                                  partial, out, arrivals);
-    else
-        match_top2_kernel<16><<<grid, QB, 0, st>>>(q, nq, t, nt, chunk, nbits, ratio_num,
-                                                   ratio_den, partial, out, arrivals);
+    cudaError_t e = launch_pdl(nbits == 256 ? match_top2_kernel<8> : match_top2_kernel<16>, grid,
+                               dim3(QB), 0, st, q, nq, t, nt, chunk, nbits, ratio_num, ratio_den,
+                               partial, out, arrivals);
+    if (e != cudaSuccess)
+        return e;
     trace_kernel(st, "match_top2");
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+size_t match_batch_scratch_bytes(const bd_match_job *jobs, int n, int sm_count)
+{
+    size_t tot = 0;
+    for (int k = 0; k < n; ++k)
+        if (jobs[k].nq > 0)
+            tot += match_scratch_bytes(jobs[k].nq, jobs[k].nt, jobs[k].nbits, sm_count);
+    return tot;
+}
+
+int match_batch_query_blocks(const bd_match_job *jobs, int n)
+{
+    int tot = 0;
+    for (int k = 0; k < n; ++k)
+        tot += match_query_blocks(jobs[k].nq);
+    return tot;
+}
+
+cudaError_t launch_match_batch(const bd_match_job *jobs, int n, void *scratch, int sm_count,
+                               cudaStream_t st, unsigned int *arrivals)
+{
+    MatchJobsDev J;
+    memset(&J, 0, sizeof(J));
+    int blocks = 0, m = 0;
+    char *sc = (char *)scratch;
+    unsigned int *arr = arrivals;
+    for (int k = 0; k < n; ++k) {
+        const bd_match_job &a = jobs[k];
+        if (a.nq <= 0)
+            continue;
+        MatchJobDev &b = J.j[m++];
+        b.q = a.q;
+        b.t = a.t;
+        b.out = a.out;
+        b.nq = a.nq;
+        b.nt = a.nt;
+        b.nbits = a.nbits;
+        b.rnum = a.ratio_num;
+        b.rden = a.ratio_den;
+        plan(a.nq, a.nt, sm_count, b.S, b.chunk);
+        b.qblocks = match_query_blocks(a.nq);
+        b.begin = blocks;
+        b.partial = (uint2 *)sc;
+        b.arrivals = arr;
+        sc += match_scratch_bytes(a.nq, a.nt, a.nbits, sm_count);
+        arr += b.qblocks;
+        blocks += b.qblocks * b.S;
+    }
+    J.n = m;
+    if (m == 0)
+        return cudaSuccess;
+    cudaError_t e = launch_pdl(match_multi_kernel, dim3(blocks), dim3(QB), 0, st, J);
+    if (e != cudaSuccess)
+        return e;
+    trace_kernel(st, "match_multi");
     note_launches(1);
     return cudaGetLastError();
 }

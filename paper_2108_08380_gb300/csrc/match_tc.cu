@@ -45,13 +45,20 @@ __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatil
     return true;
 }
 
-// Packed bits -> one byte per bit: +1.0 (E4M3 0x38) for a set bit, -1.0 (0xB8) otherwise.
-__global__ void expand_pm1_kernel(const uint32_t *__restrict__ bits, size_t words,
-                                  uint4 *__restrict__ out)
+// Packed bits -> one byte per bit: +1.0 (E4M3 0x38) for a set bit, -1.0 (0xB8)
+// otherwise; the query words [0, qwords) then the train words, in one launch.
+__global__ void expand_pm1_kernel(const uint32_t *__restrict__ qbits, size_t qwords,
+                                  uint4 *__restrict__ qout, const uint32_t *__restrict__ tbits,
+                                  size_t twords, uint4 *__restrict__ tout)
 {
-    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < words;
-         w += (size_t)gridDim.x * blockDim.x) {
-        const uint32_t v = __ldg(bits + w);
+    dev::griddep_wait();  // programmatic launch: the descriptors come from the previous kernel
+    dev::griddep_launch_dependents();
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < qwords + twords;
+         g += (size_t)gridDim.x * blockDim.x) {
+        const bool isq = g < qwords;
+        const size_t w = isq ? g : g - qwords;
+        uint4 *out = isq ? qout : tout;
+        const uint32_t v = __ldg((isq ? qbits : tbits) + w);
         uint32_t o[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -130,6 +137,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) match_tc_kernel(
         dev::fence_mbar_init();
         abort_flag = 0;
     }
+    // programmatic launch: the codes were written by the previous kernel
+    dev::griddep_wait();
+    dev::griddep_launch_dependents();
     if (warp == 0)
         dev::tmem_alloc(&tmem_slot, 2 * BN);
     dev::tc_fence_before();
@@ -352,11 +362,13 @@ cudaError_t launch_match_tc_keys(bd_ctx *ctx, const uint32_t *q, int nq, const u
     uint8_t *tx = qx + align_up((size_t)nq * nbits, 256);
     uint2 *partial = (uint2 *)(tx + align_up((size_t)(nt > 0 ? nt : 1) * nbits, 256));
     const size_t qw = (size_t)nq * (nbits / 32), tw = (size_t)nt * (nbits / 32);
-    expand_pm1_kernel<<<(int)((qw + 255) / 256 < 4096 ? (qw + 255) / 256 : 4096), 256, 0, st>>>(
-        q, qw, reinterpret_cast<uint4 *>(qx));
-    if (nt > 0)
-        expand_pm1_kernel<<<(int)((tw + 255) / 256 < 4096 ? (tw + 255) / 256 : 4096), 256, 0, st>>>(
-            t, tw, reinterpret_cast<uint4 *>(tx));
+    const size_t ew = qw + tw;
+    cudaError_t e = launch_pdl(expand_pm1_kernel,
+                               dim3((unsigned)((ew + 255) / 256 < 4096 ? (ew + 255) / 256 : 4096)),
+                               dim3(256), 0, st, q, qw, reinterpret_cast<uint4 *>(qx),
+                               nt > 0 ? t : q, tw, reinterpret_cast<uint4 *>(tx));
+    if (e != cudaSuccess)
+        return e;
     trace_kernel(st, "expand_pm1");
     CUtensorMap tmQ, tmT;
     if (!encode_tmap_2d_u8(&tmQ, qx, (uint64_t)nbits, (uint64_t)nq, (uint64_t)nbits, 128, 128) ||
@@ -365,26 +377,16 @@ cudaError_t launch_match_tc_keys(bd_ctx *ctx, const uint32_t *q, int nq, const u
         return cudaErrorInvalidValue;
     dim3 grid((nq + BM - 1) / BM, S);
     const size_t smem = (size_t)(BM + 2 * BN) * nbits + 1024;
-    cudaError_t e;
-    if (nbits == 256) {
-        e = cudaFuncSetAttribute(match_tc_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        match_tc_kernel<256><<<grid, NTHREADS, smem, st>>>(tmQ, tmT, nq, nt, per, nbits, ratio_num,
-                                                           ratio_den, partial, out, raw_keys,
-                                                           arrivals, ctx->status);
-    } else {
-        e = cudaFuncSetAttribute(match_tc_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        match_tc_kernel<512><<<grid, NTHREADS, smem, st>>>(tmQ, tmT, nq, nt, per, nbits, ratio_num,
-                                                           ratio_den, partial, out, raw_keys,
-                                                           arrivals, ctx->status);
-    }
+    auto kern = nbits == 256 ? match_tc_kernel<256> : match_tc_kernel<512>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    e = launch_pdl(kern, grid, dim3(NTHREADS), smem, st, tmQ, tmT, nq, nt, per, nbits, ratio_num,
+                   ratio_den, partial, out, raw_keys, arrivals, ctx->status);
+    if (e != cudaSuccess)
+        return e;
     trace_kernel(st, "match_tc");
-    note_launches(nt > 0 ? 3 : 2);
+    note_launches(2);
     return cudaGetLastError();
 }
 

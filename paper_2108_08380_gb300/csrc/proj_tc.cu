@@ -71,6 +71,10 @@ __global__ void __launch_bounds__(NTH) hs_proj_tc_kernel(
         band_s[t] = __ldg(band + n0 + t);
     }
     static_assert(BN <= NTH, "one thread per bias entry");
+    // programmatic launch: the prologue above overlaps the previous kernel
+    // (which writes the histograms read below)
+    dev::griddep_wait();
+    dev::griddep_launch_dependents();
     if (warp == 0)
         dev::tmem_alloc(&tmem_slot, BN);
     dev::tc_fence_before();
@@ -221,9 +225,12 @@ cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const CUtensorMap &tm_hi,
                               DeviceStatus *status, cudaStream_t st, const bd_keypoint *kps)
 {
     dim3 grid(p->nbits / BN, (n + BM - 1) / BM);
-    hs_proj_tc_kernel<<<grid, NTH, SMEM_BYTES, st>>>(tm_hi, tm_lo, p->tmap_w_hi, p->tmap_w_lo,
-                                                     p->w_has_lo ? 1 : 0, hist, p->d_Wt, p->d_bias,
-                                                     p->d_band, kps, n, p->nbits, out, status);
+    cudaError_t e = launch_pdl(hs_proj_tc_kernel, grid, dim3(NTH), SMEM_BYTES, st, tm_hi, tm_lo,
+                               p->tmap_w_hi, p->tmap_w_lo, p->w_has_lo ? 1 : 0, hist,
+                               (const float *)p->d_Wt, (const float *)p->d_bias,
+                               (const float *)p->d_band, kps, n, p->nbits, out, status);
+    if (e != cudaSuccess)
+        return e;
     trace_kernel(st, "hs_proj_tc");
     note_launches(1);
     return cudaGetLastError();

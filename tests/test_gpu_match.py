@@ -168,3 +168,44 @@ def test_mnn_full_size_sampled(gpu_ctx, K, tc):
     assert np.array_equal(mnn[rows], want)
     partners = mnn[mnn >= 0]
     assert len(partners) == len(np.unique(partners))  # a partial one-to-one matching
+
+
+# ---------------------------------------------------------------------------
+# several matchings in one launch (bd_match_batch)
+
+def test_match_batch_mixed_jobs(gpu_ctx):
+    """Jobs of both widths, ragged sizes, an empty train set and an empty
+    query set: every job equals the oracle and the single-job call."""
+    import paper_2108_08380_gb300 as bd
+    rng = np.random.default_rng(77)
+    shapes = [(256, 1000, 1000), (512, 333, 777), (256, 129, 0), (512, 0, 50), (256, 5000, 3),
+              (512, 1, 1), (256, 300, 4099)]
+    jobs, host = [], []
+    for K, nq, nt in shapes:
+        t = _rand_desc(rng, nt, K)
+        q = _rand_desc(rng, nq, K)
+        if nt and nq:
+            q[: nq // 2] = _noisy(rng, t[rng.integers(0, nt, size=nq // 2)], K, K // 8)
+        jobs.append((_dev(q), _dev(t), K))
+        host.append((q, t, K))
+    outs = gpu_ctx.match_batch(jobs)
+    for (q, t, K), out, (dq, dt, _) in zip(host, outs, jobs):
+        if q.shape[0] == 0:
+            continue
+        idx, d1, d2, acc = bd.unpack_matches(out)
+        ri, r1, r2, ra = oracle.match(q, t, K)
+        assert np.array_equal(idx, ri) and np.array_equal(d1, r1)
+        assert np.array_equal(d2, r2) and np.array_equal(acc, ra)
+        single = gpu_ctx.match(dq, dt, K)
+        assert np.array_equal(single.cpu().numpy(), out.cpu().numpy())
+
+
+def test_match_batch_refuses_bad_jobs(gpu_ctx):
+    import paper_2108_08380_gb300 as bd
+    rng = np.random.default_rng(1)
+    q = _dev(_rand_desc(rng, 4, 256))
+    with pytest.raises(bd.BindescError):
+        gpu_ctx.match_batch([(q, q, 256)] * 9)          # more than BD_MATCH_MAX_JOBS
+    with pytest.raises(bd.BindescError):
+        gpu_ctx.match_batch([(q, q, 256), (q, q, 300)])  # second job invalid
+    assert gpu_ctx.match_batch([]) == []
