@@ -664,21 +664,20 @@ def roofline(wl, per_kernel, clocks, probes=None):
         popc = na * nb * words
         peak, src = probe("popc", 152 * 16 * sm_mhz * 1e6, "152 SMs x 16 POPC/clk")
         out.update(bound="alu", achieved=popc / t / 1e12, peak=peak / 1e12, unit="Tpopc/s",
-                   frac=popc / t / peak, traffic=None, peak_source=src)
+                   frac=popc / t / peak, peak_source=src)
     elif kname == "match_tc":
         K = wl.bad_bits if stage == "match_bad" else wl.hs_bits
         flops = 2.0 * na * nb * K
         peak = 2.0 * float(peaks["bf16_tflops"])
         ach = flops / t / 1e12
         out.update(bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
-                   traffic=None,
                    peak_source=f"{kind} bf16 burst x 2 (nominal FP8/BF16 dense ratio)")
     elif kname == "hs_proj_tc":
         flops = 2.0 * 128 * wl.hs_bits * wl.n
         peak = float(peaks["bf16_tflops"])
         ach = flops / t / 1e12
         out.update(bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
-                   traffic=None, peak_source=f"{kind} bf16 burst (MEASURED_PEAKS.json)")
+                   peak_source=f"{kind} bf16 burst (MEASURED_PEAKS.json)")
     else:
         # batch_persistent: integral images (HBM), BAD gathers and histogram
         # arithmetic fused in one launch.  Each part's minimum time at its
@@ -698,10 +697,48 @@ def roofline(wl, per_kernel, clocks, probes=None):
         work, rate, unit, src = parts[bound]
         scale = 1e9 if unit in ("Gload/s", "GB/s") else 1e12
         out.update(bound=bound, achieved=work / t / scale, peak=rate / scale, unit=unit,
-                   frac=work / t / rate, traffic=None, peak_source=src,
+                   frac=work / t / rate, peak_source=src,
                    parts_min_ms={k: v * 1e3 for k, v in tmin.items()},
                    frac_of_parts_sum=sum(tmin.values()) / t)
+    out["traffic"] = ncu_traffic(wl.name, key)
+    out["traffic_unit"] = "bytes per launch (ncu dram read + write, cold caches)"
     return out
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# step's kernels from one ncu --set full capture of the plain and large
+# workloads, summarised in profiles/kernels_*.md.  They hold for the kernel
+# sources whose hash is "sources" only; after any change traffic is null.
+NCU_TRAFFIC = {
+    "sources": "696b8f8327778878",
+    "plain": {"describe_batch/batch_persistent": 806912, "describe_batch/hs_proj_tc": 1795072,
+              "match/match_multi": 147712},
+    "large": {"describe_batch/batch_persistent": 38733568 + 60723200,
+              "describe_batch/hs_proj_tc": 37308672 + 5376,
+              "match_bad/match_tc": 10271232, "match_hashsift/match_tc": 20515072},
+}
+
+
+def kernel_sources_hash() -> str:
+    """sha256 (first 16 hex digits) of the CUDA sources and the C header."""
+    import glob
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2108_08380_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+                   glob.glob(os.path.join(csrc, "*.h")))
+    files.append(os.path.join(ROOT, "include", "bindesc.h"))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(wl_name: str, key: str):
+    if kernel_sources_hash() != NCU_TRAFFIC["sources"]:
+        return None
+    return NCU_TRAFFIC.get(wl_name, {}).get(key)
 
 
 # FP32/SFU operations one patch pixel of the HashSIFT histogram needs:
