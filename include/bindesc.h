@@ -240,12 +240,18 @@ typedef struct bd_batch bd_batch;
  *  bad_kp_per_item  keypoints per BAD work item (multiple of 4, 4..256)
  *  ctas_per_sm      resident CTAs per SM of the persistent grid (0 = the most
  *                   that fit)
- *  hs_first         1: HashSIFT items are queued before the integral pass-2
- *                   tiles and BAD items; 0: after them. */
+ *  hs_first         where the HashSIFT items (which depend on nothing) sit in
+ *                   the queue: 0 after the BAD items, 1 before the integral
+ *                   pass-2 tiles, 2 one grid's worth before the pass-2 tiles,
+ *                   one before the BAD items and the rest after them.
+ *  hs_kp_per_item   HashSIFT keypoints per work item: 1 = the CTA's four warps
+ *                   share each keypoint (lower latency, for few keypoints),
+ *                   4 = one keypoint per warp (higher throughput). */
 typedef struct bd_batch_config {
     int bad_kp_per_item;
     int ctas_per_sm;
     int hs_first;
+    int hs_kp_per_item;
 } bd_batch_config;
 
 /* Plans the description of n_img images with BAD and/or HashSIFT (either

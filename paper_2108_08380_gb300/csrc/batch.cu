@@ -36,8 +36,10 @@ struct BatchKernelArgs {
     const BatchImageDev *imgs;
     const uint8_t *const *img_ptr;
     int n_img, n_tiles, n_kp, n_bad_items, bad_per_item;
-    int hs_items;            // ceil(n_kp / 4) if HashSIFT is on, else 0
+    int hs_items;            // ceil(n_kp / hs_per_item) if HashSIFT is on, else 0
+    int hs_per_item;         // 1: the CTA shares a keypoint; 4: one keypoint per warp
     int hs_first;
+    int hs_pre_final, hs_pre_bad;  // HashSIFT items queued before the pass-2 tiles / the BAD items
     uint32_t *ii, *carry;
     unsigned int *work, *exit_count, *stats_done, *final_done;
     dev::BadTables bad;
@@ -120,13 +122,14 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
     dev::griddep_wait();
     dev::griddep_launch_dependents();
 
-    // item ranges
-    const int e_stats = A.n_tiles;
+    // queue: [pass-1 tiles][HashSIFT a][pass-2 tiles][HashSIFT b][BAD items][HashSIFT rest]
     const int n_hs = A.hs_items;
-    const int b_hs = A.hs_first ? e_stats : e_stats + A.n_tiles + A.n_bad_items;
-    const int b_final = A.hs_first ? e_stats + n_hs : e_stats;
-    const int b_bad = b_final + A.n_tiles;
-    const int total = 2 * A.n_tiles + n_hs + A.n_bad_items;
+    const int e0 = A.n_tiles;
+    const int e1 = e0 + A.hs_pre_final;
+    const int e2 = e1 + A.n_tiles;
+    const int e3 = e2 + A.hs_pre_bad;
+    const int e4 = e3 + A.n_bad_items;
+    const int total = e4 + (n_hs - A.hs_pre_final - A.hs_pre_bad);
 
     for (;;) {
         if (t == 0)
@@ -136,10 +139,31 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
         __syncthreads();
         if (item >= total)
             break;
-        if (item < e_stats) {
-            const int im = find_image(A.imgs, A.n_img, item, 0);
+        // item -> (kind, index): 0 pass-1 tile, 1 HashSIFT, 2 pass-2 tile, 3 BAD
+        int kind, idx;
+        if (item < e0) {
+            kind = 0;
+            idx = item;
+        } else if (item < e1) {
+            kind = 1;
+            idx = item - e0;
+        } else if (item < e2) {
+            kind = 2;
+            idx = item - e1;
+        } else if (item < e3) {
+            kind = 1;
+            idx = A.hs_pre_final + item - e2;
+        } else if (item < e4) {
+            kind = 3;
+            idx = item - e3;
+        } else {
+            kind = 1;
+            idx = A.hs_pre_final + A.hs_pre_bad + item - e4;
+        }
+        if (kind == 0) {
+            const int im = find_image(A.imgs, A.n_img, idx, 0);
             const BatchImageDev &I = A.imgs[im];
-            const int tl = item - I.tile_begin;
+            const int tl = idx - I.tile_begin;
             dev::ii_stats_tile(U.s, A.img_ptr[im], I.w, I.h, I.pitch, A.carry + I.cs_off,
                                A.carry + I.rs_off, A.carry + I.tt_off, I.ntx, tl % I.ntx, tl / I.ntx);
             __syncthreads();
@@ -147,19 +171,29 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                 __threadfence();
                 atomicAdd(A.stats_done + im, 1u);
             }
-        } else if (item >= b_hs && item < b_hs + n_hs) {
-            // four keypoints per item, one per warp
-            const int k = (item - b_hs) * 4 + (t >> 5);
-            if (k < A.n_kp) {
+        } else if (kind == 1) {
+            if (A.hs_per_item == 1) {
+                // one keypoint shared by the CTA's four warps
+                const int k = idx;
                 const int im = find_image(A.imgs, A.n_img, k, 1);
                 const BatchImageDev &I = A.imgs[im];
-                dev::hs_hist_image_warp(U.h[t >> 5], A.img_ptr[im], I.w, I.h, I.pitch, A.kps[k],
-                                        A.spacing, A.hist, A.hist16, (size_t)k, (size_t)A.n_kp,
-                                        A.status);
+                dev::hs_hist_image_cta(U.h[0], A.img_ptr[im], I.w, I.h, I.pitch, A.kps[k],
+                                       A.spacing, A.hist, A.hist16, (size_t)k, (size_t)A.n_kp,
+                                       A.status);
+            } else {
+                // four keypoints, one per warp
+                const int k = idx * 4 + (t >> 5);
+                if (k < A.n_kp) {
+                    const int im = find_image(A.imgs, A.n_img, k, 1);
+                    const BatchImageDev &I = A.imgs[im];
+                    dev::hs_hist_image_warp(U.h[t >> 5], A.img_ptr[im], I.w, I.h, I.pitch,
+                                            A.kps[k], A.spacing, A.hist, A.hist16, (size_t)k,
+                                            (size_t)A.n_kp, A.status);
+                }
             }
             __syncthreads();
-        } else if (item >= b_final && item < b_final + A.n_tiles) {
-            const int tile = item - b_final;
+        } else if (kind == 2) {
+            const int tile = idx;
             const int im = find_image(A.imgs, A.n_img, tile, 0);
             const BatchImageDev &I = A.imgs[im];
             if (cta_wait_count(A.stats_done + im, (unsigned)(I.ntx * I.nty), &flag_s, A.status)) {
@@ -173,8 +207,8 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                 __threadfence();
                 atomicAdd(A.final_done + im, 1u);
             }
-        } else if (item >= b_bad && item < b_bad + A.n_bad_items) {
-            const int bi = item - b_bad;
+        } else {
+            const int bi = idx;
             const int im = find_image(A.imgs, A.n_img, bi, 2);
             const BatchImageDev &I = A.imgs[im];
             if (cta_wait_count(A.final_done + im, (unsigned)(I.ntx * I.nty), &flag_s, A.status)) {
@@ -229,7 +263,7 @@ struct bd_batch {
     float *d_hist = nullptr;
     __nv_bfloat16 *d_hist16 = nullptr;
     CUtensorMap tm_hi, tm_lo;
-    bd_batch_config cfg = {8, 0, 1};
+    bd_batch_config cfg = {8, 0, 1, 4};
     int max_ctas_per_sm = 0;
     int occ4 = 0;  // resident CTAs per SM of the 128-register variant
     // graph replay
@@ -255,7 +289,8 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     A.n_kp = b->n_kp;
     A.bad_per_item = b->cfg.bad_kp_per_item;
     A.n_bad_items = (b->bad && bad_out) ? b->n_bad_items : 0;
-    A.hs_items = (b->hs && hs_out) ? (b->n_kp + 3) / 4 : 0;
+    A.hs_per_item = b->cfg.hs_kp_per_item;
+    A.hs_items = (b->hs && hs_out) ? (b->n_kp + A.hs_per_item - 1) / A.hs_per_item : 0;
     A.hs_first = b->cfg.hs_first;
     A.ii = b->d_ii;
     A.carry = b->d_carry;
@@ -276,6 +311,20 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     if (per_sm > b->max_ctas_per_sm)
         per_sm = b->max_ctas_per_sm;
     const int grid = per_sm * ctx->sm_count;
+    // HashSIFT items (no dependency) fill the waits of the integral / BAD chain:
+    // 0 all after the BAD items, 1 all before the pass-2 tiles, 2 one grid's
+    // worth before the pass-2 tiles and one before the BAD items
+    if (b->cfg.hs_first == 1) {
+        A.hs_pre_final = A.hs_items;
+        A.hs_pre_bad = 0;
+    } else if (b->cfg.hs_first == 2) {
+        A.hs_pre_final = A.hs_items < grid ? A.hs_items : grid;
+        const int rest = A.hs_items - A.hs_pre_final;
+        A.hs_pre_bad = rest < grid ? rest : grid;
+    } else {
+        A.hs_pre_final = 0;
+        A.hs_pre_bad = 0;
+    }
     const bool wide = per_sm > b->occ4;  // needs the 80-register variant to be resident
     if (A.bad_nw == 16)
         e = launch_pdl(wide ? batch_persistent_kernel<16, 6> : batch_persistent_kernel<16, 4>,
@@ -463,7 +512,8 @@ bd_status bd_batch_set_config(bd_batch *b, const bd_batch_config *cfg)
     if (!b || !cfg)
         return BD_ERR_INVALID;
     if (cfg->bad_kp_per_item < 4 || cfg->bad_kp_per_item > 256 || (cfg->bad_kp_per_item & 3) ||
-        cfg->ctas_per_sm < 0 || (cfg->hs_first != 0 && cfg->hs_first != 1))
+        cfg->ctas_per_sm < 0 || cfg->hs_first < 0 || cfg->hs_first > 2 ||
+        (cfg->hs_kp_per_item != 1 && cfg->hs_kp_per_item != 4))
         return set_err(b->ctx, BD_ERR_INVALID, "bd_batch_set_config: bad configuration");
     b->cfg = *cfg;
     int items = 0;
@@ -581,10 +631,12 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     cudaEventCreate(&e1);
     bd_batch_config win = b->cfg;
     float win_ms = 1e30f;
-    for (int hs_first = 0; hs_first < 2; ++hs_first) {
+    const int hs_modes[] = {1, 4};
+    for (int hm : hs_modes) {
+    for (int hs_first = 0; hs_first < 3; ++hs_first) {
         for (int it : items) {
             for (int c : per_sm) {
-                bd_batch_config cfg = {it, c, hs_first};
+                bd_batch_config cfg = {it, c, hs_first, hm};
                 bd_status s = bd_batch_set_config(b, &cfg);
                 if (s == BD_OK)
                     s = bd_describe_batch(ctx, b, imgs, kps, bad_out, hs_out, 0);  // warm-up
@@ -607,6 +659,7 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
                 }
             }
         }
+    }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

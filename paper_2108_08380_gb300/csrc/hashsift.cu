@@ -12,17 +12,26 @@ namespace {
 using dev::NT;
 using dev::PS;
 
-// One warp per keypoint (hs_hist_warp); the CTA's warps take independent keypoints.
+// Coop = false: one warp per keypoint (hs_hist_warp), the CTA's warps take
+// independent keypoints; Coop = true: the CTA's four warps share each
+// keypoint (hs_hist_cta), for few keypoints.
+template <bool Coop>
 __global__ void __launch_bounds__(NT) hs_hist_image_kernel(
     const uint8_t *__restrict__ img, int w, int h, int pitch, const bd_keypoint *__restrict__ kps,
     int n, float spacing, float *__restrict__ hist, __nv_bfloat16 *__restrict__ hist16,
     DeviceStatus *status)
 {
-    __shared__ dev::WarpHist S[NT / 32];
-    const int warp = threadIdx.x >> 5;
-    for (int k = blockIdx.x * (NT / 32) + warp; k < n; k += gridDim.x * (NT / 32))
-        dev::hs_hist_image_warp(S[warp], img, w, h, pitch, kps[k], spacing, hist, hist16,
-                                (size_t)k, (size_t)n, status);
+    __shared__ dev::WarpHist S[Coop ? 1 : NT / 32];
+    if (Coop) {
+        for (int k = blockIdx.x; k < n; k += gridDim.x)
+            dev::hs_hist_image_cta(S[0], img, w, h, pitch, kps[k], spacing, hist, hist16,
+                                   (size_t)k, (size_t)n, status);
+    } else {
+        const int warp = threadIdx.x >> 5;
+        for (int k = blockIdx.x * (NT / 32) + warp; k < n; k += gridDim.x * (NT / 32))
+            dev::hs_hist_image_warp(S[warp], img, w, h, pitch, kps[k], spacing, hist, hist16,
+                                    (size_t)k, (size_t)n, status);
+    }
 }
 
 __global__ void __launch_bounds__(NT) hs_hist_patch_kernel(const float *__restrict__ patches,
@@ -211,9 +220,13 @@ cudaError_t launch_hs_hist_image(const bd_hs_params *p, const uint8_t *img, int 
                                  __nv_bfloat16 *hist16, DeviceStatus *status, cudaStream_t st,
                                  int sm_count)
 {
-    hs_hist_image_kernel<<<grid_for((n + 3) / 4, sm_count, 12), NT, 0, st>>>(img, w, h, pitch, kps, n,
-                                                                   p->spacing, hist, hist16,
-                                                                   status);
+    // few keypoints: the CTA shares each one (latency); many: one per warp (throughput)
+    if (n <= 2 * 12 * sm_count)
+        hs_hist_image_kernel<true><<<grid_for(n, sm_count, 12), NT, 0, st>>>(
+            img, w, h, pitch, kps, n, p->spacing, hist, hist16, status);
+    else
+        hs_hist_image_kernel<false><<<grid_for((n + 3) / 4, sm_count, 12), NT, 0, st>>>(
+            img, w, h, pitch, kps, n, p->spacing, hist, hist16, status);
     trace_kernel(st, "hs_hist_image");
     note_launches(1);
     return cudaGetLastError();

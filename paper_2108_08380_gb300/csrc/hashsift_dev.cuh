@@ -296,6 +296,7 @@ constexpr int kPRow = 40;  // padded patch row: bank (8 i + j) % 32 is distinct 
 struct WarpHist {
     float P[PS][kPRow];    // patch samples [row][column]
     float priv[4][8][32];  // [cell row][bin][lane]
+    float wss[4];          // per-warp sums of squares (cooperative mode)
 };
 
 // Gaussian weight exp(-(d^2) / 512) of row / column index i (sigma = 16 about
@@ -402,6 +403,97 @@ __device__ __forceinline__ void hs_hist_warp(WarpHist &S, const Src &src, bool v
         }
     }
     __syncwarp();
+}
+
+// The same histogram by the four warps of a 128-thread CTA sharing one
+// keypoint (lower latency when keypoints are few): warp w samples and votes
+// rows [8w, 8w + 8), i.e. cell row w, and normalises its 32 entries with the
+// CTA's sum of squares.  All 128 threads call it; S is the CTA's buffer.
+template <class Src>
+__device__ __forceinline__ void hs_hist_cta(WarpHist &S, const Src &src, bool valid,
+                                            float *__restrict__ hist,
+                                            __nv_bfloat16 *__restrict__ hist16, size_t k,
+                                            size_t n, float *__restrict__ norm_out)
+{
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    {
+        float4 *z = reinterpret_cast<float4 *>(&S.priv[w][0][0]);
+        z[lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        z[lane + 32] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    if (valid) {
+        const int bi = lane >> 3, bj = lane & 7;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {  // blocks 8w .. 8w + 7: rows 8w .. 8w + 7
+            const int bb = 8 * w + q;
+            const int i = 4 * (bb >> 2) + bi, j = 8 * (bb & 3) + bj;
+            S.P[i][j] = src.at(i, j);
+        }
+    }
+    __syncthreads();
+    if (valid) {
+        const float g_half = 0.5f * gauss16(lane);
+        float up = S.P[w > 0 ? 8 * w - 1 : 0][lane];
+        float here = S.P[8 * w][lane];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int i = 8 * w + r;
+            const float down = S.P[i < PS - 1 ? i + 1 : PS - 1][lane];
+            vote_px(S, lane, i, up, here, down, g_half);
+            up = here;
+            here = down;
+        }
+    }
+    __syncwarp();
+    const int cj = lane >> 3, b = lane & 7;
+    float H = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        H += S.priv[w][b][cj * 8 + ((q + b) & 7)];
+    float ss = H * H;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        ss += __shfl_xor_sync(kFull, ss, o);
+    if (lane == 0)
+        S.wss[w] = ss;
+    __syncthreads();
+    const float nrm = sqrtf(S.wss[0] + S.wss[1] + S.wss[2] + S.wss[3]);
+    if (norm_out && t == 0)
+        norm_out[k] = valid ? nrm : 0.0f;
+    const float hv = (valid && nrm > 0.0f) ? H / nrm : 0.0f;
+    const size_t e = k * kHistDim + w * 32 + lane;
+    hist[e] = hv;
+    if (hist16) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(hv);
+        hist16[e] = hi;
+        hist16[n * kHistDim + e] = __float2bfloat16_rn(hv - __bfloat162float(hi));
+    }
+    __syncthreads();  // S is reused by the next keypoint
+}
+
+// Histogram of keypoint k of n sampled from the image by the whole CTA.
+__device__ __forceinline__ void hs_hist_image_cta(WarpHist &S, const uint8_t *img, int w, int h,
+                                                  int pitch, const bd_keypoint &kp, float spacing,
+                                                  float *hist, __nv_bfloat16 *hist16, size_t k,
+                                                  size_t n, DeviceStatus *status)
+{
+    const bool valid = kp_valid(kp);
+    ColSampler<false> edge;
+    if (!valid) {
+        if (threadIdx.x == 0)
+            raise_flag(status, BD_FLAG_INVALID_KEYPOINT);
+        hs_hist_cta(S, edge, false, hist, hist16, k, n, nullptr);
+        return;
+    }
+    const Frame f = make_frame(kp, spacing);
+    if (col_interior(f, w, h)) {
+        ColSampler<true> in;
+        in.c = col_frame(img, w, h, pitch, f);
+        hs_hist_cta(S, in, true, hist, hist16, k, n, nullptr);
+    } else {
+        edge.c = col_frame(img, w, h, pitch, f);
+        hs_hist_cta(S, edge, true, hist, hist16, k, n, nullptr);
+    }
 }
 
 // Histogram of keypoint k of n sampled from the image; all 32 lanes call it.
