@@ -47,7 +47,6 @@ struct BatchKernelArgs {
     uint32_t *bad_out;
     float spacing;
     float *hist;
-    __nv_bfloat16 *hist16;
     const bd_keypoint *kps;
     DeviceStatus *status;
 };
@@ -178,8 +177,7 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                 const int im = find_image(A.imgs, A.n_img, k, 1);
                 const BatchImageDev &I = A.imgs[im];
                 dev::hs_hist_image_cta(U.h[0], A.img_ptr[im], I.w, I.h, I.pitch, A.kps[k],
-                                       A.spacing, A.hist, A.hist16, (size_t)k, (size_t)A.n_kp,
-                                       A.status);
+                                       A.spacing, A.hist, (size_t)k, A.status);
             } else {
                 // four keypoints, one per warp
                 const int k = idx * 4 + (t >> 5);
@@ -187,8 +185,7 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                     const int im = find_image(A.imgs, A.n_img, k, 1);
                     const BatchImageDev &I = A.imgs[im];
                     dev::hs_hist_image_warp(U.h[t >> 5], A.img_ptr[im], I.w, I.h, I.pitch,
-                                            A.kps[k], A.spacing, A.hist, A.hist16, (size_t)k,
-                                            (size_t)A.n_kp, A.status);
+                                            A.kps[k], A.spacing, A.hist, (size_t)k, A.status);
                 }
             }
             __syncthreads();
@@ -261,8 +258,6 @@ struct bd_batch {
     uint32_t *d_ii = nullptr, *d_carry = nullptr;
     unsigned int *d_counters = nullptr;  // [work][exit][stats_done n_img][final_done n_img], zero between launches
     float *d_hist = nullptr;
-    __nv_bfloat16 *d_hist16 = nullptr;
-    CUtensorMap tm_hi, tm_lo;
     bd_batch_config cfg = {8, 0, 1, 4};
     int max_ctas_per_sm = 0;
     int occ4 = 0;  // resident CTAs per SM of the 128-register variant
@@ -304,7 +299,6 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     A.bad_out = bad_out;
     A.spacing = b->hs ? b->hs->spacing : 1.f;
     A.hist = b->d_hist;
-    A.hist16 = (b->hs && b->hs->precision == BD_HS_BF16_RESCUE) ? b->d_hist16 : nullptr;
     A.kps = kps;
     A.status = ctx->status;
     int per_sm = b->cfg.ctas_per_sm > 0 ? b->cfg.ctas_per_sm : b->max_ctas_per_sm;
@@ -345,7 +339,7 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
         if (p->precision == BD_HS_FP32)
             e = launch_hs_proj_fp32(p, b->d_hist, b->n_kp, hs_out, st, kps);
         else
-            e = launch_hs_proj_tc(p, b->tm_hi, b->tm_lo, b->d_hist, b->n_kp, hs_out, ctx->status, st,
+            e = launch_hs_proj_tc(p, b->d_hist, b->n_kp, hs_out, ctx->status, st,
                                   kps);
         ++nk;
         if (e != cudaSuccess)
@@ -454,7 +448,6 @@ bd_status bd_batch_create(bd_ctx *ctx, const bd_bad_params *bad, const bd_hs_par
         if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(unsigned int) * (2 + 2 * (size_t)n_img));
         if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, sizeof(unsigned int) * (2 + 2 * (size_t)n_img));
         if (e == cudaSuccess && hs) e = cudaMalloc(&b->d_hist, sizeof(float) * kHistDim * (size_t)(b->n_kp > 0 ? b->n_kp : 1));
-        if (e == cudaSuccess && hs) e = cudaMalloc(&b->d_hist16, sizeof(__nv_bfloat16) * 2 * kHistDim * (size_t)(b->n_kp > 0 ? b->n_kp : 1));
         if (e == cudaSuccess) e = cudaMemcpy(b->d_imgs, b->imgs.data(), sizeof(BatchImageDev) * n_img, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
         int o[4] = {0, 0, 0, 0};
@@ -471,14 +464,6 @@ bd_status bd_batch_create(bd_ctx *ctx, const bd_bad_params *bad, const bd_hs_par
     if (e != cudaSuccess) {
         bd_batch_destroy(b);
         return cuda_err(ctx, e, "bd_batch_create");
-    }
-    if (hs && hs->precision == BD_HS_BF16_RESCUE && b->n_kp > 0) {
-        if (!encode_tmap_2d_bf16(&b->tm_hi, b->d_hist16, 128, (uint64_t)b->n_kp, 256, 64, 128) ||
-            !encode_tmap_2d_bf16(&b->tm_lo, b->d_hist16 + (size_t)b->n_kp * kHistDim, 128,
-                                 (uint64_t)b->n_kp, 256, 64, 128)) {
-            bd_batch_destroy(b);
-            return set_err(ctx, BD_ERR_CUDA, "bd_batch_create: TMA descriptors");
-        }
     }
     *out = b;
     return BD_OK;
@@ -501,7 +486,6 @@ void bd_batch_destroy(bd_batch *b)
     if (b->d_carry) cudaFree(b->d_carry);
     if (b->d_counters) cudaFree(b->d_counters);
     if (b->d_hist) cudaFree(b->d_hist);
-    if (b->d_hist16) cudaFree(b->d_hist16);
     if (prev >= 0 && prev != b->ctx->device)
         cudaSetDevice(prev);
     delete b;

@@ -153,15 +153,13 @@ cudaError_t launch_bad_gather(const bd_bad_params *p, const uint32_t *ii, int ii
 cudaError_t launch_hs_warp(const bd_hs_params *p, const uint8_t *img, int w, int h, int pitch,
                            const bd_keypoint *kps, int n, float *patches, DeviceStatus *status,
                            cudaStream_t st, int sm_count);
-// hist16 (nullable) receives the BF16 head [n][128] followed by the BF16 tail [n][128]
-cudaError_t launch_hs_hist_patches(const float *patches, int n, float *hist,
-                                   __nv_bfloat16 *hist16, cudaStream_t st, int sm_count,
+cudaError_t launch_hs_hist_patches(const float *patches, int n, float *hist, cudaStream_t st,
+                                   int sm_count,
                                    float *norm_out = nullptr);
 cudaError_t launch_hs_hist_image(const bd_hs_params *p, const uint8_t *img, int w, int h, int pitch,
                                  const bd_keypoint *kps, int n, float *hist,
-                                 __nv_bfloat16 *hist16, DeviceStatus *status, cudaStream_t st,
+                                 DeviceStatus *status, cudaStream_t st,
                                  int sm_count);
-cudaError_t launch_hs_to_bf16(const float *hist, int n, __nv_bfloat16 *hist16, cudaStream_t st);
 cudaError_t launch_hs_proj_fp32(const bd_hs_params *p, const float *hist, int n, uint32_t *out,
                                 cudaStream_t st, const bd_keypoint *kps);
 // FP32 projection with any W [128][K] / bias; relaxed (nullable) gets tanh(m * inv_t)
@@ -170,8 +168,7 @@ cudaError_t launch_hs_proj_fp32_raw(const float *W, const float *bias, int K, co
                                     cudaStream_t st);
 // raises the projection kernel's dynamic shared-memory limit (per device, at set-up)
 cudaError_t prepare_hs_proj_tc();
-cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const CUtensorMap &tm_hi,
-                              const CUtensorMap &tm_lo, const float *hist, int n, uint32_t *out,
+cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const float *hist, int n, uint32_t *out,
                               DeviceStatus *status, cudaStream_t st, const bd_keypoint *kps);
 
 size_t match_scratch_bytes(int nq, int nt, int nbits, int sm_count);
@@ -400,6 +397,31 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
             smem_u32(bar))
         : "memory");
 }
+
+// Generic-proxy writes to shared memory made visible to the async proxy
+// (tensor-core operand reads) of the CTA; then a barrier before the MMA.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// TMEM loads issued without waiting: call tmem_wait_ld() before using r.
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // 32 lanes x 32 consecutive 32-bit TMEM columns: thread t of the warp gets
 // lane (warp's lane base + t), columns [col, col+32).

@@ -372,7 +372,7 @@ size_t bd_scratch_bytes_hashsift(int n)
 {
     if (n < 0)
         return 0;
-    return align_up((size_t)n * kHistDim * 4, 256) + align_up((size_t)n * kHistDim * 4, 256);
+    return align_up((size_t)n * kHistDim * 4, 256);
 }
 
 size_t bd_scratch_bytes_match(int nq, int nt, int nbits)
@@ -704,27 +704,20 @@ bd_status bd_hashsift_hist(bd_ctx *ctx, const float *patches, int n, float *hist
     if (n == 0)
         return BD_OK;
     TraceScope scope(ctx, ctx->stream);
-    BD_LAUNCH(ctx, launch_hs_hist_patches(patches, n, hist, nullptr, ctx->stream, ctx->sm_count),
+    BD_LAUNCH(ctx, launch_hs_hist_patches(patches, n, hist, ctx->stream, ctx->sm_count),
               "histogram kernel");
     return BD_OK;
 }
 
-static bd_status project(bd_ctx *ctx, const bd_hs_params *p, const float *hist,
-                         __nv_bfloat16 *hist16, bool need_convert, int n, uint32_t *out,
-                         const bd_keypoint *kps)
+static bd_status project(bd_ctx *ctx, const bd_hs_params *p, const float *hist, int n,
+                         uint32_t *out, const bd_keypoint *kps)
 {
     if (p->precision == BD_HS_FP32) {
         BD_LAUNCH(ctx, launch_hs_proj_fp32(p, hist, n, out, ctx->stream, kps),
                   "FP32 projection kernel");
         return BD_OK;
     }
-    if (need_convert)
-        BD_LAUNCH(ctx, launch_hs_to_bf16(hist, n, hist16, ctx->stream), "BF16 conversion kernel");
-    CUtensorMap tm_hi, tm_lo;
-    if (!encode_tmap_2d_bf16(&tm_hi, hist16, 128, (uint64_t)n, 256, 64, 128) ||
-        !encode_tmap_2d_bf16(&tm_lo, hist16 + (size_t)n * kHistDim, 128, (uint64_t)n, 256, 64, 128))
-        return set_err(ctx, BD_ERR_CUDA, "cannot encode the TMA descriptors of the histograms");
-    BD_LAUNCH(ctx, launch_hs_proj_tc(p, tm_hi, tm_lo, hist, n, out, ctx->status, ctx->stream, kps),
+    BD_LAUNCH(ctx, launch_hs_proj_tc(p, hist, n, out, ctx->status, ctx->stream, kps),
               "tcgen05 projection kernel");
     return BD_OK;
 }
@@ -737,17 +730,10 @@ bd_status bd_hashsift_project(bd_ctx *ctx, const bd_hs_params *p, const float *h
         return set_err(ctx, BD_ERR_INVALID, "bd_hashsift_project: bad arguments");
     if (n == 0)
         return BD_OK;
-    __nv_bfloat16 *h16 = nullptr;
     if (p->precision == BD_HS_BF16_RESCUE && ((uintptr_t)hist & 15))
         return set_err(ctx, BD_ERR_INVALID, "bd_hashsift_project: hist must be 16-byte aligned");
-    if (p->precision == BD_HS_BF16_RESCUE) {
-        bd_status s = ensure_scratch(ctx, align_up((size_t)n * 512, 256));
-        if (s != BD_OK)
-            return s;
-        h16 = (__nv_bfloat16 *)ctx->scratch;
-    }
     TraceScope scope(ctx, ctx->stream);
-    return project(ctx, p, hist, h16, true, n, out, nullptr);
+    return project(ctx, p, hist, n, out, nullptr);
 }
 
 bd_status bd_hashsift_describe(bd_ctx *ctx, const bd_hs_params *p, const uint8_t *img, int w,
@@ -765,15 +751,12 @@ bd_status bd_hashsift_describe(bd_ctx *ctx, const bd_hs_params *p, const uint8_t
     if (s != BD_OK)
         return s;
     float *h32 = hist_out ? hist_out : (float *)ctx->scratch;
-    __nv_bfloat16 *h16 =
-        (__nv_bfloat16 *)((char *)ctx->scratch + align_up((size_t)n * kHistDim * 4, 256));
-    const bool tc = p->precision == BD_HS_BF16_RESCUE;
     TraceScope scope(ctx, ctx->stream);
     BD_LAUNCH(ctx,
-              launch_hs_hist_image(p, img, w, h, pitch, kps, n, h32, tc ? h16 : nullptr,
-                                   ctx->status, ctx->stream, ctx->sm_count),
+              launch_hs_hist_image(p, img, w, h, pitch, kps, n, h32, ctx->status, ctx->stream,
+                                   ctx->sm_count),
               "fused warp + histogram kernel");
-    return project(ctx, p, h32, h16, false, n, out, kps);
+    return project(ctx, p, h32, n, out, kps);
 }
 
 static bd_status ensure_arrivals(bd_ctx *ctx, int qblocks)

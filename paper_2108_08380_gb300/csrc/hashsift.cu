@@ -18,25 +18,23 @@ using dev::PS;
 template <bool Coop>
 __global__ void __launch_bounds__(NT) hs_hist_image_kernel(
     const uint8_t *__restrict__ img, int w, int h, int pitch, const bd_keypoint *__restrict__ kps,
-    int n, float spacing, float *__restrict__ hist, __nv_bfloat16 *__restrict__ hist16,
-    DeviceStatus *status)
+    int n, float spacing, float *__restrict__ hist, DeviceStatus *status)
 {
     __shared__ dev::WarpHist S[Coop ? 1 : NT / 32];
     if (Coop) {
         for (int k = blockIdx.x; k < n; k += gridDim.x)
-            dev::hs_hist_image_cta(S[0], img, w, h, pitch, kps[k], spacing, hist, hist16,
-                                   (size_t)k, (size_t)n, status);
+            dev::hs_hist_image_cta(S[0], img, w, h, pitch, kps[k], spacing, hist, (size_t)k,
+                                   status);
     } else {
         const int warp = threadIdx.x >> 5;
         for (int k = blockIdx.x * (NT / 32) + warp; k < n; k += gridDim.x * (NT / 32))
-            dev::hs_hist_image_warp(S[warp], img, w, h, pitch, kps[k], spacing, hist, hist16,
-                                    (size_t)k, (size_t)n, status);
+            dev::hs_hist_image_warp(S[warp], img, w, h, pitch, kps[k], spacing, hist, (size_t)k,
+                                    status);
     }
 }
 
 __global__ void __launch_bounds__(NT) hs_hist_patch_kernel(const float *__restrict__ patches,
                                                            int n, float *__restrict__ hist,
-                                                           __nv_bfloat16 *__restrict__ hist16,
                                                            float *__restrict__ norm_out)
 {
     __shared__ dev::WarpHist S[NT / 32];
@@ -44,7 +42,7 @@ __global__ void __launch_bounds__(NT) hs_hist_patch_kernel(const float *__restri
     for (int k = blockIdx.x * (NT / 32) + warp; k < n; k += gridDim.x * (NT / 32)) {
         dev::PatchMem src;
         src.p = patches + (size_t)k * PS * PS;
-        dev::hs_hist_warp(S[warp], src, true, lane, hist, hist16, (size_t)k, (size_t)n, norm_out);
+        dev::hs_hist_warp(S[warp], src, true, lane, hist, (size_t)k, norm_out);
     }
 }
 
@@ -83,17 +81,6 @@ __global__ void __launch_bounds__(NT) hs_warp_kernel(const uint8_t *__restrict__
     }
 }
 
-__global__ void hs_to_bf16_kernel(const float *__restrict__ src, size_t count,
-                                  __nv_bfloat16 *__restrict__ dst)
-{
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const float v = src[i];
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        dst[i] = hi;
-        dst[count + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
-    }
-}
 
 // ---------------------------------------------------------------------------
 // FP32 projection: margins m = W^T f + b, bit = m > 0.  The sum runs in four
@@ -204,11 +191,11 @@ cudaError_t launch_hs_warp(const bd_hs_params *p, const uint8_t *img, int w, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_hs_hist_patches(const float *patches, int n, float *hist,
-                                   __nv_bfloat16 *hist16, cudaStream_t st, int sm_count,
+cudaError_t launch_hs_hist_patches(const float *patches, int n, float *hist, cudaStream_t st,
+                                   int sm_count,
                                    float *norm_out)
 {
-    hs_hist_patch_kernel<<<grid_for((n + 3) / 4, sm_count, 12), NT, 0, st>>>(patches, n, hist, hist16,
+    hs_hist_patch_kernel<<<grid_for((n + 3) / 4, sm_count, 12), NT, 0, st>>>(patches, n, hist,
                                                                    norm_out);
     trace_kernel(st, "hs_hist_patch");
     note_launches(1);
@@ -217,32 +204,21 @@ cudaError_t launch_hs_hist_patches(const float *patches, int n, float *hist,
 
 cudaError_t launch_hs_hist_image(const bd_hs_params *p, const uint8_t *img, int w, int h, int pitch,
                                  const bd_keypoint *kps, int n, float *hist,
-                                 __nv_bfloat16 *hist16, DeviceStatus *status, cudaStream_t st,
+                                 DeviceStatus *status, cudaStream_t st,
                                  int sm_count)
 {
     // few keypoints: the CTA shares each one (latency); many: one per warp (throughput)
     if (n <= 2 * 12 * sm_count)
         hs_hist_image_kernel<true><<<grid_for(n, sm_count, 12), NT, 0, st>>>(
-            img, w, h, pitch, kps, n, p->spacing, hist, hist16, status);
+            img, w, h, pitch, kps, n, p->spacing, hist, status);
     else
         hs_hist_image_kernel<false><<<grid_for((n + 3) / 4, sm_count, 12), NT, 0, st>>>(
-            img, w, h, pitch, kps, n, p->spacing, hist, hist16, status);
+            img, w, h, pitch, kps, n, p->spacing, hist, status);
     trace_kernel(st, "hs_hist_image");
     note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_hs_to_bf16(const float *hist, int n, __nv_bfloat16 *hist16, cudaStream_t st)
-{
-    const size_t cnt = (size_t)n * kHistDim;
-    int blocks = (int)((cnt + 255) / 256);
-    if (blocks > 4096)
-        blocks = 4096;
-    hs_to_bf16_kernel<<<blocks, 256, 0, st>>>(hist, cnt, hist16);
-    trace_kernel(st, "hs_to_bf16");
-    note_launches(1);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_hs_proj_fp32_raw(const float *W, const float *bias, int K, const float *hist,
                                     int n, uint32_t *out, float *relaxed, float inv_t,

@@ -334,13 +334,12 @@ __device__ __forceinline__ void vote_px(WarpHist &S, int lane, int i, float up, 
 }
 
 // Histogram of one keypoint by one warp: rows from `src` (a ColSampler or a
-// PatchCol of this lane's column), output like the oracle's [cell][bin]
-// order, L2-normalised, with optional BF16 head/tail copies and norm.
+// PatchMem), output like the oracle's [cell][bin] order, L2-normalised,
+// with the optional norm.
 template <class Src>
 __device__ __forceinline__ void hs_hist_warp(WarpHist &S, const Src &src, bool valid, int lane,
-                                             float *__restrict__ hist,
-                                             __nv_bfloat16 *__restrict__ hist16, size_t k,
-                                             size_t n, float *__restrict__ norm_out)
+                                             float *__restrict__ hist, size_t k,
+                                             float *__restrict__ norm_out)
 {
     {
         float4 *z = reinterpret_cast<float4 *>(&S.priv[0][0][0]);
@@ -394,13 +393,7 @@ __device__ __forceinline__ void hs_hist_warp(WarpHist &S, const Src &src, bool v
 #pragma unroll
     for (int ci = 0; ci < 4; ++ci) {
         const float hv = (valid && nrm > 0.0f) ? H[ci] / nrm : 0.0f;
-        const size_t e = k * kHistDim + ci * 32 + lane;
-        hist[e] = hv;
-        if (hist16) {
-            const __nv_bfloat16 hi = __float2bfloat16_rn(hv);
-            hist16[e] = hi;
-            hist16[n * kHistDim + e] = __float2bfloat16_rn(hv - __bfloat162float(hi));
-        }
+        hist[k * kHistDim + ci * 32 + lane] = hv;
     }
     __syncwarp();
 }
@@ -411,9 +404,8 @@ __device__ __forceinline__ void hs_hist_warp(WarpHist &S, const Src &src, bool v
 // CTA's sum of squares.  All 128 threads call it; S is the CTA's buffer.
 template <class Src>
 __device__ __forceinline__ void hs_hist_cta(WarpHist &S, const Src &src, bool valid,
-                                            float *__restrict__ hist,
-                                            __nv_bfloat16 *__restrict__ hist16, size_t k,
-                                            size_t n, float *__restrict__ norm_out)
+                                            float *__restrict__ hist, size_t k,
+                                            float *__restrict__ norm_out)
 {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     {
@@ -461,46 +453,38 @@ __device__ __forceinline__ void hs_hist_cta(WarpHist &S, const Src &src, bool va
     if (norm_out && t == 0)
         norm_out[k] = valid ? nrm : 0.0f;
     const float hv = (valid && nrm > 0.0f) ? H / nrm : 0.0f;
-    const size_t e = k * kHistDim + w * 32 + lane;
-    hist[e] = hv;
-    if (hist16) {
-        const __nv_bfloat16 hi = __float2bfloat16_rn(hv);
-        hist16[e] = hi;
-        hist16[n * kHistDim + e] = __float2bfloat16_rn(hv - __bfloat162float(hi));
-    }
+    hist[k * kHistDim + w * 32 + lane] = hv;
     __syncthreads();  // S is reused by the next keypoint
 }
 
 // Histogram of keypoint k of n sampled from the image by the whole CTA.
 __device__ __forceinline__ void hs_hist_image_cta(WarpHist &S, const uint8_t *img, int w, int h,
                                                   int pitch, const bd_keypoint &kp, float spacing,
-                                                  float *hist, __nv_bfloat16 *hist16, size_t k,
-                                                  size_t n, DeviceStatus *status)
+                                                  float *hist, size_t k, DeviceStatus *status)
 {
     const bool valid = kp_valid(kp);
     ColSampler<false> edge;
     if (!valid) {
         if (threadIdx.x == 0)
             raise_flag(status, BD_FLAG_INVALID_KEYPOINT);
-        hs_hist_cta(S, edge, false, hist, hist16, k, n, nullptr);
+        hs_hist_cta(S, edge, false, hist, k, nullptr);
         return;
     }
     const Frame f = make_frame(kp, spacing);
     if (col_interior(f, w, h)) {
         ColSampler<true> in;
         in.c = col_frame(img, w, h, pitch, f);
-        hs_hist_cta(S, in, true, hist, hist16, k, n, nullptr);
+        hs_hist_cta(S, in, true, hist, k, nullptr);
     } else {
         edge.c = col_frame(img, w, h, pitch, f);
-        hs_hist_cta(S, edge, true, hist, hist16, k, n, nullptr);
+        hs_hist_cta(S, edge, true, hist, k, nullptr);
     }
 }
 
 // Histogram of keypoint k of n sampled from the image; all 32 lanes call it.
 __device__ __forceinline__ void hs_hist_image_warp(WarpHist &S, const uint8_t *img, int w, int h,
                                                    int pitch, const bd_keypoint &kp, float spacing,
-                                                   float *hist, __nv_bfloat16 *hist16, size_t k,
-                                                   size_t n, DeviceStatus *status)
+                                                   float *hist, size_t k, DeviceStatus *status)
 {
     const int lane = threadIdx.x & 31;
     const bool valid = kp_valid(kp);
@@ -508,17 +492,17 @@ __device__ __forceinline__ void hs_hist_image_warp(WarpHist &S, const uint8_t *i
     if (!valid) {
         if (lane == 0)
             raise_flag(status, BD_FLAG_INVALID_KEYPOINT);
-        hs_hist_warp(S, edge, false, lane, hist, hist16, k, n, nullptr);
+        hs_hist_warp(S, edge, false, lane, hist, k, nullptr);
         return;
     }
     const Frame f = make_frame(kp, spacing);
     if (col_interior(f, w, h)) {
         ColSampler<true> in;
         in.c = col_frame(img, w, h, pitch, f, lane);
-        hs_hist_warp(S, in, true, lane, hist, hist16, k, n, nullptr);
+        hs_hist_warp(S, in, true, lane, hist, k, nullptr);
     } else {
         edge.c = col_frame(img, w, h, pitch, f, lane);
-        hs_hist_warp(S, edge, true, lane, hist, hist16, k, n, nullptr);
+        hs_hist_warp(S, edge, true, lane, hist, k, nullptr);
     }
 }
 

@@ -547,7 +547,7 @@ bd_status bd_train_forward(bd_ctx *ctx, bd_train *tr, const float *patches, cons
             patches, rows, bp->d_patch_box, bp->d_patch_side, theta, inv_scale, tr->r_bad, tr->bits_bad);
     trace_kernel(st, "train_bad_fwd");
     // relaxed HashSIFT
-    e = launch_hs_hist_patches(patches, rows, tr->h, nullptr, st, sm, tr->norm);
+    e = launch_hs_hist_patches(patches, rows, tr->h, st, sm, tr->norm);
     if (e == cudaSuccess)
         e = launch_hs_proj_fp32_raw(W, b, tr->kh, tr->h, rows, tr->bits_hs, tr->r_hs, 1.0f / tr->T, st);
     // mining on hard codes, or the given mining
