@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                 const int k = idx;
                 const int im = find_image(A.imgs, A.n_img, k, 1);
                 const BatchImageDev &I = A.imgs[im];
-                dev::hs_hist_image_cta(U.h[0], A.img_ptr[im], I.w, I.h, I.pitch, A.kps[k],
+                dev::hs_hist_image_cta<false>(U.h[0], A.img_ptr[im], I.w, I.h, I.pitch, A.kps[k],
                                        A.spacing, A.hist, (size_t)k, A.status);
             } else {
                 // four keypoints, one per warp
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                 if (k < A.n_kp) {
                     const int im = find_image(A.imgs, A.n_img, k, 1);
                     const BatchImageDev &I = A.imgs[im];
-                    dev::hs_hist_image_warp(U.h[t >> 5], A.img_ptr[im], I.w, I.h, I.pitch,
+                    dev::hs_hist_image_warp<false>(U.h[t >> 5], A.img_ptr[im], I.w, I.h, I.pitch,
                                             A.kps[k], A.spacing, A.hist, (size_t)k, A.status);
                 }
             }

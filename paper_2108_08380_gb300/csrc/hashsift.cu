@@ -23,12 +23,12 @@ __global__ void __launch_bounds__(NT) hs_hist_image_kernel(
     __shared__ dev::WarpHist S[Coop ? 1 : NT / 32];
     if (Coop) {
         for (int k = blockIdx.x; k < n; k += gridDim.x)
-            dev::hs_hist_image_cta(S[0], img, w, h, pitch, kps[k], spacing, hist, (size_t)k,
+            dev::hs_hist_image_cta<true>(S[0], img, w, h, pitch, kps[k], spacing, hist, (size_t)k,
                                    status);
     } else {
         const int warp = threadIdx.x >> 5;
         for (int k = blockIdx.x * (NT / 32) + warp; k < n; k += gridDim.x * (NT / 32))
-            dev::hs_hist_image_warp(S[warp], img, w, h, pitch, kps[k], spacing, hist, (size_t)k,
+            dev::hs_hist_image_warp<true>(S[warp], img, w, h, pitch, kps[k], spacing, hist, (size_t)k,
                                     status);
     }
 }

@@ -294,10 +294,87 @@ struct PatchMem {
 constexpr int kPRow = 40;  // padded patch row: bank (8 i + j) % 32 is distinct per block and per row
 
 struct WarpHist {
-    float P[PS][kPRow];    // patch samples [row][column]
+    union {
+        float P[PS][kPRow];               // patch samples [row][column]
+        uint32_t win[PS * kPRow];         // or the keypoint's image footprint (bytes)
+    };
     float priv[4][8][32];  // [cell row][bin][lane]
     float wss[4];          // per-warp sums of squares (cooperative mode)
 };
+constexpr int kWinBytes = PS * kPRow * 4;
+
+// Image footprint of a keypoint staged in shared memory: image rows
+// [y0, y0 + nr), bytes [x0, x0 + 4 wpr) of each (x0 word-aligned), row
+// stride S bytes with S / 4 odd so that rows fall on different banks.
+struct WinGeom {
+    int x0, y0, nr, wpr, S;
+};
+
+// Footprint of the keypoint's 32x32 samples (every bilinear tap, with the
+// split_floor step) when it lies inside the image, fits kWinBytes and the
+// image rows are word-aligned; false otherwise (the sampler reads global
+// memory then).
+__device__ __forceinline__ bool win_geom(const Frame &f, const uint8_t *img, int w, int h,
+                                         int pitch, WinGeom &g)
+{
+    if ((reinterpret_cast<uintptr_t>(img) & 3) || (pitch & 3))
+        return false;
+    const float reach = 15.5f * (fabsf(f.A) + fabsf(f.B));  // |sample offset| <= reach + 0.5
+    if (!(reach < 60.0f))
+        return false;
+    const int m = (int)reach + 3;  // taps reach one pixel beyond; split_floor may step one back
+    const int x0 = (f.ix - m) & ~3, x1 = f.ix + m + 2;
+    const int y0 = f.iy - m, y1 = f.iy + m + 2;
+    if (f.ix - m < 0 || y0 < 0 || y1 > h)
+        return false;
+    const int wpr = (x1 - x0 + 3) >> 2;
+    if (wpr > 32 || x0 + 4 * wpr > w)
+        return false;
+    const int S = 4 * (wpr | 1);
+    if ((y1 - y0) * S > kWinBytes)
+        return false;
+    g.x0 = x0;
+    g.y0 = y0;
+    g.nr = y1 - y0;
+    g.wpr = wpr;
+    g.S = S;
+    return true;
+}
+
+// Copies the footprint into the window with word loads, threads t0 .. t0 +
+// nthr - 1 of the caller's group (32: one warp; 128: the CTA); rows are
+// spread over the group in blocks of the next power of two >= wpr words.
+__device__ __forceinline__ void win_stage(uint32_t *win, const WinGeom &g, const uint8_t *img,
+                                          int pitch, int tid, int nthr)
+{
+    const int wp2 = g.wpr <= 8 ? 8 : (g.wpr <= 16 ? 16 : 32);
+    const int rpi = nthr / wp2;  // rows per pass
+    const int rr = tid / wp2, c = tid % wp2;
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(img + (size_t)g.y0 * pitch + g.x0);
+    const int pw = pitch >> 2, sw = g.S >> 2;
+    if (c < g.wpr)
+        for (int r = rr; r < g.nr; r += rpi)
+            win[r * sw + c] = __ldg(src + (size_t)r * pw + c);
+}
+
+// Bilinear sample (i, j) of the patch from the staged footprint, with the
+// same arithmetic as ColSampler (identical values).
+__device__ __forceinline__ float win_sample(const uint8_t *win, const WinGeom &g,
+                                            const ColFrame &c, int i, int j)
+{
+    const float u = (float)j - 15.5f, v = (float)i - 15.5f;
+    const float ox = fmaf(c.A, u, fmaf(-c.B, v, c.cx));
+    const float oy = fmaf(c.B, u, fmaf(c.A, v, c.cy));
+    float ax, ay;
+    const int x0 = split_floor(ox, ax) + c.ix - g.x0;
+    const int y0 = split_floor(oy, ay) + c.iy - g.y0;
+    const uint8_t *p = win + y0 * g.S + x0;
+    const float i00 = u8f(p[0]), i01 = u8f(p[1]);
+    const float i10 = u8f(p[g.S]), i11 = u8f(p[g.S + 1]);
+    const float top = fmaf(ax, i01 - i00, i00);
+    const float bot = fmaf(ax, i11 - i10, i10);
+    return fmaf(ay, bot - top, top);
+}
 
 // Gaussian weight exp(-(d^2) / 512) of row / column index i (sigma = 16 about
 // 15.5); __expf's relative error (~2^-21) is far below the histogram tolerance.
@@ -457,7 +534,114 @@ __device__ __forceinline__ void hs_hist_cta(WarpHist &S, const Src &src, bool va
     __syncthreads();  // S is reused by the next keypoint
 }
 
+// Zeroes a lane-private histogram block: warp mode all four cell rows, CTA
+// mode the warp's own cell row.
+__device__ __forceinline__ void priv_zero_warp(WarpHist &S, int lane)
+{
+    float4 *z = reinterpret_cast<float4 *>(&S.priv[0][0][0]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        z[q * 32 + lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+// Cell-row sums, L2 norm and output of a warp-mode histogram.
+__device__ __forceinline__ void warp_finish(WarpHist &S, int lane, bool valid,
+                                            float *__restrict__ hist, size_t k)
+{
+    const int cj = lane >> 3, b = lane & 7;
+    float H[4];
+    float ss = 0.0f;
+#pragma unroll
+    for (int ci = 0; ci < 4; ++ci) {
+        float s = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            s += S.priv[ci][b][cj * 8 + ((q + b) & 7)];
+        H[ci] = s;
+        ss += s * s;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        ss += __shfl_xor_sync(kFull, ss, o);
+    const float nrm = sqrtf(ss);
+#pragma unroll
+    for (int ci = 0; ci < 4; ++ci)
+        hist[k * kHistDim + ci * 32 + lane] = (valid && nrm > 0.0f) ? H[ci] / nrm : 0.0f;
+    __syncwarp();
+}
+
+// Warp mode from a staged footprint: the lane samples its column on the fly
+// (one sample per pixel, taps from shared memory) while it votes.
+__device__ __forceinline__ void hs_hist_warp_win(WarpHist &S, const WinGeom &g, const ColFrame &c,
+                                                 const uint8_t *img, int pitch, int lane,
+                                                 float *__restrict__ hist, size_t k)
+{
+    priv_zero_warp(S, lane);
+    win_stage(S.win, g, img, pitch, lane, 32);
+    __syncwarp();
+    const uint8_t *win = reinterpret_cast<const uint8_t *>(S.win);
+    const float g_half = 0.5f * gauss16(lane);
+    float here = win_sample(win, g, c, 0, lane);
+    float up = here;  // replicated row -1
+#pragma unroll 4
+    for (int i = 0; i < PS; ++i) {
+        const float down = i < PS - 1 ? win_sample(win, g, c, i + 1, lane) : here;
+        vote_px(S, lane, i, up, here, down, g_half);
+        up = here;
+        here = down;
+    }
+    __syncwarp();
+    warp_finish(S, lane, true, hist, k);
+}
+
+// CTA mode from a staged footprint: the CTA stages it, warp w samples rows
+// 8w - 1 .. 8w + 8 on the fly and votes rows [8w, 8w + 8).
+__device__ __forceinline__ void hs_hist_cta_win(WarpHist &S, const WinGeom &g, const ColFrame &c,
+                                                const uint8_t *img, int pitch,
+                                                float *__restrict__ hist, size_t k)
+{
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    {
+        float4 *z = reinterpret_cast<float4 *>(&S.priv[w][0][0]);
+        z[lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        z[lane + 32] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    win_stage(S.win, g, img, pitch, t, 128);
+    __syncthreads();
+    const uint8_t *win = reinterpret_cast<const uint8_t *>(S.win);
+    const float g_half = 0.5f * gauss16(lane);
+    float up = win_sample(win, g, c, w > 0 ? 8 * w - 1 : 0, lane);
+    float here = win_sample(win, g, c, 8 * w, lane);
+#pragma unroll 4
+    for (int r = 0; r < 8; ++r) {
+        const int i = 8 * w + r;
+        const float down = i < PS - 1 ? win_sample(win, g, c, i + 1, lane) : here;
+        vote_px(S, lane, i, up, here, down, g_half);
+        up = here;
+        here = down;
+    }
+    __syncwarp();
+    const int cj = lane >> 3, b = lane & 7;
+    float H = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        H += S.priv[w][b][cj * 8 + ((q + b) & 7)];
+    float ss = H * H;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        ss += __shfl_xor_sync(kFull, ss, o);
+    if (lane == 0)
+        S.wss[w] = ss;
+    __syncthreads();
+    const float nrm = sqrtf(S.wss[0] + S.wss[1] + S.wss[2] + S.wss[3]);
+    hist[k * kHistDim + w * 32 + lane] = nrm > 0.0f ? H / nrm : 0.0f;
+    __syncthreads();  // S is reused by the next keypoint
+}
+
 // Histogram of keypoint k of n sampled from the image by the whole CTA.
+// UseWin: stage the footprint in shared memory when it fits (the per-image
+// kernel; the batched kernel keeps the smaller code without it).
+template <bool UseWin>
 __device__ __forceinline__ void hs_hist_image_cta(WarpHist &S, const uint8_t *img, int w, int h,
                                                   int pitch, const bd_keypoint &kp, float spacing,
                                                   float *hist, size_t k, DeviceStatus *status)
@@ -471,7 +655,10 @@ __device__ __forceinline__ void hs_hist_image_cta(WarpHist &S, const uint8_t *im
         return;
     }
     const Frame f = make_frame(kp, spacing);
-    if (col_interior(f, w, h)) {
+    WinGeom g;
+    if (UseWin && win_geom(f, img, w, h, pitch, g)) {
+        hs_hist_cta_win(S, g, col_frame(img, w, h, pitch, f), img, pitch, hist, k);
+    } else if (col_interior(f, w, h)) {
         ColSampler<true> in;
         in.c = col_frame(img, w, h, pitch, f);
         hs_hist_cta(S, in, true, hist, k, nullptr);
@@ -482,6 +669,7 @@ __device__ __forceinline__ void hs_hist_image_cta(WarpHist &S, const uint8_t *im
 }
 
 // Histogram of keypoint k of n sampled from the image; all 32 lanes call it.
+template <bool UseWin>
 __device__ __forceinline__ void hs_hist_image_warp(WarpHist &S, const uint8_t *img, int w, int h,
                                                    int pitch, const bd_keypoint &kp, float spacing,
                                                    float *hist, size_t k, DeviceStatus *status)
@@ -496,7 +684,10 @@ __device__ __forceinline__ void hs_hist_image_warp(WarpHist &S, const uint8_t *i
         return;
     }
     const Frame f = make_frame(kp, spacing);
-    if (col_interior(f, w, h)) {
+    WinGeom g;
+    if (UseWin && win_geom(f, img, w, h, pitch, g)) {
+        hs_hist_warp_win(S, g, col_frame(img, w, h, pitch, f, lane), img, pitch, lane, hist, k);
+    } else if (col_interior(f, w, h)) {
         ColSampler<true> in;
         in.c = col_frame(img, w, h, pitch, f, lane);
         hs_hist_warp(S, in, true, lane, hist, k, nullptr);
