@@ -128,7 +128,7 @@ class Workload:
             self.plan.set_config(*config)
             self.tuned = self.plan.config()
         elif autotune:
-            self.tuned, _ = self.plan.autotune(self.dimg, self.dkps, self.bad, self.hs, reps=3)
+            self.tuned, _ = self.plan.autotune(self.dimg, self.dkps, self.bad, self.hs, reps=5)
         if self.match:
             na = int(self.offsets[1])
             self.m_bad = torch.empty((na, 3), dtype=i32, device=dev)

@@ -280,8 +280,10 @@ bd_status bd_describe_batch(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
                             const bd_keypoint *kps, uint32_t *bad_out, uint32_t *hs_out,
                             int use_graph);
 
-/* Times every candidate launch shape (reps launches each, CUDA events on the
- * context's stream), keeps the fastest in the plan and returns it. */
+/* Times every candidate launch shape (reps launches each after a warm-up
+ * launch, CUDA events on the context's stream), re-times the four fastest
+ * with 3 x reps launches, keeps the fastest of those in the plan and returns
+ * it (best_ms: its mean time per launch). */
 bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs,
                             const bd_keypoint *kps, uint32_t *bad_out, uint32_t *hs_out,
                             int reps, bd_batch_config *best, float *best_ms);

@@ -15,6 +15,8 @@
 // skips the item.
 #include <string.h>
 
+#include <algorithm>
+
 #include <vector>
 
 #include "bad_dev.cuh"
@@ -613,41 +615,57 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // mean time of `r` launches of configuration c (after one warm-up launch)
+    auto time_cfg = [&](const bd_batch_config &c, int r, float *ms) -> bd_status {
+        bd_status s = bd_batch_set_config(b, &c);
+        if (s == BD_OK)
+            s = bd_describe_batch(ctx, b, imgs, kps, bad_out, hs_out, 0);
+        if (s != BD_OK)
+            return s;
+        cudaEventRecord(e0, ctx->stream);
+        for (int q = 0; q < r; ++q)
+            bd_describe_batch(ctx, b, imgs, kps, bad_out, hs_out, 0);
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(ms, e0, e1);
+        *ms /= r;
+        return BD_OK;
+    };
+    // sweep, then re-time the four fastest with three times the repetitions
+    std::vector<std::pair<float, bd_batch_config>> res;
+    bd_status s = BD_OK;
+    for (int hm : {1, 4})
+        for (int hs_first = 0; hs_first < 3 && s == BD_OK; ++hs_first)
+            for (int it : items)
+                for (int c : per_sm) {
+                    if (s != BD_OK)
+                        break;
+                    bd_batch_config cfg = {it, c, hs_first, hm};
+                    float ms = 0.f;
+                    s = time_cfg(cfg, reps, &ms);
+                    res.push_back({ms, cfg});
+                }
     bd_batch_config win = b->cfg;
     float win_ms = 1e30f;
-    const int hs_modes[] = {1, 4};
-    for (int hm : hs_modes) {
-    for (int hs_first = 0; hs_first < 3; ++hs_first) {
-        for (int it : items) {
-            for (int c : per_sm) {
-                bd_batch_config cfg = {it, c, hs_first, hm};
-                bd_status s = bd_batch_set_config(b, &cfg);
-                if (s == BD_OK)
-                    s = bd_describe_batch(ctx, b, imgs, kps, bad_out, hs_out, 0);  // warm-up
-                if (s != BD_OK) {
-                    cudaEventDestroy(e0);
-                    cudaEventDestroy(e1);
-                    return s;
-                }
-                cudaEventRecord(e0, ctx->stream);
-                for (int r = 0; r < reps; ++r)
-                    bd_describe_batch(ctx, b, imgs, kps, bad_out, hs_out, 0);
-                cudaEventRecord(e1, ctx->stream);
-                cudaEventSynchronize(e1);
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                ms /= reps;
-                if (ms < win_ms) {
-                    win_ms = ms;
-                    win = cfg;
-                }
+    if (s == BD_OK) {
+        std::sort(res.begin(), res.end(),
+                  [](const std::pair<float, bd_batch_config> &x,
+                     const std::pair<float, bd_batch_config> &y) { return x.first < y.first; });
+        const size_t top = res.size() < 4 ? res.size() : 4;
+        for (size_t q = 0; q < top && s == BD_OK; ++q) {
+            float ms = 0.f;
+            s = time_cfg(res[q].second, 3 * reps, &ms);
+            if (ms < win_ms) {
+                win_ms = ms;
+                win = res[q].second;
             }
         }
     }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    bd_status s = bd_batch_set_config(b, &win);
+    if (s != BD_OK)
+        return s;
+    s = bd_batch_set_config(b, &win);
     if (best)
         *best = win;
     if (best_ms)
