@@ -10,7 +10,8 @@ Every function follows a definition of the paper (Suarez et al., RA-L 2021):
 Sec. III-A for the integral image, the box features and the BAD stumps,
 Sec. III-B for the HashSIFT histogram and hash, Sec. IV-C for nearest
 neighbour matching, Eq. 1 / Eq. 3 for the triplet ranking loss of the
-training step (``bd_oracle_train.c``); the readings taken where the paper is
+training step (``bd_oracle_train.c``), the feature-selection round
+(``bd_oracle_select.c``); the readings taken where the paper is
 silent are listed at the top of the two C files.
 """
 from __future__ import annotations
@@ -23,7 +24,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = [os.path.join(_HERE, "bd_oracle.c"), os.path.join(_HERE, "bd_oracle_train.c")]
+_SRC = [os.path.join(_HERE, "bd_oracle.c"), os.path.join(_HERE, "bd_oracle_train.c"),
+        os.path.join(_HERE, "bd_oracle_select.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -331,3 +333,47 @@ def train_codes(patches, bad, theta, hs):
     lib().or_train_codes(_f64p(P), ctypes.c_int(n), ctypes.c_int(Kb), _u8p(c), _u8p(s), _f64p(th),
                          ctypes.c_int(Kh), _f64p(W), _f64p(b), _u32p(bb), _u32p(bh), _f64p(fb), _f64p(mh))
     return bb, bh, fb, mh
+
+
+# ---------------------------------------------------------------------------
+# feature selection (Algorithms 1 and 2, integer-sorted thresholds)
+# ---------------------------------------------------------------------------
+
+SELECT_QMIN = -2551
+
+
+def select_key(patch, cand) -> int:
+    """ceil(10 (sum1 - sum2) / s^2) of one uint8 32x32 patch; cand = (x1, y1, x2, y2, s)."""
+    p = np.ascontiguousarray(patch, dtype=np.uint8).reshape(32, 32)
+    c = np.ascontiguousarray(cand, dtype=np.int32)
+    return int(lib().or_select_key(_u8p(p), _i32p(c)))
+
+
+def find_threshold(patches, cand, sap, san, tau: int):
+    """Algorithm 2 for one candidate: (theta numerator q, loss); patches [3, n, 32, 32] uint8."""
+    P = np.ascontiguousarray(patches, dtype=np.uint8).reshape(3, -1, 32, 32)
+    n = P.shape[1]
+    c = np.ascontiguousarray(cand, dtype=np.int32)
+    a = np.ascontiguousarray(sap, dtype=np.int32)
+    b = np.ascontiguousarray(san, dtype=np.int32)
+    q = ctypes.c_int32(0)
+    loss = ctypes.c_int64(0)
+    lib().or_find_threshold(_u8p(P), n, _i32p(c), _i32p(a), _i32p(b), int(tau), ctypes.byref(q),
+                            ctypes.byref(loss))
+    return int(q.value), int(loss.value)
+
+
+def select_feature(patches, cands, sap, san, tau: int):
+    """Algorithm 1, one round: (theta_q [J], loss [J], best index)."""
+    P = np.ascontiguousarray(patches, dtype=np.uint8).reshape(3, -1, 32, 32)
+    n = P.shape[1]
+    C = np.ascontiguousarray(cands, dtype=np.int32).reshape(-1, 5)
+    J = C.shape[0]
+    a = np.ascontiguousarray(sap, dtype=np.int32)
+    b = np.ascontiguousarray(san, dtype=np.int32)
+    tq = np.empty(J, dtype=np.int32)
+    loss = np.empty(J, dtype=np.int64)
+    best = ctypes.c_int32(-1)
+    lib().or_select_feature(_u8p(P), n, _i32p(C), J, _i32p(a), _i32p(b), int(tau), _i32p(tq),
+                            loss.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(best))
+    return tq, loss, int(best.value)
