@@ -424,6 +424,41 @@ bd_status bd_match_mnn(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t
                        bd_match_result *out, int32_t *mnn);
 
 /* ------------------------------------------------------------------------ */
+/* BAD feature selection (Algorithm 1 with Algorithm 2)                      */
+
+/* Threshold numerator with h = -1 for every patch (theta = -255.1). */
+#define BD_SELECT_QMIN (-2551)
+
+/* One round of the greedy BAD learning of Algorithm 1: for each of J
+ * candidate box pairs, the threshold with the lowest per-step triplet loss
+ *   L_h = sum_i [tau - S_ap[i] - h(a_i) h(p_i) + S_an[i] + h(a_i) h(n_i)]_+
+ * (Sec. III-A; S_ap, S_an: similarities of the bits chosen before) found by
+ * Algorithm 2 in its integer-sorted form, and the best candidate.
+ *  - patches  device, 3 x n uint8 32x32 patches: anchors [0, n), positives
+ *             [n, 2n), negatives [2n, 3n) (the triplets, already mined).
+ *  - sim_ap, sim_an  device, n int32 each.
+ *  - centres  host, J x 4 int32 (x1, y1, x2, y2) box centres in the patch
+ *             frame; sides host, J int32 in [1, 32]; a box covers
+ *             [c - floor(s/2), c - floor(s/2) + s) and pixels outside the patch
+ *             count as 0; |centre| < 2^15.
+ *  - f = (sum1 - sum2) / s^2 is compared with thresholds theta = q / 10 on
+ *    the 0.1 grid: h = +1 iff 10 f <= q, i.e. iff ceil(10 f) <= q, for q in
+ *    [BD_SELECT_QMIN, 2550]; the result is a BAD stump with thr_num = q and
+ *    thr_den = 10.
+ *  - theta_q (device, J int32): the lowest q with the minimal loss of each
+ *    candidate; loss (device, J int64, 8-byte aligned): that loss; best
+ *    (device, one int32): the first candidate with the minimal loss.
+ *  - Scratch: 256 bytes + J x 3n x 2 bytes of keys (processed in passes of
+ *    fewer candidates when that exceeds 1 GiB), plus the candidates.
+ *  - Errors: BD_ERR_INVALID for n < 1 or n > 2^20, J < 1 or J >= 2^20, a side
+ *    outside [1, 32], a centre out of range, null or misaligned pointers,
+ *    or tau outside [-2^20, 2^20]. */
+bd_status bd_select_feature(bd_ctx *ctx, const uint8_t *patches, int n, const int32_t *sim_ap,
+                            const int32_t *sim_an, int tau, const int32_t *centres,
+                            const int32_t *sides, int J, int32_t *theta_q, int64_t *loss,
+                            int32_t *best);
+
+/* ------------------------------------------------------------------------ */
 /* Measurement probes (the paper has no counterpart: they give each kernel's  */
 /* roofline a measured denominator)                                          */
 

@@ -84,6 +84,7 @@ _SIGS = [
     ("bd_bad_describe_noalloc", _I, [_P, _P, _I, _I, _I, _P, _I, _P, _P]),
     ("bd_match_batch", _I, [_P, _P, _I]),
     ("bd_match_mnn", _I, [_P, _P, _I, _P, _I, _I, _I, _I, _I, _P, _P]),
+    ("bd_select_feature", _I, [_P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P, _P]),
     ("bd_probe", _I, [_P, _I, _P, ctypes.c_size_t, ctypes.c_size_t, _I, _P,
                       ctypes.POINTER(ctypes.c_uint64)]),
 ]
@@ -363,6 +364,25 @@ class Context:
                                        ratio_den, int(bool(tensor_cores)), _ptr(out), _ptr(mnn)),
                     "bd_match_mnn")
         return out, mnn
+
+    def select_feature(self, patches, sim_ap, sim_an, tau: int, centres, sides):
+        """bd_select_feature: patches uint8 [3, n, 32, 32] (device), sim_ap / sim_an
+        int32 [n] (device), centres int32 [J, 4] and sides int32 [J] (host numpy).
+        Returns (theta_q int32 [J], loss int64 [J], best int32 [1]) device tensors."""
+        import numpy as np
+        torch = self._torch
+        n = patches.shape[1] if patches.dim() == 4 else patches.shape[0] // 3
+        c = np.ascontiguousarray(centres, dtype=np.int32).reshape(-1, 4)
+        s = np.ascontiguousarray(sides, dtype=np.int32).reshape(-1)
+        J = c.shape[0]
+        tq = torch.empty(J, dtype=torch.int32, device=patches.device)
+        loss = torch.empty(J, dtype=torch.int64, device=patches.device)
+        best = torch.empty(1, dtype=torch.int32, device=patches.device)
+        self._stream()
+        self._check(lib().bd_select_feature(self.handle, _ptr(patches), n, _ptr(sim_ap), _ptr(sim_an),
+                                            int(tau), _np_ptr(c), _np_ptr(s), J, _ptr(tq),
+                                            _ptr(loss), _ptr(best)), "bd_select_feature")
+        return tq, loss, best
 
     def probe(self, kind: int, reps: int, table=None, window_words: int = 0, sink=None) -> int:
         """Enqueues one bd_probe kernel on the current stream; returns the

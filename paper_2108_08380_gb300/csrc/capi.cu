@@ -918,6 +918,51 @@ bd_status bd_match_mnn(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t
     return BD_OK;
 }
 
+bd_status bd_select_feature(bd_ctx *ctx, const uint8_t *patches, int n, const int32_t *sim_ap,
+                            const int32_t *sim_an, int tau, const int32_t *centres,
+                            const int32_t *sides, int J, int32_t *theta_q, int64_t *loss,
+                            int32_t *best)
+{
+    BD_GUARD(ctx);
+    if (n < 1 || n > (1 << 20) || J < 1 || J >= (1 << 20) || !patches || !sim_ap || !sim_an ||
+        !centres || !sides || !theta_q || !loss || !best || ((uintptr_t)loss & 7) ||
+        ((uintptr_t)sim_ap & 3) || ((uintptr_t)sim_an & 3) || ((uintptr_t)theta_q & 3) ||
+        ((uintptr_t)best & 3) || tau < -(1 << 20) || tau > (1 << 20))
+        return set_err(ctx, BD_ERR_INVALID, "bd_select_feature: bad arguments");
+    for (int j = 0; j < J; ++j) {
+        if (sides[j] < 1 || sides[j] > 32)
+            return set_err(ctx, BD_ERR_INVALID, "bd_select_feature: side of candidate %d", j);
+        for (int q = 0; q < 4; ++q)
+            if (centres[4 * j + q] <= -(1 << 15) || centres[4 * j + q] >= (1 << 15))
+                return set_err(ctx, BD_ERR_INVALID, "bd_select_feature: centre of candidate %d", j);
+    }
+    // scratch: [candidates][state + keys], the keys capped at 1 GiB per pass
+    const size_t cand_bytes = align_up((size_t)J * 16, 256) + align_up((size_t)J * 4, 256);
+    size_t work = select_scratch_bytes(n, J);
+    const size_t cap = ((size_t)1 << 30) + 256;
+    if (work > cap)
+        work = cap;
+    if (work < select_scratch_bytes(n, 1))
+        work = select_scratch_bytes(n, 1);
+    bd_status s = ensure_scratch(ctx, cand_bytes + work);
+    if (s != BD_OK)
+        return s;
+    int32_t *d_xy = (int32_t *)ctx->scratch;
+    int32_t *d_side = (int32_t *)((char *)ctx->scratch + align_up((size_t)J * 16, 256));
+    cudaError_t e = cudaMemcpyAsync(d_xy, centres, (size_t)J * 16, cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_side, sides, (size_t)J * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess)
+        return cuda_err(ctx, e, "bd_select_feature: candidate upload");
+    TraceScope scope(ctx, ctx->stream);
+    BD_LAUNCH(ctx,
+              launch_select_feature(patches, n, sim_ap, sim_an, tau, d_xy, d_side, J, theta_q, loss,
+                                    best, (char *)ctx->scratch + cand_bytes, work, ctx->stream),
+              "feature selection kernels");
+    return BD_OK;
+}
+
 bd_status bd_probe(bd_ctx *ctx, int kind, const uint32_t *table, size_t table_words,
                    size_t window_words, int reps, uint32_t *sink, uint64_t *units)
 {
