@@ -262,9 +262,43 @@ def max_over_ranks(x: float, dist, device) -> float:
     return float(t.item())
 
 
+def run_reference_select(args):
+    """The oracle on the feature-selection workload: steps of a bounded number
+    of candidates over all triplets."""
+    import oracle
+    import synth
+    sw = synth.select_workload(1005)
+    n = sw.patches.shape[1]
+    sample = 2
+    cands = np.concatenate([sw.centres[:sample], sw.sides[:sample, None]], axis=1)
+    oracle.select_feature(sw.patches[:, :64], cands[:1], sw.sim_ap[:64], sw.sim_an[:64], sw.tau)
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        oracle.select_feature(sw.patches, cands, sw.sim_ap, sw.sim_an, sw.tau)
+    dt = time.perf_counter() - t0
+    value = max(1, args.steps) * sample / dt
+    print(json.dumps({
+        "impl": "reference", "metric": "BAD feature-selection rounds: candidates evaluated per second "
+        "(Algorithm 1 with Algorithm 2, 0.1 threshold grid)", "value": value, "unit": "candidates/s",
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64 (exact integer)", "data": "synthetic",
+        "config": {"workload": f"{n} triplets, {sample} of the 1000 candidates per step"},
+        "cpu_baseline": {"value": value, "unit": "candidates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} candidates over all {n} triplets per step, single-threaded C"},
+        "e2e": {"value": value, "unit": "candidates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
+        return
+    if args.workload == "select":
+        return run_reference_select(args)
+    if args.workload == "train":
+        print(json.dumps({"impl": "reference", "unavailable": "the training step's oracle is an FP64 "
+                          "gradient check on small batches; use --workload plain|large|batch|select"}))
         return
     wl = Workload(args.workload)
     sample = args.ref_sample_kp
@@ -791,13 +825,125 @@ def run_train(args):
                       "kernel_ms": kern}), flush=True)
 
 
+def run_select(args):
+    """Feature-selection workload (Algorithm 1 round with Algorithm 2): 65536
+    triplets of uint8 32x32 patches, 1000 candidate box pairs; one step = one
+    bd_select_feature call (keys of every candidate on every patch, threshold
+    search per candidate, best candidate)."""
+    import torch
+    import paper_2108_08380_gb300 as bd
+    import synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    sw = synth.select_workload(1005 + 100 * rank)
+    n, J = sw.patches.shape[1], sw.centres.shape[0]
+    ctx = bd.Context(local)
+    dP = torch.from_numpy(sw.patches).cuda()
+    dap = torch.from_numpy(sw.sim_ap).cuda()
+    dan = torch.from_numpy(sw.sim_an).cuda()
+    step = lambda: ctx.select_feature(dP, dap, dan, sw.tau, sw.centres, sw.sides)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    props = torch.cuda.get_device_properties(local)
+    sampler = ClockSampler(getattr(props, "uuid", None) and f"GPU-{props.uuid}" or str(local))
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = bd.kernel_launches()
+    t0 = time.time()
+    for s in range(K):
+        torch.cuda._sleep(1_000_000)
+        ev[s][0].record()
+        step()
+        ev[s][1].record()
+    torch.cuda.synchronize()
+    t1 = time.time()
+    launches = bd.kernel_launches() - launches0
+    time.sleep(0.15)
+    sampler.stop()
+    clocks = sampler.summary(t0 - 0.05, t1 + 0.05)
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    # kernel times from a traced pass
+    ctx.trace(True)
+    kern = {}
+    for _ in range(K):
+        torch.cuda._sleep(1_000_000)
+        ctx.trace_reset()
+        step()
+        torch.cuda.synchronize()
+        for name, kms in ctx.trace_read():
+            kern[name] = kern.get(name, 0.0) + kms / K
+    ctx.trace(False)
+    peaks, kind = load_peaks()
+    key_bytes = J * 3 * n * 2
+    traffic = {"select_keys": 3 * n * 1024 + key_bytes, "select_threshold": key_bytes + 8 * n}
+    dom = max(kern, key=kern.get)
+    ach = traffic[dom] / (kern[dom] * 1e-3) / 1e9
+    roof = {"kernel": dom, "ms": kern[dom], "bound": "hbm", "achieved": ach,
+            "peak": float(peaks["hbm_gbs"]), "unit": "GB/s", "frac": ach / float(peaks["hbm_gbs"]),
+            "traffic": None, "peak_source": f"{kind} HBM copy",
+            "algorithmic_bytes": traffic[dom]}
+    # end to end: patches and similarities from pinned host memory, results back
+    hP = torch.from_numpy(sw.patches).pin_memory()
+    hap = torch.from_numpy(sw.sim_ap).pin_memory()
+    han = torch.from_numpy(sw.sim_an).pin_memory()
+    out_h = [torch.empty(J, dtype=torch.int32).pin_memory(), torch.empty(J, dtype=torch.int64).pin_memory(),
+             torch.empty(1, dtype=torch.int32).pin_memory()]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(3, min(K, 20))
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        dP.copy_(hP, non_blocking=True)
+        dap.copy_(hap, non_blocking=True)
+        dan.copy_(han, non_blocking=True)
+        outs = step()
+        for h, d in zip(out_h, outs):
+            h.copy_(d, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / reps
+    line = {
+        "metric": "BAD feature-selection rounds: candidates evaluated per second (Algorithm 1 with "
+                  "Algorithm 2, 0.1 threshold grid)",
+        "value": world * J / (ms * 1e-3), "unit": "candidates/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8/int16/int32 (exact integer)", "data": "synthetic",
+        "config": {"workload": f"{n} triplets of uint8 32x32 patches, {J} candidate box pairs "
+                               "(sides 1-15), 128 earlier bits, tau 64",
+                   "l2": "inputs and the 393 MB key matrix exceed L2"},
+        "triplet_candidate_evals_per_s": world * J * n / (ms * 1e-3),
+        "kernel_ms": kern, "roofline": roof, "clocks": clocks,
+        "e2e": {"value": world * J / (e2e_ms * 1e-3), "unit": "candidates/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(sw.patches.nbytes + sw.sim_ap.nbytes + sw.sim_an.nbytes),
+                "d2h_bytes_per_step": int(J * 12 + 4)},
+        "gpu_launches": int(launches),
+    }
+    if not args.no_cpu_baseline and rank == 0:
+        import oracle
+        sample = 2
+        t0 = time.perf_counter()
+        cands = np.concatenate([sw.centres[:sample], sw.sides[:sample, None]], axis=1)
+        oracle.select_feature(sw.patches, cands, sw.sim_ap, sw.sim_an, sw.tau)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": sample / dt, "unit": "candidates/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"{sample} candidates over all {n} triplets, single-threaded C, "
+                                          f"{dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["plain", "large", "batch", "train"], default="plain")
+    ap.add_argument("--workload", choices=["plain", "large", "batch", "train", "select"],
+                    default="plain")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-components", action="store_true",
@@ -815,6 +961,8 @@ def main():
         run_reference(args)
     elif args.workload == "train":
         run_train(args)
+    elif args.workload == "select":
+        run_select(args)
     else:
         run_ours(args)
 

@@ -336,3 +336,32 @@ def triplet_workload(seed: int = 1003, n: int = 65536, n_images: int = 4,
             if len(sel2):
                 out[2, c0 + sel2] = _sample_patches(imgs[im], nx[sel2], ny[sel2], I[sel2])
     return TripletWorkload(out)
+
+
+class SelectWorkload:
+    """Inputs of one feature-selection round: uint8 triplet patches, the
+    similarities of the bits chosen before, candidate box pairs."""
+
+    def __init__(self, patches, sim_ap, sim_an, tau, centres, sides):
+        self.patches = patches
+        self.sim_ap = sim_ap
+        self.sim_an = sim_an
+        self.tau = tau
+        self.centres = centres
+        self.sides = sides
+
+
+def select_workload(seed: int = 1005, n: int = 65536, J: int = 1000, prev_bits: int = 128,
+                    max_side: int = 15) -> SelectWorkload:
+    """n triplets of uint8 32x32 patches (the training generator, rounded),
+    similarities of `prev_bits` earlier bits drawn as 2 Binomial(prev_bits, p) -
+    prev_bits with p = 0.8 for matching and 0.5 for non-matching pairs, margin
+    tau = prev_bits / 2, and J candidates: centres U{0..31}^2, sides U{1..max_side}."""
+    rng = np.random.default_rng(seed)
+    tw = triplet_workload(seed, n=n)
+    patches = np.clip(np.rint(tw.patches), 0, 255).astype(np.uint8)
+    sim_ap = (2 * rng.binomial(prev_bits, 0.8, size=n) - prev_bits).astype(np.int32)
+    sim_an = (2 * rng.binomial(prev_bits, 0.5, size=n) - prev_bits).astype(np.int32)
+    centres = rng.integers(0, 32, size=(J, 4)).astype(np.int32)
+    sides = rng.integers(1, max_side + 1, size=J).astype(np.int32)
+    return SelectWorkload(patches, sim_ap, sim_an, prev_bits // 2, centres, sides)
