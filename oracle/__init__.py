@@ -185,6 +185,19 @@ def hs_hist(patches) -> np.ndarray:
     return H
 
 
+HS_TRILINEAR, HS_CLIP, HS_ROOT = 1, 2, 4
+
+
+def hs_hist_variant(patches, flags: int) -> np.ndarray:
+    """float64 [n, 128] histograms with the SIFT variants in `flags`
+    (HS_TRILINEAR, HS_CLIP, HS_ROOT), unit L2 norm."""
+    P = np.ascontiguousarray(patches, dtype=np.float64).reshape(-1, 1024)
+    H = np.empty((P.shape[0], 128), dtype=np.float64)
+    for i in range(P.shape[0]):
+        lib().or_hs_hist_variant(_f64p(P[i]), int(flags), _f64p(H[i]))
+    return H
+
+
 def hs_hist_raw(patch):
     """(unnormalised histogram [128], its L2 norm) of one 32x32 patch."""
     P = np.ascontiguousarray(patch, dtype=np.float64).reshape(1024)

@@ -264,6 +264,79 @@ double or_hs_hist_raw(const double *P, double *H)
     return sqrt(nn);
 }
 
+/* SIFT variants of the histogram before hashing (the paper names RootSIFT,
+ * Sec. II; SIFT's trilinear binning and 0.2 clip are Lowe's).  flags:
+ *   1 trilinear: each vote is shared by the two nearest cell rows and cell
+ *     columns (cell c's centre at pixel 8c + 3.5, weight 1 - |x - centre| / 8,
+ *     cells outside the 4x4 grid dropped) instead of going to the pixel's cell;
+ *   2 clip: L2-normalise, clip every entry at 0.2, L2-normalise again;
+ *   4 root (RootSIFT): divide by the L1 norm, take square roots (unit L2 norm).
+ * Applied in the order binning, clip, root; a zero histogram stays zero. */
+void or_hs_hist_variant(const double *P, int flags, double *h)
+{
+    double H[128];
+    if (flags & 1) {
+        for (int q = 0; q < 128; ++q)
+            H[q] = 0.0;
+        for (int i = 0; i < 32; ++i) {
+            for (int j = 0; j < 32; ++j) {
+                const int jl = j > 0 ? j - 1 : 0, jr = j < 31 ? j + 1 : 31;
+                const int iu = i > 0 ? i - 1 : 0, id = i < 31 ? i + 1 : 31;
+                const double gx = 0.5 * (P[i * 32 + jr] - P[i * 32 + jl]);
+                const double gy = 0.5 * (P[id * 32 + j] - P[iu * 32 + j]);
+                const double m = sqrt(gx * gx + gy * gy);
+                double phi = atan2(gy, gx);
+                if (phi < 0.0)
+                    phi += 2.0 * OR_PI;
+                const double t = phi * 8.0 / (2.0 * OR_PI);
+                const double w1 = t - floor(t);
+                const int b0 = ((int)floor(t)) % 8, b1 = (b0 + 1) % 8;
+                const double di = (double)i - 15.5, dj = (double)j - 15.5;
+                const double g = exp(-(di * di + dj * dj) / (2.0 * 16.0 * 16.0));
+                for (int ci = 0; ci < 4; ++ci) {
+                    const double wy = 1.0 - fabs((double)i - (8.0 * ci + 3.5)) / 8.0;
+                    if (wy <= 0.0)
+                        continue;
+                    for (int cj = 0; cj < 4; ++cj) {
+                        const double wx = 1.0 - fabs((double)j - (8.0 * cj + 3.5)) / 8.0;
+                        if (wx <= 0.0)
+                            continue;
+                        const int cell = ci * 4 + cj;
+                        H[cell * 8 + b0] += g * m * wy * wx * (1.0 - w1);
+                        H[cell * 8 + b1] += g * m * wy * wx * w1;
+                    }
+                }
+            }
+        }
+    } else {
+        or_hs_hist_raw(P, H);
+    }
+    double n2 = 0.0;
+    for (int q = 0; q < 128; ++q)
+        n2 += H[q] * H[q];
+    double nrm = sqrt(n2);
+    for (int q = 0; q < 128; ++q)
+        h[q] = nrm > 0.0 ? H[q] / nrm : 0.0;
+    if ((flags & 2) && nrm > 0.0) {
+        n2 = 0.0;
+        for (int q = 0; q < 128; ++q) {
+            if (h[q] > 0.2)
+                h[q] = 0.2;
+            n2 += h[q] * h[q];
+        }
+        nrm = sqrt(n2);
+        for (int q = 0; q < 128; ++q)
+            h[q] /= nrm;
+    }
+    if (flags & 4) {
+        double l1 = 0.0;
+        for (int q = 0; q < 128; ++q)
+            l1 += h[q];
+        for (int q = 0; q < 128; ++q)
+            h[q] = l1 > 0.0 ? sqrt(h[q] / l1) : 0.0;
+    }
+}
+
 /* L2-normalised histogram h of n patches (patches: n x 1024, hist: n x 128). */
 void or_hs_hist(const double *patches, int n, double *hist)
 {

@@ -208,3 +208,84 @@ def test_describe_consistent_with_stages():
     assert np.array_equal(out["hist"], h)
     m, bits = oracle.hs_project(h, hs.W, hs.b)
     assert np.array_equal(out["bits"], bits)
+
+
+# ---------------------------------------------------------------------------
+# SIFT variants before hashing (trilinear binning, 0.2 clip, RootSIFT)
+
+def _ramp(a=3.0):
+    j = np.arange(32, dtype=np.float64)
+    return np.tile(a * j, (32, 1))
+
+
+def test_variant_none_is_the_base_histogram():
+    rng = np.random.default_rng(3)
+    P = rng.uniform(0, 255, size=(4, 32, 32))
+    assert np.allclose(oracle.hs_hist_variant(P, 0), oracle.hs_hist(P), atol=1e-15)
+
+
+def test_trilinear_ramp_is_separable_and_symmetric():
+    """Horizontal ramp: every vote in bin 0 with weight g_i g_j m_j, so the
+    4x4 cell matrix of bin 0 has rank one and the grid's mirror symmetries."""
+    h = oracle.hs_hist_variant(_ramp(), oracle.HS_TRILINEAR)[0].reshape(4, 4, 8)
+    assert np.allclose(h[:, :, 1:], 0.0)
+    M = h[:, :, 0]
+    assert np.linalg.matrix_rank(M, tol=1e-12) == 1
+    assert np.allclose(M, M[::-1, :]) and np.allclose(M, M[:, ::-1])
+    base = oracle.hs_hist(_ramp())[0].reshape(4, 4, 8)[:, :, 0]
+    assert not np.allclose(M / M.sum(), base / base.sum())  # the binning did change
+
+
+def test_trilinear_vertical_edge_weights():
+    """A step between columns 4 and 5 has gradient (of equal magnitude) at
+    columns 4 and 5 only; with cell centres at 3.5 and 11.5 cell column 1 over
+    cell column 0 is (w1(4) g4 + w1(5) g5) / (w0(4) g4 + w0(5) g5), w the
+    linear column weights and g the Gaussian column factors; cell columns 2
+    and 3 get nothing."""
+    P = np.zeros((32, 32))
+    P[:, 5:] = 200.0
+    h = oracle.hs_hist_variant(P, oracle.HS_TRILINEAR)[0].reshape(4, 4, 8)
+    col = h[:, :, 0].sum(axis=0)
+    assert np.allclose(col[2:], 0.0)
+    g = lambda j: np.exp(-((j - 15.5) ** 2) / 512.0)
+    w = lambda j, c: max(0.0, 1.0 - abs(j - (8 * c + 3.5)) / 8.0)
+    ratio = (w(4, 1) * g(4) + w(5, 1) * g(5)) / (w(4, 0) * g(4) + w(5, 0) * g(5))
+    assert np.isclose(col[1] / col[0], ratio, rtol=1e-12)
+
+
+def test_clip_keeps_order_and_scales_the_small_entries():
+    rng = np.random.default_rng(5)
+    P = rng.uniform(0, 255, size=(3, 32, 32))
+    P[0] = _ramp()
+    base = oracle.hs_hist(P)
+    clip = oracle.hs_hist_variant(P, oracle.HS_CLIP)
+    for b, c in zip(base, clip):
+        assert np.isclose(np.linalg.norm(c), 1.0)
+        small = (b > 0) & (b < 0.2)
+        big = b >= 0.2
+        if small.any():
+            s = c[small] / b[small]
+            assert np.allclose(s, s[0]) and s[0] >= 1.0 - 1e-12  # one common factor
+        if big.any():
+            assert np.allclose(c[big], c[big][0])  # clipped entries become equal
+            assert c[big][0] >= c[small].max() - 1e-12 if small.any() else True
+
+
+def test_rootsift_is_the_hellinger_kernel():
+    """RootSIFT(x) . RootSIFT(y) = sum_i sqrt(x_i y_i) of the L1-normalised
+    histograms (the Hellinger kernel), and RootSIFT has unit L2 norm."""
+    rng = np.random.default_rng(6)
+    P = rng.uniform(0, 255, size=(5, 32, 32))
+    base = oracle.hs_hist(P)
+    r = oracle.hs_hist_variant(P, oracle.HS_ROOT)
+    l1 = base / base.sum(axis=1, keepdims=True)
+    for a in range(5):
+        assert np.isclose(np.linalg.norm(r[a]), 1.0)
+        for b in range(5):
+            assert np.isclose(r[a] @ r[b], np.sqrt(l1[a] * l1[b]).sum(), rtol=1e-12)
+
+
+def test_variants_of_a_flat_patch_stay_zero():
+    P = np.full((32, 32), 42.0)
+    for f in range(8):
+        assert np.all(oracle.hs_hist_variant(P, f) == 0.0)
