@@ -163,7 +163,11 @@ bd_status bd_bad_params_table(const bd_bad_params *p, int32_t *offsets, int32_t 
 /* HashSIFT parameters (Sec. III-B)                                          */
 
 #define BD_HS_FP32 0        /* projection on CUDA cores in FP32 */
-#define BD_HS_BF16_RESCUE 1 /* tcgen05 BF16 x BF16 -> FP32 (split head/tail), FP32 re-check near 0 */
+#define BD_HS_BF16_RESCUE 1
+/* SIFT variants of the histogram before hashing (bd_hs_params_set_variant) */
+#define BD_HS_VARIANT_TRILINEAR 1 /* votes shared by the 2 x 2 nearest cells */
+#define BD_HS_VARIANT_CLIP 2      /* L2-normalise, clip at 0.2, renormalise */
+#define BD_HS_VARIANT_ROOT 4      /* RootSIFT: L1-normalise, square roots */ /* tcgen05 BF16 x BF16 -> FP32 (split head/tail), FP32 re-check near 0 */
 
 /* Learned hash B = [W^T | b], copied from host memory.
  *  nbits     256 or 512.
@@ -181,6 +185,18 @@ bd_status bd_bad_params_table(const bd_bad_params *p, int32_t *offsets, int32_t 
  *            for every bit (a smaller band may differ from FP32 mode). */
 bd_status bd_hs_params_create(bd_ctx *ctx, int nbits, const float *W, const float *bias,
                               float spacing, int precision, float band, bd_hs_params **out);
+/* Selects SIFT variants of the histogram for the descriptor calls that use
+ * p (the paper's HashSIFT hashes the plain histogram; it names RootSIFT as
+ * the key improvement of histogram descriptors, Sec. II): any OR of
+ * BD_HS_VARIANT_TRILINEAR (each vote shared by the two nearest cell rows and
+ * cell columns, cell c centred at pixel 8c + 3.5 with weight 1 - |d| / 8),
+ * BD_HS_VARIANT_CLIP (Lowe's 0.2 clip with renormalisation) and
+ * BD_HS_VARIANT_ROOT (L1 normalisation and square roots); applied in that
+ * order.  0 restores the plain histogram.  bd_hashsift_describe supports all
+ * of them; bd_batch_create refuses parameters with TRILINEAR
+ * (BD_ERR_UNSUPPORTED).  Errors: BD_ERR_INVALID for other bits. */
+bd_status bd_hs_params_set_variant(bd_hs_params *p, int flags);
+
 void bd_hs_params_destroy(bd_hs_params *p);
 
 /* ------------------------------------------------------------------------ */

@@ -30,6 +30,9 @@ BD_FLAG_INVALID_KEYPOINT = 0x1
 BD_FLAG_TIMEOUT = 0x2
 BD_HS_FP32 = 0
 BD_HS_BF16_RESCUE = 1
+BD_HS_VARIANT_TRILINEAR = 1
+BD_HS_VARIANT_CLIP = 2
+BD_HS_VARIANT_ROOT = 4
 BD_PROBE_GATHER = 0
 BD_PROBE_POPC = 1
 BD_PROBE_FFMA = 2
@@ -83,6 +86,7 @@ _SIGS = [
     ("bd_train_backward", _I, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     ("bd_bad_describe_noalloc", _I, [_P, _P, _I, _I, _I, _P, _I, _P, _P]),
     ("bd_match_batch", _I, [_P, _P, _I]),
+    ("bd_hs_params_set_variant", _I, [_P, _I]),
     ("bd_match_mnn", _I, [_P, _P, _I, _P, _I, _I, _I, _I, _I, _P, _P]),
     ("bd_select_feature", _I, [_P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P, _P]),
     ("bd_probe", _I, [_P, _I, _P, ctypes.c_size_t, ctypes.c_size_t, _I, _P,
@@ -639,6 +643,12 @@ class HsParamsHandle:
         ctx._check(st, "bd_hs_params_create")
         self.handle = h
         ctx._adopt(self)
+
+    def set_variant(self, flags: int):
+        """bd_hs_params_set_variant: OR of BD_HS_VARIANT_* (0 = the plain histogram)."""
+        st = lib().bd_hs_params_set_variant(self.handle, int(flags))
+        if st != BD_OK:
+            raise BindescError(st, "bd_hs_params_set_variant")
 
     def close(self):
         if getattr(self, "handle", None):

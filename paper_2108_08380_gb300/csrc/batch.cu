@@ -40,6 +40,7 @@ struct BatchKernelArgs {
     int n_img, n_tiles, n_kp, n_bad_items, bad_per_item;
     int hs_items;            // ceil(n_kp / hs_per_item) if HashSIFT is on, else 0
     int hs_per_item;         // 1: the CTA shares a keypoint; 4: one keypoint per warp
+    int hs_flags;            // BD_HS_VARIANT_CLIP / _ROOT
     int hs_first;
     int hs_pre_final, hs_pre_bad;  // HashSIFT items queued before the pass-2 tiles / the BAD items
     uint32_t *ii, *carry;
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                 const int im = find_image(A.imgs, A.n_img, k, 1);
                 const BatchImageDev &I = A.imgs[im];
                 dev::hs_hist_image_cta<false>(U.h[0], A.img_ptr[im], I.w, I.h, I.pitch, A.kps[k],
-                                       A.spacing, A.hist, (size_t)k, A.status);
+                                       A.spacing, A.hist, (size_t)k, A.status, A.hs_flags);
             } else {
                 // four keypoints, one per warp
                 const int k = idx * 4 + (t >> 5);
@@ -187,7 +188,8 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                     const int im = find_image(A.imgs, A.n_img, k, 1);
                     const BatchImageDev &I = A.imgs[im];
                     dev::hs_hist_image_warp<false>(U.h[t >> 5], A.img_ptr[im], I.w, I.h, I.pitch,
-                                            A.kps[k], A.spacing, A.hist, (size_t)k, A.status);
+                                            A.kps[k], A.spacing, A.hist, (size_t)k, A.status,
+                                            A.hs_flags);
                 }
             }
             __syncthreads();
@@ -300,6 +302,7 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     A.bad_nw = b->bad ? b->bad->nbits / 32 : 8;
     A.bad_out = bad_out;
     A.spacing = b->hs ? b->hs->spacing : 1.f;
+    A.hs_flags = b->hs ? b->hs->variant : 0;
     A.hist = b->d_hist;
     A.kps = kps;
     A.status = ctx->status;
@@ -393,6 +396,9 @@ bd_status bd_batch_create(bd_ctx *ctx, const bd_bad_params *bad, const bd_hs_par
     *out = nullptr;
     if ((!bad && !hs) || n_img < 1 || n_img > 65536 || !w || !h || !pitch || !kp_offsets)
         return set_err(ctx, BD_ERR_INVALID, "bd_batch_create: bad arguments");
+    if (hs && (hs->variant & BD_HS_VARIANT_TRILINEAR))
+        return set_err(ctx, BD_ERR_UNSUPPORTED,
+                       "bd_batch_create: trilinear binning is not available in the batched kernel");
     if (kp_offsets[0] != 0)
         return set_err(ctx, BD_ERR_INVALID, "bd_batch_create: kp_offsets[0] must be 0");
     bd_batch *b = new bd_batch();
@@ -533,6 +539,9 @@ bd_status bd_describe_batch(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
         return BD_ERR_INVALID;
     if ((b->n_kp > 0 && !kps) || (!bad_out && !hs_out) || (bad_out && !b->bad) || (hs_out && !b->hs))
         return set_err(ctx, BD_ERR_INVALID, "bd_describe_batch: bad arguments");
+    if (b->hs && (b->hs->variant & BD_HS_VARIANT_TRILINEAR))
+        return set_err(ctx, BD_ERR_UNSUPPORTED,
+                       "bd_describe_batch: trilinear binning is not available in the batched kernel");
     for (int i = 0; i < b->n_img; ++i)
         if (!imgs[i])
             return set_err(ctx, BD_ERR_INVALID, "bd_describe_batch: image %d is NULL", i);
@@ -560,8 +569,10 @@ bd_status bd_describe_batch(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     key.push_back(kps);
     key.push_back(bad_out);
     key.push_back(hs_out);
-    // the graph holds the trace events or not: re-capture when tracing is switched
+    // the graph holds the trace events or not, and the variant flags as a
+    // kernel argument: re-capture when either changes
     key.push_back(reinterpret_cast<const void *>((uintptr_t)(ctx->trace ? 1 : 0)));
+    key.push_back(reinterpret_cast<const void *>((uintptr_t)(b->hs ? b->hs->variant : 0)));
     if (!b->gexec || key != b->gkey) {
         drop_graph(b);
         cudaGraph_t g = nullptr;

@@ -87,6 +87,7 @@ struct bd_hs_params {
     bd_ctx *ctx = nullptr;
     int nbits = 0;
     int precision = BD_HS_FP32;
+    int variant = 0;  // BD_HS_VARIANT_* flags
     float spacing = 1.f;
     float *d_W = nullptr;           // [128][K] FP32 (row-major, as given)
     float *d_Wt = nullptr;          // [K][128] FP32 (per-bit rows, for the FP32 re-check)

@@ -620,6 +620,16 @@ bd_status bd_hs_params_create(bd_ctx *ctx, int nbits, const float *W, const floa
     return BD_OK;
 }
 
+bd_status bd_hs_params_set_variant(bd_hs_params *p, int flags)
+{
+    if (!p)
+        return BD_ERR_INVALID;
+    if (flags & ~(BD_HS_VARIANT_TRILINEAR | BD_HS_VARIANT_CLIP | BD_HS_VARIANT_ROOT))
+        return set_err(p->ctx, BD_ERR_INVALID, "bd_hs_params_set_variant: unknown flags 0x%x", flags);
+    p->variant = flags;
+    return BD_OK;
+}
+
 void bd_hs_params_destroy(bd_hs_params *p)
 {
     if (!p)

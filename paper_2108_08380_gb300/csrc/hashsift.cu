@@ -18,19 +18,33 @@ using dev::PS;
 template <bool Coop>
 __global__ void __launch_bounds__(NT) hs_hist_image_kernel(
     const uint8_t *__restrict__ img, int w, int h, int pitch, const bd_keypoint *__restrict__ kps,
-    int n, float spacing, float *__restrict__ hist, DeviceStatus *status)
+    int n, float spacing, float *__restrict__ hist, DeviceStatus *status, int flags)
 {
     __shared__ dev::WarpHist S[Coop ? 1 : NT / 32];
     if (Coop) {
         for (int k = blockIdx.x; k < n; k += gridDim.x)
             dev::hs_hist_image_cta<true>(S[0], img, w, h, pitch, kps[k], spacing, hist, (size_t)k,
-                                   status);
+                                         status, flags);
     } else {
         const int warp = threadIdx.x >> 5;
         for (int k = blockIdx.x * (NT / 32) + warp; k < n; k += gridDim.x * (NT / 32))
-            dev::hs_hist_image_warp<true>(S[warp], img, w, h, pitch, kps[k], spacing, hist, (size_t)k,
-                                    status);
+            dev::hs_hist_image_warp<true>(S[warp], img, w, h, pitch, kps[k], spacing, hist,
+                                          (size_t)k, status, flags);
     }
+}
+
+// Trilinear-binned histograms (SIFT variant), one warp per keypoint, two
+// warps per CTA (13 KB of shared memory each).
+constexpr int NT_TRI = 64;
+__global__ void __launch_bounds__(NT_TRI) hs_hist_image_tri_kernel(
+    const uint8_t *__restrict__ img, int w, int h, int pitch, const bd_keypoint *__restrict__ kps,
+    int n, float spacing, float *__restrict__ hist, DeviceStatus *status, int flags)
+{
+    __shared__ dev::WarpHistTri S[NT_TRI / 32];
+    const int warp = threadIdx.x >> 5;
+    for (int k = blockIdx.x * (NT_TRI / 32) + warp; k < n; k += gridDim.x * (NT_TRI / 32))
+        dev::hs_hist_image_warp_tri(S[warp], img, w, h, pitch, kps[k], spacing, hist, (size_t)k,
+                                    status, flags);
 }
 
 __global__ void __launch_bounds__(NT) hs_hist_patch_kernel(const float *__restrict__ patches,
@@ -42,7 +56,7 @@ __global__ void __launch_bounds__(NT) hs_hist_patch_kernel(const float *__restri
     for (int k = blockIdx.x * (NT / 32) + warp; k < n; k += gridDim.x * (NT / 32)) {
         dev::PatchMem src;
         src.p = patches + (size_t)k * PS * PS;
-        dev::hs_hist_warp(S[warp], src, true, lane, hist, (size_t)k, norm_out);
+        dev::hs_hist_warp(S[warp], src, true, lane, hist, (size_t)k, norm_out, 0);
     }
 }
 
@@ -207,13 +221,17 @@ cudaError_t launch_hs_hist_image(const bd_hs_params *p, const uint8_t *img, int 
                                  DeviceStatus *status, cudaStream_t st,
                                  int sm_count)
 {
+    const int flags = p->variant;
     // few keypoints: the CTA shares each one (latency); many: one per warp (throughput)
-    if (n <= 2 * 12 * sm_count)
+    if (flags & BD_HS_VARIANT_TRILINEAR)
+        hs_hist_image_tri_kernel<<<grid_for((n + 1) / 2, sm_count, 16), NT_TRI, 0, st>>>(
+            img, w, h, pitch, kps, n, p->spacing, hist, status, flags);
+    else if (n <= 2 * 12 * sm_count)
         hs_hist_image_kernel<true><<<grid_for(n, sm_count, 12), NT, 0, st>>>(
-            img, w, h, pitch, kps, n, p->spacing, hist, status);
+            img, w, h, pitch, kps, n, p->spacing, hist, status, flags);
     else
         hs_hist_image_kernel<false><<<grid_for((n + 3) / 4, sm_count, 12), NT, 0, st>>>(
-            img, w, h, pitch, kps, n, p->spacing, hist, status);
+            img, w, h, pitch, kps, n, p->spacing, hist, status, flags);
     trace_kernel(st, "hs_hist_image");
     note_launches(1);
     return cudaGetLastError();

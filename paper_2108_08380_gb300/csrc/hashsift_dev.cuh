@@ -410,13 +410,92 @@ __device__ __forceinline__ void vote_px(WarpHist &S, int lane, int i, float up, 
     col[b1 * 32] += v1;
 }
 
+// Zeroes the lane-private histogram (warp mode: all four cell rows).
+__device__ __forceinline__ void priv_zero_warp(WarpHist &S, int lane)
+{
+    float4 *z = reinterpret_cast<float4 *>(&S.priv[0][0][0]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        z[q * 32 + lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+__device__ __forceinline__ float warp_sum_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// SIFT variants after L2 normalisation (flags: HS_CLIP 0.2 clip and
+// renormalise, HS_ROOT L1-normalise and take square roots) of a histogram
+// spread over the warp, n entries per lane.
+template <int N>
+__device__ __forceinline__ void variants_warp(float (&h)[N], int flags)
+{
+    if (flags & BD_HS_VARIANT_CLIP) {
+        float ss = 0.0f;
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            h[q] = fminf(h[q], 0.2f);
+            ss += h[q] * h[q];
+        }
+        const float nrm = sqrtf(warp_sum_f(ss));
+#pragma unroll
+        for (int q = 0; q < N; ++q)
+            h[q] = nrm > 0.0f ? h[q] / nrm : 0.0f;
+    }
+    if (flags & BD_HS_VARIANT_ROOT) {
+        float l1 = 0.0f;
+#pragma unroll
+        for (int q = 0; q < N; ++q)
+            l1 += h[q];
+        l1 = warp_sum_f(l1);
+#pragma unroll
+        for (int q = 0; q < N; ++q)
+            h[q] = l1 > 0.0f ? sqrtf(h[q] / l1) : 0.0f;
+    }
+}
+
+// Cell sums, L2 norm, variants and output of a warp-mode histogram: lane
+// (cell column cj, bin b) owns entries ci*32 + lane, ci = 0..3.
+__device__ __forceinline__ void warp_finish(WarpHist &S, int lane, bool valid,
+                                            float *__restrict__ hist, size_t k,
+                                            float *__restrict__ norm_out, int flags)
+{
+    const int cj = lane >> 3, b = lane & 7;
+    float H[4];
+    float ss = 0.0f;
+#pragma unroll
+    for (int ci = 0; ci < 4; ++ci) {
+        float s = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            s += S.priv[ci][b][cj * 8 + ((q + b) & 7)];
+        H[ci] = s;
+        ss += s * s;
+    }
+    const float nrm = sqrtf(warp_sum_f(ss));
+    if (norm_out && lane == 0)
+        norm_out[k] = valid ? nrm : 0.0f;
+#pragma unroll
+    for (int ci = 0; ci < 4; ++ci)
+        H[ci] = (valid && nrm > 0.0f) ? H[ci] / nrm : 0.0f;
+    if (flags)
+        variants_warp<4>(H, flags);
+#pragma unroll
+    for (int ci = 0; ci < 4; ++ci)
+        hist[k * kHistDim + ci * 32 + lane] = H[ci];
+    __syncwarp();
+}
+
 // Histogram of one keypoint by one warp: rows from `src` (a ColSampler or a
 // PatchMem), output like the oracle's [cell][bin] order, L2-normalised,
 // with the optional norm.
 template <class Src>
 __device__ __forceinline__ void hs_hist_warp(WarpHist &S, const Src &src, bool valid, int lane,
                                              float *__restrict__ hist, size_t k,
-                                             float *__restrict__ norm_out)
+                                             float *__restrict__ norm_out, int flags)
 {
     {
         float4 *z = reinterpret_cast<float4 *>(&S.priv[0][0][0]);
@@ -448,31 +527,46 @@ __device__ __forceinline__ void hs_hist_warp(WarpHist &S, const Src &src, bool v
         }
     }
     __syncwarp();
-    // entry (cell row ci, cell column cj, bin b) = ci*32 + lane, lane = cj*8 + b
+    warp_finish(S, lane, valid, hist, k, norm_out, flags);
+}
+
+// CTA-wide sum of one float per thread (the four warps of a 128-thread CTA).
+__device__ __forceinline__ float cta_sum4(WarpHist &S, float v, int lane, int w)
+{
+    v = warp_sum_f(v);
+    __syncthreads();  // earlier readers of wss are done
+    if (lane == 0)
+        S.wss[w] = v;
+    __syncthreads();
+    return S.wss[0] + S.wss[1] + S.wss[2] + S.wss[3];
+}
+
+// Cell sums of warp w's cell row, L2 norm over the CTA, variants, output.
+__device__ __forceinline__ void cta_finish(WarpHist &S, int t, bool valid,
+                                           float *__restrict__ hist, size_t k,
+                                           float *__restrict__ norm_out, int flags)
+{
+    const int lane = t & 31, w = t >> 5;
     const int cj = lane >> 3, b = lane & 7;
-    float H[4];
-    float ss = 0.0f;
+    float H = 0.0f;
 #pragma unroll
-    for (int ci = 0; ci < 4; ++ci) {
-        float s = 0.0f;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            s += S.priv[ci][b][cj * 8 + ((q + b) & 7)];
-        H[ci] = s;
-        ss += s * s;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        ss += __shfl_xor_sync(kFull, ss, o);
-    const float nrm = sqrtf(ss);
-    if (norm_out && lane == 0)
+    for (int q = 0; q < 8; ++q)
+        H += S.priv[w][b][cj * 8 + ((q + b) & 7)];
+    const float nrm = sqrtf(cta_sum4(S, H * H, lane, w));
+    if (norm_out && t == 0)
         norm_out[k] = valid ? nrm : 0.0f;
-#pragma unroll
-    for (int ci = 0; ci < 4; ++ci) {
-        const float hv = (valid && nrm > 0.0f) ? H[ci] / nrm : 0.0f;
-        hist[k * kHistDim + ci * 32 + lane] = hv;
+    float hv = (valid && nrm > 0.0f) ? H / nrm : 0.0f;
+    if (flags & BD_HS_VARIANT_CLIP) {
+        hv = fminf(hv, 0.2f);
+        const float n2 = sqrtf(cta_sum4(S, hv * hv, lane, w));
+        hv = n2 > 0.0f ? hv / n2 : 0.0f;
     }
-    __syncwarp();
+    if (flags & BD_HS_VARIANT_ROOT) {
+        const float l1 = cta_sum4(S, hv, lane, w);
+        hv = l1 > 0.0f ? sqrtf(hv / l1) : 0.0f;
+    }
+    hist[k * kHistDim + w * 32 + lane] = hv;
+    __syncthreads();  // S is reused by the next keypoint
 }
 
 // The same histogram by the four warps of a 128-thread CTA sharing one
@@ -482,7 +576,7 @@ __device__ __forceinline__ void hs_hist_warp(WarpHist &S, const Src &src, bool v
 template <class Src>
 __device__ __forceinline__ void hs_hist_cta(WarpHist &S, const Src &src, bool valid,
                                             float *__restrict__ hist, size_t k,
-                                            float *__restrict__ norm_out)
+                                            float *__restrict__ norm_out, int flags)
 {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     {
@@ -514,67 +608,14 @@ __device__ __forceinline__ void hs_hist_cta(WarpHist &S, const Src &src, bool va
         }
     }
     __syncwarp();
-    const int cj = lane >> 3, b = lane & 7;
-    float H = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-        H += S.priv[w][b][cj * 8 + ((q + b) & 7)];
-    float ss = H * H;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        ss += __shfl_xor_sync(kFull, ss, o);
-    if (lane == 0)
-        S.wss[w] = ss;
-    __syncthreads();
-    const float nrm = sqrtf(S.wss[0] + S.wss[1] + S.wss[2] + S.wss[3]);
-    if (norm_out && t == 0)
-        norm_out[k] = valid ? nrm : 0.0f;
-    const float hv = (valid && nrm > 0.0f) ? H / nrm : 0.0f;
-    hist[k * kHistDim + w * 32 + lane] = hv;
-    __syncthreads();  // S is reused by the next keypoint
-}
-
-// Zeroes a lane-private histogram block: warp mode all four cell rows, CTA
-// mode the warp's own cell row.
-__device__ __forceinline__ void priv_zero_warp(WarpHist &S, int lane)
-{
-    float4 *z = reinterpret_cast<float4 *>(&S.priv[0][0][0]);
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-        z[q * 32 + lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-}
-
-// Cell-row sums, L2 norm and output of a warp-mode histogram.
-__device__ __forceinline__ void warp_finish(WarpHist &S, int lane, bool valid,
-                                            float *__restrict__ hist, size_t k)
-{
-    const int cj = lane >> 3, b = lane & 7;
-    float H[4];
-    float ss = 0.0f;
-#pragma unroll
-    for (int ci = 0; ci < 4; ++ci) {
-        float s = 0.0f;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            s += S.priv[ci][b][cj * 8 + ((q + b) & 7)];
-        H[ci] = s;
-        ss += s * s;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        ss += __shfl_xor_sync(kFull, ss, o);
-    const float nrm = sqrtf(ss);
-#pragma unroll
-    for (int ci = 0; ci < 4; ++ci)
-        hist[k * kHistDim + ci * 32 + lane] = (valid && nrm > 0.0f) ? H[ci] / nrm : 0.0f;
-    __syncwarp();
+    cta_finish(S, t, valid, hist, k, norm_out, flags);
 }
 
 // Warp mode from a staged footprint: the lane samples its column on the fly
 // (one sample per pixel, taps from shared memory) while it votes.
 __device__ __forceinline__ void hs_hist_warp_win(WarpHist &S, const WinGeom &g, const ColFrame &c,
                                                  const uint8_t *img, int pitch, int lane,
-                                                 float *__restrict__ hist, size_t k)
+                                                 float *__restrict__ hist, size_t k, int flags)
 {
     priv_zero_warp(S, lane);
     win_stage(S.win, g, img, pitch, lane, 32);
@@ -591,14 +632,14 @@ __device__ __forceinline__ void hs_hist_warp_win(WarpHist &S, const WinGeom &g, 
         here = down;
     }
     __syncwarp();
-    warp_finish(S, lane, true, hist, k);
+    warp_finish(S, lane, true, hist, k, nullptr, flags);
 }
 
 // CTA mode from a staged footprint: the CTA stages it, warp w samples rows
 // 8w - 1 .. 8w + 8 on the fly and votes rows [8w, 8w + 8).
 __device__ __forceinline__ void hs_hist_cta_win(WarpHist &S, const WinGeom &g, const ColFrame &c,
                                                 const uint8_t *img, int pitch,
-                                                float *__restrict__ hist, size_t k)
+                                                float *__restrict__ hist, size_t k, int flags)
 {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     {
@@ -621,21 +662,143 @@ __device__ __forceinline__ void hs_hist_cta_win(WarpHist &S, const WinGeom &g, c
         here = down;
     }
     __syncwarp();
+    cta_finish(S, t, true, hist, k, nullptr, flags);
+}
+
+// ---------------------------------------------------------------------------
+// trilinear binning (SIFT variant): a vote is shared by the two nearest cell
+// rows and columns, cell c centred at pixel 8c + 3.5 with weight 1 - |x - (8c +
+// 3.5)| / 8.  Lane j's column always splits between the same two cell columns
+// c0 = floor((j - 3.5) / 8) and c0 + 1 (slots 0 and 1), so the lane keeps a
+// private [cell row][slot][bin] histogram; the finish sums, for each cell
+// column, slot 0 of the lanes with c0 = cj and slot 1 of those with c0 = cj - 1.
+
+struct WarpHistTri {
+    float P[PS][kPRow];
+    float priv[4][2][8][32];  // [cell row][slot][bin][lane]
+};
+
+template <class Src>
+__device__ __forceinline__ void hs_hist_warp_tri(WarpHistTri &S, const Src &src, bool valid,
+                                                 int lane, float *__restrict__ hist, size_t k,
+                                                 int flags)
+{
+    {
+        float4 *z = reinterpret_cast<float4 *>(&S.priv[0][0][0][0]);
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            z[q * 32 + lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    __syncwarp();
+    if (valid) {
+        const int bi = lane >> 3, bj = lane & 7;
+#pragma unroll 8
+        for (int bb = 0; bb < 32; ++bb) {
+            const int i = 4 * (bb >> 2) + bi, j = 8 * (bb & 3) + bj;
+            S.P[i][j] = src.at(i, j);
+        }
+        __syncwarp();
+        // this lane's column weights
+        const float xc = ((float)lane - 3.5f) * 0.125f;
+        const int c0 = (int)floorf(xc);
+        const float wx1 = xc - (float)c0;
+        const float wxs[2] = {c0 >= 0 ? 1.0f - wx1 : 0.0f, c0 + 1 <= 3 ? wx1 : 0.0f};
+        const float g_half = 0.5f * gauss16(lane);
+        float up = S.P[0][lane];
+        float here = up;
+#pragma unroll 4
+        for (int i = 0; i < PS; ++i) {
+            const float down = S.P[i < PS - 1 ? i + 1 : PS - 1][lane];
+            const float left = __shfl_up_sync(kFull, here, 1);
+            const float right = __shfl_down_sync(kFull, here, 1);
+            const float gx = right - left;
+            const float gy = down - up;
+            const float m2 = gx * gx + gy * gy;
+            const float gi = __shfl_sync(kFull, g_half, i);
+            const bool any = m2 > 0.0f;
+            const float m = any ? m2 * rsqrtf(m2) : 0.0f;
+            float w1;
+            const int b0 = split_floor(orientation8(any ? gx : 1.0f, gy), w1) & 7;
+            const int b1 = (b0 + 1) & 7;
+            const float gm = (2.0f * gi * g_half) * m;
+            const float yc = ((float)i - 3.5f) * 0.125f;
+            const int r0 = (int)floorf(yc);
+            const float wy1 = yc - (float)r0;
+#pragma unroll
+            for (int dr = 0; dr < 2; ++dr) {
+                const int ci = r0 + dr;
+                if (ci < 0 || ci > 3)
+                    continue;
+                const float wy = dr ? wy1 : 1.0f - wy1;
+#pragma unroll
+                for (int sl = 0; sl < 2; ++sl) {
+                    const float v = gm * (wy * wxs[sl]);
+                    const float v1 = v * w1;
+                    float *col = &S.priv[ci][sl][0][lane];
+                    col[b0 * 32] += v - v1;
+                    col[b1 * 32] += v1;
+                }
+            }
+            up = here;
+            here = down;
+        }
+    }
+    __syncwarp();
+    // entry (ci, cj, b): slot 0 of lanes [8cj + 4, 8cj + 12), slot 1 of lanes [8cj - 4, 8cj + 4)
     const int cj = lane >> 3, b = lane & 7;
-    float H = 0.0f;
+    float H[4];
+    float ss = 0.0f;
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-        H += S.priv[w][b][cj * 8 + ((q + b) & 7)];
-    float ss = H * H;
+    for (int ci = 0; ci < 4; ++ci) {
+        float s = 0.0f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        ss += __shfl_xor_sync(kFull, ss, o);
-    if (lane == 0)
-        S.wss[w] = ss;
-    __syncthreads();
-    const float nrm = sqrtf(S.wss[0] + S.wss[1] + S.wss[2] + S.wss[3]);
-    hist[k * kHistDim + w * 32 + lane] = nrm > 0.0f ? H / nrm : 0.0f;
-    __syncthreads();  // S is reused by the next keypoint
+        for (int q = 0; q < 8; ++q) {
+            const int la = 8 * cj + 4 + ((q + b) & 7);
+            const int lb = 8 * cj - 4 + ((q + b) & 7);
+            if (la < 32)
+                s += S.priv[ci][0][b][la];
+            if (lb >= 0)
+                s += S.priv[ci][1][b][lb];
+        }
+        H[ci] = s;
+        ss += s * s;
+    }
+    const float nrm = sqrtf(warp_sum_f(ss));
+#pragma unroll
+    for (int ci = 0; ci < 4; ++ci)
+        H[ci] = (valid && nrm > 0.0f) ? H[ci] / nrm : 0.0f;
+    if (flags & (BD_HS_VARIANT_CLIP | BD_HS_VARIANT_ROOT))
+        variants_warp<4>(H, flags);
+#pragma unroll
+    for (int ci = 0; ci < 4; ++ci)
+        hist[k * kHistDim + ci * 32 + lane] = H[ci];
+    __syncwarp();
+}
+
+// Trilinear histogram of keypoint k sampled from the image (warp mode).
+__device__ __forceinline__ void hs_hist_image_warp_tri(WarpHistTri &S, const uint8_t *img, int w,
+                                                       int h, int pitch, const bd_keypoint &kp,
+                                                       float spacing, float *hist, size_t k,
+                                                       DeviceStatus *status, int flags)
+{
+    const int lane = threadIdx.x & 31;
+    const bool valid = kp_valid(kp);
+    ColSampler<false> edge;
+    if (!valid) {
+        if (lane == 0)
+            raise_flag(status, BD_FLAG_INVALID_KEYPOINT);
+        hs_hist_warp_tri(S, edge, false, lane, hist, k, flags);
+        return;
+    }
+    const Frame f = make_frame(kp, spacing);
+    if (col_interior(f, w, h)) {
+        ColSampler<true> in;
+        in.c = col_frame(img, w, h, pitch, f, lane);
+        hs_hist_warp_tri(S, in, true, lane, hist, k, flags);
+    } else {
+        edge.c = col_frame(img, w, h, pitch, f, lane);
+        hs_hist_warp_tri(S, edge, true, lane, hist, k, flags);
+    }
 }
 
 // Histogram of keypoint k of n sampled from the image by the whole CTA.
@@ -644,27 +807,28 @@ __device__ __forceinline__ void hs_hist_cta_win(WarpHist &S, const WinGeom &g, c
 template <bool UseWin>
 __device__ __forceinline__ void hs_hist_image_cta(WarpHist &S, const uint8_t *img, int w, int h,
                                                   int pitch, const bd_keypoint &kp, float spacing,
-                                                  float *hist, size_t k, DeviceStatus *status)
+                                                  float *hist, size_t k, DeviceStatus *status,
+                                                  int flags)
 {
     const bool valid = kp_valid(kp);
     ColSampler<false> edge;
     if (!valid) {
         if (threadIdx.x == 0)
             raise_flag(status, BD_FLAG_INVALID_KEYPOINT);
-        hs_hist_cta(S, edge, false, hist, k, nullptr);
+        hs_hist_cta(S, edge, false, hist, k, nullptr, flags);
         return;
     }
     const Frame f = make_frame(kp, spacing);
     WinGeom g;
     if (UseWin && win_geom(f, img, w, h, pitch, g)) {
-        hs_hist_cta_win(S, g, col_frame(img, w, h, pitch, f), img, pitch, hist, k);
+        hs_hist_cta_win(S, g, col_frame(img, w, h, pitch, f), img, pitch, hist, k, flags);
     } else if (col_interior(f, w, h)) {
         ColSampler<true> in;
         in.c = col_frame(img, w, h, pitch, f);
-        hs_hist_cta(S, in, true, hist, k, nullptr);
+        hs_hist_cta(S, in, true, hist, k, nullptr, flags);
     } else {
         edge.c = col_frame(img, w, h, pitch, f);
-        hs_hist_cta(S, edge, true, hist, k, nullptr);
+        hs_hist_cta(S, edge, true, hist, k, nullptr, flags);
     }
 }
 
@@ -672,7 +836,8 @@ __device__ __forceinline__ void hs_hist_image_cta(WarpHist &S, const uint8_t *im
 template <bool UseWin>
 __device__ __forceinline__ void hs_hist_image_warp(WarpHist &S, const uint8_t *img, int w, int h,
                                                    int pitch, const bd_keypoint &kp, float spacing,
-                                                   float *hist, size_t k, DeviceStatus *status)
+                                                   float *hist, size_t k, DeviceStatus *status,
+                                                   int flags)
 {
     const int lane = threadIdx.x & 31;
     const bool valid = kp_valid(kp);
@@ -680,20 +845,21 @@ __device__ __forceinline__ void hs_hist_image_warp(WarpHist &S, const uint8_t *i
     if (!valid) {
         if (lane == 0)
             raise_flag(status, BD_FLAG_INVALID_KEYPOINT);
-        hs_hist_warp(S, edge, false, lane, hist, k, nullptr);
+        hs_hist_warp(S, edge, false, lane, hist, k, nullptr, flags);
         return;
     }
     const Frame f = make_frame(kp, spacing);
     WinGeom g;
     if (UseWin && win_geom(f, img, w, h, pitch, g)) {
-        hs_hist_warp_win(S, g, col_frame(img, w, h, pitch, f, lane), img, pitch, lane, hist, k);
+        hs_hist_warp_win(S, g, col_frame(img, w, h, pitch, f, lane), img, pitch, lane, hist, k,
+                         flags);
     } else if (col_interior(f, w, h)) {
         ColSampler<true> in;
         in.c = col_frame(img, w, h, pitch, f, lane);
-        hs_hist_warp(S, in, true, lane, hist, k, nullptr);
+        hs_hist_warp(S, in, true, lane, hist, k, nullptr, flags);
     } else {
         edge.c = col_frame(img, w, h, pitch, f, lane);
-        hs_hist_warp(S, edge, true, lane, hist, k, nullptr);
+        hs_hist_warp(S, edge, true, lane, hist, k, nullptr, flags);
     }
 }
 

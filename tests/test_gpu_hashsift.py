@@ -182,3 +182,72 @@ def test_ragged_counts(gpu_ctx, n):
     ref = oracle.hs_describe(img, kps[sel], hs)
     agree = (_bits(a[sel], 256) == (ref["margins"] > 0)) | (np.abs(ref["margins"]) < 1e-3)
     assert agree.all()
+
+
+# ---------------------------------------------------------------------------
+# SIFT variants before hashing (bd_hs_params_set_variant)
+
+_VARIANTS = [0, 2, 4, 6, 1, 7]
+
+
+@pytest.mark.parametrize("flags", _VARIANTS)
+@pytest.mark.parametrize("n", [1000, 5000])
+def test_variant_histograms_and_bits(gpu_ctx, plain, flags, n):
+    """Histograms within 1e-5 of the oracle's variant on the GPU's own patches
+    (the patch warp is pinned separately) and bits exact outside the error
+    band; 1000 keypoints run the cooperative kernel, 5000 the warp kernel
+    (trilinear always the warp kernel).  RootSIFT is compared squared: its
+    square is the L1-normalised histogram, while the square root turns an
+    absolute error e of a near-zero entry into up to sqrt(e)."""
+    import paper_2108_08380_gb300 as bd
+    rng = np.random.default_rng(n + flags)
+    kps = synth.make_keypoints(n, 640, 480, rng, border=32.0, scales=(1.0,), angle_bins=None)
+    kps[:5, 0] = rng.uniform(-10, 8, size=5)  # some footprints leave the image
+    hp = gpu_ctx.hs_params(plain.hs, precision=bd.BD_HS_FP32)
+    hp.set_variant(flags)
+    import torch
+    hist = torch.empty((n, 128), dtype=torch.float32, device="cuda")
+    bits = gpu_ctx.hashsift_describe(hp, _dev(plain.img_a), _dev(kps), hist_out=hist).cpu().numpy()
+    h = hist.cpu().numpy().astype(np.float64)
+    P = gpu_ctx.hashsift_warp(hp, _dev(plain.img_a), _dev(kps)).cpu().numpy().astype(np.float64)
+    ref = oracle.hs_hist_variant(P, flags)
+    if flags & bd.BD_HS_VARIANT_ROOT:
+        assert np.abs(h * h - ref * ref).max() <= 1e-5
+    else:
+        assert np.abs(h - ref).max() <= 1e-5
+    margins, rbits = oracle.hs_project(ref, plain.hs.W, plain.hs.b)
+    tol = _margins_tol(h, ref, plain.hs.W)
+    sure = np.abs(margins) > tol
+    got = _bits(bits, plain.hs.nbits)
+    want = _bits(rbits, plain.hs.nbits)
+    assert np.array_equal(got[sure], want[sure])
+
+
+def test_variant_batch_matches_per_image_and_refuses_trilinear(gpu_ctx, plain):
+    import paper_2108_08380_gb300 as bd
+    import torch
+    hp = gpu_ctx.hs_params(plain.hs, precision=bd.BD_HS_BF16_RESCUE)
+    hp.set_variant(bd.BD_HS_VARIANT_CLIP | bd.BD_HS_VARIANT_ROOT)
+    img = _dev(plain.img_a)
+    kps = _dev(plain.kps_a)
+    n = plain.kps_a.shape[0]
+    flags = bd.BD_HS_VARIANT_CLIP | bd.BD_HS_VARIANT_ROOT
+    P = gpu_ctx.hashsift_warp(hp, img, kps).cpu().numpy().astype(np.float64)
+    ref = oracle.hs_hist_variant(P, flags)
+    margins, _ = oracle.hs_project(ref, plain.hs.W, plain.hs.b)
+    sure = np.abs(margins) > _margins_tol(ref + 1e-5, ref, plain.hs.W)  # 1e-5 histogram error
+    want = margins > 0
+    one = gpu_ctx.hashsift_describe(hp, img, kps).cpu().numpy()
+    assert np.array_equal(_bits(one, plain.hs.nbits)[sure], want[sure])
+    plan = gpu_ctx.batch(None, hp, [img], [0, n])
+    out = torch.empty((n, plain.hs.nbits // 32), dtype=torch.int32, device="cuda")
+    for mode in (1, 4):
+        plan.set_config(8, 4, 0, mode)
+        plan.describe([img], kps, None, out)
+        assert np.array_equal(_bits(out.cpu().numpy(), plain.hs.nbits)[sure], want[sure])
+    plan.close()
+    hp.set_variant(bd.BD_HS_VARIANT_TRILINEAR)
+    with pytest.raises(bd.BindescError):
+        gpu_ctx.batch(None, hp, [img], [0, n])
+    with pytest.raises(bd.BindescError):
+        hp.set_variant(8)
