@@ -949,7 +949,7 @@ def main():
     ap.add_argument("--no-components", action="store_true",
                     help="skip the per-stage component measurements")
     ap.add_argument("--batch-config", default=None,
-                    help="bad_kp_per_item,ctas_per_sm,hs_first[,hs_kp_per_item] for the persistent kernel "
+                    help="bad_kp_per_item,ctas_per_sm,hs_first[,hs_kp_per_item[,proj_fused]] for the persistent kernel "
                          "instead of the autotuner's pick")
     ap.add_argument("--match", choices=["auto", "tensor", "popc"], default="auto",
                     help="matching kernel: tensor cores (bd_match_tc), POPC (bd_match), or auto "

@@ -262,12 +262,19 @@ typedef struct bd_batch bd_batch;
  *                   one before the BAD items and the rest after them.
  *  hs_kp_per_item   HashSIFT keypoints per work item: 1 = the CTA's four warps
  *                   share each keypoint (lower latency, for few keypoints),
- *                   4 = one keypoint per warp (higher throughput). */
+ *                   4 = one keypoint per warp (higher throughput).
+ *  proj_fused       0: the tcgen05 projection kernel hashes the histograms
+ *                   after the persistent kernel (the parameters' precision);
+ *                   1: the persistent kernel projects them itself, 32 x 32
+ *                   tiles in FP32 in the FP32 path's summation order (the
+ *                   same bits as both paths; no rescue, one launch fewer, for
+ *                   small batches). */
 typedef struct bd_batch_config {
     int bad_kp_per_item;
     int ctas_per_sm;
     int hs_first;
     int hs_kp_per_item;
+    int proj_fused;
 } bd_batch_config;
 
 /* Plans the description of n_img images with BAD and/or HashSIFT (either

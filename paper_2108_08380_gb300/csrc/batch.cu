@@ -41,6 +41,12 @@ struct BatchKernelArgs {
     int hs_items;            // ceil(n_kp / hs_per_item) if HashSIFT is on, else 0
     int hs_per_item;         // 1: the CTA shares a keypoint; 4: one keypoint per warp
     int hs_flags;            // BD_HS_VARIANT_CLIP / _ROOT
+    // fused FP32 projection items (proj_fused): [ceil(n_kp/32)] x [K/32] tiles
+    int proj_items, proj_cols;  // 0 when the tcgen05 kernel projects after this one
+    unsigned int *hs_group_done;  // [ceil(n_kp/32)] histograms finished per 32 keypoints
+    const float *W, *bias;      // FP32 W [128][K] (row-major), bias [K]
+    int hs_nbits;
+    uint32_t *hs_out;
     int hs_first;
     int hs_pre_final, hs_pre_bad;  // HashSIFT items queued before the pass-2 tiles / the BAD items
     uint32_t *ii, *carry;
@@ -105,6 +111,71 @@ __device__ __forceinline__ int find_image(const BatchImageDev *imgs, int n_img, 
     return lo;
 }
 
+// Fused FP32 projection (Sec. III-B, D = sgn(W^T h + b)) of keypoints
+// [k0, k0 + nk) and bits [32 cb, 32 cb + 32): 128 threads, thread (row t/4,
+// columns 8 (t%4) + [0, 8)); each margin is summed in the FP32 projection
+// kernel's order (four 32-term chunks from zero, added in sequence), so the
+// bits equal that kernel's and the tensor-core path's.
+struct ProjTile {
+    float H[32][132];  // histogram rows (padded: row r starts at bank 4r)
+    float Wt[128][32]; // W[:, 32 cb + c]
+};
+
+__device__ __forceinline__ void proj_tile(ProjTile &S, const BatchKernelArgs &A, int k0, int nk,
+                                          int cb)
+{
+    const int t = threadIdx.x;
+    for (int e = t; e < 32 * 32; e += 128) {  // 32 rows x 32 float4
+        const int r = e >> 5, c4 = e & 31;
+        const float4 v = r < nk ? __ldcg(reinterpret_cast<const float4 *>(A.hist + (size_t)(k0 + r) * kHistDim) + c4)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4 *>(&S.H[r][4 * c4]) = v;
+    }
+    for (int e = t; e < 128 * 8; e += 128) {  // 128 rows x 8 float4
+        const int k = e >> 3, c4 = e & 7;
+        *reinterpret_cast<float4 *>(&S.Wt[k][4 * c4]) =
+            __ldg(reinterpret_cast<const float4 *>(A.W + (size_t)k * A.hs_nbits + 32 * cb) + c4);
+    }
+    __syncthreads();
+    const int r = t >> 2, g = t & 3;
+    float acc[8];
+#pragma unroll 1
+    for (int k0c = 0; k0c < kHistDim; k0c += 32) {
+        float part[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            part[b] = 0.0f;
+#pragma unroll 8
+        for (int kk = k0c; kk < k0c + 32; ++kk) {
+            const float h = S.H[r][kk];
+            const float4 w0 = *reinterpret_cast<const float4 *>(&S.Wt[kk][8 * g]);
+            const float4 w1 = *reinterpret_cast<const float4 *>(&S.Wt[kk][8 * g + 4]);
+            part[0] = fmaf(h, w0.x, part[0]);
+            part[1] = fmaf(h, w0.y, part[1]);
+            part[2] = fmaf(h, w0.z, part[2]);
+            part[3] = fmaf(h, w0.w, part[3]);
+            part[4] = fmaf(h, w1.x, part[4]);
+            part[5] = fmaf(h, w1.y, part[5]);
+            part[6] = fmaf(h, w1.z, part[6]);
+            part[7] = fmaf(h, w1.w, part[7]);
+        }
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            acc[b] = k0c == 0 ? part[b] : acc[b] + part[b];
+    }
+    const int kp = k0 + r;
+    const bool ok = r < nk && dev::kp_valid(A.kps[kp < A.n_kp ? kp : 0]);
+    uint32_t byte = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+        byte |= (ok && acc[b] + __ldg(A.bias + 32 * cb + 8 * g + b) > 0.0f) ? (1u << b) : 0u;
+    uint32_t word = byte << (8 * g);
+    word |= __shfl_xor_sync(0xffffffffu, word, 1);
+    word |= __shfl_xor_sync(0xffffffffu, word, 2);
+    if (g == 0 && r < nk)
+        A.hs_out[(size_t)kp * (A.hs_nbits / 32) + cb] = word;
+}
+
 // MINB: resident CTAs per SM the register budget is sized for (4: 128 registers,
 // 6: 80); the autotuner picks the variant through ctas_per_sm.
 template <int NW, int MINB>
@@ -114,6 +185,7 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
         dev::IiStatsSmem s;
         dev::IiFinalSmem f;
         dev::WarpHist h[4];  // one per warp
+        ProjTile p;
     } U;
     __shared__ unsigned int item_s;
     __shared__ int flag_s;
@@ -131,7 +203,8 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
     const int e2 = e1 + A.n_tiles;
     const int e3 = e2 + A.hs_pre_bad;
     const int e4 = e3 + A.n_bad_items;
-    const int total = e4 + (n_hs - A.hs_pre_final - A.hs_pre_bad);
+    const int e5 = e4 + (n_hs - A.hs_pre_final - A.hs_pre_bad);
+    const int total = e5 + A.proj_items;
 
     for (;;) {
         if (t == 0)
@@ -158,9 +231,12 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
         } else if (item < e4) {
             kind = 3;
             idx = item - e3;
-        } else {
+        } else if (item < e5) {
             kind = 1;
             idx = A.hs_pre_final + A.hs_pre_bad + item - e4;
+        } else {
+            kind = 4;
+            idx = item - e5;
         }
         if (kind == 0) {
             const int im = find_image(A.imgs, A.n_img, idx, 0);
@@ -181,6 +257,10 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                 const BatchImageDev &I = A.imgs[im];
                 dev::hs_hist_image_cta<false>(U.h[0], A.img_ptr[im], I.w, I.h, I.pitch, A.kps[k],
                                        A.spacing, A.hist, (size_t)k, A.status, A.hs_flags);
+                if (A.proj_items && t == 0) {
+                    __threadfence();
+                    atomicAdd(A.hs_group_done + (k >> 5), 1u);
+                }
             } else {
                 // four keypoints, one per warp
                 const int k = idx * 4 + (t >> 5);
@@ -190,6 +270,10 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                     dev::hs_hist_image_warp<false>(U.h[t >> 5], A.img_ptr[im], I.w, I.h, I.pitch,
                                             A.kps[k], A.spacing, A.hist, (size_t)k, A.status,
                                             A.hs_flags);
+                    if (A.proj_items && (t & 31) == 0) {
+                        __threadfence();
+                        atomicAdd(A.hs_group_done + (k >> 5), 1u);
+                    }
                 }
             }
             __syncthreads();
@@ -208,6 +292,14 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                 __threadfence();
                 atomicAdd(A.final_done + im, 1u);
             }
+        } else if (kind == 4) {
+            // FP32 projection of 32 keypoints x 32 bits, once their histograms exist
+            const int g = idx / A.proj_cols, cb = idx % A.proj_cols;
+            const int k0 = g * 32;
+            const int nk = min(32, A.n_kp - k0);
+            if (cta_wait_count(A.hs_group_done + g, (unsigned)nk, &flag_s, A.status))
+                proj_tile(U.p, A, k0, nk, cb);
+            __syncthreads();
         } else {
             const int bi = idx;
             const int im = find_image(A.imgs, A.n_img, bi, 2);
@@ -239,6 +331,9 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
             A.stats_done[i] = 0u;
             A.final_done[i] = 0u;
         }
+        if (A.proj_items)
+            for (int i = t; i < (A.n_kp + 31) / 32; i += blockDim.x)
+                A.hs_group_done[i] = 0u;
     }
 }
 
@@ -260,9 +355,9 @@ struct bd_batch {
     const uint8_t **d_ptrs = nullptr;
     std::vector<const uint8_t *> last_ptrs;
     uint32_t *d_ii = nullptr, *d_carry = nullptr;
-    unsigned int *d_counters = nullptr;  // [work][exit][stats_done n_img][final_done n_img], zero between launches
+    unsigned int *d_counters = nullptr;  // [work][exit][stats_done n_img][final_done n_img][hs groups], zero between launches
     float *d_hist = nullptr;
-    bd_batch_config cfg = {8, 0, 1, 4};
+    bd_batch_config cfg = {8, 0, 1, 4, 0};
     int max_ctas_per_sm = 0;
     int occ4 = 0;  // resident CTAs per SM of the 128-register variant
     // graph replay
@@ -289,6 +384,16 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     A.bad_per_item = b->cfg.bad_kp_per_item;
     A.n_bad_items = (b->bad && bad_out) ? b->n_bad_items : 0;
     A.hs_per_item = b->cfg.hs_kp_per_item;
+    const bool fused = b->cfg.proj_fused && b->hs && hs_out && b->n_kp > 0;
+    if (fused) {
+        A.proj_cols = b->hs->nbits / 32;
+        A.proj_items = ((b->n_kp + 31) / 32) * A.proj_cols;
+        A.hs_group_done = b->d_counters + 2 + 2 * b->n_img;
+        A.W = b->hs->d_W;
+        A.bias = b->hs->d_bias;
+        A.hs_nbits = b->hs->nbits;
+        A.hs_out = hs_out;
+    }
     A.hs_items = (b->hs && hs_out) ? (b->n_kp + A.hs_per_item - 1) / A.hs_per_item : 0;
     A.hs_first = b->cfg.hs_first;
     A.ii = b->d_ii;
@@ -339,7 +444,7 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_err(ctx, e, "bd_describe_batch: persistent kernel");
-    if (A.hs_items) {
+    if (A.hs_items && !fused) {
         const bd_hs_params *p = b->hs;
         if (p->precision == BD_HS_FP32)
             e = launch_hs_proj_fp32(p, b->d_hist, b->n_kp, hs_out, st, kps);
@@ -453,8 +558,9 @@ bd_status bd_batch_create(bd_ctx *ctx, const bd_bad_params *bad, const bd_hs_par
         if (e == cudaSuccess) e = cudaMalloc(&b->d_ptrs, sizeof(void *) * n_img);
         if (e == cudaSuccess && bad) e = cudaMalloc(&b->d_ii, sizeof(uint32_t) * ii_total);
         if (e == cudaSuccess && bad) e = cudaMalloc(&b->d_carry, sizeof(uint32_t) * carry_total);
-        if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(unsigned int) * (2 + 2 * (size_t)n_img));
-        if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, sizeof(unsigned int) * (2 + 2 * (size_t)n_img));
+        const size_t ncount = 2 + 2 * (size_t)n_img + (size_t)(b->n_kp + 31) / 32;
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(unsigned int) * ncount);
+        if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, sizeof(unsigned int) * ncount);
         if (e == cudaSuccess && hs) e = cudaMalloc(&b->d_hist, sizeof(float) * kHistDim * (size_t)(b->n_kp > 0 ? b->n_kp : 1));
         if (e == cudaSuccess) e = cudaMemcpy(b->d_imgs, b->imgs.data(), sizeof(BatchImageDev) * n_img, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
@@ -505,7 +611,8 @@ bd_status bd_batch_set_config(bd_batch *b, const bd_batch_config *cfg)
         return BD_ERR_INVALID;
     if (cfg->bad_kp_per_item < 4 || cfg->bad_kp_per_item > 256 || (cfg->bad_kp_per_item & 3) ||
         cfg->ctas_per_sm < 0 || cfg->hs_first < 0 || cfg->hs_first > 2 ||
-        (cfg->hs_kp_per_item != 1 && cfg->hs_kp_per_item != 4))
+        (cfg->hs_kp_per_item != 1 && cfg->hs_kp_per_item != 4) ||
+        (cfg->proj_fused != 0 && cfg->proj_fused != 1))
         return set_err(b->ctx, BD_ERR_INVALID, "bd_batch_set_config: bad configuration");
     b->cfg = *cfg;
     int items = 0;
@@ -618,11 +725,13 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
 {
     if (!ctx || !b || reps < 1)
         return BD_ERR_INVALID;
-    const int items[] = {4, 8, 16, 32};
+    const int items[] = {4, 8, 32};
     std::vector<int> per_sm;
-    for (int c : {1, 2, 3, 4, 6, 8, 12, 16})
+    for (int c : {2, 3, 4, 6})
         if (c <= b->max_ctas_per_sm)
             per_sm.push_back(c);
+    if (per_sm.empty())
+        per_sm.push_back(1);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -645,13 +754,15 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     // sweep, then re-time the four fastest with three times the repetitions
     std::vector<std::pair<float, bd_batch_config>> res;
     bd_status s = BD_OK;
+    const bool can_fuse = b->hs && hs_out;
+    for (int fu = 0; fu < (can_fuse ? 2 : 1); ++fu)
     for (int hm : {1, 4})
         for (int hs_first = 0; hs_first < 3 && s == BD_OK; ++hs_first)
             for (int it : items)
                 for (int c : per_sm) {
                     if (s != BD_OK)
                         break;
-                    bd_batch_config cfg = {it, c, hs_first, hm};
+                    bd_batch_config cfg = {it, c, hs_first, hm, fu};
                     float ms = 0.f;
                     s = time_cfg(cfg, reps, &ms);
                     res.push_back({ms, cfg});

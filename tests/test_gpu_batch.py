@@ -165,3 +165,32 @@ def test_batched_workload_full_size_sampled(gpu_ctx):
         got = np.unpackbits(_u32(oh)[sel].view(np.uint8), axis=1, bitorder="little").astype(bool)
         sure = np.abs(ro["margins"]) > 2e-3
         assert np.array_equal(got[sure], (ro["margins"] > 0)[sure])
+
+
+@pytest.mark.parametrize("hs_mode", [1, 4])
+def test_fused_fp32_projection_equals_tensor_core_path(gpu_ctx, hs_mode):
+    """The persistent kernel's own FP32 projection tiles give the bits of the
+    tcgen05 BF16 + rescue kernel on the same histograms (both equal the FP32
+    path), for FP32 W and for W exactly in BF16, with and without BAD."""
+    import torch
+    for bf16 in (False, True):
+        imgs, kps, offs, bad, hs = _small_batch(seed=9 + bf16)
+        if not bf16:
+            rng = np.random.default_rng(3)
+            hs = synth.make_hashsift_params(256, rng)
+        bp, hp = gpu_ctx.bad_params(bad), gpu_ctx.hs_params(hs)
+        dimgs = [_dev(im) for im in imgs]
+        n = len(kps)
+        dk = _dev(kps)
+        for with_bad in (True, False):
+            b = gpu_ctx.batch(bp if with_bad else None, hp, dimgs, offs)
+            ob = torch.zeros((n, 8), dtype=torch.int32, device="cuda") if with_bad else None
+            res = []
+            for fused in (0, 1):
+                oh = torch.full((n, 8), -1, dtype=torch.int32, device="cuda")
+                b.set_config(8, 4, 2, hs_mode, fused)
+                b.describe(dimgs, dk, ob, oh, graph=bool(fused))
+                res.append(_u32(oh))
+            assert np.array_equal(res[0], res[1])
+            assert gpu_ctx.sync_status() == 0
+            b.close()
