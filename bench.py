@@ -105,7 +105,8 @@ class Workload:
             na = int(self.offsets[1])
             self.pairs_per_step = 2 * na * (self.n - na)
             if self.match_kind == "auto":
-                self.match_kind = "tensor" if na * (self.n - na) >= (1 << 24) else "popc"
+                # small pairs: matched by the describing launch itself
+                self.match_kind = "tensor" if na * (self.n - na) >= (1 << 24) else "fused"
         else:
             self.pairs_per_step = 0
 
@@ -123,16 +124,20 @@ class Workload:
         self.bad = torch.empty((n, self.bad_bits // 32), dtype=i32, device=dev)
         self.hs = torch.empty((n, self.hs_bits // 32), dtype=i32, device=dev)
         self.plan = ctx.batch(self.bp, self.hp, self.dimg, self.offsets)
+        if self.match:
+            na = int(self.offsets[1])
+            self.m_bad = torch.empty((na, 3), dtype=i32, device=dev)
+            self.m_hs = torch.empty((na, 3), dtype=i32, device=dev)
+            if self.match_kind == "fused":
+                # image A's descriptors against image B's, by the describing launch
+                self.plan.set_matches([(bd.BD_DESC_BAD, 0, 1, self.m_bad, 4, 5),
+                                       (bd.BD_DESC_HASHSIFT, 0, 1, self.m_hs, 4, 5)])
         self.tuned = None
         if config is not None:
             self.plan.set_config(*config)
             self.tuned = self.plan.config()
         elif autotune:
             self.tuned, _ = self.plan.autotune(self.dimg, self.dkps, self.bad, self.hs, reps=5)
-        if self.match:
-            na = int(self.offsets[1])
-            self.m_bad = torch.empty((na, 3), dtype=i32, device=dev)
-            self.m_hs = torch.empty((na, 3), dtype=i32, device=dev)
 
     def stages(self, ctx):
         """(label, callable) of the ABI calls of one step, in order."""
@@ -140,7 +145,9 @@ class Workload:
                                                             graph=True))]
         if self.match:
             na = int(self.offsets[1])
-            if self.match_kind == "tensor":
+            if self.match_kind == "fused":
+                pass  # done by describe_batch (bd_batch_set_matches)
+            elif self.match_kind == "tensor":
                 st += [
                     ("match_bad", lambda: ctx.match(self.bad[:na], self.bad[na:], self.bad_bits,
                                                     4, 5, out=self.m_bad, tensor_cores=True)),
@@ -467,9 +474,11 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "u8/int32 (BAD, matching), f32 + bf16 tensor (HashSIFT)",
         "data": "synthetic",
         "config": dict(wl.config, l2="flushed between steps (512 MB write)",
-                       matching=("tensor cores (FP8 +-1, tcgen05), one call per descriptor type"
-                                 if wl.match_kind == "tensor"
-                                 else "POPC, both descriptor types in one bd_match_batch launch")
+                       matching={"tensor": "tensor cores (FP8 +-1, tcgen05), one call per "
+                                           "descriptor type",
+                                 "popc": "POPC, both descriptor types in one bd_match_batch launch",
+                                 "fused": "POPC, both descriptor types matched by the describing "
+                                          "launch itself (bd_batch_set_matches)"}[wl.match_kind]
                        if wl.match else None,
                        parallelism=(f"{world} ranks, independent inputs per rank (weak scaling)"
                                     if world > 1 else "single GPU")),
@@ -726,10 +735,14 @@ def roofline(wl, per_kernel, clocks, probes=None):
             "alu": (HS_OPS_PER_PIXEL * 1024.0 * wl.n, f_rate, "Tops/s", f_src),
             "hbm": (6.0 * px, float(peaks["hbm_gbs"]) * 1e9, "GB/s", f"{kind} HBM copy"),
         }
+        if wl.match and wl.match_kind == "fused":  # the matchings are its last items
+            p_rate, p_src = probe("popc", 152 * 16 * sm_mhz * 1e6, "152 SMs x 16 POPC/clk")
+            words = wl.bad_bits // 32 + wl.hs_bits // 32
+            parts["popc"] = (float(na) * nb * words, p_rate, "Tpopc/s", p_src)
         tmin = {k: v[0] / v[1] for k, v in parts.items()}
         bound = max(tmin, key=tmin.get)
         work, rate, unit, src = parts[bound]
-        scale = 1e9 if unit in ("Gload/s", "GB/s") else 1e12
+        scale = 1e9 if unit in ("Gload/s", "GB/s") else 1e12  # Tops/s, Tpopc/s
         out.update(bound=bound, achieved=work / t / scale, peak=rate / scale, unit=unit,
                    frac=work / t / rate, peak_source=src,
                    parts_min_ms={k: v * 1e3 for k, v in tmin.items()},
@@ -951,9 +964,10 @@ def main():
     ap.add_argument("--batch-config", default=None,
                     help="bad_kp_per_item,ctas_per_sm,hs_first[,hs_kp_per_item[,proj_fused]] for the persistent kernel "
                          "instead of the autotuner's pick")
-    ap.add_argument("--match", choices=["auto", "tensor", "popc"], default="auto",
-                    help="matching kernel: tensor cores (bd_match_tc), POPC (bd_match), or auto "
-                         "(tensor cores from 2^24 query-train pairs up)")
+    ap.add_argument("--match", choices=["auto", "tensor", "popc", "fused"], default="auto",
+                    help="matching: tensor cores (bd_match_tc), POPC (bd_match_batch), fused into "
+                         "the describing launch (bd_batch_set_matches), or auto (tensor cores from "
+                         "2^24 query-train pairs up, else fused)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-sample-kp", type=int, default=250)
     args = ap.parse_args()

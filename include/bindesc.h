@@ -58,6 +58,9 @@ typedef struct bd_keypoint {
     float x, y, scale, angle;
 } bd_keypoint;
 
+/* Most matchings of one bd_match_batch call or of one batch plan. */
+#define BD_MATCH_MAX_JOBS 8
+
 /* One query's result: train index of the nearest neighbour (-1 if the train
  * set is empty), its Hamming distance d1, the second-smallest distance d2
  * (nbits+1 when there is no second entry) and the ratio-test verdict. */
@@ -311,6 +314,63 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
                             const bd_keypoint *kps, uint32_t *bad_out, uint32_t *hs_out,
                             int reps, bd_batch_config *best, float *best_ms);
 
+/* Item timeline of the persistent kernel (tracing aid).  One record per work
+ * item of the last bd_describe_batch, indexed by queue position; times are
+ * the GPU's global nanosecond timer read by the CTA's thread 0:
+ *  t_claim  the item was taken from the queue
+ *  t_ready  its dependency counters were complete (= t_claim without a wait)
+ *  t_end    its work was done, before it published its own completion
+ * so an item's t_ready is never below the t_end of an item it waited on. */
+enum {
+    BD_ITEM_II_PASS1 = 0,   /* integral pass-1 tile (row prefixes, carries) */
+    BD_ITEM_HASHSIFT = 1,   /* HashSIFT histogram(s) */
+    BD_ITEM_II_PASS2 = 2,   /* integral pass-2 tile (final table) */
+    BD_ITEM_BAD = 3,        /* BAD descriptors of a keypoint group */
+    BD_ITEM_PROJ = 4,       /* fused projection tile (proj_fused) */
+    BD_ITEM_MATCH = 5       /* matching of a query block against a train slice */
+};
+typedef struct bd_batch_event {
+    int32_t kind;    /* BD_ITEM_* */
+    int32_t index;   /* index among the items of its kind */
+    int32_t sm;      /* SM that ran it */
+    int32_t cta;     /* CTA of the persistent grid */
+    uint64_t t_claim, t_ready, t_end;
+} bd_batch_event;
+
+/* Matchings done by the batched launch itself (Sec. IV-C nearest-neighbour
+ * matching with the ratio test): after describing, the descriptors of
+ * query_image are matched against those of train_image, read from the same
+ * call's outputs; each job writes n_kp(query_image) records to out, exactly
+ * the records bd_match returns on those descriptors (nbits = the plan's BAD
+ * or HashSIFT length).  A job whose query image has no keypoints writes
+ * nothing. */
+enum { BD_DESC_BAD = 0, BD_DESC_HASHSIFT = 1 };
+typedef struct bd_batch_match {
+    int desc;                  /* BD_DESC_BAD or BD_DESC_HASHSIFT */
+    int query_image, train_image;
+    int ratio_num, ratio_den;  /* 0 < ratio_num <= ratio_den */
+    bd_match_result *out;      /* device, n_kp(query_image) records, 4-byte aligned */
+} bd_batch_match;
+
+/* Sets the plan's matchings (host array, copied; 0 <= n_jobs <=
+ * BD_MATCH_MAX_JOBS, 0 clears them).  BAD jobs need BAD parameters in the
+ * plan, HashSIFT jobs HashSIFT parameters; bd_describe_batch then refuses a
+ * call without the outputs the jobs read (BD_ERR_INVALID).  When the
+ * persistent kernel holds every descriptor the jobs read (BAD jobs only, or
+ * proj_fused = 1), the matchings are its last work items, each waiting for
+ * the descriptors of its two images; otherwise one matching launch follows
+ * the projection. */
+bd_status bd_batch_set_matches(bd_batch *b, const bd_batch_match *jobs, int n_jobs);
+
+/* enable != 0: later launches of the plan record the timeline (device buffer
+ * owned by the plan; the graph is re-captured); 0 turns it off. */
+bd_status bd_batch_set_timeline(bd_batch *b, int enable);
+/* Waits for the context's stream and copies up to cap records of the last
+ * launch to host memory `out`; *n = the number of items of that launch
+ * (records past cap are not copied).  BD_ERR_INVALID when the timeline is off
+ * or no launch recorded one. */
+bd_status bd_batch_get_timeline(bd_batch *b, bd_batch_event *out, int cap, int *n);
+
 /* ------------------------------------------------------------------------ */
 /* Differentiable training step (relaxed descriptors, Sec. III-A Eq. 1,      */
 /* Sec. III-B Eq. 3)                                                         */
@@ -402,8 +462,6 @@ bd_status bd_match_tc(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t,
 
 /* ------------------------------------------------------------------------ */
 /* Several matchings in one launch                                           */
-
-#define BD_MATCH_MAX_JOBS 8
 
 /* One matching of a bd_match_batch call: the arguments of bd_match. */
 typedef struct {

@@ -91,6 +91,9 @@ _SIGS = [
     ("bd_select_feature", _I, [_P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P, _P]),
     ("bd_probe", _I, [_P, _I, _P, ctypes.c_size_t, ctypes.c_size_t, _I, _P,
                       ctypes.POINTER(ctypes.c_uint64)]),
+    ("bd_batch_set_timeline", _I, [_P, _I]),
+    ("bd_batch_set_matches", _I, [_P, _P, _I]),
+    ("bd_batch_get_timeline", _I, [_P, _P, _I, ctypes.POINTER(_I)]),
 ]
 
 _lock = threading.Lock()
@@ -420,6 +423,29 @@ class BatchConfig(ctypes.Structure):
                 "proj_fused": self.proj_fused}
 
 
+class BatchEvent(ctypes.Structure):
+    """bd_batch_event: one work item of the persistent kernel."""
+    _fields_ = [("kind", ctypes.c_int32), ("index", ctypes.c_int32), ("sm", ctypes.c_int32),
+                ("cta", ctypes.c_int32), ("t_claim", ctypes.c_uint64),
+                ("t_ready", ctypes.c_uint64), ("t_end", ctypes.c_uint64)]
+
+
+# work item kinds of the batched kernel's queue (bd_batch_event.kind)
+BD_ITEM_II_PASS1, BD_ITEM_HASHSIFT, BD_ITEM_II_PASS2, BD_ITEM_BAD, BD_ITEM_PROJ = 0, 1, 2, 3, 4
+BD_ITEM_MATCH = 5
+# descriptor of a batch matching (bd_batch_match.desc)
+BD_DESC_BAD, BD_DESC_HASHSIFT = 0, 1
+
+
+class BatchMatch(ctypes.Structure):
+    """bd_batch_match: one matching done by the batched launch."""
+    _fields_ = [("desc", ctypes.c_int), ("query_image", ctypes.c_int),
+                ("train_image", ctypes.c_int), ("ratio_num", ctypes.c_int),
+                ("ratio_den", ctypes.c_int), ("out", ctypes.c_void_p)]
+BATCH_EVENT_DTYPE = [("kind", "<i4"), ("index", "<i4"), ("sm", "<i4"), ("cta", "<i4"),
+                     ("t_claim", "<u8"), ("t_ready", "<u8"), ("t_end", "<u8")]
+
+
 class Batch:
     """A bd_batch plan: many images described by one persistent launch."""
 
@@ -478,6 +504,40 @@ class Batch:
                                      ctypes.byref(c), ctypes.byref(ms))
         self.ctx._check(st, "bd_batch_autotune")
         return c.as_dict(), float(ms.value)
+
+    def set_matches(self, jobs):
+        """jobs: (desc, query_image, train_image, out, ratio_num, ratio_den)
+        tuples; out is an int32 (n_kp(query_image), 3) device tensor (or None
+        when that image has no keypoints).  [] clears them."""
+        arr = (BatchMatch * max(1, len(jobs)))()
+        self._match_outs = []
+        for i, (desc, qi, ti, out, rn, rd) in enumerate(jobs):
+            if out is not None:
+                self._match_outs.append(out)  # kept alive with the plan
+            arr[i] = BatchMatch(int(desc), int(qi), int(ti), int(rn), int(rd),
+                                out.data_ptr() if out is not None else None)
+        self.ctx._stream()
+        self.ctx._check(lib().bd_batch_set_matches(self.handle, ctypes.cast(arr, ctypes.c_void_p),
+                                                   len(jobs)), "bd_batch_set_matches")
+
+    def set_timeline(self, enable: bool = True):
+        self.ctx._stream()
+        self.ctx._check(lib().bd_batch_set_timeline(self.handle, int(bool(enable))),
+                        "bd_batch_set_timeline")
+
+    def timeline(self):
+        """Item records of the last launch as a numpy structured array
+        (fields of bd_batch_event), in queue order."""
+        import numpy as np
+        n = ctypes.c_int(0)
+        self.ctx._check(lib().bd_batch_get_timeline(self.handle, None, 0, ctypes.byref(n)),
+                        "bd_batch_get_timeline")
+        out = np.zeros(n.value, dtype=BATCH_EVENT_DTYPE)
+        assert out.itemsize == ctypes.sizeof(BatchEvent)
+        if n.value:
+            self.ctx._check(lib().bd_batch_get_timeline(self.handle, _np_ptr(out), n.value,
+                                                        ctypes.byref(n)), "bd_batch_get_timeline")
+        return out
 
     def __del__(self):
         try:

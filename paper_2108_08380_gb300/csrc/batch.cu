@@ -22,6 +22,7 @@
 #include "bad_dev.cuh"
 #include "hashsift_dev.cuh"
 #include "integral_dev.cuh"
+#include "match_dev.cuh"
 
 namespace bd {
 
@@ -32,6 +33,18 @@ struct BatchImageDev {
     int bad_item_begin;      // first BAD item of this image
     size_t ii_off;           // integral table offset (entries)
     size_t cs_off, rs_off, tt_off;  // carry offsets (entries)
+};
+
+// A matching run by the persistent kernel (bd_batch_set_matches): the
+// descriptors of one image against those of another, both from this launch.
+struct BatchMatchDev {
+    const uint32_t *q, *t;
+    bd_match_result *out;
+    uint2 *partial;
+    unsigned int *arrivals;
+    int nq, nt, nbits, rnum, rden, S, chunk, qblocks, begin;
+    int desc;                  // BD_DESC_BAD / BD_DESC_HASHSIFT
+    int qkp, tkp;              // first keypoint (batch index) of the query / train image
 };
 
 struct BatchKernelArgs {
@@ -58,17 +71,31 @@ struct BatchKernelArgs {
     float *hist;
     const bd_keypoint *kps;
     DeviceStatus *status;
+    bd_batch_event *events;  // item timeline, or NULL
+    // matchings (last in the queue)
+    int n_mjobs, match_items;
+    unsigned int *bad_grp_done;   // [ceil(n_kp/32)] BAD descriptors written per 32 keypoints
+    unsigned int *bits_grp_done;  // [ceil(n_kp/32)] projection tiles written per 32 keypoints
+    BatchMatchDev mj[BD_MATCH_MAX_JOBS];
 };
 
 namespace {
 
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+constexpr int kMatchTile = 128;  // train descriptors per shared-memory tile of a matching item
 
 __device__ __forceinline__ unsigned long long gtimer()
 {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+
+__device__ __forceinline__ int smid()
+{
+    int v;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(v));
+    return v;
 }
 
 // thread 0 waits until *ctr >= target (bounded); the CTA learns the outcome.
@@ -93,6 +120,43 @@ __device__ __forceinline__ bool cta_wait_count(const unsigned int *ctr, unsigned
     }
     __syncthreads();
     return *flag_s != 0;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Waits until every 32-keypoint group overlapping [k0, k1) is complete:
+// ctr[g] >= per_group (projection tiles) or, with per_group = 0, >= the
+// group's keypoint count (BAD words).  Thread i checks group g0 + i, so the
+// checks of all groups take one round trip; each spin is bounded like
+// cta_wait_count.  Called by the whole CTA.
+__device__ __forceinline__ bool cta_wait_groups(const unsigned int *ctr, int k0, int k1, int n_kp,
+                                                unsigned int per_group, DeviceStatus *status)
+{
+    int ok = 1;
+    const int g0 = k0 >> 5;
+    const int ng = k1 > k0 ? ((k1 - 1) >> 5) - g0 + 1 : 0;
+    for (int i = threadIdx.x; i < ng; i += blockDim.x) {
+        const int g = g0 + i;
+        const unsigned int target = per_group ? per_group : (unsigned)min(32, n_kp - 32 * g);
+        if (ld_acquire(ctr + g) < target) {
+            const unsigned long long t0 = gtimer();
+            while (ld_acquire(ctr + g) < target) {
+                __nanosleep(200);
+                if (gtimer() - t0 > kWaitNs) {
+                    ok = 0;
+                    dev::raise_flag(status, BD_FLAG_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    return __syncthreads_and(ok) != 0;
 }
 
 __device__ __forceinline__ int find_image(const BatchImageDev *imgs, int n_img, int key, int which)
@@ -186,9 +250,14 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
         dev::IiFinalSmem f;
         dev::WarpHist h[4];  // one per warp
         ProjTile p;
+        struct {
+            uint4 tile[kMatchTile * 16 / 4];  // train descriptors of a matching item
+            uint2 wpair[128];                 // the warps' top-2 pairs
+        } m;
     } U;
     __shared__ unsigned int item_s;
     __shared__ int flag_s;
+    __shared__ int last_cta_s;
     const int t = threadIdx.x;
     // launched with programmatic serialization: wait for the previous kernel
     // (which may still read this launch's outputs), then let the next one
@@ -204,8 +273,10 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
     const int e3 = e2 + A.hs_pre_bad;
     const int e4 = e3 + A.n_bad_items;
     const int e5 = e4 + (n_hs - A.hs_pre_final - A.hs_pre_bad);
-    const int total = e5 + A.proj_items;
+    const int e6 = e5 + A.proj_items;
+    const int total = e6 + A.match_items;
 
+    unsigned long long t_claim = 0, t_ready = 0;
     for (;;) {
         if (t == 0)
             item_s = atomicAdd(A.work, 1u);
@@ -214,6 +285,8 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
         __syncthreads();
         if (item >= total)
             break;
+        if (A.events && t == 0)
+            t_claim = t_ready = gtimer();
         // item -> (kind, index): 0 pass-1 tile, 1 HashSIFT, 2 pass-2 tile, 3 BAD
         int kind, idx;
         if (item < e0) {
@@ -234,10 +307,31 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
         } else if (item < e5) {
             kind = 1;
             idx = A.hs_pre_final + A.hs_pre_bad + item - e4;
-        } else {
+        } else if (item < e6) {
             kind = 4;
             idx = item - e5;
+        } else {
+            kind = 5;
+            idx = item - e6;
         }
+        // thread 0: the item's work is done (before it publishes completion)
+        auto record = [&]() {
+            if (A.events && t == 0) {
+                bd_batch_event ev;
+                ev.kind = kind;
+                ev.index = idx;
+                ev.sm = smid();
+                ev.cta = (int)blockIdx.x;
+                ev.t_claim = t_claim;
+                ev.t_ready = t_ready;
+                ev.t_end = gtimer();
+                A.events[item] = ev;
+            }
+        };
+        auto mark_ready = [&]() {
+            if (A.events && t == 0)
+                t_ready = gtimer();
+        };
         if (kind == 0) {
             const int im = find_image(A.imgs, A.n_img, idx, 0);
             const BatchImageDev &I = A.imgs[im];
@@ -245,6 +339,7 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
             dev::ii_stats_tile(U.s, A.img_ptr[im], I.w, I.h, I.pitch, A.carry + I.cs_off,
                                A.carry + I.rs_off, A.carry + I.tt_off, I.ntx, tl % I.ntx, tl / I.ntx);
             __syncthreads();
+            record();
             if (t == 0) {
                 __threadfence();
                 atomicAdd(A.stats_done + im, 1u);
@@ -277,17 +372,20 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                 }
             }
             __syncthreads();
+            record();
         } else if (kind == 2) {
             const int tile = idx;
             const int im = find_image(A.imgs, A.n_img, tile, 0);
             const BatchImageDev &I = A.imgs[im];
             if (cta_wait_count(A.stats_done + im, (unsigned)(I.ntx * I.nty), &flag_s, A.status)) {
+                mark_ready();
                 const int tl = tile - I.tile_begin;
                 dev::ii_final_tile(U.f, A.img_ptr[im], I.w, I.h, I.pitch, A.carry + I.cs_off,
                                    A.carry + I.rs_off, A.carry + I.tt_off, I.ntx, A.ii + I.ii_off,
                                    I.w + 1, tl % I.ntx, tl / I.ntx);
             }
             __syncthreads();
+            record();
             if (t == 0) {
                 __threadfence();
                 atomicAdd(A.final_done + im, 1u);
@@ -297,14 +395,49 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
             const int g = idx / A.proj_cols, cb = idx % A.proj_cols;
             const int k0 = g * 32;
             const int nk = min(32, A.n_kp - k0);
-            if (cta_wait_count(A.hs_group_done + g, (unsigned)nk, &flag_s, A.status))
+            if (cta_wait_count(A.hs_group_done + g, (unsigned)nk, &flag_s, A.status)) {
+                mark_ready();
                 proj_tile(U.p, A, k0, nk, cb);
+            }
             __syncthreads();
+            record();
+            if (A.n_mjobs && t == 0) {
+                __threadfence();
+                atomicAdd(A.bits_grp_done + g, 1u);
+            }
+        } else if (kind == 5) {
+            int j = 0;
+            while (j + 1 < A.n_mjobs && idx >= A.mj[j + 1].begin)
+                ++j;
+            const BatchMatchDev &M = A.mj[j];
+            const int local = idx - M.begin;
+            // this item's queries and train slice only
+            const bool bad = M.desc == BD_DESC_BAD;
+            const unsigned int *done = bad ? A.bad_grp_done : A.bits_grp_done;
+            const unsigned int per = bad ? 0u : (unsigned)A.proj_cols;
+            const int bx = local % M.qblocks, by = local / M.qblocks;
+            const int q0 = M.qkp + bx * 32, q1 = M.qkp + min(M.nq, bx * 32 + 32);
+            const int t0 = M.tkp + by * M.chunk, t1 = M.tkp + min(M.nt, by * M.chunk + M.chunk);
+            const bool q_ok = cta_wait_groups(done, q0, q1, A.n_kp, per, A.status);
+            if (cta_wait_groups(done, t0, t1, A.n_kp, per, A.status) && q_ok) {
+                mark_ready();
+                if (M.nbits == 256)
+                    dev::match_block32<8, kMatchTile>(U.m.tile, U.m.wpair, M.q, M.nq, M.t, M.nt,
+                                                      M.chunk, M.nbits, M.rnum, M.rden, bx, by, M.S,
+                                                      M.partial, M.out, M.arrivals, last_cta_s);
+                else
+                    dev::match_block32<16, kMatchTile>(U.m.tile, U.m.wpair, M.q, M.nq, M.t, M.nt,
+                                                       M.chunk, M.nbits, M.rnum, M.rden, bx, by, M.S,
+                                                       M.partial, M.out, M.arrivals, last_cta_s);
+            }
+            __syncthreads();
+            record();
         } else {
             const int bi = idx;
             const int im = find_image(A.imgs, A.n_img, bi, 2);
             const BatchImageDev &I = A.imgs[im];
             if (cta_wait_count(A.final_done + im, (unsigned)(I.ntx * I.nty), &flag_s, A.status)) {
+                mark_ready();
                 const int k0 = I.kp_begin + (bi - I.bad_item_begin) * A.bad_per_item;
                 const int k1 = min(I.kp_end, k0 + A.bad_per_item);
                 for (int k = k0 + (t >> 5); k < k1; k += 4)
@@ -313,6 +446,14 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                                                       A.status);
             }
             __syncthreads();
+            record();
+            if (A.n_mjobs && t == 0) {
+                __threadfence();
+                const int k0 = I.kp_begin + (bi - I.bad_item_begin) * A.bad_per_item;
+                const int k1 = min(I.kp_end, k0 + A.bad_per_item);
+                for (int k = k0; k < k1; k = (k | 31) + 1)
+                    atomicAdd(A.bad_grp_done + (k >> 5), (unsigned)(min(k1, (k | 31) + 1) - k));
+            }
         }
     }
     // The last CTA out resets the queue and readiness counters for the next
@@ -331,9 +472,14 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
             A.stats_done[i] = 0u;
             A.final_done[i] = 0u;
         }
-        if (A.proj_items)
-            for (int i = t; i < (A.n_kp + 31) / 32; i += blockDim.x)
+        for (int i = t; i < (A.n_kp + 31) / 32; i += blockDim.x) {
+            if (A.proj_items)
                 A.hs_group_done[i] = 0u;
+            if (A.n_mjobs) {
+                A.bad_grp_done[i] = 0u;
+                A.bits_grp_done[i] = 0u;
+            }
+        }
     }
 }
 
@@ -355,7 +501,9 @@ struct bd_batch {
     const uint8_t **d_ptrs = nullptr;
     std::vector<const uint8_t *> last_ptrs;
     uint32_t *d_ii = nullptr, *d_carry = nullptr;
-    unsigned int *d_counters = nullptr;  // [work][exit][stats_done n_img][final_done n_img][hs groups], zero between launches
+    // [work][exit][stats_done n_img][final_done n_img][hs groups][BAD groups]
+    // [projection groups] (groups of 32 keypoints), zero between launches
+    unsigned int *d_counters = nullptr;
     float *d_hist = nullptr;
     bd_batch_config cfg = {8, 0, 1, 4, 0};
     int max_ctas_per_sm = 0;
@@ -366,9 +514,111 @@ struct bd_batch {
     std::vector<const void *> gkey;
     int graph_kernels = 0;
     std::vector<TraceMark> gmarks;  // trace events recorded by the graph's nodes
+    // item timeline
+    bd_batch_event *d_events = nullptr;
+    int ev_cap = 0;      // records the buffer holds (every configuration fits)
+    int last_items = -1; // items of the last launch that recorded one
+    // matchings
+    std::vector<bd_batch_match> mjobs;
+    void *d_mscratch = nullptr;         // slice partials of every job
+    unsigned int *d_marrivals = nullptr; // per query block, reset by the kernels
+    int m_qblocks = 0;                  // query blocks of all jobs
+    int m_max_items = 0;                // matching items of the finest split
 };
 
 namespace {
+
+constexpr int kMatchQB = 32;        // queries per matching item (one per lane)
+constexpr int kMatchMaxSlices = 8;  // train slices per query block in the persistent kernel
+
+int img_kp(const bd_batch *b, int i) { return b->imgs[i].kp_end - b->imgs[i].kp_begin; }
+
+int job_nbits(const bd_batch *b, const bd_batch_match &j)
+{
+    return j.desc == BD_DESC_BAD ? b->bad->nbits : b->hs->nbits;
+}
+
+int max_slices(int nt)
+{
+    const int s = (nt + kMatchTile - 1) / kMatchTile;
+    return s < 1 ? 1 : (s > kMatchMaxSlices ? kMatchMaxSlices : s);
+}
+
+bool any_hs_job(const bd_batch *b)
+{
+    for (const bd_batch_match &j : b->mjobs)
+        if (j.desc == BD_DESC_HASHSIFT)
+            return true;
+    return false;
+}
+
+// The plan's matchings as bd_match_batch jobs on this call's outputs.
+int plain_jobs(const bd_batch *b, uint32_t *bad_out, uint32_t *hs_out, bd_match_job *J)
+{
+    int n = 0;
+    for (const bd_batch_match &j : b->mjobs) {
+        bd_match_job &a = J[n++];
+        a.nbits = job_nbits(b, j);
+        const int nw = a.nbits / 32;
+        uint32_t *base = j.desc == BD_DESC_BAD ? bad_out : hs_out;
+        a.q = base + (size_t)b->imgs[j.query_image].kp_begin * nw;
+        a.t = base + (size_t)b->imgs[j.train_image].kp_begin * nw;
+        a.out = j.out;
+        a.nq = img_kp(b, j.query_image);
+        a.nt = img_kp(b, j.train_image);
+        a.ratio_num = j.ratio_num;
+        a.ratio_den = j.ratio_den;
+    }
+    return n;
+}
+
+// Matching items of the persistent kernel: job j's query blocks x train
+// slices, S picked so that the jobs together fill about one grid.
+void fill_match_items(const bd_batch *b, BatchKernelArgs &A, uint32_t *bad_out, uint32_t *hs_out,
+                      int grid)
+{
+    int active = 0;
+    for (const bd_batch_match &j : b->mjobs)
+        active += img_kp(b, j.query_image) > 0 ? 1 : 0;
+    const int target = std::max(1, grid / std::max(1, active));
+    int items = 0, m = 0, aoff = 0;
+    size_t poff = 0;
+    for (const bd_batch_match &j : b->mjobs) {
+        const int nq = img_kp(b, j.query_image), nt = img_kp(b, j.train_image);
+        const int qblocks = (nq + kMatchQB - 1) / kMatchQB;
+        const int smax = max_slices(nt);
+        if (nq > 0) {
+            BatchMatchDev &M = A.mj[m++];
+            M.nbits = job_nbits(b, j);
+            const int nw = M.nbits / 32;
+            uint32_t *base = j.desc == BD_DESC_BAD ? bad_out : hs_out;
+            M.q = base + (size_t)b->imgs[j.query_image].kp_begin * nw;
+            M.t = base + (size_t)b->imgs[j.train_image].kp_begin * nw;
+            M.out = j.out;
+            M.nq = nq;
+            M.nt = nt;
+            M.rnum = j.ratio_num;
+            M.rden = j.ratio_den;
+            int S = std::min(std::max(1, (target + qblocks - 1) / qblocks), smax);
+            const int chunk = std::max(1, (nt + S - 1) / S);
+            S = std::max(1, (nt + chunk - 1) / chunk);
+            M.S = S;
+            M.chunk = chunk;
+            M.qblocks = qblocks;
+            M.begin = items;
+            M.partial = reinterpret_cast<uint2 *>(static_cast<char *>(b->d_mscratch) + poff);
+            M.arrivals = b->d_marrivals + aoff;
+            M.desc = j.desc;
+            M.qkp = b->imgs[j.query_image].kp_begin;
+            M.tkp = b->imgs[j.train_image].kp_begin;
+            items += qblocks * S;
+        }
+        poff += align_up((size_t)smax * nq * sizeof(uint2), 256);
+        aoff += qblocks;
+    }
+    A.n_mjobs = m;
+    A.match_items = items;
+}
 
 bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_t *bad_out,
                        uint32_t *hs_out, cudaStream_t st, int *kernels)
@@ -411,6 +661,8 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     A.hist = b->d_hist;
     A.kps = kps;
     A.status = ctx->status;
+    A.bad_grp_done = b->d_counters + 2 + 2 * b->n_img + (b->n_kp + 31) / 32;
+    A.bits_grp_done = A.bad_grp_done + (b->n_kp + 31) / 32;
     int per_sm = b->cfg.ctas_per_sm > 0 ? b->cfg.ctas_per_sm : b->max_ctas_per_sm;
     if (per_sm > b->max_ctas_per_sm)
         per_sm = b->max_ctas_per_sm;
@@ -429,6 +681,11 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
         A.hs_pre_final = 0;
         A.hs_pre_bad = 0;
     }
+    const bool m_in_kernel = !b->mjobs.empty() && (fused || !any_hs_job(b));
+    if (m_in_kernel)
+        fill_match_items(b, A, bad_out, hs_out, grid);
+    const int n_items = 2 * A.n_tiles + A.hs_items + A.n_bad_items + A.proj_items + A.match_items;
+    A.events = (b->d_events && n_items <= b->ev_cap) ? b->d_events : nullptr;
     const bool wide = per_sm > b->occ4;  // needs the 80-register variant to be resident
     if (A.bad_nw == 16)
         e = launch_pdl(wide ? batch_persistent_kernel<16, 6> : batch_persistent_kernel<16, 4>,
@@ -440,6 +697,7 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
         return cuda_err(ctx, e, "bd_describe_batch: persistent kernel");
     trace_kernel(st, "batch_persistent");
     note_launches(1);
+    b->last_items = A.events ? n_items : -1;
     int nk = 1;
     e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -454,6 +712,14 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
         ++nk;
         if (e != cudaSuccess)
             return cuda_err(ctx, e, "bd_describe_batch: projection kernel");
+    }
+    if (!b->mjobs.empty() && !m_in_kernel) {
+        bd_match_job J[BD_MATCH_MAX_JOBS];
+        const int n = plain_jobs(b, bad_out, hs_out, J);
+        e = launch_match_batch(J, n, b->d_mscratch, ctx->sm_count, st, b->d_marrivals);
+        ++nk;
+        if (e != cudaSuccess)
+            return cuda_err(ctx, e, "bd_describe_batch: matching kernel");
     }
     if (kernels)
         *kernels = nk;
@@ -558,7 +824,7 @@ bd_status bd_batch_create(bd_ctx *ctx, const bd_bad_params *bad, const bd_hs_par
         if (e == cudaSuccess) e = cudaMalloc(&b->d_ptrs, sizeof(void *) * n_img);
         if (e == cudaSuccess && bad) e = cudaMalloc(&b->d_ii, sizeof(uint32_t) * ii_total);
         if (e == cudaSuccess && bad) e = cudaMalloc(&b->d_carry, sizeof(uint32_t) * carry_total);
-        const size_t ncount = 2 + 2 * (size_t)n_img + (size_t)(b->n_kp + 31) / 32;
+        const size_t ncount = 2 + 2 * (size_t)n_img + 3 * ((size_t)(b->n_kp + 31) / 32);
         if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(unsigned int) * ncount);
         if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, sizeof(unsigned int) * ncount);
         if (e == cudaSuccess && hs) e = cudaMalloc(&b->d_hist, sizeof(float) * kHistDim * (size_t)(b->n_kp > 0 ? b->n_kp : 1));
@@ -600,6 +866,9 @@ void bd_batch_destroy(bd_batch *b)
     if (b->d_carry) cudaFree(b->d_carry);
     if (b->d_counters) cudaFree(b->d_counters);
     if (b->d_hist) cudaFree(b->d_hist);
+    if (b->d_events) cudaFree(b->d_events);
+    if (b->d_mscratch) cudaFree(b->d_mscratch);
+    if (b->d_marrivals) cudaFree(b->d_marrivals);
     if (prev >= 0 && prev != b->ctx->device)
         cudaSetDevice(prev);
     delete b;
@@ -649,6 +918,12 @@ bd_status bd_describe_batch(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     if (b->hs && (b->hs->variant & BD_HS_VARIANT_TRILINEAR))
         return set_err(ctx, BD_ERR_UNSUPPORTED,
                        "bd_describe_batch: trilinear binning is not available in the batched kernel");
+    for (const bd_batch_match &j : b->mjobs) {
+        uint32_t *o = j.desc == BD_DESC_BAD ? bad_out : hs_out;
+        if (!o || (reinterpret_cast<uintptr_t>(o) & 15))
+            return set_err(ctx, BD_ERR_INVALID,
+                           "bd_describe_batch: a matching needs its descriptors (16-byte aligned)");
+    }
     for (int i = 0; i < b->n_img; ++i)
         if (!imgs[i])
             return set_err(ctx, BD_ERR_INVALID, "bd_describe_batch: image %d is NULL", i);
@@ -680,6 +955,7 @@ bd_status bd_describe_batch(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     // kernel argument: re-capture when either changes
     key.push_back(reinterpret_cast<const void *>((uintptr_t)(ctx->trace ? 1 : 0)));
     key.push_back(reinterpret_cast<const void *>((uintptr_t)(b->hs ? b->hs->variant : 0)));
+    key.push_back(b->d_events);
     if (!b->gexec || key != b->gkey) {
         drop_graph(b);
         cudaGraph_t g = nullptr;
@@ -793,6 +1069,128 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     if (best_ms)
         *best_ms = win_ms;
     return s;
+}
+
+bd_status bd_batch_set_timeline(bd_batch *b, int enable)
+{
+    if (!b)
+        return BD_ERR_INVALID;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->ctx->device)
+        cudaSetDevice(b->ctx->device);
+    cudaError_t e = cudaStreamSynchronize(b->ctx->stream);
+    drop_graph(b);
+    if (b->d_events) {
+        cudaFree(b->d_events);
+        b->d_events = nullptr;
+        b->ev_cap = 0;
+    }
+    b->last_items = -1;
+    if (enable && e == cudaSuccess) {
+        // the most items any configuration queues: pass-1 and pass-2 tiles,
+        // one HashSIFT item per keypoint, BAD items of 4 keypoints, and
+        // projection tiles of 32 keypoints x 32 of at most 512 bits
+        const long long cap = 2LL * b->n_tiles + b->n_kp + (b->n_kp / 4 + b->n_img) +
+                              ((long long)(b->n_kp + 31) / 32) * 16 + b->m_max_items + 1;
+        if (cap > 0x7fffffffLL / (long long)sizeof(bd_batch_event))
+            e = cudaErrorMemoryAllocation;
+        else
+            e = cudaMalloc(&b->d_events, sizeof(bd_batch_event) * (size_t)cap);
+        if (e == cudaSuccess)
+            b->ev_cap = (int)cap;
+        else
+            b->d_events = nullptr;
+    }
+    if (prev >= 0 && prev != b->ctx->device)
+        cudaSetDevice(prev);
+    return e == cudaSuccess ? BD_OK : cuda_err(b->ctx, e, "bd_batch_set_timeline");
+}
+
+bd_status bd_batch_get_timeline(bd_batch *b, bd_batch_event *out, int cap, int *n)
+{
+    if (!b || (!out && cap > 0) || cap < 0 || !n)
+        return BD_ERR_INVALID;
+    if (!b->d_events || b->last_items < 0)
+        return set_err(b->ctx, BD_ERR_INVALID, "bd_batch_get_timeline: no timeline recorded");
+    *n = b->last_items;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->ctx->device)
+        cudaSetDevice(b->ctx->device);
+    cudaError_t e = cudaStreamSynchronize(b->ctx->stream);
+    const int m = cap < b->last_items ? cap : b->last_items;
+    if (e == cudaSuccess && m > 0)
+        e = cudaMemcpy(out, b->d_events, sizeof(bd_batch_event) * (size_t)m, cudaMemcpyDeviceToHost);
+    if (prev >= 0 && prev != b->ctx->device)
+        cudaSetDevice(prev);
+    return e == cudaSuccess ? BD_OK : cuda_err(b->ctx, e, "bd_batch_get_timeline");
+}
+
+bd_status bd_batch_set_matches(bd_batch *b, const bd_batch_match *jobs, int n_jobs)
+{
+    if (!b || n_jobs < 0 || n_jobs > BD_MATCH_MAX_JOBS || (n_jobs > 0 && !jobs))
+        return b ? set_err(b->ctx, BD_ERR_INVALID, "bd_batch_set_matches: bad arguments")
+                 : BD_ERR_INVALID;
+    for (int k = 0; k < n_jobs; ++k) {
+        const bd_batch_match &j = jobs[k];
+        const bool desc_ok = (j.desc == BD_DESC_BAD && b->bad) || (j.desc == BD_DESC_HASHSIFT && b->hs);
+        const bool img_ok = j.query_image >= 0 && j.query_image < b->n_img && j.train_image >= 0 &&
+                            j.train_image < b->n_img;
+        if (!desc_ok || !img_ok || j.ratio_num <= 0 || j.ratio_den <= 0 || j.ratio_num > j.ratio_den ||
+            (img_ok && img_kp(b, j.query_image) > 0 &&
+             (!j.out || (reinterpret_cast<uintptr_t>(j.out) & 3))) ||
+            (img_ok && img_kp(b, j.train_image) > (int)kMatchIdxMask))
+            return set_err(b->ctx, BD_ERR_INVALID, "bd_batch_set_matches: bad job %d", k);
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->ctx->device)
+        cudaSetDevice(b->ctx->device);
+    cudaError_t e = cudaStreamSynchronize(b->ctx->stream);
+    drop_graph(b);
+    if (b->d_mscratch) {
+        cudaFree(b->d_mscratch);
+        b->d_mscratch = nullptr;
+    }
+    if (b->d_marrivals) {
+        cudaFree(b->d_marrivals);
+        b->d_marrivals = nullptr;
+    }
+    b->mjobs.assign(jobs, jobs + n_jobs);
+    // scratch for either way of running them: the persistent kernel's finest
+    // split, or the matching launch's own plan
+    size_t fused_bytes = 0;
+    int qblocks = 0, items = 0;
+    for (const bd_batch_match &j : b->mjobs) {
+        const int nq = img_kp(b, j.query_image), nt = img_kp(b, j.train_image);
+        const int qb = (nq + kMatchQB - 1) / kMatchQB;
+        fused_bytes += align_up((size_t)max_slices(nt) * nq * sizeof(uint2), 256);
+        qblocks += qb;
+        items += qb * max_slices(nt);
+    }
+    bd_match_job J[BD_MATCH_MAX_JOBS];
+    const int n = plain_jobs(b, nullptr, nullptr, J);
+    const size_t plain_bytes = match_batch_scratch_bytes(J, n, b->ctx->sm_count);
+    const size_t bytes = std::max(std::max(fused_bytes, plain_bytes), (size_t)256);
+    b->m_qblocks = qblocks;
+    b->m_max_items = items;
+    if (e == cudaSuccess && n_jobs > 0)
+        e = cudaMalloc(&b->d_mscratch, bytes);
+    if (e == cudaSuccess && n_jobs > 0)
+        e = cudaMalloc(&b->d_marrivals, sizeof(unsigned int) * (size_t)std::max(qblocks, 1));
+    if (e == cudaSuccess && n_jobs > 0)
+        e = cudaMemset(b->d_marrivals, 0, sizeof(unsigned int) * (size_t)std::max(qblocks, 1));
+    if (prev >= 0 && prev != b->ctx->device)
+        cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        b->mjobs.clear();
+        return cuda_err(b->ctx, e, "bd_batch_set_matches");
+    }
+    // the timeline buffer must hold the matching items too
+    if (b->d_events)
+        return bd_batch_set_timeline(b, 1);
+    return BD_OK;
 }
 
 }  // extern "C"

@@ -61,13 +61,18 @@ __device__ __forceinline__ void ii_stats_tile(IiStatsSmem &S, const uint8_t *__r
 {
     const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
     const int x = tx * IITC + t, y0 = ty * IITR;
-    uint32_t cs = 0;
-#pragma unroll 8
+    // all 32 loads in flight at once: one memory round trip per tile
+    uint32_t px[IITR];
+#pragma unroll
     for (int r = 0; r < IITR; ++r) {
         const int y = y0 + r;
-        const uint32_t v = (x < w && y < h) ? (uint32_t)__ldg(img + (size_t)y * pitch + x) : 0u;
-        S.tile[r][t] = v;
-        cs += v;
+        px[r] = (x < w && y < h) ? (uint32_t)__ldg(img + (size_t)y * pitch + x) : 0u;
+    }
+    uint32_t cs = 0;
+#pragma unroll
+    for (int r = 0; r < IITR; ++r) {
+        S.tile[r][t] = px[r];
+        cs += px[r];
     }
     if (x < w)
         colsum[(size_t)ty * w + x] = cs;
@@ -97,10 +102,38 @@ __device__ __forceinline__ void ii_final_tile(IiFinalSmem &S, const uint8_t *__r
     const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
     const int x = tx * IITC + t, y0 = ty * IITR;
 
+    constexpr int RPW = IITR / (IITC / 32);  // rows rebuilt per warp (8)
+    // this warp's rows first (4 bytes per lane each, one word load when
+    // aligned): they do not depend on the carries, so their round trip
+    // overlaps the carry reads below
+    uint32_t px[RPW];
+    {
+        const int c0 = tx * IITC + lane * 4;
+        const bool words = ((reinterpret_cast<uintptr_t>(img) | (uintptr_t)pitch) & 3) == 0 && c0 + 3 < w;
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int y = y0 + wp * RPW + q;
+            uint32_t v = 0u;
+            if (y < h) {
+                const uint8_t *row = img + (size_t)y * pitch + c0;
+                if (words) {
+                    v = __ldg(reinterpret_cast<const uint32_t *>(row));
+                } else {
+                    const uint32_t b0 = c0 + 0 < w ? __ldg(row + 0) : 0u;
+                    const uint32_t b1 = c0 + 1 < w ? __ldg(row + 1) : 0u;
+                    const uint32_t b2 = c0 + 2 < w ? __ldg(row + 2) : 0u;
+                    const uint32_t b3 = c0 + 3 < w ? __ldg(row + 3) : 0u;
+                    v = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+                }
+            }
+            px[q] = v;
+        }
+    }
+
     // column sums of all bands above this one
     uint32_t v = 0;
     if (x < w) {
-#pragma unroll 8
+#pragma unroll 16
         for (int a = 0; a < ty; ++a)
             v += __ldcg(colsum + (size_t)a * w + x);
     }
@@ -111,45 +144,37 @@ __device__ __forceinline__ void ii_final_tile(IiFinalSmem &S, const uint8_t *__r
     for (int i = t; i < nab; i += IITC)
         g += __ldcg(tiletot + (size_t)(i / tx) * ntx + (i % tx));
     g = warp_sum_u32(g);
+    // row sums of the tiles to the left
+    uint32_t rl = 0;
+    if (wp == 0) {
+        const int y = y0 + lane;
+        if (y < h) {
+#pragma unroll 8
+            for (int a = 0; a < tx; ++a)
+                rl += __ldcg(rowsum + (size_t)y * ntx + a);
+        }
+    }
     // inclusive scan of v across the tile's columns
     uint32_t vs = warp_incl_scan_u32(v, lane);
     if (lane == 31)
         S.wtot[wp] = vs;
     if (lane == 0)
         S.gpart[wp] = g;
-    // row sums of the tiles to the left
-    if (wp == 0) {
-        uint32_t r = 0;
-        const int y = y0 + lane;
-        if (y < h) {
-#pragma unroll 8
-            for (int a = 0; a < tx; ++a)
-                r += __ldcg(rowsum + (size_t)y * ntx + a);
-        }
-        S.R[lane] = r;
-    }
+    if (wp == 0)
+        S.R[lane] = rl;
     __syncthreads();
     for (int q = 0; q < wp; ++q)
         vs += S.wtot[q];
     uint32_t acc = S.gpart[0] + S.gpart[1] + S.gpart[2] + S.gpart[3] + vs;
 
     // per-row inclusive prefix inside the tile, plus the carry from the left
-#pragma unroll 2
-    for (int q = 0; q < IITR / (IITC / 32); ++q) {
-        const int r = wp * (IITR / (IITC / 32)) + q;
-        const int y = y0 + r;
-        const int c0 = tx * IITC + lane * 4;
-        uint32_t p0 = 0, p1 = 0, p2 = 0, p3 = 0;
-        if (y < h) {
-            const uint8_t *row = img + (size_t)y * pitch;
-            p0 = c0 + 0 < w ? __ldg(row + c0 + 0) : 0u;
-            p1 = c0 + 1 < w ? __ldg(row + c0 + 1) : 0u;
-            p2 = c0 + 2 < w ? __ldg(row + c0 + 2) : 0u;
-            p3 = c0 + 3 < w ? __ldg(row + c0 + 3) : 0u;
-        }
-        p1 += p0;
-        p2 += p1;
-        p3 += p2;
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+        const int r = wp * RPW + q;
+        const uint32_t p0 = px[q] & 0xFFu;
+        const uint32_t p1 = p0 + ((px[q] >> 8) & 0xFFu);
+        const uint32_t p2 = p1 + ((px[q] >> 16) & 0xFFu);
+        const uint32_t p3 = p2 + (px[q] >> 24);
         const uint32_t incl = warp_incl_scan_u32(p3, lane);
         const uint32_t base = incl - p3 + S.R[r];
         S.rowinc[r][lane * 4 + 0] = base + p0;

@@ -1,17 +1,10 @@
-// Brute-force Hamming matching with a fused top-2 and ratio test (Sec. IV-C
-// nearest-neighbour matching; Sec. III-A: S = K - 2 * Hamming for +-1 codes).
-//
-// Each thread keeps one query descriptor in registers; a CTA of 128 queries
-// streams a slice of the train set through shared memory (all lanes read the
-// same train descriptor, a broadcast) and keeps, per query, the two smallest
-// packed keys (distance << 22 | train index).  Comparing packed keys orders
-// by distance, then by lowest index, so the first key gives the nearest
-// neighbour and the second key's distance is d2.  When the train set is split
-// across CTAs, each CTA publishes its per-slice top-2 pairs and the last CTA of
-// a query block (per-block arrival counter, reset by that CTA) merges them.
+// Brute-force Hamming matching kernels with a fused top-2 and ratio test
+// (Sec. IV-C nearest-neighbour matching): one query per thread, 128 queries
+// per CTA, the train set split across CTAs into slices merged by the last
+// CTA of each query block (the body is in match_dev.cuh).
 #include <string.h>
 
-#include "bd_internal.h"
+#include "match_dev.cuh"
 
 namespace bd {
 namespace {
@@ -19,26 +12,7 @@ namespace {
 constexpr int QB = 128;   // queries per CTA (one per thread)
 constexpr int TT = 256;   // train descriptors per shared-memory tile
 
-__device__ __forceinline__ void top2_push(uint32_t key, uint32_t &k1, uint32_t &k2)
-{
-    k2 = min(k2, max(k1, key));
-    k1 = min(k1, key);
-}
-
-__device__ __forceinline__ void finalize(uint32_t k1, uint32_t k2, int nbits, int rnum, int rden,
-                                         bd_match_result *o)
-{
-    const uint32_t d1 = k1 >> kMatchIdxBits, d2 = k2 >> kMatchIdxBits;
-    const int32_t idx = (d1 > (uint32_t)nbits) ? -1 : (int32_t)(k1 & kMatchIdxMask);
-    const uint32_t acc = ((long long)rden * d1 < (long long)rnum * d2) ? 1u : 0u;
-    uint32_t *w = reinterpret_cast<uint32_t *>(o);
-    w[0] = (uint32_t)idx;
-    w[1] = d1 | (d2 << 16);
-    w[2] = acc;
-}
-
-// One CTA of the matching: queries [bx*QB, bx*QB + QB) against train slice by
-// of S (chunk entries each); with S > 1 the last CTA of the query block merges.
+// programmatic launch: wait for the kernel that wrote the descriptors
 template <int NW>
 __device__ __forceinline__ void match_cta(uint4 *tile, const uint32_t *__restrict__ q, int nq,
                                           const uint32_t *__restrict__ t, int nt, int chunk,
@@ -47,78 +21,10 @@ __device__ __forceinline__ void match_cta(uint4 *tile, const uint32_t *__restric
                                           bd_match_result *__restrict__ out,
                                           unsigned int *__restrict__ arrivals, int &last_cta)
 {
-    // programmatic launch: wait for the kernel that wrote the descriptors
     dev::griddep_wait();
     dev::griddep_launch_dependents();
-    const int qi = bx * QB + threadIdx.x;
-    const int t0 = by * chunk;
-    const int t1 = min(nt, t0 + chunk);
-
-    uint32_t qd[NW];
-    if (qi < nq) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(q + (size_t)qi * NW);
-#pragma unroll
-        for (int v = 0; v < NW / 4; ++v) {
-            const uint4 x = __ldg(src + v);
-            qd[4 * v + 0] = x.x;
-            qd[4 * v + 1] = x.y;
-            qd[4 * v + 2] = x.z;
-            qd[4 * v + 3] = x.w;
-        }
-    } else {
-#pragma unroll
-        for (int v = 0; v < NW; ++v)
-            qd[v] = 0;
-    }
-    const uint32_t sentinel = ((uint32_t)(nbits + 1) << kMatchIdxBits) | kMatchIdxMask;
-    uint32_t k1 = sentinel, k2 = sentinel;
-
-    for (int base = t0; base < t1; base += TT) {
-        const int cnt = min(TT, t1 - base);
-        __syncthreads();
-        const uint4 *src = reinterpret_cast<const uint4 *>(t + (size_t)base * NW);
-        for (int v = threadIdx.x; v < cnt * NW / 4; v += QB)
-            tile[v] = __ldg(src + v);
-        __syncthreads();
-#pragma unroll 2
-        for (int j = 0; j < cnt; ++j) {
-            uint32_t d = 0;
-#pragma unroll
-            for (int v = 0; v < NW / 4; ++v) {
-                const uint4 x = tile[j * (NW / 4) + v];
-                d += __popc(qd[4 * v + 0] ^ x.x) + __popc(qd[4 * v + 1] ^ x.y) +
-                     __popc(qd[4 * v + 2] ^ x.z) + __popc(qd[4 * v + 3] ^ x.w);
-            }
-            top2_push((d << kMatchIdxBits) | (uint32_t)(base + j), k1, k2);
-        }
-    }
-    if (S == 1) {
-        if (qi < nq)
-            finalize(k1, k2, nbits, rnum, rden, out + qi);
-        return;
-    }
-    if (qi < nq)
-        partial[(size_t)by * nq + qi] = make_uint2(k1, k2);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned int prev = atomicAdd(arrivals + bx, 1u);
-        last_cta = prev == (unsigned)S - 1;
-        if (last_cta)
-            arrivals[bx] = 0u;  // every slice has arrived: ready for the next call
-    }
-    __syncthreads();
-    if (!last_cta || qi >= nq)
-        return;
-    __threadfence();
-    uint2 a = __ldcg(partial + qi);
-    for (int s = 1; s < S; ++s) {
-        const uint2 b = __ldcg(partial + (size_t)s * nq + qi);
-        const uint32_t m1 = min(a.x, b.x);
-        const uint32_t m2 = min(max(a.x, b.x), min(a.y, b.y));
-        a = make_uint2(m1, m2);
-    }
-    finalize(a.x, a.y, nbits, rnum, rden, out + qi);
+    dev::match_block<NW, QB, TT>(tile, q, nq, t, nt, chunk, nbits, rnum, rden, bx, by, S, partial,
+                                 out, arrivals, last_cta);
 }
 
 template <int NW>

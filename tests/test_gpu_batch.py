@@ -194,3 +194,135 @@ def test_fused_fp32_projection_equals_tensor_core_path(gpu_ctx, hs_mode):
             assert np.array_equal(res[0], res[1])
             assert gpu_ctx.sync_status() == 0
             b.close()
+
+
+@pytest.mark.parametrize("cfg", [(8, 4, 0, 4, 0), (4, 2, 1, 1, 1), (32, 6, 2, 4, 1)])
+def test_timeline_respects_dependencies(gpu_ctx, cfg):
+    """The item timeline lists every queued item once, and no item starts
+    before the items it depends on ended: pass-2 tiles after all pass-1 tiles
+    of their image, BAD items after all pass-2 tiles of their image,
+    projection tiles after the HashSIFT items of their 32 keypoints were
+    claimed.  Recording it does not change the descriptors."""
+    import math
+    import torch
+    from paper_2108_08380_gb300 import (BD_ITEM_BAD, BD_ITEM_HASHSIFT, BD_ITEM_II_PASS1,
+                                        BD_ITEM_II_PASS2, BD_ITEM_PROJ)
+    imgs, kps, offs, bad, hs = _small_batch(seed=21)
+    bp, hp = gpu_ctx.bad_params(bad), gpu_ctx.hs_params(hs)
+    dimgs = [_dev(im) for im in imgs]
+    b = gpu_ctx.batch(bp, hp, dimgs, offs)
+    n = len(kps)
+    dk = _dev(kps)
+    it, _, _, hm, fused = cfg
+    b.set_config(*cfg)
+    ob0 = torch.zeros((n, 8), dtype=torch.int32, device="cuda")
+    oh0 = torch.zeros((n, 8), dtype=torch.int32, device="cuda")
+    b.describe(dimgs, dk, ob0, oh0, graph=True)
+    b.set_timeline(True)
+    ob = torch.zeros((n, 8), dtype=torch.int32, device="cuda")
+    oh = torch.zeros((n, 8), dtype=torch.int32, device="cuda")
+    b.describe(dimgs, dk, ob, oh, graph=True)
+    ev = b.timeline()
+    assert gpu_ctx.sync_status() == 0
+    assert np.array_equal(_u32(ob), _u32(ob0)) and np.array_equal(_u32(oh), _u32(oh0))
+
+    tiles = [math.ceil(im.shape[1] / 128) * math.ceil(im.shape[0] / 32) for im in imgs]
+    tile_img = np.repeat(np.arange(len(imgs)), tiles)
+    counts = np.diff(offs)
+    bad_items = [math.ceil(c / it) for c in counts]
+    bad_img = np.repeat(np.arange(len(imgs)), bad_items)
+    n_hs = math.ceil(n / hm)
+    n_proj = math.ceil(n / 32) * 8 if fused else 0
+    expect = {BD_ITEM_II_PASS1: sum(tiles), BD_ITEM_II_PASS2: sum(tiles), BD_ITEM_BAD: sum(bad_items),
+              BD_ITEM_HASHSIFT: n_hs, BD_ITEM_PROJ: n_proj}
+    assert len(ev) == sum(expect.values())
+    by = {}
+    for kind, cnt in expect.items():
+        e = ev[ev["kind"] == kind]
+        e = e[np.argsort(e["index"])]
+        assert np.array_equal(e["index"], np.arange(cnt)), kind
+        by[kind] = e
+    assert np.all(ev["t_claim"] <= ev["t_ready"]) and np.all(ev["t_ready"] <= ev["t_end"])
+    assert np.all(ev["cta"] >= 0) and np.all(ev["sm"] >= 0)
+    p1, p2, bd = by[BD_ITEM_II_PASS1], by[BD_ITEM_II_PASS2], by[BD_ITEM_BAD]
+    for i in range(len(imgs)):
+        end1 = p1["t_end"][tile_img == i].max()
+        assert np.all(p2["t_ready"][tile_img == i] >= end1)
+        if bad_items[i]:
+            end2 = p2["t_end"][tile_img == i].max()
+            assert np.all(bd["t_ready"][bad_img == i] >= end2)
+    if fused:
+        hsi, pr = by[BD_ITEM_HASHSIFT], by[BD_ITEM_PROJ]
+        for g in range(math.ceil(n / 32)):
+            first, last = (32 * g) // hm, (min(n, 32 * g + 32) - 1) // hm
+            claimed = hsi["t_claim"][first:last + 1].max()
+            assert np.all(pr["t_ready"][g * 8:(g + 1) * 8] >= claimed)
+    b.set_timeline(False)
+    b.close()
+
+
+@pytest.mark.parametrize("fused,graph", [(1, True), (1, False), (0, True)])
+def test_batch_matchings_equal_bd_match(gpu_ctx, fused, graph):
+    """Matchings set on the plan give the records bd_match gives on the same
+    descriptors: inside the persistent launch (proj_fused = 1) or as the
+    matching launch after the projection (proj_fused = 0).  Jobs cover both
+    descriptors, both directions, an image pair of very different sizes, a
+    query image and a train image without keypoints."""
+    import torch
+    from paper_2108_08380_gb300 import BD_DESC_BAD, BD_DESC_HASHSIFT
+    imgs, kps, offs, bad, hs = _small_batch(seed=31)
+    bp, hp = gpu_ctx.bad_params(bad), gpu_ctx.hs_params(hs)
+    dimgs = [_dev(im) for im in imgs]
+    b = gpu_ctx.batch(bp, hp, dimgs, offs)
+    n = len(kps)
+    dk = _dev(kps)
+    cnt = np.diff(offs)
+    spec = [(BD_DESC_BAD, 0, 5, 4, 5), (BD_DESC_HASHSIFT, 0, 5, 4, 5), (BD_DESC_BAD, 5, 0, 7, 10),
+            (BD_DESC_HASHSIFT, 3, 4, 1, 1), (BD_DESC_BAD, 2, 0, 4, 5), (BD_DESC_HASHSIFT, 1, 2, 4, 5),
+            (BD_DESC_BAD, 4, 4, 4, 5), (BD_DESC_HASHSIFT, 5, 3, 9, 10)]
+    outs = [torch.full((max(int(cnt[q]), 1), 3), -7, dtype=torch.int32, device="cuda")
+            if cnt[q] else None for (_, q, _, _, _) in spec]
+    b.set_config(8, 4, 2, 4, fused)
+    b.set_matches([(d, q, t, o, rn, rd) for (d, q, t, rn, rd), o in zip(spec, outs)])
+    ob = torch.zeros((n, 8), dtype=torch.int32, device="cuda")
+    oh = torch.zeros((n, 8), dtype=torch.int32, device="cuda")
+    for _ in range(2):  # the second call reuses the reset counters
+        b.describe(dimgs, dk, ob, oh, graph=graph)
+    assert gpu_ctx.sync_status() == 0
+    for (d, q, t, rn, rd), o in zip(spec, outs):
+        if o is None:
+            continue
+        desc = ob if d == BD_DESC_BAD else oh
+        qd = desc[offs[q]:offs[q + 1]].contiguous()
+        td = desc[offs[t]:offs[t + 1]].contiguous()
+        ref = gpu_ctx.match(qd, td, 256, rn, rd)
+        assert np.array_equal(o.cpu().numpy(), ref.cpu().numpy()), (d, q, t)
+    # one job straight against the oracle
+    d0 = _u32(ob)
+    import paper_2108_08380_gb300 as bdm
+    got = bdm.unpack_matches(outs[0])
+    exp = oracle.match(d0[offs[0]:offs[1]], d0[offs[5]:offs[6]], 256)
+    for g, r in zip(got, exp):
+        assert np.array_equal(g, r)
+    b.set_matches([])
+    b.close()
+
+
+def test_batch_matchings_rejected_without_descriptors(gpu_ctx):
+    import torch
+    from paper_2108_08380_gb300 import BD_DESC_BAD, BD_DESC_HASHSIFT, BindescError
+    imgs, kps, offs, bad, hs = _small_batch(seed=32)
+    bp = gpu_ctx.bad_params(bad)
+    dimgs = [_dev(im) for im in imgs]
+    b = gpu_ctx.batch(bp, None, dimgs, offs)
+    o = torch.zeros((int(offs[1]), 3), dtype=torch.int32, device="cuda")
+    with pytest.raises(BindescError):  # no HashSIFT parameters in the plan
+        b.set_matches([(BD_DESC_HASHSIFT, 0, 5, o, 4, 5)])
+    with pytest.raises(BindescError):  # image out of range
+        b.set_matches([(BD_DESC_BAD, 0, 6, o, 4, 5)])
+    with pytest.raises(BindescError):  # ratio above 1
+        b.set_matches([(BD_DESC_BAD, 0, 5, o, 5, 4)])
+    b.set_matches([(BD_DESC_BAD, 0, 5, o, 4, 5)])
+    with pytest.raises(BindescError):  # the BAD output the job reads is missing
+        b.describe(dimgs, _dev(kps), None, None)
+    b.close()
