@@ -262,7 +262,8 @@ typedef struct bd_batch bd_batch;
  *  hs_first         where the HashSIFT items (which depend on nothing) sit in
  *                   the queue: 0 after the BAD items, 1 before the integral
  *                   pass-2 tiles, 2 one grid's worth before the pass-2 tiles,
- *                   one before the BAD items and the rest after them.
+ *                   one before the BAD items and the rest after them, 3 spread
+ *                   evenly among the BAD items.
  *  hs_kp_per_item   HashSIFT keypoints per work item: 1 = the CTA's four warps
  *                   share each keypoint (lower latency, for few keypoints),
  *                   4 = one keypoint per warp (higher throughput).
@@ -271,13 +272,17 @@ typedef struct bd_batch bd_batch;
  *                   1: the persistent kernel projects them itself, 32 x 32
  *                   tiles in FP32 in the FP32 path's summation order (the
  *                   same bits as both paths; no rescue, one launch fewer, for
- *                   small batches). */
+ *                   small batches).
+ *  bad_shared       0: one BAD keypoint per warp; 1: the CTA's four warps share
+ *                   each keypoint, a quarter of its words each (one
+ *                   integral-image window per CTA in L1 instead of four). */
 typedef struct bd_batch_config {
     int bad_kp_per_item;
     int ctas_per_sm;
     int hs_first;
     int hs_kp_per_item;
     int proj_fused;
+    int bad_shared;
 } bd_batch_config;
 
 /* Plans the description of n_img images with BAD and/or HashSIFT (either

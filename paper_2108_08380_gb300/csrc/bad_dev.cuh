@@ -55,17 +55,20 @@ __device__ __forceinline__ void bad_cell(const BadTables &T, const bd_keypoint &
         b += T.nbins;
 }
 
-// Writes the NW words of keypoint kp to out[0..NW); all 32 lanes call it.
-template <int NW, bool ReadOnly>
-__device__ __forceinline__ void bad_describe_warp(const BadTables &T, const uint32_t *ii, int stride,
-                                                  int w, int h, const bd_keypoint &kp,
-                                                  uint32_t *out, DeviceStatus *status)
+// Writes words [word0, word0 + WPW) of the NW words of keypoint kp to
+// out[word0 ..]; all 32 lanes of the warp call it.  WPW = NW: the whole
+// descriptor by one warp; WPW = NW / 4: the four warps of a CTA share the
+// keypoint (its integral-image window is then read by one CTA, not four).
+template <int NW, int WPW, bool ReadOnly>
+__device__ __forceinline__ void bad_describe_words(const BadTables &T, const uint32_t *ii,
+                                                   int stride, int w, int h, const bd_keypoint &kp,
+                                                   uint32_t *out, DeviceStatus *status, int word0)
 {
     constexpr int K = NW * 32;
     const int lane = threadIdx.x & 31;
     if (!kp_valid(kp)) {
-        if (lane < NW)
-            out[lane] = 0u;
+        if (lane < WPW)
+            out[word0 + lane] = 0u;
         if (lane == 0)
             raise_flag(status, BD_FLAG_INVALID_KEYPOINT);
         return;
@@ -79,9 +82,9 @@ __device__ __forceinline__ void bad_describe_warp(const BadTables &T, const uint
     uint32_t mine = 0;
     // a group's table reads first, then all its gathers: the warp keeps
     // 8 x 8 independent loads in flight instead of walking the bits in series
-    constexpr int G = NW < 8 ? NW : 8;
+    constexpr int G = WPW < 8 ? WPW : 8;
 #pragma unroll 1
-    for (int j0 = 0; j0 < NW; j0 += G) {
+    for (int j0 = word0; j0 < word0 + WPW; j0 += G) {
         short4 c[G];
         int2 s[G];
 #pragma unroll
@@ -95,12 +98,21 @@ __device__ __forceinline__ void bad_describe_warp(const BadTables &T, const uint
             const uint32_t s2 = box_sum<ReadOnly>(ii, stride, w, h, ix + c[g].z, iy + c[g].w, s[g].x);
             const bool bit = ((int)s1 - (int)s2) <= s[g].y;
             const uint32_t word = __ballot_sync(0xffffffffu, bit);
-            if (lane == j0 + g)
+            if (lane == j0 - word0 + g)
                 mine = word;
         }
     }
-    if (lane < NW)
-        out[lane] = mine;
+    if (lane < WPW)
+        out[word0 + lane] = mine;
+}
+
+// Writes the NW words of keypoint kp to out[0..NW); all 32 lanes call it.
+template <int NW, bool ReadOnly>
+__device__ __forceinline__ void bad_describe_warp(const BadTables &T, const uint32_t *ii, int stride,
+                                                  int w, int h, const bd_keypoint &kp,
+                                                  uint32_t *out, DeviceStatus *status)
+{
+    bad_describe_words<NW, NW, ReadOnly>(T, ii, stride, w, h, kp, out, status, 0);
 }
 
 inline BadTables bad_tables(const bd_bad_params *p)

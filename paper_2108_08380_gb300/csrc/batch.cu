@@ -51,6 +51,7 @@ struct BatchKernelArgs {
     const BatchImageDev *imgs;
     const uint8_t *const *img_ptr;
     int n_img, n_tiles, n_kp, n_bad_items, bad_per_item;
+    int bad_shared;          // 1: the CTA's four warps share each BAD keypoint
     int hs_items;            // ceil(n_kp / hs_per_item) if HashSIFT is on, else 0
     int hs_per_item;         // 1: the CTA shares a keypoint; 4: one keypoint per warp
     int hs_flags;            // BD_HS_VARIANT_CLIP / _ROOT
@@ -62,6 +63,7 @@ struct BatchKernelArgs {
     uint32_t *hs_out;
     int hs_first;
     int hs_pre_final, hs_pre_bad;  // HashSIFT items queued before the pass-2 tiles / the BAD items
+    int hs_mix;                    // 1: the other HashSIFT items are spread evenly among the BAD items
     uint32_t *ii, *carry;
     unsigned int *work, *exit_count, *stats_done, *final_done;
     dev::BadTables bad;
@@ -241,7 +243,7 @@ __device__ __forceinline__ void proj_tile(ProjTile &S, const BatchKernelArgs &A,
 }
 
 // MINB: resident CTAs per SM the register budget is sized for (4: 128 registers,
-// 6: 80); the autotuner picks the variant through ctas_per_sm.
+// 5: 102, 6: 80); the autotuner picks the variant through ctas_per_sm.
 template <int NW, int MINB>
 __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernelArgs A)
 {
@@ -271,8 +273,9 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
     const int e1 = e0 + A.hs_pre_final;
     const int e2 = e1 + A.n_tiles;
     const int e3 = e2 + A.hs_pre_bad;
-    const int e4 = e3 + A.n_bad_items;
-    const int e5 = e4 + (n_hs - A.hs_pre_final - A.hs_pre_bad);
+    const int n_rest = n_hs - A.hs_pre_final - A.hs_pre_bad;  // HashSIFT items after the pass-2 tiles
+    const int e4 = e3 + A.n_bad_items + (A.hs_mix ? n_rest : 0);
+    const int e5 = e4 + (A.hs_mix ? 0 : n_rest);
     const int e6 = e5 + A.proj_items;
     const int total = e6 + A.match_items;
 
@@ -302,8 +305,22 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
             kind = 1;
             idx = A.hs_pre_final + item - e2;
         } else if (item < e4) {
-            kind = 3;
-            idx = item - e3;
+            if (!A.hs_mix) {
+                kind = 3;
+                idx = item - e3;
+            } else {
+                // item i of the mixed run is the BAD item floor(i nb / N) when
+                // that count steps at i (nb of the N steps), else a HashSIFT item
+                const long long i = item - e3, nb = A.n_bad_items, N = nb + n_rest;
+                const long long before = i * nb / N, after = (i + 1) * nb / N;
+                if (after > before) {
+                    kind = 3;
+                    idx = (int)before;
+                } else {
+                    kind = 1;
+                    idx = A.hs_pre_final + A.hs_pre_bad + (int)(i - before);
+                }
+            }
         } else if (item < e5) {
             kind = 1;
             idx = A.hs_pre_final + A.hs_pre_bad + item - e4;
@@ -440,10 +457,17 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                 mark_ready();
                 const int k0 = I.kp_begin + (bi - I.bad_item_begin) * A.bad_per_item;
                 const int k1 = min(I.kp_end, k0 + A.bad_per_item);
-                for (int k = k0 + (t >> 5); k < k1; k += 4)
-                    dev::bad_describe_warp<NW, false>(A.bad, A.ii + I.ii_off, I.w + 1, I.w, I.h,
-                                                      A.kps[k], A.bad_out + (size_t)k * NW,
-                                                      A.status);
+                if (A.bad_shared) {
+                    for (int k = k0; k < k1; ++k)
+                        dev::bad_describe_words<NW, NW / 4, false>(
+                            A.bad, A.ii + I.ii_off, I.w + 1, I.w, I.h, A.kps[k],
+                            A.bad_out + (size_t)k * NW, A.status, (t >> 5) * (NW / 4));
+                } else {
+                    for (int k = k0 + (t >> 5); k < k1; k += 4)
+                        dev::bad_describe_warp<NW, false>(A.bad, A.ii + I.ii_off, I.w + 1, I.w, I.h,
+                                                          A.kps[k], A.bad_out + (size_t)k * NW,
+                                                          A.status);
+                }
             }
             __syncthreads();
             record();
@@ -505,9 +529,10 @@ struct bd_batch {
     // [projection groups] (groups of 32 keypoints), zero between launches
     unsigned int *d_counters = nullptr;
     float *d_hist = nullptr;
-    bd_batch_config cfg = {8, 0, 1, 4, 0};
+    bd_batch_config cfg = {8, 0, 1, 4, 0, 0};
     int max_ctas_per_sm = 0;
     int occ4 = 0;  // resident CTAs per SM of the 128-register variant
+    int occ5 = 0;  // of the 102-register variant
     // graph replay
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -632,6 +657,7 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     A.n_tiles = (b->bad && bad_out) ? b->n_tiles : 0;
     A.n_kp = b->n_kp;
     A.bad_per_item = b->cfg.bad_kp_per_item;
+    A.bad_shared = b->cfg.bad_shared;
     A.n_bad_items = (b->bad && bad_out) ? b->n_bad_items : 0;
     A.hs_per_item = b->cfg.hs_kp_per_item;
     const bool fused = b->cfg.proj_fused && b->hs && hs_out && b->n_kp > 0;
@@ -669,7 +695,8 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     const int grid = per_sm * ctx->sm_count;
     // HashSIFT items (no dependency) fill the waits of the integral / BAD chain:
     // 0 all after the BAD items, 1 all before the pass-2 tiles, 2 one grid's
-    // worth before the pass-2 tiles and one before the BAD items
+    // worth before the pass-2 tiles and one before the BAD items, 3 spread
+    // evenly among the BAD items (gather-bound and issue-bound work side by side)
     if (b->cfg.hs_first == 1) {
         A.hs_pre_final = A.hs_items;
         A.hs_pre_bad = 0;
@@ -681,18 +708,22 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
         A.hs_pre_final = 0;
         A.hs_pre_bad = 0;
     }
+    A.hs_mix = b->cfg.hs_first == 3 && A.n_bad_items > 0 ? 1 : 0;
     const bool m_in_kernel = !b->mjobs.empty() && (fused || !any_hs_job(b));
     if (m_in_kernel)
         fill_match_items(b, A, bad_out, hs_out, grid);
     const int n_items = 2 * A.n_tiles + A.hs_items + A.n_bad_items + A.proj_items + A.match_items;
     A.events = (b->d_events && n_items <= b->ev_cap) ? b->d_events : nullptr;
-    const bool wide = per_sm > b->occ4;  // needs the 80-register variant to be resident
+    // the largest register budget that keeps per_sm CTAs resident
+    const int budget = per_sm <= b->occ4 ? 4 : (per_sm <= b->occ5 ? 5 : 6);
+    void (*kern)(BatchKernelArgs);
     if (A.bad_nw == 16)
-        e = launch_pdl(wide ? batch_persistent_kernel<16, 6> : batch_persistent_kernel<16, 4>,
-                       dim3(grid), dim3(128), 0, st, A);
+        kern = budget == 4 ? batch_persistent_kernel<16, 4>
+                           : (budget == 5 ? batch_persistent_kernel<16, 5> : batch_persistent_kernel<16, 6>);
     else
-        e = launch_pdl(wide ? batch_persistent_kernel<8, 6> : batch_persistent_kernel<8, 4>,
-                       dim3(grid), dim3(128), 0, st, A);
+        kern = budget == 4 ? batch_persistent_kernel<8, 4>
+                           : (budget == 5 ? batch_persistent_kernel<8, 5> : batch_persistent_kernel<8, 6>);
+    e = launch_pdl(kern, dim3(grid), dim3(128), 0, st, A);
     if (e != cudaSuccess)
         return cuda_err(ctx, e, "bd_describe_batch: persistent kernel");
     trace_kernel(st, "batch_persistent");
@@ -830,14 +861,17 @@ bd_status bd_batch_create(bd_ctx *ctx, const bd_bad_params *bad, const bd_hs_par
         if (e == cudaSuccess && hs) e = cudaMalloc(&b->d_hist, sizeof(float) * kHistDim * (size_t)(b->n_kp > 0 ? b->n_kp : 1));
         if (e == cudaSuccess) e = cudaMemcpy(b->d_imgs, b->imgs.data(), sizeof(BatchImageDev) * n_img, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
-        int o[4] = {0, 0, 0, 0};
+        int o[6] = {0, 0, 0, 0, 0, 0};
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[0], batch_persistent_kernel<8, 4>, 128, 0);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[1], batch_persistent_kernel<16, 4>, 128, 0);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[2], batch_persistent_kernel<8, 6>, 128, 0);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], batch_persistent_kernel<16, 6>, 128, 0);
-        b->occ4 = o[0] < o[1] ? o[0] : o[1];
-        const int occ6 = o[2] < o[3] ? o[2] : o[3];
-        b->max_ctas_per_sm = occ6 > b->occ4 ? occ6 : b->occ4;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[2], batch_persistent_kernel<8, 5>, 128, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], batch_persistent_kernel<16, 5>, 128, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[4], batch_persistent_kernel<8, 6>, 128, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[5], batch_persistent_kernel<16, 6>, 128, 0);
+        b->occ4 = std::min(o[0], o[1]);
+        b->occ5 = std::max(b->occ4, std::min(o[2], o[3]));
+        const int occ6 = std::min(o[4], o[5]);
+        b->max_ctas_per_sm = std::max(occ6, b->occ5);
         if (prev >= 0 && prev != ctx->device)
             cudaSetDevice(prev);
     }
@@ -879,9 +913,10 @@ bd_status bd_batch_set_config(bd_batch *b, const bd_batch_config *cfg)
     if (!b || !cfg)
         return BD_ERR_INVALID;
     if (cfg->bad_kp_per_item < 4 || cfg->bad_kp_per_item > 256 || (cfg->bad_kp_per_item & 3) ||
-        cfg->ctas_per_sm < 0 || cfg->hs_first < 0 || cfg->hs_first > 2 ||
+        cfg->ctas_per_sm < 0 || cfg->hs_first < 0 || cfg->hs_first > 3 ||
         (cfg->hs_kp_per_item != 1 && cfg->hs_kp_per_item != 4) ||
-        (cfg->proj_fused != 0 && cfg->proj_fused != 1))
+        (cfg->proj_fused != 0 && cfg->proj_fused != 1) ||
+        (cfg->bad_shared != 0 && cfg->bad_shared != 1))
         return set_err(b->ctx, BD_ERR_INVALID, "bd_batch_set_config: bad configuration");
     b->cfg = *cfg;
     int items = 0;
@@ -1003,7 +1038,7 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
         return BD_ERR_INVALID;
     const int items[] = {4, 8, 32};
     std::vector<int> per_sm;
-    for (int c : {2, 3, 4, 6})
+    for (int c : {2, 3, 4, 5, 6})
         if (c <= b->max_ctas_per_sm)
             per_sm.push_back(c);
     if (per_sm.empty())
@@ -1031,14 +1066,16 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     std::vector<std::pair<float, bd_batch_config>> res;
     bd_status s = BD_OK;
     const bool can_fuse = b->hs && hs_out;
+    const bool with_bad = b->bad && bad_out;
+    for (int bs = 0; bs < (with_bad ? 2 : 1); ++bs)
     for (int fu = 0; fu < (can_fuse ? 2 : 1); ++fu)
     for (int hm : {1, 4})
-        for (int hs_first = 0; hs_first < 3 && s == BD_OK; ++hs_first)
+        for (int hs_first = 0; hs_first < 4 && s == BD_OK; ++hs_first)
             for (int it : items)
                 for (int c : per_sm) {
                     if (s != BD_OK)
                         break;
-                    bd_batch_config cfg = {it, c, hs_first, hm, fu};
+                    bd_batch_config cfg = {it, c, hs_first, hm, fu, bs};
                     float ms = 0.f;
                     s = time_cfg(cfg, reps, &ms);
                     res.push_back({ms, cfg});

@@ -196,7 +196,8 @@ def test_fused_fp32_projection_equals_tensor_core_path(gpu_ctx, hs_mode):
             b.close()
 
 
-@pytest.mark.parametrize("cfg", [(8, 4, 0, 4, 0), (4, 2, 1, 1, 1), (32, 6, 2, 4, 1)])
+@pytest.mark.parametrize("cfg", [(8, 4, 0, 4, 0, 0), (4, 2, 1, 1, 1, 0), (32, 6, 2, 4, 1, 1),
+                                 (8, 4, 3, 4, 1, 1), (4, 3, 3, 1, 0, 0)])
 def test_timeline_respects_dependencies(gpu_ctx, cfg):
     """The item timeline lists every queued item once, and no item starts
     before the items it depends on ended: pass-2 tiles after all pass-1 tiles
@@ -213,7 +214,7 @@ def test_timeline_respects_dependencies(gpu_ctx, cfg):
     b = gpu_ctx.batch(bp, hp, dimgs, offs)
     n = len(kps)
     dk = _dev(kps)
-    it, _, _, hm, fused = cfg
+    it, _, _, hm, fused, _ = cfg
     b.set_config(*cfg)
     ob0 = torch.zeros((n, 8), dtype=torch.int32, device="cuda")
     oh0 = torch.zeros((n, 8), dtype=torch.int32, device="cuda")
@@ -325,4 +326,29 @@ def test_batch_matchings_rejected_without_descriptors(gpu_ctx):
     b.set_matches([(BD_DESC_BAD, 0, 5, o, 4, 5)])
     with pytest.raises(BindescError):  # the BAD output the job reads is missing
         b.describe(dimgs, _dev(kps), None, None)
+    b.close()
+
+
+@pytest.mark.parametrize("bits,levels", [(256, 1), (512, 5)])
+def test_bad_shared_keypoints_equal_per_image_calls(gpu_ctx, bits, levels):
+    """bad_shared = 1 (the CTA's four warps split each keypoint's words) gives
+    the per-image BAD bits, invalid keypoints included (all-zero words)."""
+    import torch
+    imgs, kps, offs, bad, hs = _small_batch(seed=41, bad_bits=bits, hs_bits=256, levels=levels)
+    kps[3, 1] = np.inf
+    kps[1200, 3] = 1e30
+    bp, hp = gpu_ctx.bad_params(bad), gpu_ctx.hs_params(hs)
+    dimgs = [_dev(im) for im in imgs]
+    b = gpu_ctx.batch(bp, None, dimgs, offs)
+    n = len(kps)
+    dk = _dev(kps)
+    ref, _ = _per_image(gpu_ctx, bp, hp, imgs, kps, offs)
+    gpu_ctx.sync_status()
+    for it in (4, 8, 32):
+        ob = torch.full((n, bits // 32), -1, dtype=torch.int32, device="cuda")
+        b.set_config(it, 4, 0, 4, 0, 1)
+        b.describe(dimgs, dk, ob, None, graph=True)
+        gpu_ctx.sync_status()
+        assert np.array_equal(_u32(ob), ref), it
+    assert np.all(_u32(ob)[[3, 1200]] == 0)
     b.close()
