@@ -753,26 +753,32 @@ def roofline(wl, per_kernel, clocks, probes=None):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# step's kernels from one ncu --set full capture of the plain and large
-# workloads, summarised in profiles/kernels_*.md.  They hold for the kernel
-# sources whose hash is "sources" only; after any change traffic is null.
+# step's kernels from one ncu --set full capture per workload, summarised in
+# profiles/*.md, with the hash of the kernel's own sources at capture time;
+# a kernel whose sources changed since has traffic null.
+KERNEL_SOURCES = {
+    "batch_persistent": ["batch.cu", "bad_dev.cuh", "hashsift_dev.cuh", "integral_dev.cuh",
+                         "match_dev.cuh", "bd_internal.h"],
+    "hs_proj_tc": ["proj_tc.cu", "bd_internal.h"],
+    "match_tc": ["match_tc.cu", "bd_internal.h"],
+    "match_multi": ["match.cu", "match_dev.cuh", "bd_internal.h"],
+}
 NCU_TRAFFIC = {
-    "sources": "696b8f8327778878",
-    "plain": {"describe_batch/batch_persistent": 806912, "describe_batch/hs_proj_tc": 1795072,
-              "match/match_multi": 147712},
-    "large": {"describe_batch/batch_persistent": 38733568 + 60723200,
-              "describe_batch/hs_proj_tc": 37308672 + 5376,
-              "match_bad/match_tc": 10271232, "match_hashsift/match_tc": 20515072},
+    "plain": {"describe_batch/batch_persistent": (1004544, "afa01f3f29981ea9")},
+    "large": {"describe_batch/batch_persistent": (38534656 + 49448448, "afa01f3f29981ea9"),
+              "describe_batch/hs_proj_tc": (21686784 + 512, "c1091bfc3acad8ea"),
+              "match_bad/match_tc": (10271232, "38e54003bf0f64e1"),
+              "match_hashsift/match_tc": (20514560, "38e54003bf0f64e1")},
+    "batch": {"describe_batch/batch_persistent": (332636928 + 314133248, "afa01f3f29981ea9"),
+              "describe_batch/hs_proj_tc": (106037248 + 7576832, "c1091bfc3acad8ea")},
 }
 
 
-def kernel_sources_hash() -> str:
-    """sha256 (first 16 hex digits) of the CUDA sources and the C header."""
-    import glob
+def kernel_sources_hash(kernel: str) -> str:
+    """sha256 (first 16 hex digits) of a kernel's CUDA sources and the C header."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2108_08380_gb300", "csrc")
-    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
-                   glob.glob(os.path.join(csrc, "*.h")))
+    files = [os.path.join(csrc, f) for f in KERNEL_SOURCES[kernel]]
     files.append(os.path.join(ROOT, "include", "bindesc.h"))
     h = hashlib.sha256()
     for f in files:
@@ -783,9 +789,11 @@ def kernel_sources_hash() -> str:
 
 
 def ncu_traffic(wl_name: str, key: str):
-    if kernel_sources_hash() != NCU_TRAFFIC["sources"]:
+    ent = NCU_TRAFFIC.get(wl_name, {}).get(key)
+    kname = key.split("/")[-1]
+    if ent is None or kname not in KERNEL_SOURCES:
         return None
-    return NCU_TRAFFIC.get(wl_name, {}).get(key)
+    return ent[0] if kernel_sources_hash(kname) == ent[1] else None
 
 
 # FP32/SFU operations one patch pixel of the HashSIFT histogram needs:
