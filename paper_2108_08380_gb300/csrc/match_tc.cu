@@ -5,17 +5,23 @@
 // epilogue turns S into the distance (K - S)/2 and keeps a per-query top-2 of
 // packed (distance << 22 | index) keys, exactly like the POPC kernel.
 //
-// CTA = 12 warps, one 128-query tile, a range of 128-row train tiles:
-//  - warp 0 (one lane) loads the query tile once and the train tiles into a
+// Persistent grid (two CTAs per SM at K = 256), stream-K split: CTA c takes an
+// equal contiguous range of the (128-query block, 128-entry train tile) pairs
+// in query-block-major order.  CTA = 12 warps:
+//  - warp 0 (one lane) loads a block's query tile when the block changes
+//    (after the MMAs that read the previous one) and the train tiles into a
 //    two-stage shared-memory ring with TMA (128-byte swizzle);
 //  - warp 1 (one lane) issues K/32 MMAs per train tile into one of two TMEM
 //    accumulators (128 x 128 FP32 each) and commits them to mbarriers;
 //  - warps 4..11 drain the accumulators: warps w and w+4 share TMEM lane
 //    quadrant w%4 (32 queries) and take 64 columns each, freeing the buffer
-//    for the next MMA before they update their top-2 keys.
-// Train tiles are split across CTAs; partial top-2 pairs are merged by the
-// last CTA of each query block (per-block arrival counter).  Every wait is
-// bounded by the GPU timer; on expiry the CTA raises BD_FLAG_TIMEOUT.
+//    for the next MMA before they update their top-2 keys; at the end of the
+//    CTA's part of a block they merge the halves and write the pair, and the
+//    last CTA of the block (per-block arrival counter) merges the parts.
+// Every wait is bounded by the GPU timer; on expiry the CTA raises
+// BD_FLAG_TIMEOUT.
+#include <algorithm>
+
 #include "bd_internal.h"
 
 namespace bd {
@@ -99,10 +105,41 @@ __device__ __forceinline__ void finalize(uint32_t k1, uint32_t k2, int nbits, in
     w[2] = acc;
 }
 
-template <int K>
-__global__ void __launch_bounds__(NTHREADS, 1) match_tc_kernel(
+// Stream-K split of the (query block, train tile) pairs, query-block major:
+// CTA c of G takes pairs [T c / G, T (c + 1) / G).  The CTA holding pair p is
+// ((p + 1) G - 1) / T; the CTAs covering query block qb are first(qb) ..
+// last(qb), and their partial top-2 pairs go to slots first(qb) + qb + (c -
+// first(qb)) of a (G + #blocks) x 128 array (the slots of consecutive blocks
+// never overlap).
+__device__ __forceinline__ int cta_of(long long p, long long T, int G)
+{
+    return (int)(((p + 1) * G - 1) / T);
+}
+
+// Named barrier of the eight epilogue warps (threads 128..383).
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// The same barrier, returning to every epilogue thread whether any of them
+// passed v = true.
+__device__ __forceinline__ bool epi_sync_or(bool v)
+{
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\t"
+                 "setp.ne.u32 p, %1, 0;\n\t"
+                 "bar.red.or.pred q, 1, 256, p;\n\t"
+                 "selp.u32 %0, 1, 0, q;\n\t}"
+                 : "=r"(r)
+                 : "r"((uint32_t)v)
+                 : "memory");
+    return r != 0;
+}
+
+// MINB: resident CTAs per SM (2 for K = 256: 96 KB of shared memory each and
+// at most 85 registers per thread; 1 for K = 512).
+template <int K, int MINB>
+__global__ void __launch_bounds__(NTHREADS, MINB) match_tc_kernel(
     const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmT, int nq,
-    int nt, int tiles_per_split, int nbits, int rnum, int rden, uint2 *__restrict__ partial,
+    int nt, int nbits, int rnum, int rden, uint2 *__restrict__ partial,
     bd_match_result *__restrict__ out, uint2 *__restrict__ raw_keys,
     unsigned int *__restrict__ arrivals, DeviceStatus *status)
 {
@@ -114,20 +151,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) match_tc_kernel(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;
     uint8_t *sB0 = smem + A_BYTES;
-    __shared__ uint64_t bar_a, bar_bf[2], bar_be[2], bar_tf[2], bar_te[2];
+    __shared__ uint64_t bar_a, bar_ae, bar_bf[2], bar_be[2], bar_tf[2], bar_te[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     __shared__ int last_cta;
     __shared__ uint2 half_keys[BM];
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int qb = blockIdx.x, split = blockIdx.y;
-    const int ntiles = (nt + BN - 1) / BN;
-    const int tile0 = split * tiles_per_split;
-    const int count = max(0, min(ntiles, tile0 + tiles_per_split) - tile0);
+    const int nqb = (nq + BM - 1) / BM;
+    const int ntl = max(1, (nt + BN - 1) / BN);
+    const long long T = (long long)nqb * ntl;
+    const int G = (int)gridDim.x, c = (int)blockIdx.x;
+    const long long p0 = T * c / G, p1 = T * (c + 1) / G;
 
     if (t == 0) {
         dev::mbar_init(&bar_a, 1);
+        dev::mbar_init(&bar_ae, 1);
         for (int s = 0; s < 2; ++s) {
             dev::mbar_init(&bar_bf[s], 1);
             dev::mbar_init(&bar_be[s], 1);
@@ -149,163 +188,189 @@ __global__ void __launch_bounds__(NTHREADS, 1) match_tc_kernel(
     const uint32_t sentinel = ((uint32_t)(nbits + 1) << kMatchIdxBits) | kMatchIdxMask;
 
     int issued = 0;  // MMA commits (warp 1)
-    if (warp == 0 && lane == 0 && count > 0) {
-        dev::mbar_arrive_expect_tx(&bar_a, A_BYTES);
-        for (int c = 0; c < CH; ++c)
-            dev::tma_load_2d(sA + c * BM * 128, &tmQ, c * 128, qb * BM, &bar_a);
-        for (int i = 0; i < count; ++i) {
-            const int s = i & 1;
-            if (i >= 2 && !wait_bar(&bar_be[s], ((i >> 1) - 1) & 1, &abort_flag)) {
-                abort_flag = 1;
-                break;
-            }
-            uint8_t *sB = sB0 + s * B_BYTES;
-            dev::mbar_arrive_expect_tx(&bar_bf[s], B_BYTES);
-            for (int c = 0; c < CH; ++c)
-                dev::tma_load_2d(sB + c * BN * 128, &tmT, c * 128, (tile0 + i) * BN, &bar_bf[s]);
-        }
-    } else if (warp == 1 && lane == 0 && count > 0) {
-        const uint32_t idesc = dev::umma_idesc_e4m3_f32(BM, BN);
-        bool ok = wait_bar(&bar_a, 0, &abort_flag);
-        for (int i = 0; ok && i < count; ++i) {
-            const int s = i & 1;
-            ok = wait_bar(&bar_bf[s], (i >> 1) & 1, &abort_flag);
-            if (ok && i >= 2)
-                ok = wait_bar(&bar_te[s], ((i >> 1) - 1) & 1, &abort_flag);
+    if (warp == 0 && lane == 0) {
+        // producer: the query tile at each new block, the train tiles through a
+        // two-stage ring
+        bool ok = true;
+        int i = 0, seg = 0;
+        for (long long p = p0; ok && p < p1; ++seg) {
+            const int qb = (int)(p / ntl);
+            const long long pend = min(p1, (long long)(qb + 1) * ntl);
+            if (seg > 0)
+                ok = wait_bar(&bar_ae, (seg - 1) & 1, &abort_flag);
             if (!ok)
                 break;
-            dev::tc_fence_after();
-            const uint8_t *sB = sB0 + s * B_BYTES;
-#pragma unroll
-            for (int c = 0; c < CH; ++c)
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const uint64_t a = dev::umma_desc_sw128(dev::smem_u32(sA + c * BM * 128 + u * 32));
-                    const uint64_t b = dev::umma_desc_sw128(dev::smem_u32(sB + c * BN * 128 + u * 32));
-                    dev::umma_e4m3(tmem + s * BN, a, b, idesc, (c | u) ? 1u : 0u);
-                }
-            dev::umma_commit(&bar_be[s]);
-            dev::umma_commit(&bar_tf[s]);
-            ++issued;
+            dev::mbar_arrive_expect_tx(&bar_a, A_BYTES);
+            for (int ch = 0; ch < CH; ++ch)
+                dev::tma_load_2d(sA + ch * BM * 128, &tmQ, ch * 128, qb * BM, &bar_a);
+            for (; ok && p < pend; ++p, ++i) {
+                const int s = i & 1;
+                if (i >= 2)
+                    ok = wait_bar(&bar_be[s], ((i >> 1) - 1) & 1, &abort_flag);
+                if (!ok)
+                    break;
+                uint8_t *sB = sB0 + s * B_BYTES;
+                dev::mbar_arrive_expect_tx(&bar_bf[s], B_BYTES);
+                for (int ch = 0; ch < CH; ++ch)
+                    dev::tma_load_2d(sB + ch * BN * 128, &tmT, ch * 128, (int)(p % ntl) * BN,
+                                     &bar_bf[s]);
+            }
         }
         if (!ok)
             abort_flag = 1;
-    }
-
-    uint32_t k1 = sentinel, k2 = sentinel;
-    const int ew = warp - 4, quad = warp & 3, half = ew >> 2;
-    const int row = quad * 32 + lane;
-    if (warp >= 4) {
-        uint32_t ka1 = sentinel, ka2 = sentinel, kb1 = sentinel, kb2 = sentinel;
-        for (int i = 0; i < count; ++i) {
-            const int s = i & 1;
-            if (!wait_bar(&bar_tf[s], (i >> 1) & 1, &abort_flag)) {
-                abort_flag = 1;
-                break;
-            }
-            dev::tc_fence_after();
-            uint32_t r0[32], r1[32];
-            const uint32_t col = (uint32_t)(s * BN + half * 64);
-            dev::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + col, r0);
-            dev::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + col + 32, r1);
-            dev::tc_fence_before();
-            __syncwarp();
-            if (lane == 0)
-                dev::mbar_arrive(&bar_te[s]);
-            const int j0 = (tile0 + i) * BN + half * 64;
-            const int valid = nt - j0;
-            // Tile-local keys in FP32: f = 256 S - jl (jl < 64) is exact and larger
-            // f means larger S (smaller distance), then smaller jl.  The two best
-            // f of the 64 columns become global integer keys once per tile.
-            float f1 = -INFINITY, f2 = -INFINITY;
-            if (valid >= 64) {
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = dev::umma_idesc_e4m3_f32(BM, BN);
+        bool ok = true;
+        int i = 0, seg = 0;
+        for (long long p = p0; ok && p < p1; ++seg) {
+            const int qb = (int)(p / ntl);
+            const long long pend = min(p1, (long long)(qb + 1) * ntl);
+            ok = wait_bar(&bar_a, seg & 1, &abort_flag);
+            for (; ok && p < pend; ++p, ++i) {
+                const int s = i & 1;
+                ok = wait_bar(&bar_bf[s], (i >> 1) & 1, &abort_flag);
+                if (ok && i >= 2)
+                    ok = wait_bar(&bar_te[s], ((i >> 1) - 1) & 1, &abort_flag);
+                if (!ok)
+                    break;
+                dev::tc_fence_after();
+                const uint8_t *sB = sB0 + s * B_BYTES;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float f = fmaf(__uint_as_float(r0[j]), 256.0f, -(float)j);
-                    f2 = fmaxf(f2, fminf(f1, f));
-                    f1 = fmaxf(f1, f);
+                for (int ch = 0; ch < CH; ++ch)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint64_t a = dev::umma_desc_sw128(dev::smem_u32(sA + ch * BM * 128 + u * 32));
+                        const uint64_t b = dev::umma_desc_sw128(dev::smem_u32(sB + ch * BN * 128 + u * 32));
+                        dev::umma_e4m3(tmem + s * BN, a, b, idesc, (ch | u) ? 1u : 0u);
+                    }
+                dev::umma_commit(&bar_be[s]);
+                dev::umma_commit(&bar_tf[s]);
+                ++issued;
+            }
+            if (ok)
+                dev::umma_commit(&bar_ae);  // the query tile may be replaced once these finish
+        }
+        if (!ok)
+            abort_flag = 1;
+    } else if (warp >= 4) {
+        const int ew = warp - 4, quad = warp & 3, half = ew >> 2;
+        const int row = quad * 32 + lane;
+        const bool owner = half == 0;
+        int i = 0;
+        for (long long p = p0; p < p1;) {
+            const int qb = (int)(p / ntl);
+            const long long pend = min(p1, (long long)(qb + 1) * ntl);
+            uint32_t k1 = sentinel, k2 = sentinel;
+            for (; p < pend; ++p, ++i) {
+                const int s = i & 1;
+                // a failed wait skips the work but keeps the loop, so that all
+                // eight warps reach the block's barriers below
+                if (!wait_bar(&bar_tf[s], (i >> 1) & 1, &abort_flag)) {
+                    abort_flag = 1;
+                    continue;
+                }
+                dev::tc_fence_after();
+                uint32_t r[32];
+                const uint32_t col = (uint32_t)(s * BN + half * 64);
+                const int j0 = (int)(p % ntl) * BN + half * 64;
+                const int valid = nt - j0;
+                // Tile-local keys in FP32: f = 256 S - jl (jl < 64) is exact and
+                // larger f means larger S (smaller distance), then smaller jl.
+                // The two best f of the 64 columns become global integer keys
+                // once per tile.  Two 32-column loads; the buffer is released
+                // after the second.  (Packing two 16-bit keys per register for
+                // packed min/max measured slower.)
+                float f1 = -INFINITY, f2 = -INFINITY;
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    dev::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + col + 32 * hh, r);
+                    if (hh == 1) {
+                        dev::tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0)
+                            dev::mbar_arrive(&bar_te[s]);
+                    }
+                    if (valid >= 32 * hh + 32) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float f = fmaf(__uint_as_float(r[j]), 256.0f, -(float)(32 * hh + j));
+                            f2 = fmaxf(f2, fminf(f1, f));
+                            f1 = fmaxf(f1, f);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float f = 32 * hh + j < valid
+                                                ? fmaf(__uint_as_float(r[j]), 256.0f, -(float)(32 * hh + j))
+                                                : -INFINITY;
+                            f2 = fmaxf(f2, fminf(f1, f));
+                            f1 = fmaxf(f1, f);
+                        }
+                    }
                 }
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float f = fmaf(__uint_as_float(r1[j]), 256.0f, -(float)(32 + j));
-                    f2 = fmaxf(f2, fminf(f1, f));
-                    f1 = fmaxf(f1, f);
+                for (int bb = 0; bb < 2; ++bb) {
+                    const float f = bb ? f2 : f1;
+                    if (f == -INFINITY)
+                        continue;
+                    const int S = (int)ceilf(f * (1.0f / 256.0f));  // f = 256 S - jl, 0 <= jl < 64
+                    const int jl = 256 * S - (int)f;
+                    const uint32_t d = (uint32_t)((K - S) >> 1);
+                    top2_push((d << kMatchIdxBits) | (uint32_t)(j0 + jl), k1, k2);
+                }
+            }
+            // end of this CTA's part of query block qb: merge the two column
+            // halves, then the CTAs' parts (last arriver), and write; on an
+            // abort every epilogue warp leaves here together
+            if (!owner)
+                half_keys[row] = make_uint2(k1, k2);
+            if (epi_sync_or(*(volatile int *)&abort_flag != 0))
+                break;
+            if (owner)
+                top2_merge(half_keys[row].x, half_keys[row].y, k1, k2);
+            const int query = qb * BM + row;
+            const int first = cta_of((long long)qb * ntl, T, G);
+            const int last = cta_of((long long)(qb + 1) * ntl - 1, T, G);
+            if (first == last) {
+                if (owner && query < nq) {
+                    if (raw_keys)
+                        raw_keys[query] = make_uint2(k1, k2);
+                    else
+                        finalize(k1, k2, nbits, rnum, rden, out + query);
                 }
             } else {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float f = j < valid ? fmaf(__uint_as_float(r0[j]), 256.0f, -(float)j) : -INFINITY;
-                    f2 = fmaxf(f2, fminf(f1, f));
-                    f1 = fmaxf(f1, f);
+                uint2 *slots = partial + (size_t)(first + qb) * BM;
+                if (owner)
+                    slots[(size_t)(c - first) * BM + row] = make_uint2(k1, k2);
+                __threadfence();
+                epi_sync();
+                if (t == 128) {
+                    const unsigned int prev = atomicAdd(arrivals + qb, 1u);
+                    last_cta = prev == (unsigned)(last - first);
+                    if (last_cta)
+                        arrivals[qb] = 0u;
                 }
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float f = j + 32 < valid ? fmaf(__uint_as_float(r1[j]), 256.0f, -(float)(32 + j))
-                                                   : -INFINITY;
-                    f2 = fmaxf(f2, fminf(f1, f));
-                    f1 = fmaxf(f1, f);
+                epi_sync();
+                if (last_cta && owner && query < nq) {
+                    __threadfence();
+                    uint2 a = __ldcg(slots + row);
+                    for (int sl = 1; sl <= last - first; ++sl) {
+                        const uint2 b = __ldcg(slots + (size_t)sl * BM + row);
+                        top2_merge(b.x, b.y, a.x, a.y);
+                    }
+                    if (raw_keys)
+                        raw_keys[query] = a;
+                    else
+                        finalize(a.x, a.y, nbits, rnum, rden, out + query);
                 }
             }
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const float f = b ? f2 : f1;
-                if (f == -INFINITY)
-                    continue;
-                const int S = (int)ceilf(f * (1.0f / 256.0f));  // f = 256 S - jl, 0 <= jl < 64
-                const int jl = 256 * S - (int)f;
-                const uint32_t d = (uint32_t)((K - S) >> 1);
-                top2_push((d << kMatchIdxBits) | (uint32_t)(j0 + jl), ka1, ka2);
-            }
+            epi_sync();  // half_keys and last_cta are reused by the next block
         }
-        top2_merge(kb1, kb2, ka1, ka2);
-        k1 = ka1;
-        k2 = ka2;
-        if (half == 1)
-            half_keys[row] = make_uint2(k1, k2);
     }
     __syncthreads();
     const bool aborted = abort_flag != 0;
-    const int query = qb * BM + row;
-    const bool owner = warp >= 4 && half == 0;
-    if (owner) {
-        const uint2 o = half_keys[row];
-        top2_merge(o.x, o.y, k1, k2);
-    }
-    if (aborted) {
-        if (t == 0)
-            dev::raise_flag(status, BD_FLAG_TIMEOUT);
-    } else if (gridDim.y == 1) {
-        if (owner && query < nq) {
-            if (raw_keys)
-                raw_keys[query] = make_uint2(k1, k2);
-            else
-                finalize(k1, k2, nbits, rnum, rden, out + query);
-        }
-    } else {
-        if (owner && query < nq)
-            partial[(size_t)split * nq + query] = make_uint2(k1, k2);
-        __threadfence();
-        __syncthreads();
-        if (t == 0) {
-            const unsigned int prev = atomicAdd(arrivals + qb, 1u);
-            last_cta = prev == gridDim.y - 1;
-            if (last_cta)
-                arrivals[qb] = 0u;
-        }
-        __syncthreads();
-        if (last_cta && owner && query < nq) {
-            __threadfence();
-            uint2 a = __ldcg(partial + query);
-            for (int s = 1; s < (int)gridDim.y; ++s) {
-                const uint2 b = __ldcg(partial + (size_t)s * nq + query);
-                top2_merge(b.x, b.y, a.x, a.y);
-            }
-            if (raw_keys)
-                raw_keys[query] = a;
-            else
-                finalize(a.x, a.y, nbits, rnum, rden, out + query);
-        }
-    }
+    if (aborted && t == 0)
+        dev::raise_flag(status, BD_FLAG_TIMEOUT);
     if (aborted && warp == 1 && lane == 0) {
         // let issued MMAs finish before TMEM is released
         for (int i = 0; i < issued; ++i) {
@@ -321,21 +386,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) match_tc_kernel(
         dev::tmem_dealloc(tmem, 2 * BN);
 }
 
-void tc_plan(int nq, int nt, int sm_count, int &S, int &per)
+// Persistent grid: as many CTAs as are resident (two per SM at K = 256, one
+// at K = 512), at most one per (query block, train tile) pair.
+int tc_grid(int nq, int nt, int nbits, int sm_count)
 {
-    const int qb = (nq + BM - 1) / BM;
-    const int ntiles = (nt + BN - 1) / BN;
-    S = (4 * sm_count + qb - 1) / qb;
-    if (S > ntiles)
-        S = ntiles;
-    if (S < 1)
-        S = 1;
-    per = (ntiles + S - 1) / S;
-    if (per < 1)
-        per = 1;
-    S = (ntiles + per - 1) / per;
-    if (S < 1)
-        S = 1;
+    const long long T = (long long)((nq + BM - 1) / BM) * (long long)std::max(1, (nt + BN - 1) / BN);
+    const long long g = (long long)(nbits == 256 ? 2 : 1) * sm_count;
+    return (int)std::max(1LL, std::min(T, g));
 }
 
 }  // namespace
@@ -344,10 +401,9 @@ int match_tc_query_blocks(int nq) { return (nq + BM - 1) / BM; }
 
 size_t match_tc_scratch_bytes(int nq, int nt, int nbits, int sm_count)
 {
-    int S, per;
-    tc_plan(nq, nt, sm_count, S, per);
+    const int G = tc_grid(nq, nt, nbits, sm_count);
     return align_up((size_t)nq * nbits, 256) + align_up((size_t)(nt > 0 ? nt : 1) * nbits, 256) +
-           (S > 1 ? align_up((size_t)S * nq * sizeof(uint2), 256) : 0);
+           align_up((size_t)(G + match_tc_query_blocks(nq)) * BM * sizeof(uint2), 256);
 }
 
 cudaError_t launch_match_tc_keys(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt,
@@ -356,8 +412,7 @@ cudaError_t launch_match_tc_keys(bd_ctx *ctx, const uint32_t *q, int nq, const u
                                  unsigned int *arrivals)
 {
     const int sm_count = ctx->sm_count;
-    int S, per;
-    tc_plan(nq, nt, sm_count, S, per);
+    const int G = tc_grid(nq, nt, nbits, sm_count);
     uint8_t *qx = (uint8_t *)scratch;
     uint8_t *tx = qx + align_up((size_t)nq * nbits, 256);
     uint2 *partial = (uint2 *)(tx + align_up((size_t)(nt > 0 ? nt : 1) * nbits, 256));
@@ -375,13 +430,12 @@ cudaError_t launch_match_tc_keys(bd_ctx *ctx, const uint32_t *q, int nq, const u
         !encode_tmap_2d_u8(&tmT, tx, (uint64_t)nbits, (uint64_t)(nt > 0 ? nt : 1), (uint64_t)nbits,
                            128, 128))
         return cudaErrorInvalidValue;
-    dim3 grid((nq + BM - 1) / BM, S);
     const size_t smem = (size_t)(BM + 2 * BN) * nbits + 1024;
-    auto kern = nbits == 256 ? match_tc_kernel<256> : match_tc_kernel<512>;
+    auto kern = nbits == 256 ? match_tc_kernel<256, 2> : match_tc_kernel<512, 1>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    e = launch_pdl(kern, grid, dim3(NTHREADS), smem, st, tmQ, tmT, nq, nt, per, nbits, ratio_num,
+    e = launch_pdl(kern, dim3(G), dim3(NTHREADS), smem, st, tmQ, tmT, nq, nt, nbits, ratio_num,
                    ratio_den, partial, out, raw_keys, arrivals, ctx->status);
     if (e != cudaSuccess)
         return e;
