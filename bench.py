@@ -115,19 +115,38 @@ class Workload:
         import torch
         import paper_2108_08380_gb300 as bd
         dev = "cuda"
-        self.dimg = [torch.from_numpy(im).to(dev) for im in self.images]
-        self.dkps = torch.from_numpy(self.kps).to(dev)
+        # the step's inputs (images, keypoints) live in one device arena and its
+        # outputs in another, so that the end-to-end measurement moves each
+        # with one copy; the tensors below are views into them
+        in_parts = [im.nbytes for im in self.images] + [self.kps.nbytes]
+        in_off, tot = [], 0
+        for nb in in_parts:
+            in_off.append(tot)
+            tot += (nb + 255) // 256 * 256
+        self.host_in = np.zeros(tot, np.uint8)
+        for im, o in zip(self.images, in_off):
+            self.host_in[o:o + im.nbytes] = im.reshape(-1)
+        self.host_in[in_off[-1]:in_off[-1] + self.kps.nbytes] = self.kps.view(np.uint8).reshape(-1)
+        self.in_arena = torch.from_numpy(self.host_in).to(dev)
+        self.dimg = [self.in_arena[o:o + im.nbytes].view(im.shape) for im, o in zip(self.images, in_off)]
+        self.dkps = self.in_arena[in_off[-1]:in_off[-1] + self.kps.nbytes].view(torch.float32) \
+            .view(self.kps.shape)
         self.bp = ctx.bad_params(self.wl.bad)
         self.hp = ctx.hs_params(self.wl.hs, precision=bd.BD_HS_BF16_RESCUE, band=self.band)
         n = self.n
-        i32 = torch.int32
-        self.bad = torch.empty((n, self.bad_bits // 32), dtype=i32, device=dev)
-        self.hs = torch.empty((n, self.hs_bits // 32), dtype=i32, device=dev)
+        na = int(self.offsets[1]) if self.match else 0
+        shapes = [(n, self.bad_bits // 32), (n, self.hs_bits // 32)] + \
+            ([(na, 3), (na, 3)] if self.match else [])
+        out_off, tot = [], 0
+        for sh in shapes:
+            out_off.append(tot)
+            tot += (sh[0] * sh[1] + 63) // 64 * 64
+        self.out_arena = torch.empty(tot, dtype=torch.int32, device=dev)
+        views = [self.out_arena[o:o + sh[0] * sh[1]].view(sh) for sh, o in zip(shapes, out_off)]
+        self.bad, self.hs = views[0], views[1]
         self.plan = ctx.batch(self.bp, self.hp, self.dimg, self.offsets)
         if self.match:
-            na = int(self.offsets[1])
-            self.m_bad = torch.empty((na, 3), dtype=i32, device=dev)
-            self.m_hs = torch.empty((na, 3), dtype=i32, device=dev)
+            self.m_bad, self.m_hs = views[2], views[3]
             if self.match_kind == "fused":
                 # image A's descriptors against image B's, by the describing launch
                 self.plan.set_matches([(bd.BD_DESC_BAD, 0, 1, self.m_bad, 4, 5),
@@ -648,28 +667,24 @@ def measure_components(ctx, wl, probes):
 
 
 def measure_e2e(ctx, wl, stages, steps):
-    """Same step through the API with host buffers: H2D of every image and of
-    the keypoints from pinned memory, the step, D2H of all descriptors and
-    match records, inside the timed region."""
+    """Same step through the API with host buffers: H2D of the step's inputs
+    (every image and the keypoints, staged in one pinned buffer) as one copy,
+    the step, D2H of all descriptors and match records (one arena) as one
+    copy, inside the timed region."""
     import torch
-    host_in = [torch.from_numpy(im).pin_memory() for im in wl.images] + \
-        [torch.from_numpy(wl.kps).pin_memory()]
-    dev_in = list(wl.dimg) + [wl.dkps]
-    dev_out = wl.outputs()
-    host_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in dev_out]
-    bi = sum(t.numel() * t.element_size() for t in host_in)
-    bo = sum(t.numel() * t.element_size() for t in host_out)
+    host_in = torch.from_numpy(wl.host_in).pin_memory()
+    host_out = torch.empty(wl.out_arena.shape, dtype=wl.out_arena.dtype).pin_memory()
+    bi = host_in.numel() * host_in.element_size()
+    bo = host_out.numel() * host_out.element_size()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
     for _ in range(steps):
-        for d, h in zip(dev_in, host_in):
-            d.copy_(h, non_blocking=True)
+        wl.in_arena.copy_(host_in, non_blocking=True)
         for _, fn in stages:
             fn()
-        for h, d in zip(host_out, dev_out):
-            h.copy_(d, non_blocking=True)
+        host_out.copy_(wl.out_arena, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
