@@ -199,10 +199,11 @@ cudaError_t launch_mnn_cross(const bd_match_result *fwd, const bd_match_result *
                              int32_t *mnn, cudaStream_t st);
 
 // feature selection round: scratch = state + candidate-major int16 keys (J x 3n)
+size_t select_scratch_bytes_pass(int n, int J, int jn);
 size_t select_scratch_bytes(int n, int J);
 cudaError_t launch_select_feature(const uint8_t *patches, int n, const int32_t *sap,
                                   const int32_t *san, int tau, const int32_t *cand_xy,
-                                  const int32_t *cand_side, int J, int32_t *theta_q,
+                                  const int32_t *cand_side, int max_side, int J, int32_t *theta_q,
                                   int64_t *loss, int32_t *best, void *scratch, size_t scratch_bytes,
                                   cudaStream_t st);
 

@@ -939,7 +939,9 @@ bd_status bd_select_feature(bd_ctx *ctx, const uint8_t *patches, int n, const in
         ((uintptr_t)sim_ap & 3) || ((uintptr_t)sim_an & 3) || ((uintptr_t)theta_q & 3) ||
         ((uintptr_t)best & 3) || tau < -(1 << 20) || tau > (1 << 20))
         return set_err(ctx, BD_ERR_INVALID, "bd_select_feature: bad arguments");
+    int max_side = 1;
     for (int j = 0; j < J; ++j) {
+        max_side = sides[j] > max_side ? sides[j] : max_side;
         if (sides[j] < 1 || sides[j] > 32)
             return set_err(ctx, BD_ERR_INVALID, "bd_select_feature: side of candidate %d", j);
         for (int q = 0; q < 4; ++q)
@@ -952,8 +954,8 @@ bd_status bd_select_feature(bd_ctx *ctx, const uint8_t *patches, int n, const in
     const size_t cap = ((size_t)1 << 30) + 256;
     if (work > cap)
         work = cap;
-    if (work < select_scratch_bytes(n, 1))
-        work = select_scratch_bytes(n, 1);
+    if (work < select_scratch_bytes_pass(n, J, 1))
+        work = select_scratch_bytes_pass(n, J, 1);
     bd_status s = ensure_scratch(ctx, cand_bytes + work);
     if (s != BD_OK)
         return s;
@@ -967,7 +969,7 @@ bd_status bd_select_feature(bd_ctx *ctx, const uint8_t *patches, int n, const in
         return cuda_err(ctx, e, "bd_select_feature: candidate upload");
     TraceScope scope(ctx, ctx->stream);
     BD_LAUNCH(ctx,
-              launch_select_feature(patches, n, sim_ap, sim_an, tau, d_xy, d_side, J, theta_q, loss,
+              launch_select_feature(patches, n, sim_ap, sim_an, tau, d_xy, d_side, max_side, J, theta_q, loss,
                                     best, (char *)ctx->scratch + cand_bytes, work, ctx->stream),
               "feature selection kernels");
     return BD_OK;

@@ -2,10 +2,16 @@
 // of Algorithm 2 in its integer-sorted form (Sec. III-A: thresholds on a 0.1
 // grid over [-255, 255], 5102 values).
 //
+//  0. select_geom_kernel: per candidate box pair, the eight summed-area-table
+//     offsets of the two boxes' corners (clamped to the patch), s^2 and
+//     1/s^2, once per call (they do not depend on the patch).
 //  1. select_keys_kernel: 16 patches per CTA, each patch's summed-area table
-//     in shared memory; for every candidate box pair j it writes the exact
-//     key ceil(10 (sum1 - sum2) / s^2) of every patch, candidate-major
-//     (keys[j][patch], int16), so that step 2 reads them coalesced.
+//     in shared memory (rows from 16-byte loads, prefix sums along rows, then
+//     down columns); for every candidate box pair j it writes the exact key
+//     ceil(10 (sum1 - sum2) / s^2) of every patch, candidate-major
+//     (keys[j][patch], int16), so that step 2 reads them coalesced.  The
+//     division is a reciprocal estimate corrected by one integer step each
+//     way, which makes it exact.
 //  2. select_threshold_kernel: one CTA per candidate.  Each triplet adds the
 //     changes of its per-step loss term at its distinct keys into a 5102-bin
 //     shared-memory histogram (integer, exact) and its term at the lowest
@@ -22,50 +28,99 @@ constexpr int kQMin = BD_SELECT_QMIN;   // threshold numerator with h = -1 every
 constexpr int kBins = 2550 - kQMin + 1;  // thresholds q in [kQMin, 2550]
 constexpr int SK_PATCHES = 16;           // patches per CTA of the key kernel
 constexpr int ST_THREADS = 256;
+constexpr int SAT = 33;                  // summed-area table row length (entries)
 
 struct SelectState {
     unsigned long long best_key;
     unsigned int arrived;
 };
 
+// Corner offsets of candidate j: box b's table entries (ya, xa), (ya, xb),
+// (yb, xa), (yb, xb) at off[4 b + 0..3]; sum = T[3] - T[1] - T[2] + T[0].
+struct CandGeom {
+    uint16_t off[8];
+    int den;       // s^2
+    float inv;     // 1 / s^2 (rounded)
+    int pad[2];
+};
+static_assert(sizeof(CandGeom) == 32, "two 16-byte loads per candidate");
+
+__global__ void select_geom_kernel(const int4 *__restrict__ cand, const int *__restrict__ side,
+                                   int J, CandGeom *__restrict__ geom)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J)
+        return;
+    const int4 c = __ldg(cand + j);
+    const int s = min(max(__ldg(side + j), 1), 32);  // validated on the host
+    CandGeom g;
+    const int cx[2] = {c.x, c.z}, cy[2] = {c.y, c.w};
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const int xa = min(max(cx[b] - s / 2, 0), 32), xb = min(max(cx[b] - s / 2 + s, 0), 32);
+        const int ya = min(max(cy[b] - s / 2, 0), 32), yb = min(max(cy[b] - s / 2 + s, 0), 32);
+        g.off[4 * b + 0] = (uint16_t)(ya * SAT + xa);
+        g.off[4 * b + 1] = (uint16_t)(ya * SAT + xb);
+        g.off[4 * b + 2] = (uint16_t)(yb * SAT + xa);
+        g.off[4 * b + 3] = (uint16_t)(yb * SAT + xb);
+    }
+    g.den = s * s;
+    g.inv = 1.0f / (float)(s * s);
+    g.pad[0] = g.pad[1] = 0;
+    geom[j] = g;
+}
+
 __global__ void __launch_bounds__(256) select_keys_kernel(const uint8_t *__restrict__ patches,
-                                                          int rows, const int4 *__restrict__ cand,
-                                                          const int *__restrict__ side, int j0,
-                                                          int jn, int16_t *__restrict__ keys,
+                                                          int rows, const CandGeom *__restrict__ geom,
+                                                          int j0, int jn, int16_t *__restrict__ keys,
                                                           SelectState *state, int init)
 {
-    __shared__ uint32_t sat[SK_PATCHES][33 * 33];
+    __shared__ uint32_t sat[SK_PATCHES][SAT * SAT];
     const int t = threadIdx.x;
     const int p0 = blockIdx.x * SK_PATCHES;
     if (init && blockIdx.x == 0 && t == 0) {
         state->best_key = ~0ull;
         state->arrived = 0u;
     }
-    // summed-area tables: thread (patch t/16, row band t%16) builds rows by prefix sums
+    // summed-area tables: thread (patch t/16, rows t%16 and t%16 + 16) loads
+    // its two 32-byte rows with 16-byte loads and writes their prefix sums
     {
-        const int pi = t >> 4, lane16 = t & 15;
+        const int pi = t >> 4, r0 = t & 15;
         uint32_t *S = sat[pi];
         const bool in = p0 + pi < rows;
-        const uint8_t *src = patches + (size_t)(p0 + pi) * 1024;
-        if (lane16 == 0)
+        const uint4 *src = reinterpret_cast<const uint4 *>(patches + (size_t)(p0 + pi) * 1024);
+        uint4 v[4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            v[2 * h] = in ? __ldg(src + 2 * (r0 + 16 * h)) : make_uint4(0u, 0u, 0u, 0u);
+            v[2 * h + 1] = in ? __ldg(src + 2 * (r0 + 16 * h) + 1) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        if (r0 == 0)
             for (int x = 0; x <= 32; ++x)
                 S[x] = 0u;
-        // row y + 1 of the table = row y prefix sums (two rows per thread)
-        for (int y = lane16; y < 32; y += 16) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int y = r0 + 16 * h;
+            uint32_t *R = S + (y + 1) * SAT;
+            const uint32_t w[8] = {v[2 * h].x, v[2 * h].y, v[2 * h].z, v[2 * h].w,
+                                   v[2 * h + 1].x, v[2 * h + 1].y, v[2 * h + 1].z, v[2 * h + 1].w};
             uint32_t acc = 0;
-            S[(y + 1) * 33] = 0u;
-            for (int x = 0; x < 32; ++x) {
-                acc += in ? (uint32_t)__ldg(src + y * 32 + x) : 0u;
-                S[(y + 1) * 33 + x + 1] = acc;
-            }
+            R[0] = 0u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb) {
+                    acc += (w[q] >> (8 * bb)) & 0xFFu;
+                    R[4 * q + bb + 1] = acc;
+                }
         }
         __syncthreads();
         // column sums down the table
-        for (int x = lane16; x <= 32; x += 16) {
+        for (int x = r0; x <= 32; x += 16) {
             uint32_t acc = 0;
             for (int y = 1; y <= 32; ++y) {
-                acc += S[y * 33 + x];
-                S[y * 33 + x] = acc;
+                acc += S[y * SAT + x];
+                S[y * SAT + x] = acc;
             }
         }
     }
@@ -74,24 +129,122 @@ __global__ void __launch_bounds__(256) select_keys_kernel(const uint8_t *__restr
     const int pi = t & 15, jj = t >> 4;
     const int p = p0 + pi;
     const uint32_t *S = sat[pi];
+    const uint4 *gq = reinterpret_cast<const uint4 *>(geom + j0);
+#pragma unroll 2
     for (int j = jj; j < jn; j += 16) {
-        const int4 c = __ldg(cand + j0 + j);
-        const int s = min(max(__ldg(side + j0 + j), 1), 32);  // validated on the host
-        auto box = [&](int cx, int cy) -> int {
-            const int xa = min(max(cx - s / 2, 0), 32), xb = min(max(cx - s / 2 + s, 0), 32);
-            const int ya = min(max(cy - s / 2, 0), 32), yb = min(max(cy - s / 2 + s, 0), 32);
-            return (int)(S[yb * 33 + xb] - S[ya * 33 + xb] - S[yb * 33 + xa] + S[ya * 33 + xa]);
-        };
-        const int num = 10 * (box(c.x, c.y) - box(c.z, c.w));
-        const int den = s * s;
-        // ceil(num / den) exactly: a float estimate, then integer corrections
-        int q = __float2int_ru(__fdiv_rn((float)num, (float)den));
-        q = min(max(q, -4096), 4096);  // |num / den| <= 2550
+        const uint4 ga = __ldg(gq + 2 * j), gb = __ldg(gq + 2 * j + 1);
+        const uint32_t o[4] = {ga.x, ga.y, ga.z, ga.w};  // two 16-bit offsets each
+        uint32_t T[8];
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            q += q * den < num ? 1 : 0;
-            q -= (q - 1) * den >= num ? 1 : 0;
+        for (int q = 0; q < 4; ++q) {
+            T[2 * q] = S[o[q] & 0xFFFFu];
+            T[2 * q + 1] = S[o[q] >> 16];
         }
+        const int s1 = (int)(T[3] - T[1] - T[2] + T[0]);
+        const int s2 = (int)(T[7] - T[5] - T[6] + T[4]);
+        const int num = 10 * (s1 - s2);
+        const int den = (int)gb.x;
+        // ceil(num / den) exactly: |num| < 2^22, so the reciprocal estimate is
+        // within one of it, and one integer step each way settles it
+        int q = __float2int_ru((float)num * __uint_as_float(gb.y));
+        q += q * den < num ? 1 : 0;
+        q -= (q - 1) * den >= num ? 1 : 0;
+        if (p < rows)
+            keys[(size_t)j * rows + p] = (int16_t)q;
+    }
+}
+
+// The same keys from 16-bit tables for candidates of side <= 16: a box sum is
+// then below 2^16, so tables kept mod 2^16 give it exactly.  32 patches per
+// CTA in the same shared memory; warp w takes candidates w, w + 8, ... for
+// its 32 patches, one per lane, so the eight table reads of a key fall on 32
+// distinct banks (patch tables 545 words apart) and the key stores are 64-byte
+// runs.
+constexpr int SK16_PATCHES = 32;
+constexpr int SAT16 = 1090;  // halfwords per patch table (33 x 33, padded)
+
+__global__ void __launch_bounds__(256) select_keys16_kernel(const uint8_t *__restrict__ patches,
+                                                            int rows,
+                                                            const CandGeom *__restrict__ geom,
+                                                            int j0, int jn,
+                                                            int16_t *__restrict__ keys,
+                                                            SelectState *state, int init)
+{
+    __shared__ uint16_t sat[SK16_PATCHES * SAT16];
+    const int t = threadIdx.x;
+    const int p0 = blockIdx.x * SK16_PATCHES;
+    if (init && blockIdx.x == 0 && t == 0) {
+        state->best_key = ~0ull;
+        state->arrived = 0u;
+    }
+    // row prefix sums: thread (patch t/8, rows t%8 + 8 h), 16-byte loads
+    {
+        const int pi = t >> 3, r0 = t & 7;
+        uint16_t *S = sat + pi * SAT16;
+        const bool in = p0 + pi < rows;
+        const uint4 *src = reinterpret_cast<const uint4 *>(patches + (size_t)(p0 + pi) * 1024);
+        uint4 v[8];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            v[2 * h] = in ? __ldg(src + 2 * (r0 + 8 * h)) : make_uint4(0u, 0u, 0u, 0u);
+            v[2 * h + 1] = in ? __ldg(src + 2 * (r0 + 8 * h) + 1) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        if (r0 == 0)
+            for (int x = 0; x <= 32; ++x)
+                S[x] = 0;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            uint16_t *R = S + (r0 + 8 * h + 1) * SAT;
+            const uint32_t w[8] = {v[2 * h].x, v[2 * h].y, v[2 * h].z, v[2 * h].w,
+                                   v[2 * h + 1].x, v[2 * h + 1].y, v[2 * h + 1].z, v[2 * h + 1].w};
+            uint32_t acc = 0;
+            R[0] = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb) {
+                    acc += (w[q] >> (8 * bb)) & 0xFFu;
+                    R[4 * q + bb + 1] = (uint16_t)acc;
+                }
+        }
+    }
+    __syncthreads();
+    // column sums: each thread one (patch, column), the 32 entries in registers
+    for (int c = t; c < SK16_PATCHES * SAT; c += 256) {
+        uint16_t *S = sat + (c / SAT) * SAT16 + c % SAT;
+        uint32_t v[32];
+#pragma unroll
+        for (int y = 0; y < 32; ++y)
+            v[y] = S[(y + 1) * SAT];
+        uint32_t acc = 0;
+#pragma unroll
+        for (int y = 0; y < 32; ++y) {
+            acc += v[y];
+            S[(y + 1) * SAT] = (uint16_t)acc;
+        }
+    }
+    __syncthreads();
+    const int lane = t & 31, w = t >> 5;
+    const int p = p0 + lane;
+    const uint16_t *S = sat + lane * SAT16;
+    const uint4 *gq = reinterpret_cast<const uint4 *>(geom + j0);
+#pragma unroll 2
+    for (int j = w; j < jn; j += 8) {
+        const uint4 ga = __ldg(gq + 2 * j), gb = __ldg(gq + 2 * j + 1);
+        const uint32_t o[4] = {ga.x, ga.y, ga.z, ga.w};
+        uint32_t T[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            T[2 * q] = S[o[q] & 0xFFFFu];
+            T[2 * q + 1] = S[o[q] >> 16];
+        }
+        const int s1 = (int)((T[3] - T[1] - T[2] + T[0]) & 0xFFFFu);
+        const int s2 = (int)((T[7] - T[5] - T[6] + T[4]) & 0xFFFFu);
+        const int num = 10 * (s1 - s2);
+        const int den = (int)gb.x;
+        int q = __float2int_ru((float)num * __uint_as_float(gb.y));
+        q += q * den < num ? 1 : 0;
+        q -= (q - 1) * den >= num ? 1 : 0;
         if (p < rows)
             keys[(size_t)j * rows + p] = (int16_t)q;
     }
@@ -120,9 +273,7 @@ __global__ void __launch_bounds__(ST_THREADS) select_threshold_kernel(
         hist[b] = 0;
     __syncthreads();
     long long base = 0;
-    for (int i = t; i < n; i += ST_THREADS) {
-        const int k0 = kj[i], k1 = kj[n + i], k2 = kj[2 * n + i];
-        const int a = __ldg(sap + i), c = __ldg(san + i);
+    auto triplet = [&](int k0, int k1, int k2, int a, int c) {
         base += sel_term(tau, a, c, -1, -1, -1);
         const int k[3] = {k0, k1, k2};
 #pragma unroll
@@ -141,6 +292,24 @@ __global__ void __launch_bounds__(ST_THREADS) select_threshold_kernel(
             if (at != below)
                 atomicAdd(&hist[key - kQMin], at - below);
         }
+    };
+    if ((n & 3) == 0) {
+        // four triplets per iteration: 8-byte key loads, 16-byte similarity loads
+        const short4 *k04 = reinterpret_cast<const short4 *>(kj);
+        const short4 *k14 = reinterpret_cast<const short4 *>(kj + n);
+        const short4 *k24 = reinterpret_cast<const short4 *>(kj + 2 * n);
+        const int4 *a4 = reinterpret_cast<const int4 *>(sap), *c4 = reinterpret_cast<const int4 *>(san);
+        for (int i = t; i < (n >> 2); i += ST_THREADS) {
+            const short4 x = __ldg(k04 + i), y = __ldg(k14 + i), z = __ldg(k24 + i);
+            const int4 a = __ldg(a4 + i), c = __ldg(c4 + i);
+            triplet(x.x, y.x, z.x, a.x, c.x);
+            triplet(x.y, y.y, z.y, a.y, c.y);
+            triplet(x.z, y.z, z.z, a.z, c.z);
+            triplet(x.w, y.w, z.w, a.w, c.w);
+        }
+    } else {
+        for (int i = t; i < n; i += ST_THREADS)
+            triplet(kj[i], kj[n + i], kj[2 * n + i], __ldg(sap + i), __ldg(san + i));
     }
     // base loss: block sum
 #pragma unroll
@@ -225,30 +394,46 @@ __global__ void __launch_bounds__(ST_THREADS) select_threshold_kernel(
 
 }  // namespace
 
-size_t select_scratch_bytes(int n, int J)
+// Scratch for J candidates whose keys are made jn at a time (jn <= J).
+size_t select_scratch_bytes_pass(int n, int J, int jn)
 {
-    return align_up(sizeof(SelectState), 256) + align_up((size_t)J * 3 * n * 2, 256);
+    return align_up(sizeof(SelectState), 256) + align_up((size_t)J * sizeof(CandGeom), 256) +
+           align_up((size_t)jn * 3 * n * 2, 256);
 }
+
+size_t select_scratch_bytes(int n, int J) { return select_scratch_bytes_pass(n, J, J); }
 
 cudaError_t launch_select_feature(const uint8_t *patches, int n, const int32_t *sap,
                                   const int32_t *san, int tau, const int32_t *cand_xy,
-                                  const int32_t *cand_side, int J, int32_t *theta_q,
+                                  const int32_t *cand_side, int max_side, int J, int32_t *theta_q,
                                   int64_t *loss, int32_t *best, void *scratch, size_t scratch_bytes,
                                   cudaStream_t st)
 {
     SelectState *state = (SelectState *)scratch;
-    int16_t *keys = (int16_t *)((char *)scratch + align_up(sizeof(SelectState), 256));
+    const size_t head = align_up(sizeof(SelectState), 256);
+    CandGeom *geom = (CandGeom *)((char *)scratch + head);
+    const size_t head2 = head + align_up((size_t)J * sizeof(CandGeom), 256);
+    int16_t *keys = (int16_t *)((char *)scratch + head2);
     const int rows = 3 * n;
     // candidates per pass: as many as the scratch area holds
     const size_t per = (size_t)rows * 2;
-    long long cap = (long long)((scratch_bytes - align_up(sizeof(SelectState), 256)) / per);
+    if (scratch_bytes <= head2)
+        return cudaErrorInvalidValue;
+    long long cap = (long long)((scratch_bytes - head2) / per);
     if (cap < 1)
         return cudaErrorInvalidValue;
+    select_geom_kernel<<<(J + 127) / 128, 128, 0, st>>>(reinterpret_cast<const int4 *>(cand_xy),
+                                                        cand_side, J, geom);
+    trace_kernel(st, "select_geom");
+    note_launches(1);
     for (int j0 = 0; j0 < J; j0 += (int)cap) {
         const int jn = (int)((long long)(J - j0) < cap ? J - j0 : cap);
-        select_keys_kernel<<<(rows + SK_PATCHES - 1) / SK_PATCHES, 256, 0, st>>>(
-            patches, rows, reinterpret_cast<const int4 *>(cand_xy), cand_side, j0, jn, keys, state,
-            j0 == 0 ? 1 : 0);
+        if (max_side <= 16)
+            select_keys16_kernel<<<(rows + SK16_PATCHES - 1) / SK16_PATCHES, 256, 0, st>>>(
+                patches, rows, geom, j0, jn, keys, state, j0 == 0 ? 1 : 0);
+        else
+            select_keys_kernel<<<(rows + SK_PATCHES - 1) / SK_PATCHES, 256, 0, st>>>(
+                patches, rows, geom, j0, jn, keys, state, j0 == 0 ? 1 : 0);
         trace_kernel(st, "select_keys");
         select_threshold_kernel<<<jn, ST_THREADS, 0, st>>>(keys, n, sap, san, tau, j0, theta_q,
                                                            reinterpret_cast<long long *>(loss),

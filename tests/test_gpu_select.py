@@ -38,6 +38,23 @@ def test_select_exact(gpu_ctx, n, J, tau):
     assert best == rb
 
 
+@pytest.mark.parametrize("smax", [16, 17, 32])
+def test_select_exact_large_boxes(gpu_ctx, smax):
+    """Sides up to 16 take the 16-bit summed-area tables (box sums below
+    2^16), larger ones the 32-bit tables; bright patches push side-16 sums to
+    their largest value, 256 x 255."""
+    n, J = 260, 48
+    P, sap, san, centres, sides = _problem(smax, n, J, smax=smax)
+    P[:, :40] = 255
+    sides[:4] = smax
+    tq, loss, best = _run(gpu_ctx, P, sap, san, 24, centres, sides)
+    cands = np.concatenate([centres, sides[:, None]], axis=1)
+    rq, rl, rb = oracle.select_feature(P, cands, sap, san, 24)
+    assert np.array_equal(tq, rq)
+    assert np.array_equal(loss, rl)
+    assert best == rb
+
+
 def test_select_ties_and_flat_patches(gpu_ctx):
     """Flat patches: every key is 0, the lowest threshold wins; duplicated
     candidates: the first copy is chosen."""
