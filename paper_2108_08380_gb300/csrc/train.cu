@@ -3,8 +3,10 @@
 //
 // Rows of the patch tensor: [0,n) anchors, [n,2n) positives, [2n,3n) negatives.
 //  forward
-//   - relaxed BAD: per-patch summed-area table in FP64 (so the hard bit
-//     [f <= theta] is decided in double precision), r = tanh((theta - f)/(255 T));
+//   - relaxed BAD: one warp per patch builds its summed-area table in 64-bit
+//     fixed point (value x 2^32, exact for |v| >= 2^-9), so box sums are exact
+//     integer sums and the hard bit [f <= theta] is the exact comparison
+//     D <= floor(theta s^2 2^32); r = tanh((theta - f)/(255 T)) in FP32;
 //   - relaxed HashSIFT: the patch histogram kernel, then the FP32 projection
 //     with r = tanh((W^T h + b)/T) and hard bits [m > 0];
 //   - mining on hard codes: for anchor i the negative j != i with the smallest
@@ -44,13 +46,19 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-__device__ __forceinline__ double sat_box(const double (*S)[34], int x0, int y0, int s)
+// 2^32 (the fixed-point scale of the BAD summed-area tables).
+constexpr double kFix = 4294967296.0;
+
+__device__ __forceinline__ long long sat_box64(const long long (*S)[33], int x0, int y0, int s)
 {
     const int xa = min(max(x0, 0), 32), xb = min(max(x0 + s, 0), 32);
     const int ya = min(max(y0, 0), 32), yb = min(max(y0 + s, 0), 32);
     return S[yb][xb] - S[ya][xb] - S[yb][xa] + S[ya][xa];
 }
 
+// Relaxed BAD forward, one warp per patch (four per CTA, no CTA barrier in the
+// patch loop).  Each CTA first turns the thresholds into their fixed-point
+// bounds floor(theta_k s_k^2 2^32) and scales 2^-32 / s_k^2.
 template <int NW>
 __global__ void __launch_bounds__(128) train_bad_fwd_kernel(const float *__restrict__ patches, int rows,
                                                             const short4 *__restrict__ box,
@@ -60,48 +68,64 @@ __global__ void __launch_bounds__(128) train_bad_fwd_kernel(const float *__restr
                                                             uint32_t *__restrict__ bits)
 {
     constexpr int K = NW * 32;
-    __shared__ double S[33][34];
-    __shared__ float P[32][33];
+    __shared__ long long S[4][33][33];
+    __shared__ float P[4][32][33];
+    __shared__ long long thr[K];
+    __shared__ float fscale[K];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    for (int k = t; k < K; k += 128) {
+        const int sk = __ldg(side + k);
+        const double s2 = (double)sk * (double)sk;
+        thr[k] = (long long)floor((double)__ldg(theta + k) * s2 * kFix);  // exact product
+        fscale[k] = (float)(1.0 / (s2 * kFix));
+    }
+    __syncthreads();
+    long long (*Sw)[33] = S[warp];
+    float (*Pw)[33] = P[warp];
+    for (int row = blockIdx.x * 4 + warp; row < rows; row += gridDim.x * 4) {
         const float *p = patches + (size_t)row * 1024;
-        __syncthreads();
+        __syncwarp();
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int e = t + q * 128;
-            P[e >> 5][e & 31] = __ldg(p + e);
-        }
-        if (t < 33) {
-            S[0][t] = 0.0;
-            S[t][0] = 0.0;
-        }
-        __syncthreads();
-        if (t < 32) {  // row prefix of patch row t
-            double acc = 0.0;
+        for (int q = 0; q < 32; ++q)
+            Pw[q][lane] = __ldg(p + q * 32 + lane);
+        __syncwarp();
+        // row y = lane: prefix sums of the fixed-point values
+        {
+            long long acc = 0;
+            Sw[lane + 1][0] = 0;
+#pragma unroll 8
             for (int x = 0; x < 32; ++x) {
-                acc += (double)P[t][x];
-                S[t + 1][x + 1] = acc;
+                acc += __float2ll_rn(Pw[lane][x] * 4294967296.0f);
+                Sw[lane + 1][x + 1] = acc;
+            }
+            Sw[0][lane] = 0;
+            if (lane == 0)
+                Sw[0][32] = 0;
+        }
+        __syncwarp();
+        // column x = lane + 1: the 32 row prefixes into registers, then down
+        {
+            long long v[32];
+#pragma unroll
+            for (int y = 0; y < 32; ++y)
+                v[y] = Sw[y + 1][lane + 1];
+            long long acc = 0;
+#pragma unroll
+            for (int y = 0; y < 32; ++y) {
+                acc += v[y];
+                Sw[y + 1][lane + 1] = acc;
             }
         }
-        __syncthreads();
-        if (t < 32) {  // column prefix of column t + 1
-            double acc = 0.0;
-            for (int y = 1; y <= 32; ++y) {
-                acc += S[y][t + 1];
-                S[y][t + 1] = acc;
-            }
-        }
-        __syncthreads();
-        for (int j = warp; j < NW; j += 4) {
+        __syncwarp();
+#pragma unroll 2
+        for (int j = 0; j < NW; ++j) {
             const int k = j * 32 + lane;
             const short4 b = __ldg(box + k);
             const int s = __ldg(side + k);
-            const double d = sat_box(S, b.x, b.y, s) - sat_box(S, b.z, b.w, s);
-            const double th = (double)__ldg(theta + k);
-            const double s2 = (double)s * (double)s;
-            const bool bit = d <= th * s2;  // f = d / s^2 <= theta
-            const float f = (float)(d / s2);
-            r[(size_t)row * K + k] = tanhf(((float)th - f) * inv_scale);
+            const long long d = sat_box64(Sw, b.x, b.y, s) - sat_box64(Sw, b.z, b.w, s);
+            const bool bit = d <= thr[k];  // f = d 2^-32 / s^2 <= theta, exactly
+            const float f = (float)d * fscale[k];
+            r[(size_t)row * K + k] = tanhf((__ldg(theta + k) - f) * inv_scale);
             const uint32_t word = __ballot_sync(FULL, bit);
             if (lane == 0)
                 bits[(size_t)row * NW + j] = word;
@@ -540,10 +564,10 @@ bd_status bd_train_forward(bd_ctx *ctx, bd_train *tr, const float *patches, cons
     cudaError_t e = cudaSuccess;
     // relaxed BAD
     if (tr->kb == 256)
-        train_bad_fwd_kernel<8><<<grid_rows(rows, sm, 16), 128, 0, st>>>(
+        train_bad_fwd_kernel<8><<<grid_rows((rows + 3) / 4, sm, 4), 128, 0, st>>>(
             patches, rows, bp->d_patch_box, bp->d_patch_side, theta, inv_scale, tr->r_bad, tr->bits_bad);
     else
-        train_bad_fwd_kernel<16><<<grid_rows(rows, sm, 16), 128, 0, st>>>(
+        train_bad_fwd_kernel<16><<<grid_rows((rows + 3) / 4, sm, 3), 128, 0, st>>>(
             patches, rows, bp->d_patch_box, bp->d_patch_side, theta, inv_scale, tr->r_bad, tr->bits_bad);
     trace_kernel(st, "train_bad_fwd");
     // relaxed HashSIFT
