@@ -425,9 +425,13 @@ __global__ void __launch_bounds__(128) train_hs_bwd_kernel(const float *__restri
             const float m2 = gx * gx + gy * gy;
             float dgx = 0.f, dgy = 0.f;
             if (m2 > 0.f && nrm > 0.f) {
-                const float m = sqrtf(m2);
-                // the adjoint picks a bin pair from the orientation, so it uses the
-                // closer-to-exact atan2f (the vote itself is continuous in it)
+                // 1/|g| and 1/|g|^2 from one reciprocal square root; the bin
+                // pair comes from the closer-to-exact atan2f, which lands
+                // exact multiples of 45 degrees (frequent on flat-sided
+                // patches) on the same side of a bin edge as the exact angle:
+                // the histogram's derivative jumps there
+                const float im = rsqrtf(m2);
+                const float m = m2 * im;
                 float phi = atan2f(gy, gx);
                 if (phi < 0.0f)
                     phi += 6.28318530717958647692f;
@@ -439,8 +443,9 @@ __global__ void __launch_bounds__(128) train_hs_bwd_kernel(const float *__restri
                 const float g = L.g[q];
                 const float dmag = g * ((1.f - w1) * d0 + w1 * d1);
                 const float dphi = g * m * (d1 - d0) * 1.27323954473516268615f;
-                dgx = dmag * gx / m - dphi * gy / m2;
-                dgy = dmag * gy / m + dphi * gx / m2;
+                const float im2 = im * im;
+                dgx = dmag * gx * im - dphi * gy * im2;
+                dgy = dmag * gy * im + dphi * gx * im2;
             }
             gxs[i][j] = dgx;
             gys[i][j] = dgy;
