@@ -808,15 +808,19 @@ KERNEL_SOURCES = {
     "hs_proj_tc": ["proj_tc.cu", "bd_internal.h"],
     "match_tc": ["match_tc.cu", "bd_internal.h"],
     "match_multi": ["match.cu", "match_dev.cuh", "bd_internal.h"],
+    "select_keys": ["select.cu", "bd_internal.h"],
+    "select_threshold": ["select.cu", "bd_internal.h"],
 }
 NCU_TRAFFIC = {
-    "plain": {"describe_batch/batch_persistent": (1004544, "afa01f3f29981ea9")},
-    "large": {"describe_batch/batch_persistent": (38534656 + 49448448, "afa01f3f29981ea9"),
-              "describe_batch/hs_proj_tc": (21686784 + 512, "c1091bfc3acad8ea"),
-              "match_bad/match_tc": (10271232, "38e54003bf0f64e1"),
-              "match_hashsift/match_tc": (20514560, "38e54003bf0f64e1")},
-    "batch": {"describe_batch/batch_persistent": (332636928 + 314133248, "afa01f3f29981ea9"),
-              "describe_batch/hs_proj_tc": (106037248 + 7576832, "c1091bfc3acad8ea")},
+    "plain": {"describe_batch/batch_persistent": (1004544, "15990c857db35fe0")},
+    "large": {"describe_batch/batch_persistent": (38534656 + 49448448, "15990c857db35fe0"),
+              "describe_batch/hs_proj_tc": (21686784 + 512, "f8c01a07fb5d97b9"),
+              "match_bad/match_tc": (10279168, "6361374bef3b0bee"),
+              "match_hashsift/match_tc": (20522240, "6361374bef3b0bee")},
+    "select": {"select/select_keys": (201392896 + 341874432, "0bf0f3eea08c5fe9"),
+               "select/select_threshold": (394236160 + 3337472, "0bf0f3eea08c5fe9")},
+    "batch": {"describe_batch/batch_persistent": (332636928 + 314133248, "15990c857db35fe0"),
+              "describe_batch/hs_proj_tc": (106037248 + 7576832, "f8c01a07fb5d97b9")},
 }
 
 
@@ -1030,11 +1034,11 @@ def run_select(args):
     peaks, kind = load_peaks()
     key_bytes = J * 3 * n * 2
     traffic = {"select_keys": 3 * n * 1024 + key_bytes, "select_threshold": key_bytes + 8 * n}
-    dom = max(kern, key=kern.get)
+    dom = max((k for k in kern if k in traffic), key=kern.get)  # select_geom is set-up
     ach = traffic[dom] / (kern[dom] * 1e-3) / 1e9
     roof = {"kernel": dom, "ms": kern[dom], "bound": "hbm", "achieved": ach,
             "peak": float(peaks["hbm_gbs"]), "unit": "GB/s", "frac": ach / float(peaks["hbm_gbs"]),
-            "traffic": None, "peak_source": f"{kind} HBM copy",
+            "traffic": ncu_traffic("select", "select/" + dom), "peak_source": f"{kind} HBM copy",
             "algorithmic_bytes": traffic[dom]}
     # end to end: patches and similarities from pinned host memory, results back
     hP = torch.from_numpy(sw.patches).pin_memory()
