@@ -1104,8 +1104,9 @@ def main():
     ap.add_argument("--no-components", action="store_true",
                     help="skip the per-stage component measurements")
     ap.add_argument("--batch-config", default=None,
-                    help="bad_kp_per_item,ctas_per_sm,hs_first[,hs_kp_per_item[,proj_fused]] for the persistent kernel "
-                         "instead of the autotuner's pick")
+                    help="the fields of bd_batch_config (bad_kp_per_item,ctas_per_sm,hs_first"
+                         "[,hs_kp_per_item[,proj_fused[,bad_shared[,proj_half]]]]) for the "
+                         "persistent kernel instead of the autotuner's pick")
     ap.add_argument("--match", choices=["auto", "tensor", "popc", "fused"], default="auto",
                     help="matching: tensor cores (bd_match_tc), POPC (bd_match_batch), fused into "
                          "the describing launch (bd_batch_set_matches), or auto (tensor cores from "

@@ -275,7 +275,10 @@ typedef struct bd_batch bd_batch;
  *                   small batches).
  *  bad_shared       0: one BAD keypoint per warp; 1: the CTA's four warps share
  *                   each keypoint, a quarter of its words each (one
- *                   integral-image window per CTA in L1 instead of four). */
+ *                   integral-image window per CTA in L1 instead of four).
+ *  proj_half        with proj_fused = 1: 0 projects 32 keypoints x 32 bits
+ *                   per work item, 1 32 keypoints x 16 bits (twice the items,
+ *                   half the chain each; the same bits). */
 typedef struct bd_batch_config {
     int bad_kp_per_item;
     int ctas_per_sm;
@@ -283,6 +286,7 @@ typedef struct bd_batch_config {
     int hs_kp_per_item;
     int proj_fused;
     int bad_shared;
+    int proj_half;
 } bd_batch_config;
 
 /* Plans the description of n_img images with BAD and/or HashSIFT (either

@@ -415,12 +415,14 @@ class MatchJob(ctypes.Structure):
 class BatchConfig(ctypes.Structure):
     _fields_ = [("bad_kp_per_item", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("hs_first", ctypes.c_int), ("hs_kp_per_item", ctypes.c_int),
-                ("proj_fused", ctypes.c_int), ("bad_shared", ctypes.c_int)]
+                ("proj_fused", ctypes.c_int), ("bad_shared", ctypes.c_int),
+                ("proj_half", ctypes.c_int)]
 
     def as_dict(self):
         return {"bad_kp_per_item": self.bad_kp_per_item, "ctas_per_sm": self.ctas_per_sm,
                 "hs_first": self.hs_first, "hs_kp_per_item": self.hs_kp_per_item,
-                "proj_fused": self.proj_fused, "bad_shared": self.bad_shared}
+                "proj_fused": self.proj_fused, "bad_shared": self.bad_shared,
+                "proj_half": self.proj_half}
 
 
 class BatchEvent(ctypes.Structure):
@@ -485,9 +487,10 @@ class Batch:
         self.ctx._check(st, "bd_describe_batch")
 
     def set_config(self, bad_kp_per_item: int, ctas_per_sm: int, hs_first: int,
-                   hs_kp_per_item: int = 4, proj_fused: int = 0, bad_shared: int = 0):
+                   hs_kp_per_item: int = 4, proj_fused: int = 0, bad_shared: int = 0,
+                   proj_half: int = 0):
         c = BatchConfig(bad_kp_per_item, ctas_per_sm, hs_first, hs_kp_per_item, proj_fused,
-                        bad_shared)
+                        bad_shared, proj_half)
         self.ctx._check(lib().bd_batch_set_config(self.handle, ctypes.byref(c)), "bd_batch_set_config")
 
     def config(self) -> dict:

@@ -57,6 +57,7 @@ struct BatchKernelArgs {
     int hs_flags;            // BD_HS_VARIANT_CLIP / _ROOT
     // fused FP32 projection items (proj_fused): [ceil(n_kp/32)] x [K/32] tiles
     int proj_items, proj_cols;  // 0 when the tcgen05 kernel projects after this one
+    int proj_half;              // 1: 16-bit tiles (proj_cols = K / 16)
     unsigned int *hs_group_done;  // [ceil(n_kp/32)] histograms finished per 32 keypoints
     const float *W, *bias;      // FP32 W [128][K] (row-major), bias [K]
     int hs_nbits;
@@ -178,18 +179,22 @@ __device__ __forceinline__ int find_image(const BatchImageDev *imgs, int n_img, 
 }
 
 // Fused FP32 projection (Sec. III-B, D = sgn(W^T h + b)) of keypoints
-// [k0, k0 + nk) and bits [32 cb, 32 cb + 32): 128 threads, thread (row t/4,
-// columns 8 (t%4) + [0, 8)); each margin is summed in the FP32 projection
-// kernel's order (four 32-term chunks from zero, added in sequence), so the
-// bits equal that kernel's and the tensor-core path's.
+// [k0, k0 + nk) and bits [4 NB cb, 4 NB cb + 4 NB): 128 threads, thread (row
+// t/4, columns NB (t%4) + [0, NB)); NB = 8 gives 32-bit tiles, NB = 4 16-bit
+// tiles (half the work per tile, for a shorter chain at the end of a small
+// batch).  Each margin is summed in the FP32 projection kernel's order (four
+// 32-term chunks from zero, added in sequence), so the bits equal that
+// kernel's and the tensor-core path's.
 struct ProjTile {
     float H[32][132];  // histogram rows (padded: row r starts at bank 4r)
-    float Wt[128][32]; // W[:, 32 cb + c]
+    float Wt[128][32]; // W[:, 4 NB cb + c]
 };
 
+template <int NB>
 __device__ __forceinline__ void proj_tile(ProjTile &S, const BatchKernelArgs &A, int k0, int nk,
                                           int cb)
 {
+    constexpr int TW = 4 * NB;  // bits per tile
     const int t = threadIdx.x;
     for (int e = t; e < 32 * 32; e += 128) {  // 32 rows x 32 float4
         const int r = e >> 5, c4 = e & 31;
@@ -197,49 +202,51 @@ __device__ __forceinline__ void proj_tile(ProjTile &S, const BatchKernelArgs &A,
                                 : make_float4(0.f, 0.f, 0.f, 0.f);
         *reinterpret_cast<float4 *>(&S.H[r][4 * c4]) = v;
     }
-    for (int e = t; e < 128 * 8; e += 128) {  // 128 rows x 8 float4
-        const int k = e >> 3, c4 = e & 7;
+    for (int e = t; e < 128 * NB; e += 128) {  // 128 rows x NB float4
+        const int k = e / NB, c4 = e % NB;
         *reinterpret_cast<float4 *>(&S.Wt[k][4 * c4]) =
-            __ldg(reinterpret_cast<const float4 *>(A.W + (size_t)k * A.hs_nbits + 32 * cb) + c4);
+            __ldg(reinterpret_cast<const float4 *>(A.W + (size_t)k * A.hs_nbits + TW * cb) + c4);
     }
     __syncthreads();
     const int r = t >> 2, g = t & 3;
-    float acc[8];
+    float acc[NB];
 #pragma unroll 1
     for (int k0c = 0; k0c < kHistDim; k0c += 32) {
-        float part[8];
+        float part[NB];
 #pragma unroll
-        for (int b = 0; b < 8; ++b)
+        for (int b = 0; b < NB; ++b)
             part[b] = 0.0f;
 #pragma unroll 8
         for (int kk = k0c; kk < k0c + 32; ++kk) {
             const float h = S.H[r][kk];
-            const float4 w0 = *reinterpret_cast<const float4 *>(&S.Wt[kk][8 * g]);
-            const float4 w1 = *reinterpret_cast<const float4 *>(&S.Wt[kk][8 * g + 4]);
-            part[0] = fmaf(h, w0.x, part[0]);
-            part[1] = fmaf(h, w0.y, part[1]);
-            part[2] = fmaf(h, w0.z, part[2]);
-            part[3] = fmaf(h, w0.w, part[3]);
-            part[4] = fmaf(h, w1.x, part[4]);
-            part[5] = fmaf(h, w1.y, part[5]);
-            part[6] = fmaf(h, w1.z, part[6]);
-            part[7] = fmaf(h, w1.w, part[7]);
+#pragma unroll
+            for (int b4 = 0; b4 < NB; b4 += 4) {
+                const float4 w = *reinterpret_cast<const float4 *>(&S.Wt[kk][NB * g + b4]);
+                part[b4 + 0] = fmaf(h, w.x, part[b4 + 0]);
+                part[b4 + 1] = fmaf(h, w.y, part[b4 + 1]);
+                part[b4 + 2] = fmaf(h, w.z, part[b4 + 2]);
+                part[b4 + 3] = fmaf(h, w.w, part[b4 + 3]);
+            }
         }
 #pragma unroll
-        for (int b = 0; b < 8; ++b)
+        for (int b = 0; b < NB; ++b)
             acc[b] = k0c == 0 ? part[b] : acc[b] + part[b];
     }
     const int kp = k0 + r;
     const bool ok = r < nk && dev::kp_valid(A.kps[kp < A.n_kp ? kp : 0]);
-    uint32_t byte = 0;
+    uint32_t mine = 0;
 #pragma unroll
-    for (int b = 0; b < 8; ++b)
-        byte |= (ok && acc[b] + __ldg(A.bias + 32 * cb + 8 * g + b) > 0.0f) ? (1u << b) : 0u;
-    uint32_t word = byte << (8 * g);
+    for (int b = 0; b < NB; ++b)
+        mine |= (ok && acc[b] + __ldg(A.bias + TW * cb + NB * g + b) > 0.0f) ? (1u << b) : 0u;
+    uint32_t word = mine << (NB * g);
     word |= __shfl_xor_sync(0xffffffffu, word, 1);
     word |= __shfl_xor_sync(0xffffffffu, word, 2);
-    if (g == 0 && r < nk)
-        A.hs_out[(size_t)kp * (A.hs_nbits / 32) + cb] = word;
+    if (g == 0 && r < nk) {
+        if (NB == 8)
+            A.hs_out[(size_t)kp * (A.hs_nbits / 32) + cb] = word;
+        else  // the tile's half of a 32-bit word (little-endian halves)
+            reinterpret_cast<uint16_t *>(A.hs_out)[(size_t)kp * (A.hs_nbits / 16) + cb] = (uint16_t)word;
+    }
 }
 
 // MINB: resident CTAs per SM the register budget is sized for (4: 128 registers,
@@ -414,7 +421,10 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
             const int nk = min(32, A.n_kp - k0);
             if (cta_wait_count(A.hs_group_done + g, (unsigned)nk, &flag_s, A.status)) {
                 mark_ready();
-                proj_tile(U.p, A, k0, nk, cb);
+                if (A.proj_half)
+                    proj_tile<4>(U.p, A, k0, nk, cb);
+                else
+                    proj_tile<8>(U.p, A, k0, nk, cb);
             }
             __syncthreads();
             record();
@@ -529,7 +539,7 @@ struct bd_batch {
     // [projection groups] (groups of 32 keypoints), zero between launches
     unsigned int *d_counters = nullptr;
     float *d_hist = nullptr;
-    bd_batch_config cfg = {8, 0, 1, 4, 0, 0};
+    bd_batch_config cfg = {8, 0, 1, 4, 0, 0, 0};
     int max_ctas_per_sm = 0;
     int occ4 = 0;  // resident CTAs per SM of the 128-register variant
     int occ5 = 0;  // of the 102-register variant
@@ -662,7 +672,8 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     A.hs_per_item = b->cfg.hs_kp_per_item;
     const bool fused = b->cfg.proj_fused && b->hs && hs_out && b->n_kp > 0;
     if (fused) {
-        A.proj_cols = b->hs->nbits / 32;
+        A.proj_half = b->cfg.proj_half;
+        A.proj_cols = b->hs->nbits / (A.proj_half ? 16 : 32);
         A.proj_items = ((b->n_kp + 31) / 32) * A.proj_cols;
         A.hs_group_done = b->d_counters + 2 + 2 * b->n_img;
         A.W = b->hs->d_W;
@@ -916,7 +927,8 @@ bd_status bd_batch_set_config(bd_batch *b, const bd_batch_config *cfg)
         cfg->ctas_per_sm < 0 || cfg->hs_first < 0 || cfg->hs_first > 3 ||
         (cfg->hs_kp_per_item != 1 && cfg->hs_kp_per_item != 4) ||
         (cfg->proj_fused != 0 && cfg->proj_fused != 1) ||
-        (cfg->bad_shared != 0 && cfg->bad_shared != 1))
+        (cfg->bad_shared != 0 && cfg->bad_shared != 1) ||
+        (cfg->proj_half != 0 && cfg->proj_half != 1))
         return set_err(b->ctx, BD_ERR_INVALID, "bd_batch_set_config: bad configuration");
     b->cfg = *cfg;
     int items = 0;
@@ -1068,14 +1080,15 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     const bool can_fuse = b->hs && hs_out;
     const bool with_bad = b->bad && bad_out;
     for (int bs = 0; bs < (with_bad ? 2 : 1); ++bs)
-    for (int fu = 0; fu < (can_fuse ? 2 : 1); ++fu)
+    for (int fu = 0; fu < (can_fuse ? 3 : 1); ++fu)
     for (int hm : {1, 4})
         for (int hs_first = 0; hs_first < 4 && s == BD_OK; ++hs_first)
             for (int it : items)
                 for (int c : per_sm) {
                     if (s != BD_OK)
                         break;
-                    bd_batch_config cfg = {it, c, hs_first, hm, fu, bs};
+                    // fu: 0 tcgen05 projection, 1 fused 32-bit tiles, 2 fused 16-bit tiles
+                    bd_batch_config cfg = {it, c, hs_first, hm, fu ? 1 : 0, bs, fu == 2 ? 1 : 0};
                     float ms = 0.f;
                     s = time_cfg(cfg, reps, &ms);
                     res.push_back({ms, cfg});
@@ -1127,9 +1140,9 @@ bd_status bd_batch_set_timeline(bd_batch *b, int enable)
     if (enable && e == cudaSuccess) {
         // the most items any configuration queues: pass-1 and pass-2 tiles,
         // one HashSIFT item per keypoint, BAD items of 4 keypoints, and
-        // projection tiles of 32 keypoints x 32 of at most 512 bits
+        // projection tiles of 32 keypoints x 16 of at most 512 bits
         const long long cap = 2LL * b->n_tiles + b->n_kp + (b->n_kp / 4 + b->n_img) +
-                              ((long long)(b->n_kp + 31) / 32) * 16 + b->m_max_items + 1;
+                              ((long long)(b->n_kp + 31) / 32) * 32 + b->m_max_items + 1;
         if (cap > 0x7fffffffLL / (long long)sizeof(bd_batch_event))
             e = cudaErrorMemoryAllocation;
         else

@@ -186,18 +186,18 @@ def test_fused_fp32_projection_equals_tensor_core_path(gpu_ctx, hs_mode):
             b = gpu_ctx.batch(bp if with_bad else None, hp, dimgs, offs)
             ob = torch.zeros((n, 8), dtype=torch.int32, device="cuda") if with_bad else None
             res = []
-            for fused in (0, 1):
+            for fused, half in ((0, 0), (1, 0), (1, 1)):
                 oh = torch.full((n, 8), -1, dtype=torch.int32, device="cuda")
-                b.set_config(8, 4, 2, hs_mode, fused)
+                b.set_config(8, 4, 2, hs_mode, fused, 0, half)
                 b.describe(dimgs, dk, ob, oh, graph=bool(fused))
                 res.append(_u32(oh))
-            assert np.array_equal(res[0], res[1])
+            assert np.array_equal(res[0], res[1]) and np.array_equal(res[0], res[2])
             assert gpu_ctx.sync_status() == 0
             b.close()
 
 
-@pytest.mark.parametrize("cfg", [(8, 4, 0, 4, 0, 0), (4, 2, 1, 1, 1, 0), (32, 6, 2, 4, 1, 1),
-                                 (8, 4, 3, 4, 1, 1), (4, 3, 3, 1, 0, 0)])
+@pytest.mark.parametrize("cfg", [(8, 4, 0, 4, 0, 0, 0), (4, 2, 1, 1, 1, 0, 1), (32, 6, 2, 4, 1, 1, 0),
+                                 (8, 4, 3, 4, 1, 1, 1), (4, 3, 3, 1, 0, 0, 0)])
 def test_timeline_respects_dependencies(gpu_ctx, cfg):
     """The item timeline lists every queued item once, and no item starts
     before the items it depends on ended: pass-2 tiles after all pass-1 tiles
@@ -214,7 +214,7 @@ def test_timeline_respects_dependencies(gpu_ctx, cfg):
     b = gpu_ctx.batch(bp, hp, dimgs, offs)
     n = len(kps)
     dk = _dev(kps)
-    it, _, _, hm, fused, _ = cfg
+    it, _, _, hm, fused, _, half = cfg
     b.set_config(*cfg)
     ob0 = torch.zeros((n, 8), dtype=torch.int32, device="cuda")
     oh0 = torch.zeros((n, 8), dtype=torch.int32, device="cuda")
@@ -233,7 +233,8 @@ def test_timeline_respects_dependencies(gpu_ctx, cfg):
     bad_items = [math.ceil(c / it) for c in counts]
     bad_img = np.repeat(np.arange(len(imgs)), bad_items)
     n_hs = math.ceil(n / hm)
-    n_proj = math.ceil(n / 32) * 8 if fused else 0
+    ptiles = 16 if half else 8  # projection tiles per 32 keypoints at 256 bits
+    n_proj = math.ceil(n / 32) * ptiles if fused else 0
     expect = {BD_ITEM_II_PASS1: sum(tiles), BD_ITEM_II_PASS2: sum(tiles), BD_ITEM_BAD: sum(bad_items),
               BD_ITEM_HASHSIFT: n_hs, BD_ITEM_PROJ: n_proj}
     assert len(ev) == sum(expect.values())
@@ -257,12 +258,12 @@ def test_timeline_respects_dependencies(gpu_ctx, cfg):
         for g in range(math.ceil(n / 32)):
             first, last = (32 * g) // hm, (min(n, 32 * g + 32) - 1) // hm
             claimed = hsi["t_claim"][first:last + 1].max()
-            assert np.all(pr["t_ready"][g * 8:(g + 1) * 8] >= claimed)
+            assert np.all(pr["t_ready"][g * ptiles:(g + 1) * ptiles] >= claimed)
     b.set_timeline(False)
     b.close()
 
 
-@pytest.mark.parametrize("fused,graph", [(1, True), (1, False), (0, True)])
+@pytest.mark.parametrize("fused,graph", [(1, True), (1, False), (0, True), (2, True)])
 def test_batch_matchings_equal_bd_match(gpu_ctx, fused, graph):
     """Matchings set on the plan give the records bd_match gives on the same
     descriptors: inside the persistent launch (proj_fused = 1) or as the
@@ -283,7 +284,7 @@ def test_batch_matchings_equal_bd_match(gpu_ctx, fused, graph):
             (BD_DESC_BAD, 4, 4, 4, 5), (BD_DESC_HASHSIFT, 5, 3, 9, 10)]
     outs = [torch.full((max(int(cnt[q]), 1), 3), -7, dtype=torch.int32, device="cuda")
             if cnt[q] else None for (_, q, _, _, _) in spec]
-    b.set_config(8, 4, 2, 4, fused)
+    b.set_config(8, 4, 2, 4, 1 if fused else 0, 0, 1 if fused == 2 else 0)
     b.set_matches([(d, q, t, o, rn, rd) for (d, q, t, rn, rd), o in zip(spec, outs)])
     ob = torch.zeros((n, 8), dtype=torch.int32, device="cuda")
     oh = torch.zeros((n, 8), dtype=torch.int32, device="cuda")
