@@ -112,45 +112,13 @@ class Workload:
 
     # ---- GPU -----------------------------------------------------------
     def to_device(self, ctx, autotune=True, config=None):
-        import torch
         import paper_2108_08380_gb300 as bd
-        dev = "cuda"
-        # the step's inputs (images, keypoints) live in one device arena and its
-        # outputs in another, so that the end-to-end measurement moves each
-        # with one copy; the tensors below are views into them
-        in_parts = [im.nbytes for im in self.images] + [self.kps.nbytes]
-        in_off, tot = [], 0
-        for nb in in_parts:
-            in_off.append(tot)
-            tot += (nb + 255) // 256 * 256
-        self.host_in = np.zeros(tot, np.uint8)
-        for im, o in zip(self.images, in_off):
-            self.host_in[o:o + im.nbytes] = im.reshape(-1)
-        self.host_in[in_off[-1]:in_off[-1] + self.kps.nbytes] = self.kps.view(np.uint8).reshape(-1)
-        self.in_arena = torch.from_numpy(self.host_in).to(dev)
-        self.dimg = [self.in_arena[o:o + im.nbytes].view(im.shape) for im, o in zip(self.images, in_off)]
-        self.dkps = self.in_arena[in_off[-1]:in_off[-1] + self.kps.nbytes].view(torch.float32) \
-            .view(self.kps.shape)
         self.bp = ctx.bad_params(self.wl.bad)
         self.hp = ctx.hs_params(self.wl.hs, precision=bd.BD_HS_BF16_RESCUE, band=self.band)
-        n = self.n
-        na = int(self.offsets[1]) if self.match else 0
-        shapes = [(n, self.bad_bits // 32), (n, self.hs_bits // 32)] + \
-            ([(na, 3), (na, 3)] if self.match else [])
-        out_off, tot = [], 0
-        for sh in shapes:
-            out_off.append(tot)
-            tot += (sh[0] * sh[1] + 63) // 64 * 64
-        self.out_arena = torch.empty(tot, dtype=torch.int32, device=dev)
-        views = [self.out_arena[o:o + sh[0] * sh[1]].view(sh) for sh, o in zip(shapes, out_off)]
-        self.bad, self.hs = views[0], views[1]
-        self.plan = ctx.batch(self.bp, self.hp, self.dimg, self.offsets)
-        if self.match:
-            self.m_bad, self.m_hs = views[2], views[3]
-            if self.match_kind == "fused":
-                # image A's descriptors against image B's, by the describing launch
-                self.plan.set_matches([(bd.BD_DESC_BAD, 0, 1, self.m_bad, 4, 5),
-                                       (bd.BD_DESC_HASHSIFT, 0, 1, self.m_hs, 4, 5)])
+        self.set0 = DeviceSet(self, ctx)
+        for k in ("host_in", "in_arena", "dimg", "dkps", "out_arena", "bad", "hs", "plan",
+                  "m_bad", "m_hs"):
+            setattr(self, k, getattr(self.set0, k, None))
         self.tuned = None
         if config is not None:
             self.plan.set_config(*config)
@@ -158,30 +126,19 @@ class Workload:
         elif autotune:
             self.tuned, _ = self.plan.autotune(self.dimg, self.dkps, self.bad, self.hs, reps=5)
 
+    def second_set(self, ctx):
+        """Another copy of the step's device buffers and plan, in the same
+        launch configuration (double-buffered end-to-end steps)."""
+        ds = DeviceSet(self, ctx)
+        if self.tuned is not None:
+            ds.plan.set_config(*[self.tuned[k] for k in BATCH_CONFIG_FIELDS])
+        return ds
+
     def stages(self, ctx):
-        """(label, callable) of the ABI calls of one step, in order."""
-        st = [("describe_batch", lambda: self.plan.describe(self.dimg, self.dkps, self.bad, self.hs,
-                                                            graph=True))]
-        if self.match:
-            na = int(self.offsets[1])
-            if self.match_kind == "fused":
-                pass  # done by describe_batch (bd_batch_set_matches)
-            elif self.match_kind == "tensor":
-                st += [
-                    ("match_bad", lambda: ctx.match(self.bad[:na], self.bad[na:], self.bad_bits,
-                                                    4, 5, out=self.m_bad, tensor_cores=True)),
-                    ("match_hashsift", lambda: ctx.match(self.hs[:na], self.hs[na:], self.hs_bits,
-                                                         4, 5, out=self.m_hs, tensor_cores=True)),
-                ]
-            else:
-                # both descriptor types in one launch (bd_match_batch)
-                jobs = [(self.bad[:na], self.bad[na:], self.bad_bits),
-                        (self.hs[:na], self.hs[na:], self.hs_bits)]
-                st += [("match", lambda: ctx.match_batch(jobs, 4, 5, outs=[self.m_bad, self.m_hs]))]
-        return st
+        return self.set0.stages(ctx)
 
     def outputs(self):
-        return [self.bad, self.hs] + ([self.m_bad, self.m_hs] if self.match else [])
+        return self.set0.outputs()
 
     # ---- CPU oracle ----------------------------------------------------
     def oracle_step(self, sample_kp: int):
@@ -208,6 +165,81 @@ class Workload:
             oracle.match(ha, hb, self.hs_bits)
             npairs = 2 * len(da) * len(db)
         return nd, npairs
+
+
+BATCH_CONFIG_FIELDS = ("bad_kp_per_item", "ctas_per_sm", "hs_first", "hs_kp_per_item",
+                       "proj_fused", "bad_shared", "proj_half")
+
+
+class DeviceSet:
+    """One copy of a step's device buffers: an input arena (images and
+    keypoints, so the end-to-end step moves them with one copy), an output
+    arena (descriptors and match records, one copy back), views into both, and
+    the batch plan on them (with its matchings when they are fused)."""
+
+    def __init__(self, wl, ctx):
+        import torch
+        import paper_2108_08380_gb300 as bd
+        self.wl = wl
+        dev = "cuda"
+        in_parts = [im.nbytes for im in wl.images] + [wl.kps.nbytes]
+        in_off, tot = [], 0
+        for nb in in_parts:
+            in_off.append(tot)
+            tot += (nb + 255) // 256 * 256
+        self.host_in = np.zeros(tot, np.uint8)
+        for im, o in zip(wl.images, in_off):
+            self.host_in[o:o + im.nbytes] = im.reshape(-1)
+        self.host_in[in_off[-1]:in_off[-1] + wl.kps.nbytes] = wl.kps.view(np.uint8).reshape(-1)
+        self.in_arena = torch.from_numpy(self.host_in).to(dev)
+        self.dimg = [self.in_arena[o:o + im.nbytes].view(im.shape) for im, o in zip(wl.images, in_off)]
+        self.dkps = self.in_arena[in_off[-1]:in_off[-1] + wl.kps.nbytes].view(torch.float32) \
+            .view(wl.kps.shape)
+        n = wl.n
+        na = int(wl.offsets[1]) if wl.match else 0
+        shapes = [(n, wl.bad_bits // 32), (n, wl.hs_bits // 32)] + \
+            ([(na, 3), (na, 3)] if wl.match else [])
+        out_off, tot = [], 0
+        for sh in shapes:
+            out_off.append(tot)
+            tot += (sh[0] * sh[1] + 63) // 64 * 64
+        self.out_arena = torch.empty(tot, dtype=torch.int32, device=dev)
+        views = [self.out_arena[o:o + sh[0] * sh[1]].view(sh) for sh, o in zip(shapes, out_off)]
+        self.bad, self.hs = views[0], views[1]
+        self.m_bad = self.m_hs = None
+        self.plan = ctx.batch(wl.bp, wl.hp, self.dimg, wl.offsets)
+        if wl.match:
+            self.m_bad, self.m_hs = views[2], views[3]
+            if wl.match_kind == "fused":
+                # image A's descriptors against image B's, by the describing launch
+                self.plan.set_matches([(bd.BD_DESC_BAD, 0, 1, self.m_bad, 4, 5),
+                                       (bd.BD_DESC_HASHSIFT, 0, 1, self.m_hs, 4, 5)])
+
+    def stages(self, ctx):
+        """(label, callable) of the ABI calls of one step, in order."""
+        wl = self.wl
+        st = [("describe_batch", lambda: self.plan.describe(self.dimg, self.dkps, self.bad, self.hs,
+                                                            graph=True))]
+        if wl.match:
+            na = int(wl.offsets[1])
+            if wl.match_kind == "fused":
+                pass  # done by describe_batch (bd_batch_set_matches)
+            elif wl.match_kind == "tensor":
+                st += [
+                    ("match_bad", lambda: ctx.match(self.bad[:na], self.bad[na:], wl.bad_bits,
+                                                    4, 5, out=self.m_bad, tensor_cores=True)),
+                    ("match_hashsift", lambda: ctx.match(self.hs[:na], self.hs[na:], wl.hs_bits,
+                                                         4, 5, out=self.m_hs, tensor_cores=True)),
+                ]
+            else:
+                # both descriptor types in one launch (bd_match_batch)
+                jobs = [(self.bad[:na], self.bad[na:], wl.bad_bits),
+                        (self.hs[:na], self.hs[na:], wl.hs_bits)]
+                st += [("match", lambda: ctx.match_batch(jobs, 4, 5, outs=[self.m_bad, self.m_hs]))]
+        return st
+
+    def outputs(self):
+        return [self.bad, self.hs] + ([self.m_bad, self.m_hs] if self.wl.match else [])
 
 
 # ---------------------------------------------------------------------------
@@ -550,6 +582,8 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_budget)
     print(json.dumps(line), flush=True)
+    torch.cuda.synchronize()
+    ctx.close()  # plans and parameter sets first, then the context: not left to exit order
     if pg:
         pg.destroy_process_group()
 
@@ -698,29 +732,58 @@ def measure_components(ctx, wl, probes):
 
 
 def measure_e2e(ctx, wl, stages, steps):
-    """Same step through the API with host buffers: H2D of the step's inputs
-    (every image and the keypoints, staged in one pinned buffer) as one copy,
-    the step, D2H of all descriptors and match records (one arena) as one
-    copy, inside the timed region."""
+    """Same step through the API with host buffers, double-buffered: every
+    step copies its inputs (images and keypoints, staged in one pinned
+    buffer) host to device as one copy and reads all its descriptors and
+    match records back as one copy, inside the timed region; two device sets
+    (buffers and plans) let step i + 1's input copy and step i - 1's read-back
+    run while step i computes, on their own streams, as a serving loop would."""
     import torch
+    sets = [wl.set0, wl.second_set(ctx)]
     host_in = torch.from_numpy(wl.host_in).pin_memory()
-    host_out = torch.empty(wl.out_arena.shape, dtype=wl.out_arena.dtype).pin_memory()
+    host_out = [torch.empty(wl.out_arena.shape, dtype=wl.out_arena.dtype).pin_memory()
+                for _ in range(2)]
     bi = host_in.numel() * host_in.element_size()
-    bo = host_out.numel() * host_out.element_size()
+    bo = host_out[0].numel() * host_out[0].element_size()
+    s_c = torch.cuda.current_stream()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event()
+    ev_in, ev_comp, ev_out = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+    st = [ds.stages(ctx) for ds in sets]
+    for k in range(2):  # warm the second set's graph outside the timed region
+        for _, fn in st[k]:
+            fn()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    e0.record()
-    for _ in range(steps):
-        wl.in_arena.copy_(host_in, non_blocking=True)
-        for _, fn in stages:
+    e0.record(s_c)
+    s_in.wait_stream(s_c)
+    for i in range(steps):
+        k = i % 2
+        with torch.cuda.stream(s_in):
+            if i >= 2:
+                s_in.wait_event(ev_comp[k])  # step i - 2 has read this input arena
+            sets[k].in_arena.copy_(host_in, non_blocking=True)
+            ev_in[k].record(s_in)
+        s_c.wait_event(ev_in[k])
+        if i >= 2:
+            s_c.wait_event(ev_out[k])  # step i - 2's results were read back
+        for _, fn in st[k]:
             fn()
-        host_out.copy_(wl.out_arena, non_blocking=True)
-    e1.record()
+        ev_comp[k].record(s_c)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev_comp[k])
+            host_out[k].copy_(sets[k].out_arena, non_blocking=True)
+            ev_out[k].record(s_out)
+    s_c.wait_stream(s_out)
+    e1.record(s_c)
     torch.cuda.synchronize()
+    sets[1].plan.close()  # release the second plan here, not at interpreter exit
     ms = e0.elapsed_time(e1) / steps
     return {"value": wl.descriptors_per_step / (ms * 1e-3), "unit": "descriptors/s",
-            "ms_per_step": ms, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
+            "ms_per_step": ms, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
+            "pipelining": "double-buffered: the input copy of the next step and the read-back "
+                          "of the previous one overlap each step's compute"}
 
 
 def roofline(wl, per_kernel, clocks, probes=None):
@@ -978,6 +1041,10 @@ def run_train(args):
                                           f"part is understated)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    torch.cuda.synchronize()
+    ctx.close()
+    if pg is not None:
+        pg.destroy_process_group()
 
 
 def run_select(args):
@@ -1089,6 +1156,8 @@ def run_select(args):
                                           f"{dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    torch.cuda.synchronize()
+    ctx.close()
 
 
 def main():
