@@ -731,6 +731,44 @@ def measure_components(ctx, wl, probes):
     return res
 
 
+def double_buffered(steps, copy_in, compute, copy_out):
+    """Times `steps` end-to-end steps over two device buffer sets: step i runs
+    copy_in(i % 2) on an input stream, compute(i % 2) on the current stream
+    and copy_out(i % 2) on an output stream, with events so that a set's input
+    copy waits for the compute two steps back and its compute for the
+    read-back two steps back.  Returns ms per step (CUDA events)."""
+    import torch
+    s_c = torch.cuda.current_stream()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_comp = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_out = [torch.cuda.Event(), torch.cuda.Event()]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s_c)
+    s_in.wait_stream(s_c)
+    for i in range(steps):
+        k = i % 2
+        with torch.cuda.stream(s_in):
+            if i >= 2:
+                s_in.wait_event(ev_comp[k])
+            copy_in(k)
+            ev_in[k].record(s_in)
+        s_c.wait_event(ev_in[k])
+        if i >= 2:
+            s_c.wait_event(ev_out[k])
+        compute(k)
+        ev_comp[k].record(s_c)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev_comp[k])
+            copy_out(k)
+            ev_out[k].record(s_out)
+    s_c.wait_stream(s_out)
+    e1.record(s_c)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
 def measure_e2e(ctx, wl, stages, steps):
     """Same step through the API with host buffers, double-buffered: every
     step copies its inputs (images and keypoints, staged in one pinned
@@ -999,20 +1037,25 @@ def run_train(args):
                 "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                 "frac": byts / t_dom / 1e9 / float(peaks["hbm_gbs"]), "traffic": None,
                 "algorithmic_bytes": byts, "peak_source": f"{kind} HBM copy"}
-    # end to end: the patches from pinned host memory, the loss back
+    # end to end, double-buffered: the patches from pinned host memory, the
+    # loss back, every step (the gradients stay on the device, as in training)
     hP = torch.from_numpy(tw.patches).pin_memory()
-    loss_h = torch.empty(2, dtype=torch.float32).pin_memory()
-    reps = max(3, min(K, 10))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(reps):
-        P.copy_(hP, non_blocking=True)
-        loss, _ = one()
-        loss_h.copy_(loss, non_blocking=True)
-    e1.record()
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / reps
+    Ps = [P, torch.empty_like(P)]
+    losses = [None, None]
+    loss_h = [torch.empty(2, dtype=torch.float32).pin_memory() for _ in range(2)]
+
+    def copy_in(k):
+        Ps[k].copy_(hP, non_blocking=True)
+
+    def compute(k):
+        loss, _ = step.forward(Ps[k], theta, W, b)
+        step.backward(Ps[k], W, g)
+        losses[k] = loss
+
+    def copy_out(k):
+        loss_h[k].copy_(losses[k], non_blocking=True)
+
+    e2e_ms = double_buffered(max(4, min(K, 10)), copy_in, compute, copy_out)
     line = {"metric": "training steps (forward + backward) per second", "value": world * 1e3 / ms,
             "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1107,26 +1150,28 @@ def run_select(args):
             "peak": float(peaks["hbm_gbs"]), "unit": "GB/s", "frac": ach / float(peaks["hbm_gbs"]),
             "traffic": ncu_traffic("select", "select/" + dom), "peak_source": f"{kind} HBM copy",
             "algorithmic_bytes": traffic[dom]}
-    # end to end: patches and similarities from pinned host memory, results back
+    # end to end, double-buffered: patches and similarities from pinned host
+    # memory, results back, every step
     hP = torch.from_numpy(sw.patches).pin_memory()
     hap = torch.from_numpy(sw.sim_ap).pin_memory()
     han = torch.from_numpy(sw.sim_an).pin_memory()
-    out_h = [torch.empty(J, dtype=torch.int32).pin_memory(), torch.empty(J, dtype=torch.int64).pin_memory(),
-             torch.empty(1, dtype=torch.int32).pin_memory()]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = max(3, min(K, 20))
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(reps):
-        dP.copy_(hP, non_blocking=True)
-        dap.copy_(hap, non_blocking=True)
-        dan.copy_(han, non_blocking=True)
-        outs = step()
-        for h, d in zip(out_h, outs):
+    dev_in = [(dP, dap, dan), (torch.empty_like(dP), torch.empty_like(dap), torch.empty_like(dan))]
+    res = [None, None]
+    out_h = [[torch.empty(J, dtype=torch.int32).pin_memory(), torch.empty(J, dtype=torch.int64).pin_memory(),
+              torch.empty(1, dtype=torch.int32).pin_memory()] for _ in range(2)]
+
+    def copy_in(k):
+        for d, h in zip(dev_in[k], (hP, hap, han)):
+            d.copy_(h, non_blocking=True)
+
+    def compute(k):
+        res[k] = ctx.select_feature(*dev_in[k], sw.tau, sw.centres, sw.sides)
+
+    def copy_out(k):
+        for h, d in zip(out_h[k], res[k]):
             h.copy_(d, non_blocking=True)
-    e1.record()
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / reps
+
+    e2e_ms = double_buffered(max(4, min(K, 20)), copy_in, compute, copy_out)
     line = {
         "metric": "BAD feature-selection rounds: candidates evaluated per second (Algorithm 1 with "
                   "Algorithm 2, 0.1 threshold grid)",
