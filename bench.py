@@ -540,6 +540,7 @@ def run_ours(args):
     ctx.trace(False)
     ctx.trace_reset()
     ctx.rescued_count(reset=True)
+    timeline = item_timeline(wl, flush)
     # ---- end to end through the public API with pinned host buffers ----
     e2e = measure_e2e(ctx, wl, stages, max(3, min(K, 50)))
 
@@ -575,6 +576,7 @@ def run_ours(args):
         "roofline": roof,
         "probes": probes,
         "components": components,
+        "item_timeline": timeline,
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -729,6 +731,42 @@ def measure_components(ctx, wl, probes):
                                  "kernel": "tensor cores" if tc else "POPC",
                                  "mutual_pairs": int((mnn >= 0).sum().item())}
     return res
+
+
+ITEM_KINDS = {0: "integral_pass1", 1: "hashsift", 2: "integral_pass2", 3: "bad", 4: "projection",
+              5: "matching"}
+
+
+def item_timeline(wl, flush):
+    """One more step of the persistent kernel with its item timeline on (after
+    the timed steps; L2 flushed first): per work-item kind, the count, when the
+    first was claimed and the last ended (us from the first claim), the mean
+    wait for dependencies and the mean and largest work time."""
+    import torch
+    plan = wl.plan
+    plan.set_timeline(True)
+    flush.fill_(0.5)
+    torch.cuda._sleep(1_000_000)
+    for _, fn in wl.stages(plan.ctx)[:1]:
+        fn()
+    ev = plan.timeline()
+    plan.set_timeline(False)
+    if len(ev) == 0:
+        return None
+    t0 = int(ev["t_claim"].min())
+    out = {"span_us": (int(ev["t_end"].max()) - t0) / 1e3, "kinds": {}}
+    for k, name in ITEM_KINDS.items():
+        e = ev[ev["kind"] == k]
+        if len(e) == 0:
+            continue
+        out["kinds"][name] = {
+            "items": int(len(e)),
+            "first_claim_us": (int(e["t_claim"].min()) - t0) / 1e3,
+            "last_end_us": (int(e["t_end"].max()) - t0) / 1e3,
+            "wait_mean_us": float(np.mean(e["t_ready"] - e["t_claim"])) / 1e3,
+            "work_mean_us": float(np.mean(e["t_end"] - e["t_ready"])) / 1e3,
+            "work_max_us": float(np.max(e["t_end"] - e["t_ready"])) / 1e3}
+    return out
 
 
 def double_buffered(steps, copy_in, compute, copy_out):

@@ -107,8 +107,9 @@ __device__ __forceinline__ float sample(const uint8_t *__restrict__ img, int w, 
 // quantity as atan2(gy, gx) wrapped to [0, 2 pi) times 4/pi.  The first-octant
 // angle u = (4/pi) atan(r), r = min/max of |gx|, |gy| in [0, 1], comes from an
 // odd polynomial r * P(r^2) fitted here by weighted least squares on [0, 1]
-// (max error 5e-8 in exact arithmetic, 2.2e-7 evaluated in FP32); the signs
-// and the |gy| > |gx| test place it in its octant.  (gx, gy) != (0, 0).
+// (max error 5e-8 in exact arithmetic, 2.2e-7 evaluated in FP32), exact at
+// r = 0 and r = 1; the signs and the |gy| > |gx| test place it in its
+// octant.  (gx, gy) != (0, 0).
 __device__ __forceinline__ float orientation8(float gx, float gy)
 {
     const float ax = fabsf(gx), ay = fabsf(gy);
@@ -123,7 +124,9 @@ __device__ __forceinline__ float orientation8(float gx, float gy)
     p = fmaf(p, z, 0.2539675235748291f);
     p = fmaf(p, z, -0.4243689775466919f);
     p = fmaf(p, z, 1.2732386589050293f);
-    const float u = p * r;
+    // exact at the octant edges: 0 on the axes (r = 0) and 1 on the
+    // diagonals, so exact multiples of 45 degrees give exact bin edges
+    const float u = mn == mx ? 1.0f : p * r;
     float q = ay > ax ? 2.0f - u : u;  // first quadrant, [0, 2]
     if (gx < 0.0f)
         q = 4.0f - q;                  // second quadrant (gy >= 0)
