@@ -103,14 +103,17 @@ __device__ __forceinline__ float sample(const uint8_t *__restrict__ img, int w, 
     return fmaf(ay, bot - top, top);
 }
 
-// Orientation of the gradient (gx, gy) in units of pi/4, on [0, 8]: the same
-// quantity as atan2(gy, gx) wrapped to [0, 2 pi) times 4/pi.  The first-octant
-// angle u = (4/pi) atan(r), r = min/max of |gx|, |gy| in [0, 1], comes from an
-// odd polynomial r * P(r^2) fitted here by weighted least squares on [0, 1]
-// (max error 5e-8 in exact arithmetic, 2.2e-7 evaluated in FP32), exact at
-// r = 0 and r = 1; the signs and the |gy| > |gx| test place it in its
-// octant.  (gx, gy) != (0, 0).
-__device__ __forceinline__ float orientation8(float gx, float gy)
+// Orientation bin pair of the gradient (gx, gy) != (0, 0).  The angle
+// atan2(gy, gx) wrapped to [0, 2 pi) is q pi/4; the vote goes to bin floor(q)
+// with weight 1 - frac(q) and to the next bin with frac(q) = w1.  The
+// first-octant angle u = (4/pi) atan(r), r = min/max of |gx|, |gy| in [0, 1],
+// comes from an odd polynomial r * P(r^2) fitted here by weighted least
+// squares on [0, 1] (max error 5e-8 in exact arithmetic, 2.2e-7 evaluated in
+// FP32), exact at r = 0 and r = 1, so exact multiples of 45 degrees fall on
+// exact bin edges.  The octant o (0..7) follows from the signs and the
+// |gy| > |gx| test: q = o + u in even octants and o + 1 - u in odd ones, so
+// the bin is o and w1 is u or 1 - u, with no rounding of q itself.
+__device__ __forceinline__ int orient_bin(float gx, float gy, float &w1)
 {
     const float ax = fabsf(gx), ay = fabsf(gy);
     const float mn = fminf(ax, ay), mx = fmaxf(ax, ay);
@@ -124,15 +127,14 @@ __device__ __forceinline__ float orientation8(float gx, float gy)
     p = fmaf(p, z, 0.2539675235748291f);
     p = fmaf(p, z, -0.4243689775466919f);
     p = fmaf(p, z, 1.2732386589050293f);
-    // exact at the octant edges: 0 on the axes (r = 0) and 1 on the
-    // diagonals, so exact multiples of 45 degrees give exact bin edges
     const float u = mn == mx ? 1.0f : p * r;
-    float q = ay > ax ? 2.0f - u : u;  // first quadrant, [0, 2]
-    if (gx < 0.0f)
-        q = 4.0f - q;                  // second quadrant (gy >= 0)
-    if (gy < 0.0f)
-        q = 8.0f - q;                  // third / fourth quadrant
-    return q;
+    // quadrant k = 2 sy + (sx ^ sy) starts at octant 2k; within it the
+    // second octant is the one nearer the next axis (sw flipped in odd k)
+    const int sx = gx < 0.0f, sy = gy < 0.0f, sw = ay > ax;
+    const int t = sx ^ sy;
+    const int odd = t ^ sw;
+    w1 = odd ? 1.0f - u : u;
+    return 4 * sy + 2 * t + odd;
 }
 
 // Per-thread constants of the 128-thread histogram layout used by the
@@ -403,7 +405,7 @@ __device__ __forceinline__ void vote_px(WarpHist &S, int lane, int i, float up, 
     const bool any = m2 > 0.0f;
     const float m = any ? m2 * rsqrtf(m2) : 0.0f;
     float w1;
-    const int b0 = split_floor(orientation8(any ? gx : 1.0f, gy), w1) & 7;
+    const int b0 = orient_bin(any ? gx : 1.0f, gy, w1);
     const int b1 = (b0 + 1) & 7;
     // (g_i g_j) |grad|: gi and g_half carry a factor 1/2 each, m a factor 2
     const float gm = (2.0f * gi * g_half) * m;
@@ -721,7 +723,7 @@ __device__ __forceinline__ void hs_hist_warp_tri(WarpHistTri &S, const Src &src,
             const bool any = m2 > 0.0f;
             const float m = any ? m2 * rsqrtf(m2) : 0.0f;
             float w1;
-            const int b0 = split_floor(orientation8(any ? gx : 1.0f, gy), w1) & 7;
+            const int b0 = orient_bin(any ? gx : 1.0f, gy, w1);
             const int b1 = (b0 + 1) & 7;
             const float gm = (2.0f * gi * g_half) * m;
             const float yc = ((float)i - 3.5f) * 0.125f;
