@@ -342,7 +342,7 @@ def run_reference_select(args):
         "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64 (exact integer)", "data": "synthetic",
         "config": {"workload": f"{n} triplets, {sample} of the 1000 candidates per step"},
-        "cpu_baseline": {"value": value, "unit": "candidates/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "candidates/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                          "sample": f"{sample} candidates over all {n} triplets per step, single-threaded C"},
         "e2e": {"value": value, "unit": "candidates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -373,7 +373,7 @@ def run_reference_train(args):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": "65536 triplets of 32x32 FP32 patches, BAD-256 + HashSIFT-256 "
                                "relaxed at T = 0.1, mining with anchor swap, full backward"},
-        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                          "sample": f"forward + backward over {sample} of the {n} triplets per step "
                                    f"(FP64, single-threaded C), scaled linearly to a step (mining "
                                    f"within the sample, so the quadratic part is understated)"},
@@ -407,12 +407,35 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/int64/f64",
         "data": "synthetic", "config": dict(wl.config, sample_keypoints_per_image=sample),
         "matches_per_s": t_pairs / dt,
-        "cpu_baseline": {"value": value, "unit": "descriptors/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "descriptors/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                          "sample": f"first {sample} keypoints of each image per step, all stages "
                                    "(BAD, HashSIFT, both matchings), single-threaded C"},
         "e2e": {"value": value, "unit": "descriptors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def host_cpu() -> dict:
+    """The host cores this process may use and the CPU model (for the oracle
+    baselines, which run single-threaded on one of them)."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    try:
+        avail = len(os.sched_getaffinity(0))
+    except AttributeError:
+        avail = os.cpu_count() or 0
+    return {"available_cores": avail, "model": model}
 
 
 def cpu_baseline(wl, budget_s: float):
@@ -429,7 +452,7 @@ def cpu_baseline(wl, budget_s: float):
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": nd / dt, "unit": "descriptors/s", "cores": 1, "kind": "oracle",
+    return {"value": nd / dt, "unit": "descriptors/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
             "sample": f"{steps} oracle step(s) over the first {sample} keypoints of each image "
                       f"(BAD, HashSIFT, both matchings), single-threaded C, {dt:.1f} s",
             "matches_per_s": npairs / dt}
@@ -1115,7 +1138,7 @@ def run_train(args):
         oracle.train_step(tw.patches[:, :sample], bad, theta.cpu().numpy(), hs)
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": sample / n / dt, "unit": "steps/s", "cores": 1,
-                                "kind": "oracle",
+                                "kind": "oracle", "host": host_cpu(),
                                 "sample": f"forward + backward over {sample} of the {n} triplets "
                                           f"(FP64, single-threaded C), {dt:.3f} s, scaled linearly "
                                           f"to a step (mining within the sample, so the quadratic "
@@ -1234,7 +1257,7 @@ def run_select(args):
         oracle.select_feature(sw.patches, cands, sw.sim_ap, sw.sim_an, sw.tau)
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": sample / dt, "unit": "candidates/s", "cores": 1,
-                                "kind": "oracle",
+                                "kind": "oracle", "host": host_cpu(),
                                 "sample": f"{sample} candidates over all {n} triplets, single-threaded C, "
                                           f"{dt:.1f} s"}
     if rank == 0:
