@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(256) train_hs_dw_kernel(int rows, int K, const
 // Patch gradient of the HashSIFT loss (added to dpatches), one patch per CTA
 // iteration: dh = W dM, the normalisation adjoint, then the histogram adjoint.
 template <int K>
-__global__ void __launch_bounds__(128) train_hs_bwd_kernel(const float *__restrict__ patches,
+__global__ void __launch_bounds__(128, 8) train_hs_bwd_kernel(const float *__restrict__ patches,
                                                            int rows, const float *__restrict__ Wt,
                                                            const float *__restrict__ h,
                                                            const float *__restrict__ norm,
@@ -426,19 +426,21 @@ __global__ void __launch_bounds__(128) train_hs_bwd_kernel(const float *__restri
             float dgx = 0.f, dgy = 0.f;
             if (m2 > 0.f && nrm > 0.f) {
                 // 1/|g| and 1/|g|^2 from one reciprocal square root; the bin
-                // pair comes from atan2f, which lands exact multiples of 45
-                // degrees (frequent on flat-sided patches) on the same side of
-                // a bin edge as the exact angle (the histogram's derivative
-                // jumps there; the inlined polynomial measured slower here)
+                // pair from the forward's orient_bin, exact at multiples of 45
+                // degrees (frequent on flat-sided patches), where the
+                // histogram's derivative jumps
                 const float im = rsqrtf(m2);
                 const float m = m2 * im;
-                float phi = atan2f(gy, gx);
-                if (phi < 0.0f)
-                    phi += 6.28318530717958647692f;
-                const float tt = phi * 1.27323954473516268615f;
-                const float fl = floorf(tt);
-                const float w1 = tt - fl;
-                const int b0 = ((int)fl) & 7, b1 = (b0 + 1) & 7;
+                float w1;
+                int b0 = dev::orient_bin(gx, gy, w1);
+                // on a bin edge the derivative in the angle is one-sided: take
+                // the floor side (the bin that starts at the edge, w1 = 0), as
+                // the exact definition floor(q) does; the votes are the same
+                if (w1 >= 1.0f) {
+                    b0 = (b0 + 1) & 7;
+                    w1 = 0.0f;
+                }
+                const int b1 = (b0 + 1) & 7;
                 const float d0 = dH[cell * 8 + b0], d1 = dH[cell * 8 + b1];
                 const float g = L.g[q];
                 const float dmag = g * ((1.f - w1) * d0 + w1 * d1);
