@@ -275,7 +275,9 @@ typedef struct bd_batch bd_batch;
  *                   small batches).
  *  bad_shared       0: one BAD keypoint per warp; 1: the CTA's four warps share
  *                   each keypoint, a quarter of its words each (one
- *                   integral-image window per CTA in L1 instead of four).
+ *                   integral-image window per CTA in L1 instead of four);
+ *                   2: warp pairs share a keypoint, half its words each (two
+ *                   keypoints at a time, two windows per CTA).
  *  proj_half        with proj_fused = 1: 0 projects 32 keypoints x 32 bits
  *                   per work item, 1 32 keypoints x 16 bits (twice the items,
  *                   half the chain each; the same bits). */

@@ -51,7 +51,7 @@ struct BatchKernelArgs {
     const BatchImageDev *imgs;
     const uint8_t *const *img_ptr;
     int n_img, n_tiles, n_kp, n_bad_items, bad_per_item;
-    int bad_shared;          // 1: the CTA's four warps share each BAD keypoint
+    int bad_shared;          // 1: the CTA's four warps share each BAD keypoint, 2: warp pairs do
     int hs_items;            // ceil(n_kp / hs_per_item) if HashSIFT is on, else 0
     int hs_per_item;         // 1: the CTA shares a keypoint; 4: one keypoint per warp
     int hs_flags;            // BD_HS_VARIANT_CLIP / _ROOT
@@ -467,11 +467,17 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                 mark_ready();
                 const int k0 = I.kp_begin + (bi - I.bad_item_begin) * A.bad_per_item;
                 const int k1 = min(I.kp_end, k0 + A.bad_per_item);
-                if (A.bad_shared) {
+                if (A.bad_shared == 1) {
                     for (int k = k0; k < k1; ++k)
                         dev::bad_describe_words<NW, NW / 4, false>(
                             A.bad, A.ii + I.ii_off, I.w + 1, I.w, I.h, A.kps[k],
                             A.bad_out + (size_t)k * NW, A.status, (t >> 5) * (NW / 4));
+                } else if (A.bad_shared == 2) {
+                    // warp pairs: two keypoints at a time, half the words each
+                    for (int k = k0 + (t >> 6); k < k1; k += 2)
+                        dev::bad_describe_words<NW, NW / 2, false>(
+                            A.bad, A.ii + I.ii_off, I.w + 1, I.w, I.h, A.kps[k],
+                            A.bad_out + (size_t)k * NW, A.status, ((t >> 5) & 1) * (NW / 2));
                 } else {
                     for (int k = k0 + (t >> 5); k < k1; k += 4)
                         dev::bad_describe_warp<NW, false>(A.bad, A.ii + I.ii_off, I.w + 1, I.w, I.h,
@@ -927,7 +933,7 @@ bd_status bd_batch_set_config(bd_batch *b, const bd_batch_config *cfg)
         cfg->ctas_per_sm < 0 || cfg->hs_first < 0 || cfg->hs_first > 3 ||
         (cfg->hs_kp_per_item != 1 && cfg->hs_kp_per_item != 4) ||
         (cfg->proj_fused != 0 && cfg->proj_fused != 1) ||
-        (cfg->bad_shared != 0 && cfg->bad_shared != 1) ||
+        cfg->bad_shared < 0 || cfg->bad_shared > 2 ||
         (cfg->proj_half != 0 && cfg->proj_half != 1))
         return set_err(b->ctx, BD_ERR_INVALID, "bd_batch_set_config: bad configuration");
     b->cfg = *cfg;
@@ -1079,7 +1085,7 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     bd_status s = BD_OK;
     const bool can_fuse = b->hs && hs_out;
     const bool with_bad = b->bad && bad_out;
-    for (int bs = 0; bs < (with_bad ? 2 : 1); ++bs)
+    for (int bs = 0; bs < (with_bad ? 3 : 1); ++bs)
     for (int fu = 0; fu < (can_fuse ? 3 : 1); ++fu)
     for (int hm : {1, 4})
         for (int hs_first = 0; hs_first < 4 && s == BD_OK; ++hs_first)
