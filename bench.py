@@ -723,6 +723,24 @@ def measure_components(ctx, wl, probes):
         "bf16_tflops": flops / (k_bf.get("hs_proj_tc", t_bf) * 1e-3) / 1e12}
     hp32.close()
 
+    # SIFT variants before hashing (Sec. II: RootSIFT; trilinear cell binning,
+    # 0.2 clip): the same describe call with each variant on its own
+    # parameter set, histogram time against the plain histogram's
+    var = {}
+    hpv = ctx.hs_params(wl.wl.hs, precision=bd.BD_HS_BF16_RESCUE)
+    for name, flags in (("trilinear", bd.BD_HS_VARIANT_TRILINEAR), ("clip", bd.BD_HS_VARIANT_CLIP),
+                        ("root", bd.BD_HS_VARIANT_ROOT),
+                        ("all", bd.BD_HS_VARIANT_TRILINEAR | bd.BD_HS_VARIANT_CLIP
+                         | bd.BD_HS_VARIANT_ROOT)):
+        hpv.set_variant(flags)
+        kv = _kernel_ms(ctx, lambda: ctx.hashsift_describe(hpv, img, kps, out=bits_bf,
+                                                             hist_out=hist), reps)
+        tv = sum(v for kk, v in kv.items() if kk.startswith("hs_hist")) * 1e-3
+        var[name] = {"hist_ms": tv * 1e3, "patches_per_s": na / tv,
+                     "vs_plain_histogram": tv / th, "kernels": kv}
+    hpv.close()
+    res["hs_variants"] = var
+
     # matching (Sec. IV-C): POPC kernel and tensor-core kernel, same records
     if wl.match:
         q, tr = wl.bad[:na], wl.bad[na:]

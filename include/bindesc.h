@@ -166,11 +166,11 @@ bd_status bd_bad_params_table(const bd_bad_params *p, int32_t *offsets, int32_t 
 /* HashSIFT parameters (Sec. III-B)                                          */
 
 #define BD_HS_FP32 0        /* projection on CUDA cores in FP32 */
-#define BD_HS_BF16_RESCUE 1
+#define BD_HS_BF16_RESCUE 1 /* tcgen05 BF16 x BF16 -> FP32 (split head/tail), FP32 re-check near 0 */
 /* SIFT variants of the histogram before hashing (bd_hs_params_set_variant) */
 #define BD_HS_VARIANT_TRILINEAR 1 /* votes shared by the 2 x 2 nearest cells */
 #define BD_HS_VARIANT_CLIP 2      /* L2-normalise, clip at 0.2, renormalise */
-#define BD_HS_VARIANT_ROOT 4      /* RootSIFT: L1-normalise, square roots */ /* tcgen05 BF16 x BF16 -> FP32 (split head/tail), FP32 re-check near 0 */
+#define BD_HS_VARIANT_ROOT 4      /* RootSIFT: L1-normalise, square roots */
 
 /* Learned hash B = [W^T | b], copied from host memory.
  *  nbits     256 or 512.

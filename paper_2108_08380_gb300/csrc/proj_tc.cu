@@ -15,7 +15,8 @@
 //  - thread 0 loads the W^T head / tail tiles with TMA (128-byte swizzle):
 //    both phases at the start when the grid is one wave or less (BothB,
 //    96 KB of shared memory, lowest latency), else one phase at a time
-//    through one stage (64 KB, three CTAs per SM for throughput);
+//    through one stage (64 KB; two CTAs per SM either way, by registers,
+//    and three measured slower: less of the SM's memory is left as L1);
 //  - every thread loads its share of the FP32 histogram rows for both
 //    phases at once (row t/2, half t%2 of the phase's 64 values), splits
 //    them into BF16 head and tail in registers and writes the phase's A
@@ -27,11 +28,12 @@
 //  - warps w and w+4 read TMEM lane quadrant w%4 (= 32 keypoints), each half
 //    of the columns, add the FP32 bias, take the sign and the band mask
 //    without branches;
-//  - band bits are re-evaluated in FP32 by the two threads that hold the
-//    keypoint's histogram row in registers (terms [0,32) and [64,96), or
-//    [32,64) and [96,128)): each sums its two 32-term chunks from zero against
-//    the bit's FP32 W row, and the four partials are combined in the FP32
-//    projection kernel's order ((c0 + c1) + c2) + c3.
+//  - a row of zeros (a patch without gradients) projects to exactly the bias
+//    on both paths (every product is zero), so its bits are never queued;
+//  - band bits go to a list in shared memory and are re-evaluated in FP32
+//    64 at a time, four lanes per bit: lane q sums terms [32q, 32q + 32) as a
+//    chain from zero (histogram row and FP32 W row from L2), and the partials
+//    are combined in the FP32 projection kernel's order ((c0 + c1) + c2) + c3.
 // Waits on mbarriers are bounded; on a timeout the CTA raises
 // BD_FLAG_TIMEOUT, waits once more for its MMAs, frees TMEM and returns.
 #include "bd_internal.h"
@@ -45,7 +47,7 @@ constexpr int TILE = BM * 128;              // bytes of one 64-wide BF16 K chunk
 constexpr int NTH = 256;                    // threads per CTA
 // A hi/lo (one phase) + B hi/lo (both phases, or one stage)
 constexpr int smem_bytes(bool both_b) { return (both_b ? 6 : 4) * TILE + 1024; }
-static_assert(2048 + 2 * BM * BN <= 4 * TILE, "epilogue does not fit the operand area");
+static_assert(2048 + 2 * BM * BN <= 4 * TILE, "output tile and band list do not fit the operand area");
 
 // Offset of 16-byte chunk c (0..7) of row r in a 128-row x 128-byte operand
 // tile with the 128-byte swizzle: chunk positions are XORed with r mod 8.
@@ -91,6 +93,7 @@ __global__ void __launch_bounds__(NTH, 2) hs_proj_tc_kernel(
     __shared__ int abort_flag;
     __shared__ int list_n;
     __shared__ float bias_s[BN], band_s[BN];
+    __shared__ int row_nz[BM];
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     // the bit tiles of one keypoint tile are neighbours in launch order, so they
@@ -141,6 +144,19 @@ __global__ void __launch_bounds__(NTH, 2) hs_proj_tc_kernel(
 #pragma unroll
             for (int v = 0; v < 8; ++v)
                 av[p][v] = in ? __ldg(src + 16 * p + 8 * ah + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // A row of zeros projects to exactly the bias on either path: no re-check
+    {
+        uint32_t nz = 0;
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int v = 0; v < 8; ++v)
+                nz |= (__float_as_uint(av[p][v].x) | __float_as_uint(av[p][v].y) |
+                       __float_as_uint(av[p][v].z) | __float_as_uint(av[p][v].w)) & 0x7fffffffu;
+        nz |= __shfl_xor_sync(0xffffffffu, nz, 1);
+        if (ah == 0)
+            row_nz[ar] = nz != 0u;
     }
     // epilogue row and its validity, fetched early
     const int quad = warp & 3, half = warp >> 2;
@@ -224,9 +240,10 @@ __global__ void __launch_bounds__(NTH, 2) hs_proj_tc_kernel(
     dev::tc_fence_after();
 
     if (ok) {
-        // The operand area is dead now: it holds the output tile and the band masks.
-        uint32_t *out_tile = reinterpret_cast<uint32_t *>(smem);          // [128][BN/32], 2 KB
-        uint32_t *near_tile = reinterpret_cast<uint32_t *>(smem + 2048);  // [128][BN/32], 2 KB
+        // The operand area is dead now: it holds the output tile and the list
+        // of band bits (row << 7 | column, at most 128 x 128 entries).
+        uint32_t *out_tile = reinterpret_cast<uint32_t *>(smem);           // [128][BN/32], 2 KB
+        uint16_t *list = reinterpret_cast<uint16_t *>(smem + 2048);        // up to 32 KB
 #pragma unroll 1
         for (int cc = 0; cc < 2; ++cc) {
             const int c = half * 2 + cc;  // 32-column chunk of this warp
@@ -239,69 +256,56 @@ __global__ void __launch_bounds__(NTH, 2) hs_proj_tc_kernel(
                 word |= (m > 0.0f ? 1u : 0u) << j;
                 near |= (fabsf(m) < band_s[c * 32 + j] ? 1u : 0u) << j;
             }
-            if (!valid)
+            if (!valid || !row_nz[row])
                 near = 0u;
             out_tile[row * (BN / 32) + c] = valid ? word : 0u;
-            near_tile[row * (BN / 32) + c] = near;
-            if (near)
-                atomicAdd(&list_n, __popc(near));
+            if (near) {
+                int e = atomicAdd(&list_n, __popc(near));
+                for (uint32_t m = near; m; m &= m - 1, ++e)
+                    list[e] = (uint16_t)((row << 7) | (c * 32 + __ffs(m) - 1));
+            }
         }
         __syncthreads();
-        // FP32 re-check of the band bits of row ar by the two threads holding
-        // it: this thread has chunks ah and 2 + ah (av[0], av[1]); the partner
-        // (lane ^ 1) has the other two.  Both walk the same bits in step.
+        // FP32 re-check of the listed bits, 64 at a time: the four lanes of a
+        // group sum one 32-term chunk each as a chain from zero (histogram row
+        // and W row from L2), and the group's first lane combines them in the
+        // FP32 projection kernel's order ((c0 + c1) + c2) + c3 + b.
         const int total = list_n;
-        if (total) {
-            uint32_t mine[BN / 32];
-#pragma unroll
-            for (int w = 0; w < BN / 32; ++w)
-                mine[w] = near_tile[ar * (BN / 32) + w];
-            int w = 0;
+        const int g = t >> 2, q = t & 3;
 #pragma unroll 1
-            for (;;) {
-                while (w < BN / 32 && mine[w] == 0u)
-                    ++w;
-                const bool act = w < BN / 32;
-                if (!__any_sync(0xffffffffu, act))
-                    break;
-                int cc = 0;
-                if (act) {
-                    const int j = __ffs(mine[w]) - 1;
-                    mine[w] &= mine[w] - 1;
-                    cc = w * 32 + j;
-                }
-                float pa = 0.0f, pb = 0.0f;
-                if (act) {
-                    const float4 *wv = reinterpret_cast<const float4 *>(Wt32 + (size_t)(n0 + cc) * kHistDim);
-                    // terms [32 ah, 32 ah + 32), then [64 + 32 ah, ...): each a chain from zero
+        for (int e0 = 0; e0 < total; e0 += NTH / 4) {
+            const int e = e0 + g;
+            const bool act = e < total;
+            const uint32_t v = act ? (uint32_t)list[e] : 0u;
+            const int er = (int)(v >> 7), ec = (int)(v & 127u);
+            float part = 0.0f;
+            if (act) {
+                const float4 *fr = reinterpret_cast<const float4 *>(hist32 + (size_t)(m0 + er) * kHistDim) + 8 * q;
+                const float4 *wr = reinterpret_cast<const float4 *>(Wt32 + (size_t)(n0 + ec) * kHistDim) + 8 * q;
+                float4 fv[8], wv[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float4 b = __ldg(wv + 8 * ah + i);
-                        pa = fmaf(av[0][i].x, b.x, pa);
-                        pa = fmaf(av[0][i].y, b.y, pa);
-                        pa = fmaf(av[0][i].z, b.z, pa);
-                        pa = fmaf(av[0][i].w, b.w, pa);
-                    }
+                for (int i = 0; i < 8; ++i) {
+                    fv[i] = __ldg(fr + i);
+                    wv[i] = __ldg(wr + i);
+                }
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float4 b = __ldg(wv + 16 + 8 * ah + i);
-                        pb = fmaf(av[1][i].x, b.x, pb);
-                        pb = fmaf(av[1][i].y, b.y, pb);
-                        pb = fmaf(av[1][i].z, b.z, pb);
-                        pb = fmaf(av[1][i].w, b.w, pb);
-                    }
+                for (int i = 0; i < 8; ++i) {
+                    part = fmaf(fv[i].x, wv[i].x, part);
+                    part = fmaf(fv[i].y, wv[i].y, part);
+                    part = fmaf(fv[i].z, wv[i].z, part);
+                    part = fmaf(fv[i].w, wv[i].w, part);
                 }
-                const float qa = __shfl_xor_sync(0xffffffffu, pa, 1);
-                const float qb = __shfl_xor_sync(0xffffffffu, pb, 1);
-                if (act && ah == 0) {
-                    // chunks: c0 = pa, c1 = qa, c2 = pb, c3 = qb
-                    const float m32 = ((pa + qa) + pb) + qb + bias_s[cc];
-                    uint32_t &o = out_tile[ar * (BN / 32) + (cc >> 5)];
-                    if (m32 > 0.0f)
-                        o |= 1u << (cc & 31);
-                    else
-                        o &= ~(1u << (cc & 31));
-                }
+            }
+            const float c1 = __shfl_down_sync(0xffffffffu, part, 1);
+            const float c2 = __shfl_down_sync(0xffffffffu, part, 2);
+            const float c3 = __shfl_down_sync(0xffffffffu, part, 3);
+            if (act && q == 0) {
+                const float m32 = ((part + c1) + c2) + c3 + bias_s[ec];
+                uint32_t *o = &out_tile[er * (BN / 32) + (ec >> 5)];
+                if (m32 > 0.0f)
+                    atomicOr(o, 1u << (ec & 31));
+                else
+                    atomicAnd(o, ~(1u << (ec & 31)));
             }
         }
         __syncthreads();
@@ -347,8 +351,9 @@ cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const float *hist, int n, u
                               DeviceStatus *status, cudaStream_t st, const bd_keypoint *kps)
 {
     dim3 grid(p->nbits / BN, (n + BM - 1) / BM);
-    // one wave or less (two CTAs per SM with both W phases resident): latency
-    // variant; more: the single-stage variant keeps three CTAs per SM
+    // one wave or less (two CTAs per SM): both W phases resident, lowest
+    // latency; more: the single-stage variant, with more shared memory left
+    // to L1
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -136,6 +136,36 @@ def test_projection_of_oracle_histograms(gpu_ctx):
         assert np.array_equal(got[sure], refb[sure]), prec
 
 
+def test_zero_rows_project_to_the_bias_without_rescue(gpu_ctx):
+    """A histogram row of zeros (a patch without gradients) projects to exactly
+    b_k on both paths (every product is zero): its bits are b_k > 0, and none
+    of them is re-checked in FP32, even where |b_k| lies inside the band."""
+    import torch
+    rng = np.random.default_rng(21)
+    hs = synth.make_hashsift_params(512, rng)
+    b = hs.b.copy()
+    b[:8] = np.array([1e-7, -1e-7, 3e-6, -3e-6, 0.0, -0.0, 5e-5, -5e-5], np.float32)
+    hs = synth.HashSiftParams(hs.W, b, hs.spacing)
+    n = 300  # two full 128-row tiles and a ragged tail
+    h = rng.random((n, 128)).astype(np.float32)
+    h /= np.linalg.norm(h, axis=1, keepdims=True)
+    zero = rng.random(n) < 0.5
+    h[zero] = 0.0
+    want = b > 0
+    hp32 = gpu_ctx.hs_params(hs, precision=0)
+    hp16 = gpu_ctx.hs_params(hs, precision=1)
+    a = _bits(gpu_ctx.hashsift_project(hp32, torch.from_numpy(h).cuda()).cpu().numpy(), 512)
+    c = _bits(gpu_ctx.hashsift_project(hp16, torch.from_numpy(h).cuda()).cpu().numpy(), 512)
+    assert np.array_equal(a, c)
+    assert (a[zero] == want).all()
+    z = torch.zeros((n, 128), dtype=torch.float32, device="cuda")
+    gpu_ctx.rescued_count(reset=True)
+    cz = _bits(gpu_ctx.hashsift_project(hp16, z).cpu().numpy(), 512)
+    assert gpu_ctx.rescued_count(reset=True) == 0
+    assert (cz == want).all()
+    assert gpu_ctx.sync_status() == 0
+
+
 def test_fixed_band_1e3_reports_disagreements(gpu_ctx):
     """The batched workload's fixed 1e-3 band: with the split BF16 product the
     margin error is below 2^-13 ||W_k|| < 1e-3, so any bit it gets wrong (none
