@@ -13,9 +13,11 @@ __global__ void __launch_bounds__(256, 2) bad_gather_kernel(dev::BadTables T,
                                                             int n, uint32_t *__restrict__ out,
                                                             DeviceStatus *status)
 {
+    __shared__ uint32_t sums[8][2 * NW * 32];  // the box sums of each warp's keypoint
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps)
-        dev::bad_describe_warp<NW, true>(T, ii, stride, w, h, kps[i], out + (size_t)i * NW, status);
+        dev::bad_describe_warp<NW, true>(T, ii, stride, w, h, kps[i], out + (size_t)i * NW, status,
+                                         sums[threadIdx.x >> 5]);
 }
 
 }  // namespace

@@ -1,11 +1,15 @@
-// BAD descriptor of one keypoint by one warp (Sec. III-A).  Shared by the
-// per-image gather kernel (bad.cu) and the batched persistent kernel.
+// BAD descriptor of one keypoint (Sec. III-A).  Shared by the per-image
+// gather kernel (bad.cu) and the batched persistent kernel.
 //
-// Lane j owns bits j, j+32, ...; for each bit it reads the pair's rotated and
-// scaled corner offsets from the (level, angle-bin) table, takes the two box
-// sums from the integral image (4 lookups each, zero outside the image),
-// applies the exact integer stump  sum1 - sum2 <= floor(num * s'^2 / den)
-// and the warp packs 32 stumps per __ballot_sync.
+// Each bit compares two equal-sized boxes: h = +1 iff the exact integer stump
+// sum1 - sum2 <= floor(num * s'^2 / den) holds, the sums taken from the
+// integral image (4 lookups each, zero outside the image) at the box
+// positions of the keypoint's (level, angle-bin) table.  The 2K boxes of a
+// table are stored sorted by top-left row (then side, then column), so the
+// 32 boxes of one warp-wide load sit on a few image rows: about 9 cache
+// lines per load on the batched workload's tables instead of 27 when lane j
+// takes bit j.  The box sums go to shared memory by box id; then lane j of
+// word w forms bit 32 w + j and the warp packs 32 stumps per __ballot_sync.
 #pragma once
 
 #include "bd_internal.h"
@@ -14,7 +18,8 @@ namespace bd {
 namespace dev {
 
 struct BadTables {
-    const short4 *corner;   // [L][NB][K] top-left corner offsets (x1, y1, x2, y2)
+    const short4 *box;      // [L][NB][2K] (x, y, side, id = 2 k + j) of box j of pair k,
+                            // top-left corner from the keypoint's pixel; sorted per table
     const int2 *side_thr;   // [L][K] (scaled side, integer threshold)
     int nbins, nlevels;
     float angle_scale;      // float(NB / 2 pi)
@@ -55,20 +60,38 @@ __device__ __forceinline__ void bad_cell(const BadTables &T, const bd_keypoint &
         b += T.nbins;
 }
 
-// Writes words [word0, word0 + WPW) of the NW words of keypoint kp to
-// out[word0 ..]; all 32 lanes of the warp call it.  WPW = NW: the whole
-// descriptor by one warp; WPW = NW / 4: the four warps of a CTA share the
-// keypoint (its integral-image window is then read by one CTA, not four).
-template <int NW, int WPW, bool ReadOnly>
-__device__ __forceinline__ void bad_describe_words(const BadTables &T, const uint32_t *ii,
+// Barrier of the P warps sharing a keypoint: the warp itself, or named
+// barrier `id` (1 or 2, immediates so that the kernel reserves only those)
+// over their 32 P threads.
+template <int P>
+__device__ __forceinline__ void bad_sync(int id)
+{
+    if (P == 1)
+        __syncwarp();
+    else if (id == 1)
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * P) : "memory");
+    else
+        asm volatile("bar.sync 2, %0;" ::"n"(32 * P) : "memory");
+}
+
+// The NW words of keypoint kp to out[0..NW), by P warps (1, 2 or 4) that all
+// call it with the same kp: `part` is this warp's index among them, `sums`
+// 2K words of shared memory they share, `bar` their named barrier (P > 1).
+// Warp `part` sums box groups [part 2NW/P, (part + 1) 2NW/P) of 32 boxes and
+// forms words [part NW/P, (part + 1) NW/P).
+template <int NW, int P, bool ReadOnly>
+__device__ __forceinline__ void bad_describe_boxes(const BadTables &T, const uint32_t *ii,
                                                    int stride, int w, int h, const bd_keypoint &kp,
-                                                   uint32_t *out, DeviceStatus *status, int word0)
+                                                   uint32_t *out, DeviceStatus *status,
+                                                   uint32_t *sums, int part, int bar)
 {
     constexpr int K = NW * 32;
+    constexpr int GPW = 2 * NW / P;  // box groups of this warp
+    constexpr int WPW = NW / P;      // output words of this warp
     const int lane = threadIdx.x & 31;
-    if (!kp_valid(kp)) {
+    if (!kp_valid(kp)) {  // the same branch in every warp of the group
         if (lane < WPW)
-            out[word0 + lane] = 0u;
+            out[part * WPW + lane] = 0u;
         if (lane == 0)
             raise_flag(status, BD_FLAG_INVALID_KEYPOINT);
         return;
@@ -77,48 +100,53 @@ __device__ __forceinline__ void bad_describe_words(const BadTables &T, const uin
     const int iy = round_coord(kp.y);
     int l, b;
     bad_cell(T, kp, l, b);
-    const short4 *tab = T.corner + ((size_t)l * T.nbins + b) * K;
-    const int2 *st = T.side_thr + (size_t)l * K;
-    uint32_t mine = 0;
-    // a group's table reads first, then all its gathers: the warp keeps
-    // 8 x 8 independent loads in flight instead of walking the bits in series
-    constexpr int G = WPW < 8 ? WPW : 8;
+    const short4 *tab = T.box + ((size_t)l * T.nbins + b) * (2 * K) + (size_t)part * GPW * 32;
+    const int2 *st = T.side_thr + (size_t)l * K + part * WPW * 32;
+    int thr[WPW];
+#pragma unroll
+    for (int q = 0; q < WPW; ++q)
+        thr[q] = __ldg(&st[q * 32 + lane].y);
+    // a group's table reads first, then all its gathers: 8 x 4 loads in flight
+    constexpr int G = GPW < 8 ? GPW : 8;
 #pragma unroll 1
-    for (int j0 = word0; j0 < word0 + WPW; j0 += G) {
-        short4 c[G];
-        int2 s[G];
+    for (int g0 = 0; g0 < GPW; g0 += G) {
+        short4 e[G];
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            c[g] = __ldg(tab + (j0 + g) * 32 + lane);
-            s[g] = __ldg(st + (j0 + g) * 32 + lane);
-        }
+        for (int q = 0; q < G; ++q)
+            e[q] = __ldg(tab + (g0 + q) * 32 + lane);
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const uint32_t s1 = box_sum<ReadOnly>(ii, stride, w, h, ix + c[g].x, iy + c[g].y, s[g].x);
-            const uint32_t s2 = box_sum<ReadOnly>(ii, stride, w, h, ix + c[g].z, iy + c[g].w, s[g].x);
-            const bool bit = ((int)s1 - (int)s2) <= s[g].y;
-            const uint32_t word = __ballot_sync(0xffffffffu, bit);
-            if (lane == j0 - word0 + g)
-                mine = word;
-        }
+        for (int q = 0; q < G; ++q)
+            sums[e[q].w] = box_sum<ReadOnly>(ii, stride, w, h, ix + e[q].x, iy + e[q].y, e[q].z);
+    }
+    bad_sync<P>(bar);
+    uint32_t mine = 0;
+#pragma unroll
+    for (int q = 0; q < WPW; ++q) {
+        const int k = (part * WPW + q) * 32 + lane;
+        const uint2 pr = *reinterpret_cast<const uint2 *>(sums + 2 * k);
+        const uint32_t word = __ballot_sync(0xffffffffu, ((int)pr.x - (int)pr.y) <= thr[q]);
+        if (lane == q)
+            mine = word;
     }
     if (lane < WPW)
-        out[word0 + lane] = mine;
+        out[part * WPW + lane] = mine;
+    bad_sync<P>(bar);  // the sums may be overwritten by the next keypoint
 }
 
-// Writes the NW words of keypoint kp to out[0..NW); all 32 lanes call it.
+// One warp, the whole descriptor; sums: 2K words of the warp's shared memory.
 template <int NW, bool ReadOnly>
 __device__ __forceinline__ void bad_describe_warp(const BadTables &T, const uint32_t *ii, int stride,
                                                   int w, int h, const bd_keypoint &kp,
-                                                  uint32_t *out, DeviceStatus *status)
+                                                  uint32_t *out, DeviceStatus *status,
+                                                  uint32_t *sums)
 {
-    bad_describe_words<NW, NW, ReadOnly>(T, ii, stride, w, h, kp, out, status, 0);
+    bad_describe_boxes<NW, 1, ReadOnly>(T, ii, stride, w, h, kp, out, status, sums, 0, 0);
 }
 
 inline BadTables bad_tables(const bd_bad_params *p)
 {
     BadTables T;
-    T.corner = p->d_corner;
+    T.box = p->d_box;
     T.side_thr = p->d_side_thr;
     T.nbins = p->nbins;
     T.nlevels = p->nlevels;

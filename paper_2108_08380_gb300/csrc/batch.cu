@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
         dev::IiFinalSmem f;
         dev::WarpHist h[4];  // one per warp
         ProjTile p;
+        uint32_t bs[4][2 * NW * 32];  // BAD box sums: per warp, per warp pair or one shared
         struct {
             uint4 tile[kMatchTile * 16 / 4];  // train descriptors of a matching item
             uint2 wpair[128];                 // the warps' top-2 pairs
@@ -468,21 +469,23 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                 const int k0 = I.kp_begin + (bi - I.bad_item_begin) * A.bad_per_item;
                 const int k1 = min(I.kp_end, k0 + A.bad_per_item);
                 if (A.bad_shared == 1) {
+                    // the four warps share each keypoint (named barrier 1)
                     for (int k = k0; k < k1; ++k)
-                        dev::bad_describe_words<NW, NW / 4, false>(
+                        dev::bad_describe_boxes<NW, 4, false>(
                             A.bad, A.ii + I.ii_off, I.w + 1, I.w, I.h, A.kps[k],
-                            A.bad_out + (size_t)k * NW, A.status, (t >> 5) * (NW / 4));
+                            A.bad_out + (size_t)k * NW, A.status, U.bs[0], t >> 5, 1);
                 } else if (A.bad_shared == 2) {
-                    // warp pairs: two keypoints at a time, half the words each
+                    // warp pairs: two keypoints at a time (named barriers 1 and 2)
                     for (int k = k0 + (t >> 6); k < k1; k += 2)
-                        dev::bad_describe_words<NW, NW / 2, false>(
+                        dev::bad_describe_boxes<NW, 2, false>(
                             A.bad, A.ii + I.ii_off, I.w + 1, I.w, I.h, A.kps[k],
-                            A.bad_out + (size_t)k * NW, A.status, ((t >> 5) & 1) * (NW / 2));
+                            A.bad_out + (size_t)k * NW, A.status, U.bs[t >> 6], (t >> 5) & 1,
+                            1 + (t >> 6));
                 } else {
                     for (int k = k0 + (t >> 5); k < k1; k += 4)
                         dev::bad_describe_warp<NW, false>(A.bad, A.ii + I.ii_off, I.w + 1, I.w, I.h,
                                                           A.kps[k], A.bad_out + (size_t)k * NW,
-                                                          A.status);
+                                                          A.status, U.bs[t >> 5]);
                 }
             }
             __syncthreads();

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <algorithm>
 #include <vector>
 
 #include "bd_internal.h"
@@ -471,6 +472,30 @@ bd_status bd_bad_params_create(bd_ctx *ctx, int nbits, const uint8_t *centres,
             }
         }
     }
+    // The kernels' table: per (level, bin) the 2K boxes (x, y, side, id = 2 k + j),
+    // sorted by top-left row, side and column so that a warp's 32 consecutive
+    // boxes fall on few image rows.
+    std::vector<short4> box(nt * 2);
+    for (int l = 0; l < n_levels; ++l)
+        for (int b = 0; b < n_angle_bins; ++b) {
+            const size_t base = ((size_t)l * n_angle_bins + b) * nbits;
+            short4 *dst = box.data() + base * 2;
+            for (int k = 0; k < nbits; ++k) {
+                const short4 c = corner[base + k];
+                const short sp = (short)side_thr[(size_t)l * nbits + k].x;
+                dst[2 * k] = make_short4(c.x, c.y, sp, (short)(2 * k));
+                dst[2 * k + 1] = make_short4(c.z, c.w, sp, (short)(2 * k + 1));
+            }
+            std::sort(dst, dst + 2 * nbits, [](const short4 &a, const short4 &c) {
+                if (a.y != c.y)
+                    return a.y < c.y;
+                if (a.z != c.z)
+                    return a.z < c.z;
+                if (a.x != c.x)
+                    return a.x < c.x;
+                return a.w < c.w;
+            });
+        }
     std::vector<short4> pbox(nbits);
     std::vector<int> pside(nbits);
     for (int k = 0; k < nbits; ++k) {
@@ -479,7 +504,7 @@ bd_status bd_bad_params_create(bd_ctx *ctx, int nbits, const uint8_t *centres,
         pbox[k] = make_short4((short)(centres[k * 4 + 0] - s / 2), (short)(centres[k * 4 + 1] - s / 2),
                               (short)(centres[k * 4 + 2] - s / 2), (short)(centres[k * 4 + 3] - s / 2));
     }
-    cudaError_t e = cudaMalloc(&p->d_corner, nt * sizeof(short4));
+    cudaError_t e = cudaMalloc(&p->d_box, box.size() * sizeof(short4));
     if (e == cudaSuccess)
         e = cudaMalloc(&p->d_patch_box, nbits * sizeof(short4));
     if (e == cudaSuccess)
@@ -491,7 +516,7 @@ bd_status bd_bad_params_create(bd_ctx *ctx, int nbits, const uint8_t *centres,
     if (e == cudaSuccess)
         e = cudaMalloc(&p->d_side_thr, side_thr.size() * sizeof(int2));
     if (e == cudaSuccess)
-        e = cudaMemcpy(p->d_corner, corner.data(), nt * sizeof(short4), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(p->d_box, box.data(), box.size() * sizeof(short4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(p->d_side_thr, side_thr.data(), side_thr.size() * sizeof(int2),
                        cudaMemcpyHostToDevice);
@@ -509,8 +534,8 @@ void bd_bad_params_destroy(bd_bad_params *p)
         return;
     {
         DeviceGuard g(p->ctx->device);
-        if (p->d_corner)
-            cudaFree(p->d_corner);
+        if (p->d_box)
+            cudaFree(p->d_box);
         if (p->d_side_thr)
             cudaFree(p->d_side_thr);
         if (p->d_patch_box)
