@@ -20,7 +20,7 @@ namespace dev {
 struct BadTables {
     const short4 *box;      // [L][NB][2K] (x, y, side, id = 2 k + j) of box j of pair k,
                             // top-left corner from the keypoint's pixel; sorted per table
-    const int2 *side_thr;   // [L][K] (scaled side, integer threshold)
+    const int *thr;         // [L][K] integer threshold on sum1 - sum2
     int nbins, nlevels;
     float angle_scale;      // float(NB / 2 pi)
     float mids[kMaxLevels]; // float(sqrt(s_l s_{l+1}))
@@ -101,11 +101,11 @@ __device__ __forceinline__ void bad_describe_boxes(const BadTables &T, const uin
     int l, b;
     bad_cell(T, kp, l, b);
     const short4 *tab = T.box + ((size_t)l * T.nbins + b) * (2 * K) + (size_t)part * GPW * 32;
-    const int2 *st = T.side_thr + (size_t)l * K + part * WPW * 32;
+    const int *st = T.thr + (size_t)l * K + part * WPW * 32;
     int thr[WPW];
 #pragma unroll
     for (int q = 0; q < WPW; ++q)
-        thr[q] = __ldg(&st[q * 32 + lane].y);
+        thr[q] = __ldg(st + q * 32 + lane);
     // a group's table reads first, then all its gathers: 8 x 4 loads in flight
     constexpr int G = GPW < 8 ? GPW : 8;
 #pragma unroll 1
@@ -147,7 +147,7 @@ inline BadTables bad_tables(const bd_bad_params *p)
 {
     BadTables T;
     T.box = p->d_box;
-    T.side_thr = p->d_side_thr;
+    T.thr = p->d_thr;
     T.nbins = p->nbins;
     T.nlevels = p->nlevels;
     T.angle_scale = p->angle_scale;

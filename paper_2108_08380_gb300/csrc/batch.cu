@@ -190,22 +190,44 @@ struct ProjTile {
     float Wt[128][32]; // W[:, 4 NB cb + c]
 };
 
+// This thread's NB float4 of the tile's W columns [TW cb, TW cb + TW)
+// (W is a parameter: loaded before the wait for the histograms).
+template <int NB>
+__device__ __forceinline__ void proj_w_load(const BatchKernelArgs &A, int cb, float4 (&wv)[NB])
+{
+    constexpr int TW = 4 * NB;
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {  // 128 rows x NB float4
+        const int e = t + 128 * q;
+        wv[q] = __ldg(reinterpret_cast<const float4 *>(A.W + (size_t)(e / NB) * A.hs_nbits + TW * cb) +
+                      e % NB);
+    }
+}
+
 template <int NB>
 __device__ __forceinline__ void proj_tile(ProjTile &S, const BatchKernelArgs &A, int k0, int nk,
-                                          int cb)
+                                          int cb, const float4 (&wv)[NB])
 {
     constexpr int TW = 4 * NB;  // bits per tile
     const int t = threadIdx.x;
-    for (int e = t; e < 32 * 32; e += 128) {  // 32 rows x 32 float4
+    float4 hv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {  // 32 rows x 32 float4, all loads in flight
+        const int e = t + 128 * q;
         const int r = e >> 5, c4 = e & 31;
-        const float4 v = r < nk ? __ldcg(reinterpret_cast<const float4 *>(A.hist + (size_t)(k0 + r) * kHistDim) + c4)
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
-        *reinterpret_cast<float4 *>(&S.H[r][4 * c4]) = v;
+        hv[q] = r < nk ? __ldcg(reinterpret_cast<const float4 *>(A.hist + (size_t)(k0 + r) * kHistDim) + c4)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    for (int e = t; e < 128 * NB; e += 128) {  // 128 rows x NB float4
-        const int k = e / NB, c4 = e % NB;
-        *reinterpret_cast<float4 *>(&S.Wt[k][4 * c4]) =
-            __ldg(reinterpret_cast<const float4 *>(A.W + (size_t)k * A.hs_nbits + TW * cb) + c4);
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        const int e = t + 128 * q;
+        *reinterpret_cast<float4 *>(&S.Wt[e / NB][4 * (e % NB)]) = wv[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int e = t + 128 * q;
+        *reinterpret_cast<float4 *>(&S.H[e >> 5][4 * (e & 31)]) = hv[q];
     }
     __syncthreads();
     const int r = t >> 2, g = t & 3;
@@ -420,12 +442,20 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
             const int g = idx / A.proj_cols, cb = idx % A.proj_cols;
             const int k0 = g * 32;
             const int nk = min(32, A.n_kp - k0);
-            if (cta_wait_count(A.hs_group_done + g, (unsigned)nk, &flag_s, A.status)) {
-                mark_ready();
-                if (A.proj_half)
-                    proj_tile<4>(U.p, A, k0, nk, cb);
-                else
-                    proj_tile<8>(U.p, A, k0, nk, cb);
+            if (A.proj_half) {
+                float4 wv[4];
+                proj_w_load<4>(A, cb, wv);
+                if (cta_wait_count(A.hs_group_done + g, (unsigned)nk, &flag_s, A.status)) {
+                    mark_ready();
+                    proj_tile<4>(U.p, A, k0, nk, cb, wv);
+                }
+            } else {
+                float4 wv[8];
+                proj_w_load<8>(A, cb, wv);
+                if (cta_wait_count(A.hs_group_done + g, (unsigned)nk, &flag_s, A.status)) {
+                    mark_ready();
+                    proj_tile<8>(U.p, A, k0, nk, cb, wv);
+                }
             }
             __syncthreads();
             record();

@@ -78,7 +78,7 @@ struct bd_bad_params {
     int32_t *h_sides = nullptr;    // [L][K]
     // device tables
     short4 *d_box = nullptr;       // [L][NB][2K] boxes (x, y, side, id), sorted by (y, side, x)
-    int2 *d_side_thr = nullptr;    // [L][K] (scaled side, integer threshold on sum1-sum2)
+    int *d_thr = nullptr;          // [L][K] integer threshold on sum1 - sum2
     short4 *d_patch_box = nullptr; // [K] top-left corners in the 32x32 patch frame (training)
     int *d_patch_side = nullptr;   // [K] box sides in the patch frame
 };

@@ -496,6 +496,9 @@ bd_status bd_bad_params_create(bd_ctx *ctx, int nbits, const uint8_t *centres,
                 return a.w < c.w;
             });
         }
+    std::vector<int> thr(side_thr.size());
+    for (size_t i = 0; i < thr.size(); ++i)
+        thr[i] = side_thr[i].y;
     std::vector<short4> pbox(nbits);
     std::vector<int> pside(nbits);
     for (int k = 0; k < nbits; ++k) {
@@ -514,12 +517,11 @@ bd_status bd_bad_params_create(bd_ctx *ctx, int nbits, const uint8_t *centres,
     if (e == cudaSuccess)
         e = cudaMemcpy(p->d_patch_side, pside.data(), nbits * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMalloc(&p->d_side_thr, side_thr.size() * sizeof(int2));
+        e = cudaMalloc(&p->d_thr, side_thr.size() * sizeof(int));
     if (e == cudaSuccess)
         e = cudaMemcpy(p->d_box, box.data(), box.size() * sizeof(short4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(p->d_side_thr, side_thr.data(), side_thr.size() * sizeof(int2),
-                       cudaMemcpyHostToDevice);
+        e = cudaMemcpy(p->d_thr, thr.data(), thr.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         bd_bad_params_destroy(p);
         return cuda_err(ctx, e, "bd_bad_params_create: upload");
@@ -536,8 +538,8 @@ void bd_bad_params_destroy(bd_bad_params *p)
         DeviceGuard g(p->ctx->device);
         if (p->d_box)
             cudaFree(p->d_box);
-        if (p->d_side_thr)
-            cudaFree(p->d_side_thr);
+        if (p->d_thr)
+            cudaFree(p->d_thr);
         if (p->d_patch_box)
             cudaFree(p->d_patch_box);
         if (p->d_patch_side)
