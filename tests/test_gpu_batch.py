@@ -332,9 +332,10 @@ def test_batch_matchings_rejected_without_descriptors(gpu_ctx):
 
 @pytest.mark.parametrize("bits,levels", [(256, 1), (512, 5)])
 def test_bad_shared_keypoints_equal_per_image_calls(gpu_ctx, bits, levels):
-    """bad_shared = 1 (the CTA's four warps split each keypoint's words) and 2
-    (warp pairs, two keypoints at a time) give the per-image BAD bits, invalid
-    keypoints included (all-zero words)."""
+    """bad_shared = 0 (one keypoint per warp), 1 (the CTA's four warps split
+    each keypoint's boxes and words) and 2 (warp pairs, two keypoints at a
+    time) give the per-image BAD bits, invalid keypoints included (all-zero
+    words)."""
     import torch
     imgs, kps, offs, bad, hs = _small_batch(seed=41, bad_bits=bits, hs_bits=256, levels=levels)
     kps[3, 1] = np.inf
@@ -347,7 +348,7 @@ def test_bad_shared_keypoints_equal_per_image_calls(gpu_ctx, bits, levels):
     ref, _ = _per_image(gpu_ctx, bp, hp, imgs, kps, offs)
     gpu_ctx.sync_status()
     for it in (4, 8, 32):
-        for shared in (1, 2):
+        for shared in (0, 1, 2):
             ob = torch.full((n, bits // 32), -1, dtype=torch.int32, device="cuda")
             b.set_config(it, 4, 0, 4, 0, shared)
             b.describe(dimgs, dk, ob, None, graph=True)
