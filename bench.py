@@ -992,15 +992,15 @@ KERNEL_SOURCES = {
     "select_threshold": ["select.cu", "bd_internal.h"],
 }
 NCU_TRAFFIC = {
-    "plain": {"describe_batch/batch_persistent": (1004544, "15990c857db35fe0")},
-    "large": {"describe_batch/batch_persistent": (38534656 + 49448448, "15990c857db35fe0"),
-              "describe_batch/hs_proj_tc": (21686784 + 512, "f8c01a07fb5d97b9"),
-              "match_bad/match_tc": (10279168, "6361374bef3b0bee"),
-              "match_hashsift/match_tc": (20522240, "6361374bef3b0bee")},
-    "select": {"select/select_keys": (201392896 + 341874432, "0bf0f3eea08c5fe9"),
-               "select/select_threshold": (394236160 + 3337472, "0bf0f3eea08c5fe9")},
-    "batch": {"describe_batch/batch_persistent": (332636928 + 314133248, "15990c857db35fe0"),
-              "describe_batch/hs_proj_tc": (106037248 + 7576832, "f8c01a07fb5d97b9")},
+    "plain": {"describe_batch/batch_persistent": (1078272 + 3072, "297a7d942276500a")},
+    "large": {"describe_batch/batch_persistent": (38291712 + 48051200, "297a7d942276500a"),
+              "describe_batch/hs_proj_tc": (21689088 + 0, "99dda6785d778d92"),
+              "match_bad/match_tc": (10305792, "19c99d565cca98ce"),
+              "match_hashsift/match_tc": (20525824, "19c99d565cca98ce")},
+    "select": {"select/select_keys": (201392896 + 341874432, "d4480b53895862cd"),
+               "select/select_threshold": (394236160 + 3337472, "d4480b53895862cd")},
+    "batch": {"describe_batch/batch_persistent": (332435712 + 313150208, "297a7d942276500a"),
+              "describe_batch/hs_proj_tc": (106152192 + 4944384, "99dda6785d778d92")},
 }
 
 
@@ -1107,15 +1107,17 @@ def run_train(args):
         peak = 2.0 * float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]))
         roof = {"kernel": dom, "ms": kern[dom], "bound": "tensor", "achieved": flops / t_dom / 1e12,
                 "peak": peak, "unit": "TFLOP/s", "frac": flops / t_dom / 1e12 / peak,
-                "traffic": None, "algorithmic_flops": flops,
+                "traffic": ncu_traffic("train", dom), "traffic_unit": "bytes per launch (one of "
+                "the four mining matchings; ncu dram read + write)", "algorithmic_flops": flops,
                 "peak_source": f"{kind} bf16 sustained x 2 (nominal FP8/BF16 dense ratio)"}
     else:
         # the patch-bound kernels: one read of the 3n patches (4 KB each)
         byts = 3.0 * n * 4096
         roof = {"kernel": dom, "ms": kern[dom], "bound": "hbm", "achieved": byts / t_dom / 1e9,
                 "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                "frac": byts / t_dom / 1e9 / float(peaks["hbm_gbs"]), "traffic": None,
-                "algorithmic_bytes": byts, "peak_source": f"{kind} HBM copy"}
+                "frac": byts / t_dom / 1e9 / float(peaks["hbm_gbs"]),
+                "traffic": ncu_traffic("train", dom), "algorithmic_bytes": byts,
+                "peak_source": f"{kind} HBM copy"}
     # end to end, double-buffered: the patches from pinned host memory, the
     # loss back, every step (the gradients stay on the device, as in training)
     hP = torch.from_numpy(tw.patches).pin_memory()
