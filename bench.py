@@ -999,6 +999,7 @@ NCU_TRAFFIC = {
               "match_hashsift/match_tc": (20525824, "19c99d565cca98ce")},
     "select": {"select/select_keys": (201392896 + 341874432, "d4480b53895862cd"),
                "select/select_threshold": (394236160 + 3337472, "d4480b53895862cd")},
+    "train": {"match_tc": (33595904 + 0, "19c99d565cca98ce")},
     "batch": {"describe_batch/batch_persistent": (332435712 + 313150208, "297a7d942276500a"),
               "describe_batch/hs_proj_tc": (106152192 + 4944384, "99dda6785d778d92")},
 }
