@@ -179,11 +179,13 @@ int match_tc_query_blocks(int nq);
 cudaError_t launch_match_tc(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt,
                             int nbits, int ratio_num, int ratio_den, bd_match_result *out,
                             void *scratch, cudaStream_t st, unsigned int *arrivals);
-// same, returning the raw top-2 keys (distance << 22 | index) per query
+// same, returning the raw top-2 keys (distance << 22 | index) per query;
+// mine != 0 (hard-negative mining, nq == nt > 1): the nearest key among the
+// columns other than the query's own, in .x (.y is not the second nearest)
 cudaError_t launch_match_tc_keys(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt,
                                  int nbits, int ratio_num, int ratio_den, bd_match_result *out,
                                  uint2 *raw_keys, void *scratch, cudaStream_t st,
-                                 unsigned int *arrivals);
+                                 unsigned int *arrivals, int mine);
 // measurement probes (bd_probe); bad_args set when the geometry is refused
 cudaError_t launch_probe(int kind, const uint32_t *table, size_t table_words, size_t window_words,
                          int reps, uint32_t *sink, int sm_count, cudaStream_t st,

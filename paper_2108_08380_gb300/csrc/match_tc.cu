@@ -136,7 +136,11 @@ __device__ __forceinline__ bool epi_sync_or(bool v)
 
 // MINB: resident CTAs per SM (2 for K = 256: 96 KB of shared memory each and
 // at most 85 registers per thread; 1 for K = 512).
-template <int K, int MINB>
+// MINE (hard-negative mining, nq == nt): the query's own column is left out
+// when excl is set and only the nearest of the rest is kept, a maximum per
+// score instead of a top-2 -- the same key that the top-2 with the own
+// column skipped would give, since keys are unique.
+template <int K, int MINB, bool MINE>
 __global__ void __launch_bounds__(NTHREADS, MINB) match_tc_kernel(
     const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmT, int nq,
     int nt, int nbits, int rnum, int rden, uint2 *__restrict__ partial,
@@ -161,6 +165,7 @@ __global__ void __launch_bounds__(NTHREADS, MINB) match_tc_kernel(
     const int nqb = (nq + BM - 1) / BM;
     const int ntl = max(1, (nt + BN - 1) / BN);
     const long long T = (long long)nqb * ntl;
+    const bool excl = MINE && nq == nt && nt > 1;  // the own column exists and is not the only one
     const int G = (int)gridDim.x, c = (int)blockIdx.x;
     const long long p0 = T * c / G, p1 = T * (c + 1) / G;
 
@@ -281,6 +286,11 @@ __global__ void __launch_bounds__(NTHREADS, MINB) match_tc_kernel(
                 // after the second.  (Packing two 16-bit keys per register for
                 // packed min/max measured slower.)
                 float f1 = -INFINITY, f2 = -INFINITY;
+                // MINE: the query's own column (row qb BM + row) is left out;
+                // it falls in one tile of the block and there in the half
+                // that holds the warp's 32 rows, so `own` is warp-uniform
+                const int dcol = qb * BM + row - j0;
+                const bool own = MINE && excl && dcol >= 0 && dcol < 64;
 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
                     dev::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + col + 32 * hh, r);
@@ -290,26 +300,29 @@ __global__ void __launch_bounds__(NTHREADS, MINB) match_tc_kernel(
                         if (lane == 0)
                             dev::mbar_arrive(&bar_te[s]);
                     }
-                    if (valid >= 32 * hh + 32) {
+                    if (valid >= 32 * hh + 32 && !own) {
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             const float f = fmaf(__uint_as_float(r[j]), 256.0f, -(float)(32 * hh + j));
-                            f2 = fmaxf(f2, fminf(f1, f));
+                            if (!MINE)
+                                f2 = fmaxf(f2, fminf(f1, f));
                             f1 = fmaxf(f1, f);
                         }
                     } else {
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
-                            const float f = 32 * hh + j < valid
-                                                ? fmaf(__uint_as_float(r[j]), 256.0f, -(float)(32 * hh + j))
+                            const int c = 32 * hh + j;
+                            const float f = c < valid && !(own && c == dcol)
+                                                ? fmaf(__uint_as_float(r[j]), 256.0f, -(float)c)
                                                 : -INFINITY;
-                            f2 = fmaxf(f2, fminf(f1, f));
+                            if (!MINE)
+                                f2 = fmaxf(f2, fminf(f1, f));
                             f1 = fmaxf(f1, f);
                         }
                     }
                 }
 #pragma unroll
-                for (int bb = 0; bb < 2; ++bb) {
+                for (int bb = 0; bb < (MINE ? 1 : 2); ++bb) {
                     const float f = bb ? f2 : f1;
                     if (f == -INFINITY)
                         continue;
@@ -409,7 +422,7 @@ size_t match_tc_scratch_bytes(int nq, int nt, int nbits, int sm_count)
 cudaError_t launch_match_tc_keys(bd_ctx *ctx, const uint32_t *q, int nq, const uint32_t *t, int nt,
                                  int nbits, int ratio_num, int ratio_den, bd_match_result *out,
                                  uint2 *raw_keys, void *scratch, cudaStream_t st,
-                                 unsigned int *arrivals)
+                                 unsigned int *arrivals, int mine)
 {
     const int sm_count = ctx->sm_count;
     const int G = tc_grid(nq, nt, nbits, sm_count);
@@ -431,7 +444,8 @@ cudaError_t launch_match_tc_keys(bd_ctx *ctx, const uint32_t *q, int nq, const u
                            128, 128))
         return cudaErrorInvalidValue;
     const size_t smem = (size_t)(BM + 2 * BN) * nbits + 1024;
-    auto kern = nbits == 256 ? match_tc_kernel<256, 2> : match_tc_kernel<512, 1>;
+    auto kern = mine ? (nbits == 256 ? match_tc_kernel<256, 2, true> : match_tc_kernel<512, 1, true>)
+                     : (nbits == 256 ? match_tc_kernel<256, 2, false> : match_tc_kernel<512, 1, false>);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
@@ -449,7 +463,7 @@ cudaError_t launch_match_tc(bd_ctx *ctx, const uint32_t *q, int nq, const uint32
                             void *scratch, cudaStream_t st, unsigned int *arrivals)
 {
     return launch_match_tc_keys(ctx, q, nq, t, nt, nbits, ratio_num, ratio_den, out, nullptr,
-                                scratch, st, arrivals);
+                                scratch, st, arrivals, 0);
 }
 
 }  // namespace bd

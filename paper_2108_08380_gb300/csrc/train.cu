@@ -12,7 +12,8 @@
 //   - mining on hard codes: for anchor i the negative j != i with the smallest
 //     min(Hamming(a_i,n_j), Hamming(p_i,n_j)) (= the largest similarity
 //     K - 2 Hamming, Sec. III-A), lowest j on ties, from two exact
-//     tensor-core top-2 searches (match_tc.cu); anchor swap keeps p_i when it
+//     tensor-core nearest-neighbour searches that leave column i out
+//     (match_tc.cu, a maximum per score); anchor swap keeps p_i when it
 //     is closer to that negative than a_i;
 //   - the hinge loss of each descriptor.
 //  backward (mining held fixed)
@@ -133,9 +134,11 @@ __global__ void __launch_bounds__(128) train_bad_fwd_kernel(const float *__restr
     }
 }
 
-// Mining from the two top-2 searches (anchors vs negatives, positives vs
-// negatives, keys = distance << 22 | index): the first key of each pair whose
-// index is not i (any index when n == 1), then the smaller of the two keys.
+// Mining from the two searches (anchors vs negatives, positives vs
+// negatives, keys = distance << 22 | index; the searches already leave
+// column i out when n > 1, so .x is the nearest j != i and the .y fallback
+// keeps the rule for a top-2 input): the first key of each pair whose index
+// is not i (any index when n == 1), then the smaller of the two keys.
 // Smaller key = smaller min(Hamming(a_i,n_j), Hamming(p_i,n_j)), lowest j on
 // ties, i.e. the largest similarity K - 2 Hamming (Sec. III-A).
 __global__ void train_mine_combine_kernel(const uint2 *__restrict__ keys_a,
@@ -592,10 +595,10 @@ bd_status bd_train_forward(bd_ctx *ctx, bd_train *tr, const float *patches, cons
             const int nw = K / 32;
             const uint32_t *neg = bits + (size_t)2 * n * nw;
             e = launch_match_tc_keys(ctx, bits, n, neg, n, K, 1, 1, nullptr, tr->keys, tr->tc_scratch,
-                                     st, tr->arrivals);
+                                     st, tr->arrivals, 1);
             if (e == cudaSuccess)
                 e = launch_match_tc_keys(ctx, bits + (size_t)n * nw, n, neg, n, K, 1, 1, nullptr,
-                                         tr->keys + n, tr->tc_scratch, st, tr->arrivals);
+                                         tr->keys + n, tr->tc_scratch, st, tr->arrivals, 1);
             if (e == cudaSuccess) {
                 train_mine_combine_kernel<<<(n + 255) / 256, 256, 0, st>>>(
                     tr->keys, tr->keys + n, n, bits, nw, tr->mining + (size_t)(2 * d) * n,
