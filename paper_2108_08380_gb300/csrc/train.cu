@@ -379,98 +379,127 @@ __global__ void __launch_bounds__(128, 8) train_hs_bwd_kernel(const float *__res
                                                            float inv_t,
                                                            float *__restrict__ dpatches)
 {
+    // R patches per pass: dh = W dm for all R at once (each W load feeds R
+    // independent chains, each in the k order of one patch), then the pixel
+    // adjoint patch by patch
+    constexpr int R = 4;
     __shared__ float P[32][33];
     __shared__ float gxs[32][33], gys[32][33];
-    __shared__ float dm[K];
-    __shared__ float dH[128];
-    __shared__ float red[4];
+    __shared__ float dm[R][K];
+    __shared__ float dH[R][128];
+    __shared__ float red[R][4];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const dev::HistLane L = dev::hist_lane(t);
-    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    for (int row0 = blockIdx.x * R; row0 < rows; row0 += gridDim.x * R) {
+        const int nr = min(R, rows - row0);
         __syncthreads();
-        for (int k = t; k < K; k += 128) {
-            const float rv = r[(size_t)row * K + k];
-            dm[k] = dr[(size_t)row * K + k] * (1.f - rv * rv) * inv_t;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int e = t + q * 128;
-            P[e >> 5][e & 31] = __ldg(patches + (size_t)row * 1024 + e);
+        for (int e = t; e < R * K; e += 128) {
+            const int rr = e / K, k = e % K;
+            float v = 0.f;
+            if (rr < nr) {
+                const float rv = r[(size_t)(row0 + rr) * K + k];
+                v = dr[(size_t)(row0 + rr) * K + k] * (1.f - rv * rv) * inv_t;
+            }
+            dm[rr][k] = v;
         }
         __syncthreads();
         // dh_t = sum_k W[t][k] dm[k]
-        float dh = 0.f;
+        float dh[R];
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr)
+            dh[rr] = 0.f;
 #pragma unroll 8
-        for (int k = 0; k < K; ++k)
-            dh = fmaf(__ldg(Wt + (size_t)k * 128 + t), dm[k], dh);
-        const float ht = h[(size_t)row * 128 + t];
-        float hd = ht * dh;
+        for (int k = 0; k < K; ++k) {
+            const float w = __ldg(Wt + (size_t)k * 128 + t);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            hd += __shfl_xor_sync(FULL, hd, o);
-        if (lane == 0)
-            red[warp] = hd;
-        __syncthreads();
-        hd = red[0] + red[1] + red[2] + red[3];
-        const float nrm = norm[row];
-        dH[t] = nrm > 0.f ? (dh - ht * hd) / nrm : 0.f;
-        __syncthreads();
-        // per-pixel adjoint of the votes: thread t owns one pixel row of one cell
-        const int i = L.i;
-        const int iu = max(i - 1, 0), id = min(i + 1, 31);
-        const int cell = t >> 3;
+            for (int rr = 0; rr < R; ++rr)
+                dh[rr] = fmaf(w, dm[rr][k], dh[rr]);
+        }
+        float ht[R];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int j = L.j0 + q;
-            const int jl = max(j - 1, 0), jr = min(j + 1, 31);
-            const float gx = 0.5f * (P[i][jr] - P[i][jl]);
-            const float gy = 0.5f * (P[id][j] - P[iu][j]);
-            const float m2 = gx * gx + gy * gy;
-            float dgx = 0.f, dgy = 0.f;
-            if (m2 > 0.f && nrm > 0.f) {
-                // 1/|g| and 1/|g|^2 from one reciprocal square root; the bin
-                // pair from the forward's orient_bin, exact at multiples of 45
-                // degrees (frequent on flat-sided patches), where the
-                // histogram's derivative jumps
-                const float im = rsqrtf(m2);
-                const float m = m2 * im;
-                float w1;
-                int b0 = dev::orient_bin(gx, gy, w1);
-                // on a bin edge the derivative in the angle is one-sided: take
-                // the floor side (the bin that starts at the edge, w1 = 0), as
-                // the exact definition floor(q) does; the votes are the same
-                if (w1 >= 1.0f) {
-                    b0 = (b0 + 1) & 7;
-                    w1 = 0.0f;
-                }
-                const int b1 = (b0 + 1) & 7;
-                const float d0 = dH[cell * 8 + b0], d1 = dH[cell * 8 + b1];
-                const float g = L.g[q];
-                const float dmag = g * ((1.f - w1) * d0 + w1 * d1);
-                const float dphi = g * m * (d1 - d0) * 1.27323954473516268615f;
-                const float im2 = im * im;
-                dgx = dmag * gx * im - dphi * gy * im2;
-                dgy = dmag * gy * im + dphi * gx * im2;
-            }
-            gxs[i][j] = dgx;
-            gys[i][j] = dgy;
+        for (int rr = 0; rr < R; ++rr) {
+            ht[rr] = rr < nr ? h[(size_t)(row0 + rr) * 128 + t] : 0.f;
+            float hd = ht[rr] * dh[rr];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                hd += __shfl_xor_sync(FULL, hd, o);
+            if (lane == 0)
+                red[rr][warp] = hd;
         }
         __syncthreads();
-        // gather: gx(i,c) reads columns jr(c) (+) and jl(c) (-); gy likewise for rows
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int e = t + q * 128;
-            const int y = e >> 5, x = e & 31;
-            float v = 0.f;
-            if (x >= 1) v += gxs[y][x - 1];      // jr(x-1) = x
-            if (x == 31) v += gxs[y][31];        // jr(31) = 31
-            if (x <= 30) v -= gxs[y][x + 1];     // jl(x+1) = x
-            if (x == 0) v -= gxs[y][0];          // jl(0) = 0
-            if (y >= 1) v += gys[y - 1][x];
-            if (y == 31) v += gys[31][x];
-            if (y <= 30) v -= gys[y + 1][x];
-            if (y == 0) v -= gys[0][x];
-            dpatches[(size_t)row * 1024 + e] += 0.5f * v;
+        for (int rr = 0; rr < R; ++rr) {
+            const float hd = red[rr][0] + red[rr][1] + red[rr][2] + red[rr][3];
+            const float nrm = rr < nr ? norm[row0 + rr] : 0.f;
+            dH[rr][t] = nrm > 0.f ? (dh[rr] - ht[rr] * hd) / nrm : 0.f;
+        }
+        for (int rr = 0; rr < nr; ++rr) {
+            const int row = row0 + rr;
+            const float nrm = norm[row];
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = t + q * 128;
+                P[e >> 5][e & 31] = __ldg(patches + (size_t)row * 1024 + e);
+            }
+            __syncthreads();
+            // per-pixel adjoint of the votes: thread t owns one pixel row of one cell
+            const int i = L.i;
+            const int iu = max(i - 1, 0), id = min(i + 1, 31);
+            const int cell = t >> 3;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int j = L.j0 + q;
+                const int jl = max(j - 1, 0), jr = min(j + 1, 31);
+                const float gx = 0.5f * (P[i][jr] - P[i][jl]);
+                const float gy = 0.5f * (P[id][j] - P[iu][j]);
+                const float m2 = gx * gx + gy * gy;
+                float dgx = 0.f, dgy = 0.f;
+                if (m2 > 0.f && nrm > 0.f) {
+                    // 1/|g| and 1/|g|^2 from one reciprocal square root; the bin
+                    // pair from the forward's orient_bin, exact at multiples of 45
+                    // degrees (frequent on flat-sided patches), where the
+                    // histogram's derivative jumps
+                    const float im = rsqrtf(m2);
+                    const float m = m2 * im;
+                    float w1;
+                    int b0 = dev::orient_bin(gx, gy, w1);
+                    // on a bin edge the derivative in the angle is one-sided: take
+                    // the floor side (the bin that starts at the edge, w1 = 0), as
+                    // the exact definition floor(q) does; the votes are the same
+                    if (w1 >= 1.0f) {
+                        b0 = (b0 + 1) & 7;
+                        w1 = 0.0f;
+                    }
+                    const int b1 = (b0 + 1) & 7;
+                    const float d0 = dH[rr][cell * 8 + b0], d1 = dH[rr][cell * 8 + b1];
+                    const float g = L.g[q];
+                    const float dmag = g * ((1.f - w1) * d0 + w1 * d1);
+                    const float dphi = g * m * (d1 - d0) * 1.27323954473516268615f;
+                    const float im2 = im * im;
+                    dgx = dmag * gx * im - dphi * gy * im2;
+                    dgy = dmag * gy * im + dphi * gx * im2;
+                }
+                gxs[i][j] = dgx;
+                gys[i][j] = dgy;
+            }
+            __syncthreads();
+            // gather: gx(i,c) reads columns jr(c) (+) and jl(c) (-); gy likewise for rows
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = t + q * 128;
+                const int y = e >> 5, x = e & 31;
+                float v = 0.f;
+                if (x >= 1) v += gxs[y][x - 1];      // jr(x-1) = x
+                if (x == 31) v += gxs[y][31];        // jr(31) = 31
+                if (x <= 30) v -= gxs[y][x + 1];     // jl(x+1) = x
+                if (x == 0) v -= gxs[y][0];          // jl(0) = 0
+                if (y >= 1) v += gys[y - 1][x];
+                if (y == 31) v += gys[31][x];
+                if (y <= 30) v -= gys[y + 1][x];
+                if (y == 0) v -= gys[0][x];
+                dpatches[(size_t)row * 1024 + e] += 0.5f * v;
+            }
         }
     }
 }
