@@ -139,7 +139,7 @@ size_t bd_scratch_bytes_match(int nq, int nt, int nbits);
  *               of pair k in the 32x32 patch frame (values 0..31; the frame
  *               centre is (16,16)).
  *  sides        host, nbits uint8 box sides s (1..64); both boxes of a pair
- *               share s (Sec. III-A: "two boxes of size s").
+ *               share s (Sec. III-A: the two boxes of a pair have one size).
  *  thr_num      host, nbits int32; threshold theta_k = thr_num[k] / thr_den.
  *  thr_den      > 0 (1 for integer thresholds; 10 for the 0.1 grid of
  *               Sec. III-A, Alg. 2 discussion).
