@@ -992,16 +992,16 @@ KERNEL_SOURCES = {
     "select_threshold": ["select.cu", "bd_internal.h"],
 }
 NCU_TRAFFIC = {
-    "plain": {"describe_batch/batch_persistent": (1078272 + 3072, "297a7d942276500a")},
-    "large": {"describe_batch/batch_persistent": (38291712 + 48051200, "297a7d942276500a"),
-              "describe_batch/hs_proj_tc": (21689088 + 0, "99dda6785d778d92"),
-              "match_bad/match_tc": (10305792, "19c99d565cca98ce"),
-              "match_hashsift/match_tc": (20525824, "19c99d565cca98ce")},
-    "select": {"select/select_keys": (201392896 + 341874432, "d4480b53895862cd"),
-               "select/select_threshold": (394236160 + 3337472, "d4480b53895862cd")},
-    "train": {"match_tc": (33595904 + 0, "19c99d565cca98ce")},
-    "batch": {"describe_batch/batch_persistent": (332435712 + 313150208, "297a7d942276500a"),
-              "describe_batch/hs_proj_tc": (106152192 + 4944384, "99dda6785d778d92")},
+    "plain": {"describe_batch/batch_persistent": (1078272 + 3072, "1e65b635717b279b")},
+    "large": {"describe_batch/batch_persistent": (38291712 + 48051200, "1e65b635717b279b"),
+              "describe_batch/hs_proj_tc": (21689088 + 0, "6ee5b7dad2877b74"),
+              "match_bad/match_tc": (10280192, "0f3d0d8dddfa999b"),
+              "match_hashsift/match_tc": (20524288, "0f3d0d8dddfa999b")},
+    "select": {"select/select_keys": (201392896 + 341874432, "ebc7d88f9fe5476e"),
+               "select/select_threshold": (394236160 + 3337472, "ebc7d88f9fe5476e")},
+    "train": {"match_tc": (33593600 + 0, "0f3d0d8dddfa999b")},
+    "batch": {"describe_batch/batch_persistent": (332435712 + 313150208, "1e65b635717b279b"),
+              "describe_batch/hs_proj_tc": (106152192 + 4944384, "6ee5b7dad2877b74")},
 }
 
 
