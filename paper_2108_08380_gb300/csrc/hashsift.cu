@@ -124,18 +124,40 @@ __global__ void __launch_bounds__(256) hs_proj_fp32_kernel(const float *__restri
 #pragma unroll
         for (int b = 0; b < 8; ++b)
             acc[a][b] = 0.0f;
+    // this thread's share of a 32-deep K chunk (8 histogram and 16 W values),
+    // loaded into registers one chunk ahead so that the loads of chunk k + 1
+    // are in flight during chunk k's FMAs
+    constexpr int HQ = PBM * PBK / 256, WQ = PBK * PBN / 256;
+    float hq[HQ], wq[WQ];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < HQ; ++q) {
+            const int e = t + 256 * q;
+            const int row = m0 + e / PBK;
+            hq[q] = row < n ? __ldg(hist + (size_t)row * kHistDim + k0 + e % PBK) : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < WQ; ++q) {
+            const int e = t + 256 * q;
+            wq[q] = __ldg(W + (size_t)(k0 + e / PBN) * K + n0 + e % PBN);
+        }
+    };
+    load(0);
     for (int k0 = 0; k0 < kHistDim; k0 += PBK) {
         __syncthreads();
-        for (int e = t; e < PBM * PBK; e += 256) {
-            const int r = e / PBK, c = e % PBK;
-            const int row = m0 + r;
-            Hs[c][r] = row < n ? __ldg(hist + (size_t)row * kHistDim + k0 + c) : 0.0f;
+#pragma unroll
+        for (int q = 0; q < HQ; ++q) {
+            const int e = t + 256 * q;
+            Hs[e % PBK][e / PBK] = hq[q];
         }
-        for (int e = t; e < PBK * PBN; e += 256) {
-            const int r = e / PBN, c = e % PBN;
-            Ws[r][c] = __ldg(W + (size_t)(k0 + r) * K + n0 + c);
+#pragma unroll
+        for (int q = 0; q < WQ; ++q) {
+            const int e = t + 256 * q;
+            Ws[e / PBN][e % PBN] = wq[q];
         }
         __syncthreads();
+        if (k0 + PBK < kHistDim)
+            load(k0 + PBK);
         float part[4][8];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
