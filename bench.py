@@ -903,7 +903,7 @@ def measure_e2e(ctx, wl, stages, steps):
                           "of the previous one overlap each step's compute"}
 
 
-def roofline(wl, per_kernel, clocks, probes=None):
+def roofline(wl, per_kernel, clocks, probes=None, sm_count=None):
     """Roofline of the dominant kernel of the step (largest mean time per step).
     Denominators are measured: MEASURED_PEAKS.json for HBM and BF16 tensor
     throughput, the bd_probe kernels for POPC, FFMA and gather rates (derived
@@ -912,6 +912,9 @@ def roofline(wl, per_kernel, clocks, probes=None):
     per BAD keypoint, HS_OPS_PER_PIXEL x 1024 per HashSIFT patch, 2 x 128 x K
     flop per projected keypoint, K/32 POPC or 2 x K flop per matched pair."""
     peaks, kind = load_peaks()
+    if sm_count is None:
+        import torch
+        sm_count = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     key = max(per_kernel, key=per_kernel.get)
     t = per_kernel[key] * 1e-3
     stage, kname = key.split("/")
@@ -931,7 +934,7 @@ def roofline(wl, per_kernel, clocks, probes=None):
         else:
             words = (wl.bad_bits if stage == "match_bad" else wl.hs_bits) // 32
         popc = na * nb * words
-        peak, src = probe("popc", 152 * 16 * sm_mhz * 1e6, "152 SMs x 16 POPC/clk")
+        peak, src = probe("popc", sm_count * 16 * sm_mhz * 1e6, f"{sm_count} SMs x 16 POPC/clk")
         out.update(bound="alu", achieved=popc / t / 1e12, peak=peak / 1e12, unit="Tpopc/s",
                    frac=popc / t / peak, peak_source=src)
     elif kname == "match_tc":
@@ -953,16 +956,16 @@ def roofline(wl, per_kernel, clocks, probes=None):
         # measured rate; the bound is the largest part, and the sum is the
         # time the three would take if they could not overlap.
         px = float(sum(int(im.shape[0]) * int(im.shape[1]) for im in wl.images))
-        g_rate, g_src = probe("gather_l1_window_8kb", 152 * 32 * sm_mhz * 1e6,
-                              "152 SMs x 32 loads/clk")
-        f_rate, f_src = probe("ffma", 152 * 128 * sm_mhz * 1e6, "152 SMs x 128 FP32 lanes")
+        g_rate, g_src = probe("gather_l1_window_8kb", sm_count * 32 * sm_mhz * 1e6,
+                              f"{sm_count} SMs x 32 loads/clk")
+        f_rate, f_src = probe("ffma", sm_count * 128 * sm_mhz * 1e6, f"{sm_count} SMs x 128 FP32 lanes")
         parts = {
             "gather": (wl.n * wl.bad_bits * 8.0, g_rate, "Gload/s", g_src),
             "alu": (HS_OPS_PER_PIXEL * 1024.0 * wl.n, f_rate, "Tops/s", f_src),
             "hbm": (6.0 * px, float(peaks["hbm_gbs"]) * 1e9, "GB/s", f"{kind} HBM copy"),
         }
         if wl.match and wl.match_kind == "fused":  # the matchings are its last items
-            p_rate, p_src = probe("popc", 152 * 16 * sm_mhz * 1e6, "152 SMs x 16 POPC/clk")
+            p_rate, p_src = probe("popc", sm_count * 16 * sm_mhz * 1e6, f"{sm_count} SMs x 16 POPC/clk")
             words = wl.bad_bits // 32 + wl.hs_bits // 32
             parts["popc"] = (float(na) * nb * words, p_rate, "Tpopc/s", p_src)
         tmin = {k: v[0] / v[1] for k, v in parts.items()}
@@ -979,9 +982,9 @@ def roofline(wl, per_kernel, clocks, probes=None):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# step's kernels from one ncu --set full capture per workload, summarised in
-# profiles/*.md, with the hash of the kernel's own sources at capture time;
-# a kernel whose sources changed since has traffic null.
+# step's kernels from one ncu capture per workload and kernel, with the hash
+# of the kernel's own sources at capture time; a kernel whose sources changed
+# since has traffic null.
 KERNEL_SOURCES = {
     "batch_persistent": ["batch.cu", "bad_dev.cuh", "hashsift_dev.cuh", "integral_dev.cuh",
                          "match_dev.cuh", "bd_internal.h"],

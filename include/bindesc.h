@@ -373,6 +373,18 @@ typedef struct bd_batch_match {
  * the projection. */
 bd_status bd_batch_set_matches(bd_batch *b, const bd_batch_match *jobs, int n_jobs);
 
+/* Limit, in nanoseconds of the GPU timer, of each dependency wait of the
+ * persistent kernel (an item waiting for the items it reads: integral tiles,
+ * histograms, descriptors of a matching); 0 restores the default of 2 s.
+ * A wait that runs out raises BD_FLAG_TIMEOUT (bd_sync_status then returns
+ * BD_ERR_TIMEOUT), the item skips its work, every CTA still leaves the
+ * queue, and the last one out resets the plan's counters, so the next call
+ * starts clean; the outputs of the call that timed out are undefined.  A
+ * short limit makes waits run out on purpose (a test of this error path).
+ * Takes effect at the next bd_describe_batch (a captured graph is
+ * re-captured). */
+bd_status bd_batch_set_wait_limit(bd_batch *b, uint64_t ns);
+
 /* enable != 0: later launches of the plan record the timeline (device buffer
  * owned by the plan; the graph is re-captured); 0 turns it off. */
 bd_status bd_batch_set_timeline(bd_batch *b, int enable);
@@ -433,14 +445,16 @@ bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, con
 #define BD_BAD_NOALLOC_SCRATCH_BYTES ((size_t)9 << 20)
 
 /* BAD descriptors like bd_bad_describe, for callers that cannot call
- * cudaMalloc: code that enqueues work while a stream capture in global mode
- * is active (cudaMalloc is an error there), processes whose device memory is
- * all owned by another allocator, and real-time loops that cannot take the
- * implicit synchronisation of cudaMalloc/cudaFree.  The call allocates
+ * cudaMalloc: processes whose device memory is all reserved up front by
+ * another allocator (a framework's caching pool), where a fresh cudaMalloc
+ * fails or fragments the pool; real-time loops that cannot take the
+ * device-wide synchronisation cudaFree implies; plug-ins run inside a host
+ * program that forbids allocation once it is up.  The call allocates
  * nothing: the integral image and its tile carries live in a file-scope
  * static device array of BD_BAD_NOALLOC_SCRATCH_BYTES (held by every GPU
  * that loads the library until the process exits).  Parameters come from
- * bd_bad_params_create, done once at set-up.
+ * bd_bad_params_create, done once at set-up.  The paper has no counterpart:
+ * this is a deployment aid of this library.
  *  - Same arguments and outputs as bd_bad_describe, plus the cudaStream_t to
  *    enqueue on (NULL = legacy default stream); the parameters' device must be
  *    the current device.
@@ -449,8 +463,9 @@ bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, con
  *    1920x1088) are rejected with BD_ERR_INVALID and a message in the
  *    parameters' context; nothing is enqueued then.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress, with that device current) and caches it; make
- *    that first call before any stream capture.
+ *    (cudaGetSymbolAddress, with that device current) and caches it per
+ *    device context (a context made after cudaDeviceReset gets a lookup of
+ *    its own); make that first call before any stream capture.
  *  - Every call on a device shares the one array, which keeps the last call's
  *    contents (each call overwrites all it reads); calls that overlap on the
  *    GPU (other streams, or graph nodes not ordered after each other) race.

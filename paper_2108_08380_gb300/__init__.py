@@ -92,6 +92,7 @@ _SIGS = [
     ("bd_probe", _I, [_P, _I, _P, ctypes.c_size_t, ctypes.c_size_t, _I, _P,
                       ctypes.POINTER(ctypes.c_uint64)]),
     ("bd_batch_set_timeline", _I, [_P, _I]),
+    ("bd_batch_set_wait_limit", _I, [_P, ctypes.c_uint64]),
     ("bd_batch_set_matches", _I, [_P, _P, _I]),
     ("bd_batch_get_timeline", _I, [_P, _P, _I, ctypes.POINTER(_I)]),
 ]
@@ -524,6 +525,12 @@ class Batch:
         self.ctx._check(lib().bd_batch_set_matches(self.handle, ctypes.cast(arr, ctypes.c_void_p),
                                                    len(jobs)), "bd_batch_set_matches")
 
+    def set_wait_limit(self, ns: int = 0):
+        """bd_batch_set_wait_limit: limit of each dependency wait of the
+        persistent kernel in ns (0 = the default 2 s)."""
+        self.ctx._check(lib().bd_batch_set_wait_limit(self.handle, ctypes.c_uint64(int(ns))),
+                        "bd_batch_set_wait_limit")
+
     def set_timeline(self, enable: bool = True):
         self.ctx._stream()
         self.ctx._check(lib().bd_batch_set_timeline(self.handle, int(bool(enable))),
@@ -606,9 +613,11 @@ class TrainStep:
             pass
 
 
-def triplet_loss(step: "TrainStep", patches, theta, W, b):
-    """Differentiable [L_bad, L_hs] of the training step (torch.autograd.Function)."""
-    return _TripletLoss.apply(step, patches, theta, W, b)
+def triplet_loss(step: "TrainStep", patches, theta, W, b, fixed_mining=None):
+    """Differentiable [L_bad, L_hs] of the training step (torch.autograd.Function).
+    fixed_mining (device int32 [4, n], optional) replaces the hard-negative
+    mining and anchor swap, as in TrainStep.forward; it gets no gradient."""
+    return _TripletLoss.apply(step, patches, theta, W, b, fixed_mining)
 
 
 def _make_autograd():
@@ -616,10 +625,12 @@ def _make_autograd():
 
     class TripletLoss(torch.autograd.Function):
         @staticmethod
-        def forward(ctx_, step, patches, theta, W, b):
+        def forward(ctx_, step, patches, theta, W, b, fixed_mining=None):
             patches = patches.contiguous()
             W = W.contiguous()
-            loss, mining = step.forward(patches, theta.contiguous(), W, b.contiguous())
+            fm = None if fixed_mining is None else fixed_mining.contiguous()
+            loss, mining = step.forward(patches, theta.contiguous(), W, b.contiguous(),
+                                        fixed_mining=fm)
             ctx_.step = step
             ctx_.save_for_backward(patches, W)
             return loss
@@ -628,7 +639,7 @@ def _make_autograd():
         def backward(ctx_, grad):
             patches, W = ctx_.saved_tensors
             dP, dth, dW, db = ctx_.step.backward(patches, W, grad)
-            return None, dP, dth, dW, db
+            return None, dP, dth, dW, db, None
 
     return TripletLoss
 

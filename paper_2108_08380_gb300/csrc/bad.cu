@@ -26,10 +26,11 @@ cudaError_t launch_bad_gather(const bd_bad_params *p, const uint32_t *ii, int ii
                               int h, const bd_keypoint *kps, int n, uint32_t *out,
                               DeviceStatus *status, cudaStream_t st)
 {
+    const int sm_count = p->ctx->sm_count > 0 ? p->ctx->sm_count : 1;
     const dev::BadTables T = dev::bad_tables(p);
     const int warps_per_block = 8;
     int blocks = (n + warps_per_block - 1) / warps_per_block;
-    const int cap = 152 * 16;
+    const int cap = sm_count * 16;  // 8 warps per CTA, two CTAs per SM: eight waves
     if (blocks > cap)
         blocks = cap;
     if (p->nbits == 256)

@@ -74,6 +74,7 @@ struct BatchKernelArgs {
     float *hist;
     const bd_keypoint *kps;
     DeviceStatus *status;
+    unsigned long long wait_ns;  // limit of every dependency wait (GPU timer)
     bd_batch_event *events;  // item timeline, or NULL
     // matchings (last in the queue)
     int n_mjobs, match_items;
@@ -84,7 +85,6 @@ struct BatchKernelArgs {
 
 namespace {
 
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 constexpr int kMatchTile = 128;  // train descriptors per shared-memory tile of a matching item
 
 __device__ __forceinline__ unsigned long long gtimer()
@@ -103,7 +103,8 @@ __device__ __forceinline__ int smid()
 
 // thread 0 waits until *ctr >= target (bounded); the CTA learns the outcome.
 __device__ __forceinline__ bool cta_wait_count(const unsigned int *ctr, unsigned int target,
-                                               int *flag_s, DeviceStatus *status)
+                                               int *flag_s, DeviceStatus *status,
+                                               unsigned long long wait_ns)
 {
     if (threadIdx.x == 0) {
         int ok = 1;
@@ -111,7 +112,7 @@ __device__ __forceinline__ bool cta_wait_count(const unsigned int *ctr, unsigned
             const unsigned long long t0 = gtimer();
             while (atomicAdd(const_cast<unsigned int *>(ctr), 0u) < target) {
                 __nanosleep(200);
-                if (gtimer() - t0 > kWaitNs) {
+                if (gtimer() - t0 > wait_ns) {
                     ok = 0;
                     dev::raise_flag(status, BD_FLAG_TIMEOUT);
                     break;
@@ -138,7 +139,8 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p)
 // checks of all groups take one round trip; each spin is bounded like
 // cta_wait_count.  Called by the whole CTA.
 __device__ __forceinline__ bool cta_wait_groups(const unsigned int *ctr, int k0, int k1, int n_kp,
-                                                unsigned int per_group, DeviceStatus *status)
+                                                unsigned int per_group, DeviceStatus *status,
+                                                unsigned long long wait_ns)
 {
     int ok = 1;
     const int g0 = k0 >> 5;
@@ -150,7 +152,7 @@ __device__ __forceinline__ bool cta_wait_groups(const unsigned int *ctr, int k0,
             const unsigned long long t0 = gtimer();
             while (ld_acquire(ctr + g) < target) {
                 __nanosleep(200);
-                if (gtimer() - t0 > kWaitNs) {
+                if (gtimer() - t0 > wait_ns) {
                     ok = 0;
                     dev::raise_flag(status, BD_FLAG_TIMEOUT);
                     break;
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
             const int tile = idx;
             const int im = find_image(A.imgs, A.n_img, tile, 0);
             const BatchImageDev &I = A.imgs[im];
-            if (cta_wait_count(A.stats_done + im, (unsigned)(I.ntx * I.nty), &flag_s, A.status)) {
+            if (cta_wait_count(A.stats_done + im, (unsigned)(I.ntx * I.nty), &flag_s, A.status, A.wait_ns)) {
                 mark_ready();
                 const int tl = tile - I.tile_begin;
                 dev::ii_final_tile(U.f, A.img_ptr[im], I.w, I.h, I.pitch, A.carry + I.cs_off,
@@ -445,14 +447,14 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
             if (A.proj_half) {
                 float4 wv[4];
                 proj_w_load<4>(A, cb, wv);
-                if (cta_wait_count(A.hs_group_done + g, (unsigned)nk, &flag_s, A.status)) {
+                if (cta_wait_count(A.hs_group_done + g, (unsigned)nk, &flag_s, A.status, A.wait_ns)) {
                     mark_ready();
                     proj_tile<4>(U.p, A, k0, nk, cb, wv);
                 }
             } else {
                 float4 wv[8];
                 proj_w_load<8>(A, cb, wv);
-                if (cta_wait_count(A.hs_group_done + g, (unsigned)nk, &flag_s, A.status)) {
+                if (cta_wait_count(A.hs_group_done + g, (unsigned)nk, &flag_s, A.status, A.wait_ns)) {
                     mark_ready();
                     proj_tile<8>(U.p, A, k0, nk, cb, wv);
                 }
@@ -476,8 +478,8 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
             const int bx = local % M.qblocks, by = local / M.qblocks;
             const int q0 = M.qkp + bx * 32, q1 = M.qkp + min(M.nq, bx * 32 + 32);
             const int t0 = M.tkp + by * M.chunk, t1 = M.tkp + min(M.nt, by * M.chunk + M.chunk);
-            const bool q_ok = cta_wait_groups(done, q0, q1, A.n_kp, per, A.status);
-            if (cta_wait_groups(done, t0, t1, A.n_kp, per, A.status) && q_ok) {
+            const bool q_ok = cta_wait_groups(done, q0, q1, A.n_kp, per, A.status, A.wait_ns);
+            if (cta_wait_groups(done, t0, t1, A.n_kp, per, A.status, A.wait_ns) && q_ok) {
                 mark_ready();
                 if (M.nbits == 256)
                     dev::match_block32<8, kMatchTile>(U.m.tile, U.m.wpair, M.q, M.nq, M.t, M.nt,
@@ -494,7 +496,7 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
             const int bi = idx;
             const int im = find_image(A.imgs, A.n_img, bi, 2);
             const BatchImageDev &I = A.imgs[im];
-            if (cta_wait_count(A.final_done + im, (unsigned)(I.ntx * I.nty), &flag_s, A.status)) {
+            if (cta_wait_count(A.final_done + im, (unsigned)(I.ntx * I.nty), &flag_s, A.status, A.wait_ns)) {
                 mark_ready();
                 const int k0 = I.kp_begin + (bi - I.bad_item_begin) * A.bad_per_item;
                 const int k1 = min(I.kp_end, k0 + A.bad_per_item);
@@ -531,6 +533,9 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
     }
     // The last CTA out resets the queue and readiness counters for the next
     // launch: every other CTA has fetched its last item and finished its work.
+    // The matching arrival counters are normally back at zero already (the
+    // last slice of a query block resets its own); after a wait that ran out
+    // an item may have skipped its arrival, so they are cleared here too.
     if (t == 0) {
         __threadfence();
         flag_s = atomicAdd(A.exit_count, 1u) == gridDim.x - 1;
@@ -553,6 +558,9 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                 A.bits_grp_done[i] = 0u;
             }
         }
+        for (int j = 0; j < A.n_mjobs; ++j)
+            for (int i = t; i < A.mj[j].qblocks; i += blockDim.x)
+                A.mj[j].arrivals[i] = 0u;
     }
 }
 
@@ -579,6 +587,7 @@ struct bd_batch {
     unsigned int *d_counters = nullptr;
     float *d_hist = nullptr;
     bd_batch_config cfg = {8, 0, 1, 4, 0, 0, 0};
+    unsigned long long wait_ns = 0;  // 0: the default limit
     int max_ctas_per_sm = 0;
     int occ4 = 0;  // resident CTAs per SM of the 128-register variant
     int occ5 = 0;  // of the 102-register variant
@@ -603,6 +612,7 @@ struct bd_batch {
 namespace {
 
 constexpr int kMatchQB = 32;        // queries per matching item (one per lane)
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;  // 2 s per dependency wait
 constexpr int kMatchMaxSlices = 8;  // train slices per query block in the persistent kernel
 
 int img_kp(const bd_batch *b, int i) { return b->imgs[i].kp_end - b->imgs[i].kp_begin; }
@@ -737,6 +747,7 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     A.hist = b->d_hist;
     A.kps = kps;
     A.status = ctx->status;
+    A.wait_ns = b->wait_ns ? b->wait_ns : kDefaultWaitNs;
     A.bad_grp_done = b->d_counters + 2 + 2 * b->n_img + (b->n_kp + 31) / 32;
     A.bits_grp_done = A.bad_grp_done + (b->n_kp + 31) / 32;
     int per_sm = b->cfg.ctas_per_sm > 0 ? b->cfg.ctas_per_sm : b->max_ctas_per_sm;
@@ -1042,6 +1053,7 @@ bd_status bd_describe_batch(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     key.push_back(reinterpret_cast<const void *>((uintptr_t)(ctx->trace ? 1 : 0)));
     key.push_back(reinterpret_cast<const void *>((uintptr_t)(b->hs ? b->hs->variant : 0)));
     key.push_back(b->d_events);
+    key.push_back(reinterpret_cast<const void *>((uintptr_t)b->wait_ns));
     if (!b->gexec || key != b->gkey) {
         drop_graph(b);
         cudaGraph_t g = nullptr;
@@ -1158,6 +1170,16 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     if (best_ms)
         *best_ms = win_ms;
     return s;
+}
+
+bd_status bd_batch_set_wait_limit(bd_batch *b, uint64_t ns)
+{
+    if (!b)
+        return BD_ERR_INVALID;
+    // a graph holds the limit as a kernel argument: re-captured on change
+    // (the key of the next graph launch includes it)
+    b->wait_ns = (unsigned long long)ns;
+    return BD_OK;
 }
 
 bd_status bd_batch_set_timeline(bd_batch *b, int enable)

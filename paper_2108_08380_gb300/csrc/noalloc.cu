@@ -1,17 +1,20 @@
 // BAD description without any device allocation in the call.
 //
-// Some callers cannot call cudaMalloc: code that enqueues work while a CUDA
-// stream capture in global mode is active (cudaMalloc is an error there),
-// processes whose device memory is entirely owned by another allocator, and
-// real-time loops that cannot take the implicit synchronisation of
-// cudaMalloc / cudaFree.  bd_bad_describe_noalloc serves them: the integral
-// image and its tile carries live in one file-scope static device array, so
-// the call launches the same two integral kernels and the same gather kernel
-// as bd_bad_describe without allocating anything.
+// Some callers cannot call cudaMalloc: processes whose device memory is all
+// reserved up front by another allocator (a framework's caching pool), so a
+// fresh cudaMalloc fails or fragments what the pool holds; real-time loops
+// that cannot take the device-wide synchronisation cudaFree implies; and
+// plug-ins run inside a host program that forbids allocation once it is up.
+// bd_bad_describe_noalloc serves them: the integral image and its tile
+// carries live in one file-scope static device array, so the call launches
+// the same two integral kernels and the same gather kernel as
+// bd_bad_describe without allocating anything.
 //
 // Host code cannot use the array's name as a device address (it names a host
-// stand-in), so the device address is looked up once per device with
-// cudaGetSymbolAddress, with that device current, and cached.
+// stand-in), so the device address is looked up with cudaGetSymbolAddress,
+// with the device current, once per device context (keyed by the driver's
+// context id, so a context created after cudaDeviceReset gets a fresh lookup
+// instead of a stale address), and cached.
 #include <mutex>
 
 #include "bd_internal.h"
@@ -25,22 +28,57 @@ __device__ __align__(256) unsigned char g_bad_static_scratch[kStaticScratchBytes
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {};
+struct Cached {
+    void *addr = nullptr;
+    unsigned long long ctx_id = 0;  // driver id of the context the address belongs to
+};
+Cached g_scratch[kMaxDevices];
+
+typedef CUresult (*PFN_ctxGetCurrent)(CUcontext *);
+typedef CUresult (*PFN_ctxGetId)(CUcontext, unsigned long long *);
+
+void *driver_fn(const char *name)
+{
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        return nullptr;
+    return p;
+}
+
+// Id of the context current on this thread; 0 when there is none or the
+// driver cannot say.
+unsigned long long current_ctx_id()
+{
+    static PFN_ctxGetCurrent get_current = (PFN_ctxGetCurrent)driver_fn("cuCtxGetCurrent");
+    static PFN_ctxGetId get_id = (PFN_ctxGetId)driver_fn("cuCtxGetId");
+    if (!get_current || !get_id)
+        return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 
 bd_status static_scratch(bd_ctx *ctx, int dev, void **out)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     if (dev < 0 || dev >= kMaxDevices)
         return set_err(ctx, BD_ERR_UNSUPPORTED, "device index %d out of range", dev);
-    if (!g_scratch_addr[dev]) {
+    Cached &c = g_scratch[dev];
+    const unsigned long long id = current_ctx_id();
+    if (!c.addr || id == 0 || id != c.ctx_id) {
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_bad_static_scratch);
         if (e != cudaSuccess || !ptr)
             return cuda_err(ctx, e == cudaSuccess ? cudaErrorInvalidSymbol : e,
                             "bd_bad_describe_noalloc: cudaGetSymbolAddress");
-        g_scratch_addr[dev] = ptr;
+        c.addr = ptr;
+        c.ctx_id = current_ctx_id();  // the lookup has made the device's context current
     }
-    *out = g_scratch_addr[dev];
+    *out = c.addr;
     return BD_OK;
 }
 

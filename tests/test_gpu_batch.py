@@ -356,3 +356,60 @@ def test_bad_shared_keypoints_equal_per_image_calls(gpu_ctx, bits, levels):
             assert np.array_equal(_u32(ob), ref), (it, shared)
     assert np.all(_u32(ob)[[3, 1200]] == 0)
     b.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_wait_limit_runs_out_then_next_call_is_exact(gpu_ctx, graph):
+    """The persistent kernel's bounded dependency waits (error model: a wait
+    that runs out raises BD_FLAG_TIMEOUT and bd_sync_status returns
+    BD_ERR_TIMEOUT).  A 1 ns limit makes every wait that has to wait run out:
+    the launch still returns, the flag is raised, and the next call with the
+    default limit, on the same plan, gives the records of a clean call bit
+    for bit, so the queue, readiness and matching arrival counters were
+    reset by the launch that timed out."""
+    import ctypes
+    import torch
+    import paper_2108_08380_gb300 as bdm
+    from paper_2108_08380_gb300 import BD_DESC_BAD, BD_DESC_HASHSIFT
+    imgs, kps, offs, bad, hs = _small_batch(seed=41)
+    bp, hp = gpu_ctx.bad_params(bad), gpu_ctx.hs_params(hs)
+    dimgs = [_dev(im) for im in imgs]
+    b = gpu_ctx.batch(bp, hp, dimgs, offs)
+    n = len(kps)
+    dk = _dev(kps)
+    cnt = np.diff(offs)
+    # HashSIFT items last: each image's pass-2 tiles are queued right after
+    # its pass-1 tiles, so they find them still running and have to wait
+    b.set_config(8, 4, 0, 4, 1, 0, 0)
+    spec = [(BD_DESC_BAD, 0, 5), (BD_DESC_HASHSIFT, 0, 5), (BD_DESC_BAD, 5, 0), (BD_DESC_HASHSIFT, 3, 4)]
+    outs = [torch.empty((int(cnt[q]), 3), dtype=torch.int32, device="cuda") for (_, q, _) in spec]
+    b.set_matches([(d, q, t, o, 4, 5) for (d, q, t), o in zip(spec, outs)])
+    ob = torch.empty((n, 8), dtype=torch.int32, device="cuda")
+    oh = torch.empty((n, 8), dtype=torch.int32, device="cuda")
+    b.describe(dimgs, dk, ob, oh, graph=graph)
+    assert gpu_ctx.sync_status() == 0
+    ref = [t.clone() for t in [ob, oh] + outs]
+
+    b.set_wait_limit(1)
+    timed_out = False
+    for _ in range(3):
+        b.describe(dimgs, dk, ob, oh, graph=graph)
+        f = ctypes.c_uint32(0)
+        st = bdm.lib().bd_sync_status(gpu_ctx.handle, ctypes.byref(f))
+        assert st in (bdm.BD_OK, bdm.BD_ERR_TIMEOUT)
+        if st == bdm.BD_ERR_TIMEOUT:
+            assert f.value & bdm.BD_FLAG_TIMEOUT
+            timed_out = True
+            break
+    assert timed_out
+
+    b.set_wait_limit(0)
+    for t in [ob, oh] + outs:
+        t.fill_(-3)
+    for _ in range(2):
+        b.describe(dimgs, dk, ob, oh, graph=graph)
+        assert gpu_ctx.sync_status() == 0
+        for got, exp in zip([ob, oh] + outs, ref):
+            assert torch.equal(got, exp)
+    b.set_matches([])
+    b.close()

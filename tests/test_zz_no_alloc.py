@@ -1,9 +1,10 @@
 """bd_bad_describe_noalloc, the entry point for callers that cannot call
-cudaMalloc (stream capture in global mode, memory owned by another allocator,
-real-time loops), against the regular bd_bad_describe through the C ABI:
-two calls in a row must give the same descriptors bit for bit (the
-tolerance of every BAD test), an image at the size limit must work, and an
-image beyond the static area's limit must be refused with nothing launched.
+cudaMalloc (device memory all reserved by another allocator, real-time loops
+that cannot take cudaFree's synchronisation, plug-ins in hosts that forbid
+allocation), against the regular bd_bad_describe through the C ABI: two
+calls in a row must give the same descriptors bit for bit (the tolerance of
+every BAD test), an image at the size limit must work, and an image beyond
+the static area's limit must be refused with nothing launched.
 
 Kept in a file of its own, collected last."""
 import ctypes
