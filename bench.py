@@ -109,6 +109,31 @@ class Workload:
                 self.match_kind = "tensor" if na * (self.n - na) >= (1 << 24) else "fused"
         else:
             self.pairs_per_step = 0
+        self._sectors = None
+
+    def l1_sectors(self) -> float:
+        """Distinct L1 sectors of every keypoint's BAD corner reads in one step
+        (bad_l1_sectors per image; the 64-image batch counts a seeded sample
+        of 250 keypoints per image and scales it)."""
+        if self._sectors is None:
+            tot = 0.0
+            for i, im in enumerate(self.images):
+                lo, hi = int(self.offsets[i]), int(self.offsets[i + 1])
+                if hi > lo:
+                    h, w = im.shape
+                    sct, _ = bad_l1_sectors(self.bp, self.wl.bad.level_scales, self.kps[lo:hi], w, h,
+                                            sample=250 if self.name == "batch" else None, seed=i)
+                    tot += sct
+            self._sectors = tot
+        return self._sectors
+
+    def projection_path(self) -> str:
+        """The HashSIFT projection the launch configuration runs."""
+        if self.tuned and self.tuned.get("proj_fused"):
+            bits = 16 if self.tuned.get("proj_half") else 32
+            return (f"FP32 CUDA-core projection tiles ({bits} bits x 32 keypoints) inside the "
+                    "persistent kernel (proj_fused = 1), the FP32 path's summation order")
+        return "tcgen05 BF16 head/tail split with FP32 re-check of the band (hs_proj_tc)"
 
     # ---- GPU -----------------------------------------------------------
     def to_device(self, ctx, autotune=True, config=None):
@@ -458,6 +483,94 @@ def cpu_baseline(wl, budget_s: float):
             "matches_per_s": npairs / dt}
 
 
+def oracle_parity(ctx, wl, sample: int):
+    """Part of the CPU-baseline leg: the step's own outputs on the first
+    `sample` keypoints of each image against the oracle (BAD words equal;
+    HashSIFT bits equal wherever the oracle's margin clears the error the
+    histograms can cause), and the end-to-end histogram error from the image
+    (the per-image describe call, same warp and histogram routines as the
+    batched kernel) against the oracle's FP64 histograms."""
+    import torch
+    import oracle
+    bad = wl.bad.cpu().numpy().view(np.uint32)
+    hsb = wl.hs.cpu().numpy().view(np.uint32)
+    Wn = np.linalg.norm(np.asarray(wl.wl.hs.W, np.float64), axis=0)
+    bad_bad = hs_bad = hs_checked = hs_band = 0
+    herr = 0.0
+    nkp = 0
+    for i, im in enumerate(wl.images):
+        lo, hi = int(wl.offsets[i]), int(wl.offsets[i + 1])
+        hi = min(hi, lo + sample)
+        if hi <= lo:
+            continue
+        k = wl.kps[lo:hi]
+        d, _ = oracle.bad_describe(im, k, wl.wl.bad)
+        bad_bad += int((d != bad[lo:hi]).sum())
+        ref = oracle.hs_describe(im, k, wl.wl.hs)
+        hist = torch.empty((hi - lo, 128), dtype=torch.float32, device="cuda")
+        ctx.hashsift_describe(wl.hp, wl.dimg[i], wl.dkps[lo:hi], hist_out=hist)
+        h = hist.cpu().numpy().astype(np.float64)
+        e = np.abs(h - ref["hist"]).max(axis=1)
+        herr = max(herr, float(e.max()))
+        tol = (math.sqrt(128) * e[:, None] + 2.0 ** -20) * Wn[None, :] + 1e-6
+        if wl.band > 0:
+            tol = np.maximum(tol, wl.band)
+        sure = np.abs(ref["margins"]) >= tol
+        got = np.unpackbits(hsb[lo:hi].view(np.uint8), axis=1, bitorder="little")[:, :wl.hs_bits]
+        hs_bad += int((got.astype(bool)[sure] != (ref["margins"] > 0)[sure]).sum())
+        hs_checked += int(sure.sum())
+        hs_band += int((~sure).sum())
+        nkp += hi - lo
+        if wl.name == "batch" and i >= 3:
+            break
+    return {"keypoints": nkp, "bad_word_mismatches": bad_bad,
+            "hashsift_bits_checked": hs_checked, "hashsift_bit_mismatches": hs_bad,
+            "hashsift_bits_in_error_band": hs_band,
+            "hashsift_hist_e2e_max_abs_err": herr,
+            "note": "end-to-end histogram error from the image (FP32 warp positions included); "
+                    "the histogram of the same FP32 patch is held to 1e-5 in the GPU tests"}
+
+
+def run_other_workloads(args):
+    """The other configurations as compact records, each from a child
+    `bench.py --workload X` run (a fresh process and context, a few steps):
+    the 4K pair with its component rates, the 64-image batch, the training
+    step and the feature-selection round."""
+    steps = max(3, min(args.steps, 20))
+    warm = 3
+    out = {}
+    for name, extra in (("large", []), ("batch", ["--no-components"]), ("train", []),
+                        ("select", [])):
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", name, "--steps",
+               str(steps), "--warmup", str(warm), "--cpu-budget", "3", "--no-workloads", *extra]
+        t0 = time.time()
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=600,
+                               env=dict(os.environ, WORLD_SIZE="1", RANK="0", LOCAL_RANK="0"))
+            rec = None
+            for ln in reversed(r.stdout.splitlines()):
+                try:
+                    rec = json.loads(ln)
+                    break
+                except ValueError:
+                    continue
+            if r.returncode != 0 or rec is None:
+                out[name] = {"error": f"rc={r.returncode}", "stderr_tail": r.stderr[-800:]}
+                continue
+        except subprocess.TimeoutExpired:
+            out[name] = {"error": "timed out after 600 s"}
+            continue
+        for k in ("probes", "item_timeline", "kernel_ms_source", "stage_ms"):
+            rec.pop(k, None)
+        comp = rec.get("components")
+        if comp:
+            comp.pop("hs_variants", None)
+        rec["command"] = " ".join(["python", "bench.py"] + cmd[2:])
+        rec["wall_s"] = round(time.time() - t0, 1)
+        out[name] = rec
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_2108_08380_gb300 as bd
@@ -574,12 +687,20 @@ def run_ours(args):
     per_kernel = {k: float(np.mean([d.get(k, 0.0) for d in kernel_ms])) for k in keys}
     roof = roofline(wl, per_kernel, clocks, probes)
     value = world * wl.descriptors_per_step / (ms * 1e-3)
+    fused_proj = bool(wl.tuned and wl.tuned.get("proj_fused"))
+    label = "FP32 projection fused into the persistent kernel" if fused_proj else \
+        "tcgen05 BF16 + FP32 rescue projection"
+    config = dict(wl.config, workload=wl.config["workload"].replace("(BF16+rescue)", f"({label})"),
+                  hashsift_projection=wl.projection_path())
     line = {
         "metric": METRIC, "value": value, "unit": "descriptors/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8/int32 (BAD, matching), f32 + bf16 tensor (HashSIFT)",
+        "vs_baseline": None,
+        "dtype": ("u8/int32 (BAD, matching), f32 (HashSIFT histogram and projection)" if fused_proj
+                  else "u8/int32 (BAD, matching), f32 histogram + bf16 tensor projection with f32 "
+                       "re-check (HashSIFT)"),
         "data": "synthetic",
-        "config": dict(wl.config, l2="flushed between steps (512 MB write)",
+        "config": dict(config, l2="flushed between steps (512 MB write)",
                        matching={"tensor": "tensor cores (FP8 +-1, tcgen05), one call per "
                                            "descriptor type",
                                  "popc": "POPC, both descriptor types in one bd_match_batch launch",
@@ -606,6 +727,9 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_budget)
+        line["parity_sample"] = oracle_parity(ctx, wl, 200)
+    if world == 1 and not args.no_workloads:
+        line["workloads"] = run_other_workloads(args)
     print(json.dumps(line), flush=True)
     torch.cuda.synchronize()
     ctx.close()  # plans and parameter sets first, then the context: not left to exit order
@@ -635,10 +759,59 @@ def _kernel_ms(ctx, fn, reps):
     return acc
 
 
+def bad_l1_sectors(bp, level_scales, kps, w, h, sample=None, seed=0):
+    """Distinct 32-byte sectors of an image's integral table (uint32, row
+    stride w + 1, 256-byte aligned) that the 8 K corner reads of each
+    keypoint touch: the least data L1 has to hand to the warps describing
+    it, whatever the order of its reads.  The keypoint's pixel, pyramid level
+    and angle bin follow the kernels' rules (IEEE single precision); boxes
+    come from the library's own offset table.  sample: count that many
+    seeded keypoints and scale to all of them.  Returns (sectors, 128-byte
+    lines) summed over the keypoints."""
+    off, sides = bp.table()                       # [L][NB][K][2][2], [L][K]
+    L, NB, K = off.shape[0], off.shape[1], off.shape[2]
+    kps = np.asarray(kps, np.float32)
+    n = kps.shape[0]
+    idx = np.arange(n)
+    if sample is not None and sample < n:
+        idx = np.sort(np.random.default_rng(seed).choice(n, size=sample, replace=False))
+    k = kps[idx]
+    ix = np.floor(k[:, 0] + np.float32(0.5)).astype(np.int64)
+    iy = np.floor(k[:, 1] + np.float32(0.5)).astype(np.int64)
+    ls = np.asarray(level_scales, np.float64)
+    mids = np.float32(np.sqrt(ls[:-1] * ls[1:]))
+    lev = (mids[None, :] < k[:, 2:3]).sum(axis=1) if L > 1 else np.zeros(len(k), np.int64)
+    ascale = np.float32(NB / (2.0 * np.pi))
+    b = np.floor((k[:, 3] * ascale) + np.float32(0.5)).astype(np.int64) % NB
+    stride = w + 1
+    tot_s = tot_l = 0
+    for c0 in range(0, len(k), 2048):
+        sl = slice(c0, c0 + 2048)
+        o = off[lev[sl], b[sl]]                    # [m][K][2][2] centre offsets
+        s_ = sides[lev[sl]][:, :, None]            # [m][K][1]
+        x0 = ix[sl, None, None] + o[..., 0] - s_ // 2
+        y0 = iy[sl, None, None] + o[..., 1] - s_ // 2
+        xa, xb = np.clip(x0, 0, w), np.clip(x0 + s_, 0, w)
+        ya, yb = np.clip(y0, 0, h), np.clip(y0 + s_, 0, h)
+        words = np.concatenate([(ya * stride + xa).reshape(len(o), -1), (ya * stride + xb).reshape(len(o), -1),
+                                (yb * stride + xa).reshape(len(o), -1), (yb * stride + xb).reshape(len(o), -1)],
+                               axis=1)
+        for shift in (3, 5):                       # 32-byte sectors, 128-byte lines
+            q = np.sort(words >> shift, axis=1)
+            d = 1 + (np.diff(q, axis=1) != 0).sum(axis=1)
+            if shift == 3:
+                tot_s += int(d.sum())
+            else:
+                tot_l += int(d.sum())
+    scale = n / len(k)
+    return tot_s * scale, tot_l * scale
+
+
 def measure_probes(ctx):
     """Measured rates of the paths the descriptor kernels lean on (units/s):
     random 4-byte gathers from L2 (32 MB table) and within BAD-sized 8 KB
-    windows (L1 hits), POPC, FFMA and MUFU instructions."""
+    windows (L1 hits), 32-byte sectors handed out by L1 (coalesced 16-byte
+    lanes, the bound of the BAD gathers), POPC, FFMA and MUFU instructions."""
     import torch
     import paper_2108_08380_gb300 as bd
     ctx.trace(True)
@@ -646,6 +819,7 @@ def measure_probes(ctx):
     cases = {
         "gather_l2": (bd.BD_PROBE_GATHER, 16, table, 1 << 23),
         "gather_l1_window_8kb": (bd.BD_PROBE_GATHER, 64, table, 1 << 11),
+        "l1_sectors": (bd.BD_PROBE_L1_SECTORS, 512, table, 0),
         "popc": (bd.BD_PROBE_POPC, 256, None, 0),
         "ffma": (bd.BD_PROBE_FFMA, 1024, None, 0),
         "mufu_ex2": (bd.BD_PROBE_MUFU, 256, None, 0),
@@ -685,11 +859,16 @@ def measure_components(ctx, wl, probes):
     k = _kernel_ms(ctx, lambda: ctx.bad_describe(wl.bp, img, kps, out=out), reps)
     t = k.get("bad_gather", float("nan")) * 1e-3
     loads = na * wl.bad_bits * 8
+    sectors, lines = bad_l1_sectors(wl.bp, wl.wl.bad.level_scales, wl.kps[:na], w, h)
     res["bad_gather"] = {
         "ms": t * 1e3, "gathers_per_s": loads / t,
+        "l1_sectors_per_kp": sectors / na, "l1_lines_per_kp": lines / na,
+        "l1_sectors_per_s": sectors / t,
+        "frac_of_l1_sectors": sectors / t / probes["l1_sectors"]["per_s"],
         "frac_of_l2_gather": loads / t / probes["gather_l2"]["per_s"],
         "frac_of_l1_window_gather": loads / t / probes["gather_l1_window_8kb"]["per_s"],
-        "work": f"{na} kps x {wl.bad_bits} bits x 8 lookups"}
+        "work": f"{na} kps x {wl.bad_bits} bits x 8 lookups; bound: the distinct 32-byte "
+                "sectors of the keypoints' corner reads at the L1 sector rate"}
     ii_ms = sum(v for kk, v in k.items() if kk.startswith("ii_"))
     res["integral"] = {"ms": ii_ms, "bytes": 6 * w * h,
                        "gbs": 6 * w * h / (ii_ms * 1e-3) / 1e9,
@@ -908,9 +1087,10 @@ def roofline(wl, per_kernel, clocks, probes=None, sm_count=None):
     Denominators are measured: MEASURED_PEAKS.json for HBM and BF16 tensor
     throughput, the bd_probe kernels for POPC, FFMA and gather rates (derived
     from unit counts and the sampled clock only when the probes were skipped).
-    Algorithmic work per unit: 6 B per pixel (integral image), 8 x K lookups
-    per BAD keypoint, HS_OPS_PER_PIXEL x 1024 per HashSIFT patch, 2 x 128 x K
-    flop per projected keypoint, K/32 POPC or 2 x K flop per matched pair."""
+    Algorithmic work per unit: 6 B per pixel (integral image), the distinct
+    32-byte L1 sectors of a BAD keypoint's 8 x K corner reads (bad_l1_sectors),
+    HS_OPS_PER_PIXEL x 1024 per HashSIFT patch, 2 x 128 x K flop per projected
+    keypoint, K/32 POPC or 2 x K flop per matched pair."""
     peaks, kind = load_peaks()
     if sm_count is None:
         import torch
@@ -956,11 +1136,11 @@ def roofline(wl, per_kernel, clocks, probes=None, sm_count=None):
         # measured rate; the bound is the largest part, and the sum is the
         # time the three would take if they could not overlap.
         px = float(sum(int(im.shape[0]) * int(im.shape[1]) for im in wl.images))
-        g_rate, g_src = probe("gather_l1_window_8kb", sm_count * 32 * sm_mhz * 1e6,
-                              f"{sm_count} SMs x 32 loads/clk")
+        g_rate, g_src = probe("l1_sectors", sm_count * 4 * sm_mhz * 1e6,
+                              f"{sm_count} SMs x 4 sectors/clk")
         f_rate, f_src = probe("ffma", sm_count * 128 * sm_mhz * 1e6, f"{sm_count} SMs x 128 FP32 lanes")
         parts = {
-            "gather": (wl.n * wl.bad_bits * 8.0, g_rate, "Gload/s", g_src),
+            "l1": (wl.l1_sectors(), g_rate, "Gsector/s", g_src),
             "alu": (HS_OPS_PER_PIXEL * 1024.0 * wl.n, f_rate, "Tops/s", f_src),
             "hbm": (6.0 * px, float(peaks["hbm_gbs"]) * 1e9, "GB/s", f"{kind} HBM copy"),
         }
@@ -971,7 +1151,7 @@ def roofline(wl, per_kernel, clocks, probes=None, sm_count=None):
         tmin = {k: v[0] / v[1] for k, v in parts.items()}
         bound = max(tmin, key=tmin.get)
         work, rate, unit, src = parts[bound]
-        scale = 1e9 if unit in ("Gload/s", "GB/s") else 1e12  # Tops/s, Tpopc/s
+        scale = 1e9 if unit in ("Gsector/s", "GB/s") else 1e12  # Tops/s, Tpopc/s
         out.update(bound=bound, achieved=work / t / scale, peak=rate / scale, unit=unit,
                    frac=work / t / rate, peak_source=src,
                    parts_min_ms={k: v * 1e3 for k, v in tmin.items()},
@@ -1158,9 +1338,25 @@ def run_train(args):
     if not args.no_cpu_baseline and rank == 0:
         import oracle
         sample = 64
+        Ps = np.ascontiguousarray(tw.patches[:, :sample])
         t0 = time.perf_counter()
-        oracle.train_step(tw.patches[:, :sample], bad, theta.cpu().numpy(), hs)
+        ref = oracle.train_step(Ps, bad, theta.cpu().numpy(), hs)
         dt = time.perf_counter() - t0
+        # the GPU step on the same sample with the oracle's mining: gradient
+        # error norm-relative to the FP64 oracle (the bound the tests hold)
+        small = bd.TrainStep(ctx, step.bad, 256, sample, temperature=0.1)
+        dPs = torch.from_numpy(Ps).cuda()
+        fm = torch.from_numpy(np.ascontiguousarray(ref["mining"])).cuda()
+        ls_, _ = small.forward(dPs, theta, W, b, fixed_mining=fm)
+        gP, gth, gW, gb = small.backward(dPs, W, g)
+        rel = lambda a, r: float(np.linalg.norm(a.cpu().numpy().astype(np.float64) - r)
+                                 / max(np.linalg.norm(r), 1e-30))
+        line["grad_rel_err_vs_oracle"] = {
+            "triplets": sample, "loss": rel(ls_, ref["loss"]), "dtheta": rel(gth, ref["dtheta"]),
+            "dW": rel(gW, ref["dW"]), "db": rel(gb, ref["db"]), "dpatches": rel(gP, ref["dpatches"]),
+            "note": "the 65536-triplet step is held to 1e-4 against the oracle in the GPU tests; "
+                    "the oracle's gradient is pinned to central finite differences in the CPU tests"}
+        small.close()
         line["cpu_baseline"] = {"value": sample / n / dt, "unit": "steps/s", "cores": 1,
                                 "kind": "oracle", "host": host_cpu(),
                                 "sample": f"forward + backward over {sample} of the {n} triplets "
@@ -1300,6 +1496,8 @@ def main():
                     default="plain")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="the default (plain) run skips the records of the other workloads")
     ap.add_argument("--no-components", action="store_true",
                     help="skip the per-stage component measurements")
     ap.add_argument("--batch-config", default=None,

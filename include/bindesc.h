@@ -573,7 +573,8 @@ typedef enum {
     BD_PROBE_GATHER = 0, /* random 4-byte loads, read-only path (BAD stump access) */
     BD_PROBE_POPC = 1,   /* 32-bit population counts (Hamming matching) */
     BD_PROBE_FFMA = 2,   /* FP32 fused multiply-adds (histogram arithmetic) */
-    BD_PROBE_MUFU = 3    /* ex2 on the special-function unit */
+    BD_PROBE_MUFU = 3,   /* ex2 on the special-function unit */
+    BD_PROBE_L1_SECTORS = 4 /* 32-byte sectors handed out by L1 (BAD gather bound) */
 } bd_probe_kind;
 
 /* Enqueues one probe kernel on the context's stream, sized to fill every SM
@@ -586,6 +587,11 @@ typedef enum {
  *    words; per window every lane loads 64 random words of it, independent
  *    of each other.  window_words = table_words measures L2 random gathers
  *    once the table is larger than L1; a window of a few KB measures L1 hits.
+ *  - BD_PROBE_L1_SECTORS: table (device, 16-byte aligned, table_words a
+ *    power of two >= 4096) holds one 16 KB window per CTA; every lane loads
+ *    16 consecutive bytes per request (512 contiguous bytes per warp), reps
+ *    x 8 requests per warp; window_words is ignored.  *units = 32-byte
+ *    sectors delivered (16 per request).
  *  - The other kinds ignore table and window_words; each thread runs
  *    reps x 64 instructions of the kind in eight independent chains.
  *  - sink: one device uint32 that the results are added to (keeps the work

@@ -37,6 +37,7 @@ BD_PROBE_GATHER = 0
 BD_PROBE_POPC = 1
 BD_PROBE_FFMA = 2
 BD_PROBE_MUFU = 3
+BD_PROBE_L1_SECTORS = 4
 
 _STATUS_NAMES = {0: "BD_OK", 1: "BD_ERR_INVALID", 2: "BD_ERR_CUDA", 3: "BD_ERR_NOMEM",
                  4: "BD_ERR_TIMEOUT", 5: "BD_ERR_DEVICE_CHECK", 6: "BD_ERR_UNSUPPORTED"}

@@ -9,6 +9,12 @@
 //          describing one BAD-256 keypoint.  A window as large as the table
 //          gives the L2 random-gather rate; a BAD-sized window (a few KB)
 //          gives the L1-hit gather rate.
+//  l1      the L1 data path's sector rate: every lane of a warp loads 16
+//          consecutive bytes (a request = 512 contiguous bytes = 16 sectors
+//          of 32 B) from a 16 KB window per CTA that stays in L1.  The
+//          largest rate at which L1 can hand sectors to the SM's warps; the
+//          BAD gathers' bound (the distinct sectors a keypoint's corner
+//          reads touch, divided by this rate, is the least time they take).
 //  popc    32-bit population counts (matching, S = K - 2 Hamming).
 //  ffma    FP32 fused multiply-adds (histogram arithmetic).
 //  mufu    ex2 on the special-function unit (exp / rsqrt of the histogram).
@@ -67,6 +73,32 @@ __global__ void __launch_bounds__(kProbeThreads) probe_gather_kernel(
             for (int u = 0; u < 16; ++u)
                 acc += v[u];
         }
+    }
+    fold(acc, sink);
+}
+
+constexpr int kL1WindowVec = 1024;  // 16 KB window per CTA, in 16-byte vectors
+constexpr int kL1Unroll = 8;        // requests in flight per warp
+
+__global__ void __launch_bounds__(kProbeThreads) probe_l1_kernel(const uint4 *__restrict__ table,
+                                                                 uint32_t vecs_mask, int reps,
+                                                                 uint32_t *sink)
+{
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t base = (mix32(blockIdx.x * 0x9e3779b9u + 7u) & vecs_mask) & ~(uint32_t)(kL1WindowVec - 1);
+    const uint4 *win = table + base;
+    uint32_t off = warp * 32 * kL1Unroll;  // a multiple of 32 vectors: 512-byte aligned requests
+    uint32_t acc = 0;
+#pragma unroll 1
+    for (int r = 0; r < reps; ++r) {
+        uint4 v[kL1Unroll];
+#pragma unroll
+        for (int u = 0; u < kL1Unroll; ++u)
+            v[u] = __ldg(win + ((off + 32 * u + lane) & (kL1WindowVec - 1)));
+#pragma unroll
+        for (int u = 0; u < kL1Unroll; ++u)
+            acc += v[u].x ^ v[u].y ^ v[u].z ^ v[u].w;
+        off += 32 * (kL1Unroll + 1);
     }
     fold(acc, sink);
 }
@@ -186,6 +218,19 @@ cudaError_t launch_probe(int kind, const uint32_t *table, size_t table_words, si
         *units = (unsigned long long)blocks * kProbeThreads * reps * kLoadsPerWindow;
         label = "probe_gather";
         break;
+    case BD_PROBE_L1_SECTORS:
+        if (!table || !pow2(table_words) || table_words < 4 * (size_t)kL1WindowVec ||
+            table_words > ((size_t)1 << 31) || (reinterpret_cast<uintptr_t>(table) & 15)) {
+            *bad_args = true;
+            return cudaSuccess;
+        }
+        blocks = sm_count * resident_blocks(probe_l1_kernel);
+        probe_l1_kernel<<<blocks, kProbeThreads, 0, st>>>(
+            reinterpret_cast<const uint4 *>(table), (uint32_t)(table_words / 4 - 1), reps, sink);
+        // sectors: per warp and rep kL1Unroll requests of 512 B = 16 sectors
+        *units = (unsigned long long)blocks * (kProbeThreads / 32) * reps * kL1Unroll * 16;
+        label = "probe_l1";
+        break;
     case BD_PROBE_POPC:
         blocks = sm_count * resident_blocks(probe_popc_kernel);
         probe_popc_kernel<<<blocks, kProbeThreads, 0, st>>>(reps, sink);
@@ -205,7 +250,7 @@ cudaError_t launch_probe(int kind, const uint32_t *table, size_t table_words, si
         *bad_args = true;
         return cudaSuccess;
     }
-    if (kind != BD_PROBE_GATHER)
+    if (kind != BD_PROBE_GATHER && kind != BD_PROBE_L1_SECTORS)
         *units = (unsigned long long)blocks * kProbeThreads * reps * 8 * kChains;
     trace_kernel(st, label);
     note_launches(1);

@@ -17,9 +17,17 @@
 //     is closer to that negative than a_i;
 //   - the hinge loss of each descriptor.
 //  backward (mining held fixed)
-//   - dL/dr from the active hinges (negatives collect with atomics);
+//   - dL/dr from the active hinges; a negative collects one term per triplet
+//     that mined it (hard-negative mining makes hubs: one negative can be the
+//     hardest of ten thousand anchors, its dL/dr a sum of that many terms
+//     near +-1), so negatives collect in FP64 atomics and are rounded to FP32
+//     once, by a pass that also clears the accumulator for the next step;
 //   - BAD: dtheta column sums, and the box adjoint as a 2-D difference array
 //     per patch (4 corner updates per box, then a 2-D prefix sum);
+//   - the column sums over all 3n rows (dtheta, db) cancel heavily (anchors
+//     and positives pull one way, negatives the other), so each thread sums
+//     its rows with compensated (Kahan) FP32 additions and the partial sums
+//     meet in FP64 accumulators, converted to FP32 at the end;
 //   - HashSIFT: dW = H^T dM and db (split over rows), dh = W dM, the
 //     normalisation adjoint and the histogram adjoint per pixel (recomputed
 //     from the patch), gathered into the patch gradient.
@@ -36,7 +44,8 @@ struct bd_train {
     uint32_t *bits_bad = nullptr, *bits_hs = nullptr;
     int32_t *mining = nullptr;  // [4][n]
     float *dr_bad = nullptr, *dr_hs = nullptr, *Wt = nullptr;
-    double *loss_acc = nullptr;
+    double *loss_acc = nullptr;  // [2] losses, then [Kb] dtheta and [Kh] db accumulators
+    double *drn_acc = nullptr;   // [n][Kb] then [n][Kh]: negatives' dL/dr, zero between steps
     void *tc_scratch = nullptr;       // FP8 codes and partials of the top-2 searches
     uint2 *keys = nullptr;            // [2][n] top-2 keys (anchors, positives)
     unsigned int *arrivals = nullptr; // zeroed per-block arrival counters
@@ -164,6 +173,16 @@ __global__ void train_mine_combine_kernel(const uint2 *__restrict__ keys_a,
     xsel[i] = da <= dp ? 0 : 1;  // S(a,n*) >= S(p,n*) keeps the anchor
 }
 
+// Compensated FP32 summation: s + (-c) carries the sum, c the part the last
+// addition lost (Kahan).  No products, so nothing is contracted into an FMA.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
+{
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
 // Warp per triplet: hinge term, loss accumulation and (backward) dL/dr.
 template <int K>
 __global__ void __launch_bounds__(256) train_loss_kernel(const float *__restrict__ r, int n,
@@ -171,7 +190,8 @@ __global__ void __launch_bounds__(256) train_loss_kernel(const float *__restrict
                                                          const int32_t *__restrict__ xsel, float tau,
                                                          const float *__restrict__ gw,
                                                          double *__restrict__ loss_acc,
-                                                         float *__restrict__ dr)
+                                                         float *__restrict__ dr,
+                                                         double *__restrict__ drn)
 {
     constexpr int Q = K / 32;
     const int lane = threadIdx.x & 31;
@@ -210,7 +230,24 @@ __global__ void __launch_bounds__(256) train_loss_kernel(const float *__restrict
         dr[(size_t)i * K + k] = on ? w * (-rp[q] + (xs ? 0.f : rn[q])) : 0.f;
         dr[(size_t)(n + i) * K + k] = on ? w * (-ra[q] + (xs ? rn[q] : 0.f)) : 0.f;
         if (on)
-            atomicAdd(dr + (size_t)nrow * K + k, w * rx);
+            atomicAdd(drn + (size_t)nstar[i] * K + k, (double)(w * rx));
+    }
+}
+
+// Negatives' dL/dr from their FP64 accumulators (BAD rows [0, nb), then
+// HashSIFT rows), which are cleared for the next step.
+__global__ void train_drn_finish_kernel(double *__restrict__ acc, size_t nb, size_t nh,
+                                        float *__restrict__ dr_bad_neg,
+                                        float *__restrict__ dr_hs_neg)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb + nh;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const double v = acc[i];
+        acc[i] = 0.0;
+        if (i < nb)
+            dr_bad_neg[i] = (float)v;
+        else
+            dr_hs_neg[i - nb] = (float)v;
     }
 }
 
@@ -226,14 +263,14 @@ __global__ void __launch_bounds__(128) train_bad_bwd_kernel(int rows, const shor
                                                             const float *__restrict__ r,
                                                             const float *__restrict__ dr,
                                                             float inv_scale,
-                                                            float *__restrict__ dtheta,
+                                                            double *__restrict__ dtheta_acc,
                                                             float *__restrict__ dpatches)
 {
     __shared__ float D[33][33];
-    float dth[K / 128];
+    float dth[K / 128], dthc[K / 128];
 #pragma unroll
     for (int q = 0; q < K / 128; ++q)
-        dth[q] = 0.f;
+        dth[q] = dthc[q] = 0.f;
     const int t = threadIdx.x;
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
         __syncthreads();
@@ -245,7 +282,7 @@ __global__ void __launch_bounds__(128) train_bad_bwd_kernel(int rows, const shor
             const int k = q * 128 + t;
             const float rv = r[(size_t)row * K + k];
             const float dz = dr[(size_t)row * K + k] * (1.f - rv * rv);
-            dth[q] += dz * inv_scale;
+            kahan_add(dth[q], dthc[q], dz * inv_scale);
             if (dz == 0.f)
                 continue;
             const int s = __ldg(side + k);
@@ -290,7 +327,18 @@ __global__ void __launch_bounds__(128) train_bad_bwd_kernel(int rows, const shor
     }
 #pragma unroll
     for (int q = 0; q < K / 128; ++q)
-        atomicAdd(dtheta + q * 128 + t, dth[q]);
+        atomicAdd(dtheta_acc + q * 128 + t, (double)dth[q] - (double)dthc[q]);
+}
+
+// dtheta and db from their FP64 accumulators.
+__global__ void train_grad_finish_kernel(const double *__restrict__ acc, int kb, int kh,
+                                         float *__restrict__ dtheta, float *__restrict__ db)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kb)
+        dtheta[i] = (float)acc[i];
+    else if (i < kb + kh)
+        db[i - kb] = (float)acc[i];
 }
 
 __global__ void transpose_w_kernel(const float *__restrict__ W, int K, float *__restrict__ Wt)
@@ -308,7 +356,7 @@ __global__ void __launch_bounds__(256) train_hs_dw_kernel(int rows, int K, const
                                                           const float *__restrict__ r,
                                                           const float *__restrict__ dr, float inv_t,
                                                           float *__restrict__ dW,
-                                                          float *__restrict__ db)
+                                                          double *__restrict__ db_acc)
 {
     __shared__ float Hs[32][128 + 4];
     __shared__ float Ms[32][64];
@@ -322,7 +370,7 @@ __global__ void __launch_bounds__(256) train_hs_dw_kernel(int rows, int K, const
 #pragma unroll
         for (int b = 0; b < 8; ++b)
             acc[a][b] = 0.f;
-    float dbs = 0.f;
+    float dbs = 0.f, dbc = 0.f;
     for (int base = r0; base < r1; base += 32) {
         __syncthreads();
         for (int e = t; e < 32 * 128; e += 256) {
@@ -356,7 +404,7 @@ __global__ void __launch_bounds__(256) train_hs_dw_kernel(int rows, int K, const
         }
         if (t < 64)
             for (int rr = 0; rr < 32; ++rr)
-                dbs += Ms[rr][t];
+                kahan_add(dbs, dbc, Ms[rr][t]);
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -364,7 +412,7 @@ __global__ void __launch_bounds__(256) train_hs_dw_kernel(int rows, int K, const
         for (int b = 0; b < 8; ++b)
             atomicAdd(dW + (size_t)(tq * 4 + a) * K + k0 + tk * 8 + b, acc[a][b]);
     if (t < 64)
-        atomicAdd(db + k0 + t, dbs);
+        atomicAdd(db_acc + k0 + t, (double)dbs - (double)dbc);
 }
 
 // Patch gradient of the HashSIFT loss (added to dpatches), one patch per CTA
@@ -554,7 +602,9 @@ bd_status bd_train_create(bd_ctx *ctx, const bd_bad_params *bad, int hs_bits, in
     if (e == cudaSuccess) e = cudaMalloc(&tr->dr_bad, sizeof(float) * R * tr->kb);
     if (e == cudaSuccess) e = cudaMalloc(&tr->dr_hs, sizeof(float) * R * tr->kh);
     if (e == cudaSuccess) e = cudaMalloc(&tr->Wt, sizeof(float) * 128 * tr->kh);
-    if (e == cudaSuccess) e = cudaMalloc(&tr->loss_acc, sizeof(double) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&tr->loss_acc, sizeof(double) * (2 + tr->kb + tr->kh));
+    if (e == cudaSuccess) e = cudaMalloc(&tr->drn_acc, sizeof(double) * (size_t)n * (tr->kb + tr->kh));
+    if (e == cudaSuccess) e = cudaMemset(tr->drn_acc, 0, sizeof(double) * (size_t)n * (tr->kb + tr->kh));
     if (prev >= 0 && prev != ctx->device)
         cudaSetDevice(prev);
     if (e != cudaSuccess) {
@@ -577,7 +627,7 @@ void bd_train_destroy(bd_train *tr)
     for (void *p : {(void *)tr->r_bad, (void *)tr->r_hs, (void *)tr->h, (void *)tr->norm,
                     (void *)tr->bits_bad, (void *)tr->bits_hs, (void *)tr->tc_scratch,
                     (void *)tr->keys, (void *)tr->arrivals, (void *)tr->mining, (void *)tr->dr_bad,
-                    (void *)tr->dr_hs, (void *)tr->Wt, (void *)tr->loss_acc})
+                    (void *)tr->dr_hs, (void *)tr->Wt, (void *)tr->loss_acc, (void *)tr->drn_acc})
         if (p)
             cudaFree(p);
     if (prev >= 0 && prev != tr->ctx->device)
@@ -647,9 +697,11 @@ bd_status bd_train_forward(bd_ctx *ctx, bd_train *tr, const float *patches, cons
             const float tau = d == 0 ? tr->tau_bad : tr->tau_hs;
             const int32_t *ns = tr->mining + (size_t)(2 * d) * n, *xs = ns + n;
             if (K == 256)
-                train_loss_kernel<256><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, nullptr, tr->loss_acc + d, nullptr);
+                train_loss_kernel<256><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, nullptr, tr->loss_acc + d,
+                                                               nullptr, nullptr);
             else
-                train_loss_kernel<512><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, nullptr, tr->loss_acc + d, nullptr);
+                train_loss_kernel<512><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, nullptr, tr->loss_acc + d,
+                                                               nullptr, nullptr);
             trace_kernel(st, "train_loss");
         }
         train_loss_finish_kernel<<<1, 32, 0, st>>>(tr->loss_acc, loss);
@@ -683,16 +735,12 @@ bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, con
     const float inv_scale = 1.0f / (255.0f * tr->T), inv_t = 1.0f / tr->T;
     const bd_bad_params *bp = tr->bad;
     cudaError_t e = cudaSuccess;
-    // dL/dr: negatives' rows collect with atomics, so they start at zero
-    e = cudaMemsetAsync(tr->dr_bad + (size_t)2 * n * tr->kb, 0, sizeof(float) * n * tr->kb, st);
+    // dL/dr: negatives' rows collect in drn_acc (zero between steps)
+    double *dth_acc = tr->loss_acc + 2, *db_acc = dth_acc + tr->kb;
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(tr->dr_hs + (size_t)2 * n * tr->kh, 0, sizeof(float) * n * tr->kh, st);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(dtheta, 0, sizeof(float) * tr->kb, st);
+        e = cudaMemsetAsync(dth_acc, 0, sizeof(double) * (tr->kb + tr->kh), st);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(dW, 0, sizeof(float) * 128 * tr->kh, st);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(db, 0, sizeof(float) * tr->kh, st);
     if (e == cudaSuccess) {
         const int blocks = (n * 32 + 255) / 256;
         for (int d = 0; d < 2; ++d) {
@@ -701,25 +749,36 @@ bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, con
             const int K = d == 0 ? tr->kb : tr->kh;
             const float tau = d == 0 ? tr->tau_bad : tr->tau_hs;
             const int32_t *ns = tr->mining + (size_t)(2 * d) * n, *xs = ns + n;
+            double *drn = tr->drn_acc + (d == 0 ? 0 : (size_t)n * tr->kb);
             if (K == 256)
-                train_loss_kernel<256><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, grad_loss + d, nullptr, drp);
+                train_loss_kernel<256><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, grad_loss + d, nullptr,
+                                                               drp, drn);
             else
-                train_loss_kernel<512><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, grad_loss + d, nullptr, drp);
+                train_loss_kernel<512><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, grad_loss + d, nullptr,
+                                                               drp, drn);
             trace_kernel(st, "train_dr");
         }
+        train_drn_finish_kernel<<<sm * 8, 256, 0, st>>>(tr->drn_acc, (size_t)n * tr->kb,
+                                                        (size_t)n * tr->kh,
+                                                        tr->dr_bad + (size_t)2 * n * tr->kb,
+                                                        tr->dr_hs + (size_t)2 * n * tr->kh);
+        trace_kernel(st, "train_drn_finish");
         // BAD: dtheta and the patch gradient (written, not added)
         if (tr->kb == 256)
             train_bad_bwd_kernel<256><<<grid_rows(rows, sm, 12), 128, 0, st>>>(
-                rows, bp->d_patch_box, bp->d_patch_side, tr->r_bad, tr->dr_bad, inv_scale, dtheta, dpatches);
+                rows, bp->d_patch_box, bp->d_patch_side, tr->r_bad, tr->dr_bad, inv_scale, dth_acc, dpatches);
         else
             train_bad_bwd_kernel<512><<<grid_rows(rows, sm, 12), 128, 0, st>>>(
-                rows, bp->d_patch_box, bp->d_patch_side, tr->r_bad, tr->dr_bad, inv_scale, dtheta, dpatches);
+                rows, bp->d_patch_box, bp->d_patch_side, tr->r_bad, tr->dr_bad, inv_scale, dth_acc, dpatches);
         trace_kernel(st, "train_bad_bwd");
         // HashSIFT: dW, db, then the patch gradient (added)
         transpose_w_kernel<<<(128 * tr->kh + 255) / 256, 256, 0, st>>>(W, tr->kh, tr->Wt);
         dim3 g2((rows + DW_ROWS - 1) / DW_ROWS, tr->kh / 64);
-        train_hs_dw_kernel<<<g2, 256, 0, st>>>(rows, tr->kh, tr->h, tr->r_hs, tr->dr_hs, inv_t, dW, db);
+        train_hs_dw_kernel<<<g2, 256, 0, st>>>(rows, tr->kh, tr->h, tr->r_hs, tr->dr_hs, inv_t, dW, db_acc);
         trace_kernel(st, "train_hs_dw");
+        train_grad_finish_kernel<<<(tr->kb + tr->kh + 255) / 256, 256, 0, st>>>(dth_acc, tr->kb, tr->kh,
+                                                                               dtheta, db);
+        trace_kernel(st, "train_grad_finish");
         if (tr->kh == 256)
             train_hs_bwd_kernel<256><<<grid_rows(rows, sm, 8), 128, 0, st>>>(
                 patches, rows, tr->Wt, tr->h, tr->norm, tr->r_hs, tr->dr_hs, inv_t, dpatches);
@@ -729,7 +788,7 @@ bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, con
         trace_kernel(st, "train_hs_bwd");
         e = cudaGetLastError();
     }
-    note_launches(7);
+    note_launches(9);
     (void)R;
     if (prev >= 0 && prev != ctx->device)
         cudaSetDevice(prev);

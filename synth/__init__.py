@@ -305,27 +305,18 @@ def _sample_patches(img: np.ndarray, cx, cy, A) -> np.ndarray:
 def triplet_workload(seed: int = 1003, n: int = 65536, n_images: int = 4,
                      w: int = 640, h: int = 480, chunk: int = 4096) -> "TripletWorkload":
     """Positive = anchor region under rotation U(+-15 deg), scale U[0.9, 1.1],
-    plus N(0, 5) noise; negatives = random patches elsewhere."""
+    plus N(0, 5) noise; negatives = random patches elsewhere.  The random
+    draws are taken chunk by chunk in a fixed order; the patch sampling of
+    each chunk (numpy, which releases the GIL) runs on a thread pool, so the
+    result does not depend on the thread count."""
+    import concurrent.futures as cf
+    import os
     rng = np.random.default_rng(seed)
     imgs = [make_image(w, h, rng) for _ in range(n_images)]
     out = np.empty((3, n, 32, 32), dtype=np.float32)
     eye = np.eye(2)
-    for c0 in range(0, n, chunk):
-        m = min(chunk, n - c0)
-        src = rng.integers(0, n_images, size=m)
-        cx = rng.uniform(40, w - 40, size=m)
-        cy = rng.uniform(40, h - 40, size=m)
-        a = np.radians(rng.uniform(-15, 15, size=m))
-        s = rng.uniform(0.9, 1.1, size=m)
-        A = np.empty((m, 2, 2))
-        A[:, 0, 0] = s * np.cos(a)
-        A[:, 0, 1] = -s * np.sin(a)
-        A[:, 1, 0] = s * np.sin(a)
-        A[:, 1, 1] = s * np.cos(a)
-        noise = rng.normal(0.0, 5.0, size=(m, 32, 32))
-        src2 = rng.integers(0, n_images, size=m)
-        nx = rng.uniform(40, w - 40, size=m)
-        ny = rng.uniform(40, h - 40, size=m)
+
+    def fill(c0, m, src, cx, cy, A, noise, src2, nx, ny):
         I = np.broadcast_to(eye, (m, 2, 2))
         for im in range(n_images):
             sel = np.nonzero(src == im)[0]
@@ -335,6 +326,31 @@ def triplet_workload(seed: int = 1003, n: int = 65536, n_images: int = 4,
             sel2 = np.nonzero(src2 == im)[0]
             if len(sel2):
                 out[2, c0 + sel2] = _sample_patches(imgs[im], nx[sel2], ny[sel2], I[sel2])
+
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        pending = []
+        for c0 in range(0, n, chunk):
+            m = min(chunk, n - c0)
+            src = rng.integers(0, n_images, size=m)
+            cx = rng.uniform(40, w - 40, size=m)
+            cy = rng.uniform(40, h - 40, size=m)
+            a = np.radians(rng.uniform(-15, 15, size=m))
+            s = rng.uniform(0.9, 1.1, size=m)
+            A = np.empty((m, 2, 2))
+            A[:, 0, 0] = s * np.cos(a)
+            A[:, 0, 1] = -s * np.sin(a)
+            A[:, 1, 0] = s * np.sin(a)
+            A[:, 1, 1] = s * np.cos(a)
+            noise = rng.normal(0.0, 5.0, size=(m, 32, 32))
+            src2 = rng.integers(0, n_images, size=m)
+            nx = rng.uniform(40, w - 40, size=m)
+            ny = rng.uniform(40, h - 40, size=m)
+            pending.append(ex.submit(fill, c0, m, src, cx, cy, A, noise, src2, nx, ny))
+            if len(pending) >= 2 * workers:
+                pending.pop(0).result()
+        for f in pending:
+            f.result()
     return TripletWorkload(out)
 
 

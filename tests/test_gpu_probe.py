@@ -21,6 +21,15 @@ def test_probe_kinds_report_units(gpu_ctx):
     u = gpu_ctx.probe(bd.BD_PROBE_GATHER, 1, table, 1 << 16, sink=sink)
     torch.cuda.synchronize()
     assert int(sink.item()) == u  # every load read a one
+    # L1 sector probe: every vector (1, 0, 0, 0) folds to 1; two 16-byte
+    # vectors per 32-byte sector
+    table.zero_()
+    table[::4] = 1
+    sink.zero_()
+    u = gpu_ctx.probe(bd.BD_PROBE_L1_SECTORS, 3, table, sink=sink)
+    torch.cuda.synchronize()
+    assert u > 0 and u % (sms * 8 * 3 * 8 * 16) == 0
+    assert int(sink.item()) == 2 * u
     for kind in (bd.BD_PROBE_POPC, bd.BD_PROBE_FFMA, bd.BD_PROBE_MUFU):
         u = gpu_ctx.probe(kind, 3)
         assert u > 0 and u % (sms * 256 * 3 * 64) == 0
@@ -39,6 +48,8 @@ def test_probe_rejects_bad_geometry(gpu_ctx):
         gpu_ctx.probe(bd.BD_PROBE_GATHER, 1, t2, 1 << 11)     # window larger than the table
     with pytest.raises(bd.BindescError):
         gpu_ctx.probe(bd.BD_PROBE_GATHER, 1, t2, 16)          # window under 32 words
+    with pytest.raises(bd.BindescError):
+        gpu_ctx.probe(bd.BD_PROBE_L1_SECTORS, 1, t2)          # table smaller than a window
     with pytest.raises(bd.BindescError):
         gpu_ctx.probe(bd.BD_PROBE_POPC, 0)                    # no repetitions
     with pytest.raises(bd.BindescError):
