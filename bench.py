@@ -953,7 +953,7 @@ def measure_components(ctx, wl, probes):
     return res
 
 
-ITEM_KINDS = {0: "integral_pass1", 1: "hashsift", 2: "integral_pass2", 3: "bad", 4: "projection",
+ITEM_KINDS = {0: "integral_tile", 1: "hashsift", 3: "bad", 4: "projection",
               5: "matching"}
 
 

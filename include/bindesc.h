@@ -260,10 +260,10 @@ typedef struct bd_batch bd_batch;
  *  ctas_per_sm      resident CTAs per SM of the persistent grid (0 = the most
  *                   that fit)
  *  hs_first         where the HashSIFT items (which depend on nothing) sit in
- *                   the queue: 0 after the BAD items, 1 before the integral
- *                   pass-2 tiles, 2 one grid's worth before the pass-2 tiles,
- *                   one before the BAD items and the rest after them, 3 spread
- *                   evenly among the BAD items.
+ *                   the queue: 0 after the BAD items, 1 between the integral
+ *                   tiles and the BAD items, 2 one grid's worth there and the
+ *                   rest after the BAD items, 3 spread evenly among the BAD
+ *                   items, 4 before the integral tiles.
  *  hs_kp_per_item   HashSIFT keypoints per work item: 1 = the CTA's four warps
  *                   share each keypoint (lower latency, for few keypoints),
  *                   4 = one keypoint per warp (higher throughput).
@@ -305,8 +305,11 @@ bd_status bd_batch_set_config(bd_batch *b, const bd_batch_config *cfg);
 bd_status bd_batch_get_config(const bd_batch *b, bd_batch_config *cfg);
 
 /* Describes the whole batch: one persistent kernel builds every integral
- * image and computes every BAD descriptor and HashSIFT histogram from one
- * work queue, then the projection kernel hashes all histograms.
+ * image (one pass over each image: a tile publishes its column sums, row
+ * sums and total, waits for those of the tiles to its left and above, then
+ * writes its table entries) and computes every BAD descriptor and HashSIFT
+ * histogram from one work queue, then the projection kernel hashes all
+ * histograms.
  *  imgs     host array of n_img device pointers to the images
  *  kps      device, all keypoints (kp_offsets[n_img] of them)
  *  bad_out  device, n x bad_nbits/32 words, or NULL to skip BAD
@@ -331,11 +334,14 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
  *  t_claim  the item was taken from the queue
  *  t_ready  its dependency counters were complete (= t_claim without a wait)
  *  t_end    its work was done, before it published its own completion
- * so an item's t_ready is never below the t_end of an item it waited on. */
+ * so an item's t_ready is never below the t_end of an item it waited on,
+ * except that an integral tile waits for what the tiles to its left and
+ * above publish early in their work (after their t_claim, before their
+ * t_end). */
 enum {
-    BD_ITEM_II_PASS1 = 0,   /* integral pass-1 tile (row prefixes, carries) */
+    BD_ITEM_II_TILE = 0,    /* integral tile (one pass: aggregates, wait, table) */
     BD_ITEM_HASHSIFT = 1,   /* HashSIFT histogram(s) */
-    BD_ITEM_II_PASS2 = 2,   /* integral pass-2 tile (final table) */
+                            /* 2: not used */
     BD_ITEM_BAD = 3,        /* BAD descriptors of a keypoint group */
     BD_ITEM_PROJ = 4,       /* fused projection tile (proj_fused) */
     BD_ITEM_MATCH = 5       /* matching of a query block against a train slice */

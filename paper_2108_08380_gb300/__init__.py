@@ -435,7 +435,7 @@ class BatchEvent(ctypes.Structure):
 
 
 # work item kinds of the batched kernel's queue (bd_batch_event.kind)
-BD_ITEM_II_PASS1, BD_ITEM_HASHSIFT, BD_ITEM_II_PASS2, BD_ITEM_BAD, BD_ITEM_PROJ = 0, 1, 2, 3, 4
+BD_ITEM_II_TILE, BD_ITEM_HASHSIFT, BD_ITEM_BAD, BD_ITEM_PROJ, BD_ITEM_MATCH = 0, 1, 3, 4, 5
 BD_ITEM_MATCH = 5
 # descriptor of a batch matching (bd_batch_match.desc)
 BD_DESC_BAD, BD_DESC_HASHSIFT = 0, 1

@@ -3,16 +3,20 @@
 // captured CUDA graph, with launch shapes picked by an autotuner.
 //
 // The persistent kernel runs one CTA of 128 threads per resident slot and
-// claims work items from an atomic counter, in this order (or with the
-// HashSIFT items last, a tunable):
-//   [integral pass-1 tiles of all images]
-//   [HashSIFT keypoints, four per item]        (no dependency)
-//   [integral pass-2 tiles of all images]      (wait: the image's pass-1 tiles)
-//   [BAD keypoint groups, per image]           (wait: the image's pass-2 tiles)
+// claims work items from an atomic counter, in this order (where the
+// HashSIFT items sit is a tunable):
+//   [HashSIFT keypoints (hs_first = 4)]        (no dependency)
+//   [integral tiles of all images, one pass]   (wait: the aggregates of the
+//                                               tiles to the left and above)
+//   [HashSIFT keypoints (hs_first = 1, 2)]
+//   [BAD keypoint groups, per image]           (wait: all tiles of the image)
+//   [HashSIFT keypoints (hs_first = 0, 2; spread among the BAD items: 3)]
+//   [projection tiles]                         (wait: their histograms)
+//   [matching items]                           (wait: their descriptors)
 // Every wait is on items with smaller indices, already claimed by resident
-// CTAs that never wait on later items, so the queue always drains.  Waits are
-// bounded by the GPU timer; on expiry the CTA raises BD_FLAG_TIMEOUT and
-// skips the item.
+// CTAs that publish what is waited for before they wait themselves, so the
+// queue always drains.  Waits are bounded by the GPU timer; on expiry the
+// CTA raises BD_FLAG_TIMEOUT and skips the item.
 #include <string.h>
 
 #include <algorithm>
@@ -28,7 +32,8 @@ namespace bd {
 
 struct BatchImageDev {
     int w, h, pitch, ntx, nty;
-    int tile_begin;          // first pass-1/pass-2 tile of this image
+    int tile_begin;          // first integral tile of this image (row-major tiles)
+    int band_begin;          // first tile band (row of tiles) of this image
     int kp_begin, kp_end;    // keypoints of this image
     int bad_item_begin;      // first BAD item of this image
     size_t ii_off;           // integral table offset (entries)
@@ -63,10 +68,13 @@ struct BatchKernelArgs {
     int hs_nbits;
     uint32_t *hs_out;
     int hs_first;
-    int hs_pre_final, hs_pre_bad;  // HashSIFT items queued before the pass-2 tiles / the BAD items
-    int hs_mix;                    // 1: the other HashSIFT items are spread evenly among the BAD items
+    int hs_head, hs_pre_bad;  // HashSIFT items queued before the tiles / before the BAD items
+    int hs_mix;               // 1: the other HashSIFT items are spread evenly among the BAD items
     uint32_t *ii, *carry;
-    unsigned int *work, *exit_count, *stats_done, *final_done;
+    unsigned int *work, *exit_count, *final_done;
+    unsigned int *tile_pub;   // [n_tiles] 1 once the tile's aggregates are written
+    unsigned int *band_pub;   // [n_bands] tiles of the band whose aggregates are written
+    int n_bands;
     dev::BadTables bad;
     int bad_nw;
     uint32_t *bad_out;
@@ -92,6 +100,16 @@ __device__ __forceinline__ unsigned long long gtimer()
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+
+// Holds the stream for `ns` of GPU time, so that the host has enqueued the
+// call timed after it (the autotuner times calls as the benchmark's steps
+// are timed: one at a time, with the host's launch latency hidden).
+__global__ void spin_kernel(unsigned long long ns)
+{
+    const unsigned long long t0 = gtimer();
+    while (gtimer() - t0 < ns)
+        __nanosleep(1000);
 }
 
 __device__ __forceinline__ int smid()
@@ -131,6 +149,35 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p)
     unsigned int v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+// Integral tile (tx, ty): waits until the tiles to its left in its band
+// (flags pub[ty ntx + tx'], tx' < tx) and every tile of the bands above
+// (band[ty'] == ntx, ty' < ty) have published their aggregates.  Thread i
+// checks one of them (bounded like cta_wait_count).  Called by the whole CTA.
+__device__ __forceinline__ bool cta_wait_tile_preds(const unsigned int *pub,
+                                                    const unsigned int *band, int ntx, int tx,
+                                                    int ty, DeviceStatus *status,
+                                                    unsigned long long wait_ns)
+{
+    int ok = 1;
+    for (int i = threadIdx.x; i < tx + ty; i += blockDim.x) {
+        const unsigned int *ctr = i < tx ? pub + (size_t)ty * ntx + i : band + (i - tx);
+        const unsigned int target = i < tx ? 1u : (unsigned)ntx;
+        if (ld_acquire(ctr) < target) {
+            const unsigned long long t0 = gtimer();
+            while (ld_acquire(ctr) < target) {
+                __nanosleep(100);
+                if (gtimer() - t0 > wait_ns) {
+                    ok = 0;
+                    dev::raise_flag(status, BD_FLAG_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    return __syncthreads_and(ok) != 0;
 }
 
 // Waits until every 32-keypoint group overlapping [k0, k1) is complete:
@@ -279,8 +326,7 @@ template <int NW, int MINB>
 __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernelArgs A)
 {
     __shared__ union {
-        dev::IiStatsSmem s;
-        dev::IiFinalSmem f;
+        dev::IiOneSmem ii;
         dev::WarpHist h[4];  // one per warp
         ProjTile p;
         uint32_t bs[4][2 * NW * 32];  // BAD box sums: per warp, per warp pair or one shared
@@ -299,17 +345,17 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
     dev::griddep_wait();
     dev::griddep_launch_dependents();
 
-    // queue: [pass-1 tiles][HashSIFT a][pass-2 tiles][HashSIFT b][BAD items][HashSIFT rest]
+    // queue: [HashSIFT head][tiles][HashSIFT pre-BAD][BAD items (+ HashSIFT mixed)]
+    //        [HashSIFT rest][projection tiles][matching items]
     const int n_hs = A.hs_items;
-    const int e0 = A.n_tiles;
-    const int e1 = e0 + A.hs_pre_final;
-    const int e2 = e1 + A.n_tiles;
-    const int e3 = e2 + A.hs_pre_bad;
-    const int n_rest = n_hs - A.hs_pre_final - A.hs_pre_bad;  // HashSIFT items after the pass-2 tiles
-    const int e4 = e3 + A.n_bad_items + (A.hs_mix ? n_rest : 0);
-    const int e5 = e4 + (A.hs_mix ? 0 : n_rest);
-    const int e6 = e5 + A.proj_items;
-    const int total = e6 + A.match_items;
+    const int e0 = A.hs_head;
+    const int e1 = e0 + A.n_tiles;
+    const int e2 = e1 + A.hs_pre_bad;
+    const int n_rest = n_hs - A.hs_head - A.hs_pre_bad;  // HashSIFT items after the tiles and pre-BAD ones
+    const int e3 = e2 + A.n_bad_items + (A.hs_mix ? n_rest : 0);
+    const int e4 = e3 + (A.hs_mix ? 0 : n_rest);
+    const int e5 = e4 + A.proj_items;
+    const int total = e5 + A.match_items;
 
     unsigned long long t_claim = 0, t_ready = 0;
     for (;;) {
@@ -322,46 +368,43 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
             break;
         if (A.events && t == 0)
             t_claim = t_ready = gtimer();
-        // item -> (kind, index): 0 pass-1 tile, 1 HashSIFT, 2 pass-2 tile, 3 BAD
+        // item -> (kind, index): 0 integral tile, 1 HashSIFT, 3 BAD, 4 projection, 5 matching
         int kind, idx;
         if (item < e0) {
-            kind = 0;
+            kind = 1;
             idx = item;
         } else if (item < e1) {
-            kind = 1;
+            kind = 0;
             idx = item - e0;
         } else if (item < e2) {
-            kind = 2;
-            idx = item - e1;
-        } else if (item < e3) {
             kind = 1;
-            idx = A.hs_pre_final + item - e2;
-        } else if (item < e4) {
+            idx = A.hs_head + item - e1;
+        } else if (item < e3) {
             if (!A.hs_mix) {
                 kind = 3;
-                idx = item - e3;
+                idx = item - e2;
             } else {
                 // item i of the mixed run is the BAD item floor(i nb / N) when
                 // that count steps at i (nb of the N steps), else a HashSIFT item
-                const long long i = item - e3, nb = A.n_bad_items, N = nb + n_rest;
+                const long long i = item - e2, nb = A.n_bad_items, N = nb + n_rest;
                 const long long before = i * nb / N, after = (i + 1) * nb / N;
                 if (after > before) {
                     kind = 3;
                     idx = (int)before;
                 } else {
                     kind = 1;
-                    idx = A.hs_pre_final + A.hs_pre_bad + (int)(i - before);
+                    idx = A.hs_head + A.hs_pre_bad + (int)(i - before);
                 }
             }
-        } else if (item < e5) {
+        } else if (item < e4) {
             kind = 1;
-            idx = A.hs_pre_final + A.hs_pre_bad + item - e4;
-        } else if (item < e6) {
+            idx = A.hs_head + A.hs_pre_bad + item - e3;
+        } else if (item < e5) {
             kind = 4;
-            idx = item - e5;
+            idx = item - e4;
         } else {
             kind = 5;
-            idx = item - e6;
+            idx = item - e5;
         }
         // thread 0: the item's work is done (before it publishes completion)
         auto record = [&]() {
@@ -382,16 +425,30 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                 t_ready = gtimer();
         };
         if (kind == 0) {
+            // integral tile in one pass: aggregates, publish, wait for the
+            // tiles to the left and above, then the table entries
             const int im = find_image(A.imgs, A.n_img, idx, 0);
             const BatchImageDev &I = A.imgs[im];
             const int tl = idx - I.tile_begin;
-            dev::ii_stats_tile(U.s, A.img_ptr[im], I.w, I.h, I.pitch, A.carry + I.cs_off,
-                               A.carry + I.rs_off, A.carry + I.tt_off, I.ntx, tl % I.ntx, tl / I.ntx);
+            const int tx = tl % I.ntx, ty = tl / I.ntx;
+            dev::ii_one_local(U.ii, A.img_ptr[im], I.w, I.h, I.pitch, A.carry + I.cs_off,
+                              A.carry + I.rs_off, A.carry + I.tt_off, I.ntx, tx, ty);
+            if (t == 0) {
+                __threadfence();
+                atomicAdd(A.tile_pub + idx, 1u);
+                atomicAdd(A.band_pub + I.band_begin + ty, 1u);
+            }
+            if (cta_wait_tile_preds(A.tile_pub + I.tile_begin, A.band_pub + I.band_begin, I.ntx, tx,
+                                    ty, A.status, A.wait_ns)) {
+                mark_ready();
+                dev::ii_one_finish(U.ii, I.w, I.h, A.carry + I.cs_off, A.carry + I.rs_off,
+                                   A.carry + I.tt_off, I.ntx, A.ii + I.ii_off, I.w + 1, tx, ty);
+            }
             __syncthreads();
             record();
             if (t == 0) {
                 __threadfence();
-                atomicAdd(A.stats_done + im, 1u);
+                atomicAdd(A.final_done + im, 1u);
             }
         } else if (kind == 1) {
             if (A.hs_per_item == 1) {
@@ -422,23 +479,6 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
             }
             __syncthreads();
             record();
-        } else if (kind == 2) {
-            const int tile = idx;
-            const int im = find_image(A.imgs, A.n_img, tile, 0);
-            const BatchImageDev &I = A.imgs[im];
-            if (cta_wait_count(A.stats_done + im, (unsigned)(I.ntx * I.nty), &flag_s, A.status, A.wait_ns)) {
-                mark_ready();
-                const int tl = tile - I.tile_begin;
-                dev::ii_final_tile(U.f, A.img_ptr[im], I.w, I.h, I.pitch, A.carry + I.cs_off,
-                                   A.carry + I.rs_off, A.carry + I.tt_off, I.ntx, A.ii + I.ii_off,
-                                   I.w + 1, tl % I.ntx, tl / I.ntx);
-            }
-            __syncthreads();
-            record();
-            if (t == 0) {
-                __threadfence();
-                atomicAdd(A.final_done + im, 1u);
-            }
         } else if (kind == 4) {
             // FP32 projection of 32 keypoints x 32 bits, once their histograms exist
             const int g = idx / A.proj_cols, cb = idx % A.proj_cols;
@@ -546,10 +586,12 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
             *A.work = 0u;
             *A.exit_count = 0u;
         }
-        for (int i = t; i < A.n_img; i += blockDim.x) {
-            A.stats_done[i] = 0u;
+        for (int i = t; i < A.n_img; i += blockDim.x)
             A.final_done[i] = 0u;
-        }
+        for (int i = t; i < A.n_tiles; i += blockDim.x)
+            A.tile_pub[i] = 0u;
+        for (int i = t; i < A.n_bands; i += blockDim.x)
+            A.band_pub[i] = 0u;
         for (int i = t; i < (A.n_kp + 31) / 32; i += blockDim.x) {
             if (A.proj_items)
                 A.hs_group_done[i] = 0u;
@@ -576,14 +618,15 @@ struct bd_batch {
     bd_ctx *ctx = nullptr;
     const bd_bad_params *bad = nullptr;
     const bd_hs_params *hs = nullptr;
-    int n_img = 0, n_tiles = 0, n_kp = 0, n_bad_items = 0;
+    int n_img = 0, n_tiles = 0, n_bands = 0, n_kp = 0, n_bad_items = 0;
     std::vector<BatchImageDev> imgs;
     BatchImageDev *d_imgs = nullptr;
     const uint8_t **d_ptrs = nullptr;
     std::vector<const uint8_t *> last_ptrs;
     uint32_t *d_ii = nullptr, *d_carry = nullptr;
-    // [work][exit][stats_done n_img][final_done n_img][hs groups][BAD groups]
-    // [projection groups] (groups of 32 keypoints), zero between launches
+    // [work][exit][final_done n_img][hs groups][BAD groups][projection groups]
+    // (groups of 32 keypoints)[tile flags n_tiles][band counters n_bands],
+    // zero between launches
     unsigned int *d_counters = nullptr;
     float *d_hist = nullptr;
     bd_batch_config cfg = {8, 0, 1, 4, 0, 0, 0};
@@ -724,7 +767,7 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
         A.proj_half = b->cfg.proj_half;
         A.proj_cols = b->hs->nbits / (A.proj_half ? 16 : 32);
         A.proj_items = ((b->n_kp + 31) / 32) * A.proj_cols;
-        A.hs_group_done = b->d_counters + 2 + 2 * b->n_img;
+        A.hs_group_done = b->d_counters + 2 + b->n_img;
         A.W = b->hs->d_W;
         A.bias = b->hs->d_bias;
         A.hs_nbits = b->hs->nbits;
@@ -736,8 +779,11 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     A.carry = b->d_carry;
     A.work = b->d_counters;
     A.exit_count = b->d_counters + 1;
-    A.stats_done = b->d_counters + 2;
-    A.final_done = b->d_counters + 2 + b->n_img;
+    A.final_done = b->d_counters + 2;
+    const int groups = (b->n_kp + 31) / 32;
+    A.tile_pub = b->d_counters + 2 + b->n_img + 3 * groups;
+    A.band_pub = A.tile_pub + b->n_tiles;
+    A.n_bands = A.n_tiles ? b->n_bands : 0;
     if (b->bad)
         A.bad = dev::bad_tables(b->bad);
     A.bad_nw = b->bad ? b->bad->nbits / 32 : 8;
@@ -748,32 +794,30 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     A.kps = kps;
     A.status = ctx->status;
     A.wait_ns = b->wait_ns ? b->wait_ns : kDefaultWaitNs;
-    A.bad_grp_done = b->d_counters + 2 + 2 * b->n_img + (b->n_kp + 31) / 32;
-    A.bits_grp_done = A.bad_grp_done + (b->n_kp + 31) / 32;
+    A.bad_grp_done = b->d_counters + 2 + b->n_img + groups;
+    A.bits_grp_done = A.bad_grp_done + groups;
     int per_sm = b->cfg.ctas_per_sm > 0 ? b->cfg.ctas_per_sm : b->max_ctas_per_sm;
     if (per_sm > b->max_ctas_per_sm)
         per_sm = b->max_ctas_per_sm;
     const int grid = per_sm * ctx->sm_count;
     // HashSIFT items (no dependency) fill the waits of the integral / BAD chain:
-    // 0 all after the BAD items, 1 all before the pass-2 tiles, 2 one grid's
-    // worth before the pass-2 tiles and one before the BAD items, 3 spread
-    // evenly among the BAD items (gather-bound and issue-bound work side by side)
-    if (b->cfg.hs_first == 1) {
-        A.hs_pre_final = A.hs_items;
+    // 0 all after the BAD items, 1 all between the tiles and the BAD items,
+    // 2 one grid's worth there and the rest after the BAD items, 3 spread
+    // evenly among the BAD items (gather-bound and issue-bound work side by
+    // side), 4 all before the tiles (the HashSIFT chain to the projection and
+    // matching starts first)
+    A.hs_head = b->cfg.hs_first == 4 ? A.hs_items : 0;
+    if (b->cfg.hs_first == 1)
+        A.hs_pre_bad = A.hs_items;
+    else if (b->cfg.hs_first == 2)
+        A.hs_pre_bad = A.hs_items < grid ? A.hs_items : grid;
+    else
         A.hs_pre_bad = 0;
-    } else if (b->cfg.hs_first == 2) {
-        A.hs_pre_final = A.hs_items < grid ? A.hs_items : grid;
-        const int rest = A.hs_items - A.hs_pre_final;
-        A.hs_pre_bad = rest < grid ? rest : grid;
-    } else {
-        A.hs_pre_final = 0;
-        A.hs_pre_bad = 0;
-    }
     A.hs_mix = b->cfg.hs_first == 3 && A.n_bad_items > 0 ? 1 : 0;
     const bool m_in_kernel = !b->mjobs.empty() && (fused || !any_hs_job(b));
     if (m_in_kernel)
         fill_match_items(b, A, bad_out, hs_out, grid);
-    const int n_items = 2 * A.n_tiles + A.hs_items + A.n_bad_items + A.proj_items + A.match_items;
+    const int n_items = A.n_tiles + A.hs_items + A.n_bad_items + A.proj_items + A.match_items;
     A.events = (b->d_events && n_items <= b->ev_cap) ? b->d_events : nullptr;
     // the largest register budget that keeps per_sm CTAs resident
     const int budget = per_sm <= b->occ4 ? 4 : (per_sm <= b->occ5 ? 5 : 6);
@@ -870,7 +914,7 @@ bd_status bd_batch_create(bd_ctx *ctx, const bd_bad_params *bad, const bd_hs_par
     b->hs = hs;
     b->n_img = n_img;
     size_t ii_total = 0, carry_total = 0;
-    int tiles = 0, bad_items = 0;
+    int tiles = 0, bands = 0, bad_items = 0;
     for (int i = 0; i < n_img; ++i) {
         if (w[i] < 1 || h[i] < 1 || w[i] > kMaxImageSide || h[i] > kMaxImageSide || pitch[i] < w[i] ||
             255.0 * (double)w[i] * (double)h[i] >= 4294967296.0 || kp_offsets[i + 1] < kp_offsets[i]) {
@@ -885,6 +929,8 @@ bd_status bd_batch_create(bd_ctx *ctx, const bd_bad_params *bad, const bd_hs_par
         I.nty = (h[i] + kIiTileRows - 1) / kIiTileRows;
         I.tile_begin = tiles;
         tiles += I.ntx * I.nty;
+        I.band_begin = bands;
+        bands += I.nty;
         I.kp_begin = kp_offsets[i];
         I.kp_end = kp_offsets[i + 1];
         I.bad_item_begin = bad_items;
@@ -899,6 +945,7 @@ bd_status bd_batch_create(bd_ctx *ctx, const bd_bad_params *bad, const bd_hs_par
         b->imgs.push_back(I);
     }
     b->n_tiles = tiles;
+    b->n_bands = bands;
     b->n_kp = kp_offsets[n_img];
     b->cfg.bad_kp_per_item = 8;
     for (int i = 0; i < n_img; ++i) {
@@ -916,7 +963,8 @@ bd_status bd_batch_create(bd_ctx *ctx, const bd_bad_params *bad, const bd_hs_par
         if (e == cudaSuccess) e = cudaMalloc(&b->d_ptrs, sizeof(void *) * n_img);
         if (e == cudaSuccess && bad) e = cudaMalloc(&b->d_ii, sizeof(uint32_t) * ii_total);
         if (e == cudaSuccess && bad) e = cudaMalloc(&b->d_carry, sizeof(uint32_t) * carry_total);
-        const size_t ncount = 2 + 2 * (size_t)n_img + 3 * ((size_t)(b->n_kp + 31) / 32);
+        const size_t ncount = 2 + (size_t)n_img + 3 * ((size_t)(b->n_kp + 31) / 32) + (size_t)tiles +
+                              (size_t)bands;
         if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(unsigned int) * ncount);
         if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, sizeof(unsigned int) * ncount);
         if (e == cudaSuccess && hs) e = cudaMalloc(&b->d_hist, sizeof(float) * kHistDim * (size_t)(b->n_kp > 0 ? b->n_kp : 1));
@@ -974,7 +1022,7 @@ bd_status bd_batch_set_config(bd_batch *b, const bd_batch_config *cfg)
     if (!b || !cfg)
         return BD_ERR_INVALID;
     if (cfg->bad_kp_per_item < 4 || cfg->bad_kp_per_item > 256 || (cfg->bad_kp_per_item & 3) ||
-        cfg->ctas_per_sm < 0 || cfg->hs_first < 0 || cfg->hs_first > 3 ||
+        cfg->ctas_per_sm < 0 || cfg->hs_first < 0 || cfg->hs_first > 4 ||
         (cfg->hs_kp_per_item != 1 && cfg->hs_kp_per_item != 4) ||
         (cfg->proj_fused != 0 && cfg->proj_fused != 1) ||
         cfg->bad_shared < 0 || cfg->bad_shared > 2 ||
@@ -1109,21 +1157,29 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    // mean time of `r` launches of configuration c (after one warm-up launch)
+    // mean device time of `r` calls in configuration c (after one warm-up
+    // call), each call timed on its own behind a short device spin, so that
+    // neither the host's launch latency nor the overlap of back-to-back calls
+    // enters the time
     auto time_cfg = [&](const bd_batch_config &c, int r, float *ms) -> bd_status {
         bd_status s = bd_batch_set_config(b, &c);
         if (s == BD_OK)
             s = bd_describe_batch(ctx, b, imgs, kps, bad_out, hs_out, 0);
         if (s != BD_OK)
             return s;
-        cudaEventRecord(e0, ctx->stream);
-        for (int q = 0; q < r; ++q)
+        float tot = 0.f;
+        for (int q = 0; q < r; ++q) {
+            spin_kernel<<<1, 32, 0, ctx->stream>>>(30000ull);
+            cudaEventRecord(e0, ctx->stream);
             bd_describe_batch(ctx, b, imgs, kps, bad_out, hs_out, 0);
-        cudaEventRecord(e1, ctx->stream);
-        cudaEventSynchronize(e1);
-        cudaEventElapsedTime(ms, e0, e1);
-        *ms /= r;
-        return BD_OK;
+            cudaEventRecord(e1, ctx->stream);
+            cudaEventSynchronize(e1);
+            float one = 0.f;
+            cudaEventElapsedTime(&one, e0, e1);
+            tot += one;
+        }
+        *ms = tot / r;
+        return cudaGetLastError() == cudaSuccess ? BD_OK : cuda_err(ctx, cudaErrorLaunchFailure, "autotune");
     };
     // sweep, then re-time the four fastest with three times the repetitions
     std::vector<std::pair<float, bd_batch_config>> res;
@@ -1133,7 +1189,7 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     for (int bs = 0; bs < (with_bad ? 3 : 1); ++bs)
     for (int fu = 0; fu < (can_fuse ? 3 : 1); ++fu)
     for (int hm : {1, 4})
-        for (int hs_first = 0; hs_first < 4 && s == BD_OK; ++hs_first)
+        for (int hs_first = 0; hs_first < 5 && s == BD_OK; ++hs_first)
             for (int it : items)
                 for (int c : per_sm) {
                     if (s != BD_OK)
@@ -1199,10 +1255,10 @@ bd_status bd_batch_set_timeline(bd_batch *b, int enable)
     }
     b->last_items = -1;
     if (enable && e == cudaSuccess) {
-        // the most items any configuration queues: pass-1 and pass-2 tiles,
-        // one HashSIFT item per keypoint, BAD items of 4 keypoints, and
+        // the most items any configuration queues: integral tiles, one
+        // HashSIFT item per keypoint, BAD items of 4 keypoints, and
         // projection tiles of 32 keypoints x 16 of at most 512 bits
-        const long long cap = 2LL * b->n_tiles + b->n_kp + (b->n_kp / 4 + b->n_img) +
+        const long long cap = (long long)b->n_tiles + b->n_kp + (b->n_kp / 4 + b->n_img) +
                               ((long long)(b->n_kp + 31) / 32) * 32 + b->m_max_items + 1;
         if (cap > 0x7fffffffLL / (long long)sizeof(bd_batch_event))
             e = cudaErrorMemoryAllocation;

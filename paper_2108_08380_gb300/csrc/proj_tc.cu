@@ -10,44 +10,53 @@
 // the FP32 histogram and FP32 W, in the FP32 projection kernel's order: the
 // result equals the FP32 path bit for bit.
 //
-// CTA = 256 threads, tile = 128 keypoints x 128 bits, K = 128 in two 64-wide
-// phases:
-//  - thread 0 loads the W^T head / tail tiles with TMA (128-byte swizzle):
-//    both phases at the start when the grid is one wave or less (BothB,
-//    96 KB of shared memory, lowest latency), else one phase at a time
-//    through one stage (64 KB; two CTAs per SM either way, by registers,
-//    and three measured slower: less of the SM's memory is left as L1);
-//  - every thread loads its share of the FP32 histogram rows for both
-//    phases at once (row t/2, half t%2 of the phase's 64 values), splits
-//    them into BF16 head and tail in registers and writes the phase's A
-//    operands into shared memory in the same 128-byte-swizzled K-major
-//    layout TMA would produce (no separate conversion pass and no BF16 copy
-//    of the histograms in global memory);
-//  - thread 0 issues 4 x (2 or 3) MMAs of K = 16 per phase, committed to an
-//    mbarrier; the A stage is refilled for phase 1 once phase 0's MMAs are done;
-//  - warps w and w+4 read TMEM lane quadrant w%4 (= 32 keypoints), each half
-//    of the columns, add the FP32 bias, take the sign and the band mask
-//    without branches;
-//  - a row of zeros (a patch without gradients) projects to exactly the bias
-//    on both paths (every product is zero), so its bits are never queued;
-//  - band bits go to a list in shared memory and are re-evaluated in FP32
-//    64 at a time, four lanes per bit: lane q sums terms [32q, 32q + 32) as a
-//    chain from zero (histogram row and FP32 W row from L2), and the partials
-//    are combined in the FP32 projection kernel's order ((c0 + c1) + c2) + c3.
-// Waits on mbarriers are bounded; on a timeout the CTA raises
-// BD_FLAG_TIMEOUT, waits once more for its MMAs, frees TMEM and returns.
+// Persistent, warp-specialised kernel, one CTA per SM.  CTA c works on the
+// 128-bit chunk c / cpc of the hash (its W^T head and tail tiles stay in
+// shared memory for the whole launch, loaded once by TMA) and on a
+// contiguous range of 128-keypoint blocks; per block:
+//  - 7 converter warps (rows w, w + 7, ...: one coalesced 512-byte row per
+//    warp load, all of a warp's rows in flight) split the FP32 rows into BF16
+//    head and tail in registers and write them into one of two operand
+//    stages in the 128-byte-swizzled K-major layout TMA would produce (no
+//    BF16 copy of the histograms in global memory);
+//  - one thread issues 8 K-steps x (2 or 3) MMAs into one of two TMEM
+//    accumulators and commits them to the stage's "empty" barrier and the
+//    accumulator's "full" barrier;
+//  - 8 epilogue warps (TMEM lane quadrant = warp mod 4, two warps per
+//    quadrant, 64 columns each) read the accumulator, add the bias, take
+//    the sign and the band mask, release the
+//    accumulator, then re-check their rows' band bits in FP32 from the
+//    histogram row and the FP32 W^T row (L2), in the FP32 projection
+//    kernel's order: four 32-term chains from zero, ((c0 + c1) + c2) + c3,
+//    plus the bias; a row of zeros (a patch without gradients) projects to
+//    exactly the bias on both paths and is never re-checked.
+// So the conversion of block j + 1, the MMAs of block j and the epilogue of
+// block j - 1 overlap.  Every mbarrier wait is bounded; a wait that gives up
+// raises BD_FLAG_TIMEOUT and stops every role at its next block; the CTA
+// then waits (bounded) for the MMAs it issued and the W loads before it
+// frees TMEM and returns.
 #include "bd_internal.h"
 
 namespace bd {
 namespace {
 
-constexpr int BM = 128;
-constexpr int BN = 128;
-constexpr int TILE = BM * 128;              // bytes of one 64-wide BF16 K chunk of a 128-row operand
-constexpr int NTH = 256;                    // threads per CTA
-// A hi/lo (one phase) + B hi/lo (both phases, or one stage)
-constexpr int smem_bytes(bool both_b) { return (both_b ? 6 : 4) * TILE + 1024; }
-static_assert(2048 + 2 * BM * BN <= 4 * TILE, "output tile and band list do not fit the operand area");
+constexpr int BM = 128;          // keypoints per block
+constexpr int BN = 128;          // bits per chunk (one CTA's W slice)
+constexpr int TILE = BM * 128;   // bytes of one 64-wide BF16 K half of a 128-row operand
+constexpr int NCONV = 7;         // converter warps: rows cw, cw + 7, ... (16 warps in all:
+                                 // registers are granted for whole groups of 4 warps)
+constexpr int CROWS = (128 + NCONV - 1) / NCONV;  // rows per converter warp, at most
+constexpr int CBATCH = CROWS;    // rows a converter lane has in flight (all of them)
+constexpr int NZSLOTS = 8;       // zero-row flags, by block: a converter reaches block
+                                 // j + 8 only after the epilogue finished block j
+constexpr int LCAP = 256;        // band bits an epilogue warp re-checks per round
+constexpr int NEPI = 8;          // epilogue warps: TMEM lane quadrant warp mod 4, 64 columns each
+constexpr int ECOLS = BN * 4 / NEPI;  // columns per epilogue warp
+constexpr int NTH = 32 * (1 + NCONV + NEPI);
+constexpr int STAGES = 2;        // A operand stages
+constexpr int ACCS = 2;          // TMEM accumulators of BN columns
+// W (head K0, head K1, tail K0, tail K1) + STAGES x A (same four tiles)
+constexpr int smem_bytes() { return (4 + 4 * STAGES) * TILE + 1024; }
 
 // Offset of 16-byte chunk c (0..7) of row r in a 128-row x 128-byte operand
 // tile with the 128-byte swizzle: chunk positions are XORed with r mod 8.
@@ -56,313 +65,360 @@ __device__ __forceinline__ uint32_t sw128_offset(int r, int c)
     return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
 }
 
-// Splits 8 FP32 values into BF16 head and tail (x = hi + lo + O(2^-16 |x|))
-// and stores both 16-byte chunks.
-__device__ __forceinline__ void split_store8(const float4 &a, const float4 &b, uint8_t *hi_dst,
-                                             uint8_t *lo_dst)
+// BF16 head and tail of 4 FP32 values (x = hi + lo + O(2^-16 |x|)).
+__device__ __forceinline__ void split4(const float4 &a, uint2 &hi, uint2 &lo)
 {
-    const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const __nv_bfloat162 hv = __floats2bfloat162_rn(x[2 * q], x[2 * q + 1]);
-        const float2 hf = __bfloat1622float2(hv);
-        const __nv_bfloat162 lv = __floats2bfloat162_rn(x[2 * q] - hf.x, x[2 * q + 1] - hf.y);
-        h[q] = *reinterpret_cast<const uint32_t *>(&hv);
-        l[q] = *reinterpret_cast<const uint32_t *>(&lv);
-    }
-    *reinterpret_cast<uint4 *>(hi_dst) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4 *>(lo_dst) = make_uint4(l[0], l[1], l[2], l[3]);
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(a.x, a.y);
+    const __nv_bfloat162 h1 = __floats2bfloat162_rn(a.z, a.w);
+    const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+    const __nv_bfloat162 l0 = __floats2bfloat162_rn(a.x - f0.x, a.y - f0.y);
+    const __nv_bfloat162 l1 = __floats2bfloat162_rn(a.z - f1.x, a.w - f1.y);
+    hi = make_uint2(*reinterpret_cast<const uint32_t *>(&h0), *reinterpret_cast<const uint32_t *>(&h1));
+    lo = make_uint2(*reinterpret_cast<const uint32_t *>(&l0), *reinterpret_cast<const uint32_t *>(&l1));
 }
 
-template <bool BothB>
-__global__ void __launch_bounds__(NTH, 2) hs_proj_tc_kernel(
+__global__ void __launch_bounds__(NTH, 1) hs_proj_tc_kernel(
     const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int w_has_lo,
     const float *__restrict__ hist32, const float *__restrict__ Wt32,
     const float *__restrict__ bias, const float *__restrict__ band,
     const bd_keypoint *__restrict__ kps, int n, int K, uint32_t *__restrict__ out,
-    DeviceStatus *status)
+    DeviceStatus *status, int nblocks, int cpc)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *sAh = smem, *sAl = smem + TILE;
-    uint8_t *sB = smem + 2 * TILE;  // phase p: head at tile 2p, tail at 2p + 1 (BothB; else p = 0)
-    __shared__ uint64_t bar_b0, bar_b1, bar_mma0, bar_mma1;
+    uint8_t *sW = smem;              // head K0, head K1, tail K0, tail K1
+    uint8_t *sA = smem + 4 * TILE;   // stage s at s * 4 TILE: head K0, head K1, tail K0, tail K1
+    __shared__ uint64_t bar_w, bar_afull[STAGES], bar_aempty[STAGES], bar_accfull[ACCS],
+        bar_accempty[ACCS], bar_nz[NZSLOTS];
     __shared__ uint32_t tmem_slot;
-    __shared__ int abort_flag;
-    __shared__ int list_n;
-    __shared__ float bias_s[BN], band_s[BN];
-    __shared__ int row_nz[BM];
+    __shared__ int abort_s, issued_s;
+    __shared__ __align__(16) float bias_s[BN];
+    __shared__ __align__(16) float band_s[BN];
+    __shared__ uint8_t nz_s[NZSLOTS][BM];            // row has a nonzero histogram entry
+    __shared__ uint16_t list_s[NEPI][LCAP];            // band bits: row in warp << 7 | column
+    __shared__ uint32_t words_s[NEPI][32][ECOLS / 32]; // the warp's output words
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    // the bit tiles of one keypoint tile are neighbours in launch order, so they
-    // read the same histogram rows while those are still in L2
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int chunk = blockIdx.x / cpc, part = blockIdx.x % cpc;
+    const int n0 = chunk * BN;
+    const int bb0 = (int)((long long)nblocks * part / cpc);
+    const int nb = (int)((long long)nblocks * (part + 1) / cpc) - bb0;
 
     if (t == 0) {
-        dev::mbar_init(&bar_b0, 1);
-        dev::mbar_init(&bar_b1, 1);
-        dev::mbar_init(&bar_mma0, 1);
-        dev::mbar_init(&bar_mma1, 1);
+        dev::mbar_init(&bar_w, 1);
+        for (int s = 0; s < STAGES; ++s) {
+            dev::mbar_init(&bar_afull[s], 32 * NCONV);
+            dev::mbar_init(&bar_aempty[s], 1);
+        }
+        for (int a = 0; a < ACCS; ++a) {
+            dev::mbar_init(&bar_accfull[a], 1);
+            dev::mbar_init(&bar_accempty[a], 32 * NEPI);
+        }
+        for (int z = 0; z < NZSLOTS; ++z)
+            dev::mbar_init(&bar_nz[z], NCONV);  // lane 0 of each converter warp
         dev::fence_mbar_init();
-        abort_flag = 0;
-        list_n = 0;
+        abort_s = 0;
+        issued_s = 0;
     }
     if (t < BN) {
         bias_s[t] = __ldg(bias + n0 + t);
         band_s[t] = __ldg(band + n0 + t);
     }
-    static_assert(BN <= NTH, "one thread per bias entry");
+    if (warp == 0)
+        dev::tmem_alloc(&tmem_slot, ACCS * BN);
+    dev::tc_fence_before();
+    __syncthreads();
+    dev::tc_fence_after();
+    const uint32_t tmem = tmem_slot;
     // W is a parameter, not written by earlier kernels: load it right away
-    auto load_b = [&](int p) {
-        uint8_t *dst = BothB ? sB + 2 * p * TILE : sB;
-        uint64_t *bar = p == 0 ? &bar_b0 : &bar_b1;
-        dev::mbar_arrive_expect_tx(bar, (w_has_lo ? 2 : 1) * TILE);
-        dev::tma_load_2d(dst, &tmBh, 64 * p, n0, bar);
-        if (w_has_lo)
-            dev::tma_load_2d(dst + TILE, &tmBl, 64 * p, n0, bar);
-    };
     if (t == 0) {
-        load_b(0);
-        if (BothB)
-            load_b(1);
+        dev::mbar_arrive_expect_tx(&bar_w, (w_has_lo ? 4 : 2) * TILE);
+        dev::tma_load_2d(sW, &tmBh, 0, n0, &bar_w);
+        dev::tma_load_2d(sW + TILE, &tmBh, 64, n0, &bar_w);
+        if (w_has_lo) {
+            dev::tma_load_2d(sW + 2 * TILE, &tmBl, 0, n0, &bar_w);
+            dev::tma_load_2d(sW + 3 * TILE, &tmBl, 64, n0, &bar_w);
+        }
     }
     // programmatic launch: the prologue above overlaps the previous kernel
     // (which writes the histograms read below)
     dev::griddep_wait();
     dev::griddep_launch_dependents();
 
-    // this thread's histogram values: row ar, values [64p + 32 ah, + 32) of phase p
-    const int ar = t >> 1, ah = t & 1;
-    float4 av[2][8];
-    {
-        const bool in = m0 + ar < n;
-        const float4 *src = reinterpret_cast<const float4 *>(hist32 + (size_t)(m0 + ar) * kHistDim);
-#pragma unroll
-        for (int p = 0; p < 2; ++p)
-#pragma unroll
-            for (int v = 0; v < 8; ++v)
-                av[p][v] = in ? __ldg(src + 16 * p + 8 * ah + v) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    // A row of zeros projects to exactly the bias on either path: no re-check
-    {
-        uint32_t nz = 0;
-#pragma unroll
-        for (int p = 0; p < 2; ++p)
-#pragma unroll
-            for (int v = 0; v < 8; ++v)
-                nz |= (__float_as_uint(av[p][v].x) | __float_as_uint(av[p][v].y) |
-                       __float_as_uint(av[p][v].z) | __float_as_uint(av[p][v].w)) & 0x7fffffffu;
-        nz |= __shfl_xor_sync(0xffffffffu, nz, 1);
-        if (ah == 0)
-            row_nz[ar] = nz != 0u;
-    }
-    // epilogue row and its validity, fetched early
-    const int quad = warp & 3, half = warp >> 2;
-    const int row = quad * 32 + lane;
-    const int kp = m0 + row;
-    const bool valid = kp < n && (kps == nullptr || dev::kp_valid(kps[kp]));
-
-    if (warp == 0)
-        dev::tmem_alloc(&tmem_slot, BN);
-    // phase 0 A operands
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const uint32_t off = sw128_offset(ar, 4 * ah + c);
-        split_store8(av[0][2 * c], av[0][2 * c + 1], sAh + off, sAl + off);
-    }
-    dev::fence_proxy_async_smem();
-    dev::tc_fence_before();
-    __syncthreads();
-    dev::tc_fence_after();
-    const uint32_t tmem = tmem_slot;
-    const uint32_t idesc = dev::umma_idesc_bf16_f32(BM, BN);
-
-    int issued = 0;  // commits issued (thread 0)
-    auto issue = [&](int p) {
-        const uint8_t *bh = BothB ? sB + 2 * p * TILE : sB, *bl = bh + TILE;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const uint64_t ahd = dev::umma_desc_sw128(dev::smem_u32(sAh + s * 32));
-            const uint64_t ald = dev::umma_desc_sw128(dev::smem_u32(sAl + s * 32));
-            const uint64_t bhd = dev::umma_desc_sw128(dev::smem_u32(bh + s * 32));
-            const uint64_t bld = dev::umma_desc_sw128(dev::smem_u32(bl + s * 32));
-            dev::umma_bf16(tmem, ahd, bhd, idesc, (p | s) ? 1u : 0u);
-            dev::umma_bf16(tmem, ald, bhd, idesc, 1u);
-            if (w_has_lo)
-                dev::umma_bf16(tmem, ahd, bld, idesc, 1u);
-        }
-        dev::umma_commit(p == 0 ? &bar_mma0 : &bar_mma1);
-        ++issued;
-    };
-    int b_loads = BothB ? 2 : 1;  // W loads issued (thread 0)
-    if (t == 0) {
-        if (dev::mbar_wait_bounded(&bar_b0, 0)) {
-            dev::tc_fence_after();
-            issue(0);
-        } else {
-            abort_flag = 1;
-        }
-    }
-    // phase 1 A operands, once phase 0's MMAs have read the stage
-    __syncthreads();
-    bool ok = abort_flag == 0;
-    if (ok)
-        ok = dev::mbar_wait_bounded(&bar_mma0, 0);
-    if (ok) {
-        if (!BothB && t == 0) {  // the W stage is free too: its phase-1 tiles
-            load_b(1);
-            b_loads = 2;
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const uint32_t off = sw128_offset(ar, 4 * ah + c);
-            split_store8(av[1][2 * c], av[1][2 * c + 1], sAh + off, sAl + off);
-        }
-        dev::fence_proxy_async_smem();
-    }
-    dev::tc_fence_before();
-    ok = __syncthreads_and(ok) != 0;
-    dev::tc_fence_after();
-    if (ok && t == 0) {
-        if (dev::mbar_wait_bounded(&bar_b1, 0)) {
-            dev::tc_fence_after();
-            issue(1);
-        } else {
-            abort_flag = 1;
-        }
-    }
-    ok = __syncthreads_and(ok && abort_flag == 0) != 0;
-    if (ok)
-        ok = dev::mbar_wait_bounded(&bar_mma1, 0);
-    ok = __syncthreads_and(ok) != 0;
-    dev::tc_fence_after();
-
-    if (ok) {
-        // The operand area is dead now: it holds the output tile and the list
-        // of band bits (row << 7 | column, at most 128 x 128 entries).
-        uint32_t *out_tile = reinterpret_cast<uint32_t *>(smem);           // [128][BN/32], 2 KB
-        uint16_t *list = reinterpret_cast<uint16_t *>(smem + 2048);        // up to 32 KB
-#pragma unroll 1
-        for (int cc = 0; cc < 2; ++cc) {
-            const int c = half * 2 + cc;  // 32-column chunk of this warp
-            uint32_t r[32];
-            dev::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32), r);
-            uint32_t word = 0, near = 0;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float m = __uint_as_float(r[j]) + bias_s[c * 32 + j];
-                word |= (m > 0.0f ? 1u : 0u) << j;
-                near |= (fabsf(m) < band_s[c * 32 + j] ? 1u : 0u) << j;
-            }
-            if (!valid || !row_nz[row])
-                near = 0u;
-            out_tile[row * (BN / 32) + c] = valid ? word : 0u;
-            if (near) {
-                int e = atomicAdd(&list_n, __popc(near));
-                for (uint32_t m = near; m; m &= m - 1, ++e)
-                    list[e] = (uint16_t)((row << 7) | (c * 32 + __ffs(m) - 1));
-            }
-        }
-        __syncthreads();
-        // FP32 re-check of the listed bits, 64 at a time: the four lanes of a
-        // group sum one 32-term chunk each as a chain from zero (histogram row
-        // and W row from L2), and the group's first lane combines them in the
-        // FP32 projection kernel's order ((c0 + c1) + c2) + c3 + b.
-        const int total = list_n;
-        const int g = t >> 2, q = t & 3;
-#pragma unroll 1
-        for (int e0 = 0; e0 < total; e0 += NTH / 4) {
-            const int e = e0 + g;
-            const bool act = e < total;
-            const uint32_t v = act ? (uint32_t)list[e] : 0u;
-            const int er = (int)(v >> 7), ec = (int)(v & 127u);
-            float part = 0.0f;
-            if (act) {
-                const float4 *fr = reinterpret_cast<const float4 *>(hist32 + (size_t)(m0 + er) * kHistDim) + 8 * q;
-                const float4 *wr = reinterpret_cast<const float4 *>(Wt32 + (size_t)(n0 + ec) * kHistDim) + 8 * q;
-                float4 fv[8], wv[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    fv[i] = __ldg(fr + i);
-                    wv[i] = __ldg(wr + i);
-                }
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    part = fmaf(fv[i].x, wv[i].x, part);
-                    part = fmaf(fv[i].y, wv[i].y, part);
-                    part = fmaf(fv[i].z, wv[i].z, part);
-                    part = fmaf(fv[i].w, wv[i].w, part);
-                }
-            }
-            const float c1 = __shfl_down_sync(0xffffffffu, part, 1);
-            const float c2 = __shfl_down_sync(0xffffffffu, part, 2);
-            const float c3 = __shfl_down_sync(0xffffffffu, part, 3);
-            if (act && q == 0) {
-                const float m32 = ((part + c1) + c2) + c3 + bias_s[ec];
-                uint32_t *o = &out_tile[er * (BN / 32) + (ec >> 5)];
-                if (m32 > 0.0f)
-                    atomicOr(o, 1u << (ec & 31));
-                else
-                    atomicAnd(o, ~(1u << (ec & 31)));
-            }
-        }
-        __syncthreads();
-        if (t == 0 && total)
-            atomicAdd(&status->rescued, (unsigned long long)total);
-        if (t < BM && m0 + t < n) {
-            uint32_t *dst = out + (size_t)(m0 + t) * (K / 32) + n0 / 32;
-#pragma unroll
-            for (int c = 0; c < BN / 32; ++c)
-                dst[c] = out_tile[t * (BN / 32) + c];
-        }
-    } else if (t == 0) {
+    auto give_up = [&]() {
+        abort_s = 1;
         dev::raise_flag(status, BD_FLAG_TIMEOUT);
-        if (issued >= 1)
-            dev::mbar_wait_bounded(&bar_mma0, 0);  // let issued MMAs drain before freeing TMEM
-        if (issued >= 2)
-            dev::mbar_wait_bounded(&bar_mma1, 0);
-        // the W loads land before the CTA leaves
-        dev::mbar_wait_bounded(&bar_b0, 0);
-        if (b_loads >= 2)
-            dev::mbar_wait_bounded(&bar_b1, 0);
+    };
+
+    if (warp == 0) {
+        // ---- MMA issue (one thread) ----
+        if (lane == 0) {
+            const uint32_t idesc = dev::umma_idesc_bf16_f32(BM, BN);
+            int j = 0;
+            bool ok = dev::mbar_wait_bounded(&bar_w, 0);
+            for (; ok && j < nb; ++j) {
+                const int s = j % STAGES, a = j % ACCS;
+                const uint32_t ps = (uint32_t)(j / STAGES) & 1u, pa = (uint32_t)(j / ACCS) & 1u;
+                if (*(volatile int *)&abort_s || !dev::mbar_wait_bounded(&bar_afull[s], ps) ||
+                    !dev::mbar_wait_bounded(&bar_accempty[a], pa ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                dev::tc_fence_after();
+                const uint8_t *Ah = sA + s * 4 * TILE, *Al = Ah + 2 * TILE;
+                const uint32_t d = tmem + (uint32_t)(a * BN);
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint64_t ahd = dev::umma_desc_sw128(dev::smem_u32(Ah + h * TILE + k * 32));
+                        const uint64_t ald = dev::umma_desc_sw128(dev::smem_u32(Al + h * TILE + k * 32));
+                        const uint64_t bhd = dev::umma_desc_sw128(dev::smem_u32(sW + h * TILE + k * 32));
+                        dev::umma_bf16(d, ahd, bhd, idesc, (h | k) ? 1u : 0u);
+                        dev::umma_bf16(d, ald, bhd, idesc, 1u);
+                        if (w_has_lo) {
+                            const uint64_t bld =
+                                dev::umma_desc_sw128(dev::smem_u32(sW + (2 + h) * TILE + k * 32));
+                            dev::umma_bf16(d, ahd, bld, idesc, 1u);
+                        }
+                    }
+                dev::umma_commit(&bar_aempty[s]);
+                dev::umma_commit(&bar_accfull[a]);
+            }
+            if (!ok)
+                give_up();
+            issued_s = j;
+        }
+        __syncwarp();
+    } else if (warp <= NCONV) {
+        // ---- histogram rows -> BF16 head / tail operand stages ----
+        const int cw = warp - 1;
+        const int h = lane >> 4, c = (lane & 15) >> 1, sub = lane & 1;  // values 4 lane .. 4 lane + 3
+        for (int j = 0; j < nb; ++j) {
+            const int s = j % STAGES;
+            const uint32_t ps = (uint32_t)(j / STAGES) & 1u;
+            // warp-uniform decisions: the warp meets in shuffles below
+            if (__any_sync(0xffffffffu, *(volatile int *)&abort_s != 0))
+                break;
+            // the MMAs of block j - STAGES have read this stage
+            if (!__all_sync(0xffffffffu, dev::mbar_wait_bounded(&bar_aempty[s], ps ^ 1u))) {
+                give_up();
+                break;
+            }
+            const int m0 = (bb0 + j) * BM;
+            uint8_t *Ah = sA + s * 4 * TILE, *Al = Ah + 2 * TILE;
+#pragma unroll
+            for (int q0 = 0; q0 < CROWS; q0 += CBATCH) {  // CBATCH rows in flight per lane
+                float4 v[CBATCH];
+#pragma unroll
+                for (int q = 0; q < CBATCH; ++q) {
+                    const int r = cw + NCONV * (q0 + q), row = m0 + r;
+                    v[q] = (q0 + q < CROWS && r < BM && row < n)
+                               ? __ldg(reinterpret_cast<const float4 *>(hist32 + (size_t)row * kHistDim) + lane)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int q = 0; q < CBATCH; ++q) {
+                    const int r = cw + NCONV * (q0 + q);
+                    if (q0 + q >= CROWS || r >= BM)
+                        break;
+                    const uint32_t off = (uint32_t)(h * TILE) + sw128_offset(r, c) + (uint32_t)(sub * 8);
+                    uint2 hi, lo;
+                    split4(v[q], hi, lo);
+                    *reinterpret_cast<uint2 *>(Ah + off) = hi;
+                    *reinterpret_cast<uint2 *>(Al + off) = lo;
+                    const uint32_t nzl = (__float_as_uint(v[q].x) | __float_as_uint(v[q].y) |
+                                          __float_as_uint(v[q].z) | __float_as_uint(v[q].w)) & 0x7fffffffu;
+                    const bool any = __any_sync(0xffffffffu, nzl != 0u);
+                    if (lane == 0)
+                        nz_s[j % NZSLOTS][r] = any ? 1 : 0;
+                }
+            }
+            dev::fence_proxy_async_smem();
+            dev::mbar_arrive(&bar_afull[s]);
+            if (lane == 0)  // this warp's zero-row flags are written (release to the epilogue)
+                dev::mbar_arrive(&bar_nz[j % NZSLOTS]);
+        }
+    } else {
+        // ---- epilogue: TMEM -> bits, FP32 re-check of the band ----
+        const int ew = warp - 1 - NCONV;
+        const int qd = warp & 3, row = qd * 32 + lane, c0 = (ew >> 2) * ECOLS;
+        static_assert(NEPI == 8 && ECOLS == 64, "two epilogue warps per TMEM lane quadrant");
+        uint16_t *list = list_s[ew];
+        uint32_t(*wds)[ECOLS / 32] = words_s[ew];
+        unsigned long long rescued = 0;
+        for (int j = 0; j < nb; ++j) {
+            const int a = j % ACCS;
+            const uint32_t pa = (uint32_t)(j / ACCS) & 1u;
+            if (__any_sync(0xffffffffu, *(volatile int *)&abort_s != 0))
+                break;
+            if (!__all_sync(0xffffffffu, dev::mbar_wait_bounded(&bar_accfull[a], pa))) {
+                give_up();
+                break;
+            }
+            dev::tc_fence_after();
+            // the converters' zero-row flags of this block (already complete:
+            // they were written before the MMAs could start)
+            if (!__all_sync(0xffffffffu,
+                            dev::mbar_wait_bounded(&bar_nz[j % NZSLOTS], (uint32_t)(j / NZSLOTS) & 1u))) {
+                give_up();
+                break;
+            }
+            const int m0 = (bb0 + j) * BM, kp = m0 + row;
+            const bool valid = kp < n && (kps == nullptr || dev::kp_valid(kps[kp]));
+            const bool row_nz = nz_s[j % NZSLOTS][row] != 0;
+            uint32_t r[ECOLS];
+            dev::tmem_ld64(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(a * BN + c0), r);
+            uint32_t near[ECOLS / 32];
+#pragma unroll
+            for (int cc = 0; cc < ECOLS / 32; ++cc) {
+                uint32_t wd = 0, nr = 0;
+#pragma unroll
+                for (int q4 = 0; q4 < 8; ++q4) {
+                    const float4 bv = *reinterpret_cast<const float4 *>(&bias_s[c0 + cc * 32 + 4 * q4]);
+                    const float4 dv = *reinterpret_cast<const float4 *>(&band_s[c0 + cc * 32 + 4 * q4]);
+                    const float bb[4] = {bv.x, bv.y, bv.z, bv.w}, db[4] = {dv.x, dv.y, dv.z, dv.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int q = 4 * q4 + u;
+                        const float m = __uint_as_float(r[cc * 32 + q]) + bb[u];
+                        wd |= (m > 0.0f ? 1u : 0u) << q;
+                        nr |= (fabsf(m) < db[u] ? 1u : 0u) << q;
+                    }
+                }
+                wds[lane][cc] = valid ? wd : 0u;
+                near[cc] = (valid && row_nz) ? nr : 0u;
+            }
+            dev::tc_fence_before();
+            dev::mbar_arrive(&bar_accempty[a]);
+            // rounds: the lanes whose bits fit (a prefix of the warp) list
+            // them; then 8 bits per pass, 4 lanes per bit (32-term chunk q of
+            // the margin each, all loads in flight), combined in the FP32
+            // projection kernel's order ((c0 + c1) + c2) + c3 + bias
+            __syncwarp();
+            for (;;) {
+                const uint32_t cnt = __popc(near[0]) + __popc(near[1]);
+                if (__all_sync(0xffffffffu, cnt == 0u))
+                    break;
+                uint32_t incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o)
+                        incl += u;
+                }
+                const bool fits = incl <= (uint32_t)LCAP;
+                const uint32_t total = __shfl_sync(0xffffffffu, incl, 31 - __clz(__ballot_sync(0xffffffffu, fits)));
+                if (fits) {
+                    uint32_t e = incl - cnt;
+#pragma unroll
+                    for (int cc = 0; cc < ECOLS / 32; ++cc) {
+                        for (uint32_t m = near[cc]; m; m &= m - 1, ++e)
+                            list[e] = (uint16_t)((lane << 7) | (c0 + cc * 32 + __ffs(m) - 1));
+                        near[cc] = 0u;
+                    }
+                }
+                __syncwarp();
+                const int g = lane >> 2, q = lane & 3;
+#pragma unroll 1
+                for (uint32_t e0 = 0; e0 < total; e0 += 8) {
+                    const uint32_t e = e0 + (uint32_t)g;
+                    const bool act = e < total;
+                    const uint32_t v = act ? (uint32_t)list[e] : 0u;
+                    const int er = (int)(v >> 7), ec = (int)(v & 127u);
+                    float part = 0.0f;
+                    if (act) {
+                        const float4 *fr = reinterpret_cast<const float4 *>(
+                                               hist32 + (size_t)(m0 + qd * 32 + er) * kHistDim) + 8 * q;
+                        const float4 *wr = reinterpret_cast<const float4 *>(
+                                               Wt32 + (size_t)(n0 + ec) * kHistDim) + 8 * q;
+                        float4 fv[8], wv[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            fv[i] = __ldg(fr + i);
+                            wv[i] = __ldg(wr + i);
+                        }
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            part = fmaf(fv[i].x, wv[i].x, part);
+                            part = fmaf(fv[i].y, wv[i].y, part);
+                            part = fmaf(fv[i].z, wv[i].z, part);
+                            part = fmaf(fv[i].w, wv[i].w, part);
+                        }
+                    }
+                    const float c1 = __shfl_down_sync(0xffffffffu, part, 1);
+                    const float c2 = __shfl_down_sync(0xffffffffu, part, 2);
+                    const float c3 = __shfl_down_sync(0xffffffffu, part, 3);
+                    if (act && q == 0) {
+                        const float m32 = ((part + c1) + c2) + c3 + bias_s[ec];
+                        const uint32_t bit = 1u << (ec & 31);
+                        if (m32 > 0.0f)
+                            atomicOr(&wds[er][(ec - c0) >> 5], bit);
+                        else
+                            atomicAnd(&wds[er][(ec - c0) >> 5], ~bit);
+                    }
+                }
+                rescued += total;  // counted on every lane; lane 0's copy is added below
+                __syncwarp();
+            }
+            if (kp < n) {
+                uint32_t *dst = out + (size_t)kp * (K / 32) + (n0 + c0) / 32;
+#pragma unroll
+                for (int cc = 0; cc < ECOLS / 32; ++cc)
+                    dst[cc] = wds[lane][cc];
+            }
+            __syncwarp();
+        }
+        if (lane == 0 && rescued)
+            atomicAdd(&status->rescued, rescued);
+    }
+
+    // leave together; after a timeout, the MMAs issued and the W loads land
+    // before TMEM is freed and the CTA exits
+    __syncthreads();
+    if (t == 0 && abort_s) {
+        const int j = issued_s - 1;
+        if (j >= 0)
+            dev::mbar_wait_bounded(&bar_accfull[j % ACCS], (uint32_t)(j / ACCS) & 1u);
+        dev::mbar_wait_bounded(&bar_w, 0);
     }
     dev::tc_fence_before();
     __syncthreads();
+    dev::tc_fence_after();
     if (warp == 0)
-        dev::tmem_dealloc(tmem, BN);
+        dev::tmem_dealloc(tmem, ACCS * BN);
 }
 
 }  // namespace
 
 cudaError_t prepare_hs_proj_tc()
 {
-    cudaError_t e = cudaFuncSetAttribute(hs_proj_tc_kernel<true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem_bytes(true));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(hs_proj_tc_kernel<false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(false));
-    return e;
+    return cudaFuncSetAttribute(hs_proj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_bytes());
 }
 
 cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const float *hist, int n, uint32_t *out,
                               DeviceStatus *status, cudaStream_t st, const bd_keypoint *kps)
 {
-    dim3 grid(p->nbits / BN, (n + BM - 1) / BM);
-    // one wave or less (two CTAs per SM): both W phases resident, lowest
-    // latency; more: the single-stage variant, with more shared memory left
-    // to L1
+    if (n <= 0)
+        return cudaSuccess;
+    // one CTA per SM: the 128-bit chunks share the SMs, each chunk's CTAs
+    // split its 128-keypoint blocks into contiguous ranges
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const bool both_b = (long long)grid.x * grid.y <= 2LL * sms;
-    cudaError_t e = launch_pdl(both_b ? hs_proj_tc_kernel<true> : hs_proj_tc_kernel<false>, grid,
-                               dim3(NTH), (size_t)smem_bytes(both_b), st, p->tmap_w_hi,
-                               p->tmap_w_lo, p->w_has_lo ? 1 : 0, hist, (const float *)p->d_Wt,
-                               (const float *)p->d_bias, (const float *)p->d_band, kps, n,
-                               p->nbits, out, status);
+    const int chunks = p->nbits / BN;
+    const int nblocks = (n + BM - 1) / BM;
+    int cpc = sms / chunks;
+    if (cpc < 1)
+        cpc = 1;
+    if (cpc > nblocks)
+        cpc = nblocks;
+    cudaError_t e = launch_pdl(hs_proj_tc_kernel, dim3(chunks * cpc), dim3(NTH), (size_t)smem_bytes(),
+                               st, p->tmap_w_hi, p->tmap_w_lo, p->w_has_lo ? 1 : 0, hist,
+                               (const float *)p->d_Wt, (const float *)p->d_bias,
+                               (const float *)p->d_band, kps, n, p->nbits, out, status, nblocks, cpc);
     if (e != cudaSuccess)
         return e;
     trace_kernel(st, "hs_proj_tc");

@@ -18,10 +18,15 @@
 //   - the hinge loss of each descriptor.
 //  backward (mining held fixed)
 //   - dL/dr from the active hinges; a negative collects one term per triplet
-//     that mined it (hard-negative mining makes hubs: one negative can be the
-//     hardest of ten thousand anchors, its dL/dr a sum of that many terms
-//     near +-1), so negatives collect in FP64 atomics and are rounded to FP32
-//     once, by a pass that also clears the accumulator for the next step;
+//     that mined it.  Hard-negative mining makes hubs (one negative can be
+//     the hardest of ten thousand anchors, its dL/dr a sum of that many terms
+//     near +-1, which FP32 atomics round to 1e-3), so the negatives mined more
+//     than kHubMin times (at most n / kHubMin of them) collect the responses
+//     r in [-1, 1] as 64-bit fixed point (r 2^40, exact for |r| >= 2^-16: an
+//     exact, order-independent sum, |sum| <= n <= 2^20 far from overflow)
+//     with integer atomics in a compact per-hub accumulator, converted and
+//     scaled by the loss weight at the end (which also clears it); the
+//     others keep FP32 atomics;
 //   - BAD: dtheta column sums, and the box adjoint as a 2-D difference array
 //     per patch (4 corner updates per box, then a 2-D prefix sum);
 //   - the column sums over all 3n rows (dtheta, db) cancel heavily (anchors
@@ -45,7 +50,10 @@ struct bd_train {
     int32_t *mining = nullptr;  // [4][n]
     float *dr_bad = nullptr, *dr_hs = nullptr, *Wt = nullptr;
     double *loss_acc = nullptr;  // [2] losses, then [Kb] dtheta and [Kh] db accumulators
-    double *drn_acc = nullptr;   // [n][Kb] then [n][Kh]: negatives' dL/dr, zero between steps
+    int *hub = nullptr;            // [2][n] times mined (zero between steps), then hub index or -1
+    int *n_hubs = nullptr;         // [2]
+    long long *hub_acc = nullptr;  // [2][max_hubs][Kmax]: hubs' sum of r x 2^40, zero between steps
+    int max_hubs = 0;
     void *tc_scratch = nullptr;       // FP8 codes and partials of the top-2 searches
     uint2 *keys = nullptr;            // [2][n] top-2 keys (anchors, positives)
     unsigned int *arrivals = nullptr; // zeroed per-block arrival counters
@@ -55,6 +63,7 @@ namespace bd {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int kHubMin = 64;  // a negative mined more often than this is a hub
 
 // 2^32 (the fixed-point scale of the BAD summed-area tables).
 constexpr double kFix = 4294967296.0;
@@ -191,7 +200,8 @@ __global__ void __launch_bounds__(256) train_loss_kernel(const float *__restrict
                                                          const float *__restrict__ gw,
                                                          double *__restrict__ loss_acc,
                                                          float *__restrict__ dr,
-                                                         double *__restrict__ drn)
+                                                         const int *__restrict__ hub,
+                                                         long long *__restrict__ hub_acc)
 {
     constexpr int Q = K / 32;
     const int lane = threadIdx.x & 31;
@@ -229,25 +239,75 @@ __global__ void __launch_bounds__(256) train_loss_kernel(const float *__restrict
         const float rx = xs ? rp[q] : ra[q];
         dr[(size_t)i * K + k] = on ? w * (-rp[q] + (xs ? 0.f : rn[q])) : 0.f;
         dr[(size_t)(n + i) * K + k] = on ? w * (-ra[q] + (xs ? rn[q] : 0.f)) : 0.f;
-        if (on)
-            atomicAdd(drn + (size_t)nstar[i] * K + k, (double)(w * rx));
+        if (on) {
+            const int hb = hub[nstar[i]];
+            if (hb < 0)
+                atomicAdd(dr + (size_t)nrow * K + k, w * rx);
+            else
+                atomicAdd(reinterpret_cast<unsigned long long *>(hub_acc + (size_t)hb * K + k),
+                          (unsigned long long)__float2ll_rn(rx * 1099511627776.0f));  // r 2^40
+        }
     }
 }
 
-// Negatives' dL/dr from their FP64 accumulators (BAD rows [0, nb), then
-// HashSIFT rows), which are cleared for the next step.
-__global__ void train_drn_finish_kernel(double *__restrict__ acc, size_t nb, size_t nh,
-                                        float *__restrict__ dr_bad_neg,
-                                        float *__restrict__ dr_hs_neg)
+// Times each negative is mined, hub[d][nstar_d[i]] += 1 (d = i / n), as far
+// as the threshold: only "more than kHubMin" matters, so a counter past it
+// is not incremented further (a hub mined by ten thousand anchors would
+// otherwise serialise them on one address); the lanes of a warp with the
+// same negative add once, together.
+__global__ void train_hub_count_kernel(const int32_t *__restrict__ mining, int n,
+                                       int *__restrict__ hub)
 {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb + nh;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const double v = acc[i];
-        acc[i] = 0.0;
-        if (i < nb)
-            dr_bad_neg[i] = (float)v;
-        else
-            dr_hs_neg[i - nb] = (float)v;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = i < 2 * n;
+    const int d = act ? i / n : 0;
+    const int key = act ? d * n + mining[(size_t)(2 * d) * n + (i % n)] : -1;
+    const unsigned same = __match_any_sync(FULL, key);
+    if (act && (threadIdx.x & 31) == __ffs(same) - 1 &&
+        *reinterpret_cast<volatile int *>(hub + key) <= kHubMin)
+        atomicAdd(hub + key, __popc(same));
+}
+
+// The count becomes the hub index (in order of arrival) or -1.
+__global__ void train_hub_assign_kernel(int n, int *__restrict__ hub, int *__restrict__ n_hubs)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 2 * n) {
+        const int d = i / n;
+        hub[i] = hub[i] > kHubMin ? atomicAdd(n_hubs + d, 1) : -1;
+    }
+}
+
+// Hub rows of dL/dr = w (sum of r 2^40) 2^-40: lane l of a warp takes
+// negative (d, j) = 32 w + l, resets its mark to a zero count for the next
+// step's mining, and the warp converts the rows of its hubs together (lanes
+// over the columns); the accumulator is cleared.
+__global__ void train_hub_finish_kernel(int n, int kb, int kh, int *__restrict__ hub,
+                                        long long *__restrict__ hub_acc, int max_hubs,
+                                        const float *__restrict__ gw, float *__restrict__ dr_bad,
+                                        float *__restrict__ dr_hs)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+    int hb = -1;
+    if (i < 2 * n) {
+        hb = hub[i];
+        hub[i] = 0;
+    }
+    const int kmax = kb > kh ? kb : kh;
+    for (unsigned m = __ballot_sync(FULL, hb >= 0); m; m &= m - 1) {
+        const int src = __ffs(m) - 1;
+        const int ii = i - lane + src;
+        const int h = __shfl_sync(FULL, hb, src);
+        const int d = ii / n, j = ii % n;
+        const int K = d == 0 ? kb : kh;
+        // descriptor d's hubs start at d max_hubs kmax, each K entries (as train_loss writes them)
+        long long *acc = hub_acc + (size_t)d * max_hubs * kmax + (size_t)h * K;
+        float *row = d == 0 ? dr_bad + (size_t)(2 * n + j) * kb : dr_hs + (size_t)(2 * n + j) * kh;
+        const float w = gw[d];
+        for (int k = lane; k < K; k += 32) {
+            row[k] = w * (float)((double)acc[k] * 0x1p-40);
+            acc[k] = 0;
+        }
     }
 }
 
@@ -603,8 +663,13 @@ bd_status bd_train_create(bd_ctx *ctx, const bd_bad_params *bad, int hs_bits, in
     if (e == cudaSuccess) e = cudaMalloc(&tr->dr_hs, sizeof(float) * R * tr->kh);
     if (e == cudaSuccess) e = cudaMalloc(&tr->Wt, sizeof(float) * 128 * tr->kh);
     if (e == cudaSuccess) e = cudaMalloc(&tr->loss_acc, sizeof(double) * (2 + tr->kb + tr->kh));
-    if (e == cudaSuccess) e = cudaMalloc(&tr->drn_acc, sizeof(double) * (size_t)n * (tr->kb + tr->kh));
-    if (e == cudaSuccess) e = cudaMemset(tr->drn_acc, 0, sizeof(double) * (size_t)n * (tr->kb + tr->kh));
+    tr->max_hubs = n / (kHubMin + 1) + 1;
+    const size_t hub_words = 2 * (size_t)tr->max_hubs * (size_t)std::max(tr->kb, tr->kh);
+    if (e == cudaSuccess) e = cudaMalloc(&tr->hub, sizeof(int) * 2 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemset(tr->hub, 0, sizeof(int) * 2 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&tr->n_hubs, sizeof(int) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&tr->hub_acc, sizeof(long long) * hub_words);
+    if (e == cudaSuccess) e = cudaMemset(tr->hub_acc, 0, sizeof(long long) * hub_words);
     if (prev >= 0 && prev != ctx->device)
         cudaSetDevice(prev);
     if (e != cudaSuccess) {
@@ -627,7 +692,8 @@ void bd_train_destroy(bd_train *tr)
     for (void *p : {(void *)tr->r_bad, (void *)tr->r_hs, (void *)tr->h, (void *)tr->norm,
                     (void *)tr->bits_bad, (void *)tr->bits_hs, (void *)tr->tc_scratch,
                     (void *)tr->keys, (void *)tr->arrivals, (void *)tr->mining, (void *)tr->dr_bad,
-                    (void *)tr->dr_hs, (void *)tr->Wt, (void *)tr->loss_acc, (void *)tr->drn_acc})
+                    (void *)tr->dr_hs, (void *)tr->Wt, (void *)tr->loss_acc, (void *)tr->hub,
+                    (void *)tr->n_hubs, (void *)tr->hub_acc})
         if (p)
             cudaFree(p);
     if (prev >= 0 && prev != tr->ctx->device)
@@ -698,10 +764,10 @@ bd_status bd_train_forward(bd_ctx *ctx, bd_train *tr, const float *patches, cons
             const int32_t *ns = tr->mining + (size_t)(2 * d) * n, *xs = ns + n;
             if (K == 256)
                 train_loss_kernel<256><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, nullptr, tr->loss_acc + d,
-                                                               nullptr, nullptr);
+                                                               nullptr, nullptr, nullptr);
             else
                 train_loss_kernel<512><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, nullptr, tr->loss_acc + d,
-                                                               nullptr, nullptr);
+                                                               nullptr, nullptr, nullptr);
             trace_kernel(st, "train_loss");
         }
         train_loss_finish_kernel<<<1, 32, 0, st>>>(tr->loss_acc, loss);
@@ -735,7 +801,20 @@ bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, con
     const float inv_scale = 1.0f / (255.0f * tr->T), inv_t = 1.0f / tr->T;
     const bd_bad_params *bp = tr->bad;
     cudaError_t e = cudaSuccess;
-    // dL/dr: negatives' rows collect in drn_acc (zero between steps)
+    // dL/dr: negatives' rows collect with atomics (FP32, or the hubs' fixed
+    // point), so the FP32 rows start at zero; then the hubs of this mining
+    e = cudaMemsetAsync(tr->dr_bad + (size_t)2 * n * tr->kb, 0, sizeof(float) * n * tr->kb, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(tr->dr_hs + (size_t)2 * n * tr->kh, 0, sizeof(float) * n * tr->kh, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(tr->n_hubs, 0, sizeof(int) * 2, st);
+    if (e == cudaSuccess) {
+        train_hub_count_kernel<<<(2 * n + 255) / 256, 256, 0, st>>>(tr->mining, n, tr->hub);
+        trace_kernel(st, "train_hub_count");
+        train_hub_assign_kernel<<<(2 * n + 255) / 256, 256, 0, st>>>(n, tr->hub, tr->n_hubs);
+        trace_kernel(st, "train_hub_assign");
+        e = cudaGetLastError();
+    }
     double *dth_acc = tr->loss_acc + 2, *db_acc = dth_acc + tr->kb;
     if (e == cudaSuccess)
         e = cudaMemsetAsync(dth_acc, 0, sizeof(double) * (tr->kb + tr->kh), st);
@@ -749,20 +828,19 @@ bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, con
             const int K = d == 0 ? tr->kb : tr->kh;
             const float tau = d == 0 ? tr->tau_bad : tr->tau_hs;
             const int32_t *ns = tr->mining + (size_t)(2 * d) * n, *xs = ns + n;
-            double *drn = tr->drn_acc + (d == 0 ? 0 : (size_t)n * tr->kb);
+            const int *hub = tr->hub + (size_t)d * n;
+            long long *hacc = tr->hub_acc + (size_t)d * tr->max_hubs * (size_t)std::max(tr->kb, tr->kh);
             if (K == 256)
                 train_loss_kernel<256><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, grad_loss + d, nullptr,
-                                                               drp, drn);
+                                                               drp, hub, hacc);
             else
                 train_loss_kernel<512><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, grad_loss + d, nullptr,
-                                                               drp, drn);
+                                                               drp, hub, hacc);
             trace_kernel(st, "train_dr");
         }
-        train_drn_finish_kernel<<<sm * 8, 256, 0, st>>>(tr->drn_acc, (size_t)n * tr->kb,
-                                                        (size_t)n * tr->kh,
-                                                        tr->dr_bad + (size_t)2 * n * tr->kb,
-                                                        tr->dr_hs + (size_t)2 * n * tr->kh);
-        trace_kernel(st, "train_drn_finish");
+        train_hub_finish_kernel<<<(2 * n + 255) / 256, 256, 0, st>>>(
+            n, tr->kb, tr->kh, tr->hub, tr->hub_acc, tr->max_hubs, grad_loss, tr->dr_bad, tr->dr_hs);
+        trace_kernel(st, "train_hub_finish");
         // BAD: dtheta and the patch gradient (written, not added)
         if (tr->kb == 256)
             train_bad_bwd_kernel<256><<<grid_rows(rows, sm, 12), 128, 0, st>>>(
@@ -788,7 +866,7 @@ bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, con
         trace_kernel(st, "train_hs_bwd");
         e = cudaGetLastError();
     }
-    note_launches(9);
+    note_launches(11);
     (void)R;
     if (prev >= 0 && prev != ctx->device)
         cudaSetDevice(prev);

@@ -197,17 +197,17 @@ def test_fused_fp32_projection_equals_tensor_core_path(gpu_ctx, hs_mode):
 
 
 @pytest.mark.parametrize("cfg", [(8, 4, 0, 4, 0, 0, 0), (4, 2, 1, 1, 1, 0, 1), (32, 6, 2, 4, 1, 1, 0),
-                                 (8, 4, 3, 4, 1, 1, 1), (4, 3, 3, 1, 0, 0, 0)])
+                                 (8, 4, 3, 4, 1, 1, 1), (4, 3, 3, 1, 0, 0, 0), (8, 5, 4, 4, 1, 2, 0)])
 def test_timeline_respects_dependencies(gpu_ctx, cfg):
     """The item timeline lists every queued item once, and no item starts
-    before the items it depends on ended: pass-2 tiles after all pass-1 tiles
-    of their image, BAD items after all pass-2 tiles of their image,
-    projection tiles after the HashSIFT items of their 32 keypoints were
-    claimed.  Recording it does not change the descriptors."""
+    before what it depends on: an integral tile after the tiles to its left
+    and above were claimed (they publish their aggregates before they
+    wait), BAD items after all tiles of their image ended, projection tiles
+    after the HashSIFT items of their 32 keypoints were claimed.  Recording
+    it does not change the descriptors."""
     import math
     import torch
-    from paper_2108_08380_gb300 import (BD_ITEM_BAD, BD_ITEM_HASHSIFT, BD_ITEM_II_PASS1,
-                                        BD_ITEM_II_PASS2, BD_ITEM_PROJ)
+    from paper_2108_08380_gb300 import BD_ITEM_BAD, BD_ITEM_HASHSIFT, BD_ITEM_II_TILE, BD_ITEM_PROJ
     imgs, kps, offs, bad, hs = _small_batch(seed=21)
     bp, hp = gpu_ctx.bad_params(bad), gpu_ctx.hs_params(hs)
     dimgs = [_dev(im) for im in imgs]
@@ -227,7 +227,9 @@ def test_timeline_respects_dependencies(gpu_ctx, cfg):
     assert gpu_ctx.sync_status() == 0
     assert np.array_equal(_u32(ob), _u32(ob0)) and np.array_equal(_u32(oh), _u32(oh0))
 
-    tiles = [math.ceil(im.shape[1] / 128) * math.ceil(im.shape[0] / 32) for im in imgs]
+    ntx = [math.ceil(im.shape[1] / 128) for im in imgs]
+    nty = [math.ceil(im.shape[0] / 32) for im in imgs]
+    tiles = [a * b for a, b in zip(ntx, nty)]
     tile_img = np.repeat(np.arange(len(imgs)), tiles)
     counts = np.diff(offs)
     bad_items = [math.ceil(c / it) for c in counts]
@@ -235,7 +237,7 @@ def test_timeline_respects_dependencies(gpu_ctx, cfg):
     n_hs = math.ceil(n / hm)
     ptiles = 16 if half else 8  # projection tiles per 32 keypoints at 256 bits
     n_proj = math.ceil(n / 32) * ptiles if fused else 0
-    expect = {BD_ITEM_II_PASS1: sum(tiles), BD_ITEM_II_PASS2: sum(tiles), BD_ITEM_BAD: sum(bad_items),
+    expect = {BD_ITEM_II_TILE: sum(tiles), BD_ITEM_BAD: sum(bad_items),
               BD_ITEM_HASHSIFT: n_hs, BD_ITEM_PROJ: n_proj}
     assert len(ev) == sum(expect.values())
     by = {}
@@ -246,13 +248,18 @@ def test_timeline_respects_dependencies(gpu_ctx, cfg):
         by[kind] = e
     assert np.all(ev["t_claim"] <= ev["t_ready"]) and np.all(ev["t_ready"] <= ev["t_end"])
     assert np.all(ev["cta"] >= 0) and np.all(ev["sm"] >= 0)
-    p1, p2, bd = by[BD_ITEM_II_PASS1], by[BD_ITEM_II_PASS2], by[BD_ITEM_BAD]
+    tl, bd = by[BD_ITEM_II_TILE], by[BD_ITEM_BAD]
+    first = np.concatenate([[0], np.cumsum(tiles)])
     for i in range(len(imgs)):
-        end1 = p1["t_end"][tile_img == i].max()
-        assert np.all(p2["t_ready"][tile_img == i] >= end1)
+        mine = tl[first[i]:first[i + 1]]
+        claim = mine["t_claim"].reshape(nty[i], ntx[i])
+        ready = mine["t_ready"].reshape(nty[i], ntx[i])
+        for ty in range(nty[i]):
+            for tx in range(ntx[i]):
+                need = [claim[ty, :tx].max(initial=0), claim[:ty].max(initial=0)]
+                assert ready[ty, tx] >= max(need)
         if bad_items[i]:
-            end2 = p2["t_end"][tile_img == i].max()
-            assert np.all(bd["t_ready"][bad_img == i] >= end2)
+            assert np.all(bd["t_ready"][bad_img == i] >= mine["t_end"].max())
     if fused:
         hsi, pr = by[BD_ITEM_HASHSIFT], by[BD_ITEM_PROJ]
         for g in range(math.ceil(n / 32)):
