@@ -80,6 +80,8 @@ struct BatchKernelArgs {
     uint32_t *bad_out;
     float spacing;
     float *hist;
+    uint8_t *hist16;          // the histograms split into the tcgen05 projection's operand image, or NULL
+    uint8_t *hist_nz;         // per keypoint: the histogram is not all zero (with hist16)
     const bd_keypoint *kps;
     DeviceStatus *status;
     unsigned long long wait_ns;  // limit of every dependency wait (GPU timer)
@@ -458,6 +460,14 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                 const BatchImageDev &I = A.imgs[im];
                 dev::hs_hist_image_cta<false>(U.h[0], A.img_ptr[im], I.w, I.h, I.pitch, A.kps[k],
                                        A.spacing, A.hist, (size_t)k, A.status, A.hs_flags);
+                if (A.hist16) {
+                    // thread t wrote entry t of the row: split it for the projection
+                    const float x = A.hist[(size_t)k * kHistDim + t];
+                    dev::split_store(A.hist16, (size_t)k, t, x);
+                    const int nz = __syncthreads_or(x != 0.0f);
+                    if (t == 0)
+                        A.hist_nz[k] = (uint8_t)(nz ? 1 : 0);
+                }
                 if (A.proj_items && t == 0) {
                     __threadfence();
                     atomicAdd(A.hs_group_done + (k >> 5), 1u);
@@ -471,6 +481,20 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
                     dev::hs_hist_image_warp<false>(U.h[t >> 5], A.img_ptr[im], I.w, I.h, I.pitch,
                                             A.kps[k], A.spacing, A.hist, (size_t)k, A.status,
                                             A.hs_flags);
+                    if (A.hist16) {
+                        // lane l wrote entries l, 32 + l, 64 + l, 96 + l: split them
+                        const int lane = t & 31;
+                        bool nz = false;
+#pragma unroll
+                        for (int ci = 0; ci < 4; ++ci) {
+                            const float x = A.hist[(size_t)k * kHistDim + ci * 32 + lane];
+                            dev::split_store(A.hist16, (size_t)k, ci * 32 + lane, x);
+                            nz |= x != 0.0f;
+                        }
+                        nz = __any_sync(0xffffffffu, nz);
+                        if (lane == 0)
+                            A.hist_nz[k] = (uint8_t)(nz ? 1 : 0);
+                    }
                     if (A.proj_items && (t & 31) == 0) {
                         __threadfence();
                         atomicAdd(A.hs_group_done + (k >> 5), 1u);
@@ -629,6 +653,8 @@ struct bd_batch {
     // zero between launches
     unsigned int *d_counters = nullptr;
     float *d_hist = nullptr;
+    uint8_t *d_hist16 = nullptr;  // pre-split BF16 operand image for the tcgen05 projection
+    uint8_t *d_hist_nz = nullptr;
     bd_batch_config cfg = {8, 0, 1, 4, 0, 0, 0};
     unsigned long long wait_ns = 0;  // 0: the default limit
     int max_ctas_per_sm = 0;
@@ -791,6 +817,10 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     A.spacing = b->hs ? b->hs->spacing : 1.f;
     A.hs_flags = b->hs ? b->hs->variant : 0;
     A.hist = b->d_hist;
+    // the tcgen05 projection follows: the histograms are also written split
+    const bool tc_proj = b->hs && hs_out && !fused && b->hs->precision != BD_HS_FP32;
+    A.hist16 = tc_proj ? b->d_hist16 : nullptr;
+    A.hist_nz = tc_proj ? b->d_hist_nz : nullptr;
     A.kps = kps;
     A.status = ctx->status;
     A.wait_ns = b->wait_ns ? b->wait_ns : kDefaultWaitNs;
@@ -843,8 +873,8 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
         if (p->precision == BD_HS_FP32)
             e = launch_hs_proj_fp32(p, b->d_hist, b->n_kp, hs_out, st, kps);
         else
-            e = launch_hs_proj_tc(p, b->d_hist, b->n_kp, hs_out, ctx->status, st,
-                                  kps);
+            e = launch_hs_proj_tc(p, b->d_hist, b->n_kp, hs_out, ctx->status, st, kps,
+                                  b->d_hist16, b->d_hist_nz);
         ++nk;
         if (e != cudaSuccess)
             return cuda_err(ctx, e, "bd_describe_batch: projection kernel");
@@ -968,6 +998,9 @@ bd_status bd_batch_create(bd_ctx *ctx, const bd_bad_params *bad, const bd_hs_par
         if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(unsigned int) * ncount);
         if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, sizeof(unsigned int) * ncount);
         if (e == cudaSuccess && hs) e = cudaMalloc(&b->d_hist, sizeof(float) * kHistDim * (size_t)(b->n_kp > 0 ? b->n_kp : 1));
+        const size_t blocks128 = (size_t)(b->n_kp + 127) / 128;
+        if (e == cudaSuccess && hs) e = cudaMalloc(&b->d_hist16, 65536 * (blocks128 > 0 ? blocks128 : 1));
+        if (e == cudaSuccess && hs) e = cudaMalloc(&b->d_hist_nz, (size_t)(b->n_kp > 0 ? b->n_kp : 1));
         if (e == cudaSuccess) e = cudaMemcpy(b->d_imgs, b->imgs.data(), sizeof(BatchImageDev) * n_img, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
         int o[6] = {0, 0, 0, 0, 0, 0};
@@ -1009,6 +1042,8 @@ void bd_batch_destroy(bd_batch *b)
     if (b->d_carry) cudaFree(b->d_carry);
     if (b->d_counters) cudaFree(b->d_counters);
     if (b->d_hist) cudaFree(b->d_hist);
+    if (b->d_hist16) cudaFree(b->d_hist16);
+    if (b->d_hist_nz) cudaFree(b->d_hist_nz);
     if (b->d_events) cudaFree(b->d_events);
     if (b->d_mscratch) cudaFree(b->d_mscratch);
     if (b->d_marrivals) cudaFree(b->d_marrivals);

@@ -169,8 +169,12 @@ cudaError_t launch_hs_proj_fp32_raw(const float *W, const float *bias, int K, co
                                     cudaStream_t st);
 // raises the projection kernel's dynamic shared-memory limit (per device, at set-up)
 cudaError_t prepare_hs_proj_tc();
+// a16 (optional): the histograms already split into the BF16 operand image
+// (split_offset), with nz[k] != 0 for rows that are not all zero; the kernel
+// then copies each block's operands instead of converting the FP32 rows
 cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const float *hist, int n, uint32_t *out,
-                              DeviceStatus *status, cudaStream_t st, const bd_keypoint *kps);
+                              DeviceStatus *status, cudaStream_t st, const bd_keypoint *kps,
+                              const uint8_t *a16 = nullptr, const uint8_t *nz = nullptr);
 
 size_t match_scratch_bytes(int nq, int nt, int nbits, int sm_count);
 // tensor-core matching: scratch for the FP8 codes and split partials
@@ -320,6 +324,40 @@ __device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *m
         " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(smem_dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Non-tensor bulk copy global -> shared (16-byte aligned addresses, size a
+// multiple of 16), completing `bytes` of the mbarrier's transaction count.
+__device__ __forceinline__ void bulk_load(void *smem_dst, const void *gsrc, uint32_t bytes,
+                                          uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(gsrc)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Byte offset of value v (0..127) of histogram row k in the pre-split BF16
+// operand image the tcgen05 projection copies per block of 128 rows: block
+// k / 128 at 64 KB steps holds [head K0][head K1][tail K0][tail K1] tiles of
+// 128 rows x 128 bytes in the 128-byte-swizzled K-major layout (16-byte
+// chunk c of row r at position c ^ (r mod 8)); add 32 KB for the tail.
+__device__ __forceinline__ size_t split_offset(size_t k, int v)
+{
+    const int r = (int)(k & 127), h = v >> 6, c = (v & 63) >> 3, e = v & 7;
+    return (k >> 7) * 65536 + (size_t)h * 16384 + (size_t)r * 128 + (size_t)(((c ^ (r & 7)) << 4) + e * 2);
+}
+
+// Writes value x of row k, v into the pre-split image: BF16 head and tail
+// (x = hi + lo + O(2^-16 |x|)).
+__device__ __forceinline__ void split_store(uint8_t *a16, size_t k, int v, float x)
+{
+    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+    const size_t o = split_offset(k, v);
+    *reinterpret_cast<__nv_bfloat16 *>(a16 + o) = hi;
+    *reinterpret_cast<__nv_bfloat16 *>(a16 + o + 32768) = lo;
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t *smem_slot, uint32_t ncols)

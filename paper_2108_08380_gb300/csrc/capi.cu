@@ -604,7 +604,7 @@ bd_status bd_hs_params_create(bd_ctx *ctx, int nbits, const float *W, const floa
             const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
             Whi[(size_t)k * 128 + i] = hi;
             Wlo[(size_t)k * 128 + i] = lo;
-            has_lo = has_lo || __bfloat162float(lo) != 0.0f;
+            has_lo = has_lo || __bfloat162float(hi) != v;  // W is exactly BF16 only without this
             nn += (double)v * (double)v;
         }
         // With x = hi + lo + d, |d| <= 2^-16 |x| (two BF16 roundings), the three

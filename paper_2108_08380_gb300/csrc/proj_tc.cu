@@ -31,7 +31,10 @@
 //    plus the bias; a row of zeros (a patch without gradients) projects to
 //    exactly the bias on both paths and is never re-checked.
 // So the conversion of block j + 1, the MMAs of block j and the epilogue of
-// block j - 1 overlap.  Every mbarrier wait is bounded; a wait that gives up
+// block j - 1 overlap.  When the histogram producer has already written the
+// rows in that operand image (the batched kernel does, as it finishes each
+// histogram), one thread copies each block's 64 KB stage with bulk copies
+// instead, and the zero-row flags come with it: no conversion remains.  Every mbarrier wait is bounded; a wait that gives up
 // raises BD_FLAG_TIMEOUT and stops every role at its next block; the CTA
 // then waits (bounded) for the MMAs it issued and the W loads before it
 // frees TMEM and returns.
@@ -82,7 +85,8 @@ __global__ void __launch_bounds__(NTH, 1) hs_proj_tc_kernel(
     const float *__restrict__ hist32, const float *__restrict__ Wt32,
     const float *__restrict__ bias, const float *__restrict__ band,
     const bd_keypoint *__restrict__ kps, int n, int K, uint32_t *__restrict__ out,
-    DeviceStatus *status, int nblocks, int cpc)
+    DeviceStatus *status, int nblocks, int cpc, const uint8_t *__restrict__ a16,
+    const uint8_t *__restrict__ nzg)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
@@ -108,7 +112,8 @@ __global__ void __launch_bounds__(NTH, 1) hs_proj_tc_kernel(
     if (t == 0) {
         dev::mbar_init(&bar_w, 1);
         for (int s = 0; s < STAGES; ++s) {
-            dev::mbar_init(&bar_afull[s], 32 * NCONV);
+            // converter threads arrive, or the copying thread with the bytes
+            dev::mbar_init(&bar_afull[s], a16 ? 1 : 32 * NCONV);
             dev::mbar_init(&bar_aempty[s], 1);
         }
         for (int a = 0; a < ACCS; ++a) {
@@ -191,6 +196,27 @@ __global__ void __launch_bounds__(NTH, 1) hs_proj_tc_kernel(
             issued_s = j;
         }
         __syncwarp();
+    } else if (warp <= NCONV && a16) {
+        // ---- pre-split operands: bulk copies of each block's stage ----
+        if (warp == 1 && lane == 0) {
+            for (int j = 0; j < nb; ++j) {
+                const int s = j % STAGES;
+                const uint32_t ps = (uint32_t)(j / STAGES) & 1u;
+                if (*(volatile int *)&abort_s)
+                    break;
+                if (!dev::mbar_wait_bounded(&bar_aempty[s], ps ^ 1u)) {
+                    give_up();
+                    break;
+                }
+                uint8_t *dst = sA + s * 4 * TILE;
+                const uint8_t *src = a16 + (size_t)(bb0 + j) * (4 * TILE);
+                dev::mbar_arrive_expect_tx(&bar_afull[s], 4 * TILE);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    dev::bulk_load(dst + q * TILE, src + q * TILE, TILE, &bar_afull[s]);
+            }
+        }
+        __syncwarp();
     } else if (warp <= NCONV) {
         // ---- histogram rows -> BF16 head / tail operand stages ----
         const int cw = warp - 1;
@@ -253,21 +279,23 @@ __global__ void __launch_bounds__(NTH, 1) hs_proj_tc_kernel(
             const uint32_t pa = (uint32_t)(j / ACCS) & 1u;
             if (__any_sync(0xffffffffu, *(volatile int *)&abort_s != 0))
                 break;
+            // the row's keypoint and zero-row flag, loaded before the wait
+            const int m0 = (bb0 + j) * BM, kp = m0 + row;
+            const bool valid = kp < n && (kps == nullptr || dev::kp_valid(kps[kp]));
+            const uint8_t nz_row = (a16 && kp < n) ? __ldg(nzg + kp) : (uint8_t)0;
             if (!__all_sync(0xffffffffu, dev::mbar_wait_bounded(&bar_accfull[a], pa))) {
                 give_up();
                 break;
             }
             dev::tc_fence_after();
             // the converters' zero-row flags of this block (already complete:
-            // they were written before the MMAs could start)
-            if (!__all_sync(0xffffffffu,
-                            dev::mbar_wait_bounded(&bar_nz[j % NZSLOTS], (uint32_t)(j / NZSLOTS) & 1u))) {
+            // they were written before the MMAs could start), or the producer's
+            if (!a16 && !__all_sync(0xffffffffu, dev::mbar_wait_bounded(&bar_nz[j % NZSLOTS],
+                                                                       (uint32_t)(j / NZSLOTS) & 1u))) {
                 give_up();
                 break;
             }
-            const int m0 = (bb0 + j) * BM, kp = m0 + row;
-            const bool valid = kp < n && (kps == nullptr || dev::kp_valid(kps[kp]));
-            const bool row_nz = nz_s[j % NZSLOTS][row] != 0;
+            const bool row_nz = a16 ? nz_row != 0 : nz_s[j % NZSLOTS][row] != 0;
             uint32_t r[ECOLS];
             dev::tmem_ld64(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(a * BN + c0), r);
             uint32_t near[ECOLS / 32];
@@ -331,20 +359,44 @@ __global__ void __launch_bounds__(NTH, 1) hs_proj_tc_kernel(
                     if (act) {
                         const float4 *fr = reinterpret_cast<const float4 *>(
                                                hist32 + (size_t)(m0 + qd * 32 + er) * kHistDim) + 8 * q;
-                        const float4 *wr = reinterpret_cast<const float4 *>(
-                                               Wt32 + (size_t)(n0 + ec) * kHistDim) + 8 * q;
-                        float4 fv[8], wv[8];
+                        float4 fv[8];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
+                        for (int i = 0; i < 8; ++i)
                             fv[i] = __ldg(fr + i);
-                            wv[i] = __ldg(wr + i);
+                        float w[32];
+                        if (!w_has_lo) {
+                            // W is exactly BF16: its head tile in shared memory is W
+                            // (row ec, K values 32 q .. 32 q + 31: chunks 4 (q & 1) .. + 3)
+                            const uint8_t *wrow = sW + (q >> 1) * TILE + ec * 128;
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int c = 4 * (q & 1) + i;
+                                const uint4 u = *reinterpret_cast<const uint4 *>(wrow + ((c ^ (ec & 7)) << 4));
+                                const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    w[8 * i + 2 * e] = __uint_as_float(uw[e] << 16);
+                                    w[8 * i + 2 * e + 1] = __uint_as_float(uw[e] & 0xffff0000u);
+                                }
+                            }
+                        } else {
+                            const float4 *wr = reinterpret_cast<const float4 *>(
+                                                   Wt32 + (size_t)(n0 + ec) * kHistDim) + 8 * q;
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                const float4 x = __ldg(wr + i);
+                                w[4 * i] = x.x;
+                                w[4 * i + 1] = x.y;
+                                w[4 * i + 2] = x.z;
+                                w[4 * i + 3] = x.w;
+                            }
                         }
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
-                            part = fmaf(fv[i].x, wv[i].x, part);
-                            part = fmaf(fv[i].y, wv[i].y, part);
-                            part = fmaf(fv[i].z, wv[i].z, part);
-                            part = fmaf(fv[i].w, wv[i].w, part);
+                            part = fmaf(fv[i].x, w[4 * i], part);
+                            part = fmaf(fv[i].y, w[4 * i + 1], part);
+                            part = fmaf(fv[i].z, w[4 * i + 2], part);
+                            part = fmaf(fv[i].w, w[4 * i + 3], part);
                         }
                     }
                     const float c1 = __shfl_down_sync(0xffffffffu, part, 1);
@@ -399,7 +451,8 @@ cudaError_t prepare_hs_proj_tc()
 }
 
 cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const float *hist, int n, uint32_t *out,
-                              DeviceStatus *status, cudaStream_t st, const bd_keypoint *kps)
+                              DeviceStatus *status, cudaStream_t st, const bd_keypoint *kps,
+                              const uint8_t *a16, const uint8_t *nz)
 {
     if (n <= 0)
         return cudaSuccess;
@@ -410,6 +463,8 @@ cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const float *hist, int n, u
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int chunks = p->nbits / BN;
     const int nblocks = (n + BM - 1) / BM;
+    if (a16 && !nz)
+        return cudaErrorInvalidValue;
     int cpc = sms / chunks;
     if (cpc < 1)
         cpc = 1;
@@ -418,7 +473,8 @@ cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const float *hist, int n, u
     cudaError_t e = launch_pdl(hs_proj_tc_kernel, dim3(chunks * cpc), dim3(NTH), (size_t)smem_bytes(),
                                st, p->tmap_w_hi, p->tmap_w_lo, p->w_has_lo ? 1 : 0, hist,
                                (const float *)p->d_Wt, (const float *)p->d_bias,
-                               (const float *)p->d_band, kps, n, p->nbits, out, status, nblocks, cpc);
+                               (const float *)p->d_band, kps, n, p->nbits, out, status, nblocks, cpc,
+                               a16, nz);
     if (e != cudaSuccess)
         return e;
     trace_kernel(st, "hs_proj_tc");
