@@ -1175,16 +1175,16 @@ KERNEL_SOURCES = {
     "select_threshold": ["select.cu", "bd_internal.h"],
 }
 NCU_TRAFFIC = {
-    "plain": {"describe_batch/batch_persistent": (1078272 + 3072, "1e65b635717b279b")},
-    "large": {"describe_batch/batch_persistent": (38291712 + 48051200, "1e65b635717b279b"),
-              "describe_batch/hs_proj_tc": (21689088 + 0, "6ee5b7dad2877b74"),
-              "match_bad/match_tc": (10280192, "0f3d0d8dddfa999b"),
-              "match_hashsift/match_tc": (20524288, "0f3d0d8dddfa999b")},
-    "select": {"select/select_keys": (201392896 + 341874432, "ebc7d88f9fe5476e"),
-               "select/select_threshold": (394236160 + 3337472, "ebc7d88f9fe5476e")},
-    "train": {"match_tc": (33593600 + 0, "0f3d0d8dddfa999b")},
-    "batch": {"describe_batch/batch_persistent": (332435712 + 313150208, "1e65b635717b279b"),
-              "describe_batch/hs_proj_tc": (106152192 + 4944384, "6ee5b7dad2877b74")},
+    "plain": {"describe_batch/batch_persistent": (906752 + 0, "7822e209d42bd1fa")},
+    "large": {"describe_batch/batch_persistent": (45923840 + 66588416, "7822e209d42bd1fa"),
+              "describe_batch/hs_proj_tc": (31296768 + 1792, "f8872d2ab9ab7240"),
+              "match_bad/match_tc": (10284288, "0fe87184717ac856"),
+              "match_hashsift/match_tc": (20522496, "0fe87184717ac856")},
+    "select": {"select/select_keys": (201405696 + 342221568, "4be65b3b887320bd"),
+               "select/select_threshold": (394175488 + 3300096, "4be65b3b887320bd")},
+    "train": {"match_tc": (33592832 + 0, "0fe87184717ac856")},
+    "batch": {"describe_batch/batch_persistent": (286831360 + 406895872, "7822e209d42bd1fa"),
+              "describe_batch/hs_proj_tc": (162736384 + 10219776, "f8872d2ab9ab7240")},
 }
 
 
