@@ -127,6 +127,12 @@ class Workload:
             self._sectors = tot
         return self._sectors
 
+    def matching_in_kernel(self) -> bool:
+        """The plan's matchings run as work items of the persistent kernel:
+        it then holds every descriptor they read (the FP32 projection is fused;
+        with the tcgen05 projection after it they run as one matching launch)."""
+        return bool(self.match_kind == "fused" and self.tuned and self.tuned.get("proj_fused"))
+
     def projection_path(self) -> str:
         """The HashSIFT projection the launch configuration runs."""
         if self.tuned and self.tuned.get("proj_fused"):
@@ -701,12 +707,16 @@ def run_ours(args):
                        "re-check (HashSIFT)"),
         "data": "synthetic",
         "config": dict(config, l2="flushed between steps (512 MB write)",
-                       matching={"tensor": "tensor cores (FP8 +-1, tcgen05), one call per "
-                                           "descriptor type",
-                                 "popc": "POPC, both descriptor types in one bd_match_batch launch",
-                                 "fused": "POPC, both descriptor types matched by the describing "
-                                          "launch itself (bd_batch_set_matches)"}[wl.match_kind]
-                       if wl.match else None,
+                       matching=({"tensor": "tensor cores (FP8 +-1, tcgen05), one call per "
+                                            "descriptor type",
+                                  "popc": "POPC, both descriptor types in one bd_match_batch launch",
+                                  "fused": ("POPC, both descriptor types matched by the describing "
+                                            "launch itself (bd_batch_set_matches)"
+                                            if wl.matching_in_kernel() else
+                                            "POPC, both descriptor types in one matching launch of "
+                                            "the describing call after the tcgen05 projection "
+                                            "(bd_batch_set_matches)")}[wl.match_kind]
+                                 if wl.match else None),
                        parallelism=(f"{world} ranks, independent inputs per rank (weak scaling)"
                                     if world > 1 else "single GPU")),
         "matches_per_s": world * wl.pairs_per_step / (ms * 1e-3),
@@ -1144,7 +1154,7 @@ def roofline(wl, per_kernel, clocks, probes=None, sm_count=None):
             "alu": (HS_OPS_PER_PIXEL * 1024.0 * wl.n, f_rate, "Tops/s", f_src),
             "hbm": (6.0 * px, float(peaks["hbm_gbs"]) * 1e9, "GB/s", f"{kind} HBM copy"),
         }
-        if wl.match and wl.match_kind == "fused":  # the matchings are its last items
+        if wl.match and wl.match_kind == "fused" and wl.matching_in_kernel():  # its last items
             p_rate, p_src = probe("popc", sm_count * 16 * sm_mhz * 1e6, f"{sm_count} SMs x 16 POPC/clk")
             words = wl.bad_bits // 32 + wl.hs_bits // 32
             parts["popc"] = (float(na) * nb * words, p_rate, "Tpopc/s", p_src)
