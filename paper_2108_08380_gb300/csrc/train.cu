@@ -317,79 +317,6 @@ __global__ void train_loss_finish_kernel(const double *__restrict__ acc, float *
         loss[threadIdx.x] = (float)acc[threadIdx.x];
 }
 
-template <int K>
-__global__ void __launch_bounds__(128) train_bad_bwd_kernel(int rows, const short4 *__restrict__ box,
-                                                            const int *__restrict__ side,
-                                                            const float *__restrict__ r,
-                                                            const float *__restrict__ dr,
-                                                            float inv_scale,
-                                                            double *__restrict__ dtheta_acc,
-                                                            float *__restrict__ dpatches)
-{
-    __shared__ float D[33][33];
-    float dth[K / 128], dthc[K / 128];
-#pragma unroll
-    for (int q = 0; q < K / 128; ++q)
-        dth[q] = dthc[q] = 0.f;
-    const int t = threadIdx.x;
-    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-        __syncthreads();
-        for (int e = t; e < 33 * 33; e += 128)
-            (&D[0][0])[e] = 0.f;
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < K / 128; ++q) {
-            const int k = q * 128 + t;
-            const float rv = r[(size_t)row * K + k];
-            const float dz = dr[(size_t)row * K + k] * (1.f - rv * rv);
-            kahan_add(dth[q], dthc[q], dz * inv_scale);
-            if (dz == 0.f)
-                continue;
-            const int s = __ldg(side + k);
-            const float g = -dz * inv_scale / (float)(s * s);  // z = (theta - f)/(255 T)
-            const short4 b = __ldg(box + k);
-#pragma unroll
-            for (int bx = 0; bx < 2; ++bx) {
-                const int x0 = bx ? b.z : b.x, y0 = bx ? b.w : b.y;
-                const float sg = bx ? -g : g;
-                const int xa = min(max(x0, 0), 32), xb = min(max(x0 + s, 0), 32);
-                const int ya = min(max(y0, 0), 32), yb = min(max(y0 + s, 0), 32);
-                if (xa < xb && ya < yb) {
-                    atomicAdd(&D[ya][xa], sg);
-                    atomicAdd(&D[ya][xb], -sg);
-                    atomicAdd(&D[yb][xa], -sg);
-                    atomicAdd(&D[yb][xb], sg);
-                }
-            }
-        }
-        __syncthreads();
-        if (t < 32) {  // prefix along x of row t
-            float acc = 0.f;
-            for (int x = 0; x < 32; ++x) {
-                acc += D[t][x];
-                D[t][x] = acc;
-            }
-        }
-        __syncthreads();
-        if (t < 32) {  // prefix along y of column t
-            float acc = 0.f;
-            for (int y = 0; y < 32; ++y) {
-                acc += D[y][t];
-                D[y][t] = acc;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int e = t + q * 128;
-            dpatches[(size_t)row * 1024 + e] = D[e >> 5][e & 31];
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < K / 128; ++q)
-        atomicAdd(dtheta_acc + q * 128 + t, (double)dth[q] - (double)dthc[q]);
-}
-
 // dtheta and db from their FP64 accumulators.
 __global__ void train_grad_finish_kernel(const double *__restrict__ acc, int kb, int kh,
                                          float *__restrict__ dtheta, float *__restrict__ db)
@@ -475,38 +402,46 @@ __global__ void __launch_bounds__(256) train_hs_dw_kernel(int rows, int K, const
         atomicAdd(db_acc + k0 + t, (double)dbs - (double)dbc);
 }
 
-// Patch gradient of the HashSIFT loss (added to dpatches), one patch per CTA
-// iteration: dh = W dM, the normalisation adjoint, then the histogram adjoint.
-template <int K>
-__global__ void __launch_bounds__(128, 8) train_hs_bwd_kernel(const float *__restrict__ patches,
-                                                           int rows, const float *__restrict__ Wt,
-                                                           const float *__restrict__ h,
-                                                           const float *__restrict__ norm,
-                                                           const float *__restrict__ r,
-                                                           const float *__restrict__ dr,
-                                                           float inv_t,
-                                                           float *__restrict__ dpatches)
+// Patch gradient of both losses and dtheta, written once per patch: R
+// patches per pass take dh = W dm for all R at once (each W load feeds R
+// independent chains, each in the k order of one patch) and the
+// normalisation adjoint; then, patch by patch, the HashSIFT histogram
+// adjoint (recomputed from the patch) and the BAD box adjoint (a 2-D
+// difference array in shared memory, 4 corner updates per box, then a 2-D
+// prefix sum) meet in one store, BAD + 0.5 * (HashSIFT gather).  dtheta
+// columns are summed per thread with compensated additions over its rows and
+// meet in the FP64 accumulators.
+template <int KB, int KH>
+__global__ void __launch_bounds__(128, 8) train_bwd_kernel(
+    const float *__restrict__ patches, int rows, const float *__restrict__ Wt,
+    const float *__restrict__ h, const float *__restrict__ norm, const float *__restrict__ r_hs,
+    const float *__restrict__ dr_hs, float inv_t, const short4 *__restrict__ box,
+    const int *__restrict__ side, const float *__restrict__ r_bad, const float *__restrict__ dr_bad,
+    float inv_scale, double *__restrict__ dtheta_acc, float *__restrict__ dpatches)
 {
-    // R patches per pass: dh = W dm for all R at once (each W load feeds R
-    // independent chains, each in the k order of one patch), then the pixel
-    // adjoint patch by patch
     constexpr int R = 4;
+    constexpr int QB = KB / 128;  // BAD bits per thread per patch
     __shared__ float P[32][33];
     __shared__ float gxs[32][33], gys[32][33];
-    __shared__ float dm[R][K];
+    __shared__ float D[33][33];
+    __shared__ float dm[R][KH];
     __shared__ float dH[R][128];
     __shared__ float red[R][4];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const dev::HistLane L = dev::hist_lane(t);
+    float dth[QB], dthc[QB];
+#pragma unroll
+    for (int q = 0; q < QB; ++q)
+        dth[q] = dthc[q] = 0.f;
     for (int row0 = blockIdx.x * R; row0 < rows; row0 += gridDim.x * R) {
         const int nr = min(R, rows - row0);
         __syncthreads();
-        for (int e = t; e < R * K; e += 128) {
-            const int rr = e / K, k = e % K;
+        for (int e = t; e < R * KH; e += 128) {
+            const int rr = e / KH, k = e % KH;
             float v = 0.f;
             if (rr < nr) {
-                const float rv = r[(size_t)(row0 + rr) * K + k];
-                v = dr[(size_t)(row0 + rr) * K + k] * (1.f - rv * rv) * inv_t;
+                const float rv = r_hs[(size_t)(row0 + rr) * KH + k];
+                v = dr_hs[(size_t)(row0 + rr) * KH + k] * (1.f - rv * rv) * inv_t;
             }
             dm[rr][k] = v;
         }
@@ -517,7 +452,7 @@ __global__ void __launch_bounds__(128, 8) train_hs_bwd_kernel(const float *__res
         for (int rr = 0; rr < R; ++rr)
             dh[rr] = 0.f;
 #pragma unroll 8
-        for (int k = 0; k < K; ++k) {
+        for (int k = 0; k < KH; ++k) {
             const float w = __ldg(Wt + (size_t)k * 128 + t);
 #pragma unroll
             for (int rr = 0; rr < R; ++rr)
@@ -544,12 +479,21 @@ __global__ void __launch_bounds__(128, 8) train_hs_bwd_kernel(const float *__res
         for (int rr = 0; rr < nr; ++rr) {
             const int row = row0 + rr;
             const float nrm = norm[row];
+            // this patch's BAD responses and dL/dr (loads in flight meanwhile)
+            float rb[QB], drb[QB];
+#pragma unroll
+            for (int q = 0; q < QB; ++q) {
+                rb[q] = r_bad[(size_t)row * KB + q * 128 + t];
+                drb[q] = dr_bad[(size_t)row * KB + q * 128 + t];
+            }
             __syncthreads();
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int e = t + q * 128;
                 P[e >> 5][e & 31] = __ldg(patches + (size_t)row * 1024 + e);
             }
+            for (int e = t; e < 33 * 33; e += 128)
+                (&D[0][0])[e] = 0.f;
             __syncthreads();
             // per-pixel adjoint of the votes: thread t owns one pixel row of one cell
             const int i = L.i;
@@ -591,8 +535,50 @@ __global__ void __launch_bounds__(128, 8) train_hs_bwd_kernel(const float *__res
                 gxs[i][j] = dgx;
                 gys[i][j] = dgy;
             }
+            // BAD: dtheta and the box adjoints of this patch (z = (theta - f) / (255 T))
+#pragma unroll
+            for (int q = 0; q < QB; ++q) {
+                const int k = q * 128 + t;
+                const float dz = drb[q] * (1.f - rb[q] * rb[q]);
+                kahan_add(dth[q], dthc[q], dz * inv_scale);
+                if (dz == 0.f)
+                    continue;
+                const int s = __ldg(side + k);
+                const float g = -dz * inv_scale / (float)(s * s);
+                const short4 b = __ldg(box + k);
+#pragma unroll
+                for (int bx = 0; bx < 2; ++bx) {
+                    const int x0 = bx ? b.z : b.x, y0 = bx ? b.w : b.y;
+                    const float sg = bx ? -g : g;
+                    const int xa = min(max(x0, 0), 32), xb = min(max(x0 + s, 0), 32);
+                    const int ya = min(max(y0, 0), 32), yb = min(max(y0 + s, 0), 32);
+                    if (xa < xb && ya < yb) {
+                        atomicAdd(&D[ya][xa], sg);
+                        atomicAdd(&D[ya][xb], -sg);
+                        atomicAdd(&D[yb][xa], -sg);
+                        atomicAdd(&D[yb][xb], sg);
+                    }
+                }
+            }
             __syncthreads();
-            // gather: gx(i,c) reads columns jr(c) (+) and jl(c) (-); gy likewise for rows
+            if (t < 32) {  // prefix along x of row t
+                float acc = 0.f;
+                for (int x = 0; x < 32; ++x) {
+                    acc += D[t][x];
+                    D[t][x] = acc;
+                }
+            }
+            __syncthreads();
+            if (t < 32) {  // prefix along y of column t
+                float acc = 0.f;
+                for (int y = 0; y < 32; ++y) {
+                    acc += D[y][t];
+                    D[y][t] = acc;
+                }
+            }
+            __syncthreads();
+            // gather: gx(i,c) reads columns jr(c) (+) and jl(c) (-); gy likewise for
+            // rows; the patch gradient is the BAD part plus half the HashSIFT sum
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int e = t + q * 128;
@@ -606,10 +592,13 @@ __global__ void __launch_bounds__(128, 8) train_hs_bwd_kernel(const float *__res
                 if (y == 31) v += gys[31][x];
                 if (y <= 30) v -= gys[y + 1][x];
                 if (y == 0) v -= gys[0][x];
-                dpatches[(size_t)row * 1024 + e] += 0.5f * v;
+                dpatches[(size_t)row * 1024 + e] = D[y][x] + 0.5f * v;
             }
         }
     }
+#pragma unroll
+    for (int q = 0; q < QB; ++q)
+        atomicAdd(dtheta_acc + q * 128 + t, (double)dth[q] - (double)dthc[q]);
 }
 
 int grid_rows(int rows, int sm_count, int per_sm)
@@ -841,32 +830,25 @@ bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, con
         train_hub_finish_kernel<<<(2 * n + 255) / 256, 256, 0, st>>>(
             n, tr->kb, tr->kh, tr->hub, tr->hub_acc, tr->max_hubs, grad_loss, tr->dr_bad, tr->dr_hs);
         trace_kernel(st, "train_hub_finish");
-        // BAD: dtheta and the patch gradient (written, not added)
-        if (tr->kb == 256)
-            train_bad_bwd_kernel<256><<<grid_rows(rows, sm, 12), 128, 0, st>>>(
-                rows, bp->d_patch_box, bp->d_patch_side, tr->r_bad, tr->dr_bad, inv_scale, dth_acc, dpatches);
-        else
-            train_bad_bwd_kernel<512><<<grid_rows(rows, sm, 12), 128, 0, st>>>(
-                rows, bp->d_patch_box, bp->d_patch_side, tr->r_bad, tr->dr_bad, inv_scale, dth_acc, dpatches);
-        trace_kernel(st, "train_bad_bwd");
-        // HashSIFT: dW, db, then the patch gradient (added)
+        // HashSIFT: dW and db; then both patch gradients and dtheta in one pass
         transpose_w_kernel<<<(128 * tr->kh + 255) / 256, 256, 0, st>>>(W, tr->kh, tr->Wt);
         dim3 g2((rows + DW_ROWS - 1) / DW_ROWS, tr->kh / 64);
         train_hs_dw_kernel<<<g2, 256, 0, st>>>(rows, tr->kh, tr->h, tr->r_hs, tr->dr_hs, inv_t, dW, db_acc);
         trace_kernel(st, "train_hs_dw");
+        {
+            auto kern = tr->kb == 256 ? (tr->kh == 256 ? train_bwd_kernel<256, 256> : train_bwd_kernel<256, 512>)
+                                      : (tr->kh == 256 ? train_bwd_kernel<512, 256> : train_bwd_kernel<512, 512>);
+            kern<<<grid_rows(rows, sm, 8), 128, 0, st>>>(patches, rows, tr->Wt, tr->h, tr->norm, tr->r_hs,
+                                                        tr->dr_hs, inv_t, bp->d_patch_box, bp->d_patch_side,
+                                                        tr->r_bad, tr->dr_bad, inv_scale, dth_acc, dpatches);
+            trace_kernel(st, "train_bwd");
+        }
         train_grad_finish_kernel<<<(tr->kb + tr->kh + 255) / 256, 256, 0, st>>>(dth_acc, tr->kb, tr->kh,
                                                                                dtheta, db);
         trace_kernel(st, "train_grad_finish");
-        if (tr->kh == 256)
-            train_hs_bwd_kernel<256><<<grid_rows(rows, sm, 8), 128, 0, st>>>(
-                patches, rows, tr->Wt, tr->h, tr->norm, tr->r_hs, tr->dr_hs, inv_t, dpatches);
-        else
-            train_hs_bwd_kernel<512><<<grid_rows(rows, sm, 8), 128, 0, st>>>(
-                patches, rows, tr->Wt, tr->h, tr->norm, tr->r_hs, tr->dr_hs, inv_t, dpatches);
-        trace_kernel(st, "train_hs_bwd");
         e = cudaGetLastError();
     }
-    note_launches(11);
+    note_launches(10);
     (void)R;
     if (prev >= 0 && prev != ctx->device)
         cudaSetDevice(prev);
