@@ -337,7 +337,9 @@ __global__ void transpose_w_kernel(const float *__restrict__ W, int K, float *__
     }
 }
 
-// dW = H^T dM and db = colsum(dM), dM = dr (1 - r^2) / T; rows split across CTAs.
+// dW = H^T dM and db = colsum(dM), dM = dr (1 - r^2) / T; rows split across
+// CTAs, 32 rows at a time through shared memory, the next 32 rows' loads in
+// flight (registers) while the current ones are multiplied.
 constexpr int DW_ROWS = 1024;
 __global__ void __launch_bounds__(256) train_hs_dw_kernel(int rows, int K, const float *__restrict__ h,
                                                           const float *__restrict__ r,
@@ -358,22 +360,40 @@ __global__ void __launch_bounds__(256) train_hs_dw_kernel(int rows, int K, const
         for (int b = 0; b < 8; ++b)
             acc[a][b] = 0.f;
     float dbs = 0.f, dbc = 0.f;
+    // this thread's share of a 32-row chunk: H entries t + 256 e (16), dM
+    // entries t + 256 e (8) as (r, dr) pairs
+    float hv_n[16], rv_n[8], dv_n[8];
+    auto fetch = [&](int base) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int idx = t + 256 * e, rr = idx >> 7, q = idx & 127;
+            hv_n[e] = base + rr < r1 ? h[(size_t)(base + rr) * 128 + q] : 0.f;
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int idx = t + 256 * e, rr = idx >> 6, k = idx & 63;
+            const bool in = base + rr < r1;
+            rv_n[e] = in ? r[(size_t)(base + rr) * K + k0 + k] : 0.f;
+            dv_n[e] = in ? dr[(size_t)(base + rr) * K + k0 + k] : 0.f;
+        }
+    };
+    if (r0 < r1)
+        fetch(r0);
     for (int base = r0; base < r1; base += 32) {
         __syncthreads();
-        for (int e = t; e < 32 * 128; e += 256) {
-            const int rr = e >> 7, q = e & 127;
-            Hs[rr][q] = base + rr < r1 ? h[(size_t)(base + rr) * 128 + q] : 0.f;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int idx = t + 256 * e;
+            Hs[idx >> 7][idx & 127] = hv_n[e];
         }
-        for (int e = t; e < 32 * 64; e += 256) {
-            const int rr = e >> 6, k = e & 63;
-            float m = 0.f;
-            if (base + rr < r1) {
-                const float rv = r[(size_t)(base + rr) * K + k0 + k];
-                m = dr[(size_t)(base + rr) * K + k0 + k] * (1.f - rv * rv) * inv_t;
-            }
-            Ms[rr][k] = m;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int idx = t + 256 * e;
+            Ms[idx >> 6][idx & 63] = dv_n[e] * (1.f - rv_n[e] * rv_n[e]) * inv_t;
         }
         __syncthreads();
+        if (base + 32 < r1)
+            fetch(base + 32);
 #pragma unroll 4
         for (int rr = 0; rr < 32; ++rr) {
             float hv[4], mv[8];
