@@ -455,6 +455,12 @@ __global__ void __launch_bounds__(128, 8) train_bwd_kernel(
         dth[q] = dthc[q] = 0.f;
     for (int row0 = blockIdx.x * R; row0 < rows; row0 += gridDim.x * R) {
         const int nr = min(R, rows - row0);
+        // the pass's first patch's pixels, in flight during dh = W dm; each
+        // patch then loads the next one's
+        float pn[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            pn[q] = __ldg(patches + (size_t)row0 * 1024 + t + q * 128);
         __syncthreads();
         for (int e = t; e < R * KH; e += 128) {
             const int rr = e / KH, k = e % KH;
@@ -510,10 +516,15 @@ __global__ void __launch_bounds__(128, 8) train_bwd_kernel(
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int e = t + q * 128;
-                P[e >> 5][e & 31] = __ldg(patches + (size_t)row * 1024 + e);
+                P[e >> 5][e & 31] = pn[q];
             }
             for (int e = t; e < 33 * 33; e += 128)
                 (&D[0][0])[e] = 0.f;
+            if (rr + 1 < nr) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    pn[q] = __ldg(patches + (size_t)(row + 1) * 1024 + t + q * 128);
+            }
             __syncthreads();
             // per-pixel adjoint of the votes: thread t owns one pixel row of one cell
             const int i = L.i;
