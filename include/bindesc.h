@@ -263,7 +263,8 @@ typedef struct bd_batch bd_batch;
  *                   the queue: 0 after the BAD items, 1 between the integral
  *                   tiles and the BAD items, 2 one grid's worth there and the
  *                   rest after the BAD items, 3 spread evenly among the BAD
- *                   items, 4 before the integral tiles.
+ *                   items, 4 before the integral tiles, 5 spread evenly among
+ *                   the integral tiles and the BAD items.
  *  hs_kp_per_item   HashSIFT keypoints per work item: 1 = the CTA's four warps
  *                   share each keypoint (lower latency, for few keypoints),
  *                   4 = one keypoint per warp (higher throughput).

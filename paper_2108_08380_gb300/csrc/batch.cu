@@ -69,7 +69,8 @@ struct BatchKernelArgs {
     uint32_t *hs_out;
     int hs_first;
     int hs_head, hs_pre_bad;  // HashSIFT items queued before the tiles / before the BAD items
-    int hs_mix;               // 1: the other HashSIFT items are spread evenly among the BAD items
+    int hs_mix;               // 1: the other HashSIFT items are spread evenly among the BAD items,
+                              // 2: all of them among the tiles and the BAD items
     uint32_t *ii, *carry;
     unsigned int *work, *exit_count, *final_done;
     unsigned int *tile_pub;   // [n_tiles] 1 once the tile's aggregates are written
@@ -355,7 +356,7 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
     const int e2 = e1 + A.hs_pre_bad;
     const int n_rest = n_hs - A.hs_head - A.hs_pre_bad;  // HashSIFT items after the tiles and pre-BAD ones
     const int e3 = e2 + A.n_bad_items + (A.hs_mix ? n_rest : 0);
-    const int e4 = e3 + (A.hs_mix ? 0 : n_rest);
+    const int e4 = e3 + (A.hs_mix ? 0 : n_rest);  // with hs_mix == 2: tiles + BAD + every HashSIFT item
     const int e5 = e4 + A.proj_items;
     const int total = e5 + A.match_items;
 
@@ -372,7 +373,20 @@ __global__ void __launch_bounds__(128, MINB) batch_persistent_kernel(BatchKernel
             t_claim = t_ready = gtimer();
         // item -> (kind, index): 0 integral tile, 1 HashSIFT, 3 BAD, 4 projection, 5 matching
         int kind, idx;
-        if (item < e0) {
+        if (A.hs_mix == 2 && item < e4) {
+            // [tiles][BAD items] with every HashSIFT item spread evenly among
+            // them: item i is main item floor(i nm / N) when that count steps
+            // at i, else a HashSIFT item
+            const long long i = item, nm = (long long)A.n_tiles + A.n_bad_items, N = nm + n_hs;
+            const long long before = i * nm / N, after = (i + 1) * nm / N;
+            if (after > before) {
+                kind = before < A.n_tiles ? 0 : 3;
+                idx = (int)(before < A.n_tiles ? before : before - A.n_tiles);
+            } else {
+                kind = 1;
+                idx = (int)(i - before);
+            }
+        } else if (item < e0) {
             kind = 1;
             idx = item;
         } else if (item < e1) {
@@ -844,6 +858,8 @@ bd_status batch_launch(bd_ctx *ctx, bd_batch *b, const bd_keypoint *kps, uint32_
     else
         A.hs_pre_bad = 0;
     A.hs_mix = b->cfg.hs_first == 3 && A.n_bad_items > 0 ? 1 : 0;
+    if (b->cfg.hs_first == 5 && A.n_tiles + A.n_bad_items > 0)
+        A.hs_mix = 2;  // hs_head = hs_pre_bad = 0: e4 = tiles + BAD + every HashSIFT item
     const bool m_in_kernel = !b->mjobs.empty() && (fused || !any_hs_job(b));
     if (m_in_kernel)
         fill_match_items(b, A, bad_out, hs_out, grid);
@@ -1057,7 +1073,7 @@ bd_status bd_batch_set_config(bd_batch *b, const bd_batch_config *cfg)
     if (!b || !cfg)
         return BD_ERR_INVALID;
     if (cfg->bad_kp_per_item < 4 || cfg->bad_kp_per_item > 256 || (cfg->bad_kp_per_item & 3) ||
-        cfg->ctas_per_sm < 0 || cfg->hs_first < 0 || cfg->hs_first > 4 ||
+        cfg->ctas_per_sm < 0 || cfg->hs_first < 0 || cfg->hs_first > 5 ||
         (cfg->hs_kp_per_item != 1 && cfg->hs_kp_per_item != 4) ||
         (cfg->proj_fused != 0 && cfg->proj_fused != 1) ||
         cfg->bad_shared < 0 || cfg->bad_shared > 2 ||
@@ -1224,7 +1240,7 @@ bd_status bd_batch_autotune(bd_ctx *ctx, bd_batch *b, const uint8_t *const *imgs
     for (int bs = 0; bs < (with_bad ? 3 : 1); ++bs)
     for (int fu = 0; fu < (can_fuse ? 3 : 1); ++fu)
     for (int hm : {1, 4})
-        for (int hs_first = 0; hs_first < 5 && s == BD_OK; ++hs_first)
+        for (int hs_first = 0; hs_first < 6 && s == BD_OK; ++hs_first)
             for (int it : items)
                 for (int c : per_sm) {
                     if (s != BD_OK)

@@ -47,14 +47,20 @@ def _per_image(ctx, bp, hp, imgs, kps, offs):
     return np.concatenate(bad), np.concatenate(hs)
 
 
-@pytest.mark.parametrize("graph", [False, True])
-def test_batch_equals_per_image_calls(gpu_ctx, graph):
+@pytest.mark.parametrize("graph,cfg", [(False, None), (True, None), (True, (8, 4, 5, 4, 0, 0, 0)),
+                                       (False, (4, 5, 4, 4, 1, 2, 0)), (True, (32, 6, 5, 1, 1, 1, 1))])
+def test_batch_equals_per_image_calls(gpu_ctx, graph, cfg):
+    """The batched launch gives the per-image calls' bits (which are pinned to
+    the oracle) in the default shape and in shapes with every queue order of
+    the HashSIFT items, both projection paths and every BAD sharing mode."""
     import torch
     imgs, kps, offs, bad, hs = _small_batch()
     bp, hp = gpu_ctx.bad_params(bad), gpu_ctx.hs_params(hs)
     ref_bad, ref_hs = _per_image(gpu_ctx, bp, hp, imgs, kps, offs)
     dimgs = [_dev(im) for im in imgs]
     b = gpu_ctx.batch(bp, hp, dimgs, offs)
+    if cfg is not None:
+        b.set_config(*cfg)
     n = len(kps)
     ob = torch.full((n, 8), -1, dtype=torch.int32, device="cuda")
     oh = torch.full((n, 8), -1, dtype=torch.int32, device="cuda")
@@ -197,7 +203,8 @@ def test_fused_fp32_projection_equals_tensor_core_path(gpu_ctx, hs_mode):
 
 
 @pytest.mark.parametrize("cfg", [(8, 4, 0, 4, 0, 0, 0), (4, 2, 1, 1, 1, 0, 1), (32, 6, 2, 4, 1, 1, 0),
-                                 (8, 4, 3, 4, 1, 1, 1), (4, 3, 3, 1, 0, 0, 0), (8, 5, 4, 4, 1, 2, 0)])
+                                 (8, 4, 3, 4, 1, 1, 1), (4, 3, 3, 1, 0, 0, 0), (8, 5, 4, 4, 1, 2, 0),
+                                 (4, 5, 5, 4, 1, 0, 0), (32, 5, 5, 1, 0, 2, 0)])
 def test_timeline_respects_dependencies(gpu_ctx, cfg):
     """The item timeline lists every queued item once, and no item starts
     before what it depends on: an integral tile after the tiles to its left
