@@ -101,7 +101,10 @@ __global__ void __launch_bounds__(NT) hs_warp_kernel(const uint8_t *__restrict__
 // chunks of 32 terms, each a sequential fmaf chain from zero, combined as
 // ((c0 + c1) + c2) + c3 before the bias; the tensor-core path's FP32
 // re-check evaluates the same expression, so both paths give the same bits.
-// Tile: 64 keypoints x 128 bits per CTA, 4 x 8 outputs per thread.
+// Tile: 64 keypoints x 128 bits per CTA, 4 x 8 outputs per thread: rows
+// 4 ty .. 4 ty + 3, columns 4 tx .. 4 tx + 3 and 64 + 4 tx .. 64 + 4 tx + 3, so
+// that a warp's 16-byte shared loads and relaxed-response stores are
+// contiguous; the two threads of a byte combine their nibbles by a shuffle.
 // ---------------------------------------------------------------------------
 constexpr int PBM = 64, PBN = 128, PBK = 32;
 
@@ -113,8 +116,8 @@ __global__ void __launch_bounds__(256) hs_proj_fp32_kernel(const float *__restri
                                                            float *__restrict__ relaxed,
                                                            float inv_t)
 {
-    __shared__ float Hs[PBK][PBM + 4];
-    __shared__ float Ws[PBK][PBN];
+    __shared__ __align__(16) float Hs[PBK][PBM + 4];
+    __shared__ __align__(16) float Ws[PBK][PBN];
     const int t = threadIdx.x;
     const int ty = t >> 4, tx = t & 15;
     const int m0 = blockIdx.x * PBM, n0 = blockIdx.y * PBN;
@@ -166,13 +169,11 @@ __global__ void __launch_bounds__(256) hs_proj_fp32_kernel(const float *__restri
                 part[a][b] = 0.0f;
 #pragma unroll 8
         for (int kk = 0; kk < PBK; ++kk) {
-            float hv[4], wv[8];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-                hv[a] = Hs[kk][ty * 4 + a];
-#pragma unroll
-            for (int b = 0; b < 8; ++b)
-                wv[b] = Ws[kk][tx * 8 + b];
+            const float4 h4 = *reinterpret_cast<const float4 *>(&Hs[kk][ty * 4]);
+            const float4 w0 = *reinterpret_cast<const float4 *>(&Ws[kk][tx * 4]);
+            const float4 w1 = *reinterpret_cast<const float4 *>(&Ws[kk][64 + tx * 4]);
+            const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
+            const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -188,22 +189,33 @@ __global__ void __launch_bounds__(256) hs_proj_fp32_kernel(const float *__restri
     float bv[8];
 #pragma unroll
     for (int b = 0; b < 8; ++b)
-        bv[b] = __ldg(bias + n0 + tx * 8 + b);
+        bv[b] = __ldg(bias + n0 + (b < 4 ? tx * 4 + b : 64 + tx * 4 + b - 4));
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const int row = m0 + ty * 4 + a;
-        if (row >= n)
-            continue;
-        const bool ok = kps ? dev::kp_valid(kps[row]) : true;
-        uint32_t byte = 0;
+        const bool in = row < n;
+        const bool ok = in && (kps ? dev::kp_valid(kps[row]) : true);
+        uint32_t lo = 0, hi = 0;
 #pragma unroll
-        for (int b = 0; b < 8; ++b)
-            byte |= (ok && (acc[a][b] + bv[b]) > 0.0f) ? (1u << b) : 0u;
-        out[(size_t)row * (K / 8) + (n0 + tx * 8) / 8] = (uint8_t)byte;
-        if (relaxed) {
+        for (int b = 0; b < 4; ++b) {
+            lo |= (ok && (acc[a][b] + bv[b]) > 0.0f) ? (1u << b) : 0u;
+            hi |= (ok && (acc[a][b + 4] + bv[b + 4]) > 0.0f) ? (1u << b) : 0u;
+        }
+        // even tx: the low nibble of bytes tx / 2 and 8 + tx / 2; odd tx: the high
+        const uint32_t lo_p = __shfl_xor_sync(0xffffffffu, lo, 1), hi_p = __shfl_xor_sync(0xffffffffu, hi, 1);
+        if (in && !(tx & 1)) {
+            uint8_t *o = out + (size_t)row * (K / 8) + n0 / 8;
+            o[tx >> 1] = (uint8_t)(lo | (lo_p << 4));
+            o[8 + (tx >> 1)] = (uint8_t)(hi | (hi_p << 4));
+        }
+        if (relaxed && in) {
+            float v[8];
 #pragma unroll
             for (int b = 0; b < 8; ++b)
-                relaxed[(size_t)row * K + n0 + tx * 8 + b] = tanhf((acc[a][b] + bv[b]) * inv_t);
+                v[b] = tanhf((acc[a][b] + bv[b]) * inv_t);
+            float *rr = relaxed + (size_t)row * K + n0;
+            *reinterpret_cast<float4 *>(rr + tx * 4) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4 *>(rr + 64 + tx * 4) = make_float4(v[4], v[5], v[6], v[7]);
         }
     }
 }

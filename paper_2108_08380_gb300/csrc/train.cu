@@ -24,18 +24,19 @@
 //     than kHubMin times (at most n / kHubMin of them) collect the responses
 //     r in [-1, 1] as 64-bit fixed point (r 2^40, exact for |r| >= 2^-16: an
 //     exact, order-independent sum, |sum| <= n <= 2^20 far from overflow)
-//     with integer atomics in a compact per-hub accumulator, converted and
-//     scaled by the loss weight at the end (which also clears it); the
-//     others keep FP32 atomics;
+//     with integer atomics in a compact per-hub accumulator (kHubRep copies
+//     each, summed at the end), converted and scaled by the loss weight at
+//     the end (which also clears it); the others keep FP32 atomics;
 //   - BAD: dtheta column sums, and the box adjoint as a 2-D difference array
 //     per patch (4 corner updates per box, then a 2-D prefix sum);
 //   - the column sums over all 3n rows (dtheta, db) cancel heavily (anchors
 //     and positives pull one way, negatives the other), so each thread sums
 //     its rows with compensated (Kahan) FP32 additions and the partial sums
 //     meet in FP64 accumulators, converted to FP32 at the end;
-//   - HashSIFT: dW = H^T dM and db (split over rows), dh = W dM, the
-//     normalisation adjoint and the histogram adjoint per pixel (recomputed
-//     from the patch), gathered into the patch gradient.
+//   - HashSIFT: dW = H^T dM and db (split over rows); dh = W dm and the
+//     normalisation adjoint as a tiled product over patches; the histogram
+//     adjoint per pixel (recomputed from the patch), gathered into the patch
+//     gradient together with the BAD box adjoint.
 #include "hashsift_dev.cuh"
 
 using namespace bd;
@@ -49,10 +50,11 @@ struct bd_train {
     uint32_t *bits_bad = nullptr, *bits_hs = nullptr;
     int32_t *mining = nullptr;  // [4][n]
     float *dr_bad = nullptr, *dr_hs = nullptr, *Wt = nullptr;
+    float *dH = nullptr;         // [rows][128] adjoint of the normalised histograms
     double *loss_acc = nullptr;  // [2] losses, then [Kb] dtheta and [Kh] db accumulators
     int *hub = nullptr;            // [2][n] times mined (zero between steps), then hub index or -1
     int *n_hubs = nullptr;         // [2]
-    long long *hub_acc = nullptr;  // [2][max_hubs][Kmax]: hubs' sum of r x 2^40, zero between steps
+    long long *hub_acc = nullptr;  // [2][max_hubs][kHubRep][Kmax]: hubs' sum of r x 2^40, zero between steps
     int max_hubs = 0;
     void *tc_scratch = nullptr;       // FP8 codes and partials of the top-2 searches
     uint2 *keys = nullptr;            // [2][n] top-2 keys (anchors, positives)
@@ -64,6 +66,10 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kHubMin = 64;  // a negative mined more often than this is a hub
+// Copies of each hub's accumulator (anchor i adds into copy i mod kHubRep):
+// the thousands of anchors of one hub would otherwise queue on the same
+// addresses; the copies' integer sums add up exactly in any order.
+constexpr int kHubRep = 16;
 
 // 2^32 (the fixed-point scale of the BAD summed-area tables).
 constexpr double kFix = 4294967296.0;
@@ -77,7 +83,9 @@ __device__ __forceinline__ long long sat_box64(const long long (*S)[33], int x0,
 
 // Relaxed BAD forward, one warp per patch (four per CTA, no CTA barrier in the
 // patch loop).  Each CTA first turns the thresholds into their fixed-point
-// bounds floor(theta_k s_k^2 2^32) and scales 2^-32 / s_k^2.
+// bounds floor(theta_k s_k^2 2^32) and scales 2^-32 / s_k^2.  The warp's
+// 33 x 33 fixed-point table is its only per-patch shared memory (five CTAs
+// per SM).
 template <int NW>
 __global__ void __launch_bounds__(128) train_bad_fwd_kernel(const float *__restrict__ patches, int rows,
                                                             const short4 *__restrict__ box,
@@ -88,7 +96,6 @@ __global__ void __launch_bounds__(128) train_bad_fwd_kernel(const float *__restr
 {
     constexpr int K = NW * 32;
     __shared__ long long S[4][33][33];
-    __shared__ float P[4][32][33];
     __shared__ long long thr[K];
     __shared__ float fscale[K];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -100,39 +107,37 @@ __global__ void __launch_bounds__(128) train_bad_fwd_kernel(const float *__restr
     }
     __syncthreads();
     long long (*Sw)[33] = S[warp];
-    float (*Pw)[33] = P[warp];
+    // the table's zero row and column stay zero
+    Sw[0][lane + 1] = 0;
+    Sw[lane + 1][0] = 0;
+    if (lane == 0)
+        Sw[0][0] = 0;
     for (int row = blockIdx.x * 4 + warp; row < rows; row += gridDim.x * 4) {
         const float *p = patches + (size_t)row * 1024;
-        __syncwarp();
+        // column x = lane: the patch's column from global memory (a warp's
+        // loads coalesced), its prefix sums down y in fixed point
+        float v[32];
 #pragma unroll
-        for (int q = 0; q < 32; ++q)
-            Pw[q][lane] = __ldg(p + q * 32 + lane);
+        for (int y = 0; y < 32; ++y)
+            v[y] = __ldg(p + y * 32 + lane);
         __syncwarp();
-        // row y = lane: prefix sums of the fixed-point values
         {
-            long long acc = 0;
-            Sw[lane + 1][0] = 0;
-#pragma unroll 8
-            for (int x = 0; x < 32; ++x) {
-                acc += __float2ll_rn(Pw[lane][x] * 4294967296.0f);
-                Sw[lane + 1][x + 1] = acc;
-            }
-            Sw[0][lane] = 0;
-            if (lane == 0)
-                Sw[0][32] = 0;
-        }
-        __syncwarp();
-        // column x = lane + 1: the 32 row prefixes into registers, then down
-        {
-            long long v[32];
-#pragma unroll
-            for (int y = 0; y < 32; ++y)
-                v[y] = Sw[y + 1][lane + 1];
             long long acc = 0;
 #pragma unroll
             for (int y = 0; y < 32; ++y) {
-                acc += v[y];
+                acc += __float2ll_rn(v[y] * 4294967296.0f);
                 Sw[y + 1][lane + 1] = acc;
+            }
+        }
+        __syncwarp();
+        // row y = lane + 1: prefix sums along x (integer sums: the same table
+        // in any order)
+        {
+            long long acc = 0;
+#pragma unroll 8
+            for (int x = 1; x <= 32; ++x) {
+                acc += Sw[lane + 1][x];
+                Sw[lane + 1][x] = acc;
             }
         }
         __syncwarp();
@@ -193,6 +198,9 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 }
 
 // Warp per triplet: hinge term, loss accumulation and (backward) dL/dr.
+// Lane l holds elements 4 (l + 32 q) .. 4 (l + 32 q) + 3 of each row (16-byte
+// loads, stores and FP32 atomics); the CTA's 8 hinge terms meet in one FP64
+// atomic.  Launched with 256 threads.
 template <int K>
 __global__ void __launch_bounds__(256) train_loss_kernel(const float *__restrict__ r, int n,
                                                          const int32_t *__restrict__ nstar,
@@ -203,50 +211,93 @@ __global__ void __launch_bounds__(256) train_loss_kernel(const float *__restrict
                                                          const int *__restrict__ hub,
                                                          long long *__restrict__ hub_acc)
 {
-    constexpr int Q = K / 32;
-    const int lane = threadIdx.x & 31;
+    constexpr int Q = K / 128, K4 = K / 4;
+    __shared__ float part[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= n)
-        return;
-    const int xs = xsel[i];
-    const int nrow = 2 * n + nstar[i];
-    float ra[Q], rp[Q], rn[Q];
-    float sap = 0.f, sxn = 0.f;
+    const bool valid = i < n;
+    const float4 *r4 = reinterpret_cast<const float4 *>(r);
+    float4 ra[Q], rp[Q], rn[Q];
+    int xs = 0, ns = 0;
+    float term = 0.f;
+    if (valid) {
+        xs = xsel[i];
+        ns = nstar[i];
+        const size_t nrow = 2 * (size_t)n + ns;
+        float sap = 0.f, sxn = 0.f;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const int k = q * 32 + lane;
-        ra[q] = r[(size_t)i * K + k];
-        rp[q] = r[(size_t)(n + i) * K + k];
-        rn[q] = r[(size_t)nrow * K + k];
-        sap = fmaf(ra[q], rp[q], sap);
-        sxn = fmaf(xs ? rp[q] : ra[q], rn[q], sxn);
-    }
+        for (int q = 0; q < Q; ++q) {
+            const int k4 = q * 32 + lane;
+            ra[q] = r4[(size_t)i * K4 + k4];
+            rp[q] = r4[(size_t)(n + i) * K4 + k4];
+            rn[q] = r4[nrow * K4 + k4];
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        sap += __shfl_xor_sync(FULL, sap, o);
-        sxn += __shfl_xor_sync(FULL, sxn, o);
+        for (int q = 0; q < Q; ++q) {
+            const float4 x = xs ? rp[q] : ra[q];
+            sap = fmaf(ra[q].x, rp[q].x, sap);
+            sap = fmaf(ra[q].y, rp[q].y, sap);
+            sap = fmaf(ra[q].z, rp[q].z, sap);
+            sap = fmaf(ra[q].w, rp[q].w, sap);
+            sxn = fmaf(x.x, rn[q].x, sxn);
+            sxn = fmaf(x.y, rn[q].y, sxn);
+            sxn = fmaf(x.z, rn[q].z, sxn);
+            sxn = fmaf(x.w, rn[q].w, sxn);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sap += __shfl_xor_sync(FULL, sap, o);
+            sxn += __shfl_xor_sync(FULL, sxn, o);
+        }
+        term = tau - sap + sxn;
     }
-    const float term = tau - sap + sxn;
-    if (loss_acc && lane == 0 && term > 0.f)
-        atomicAdd(loss_acc, (double)term);
-    if (!dr)
+    if (loss_acc) {
+        if (lane == 0)
+            part[warp] = valid && term > 0.f ? term : 0.f;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w)
+                sum += (double)part[w];
+            if (sum != 0.0)
+                atomicAdd(loss_acc, sum);
+        }
+    }
+    if (!dr || !valid)
         return;
     const float w = *gw;
     const bool on = term > 0.f;
+    const int hb = on ? hub[ns] : -1;
+    const size_t nrow = 2 * (size_t)n + ns;
+    float4 *dr4 = reinterpret_cast<float4 *>(dr);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        const int k = q * 32 + lane;
-        const float rx = xs ? rp[q] : ra[q];
-        dr[(size_t)i * K + k] = on ? w * (-rp[q] + (xs ? 0.f : rn[q])) : 0.f;
-        dr[(size_t)(n + i) * K + k] = on ? w * (-ra[q] + (xs ? rn[q] : 0.f)) : 0.f;
+        const int k4 = q * 32 + lane;
+        const float4 a = ra[q], p = rp[q], ng = rn[q];
+        const float4 x = xs ? p : a;
+        float4 da = make_float4(0.f, 0.f, 0.f, 0.f), dp = da;
         if (on) {
-            const int hb = hub[nstar[i]];
-            if (hb < 0)
-                atomicAdd(dr + (size_t)nrow * K + k, w * rx);
-            else
-                atomicAdd(reinterpret_cast<unsigned long long *>(hub_acc + (size_t)hb * K + k),
-                          (unsigned long long)__float2ll_rn(rx * 1099511627776.0f));  // r 2^40
+            da = make_float4(w * (-p.x + (xs ? 0.f : ng.x)), w * (-p.y + (xs ? 0.f : ng.y)),
+                             w * (-p.z + (xs ? 0.f : ng.z)), w * (-p.w + (xs ? 0.f : ng.w)));
+            dp = make_float4(w * (-a.x + (xs ? ng.x : 0.f)), w * (-a.y + (xs ? ng.y : 0.f)),
+                             w * (-a.z + (xs ? ng.z : 0.f)), w * (-a.w + (xs ? ng.w : 0.f)));
         }
+        dr4[(size_t)i * K4 + k4] = da;
+        dr4[(size_t)(n + i) * K4 + k4] = dp;
+        if (on && hb < 0)
+            atomicAdd(dr4 + nrow * K4 + k4, make_float4(w * x.x, w * x.y, w * x.z, w * x.w));
+    }
+    if (on && hb >= 0) {
+        // a hub: r 2^40 into copy i mod kHubRep, element k = 32 q + lane (a
+        // warp's 8-byte atomics on 256 contiguous bytes)
+        const float *xr = r + (size_t)(xs ? n + i : i) * K;
+        unsigned long long *acc = reinterpret_cast<unsigned long long *>(
+            hub_acc + ((size_t)hb * kHubRep + (i & (kHubRep - 1))) * K);
+#pragma unroll
+        for (int q = 0; q < K / 32; ++q)
+            atomicAdd(acc + q * 32 + lane,
+                      (unsigned long long)__float2ll_rn(xr[q * 32 + lane] * 1099511627776.0f));
     }
 }
 
@@ -300,13 +351,19 @@ __global__ void train_hub_finish_kernel(int n, int kb, int kh, int *__restrict__
         const int h = __shfl_sync(FULL, hb, src);
         const int d = ii / n, j = ii % n;
         const int K = d == 0 ? kb : kh;
-        // descriptor d's hubs start at d max_hubs kmax, each K entries (as train_loss writes them)
-        long long *acc = hub_acc + (size_t)d * max_hubs * kmax + (size_t)h * K;
+        // descriptor d's hubs start at d max_hubs kHubRep kmax, each kHubRep
+        // copies of K entries (as train_loss writes them)
+        long long *acc = hub_acc + ((size_t)d * max_hubs * kmax + (size_t)h * K) * kHubRep;
         float *row = d == 0 ? dr_bad + (size_t)(2 * n + j) * kb : dr_hs + (size_t)(2 * n + j) * kh;
         const float w = gw[d];
         for (int k = lane; k < K; k += 32) {
-            row[k] = w * (float)((double)acc[k] * 0x1p-40);
-            acc[k] = 0;
+            long long sum = 0;
+#pragma unroll
+            for (int c = 0; c < kHubRep; ++c) {
+                sum += acc[(size_t)c * K + k];
+                acc[(size_t)c * K + k] = 0;
+            }
+            row[k] = w * (float)((double)sum * 0x1p-40);
         }
     }
 }
@@ -347,10 +404,12 @@ __global__ void __launch_bounds__(256) train_hs_dw_kernel(int rows, int K, const
                                                           float *__restrict__ dW,
                                                           double *__restrict__ db_acc)
 {
-    __shared__ float Hs[32][128 + 4];
-    __shared__ float Ms[32][64];
+    __shared__ __align__(16) float Hs[32][128 + 4];
+    __shared__ __align__(16) float Ms[32][64];
     const int t = threadIdx.x;
-    const int tq = t >> 3, tk = t & 7;  // 32 x 8 threads: 4 q x 8 k outputs each
+    // 32 x 8 threads: 4 q x 8 k outputs each, k = 4 tk .. 4 tk + 3 and
+    // 32 + 4 tk .. 32 + 4 tk + 3 (a warp's 16-byte shared loads contiguous)
+    const int tq = t >> 3, tk = t & 7;
     const int k0 = blockIdx.y * 64;
     const int r0 = blockIdx.x * DW_ROWS, r1 = min(rows, r0 + DW_ROWS);
     float acc[4][8];
@@ -396,13 +455,11 @@ __global__ void __launch_bounds__(256) train_hs_dw_kernel(int rows, int K, const
             fetch(base + 32);
 #pragma unroll 4
         for (int rr = 0; rr < 32; ++rr) {
-            float hv[4], mv[8];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-                hv[a] = Hs[rr][tq * 4 + a];
-#pragma unroll
-            for (int b = 0; b < 8; ++b)
-                mv[b] = Ms[rr][tk * 8 + b];
+            const float4 h4 = *reinterpret_cast<const float4 *>(&Hs[rr][tq * 4]);
+            const float4 m0 = *reinterpret_cast<const float4 *>(&Ms[rr][tk * 4]);
+            const float4 m1 = *reinterpret_cast<const float4 *>(&Ms[rr][32 + tk * 4]);
+            const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
+            const float mv[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -417,214 +474,301 @@ __global__ void __launch_bounds__(256) train_hs_dw_kernel(int rows, int K, const
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b)
-            atomicAdd(dW + (size_t)(tq * 4 + a) * K + k0 + tk * 8 + b, acc[a][b]);
+            atomicAdd(dW + (size_t)(tq * 4 + a) * K + k0 + (b < 4 ? tk * 4 + b : 32 + tk * 4 + b - 4),
+                      acc[a][b]);
     if (t < 64)
         atomicAdd(db_acc + k0 + t, (double)dbs - (double)dbc);
 }
 
-// Patch gradient of both losses and dtheta, written once per patch: R
-// patches per pass take dh = W dm for all R at once (each W load feeds R
-// independent chains, each in the k order of one patch) and the
-// normalisation adjoint; then, patch by patch, the HashSIFT histogram
-// adjoint (recomputed from the patch) and the BAD box adjoint (a 2-D
-// difference array in shared memory, 4 corner updates per box, then a 2-D
-// prefix sum) meet in one store, BAD + 0.5 * (HashSIFT gather).  dtheta
-// columns are summed per thread with compensated additions over its rows and
-// meet in the FP64 accumulators.
-template <int KB, int KH>
-__global__ void __launch_bounds__(128, 8) train_bwd_kernel(
-    const float *__restrict__ patches, int rows, const float *__restrict__ Wt,
-    const float *__restrict__ h, const float *__restrict__ norm, const float *__restrict__ r_hs,
-    const float *__restrict__ dr_hs, float inv_t, const short4 *__restrict__ box,
-    const int *__restrict__ side, const float *__restrict__ r_bad, const float *__restrict__ dr_bad,
-    float inv_scale, double *__restrict__ dtheta_acc, float *__restrict__ dpatches)
+// Adjoint of the normalised histogram, dH = (dh - h (h . dh)) / |h| with
+// dh = W dm, dm = dr (1 - r^2) / T: a 64-patch x 128-dim tile per CTA, 4 x 8
+// outputs per thread (columns 4 tx .. 4 tx + 3 and 64 + 4 tx .. 64 + 4 tx + 3,
+// so that a warp's 16-byte shared loads are contiguous), k in 32-deep chunks
+// through shared memory with the next chunk's loads in flight.  Each dh is
+// one fmaf chain over k = 0 .. K-1; h . dh sums the thread's 8 products, then
+// the 16 threads of the row by a butterfly.  Rows of zero norm get dH = 0.
+constexpr int DH_M = 64, DH_K = 32;
+__global__ void __launch_bounds__(256) train_dh_kernel(int rows, int K, const float *__restrict__ Wt,
+                                                       const float *__restrict__ h,
+                                                       const float *__restrict__ norm,
+                                                       const float *__restrict__ r,
+                                                       const float *__restrict__ dr, float inv_t,
+                                                       float *__restrict__ dH)
 {
-    constexpr int R = 4;
+    __shared__ __align__(16) float Ds[DH_K][DH_M + 4];
+    __shared__ __align__(16) float Ws[DH_K][128];
+    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+    const int m0 = blockIdx.x * DH_M;
+    float acc[4][8];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            acc[a][b] = 0.f;
+    constexpr int DQ = DH_M * DH_K / 256, WQ = DH_K * 128 / 256;
+    float dq[DQ], wq[WQ];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < DQ; ++q) {
+            const int e = t + 256 * q, row = m0 + e / DH_K, k = k0 + e % DH_K;
+            float v = 0.f;
+            if (row < rows) {
+                const float rv = r[(size_t)row * K + k];
+                v = dr[(size_t)row * K + k] * (1.f - rv * rv) * inv_t;
+            }
+            dq[q] = v;
+        }
+#pragma unroll
+        for (int q = 0; q < WQ; ++q) {
+            const int e = t + 256 * q;
+            wq[q] = __ldg(Wt + (size_t)(k0 + e / 128) * 128 + e % 128);
+        }
+    };
+    load(0);
+    for (int k0 = 0; k0 < K; k0 += DH_K) {
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < DQ; ++q) {
+            const int e = t + 256 * q;
+            Ds[e % DH_K][e / DH_K] = dq[q];
+        }
+#pragma unroll
+        for (int q = 0; q < WQ; ++q) {
+            const int e = t + 256 * q;
+            Ws[e / 128][e % 128] = wq[q];
+        }
+        __syncthreads();
+        if (k0 + DH_K < K)
+            load(k0 + DH_K);
+#pragma unroll 8
+        for (int kk = 0; kk < DH_K; ++kk) {
+            const float4 dv = *reinterpret_cast<const float4 *>(&Ds[kk][ty * 4]);
+            const float4 w0 = *reinterpret_cast<const float4 *>(&Ws[kk][tx * 4]);
+            const float4 w1 = *reinterpret_cast<const float4 *>(&Ws[kk][64 + tx * 4]);
+            const float d[4] = {dv.x, dv.y, dv.z, dv.w};
+            const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b)
+                    acc[a][b] = fmaf(w[b], d[a], acc[a][b]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int row = m0 + ty * 4 + a;
+        const bool in = row < rows;
+        float hv[8];
+        if (in) {
+            const float4 h0 = *reinterpret_cast<const float4 *>(h + (size_t)row * 128 + tx * 4);
+            const float4 h1 = *reinterpret_cast<const float4 *>(h + (size_t)row * 128 + 64 + tx * 4);
+            hv[0] = h0.x; hv[1] = h0.y; hv[2] = h0.z; hv[3] = h0.w;
+            hv[4] = h1.x; hv[5] = h1.y; hv[6] = h1.z; hv[7] = h1.w;
+        } else {
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+                hv[b] = 0.f;
+        }
+        float hd = 0.f;
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            hd = fmaf(hv[b], acc[a][b], hd);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1)
+            hd += __shfl_xor_sync(FULL, hd, o);
+        const float nrm = in ? norm[row] : 0.f;
+        float o8[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            o8[b] = nrm > 0.f ? (acc[a][b] - hv[b] * hd) / nrm : 0.f;
+        if (in) {
+            *reinterpret_cast<float4 *>(dH + (size_t)row * 128 + tx * 4) = make_float4(o8[0], o8[1], o8[2], o8[3]);
+            *reinterpret_cast<float4 *>(dH + (size_t)row * 128 + 64 + tx * 4) =
+                make_float4(o8[4], o8[5], o8[6], o8[7]);
+        }
+    }
+}
+
+// Patch gradient of both losses and dtheta, written once per patch: the
+// HashSIFT histogram adjoint per pixel (recomputed from the patch, with the
+// patch's dH from train_dh_kernel) and the BAD box adjoint (a 2-D difference
+// array in shared memory, 4 corner updates per box, then 2-D prefix sums by
+// warp scans) meet in one store, BAD + 0.5 * (HashSIFT gather).  The next
+// patch's pixels and dH are in flight while the current patch is processed.
+// dtheta columns are summed per thread with compensated additions over its
+// rows and meet in the FP64 accumulators.
+template <int KB>
+__global__ void __launch_bounds__(128, 8) train_bwd_kernel(
+    const float *__restrict__ patches, int rows, const float *__restrict__ dHg,
+    const short4 *__restrict__ box, const int *__restrict__ side, const float *__restrict__ r_bad,
+    const float *__restrict__ dr_bad, float inv_scale, double *__restrict__ dtheta_acc,
+    float *__restrict__ dpatches)
+{
     constexpr int QB = KB / 128;  // BAD bits per thread per patch
     __shared__ float P[32][33];
     __shared__ float gxs[32][33], gys[32][33];
     __shared__ float D[33][33];
-    __shared__ float dm[R][KH];
-    __shared__ float dH[R][128];
-    __shared__ float red[R][4];
+    __shared__ float dH[128];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const dev::HistLane L = dev::hist_lane(t);
     float dth[QB], dthc[QB];
 #pragma unroll
     for (int q = 0; q < QB; ++q)
         dth[q] = dthc[q] = 0.f;
-    for (int row0 = blockIdx.x * R; row0 < rows; row0 += gridDim.x * R) {
-        const int nr = min(R, rows - row0);
-        // the pass's first patch's pixels, in flight during dh = W dm; each
-        // patch then loads the next one's
-        float pn[8];
+    float pn[8], hn = 0.f;
+    int row = blockIdx.x;
+    if (row < rows) {
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-            pn[q] = __ldg(patches + (size_t)row0 * 1024 + t + q * 128);
+            pn[q] = __ldg(patches + (size_t)row * 1024 + t + q * 128);
+        hn = dHg[(size_t)row * 128 + t];
+    }
+    for (; row < rows; row += gridDim.x) {
+        // this patch's BAD responses and dL/dr (loads in flight meanwhile)
+        float rb[QB], drb[QB];
+#pragma unroll
+        for (int q = 0; q < QB; ++q) {
+            rb[q] = r_bad[(size_t)row * KB + q * 128 + t];
+            drb[q] = dr_bad[(size_t)row * KB + q * 128 + t];
+        }
         __syncthreads();
-        for (int e = t; e < R * KH; e += 128) {
-            const int rr = e / KH, k = e % KH;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = t + q * 128;
+            P[e >> 5][e & 31] = pn[q];
+        }
+        dH[t] = hn;
+        for (int e = t; e < 33 * 33; e += 128)
+            (&D[0][0])[e] = 0.f;
+        const int next = row + gridDim.x;
+        if (next < rows) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                pn[q] = __ldg(patches + (size_t)next * 1024 + t + q * 128);
+            hn = dHg[(size_t)next * 128 + t];
+        }
+        __syncthreads();
+        // per-pixel adjoint of the votes: thread t owns one pixel row of one cell
+        const int i = L.i;
+        const int iu = max(i - 1, 0), id = min(i + 1, 31);
+        const int cell = t >> 3;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int j = L.j0 + q;
+            const int jl = max(j - 1, 0), jr = min(j + 1, 31);
+            const float gx = 0.5f * (P[i][jr] - P[i][jl]);
+            const float gy = 0.5f * (P[id][j] - P[iu][j]);
+            const float m2 = gx * gx + gy * gy;
+            float dgx = 0.f, dgy = 0.f;
+            if (m2 > 0.f) {
+                // 1/|g| and 1/|g|^2 from one reciprocal square root; the bin
+                // pair from the forward's orient_bin, exact at multiples of 45
+                // degrees (frequent on flat-sided patches), where the
+                // histogram's derivative jumps
+                const float im = rsqrtf(m2);
+                const float m = m2 * im;
+                float w1;
+                int b0 = dev::orient_bin(gx, gy, w1);
+                // on a bin edge the derivative in the angle is one-sided: take
+                // the floor side (the bin that starts at the edge, w1 = 0), as
+                // the exact definition floor(q) does; the votes are the same
+                if (w1 >= 1.0f) {
+                    b0 = (b0 + 1) & 7;
+                    w1 = 0.0f;
+                }
+                const int b1 = (b0 + 1) & 7;
+                const float d0 = dH[cell * 8 + b0], d1 = dH[cell * 8 + b1];
+                const float g = L.g[q];
+                const float dmag = g * ((1.f - w1) * d0 + w1 * d1);
+                const float dphi = g * m * (d1 - d0) * 1.27323954473516268615f;
+                const float im2 = im * im;
+                dgx = dmag * gx * im - dphi * gy * im2;
+                dgy = dmag * gy * im + dphi * gx * im2;
+            }
+            gxs[i][j] = dgx;
+            gys[i][j] = dgy;
+        }
+        // BAD: dtheta and the box adjoints of this patch (z = (theta - f) / (255 T))
+#pragma unroll
+        for (int q = 0; q < QB; ++q) {
+            const int k = q * 128 + t;
+            const float dz = drb[q] * (1.f - rb[q] * rb[q]);
+            kahan_add(dth[q], dthc[q], dz * inv_scale);
+            if (dz == 0.f)
+                continue;
+            const int s = __ldg(side + k);
+            const float g = -dz * inv_scale / (float)(s * s);
+            const short4 b = __ldg(box + k);
+#pragma unroll
+            for (int bx = 0; bx < 2; ++bx) {
+                const int x0 = bx ? b.z : b.x, y0 = bx ? b.w : b.y;
+                const float sg = bx ? -g : g;
+                const int xa = min(max(x0, 0), 32), xb = min(max(x0 + s, 0), 32);
+                const int ya = min(max(y0, 0), 32), yb = min(max(y0 + s, 0), 32);
+                if (xa < xb && ya < yb) {
+                    atomicAdd(&D[ya][xa], sg);
+                    atomicAdd(&D[ya][xb], -sg);
+                    atomicAdd(&D[yb][xa], -sg);
+                    atomicAdd(&D[yb][xb], sg);
+                }
+            }
+        }
+        __syncthreads();
+        // prefix sums of the 32 x 32 corner: along x (warp w rows 8w .. 8w + 7,
+        // lane = x), then along y (warp w columns 8w .. 8w + 7, lane = y);
+        // row 32 and column 32 only hold the boxes' far corners
+        {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = D[warp * 8 + u][lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float x = __shfl_up_sync(FULL, v[u], o);
+                    if (lane >= o)
+                        v[u] += x;
+                }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                D[warp * 8 + u][lane] = v[u];
+        }
+        __syncthreads();
+        {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = D[lane][warp * 8 + u];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float x = __shfl_up_sync(FULL, v[u], o);
+                    if (lane >= o)
+                        v[u] += x;
+                }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                D[lane][warp * 8 + u] = v[u];
+        }
+        __syncthreads();
+        // gather: gx(i,c) reads columns jr(c) (+) and jl(c) (-); gy likewise for
+        // rows; the patch gradient is the BAD part plus half the HashSIFT sum
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = t + q * 128;
+            const int y = e >> 5, x = e & 31;
             float v = 0.f;
-            if (rr < nr) {
-                const float rv = r_hs[(size_t)(row0 + rr) * KH + k];
-                v = dr_hs[(size_t)(row0 + rr) * KH + k] * (1.f - rv * rv) * inv_t;
-            }
-            dm[rr][k] = v;
-        }
-        __syncthreads();
-        // dh_t = sum_k W[t][k] dm[k]
-        float dh[R];
-#pragma unroll
-        for (int rr = 0; rr < R; ++rr)
-            dh[rr] = 0.f;
-#pragma unroll 8
-        for (int k = 0; k < KH; ++k) {
-            const float w = __ldg(Wt + (size_t)k * 128 + t);
-#pragma unroll
-            for (int rr = 0; rr < R; ++rr)
-                dh[rr] = fmaf(w, dm[rr][k], dh[rr]);
-        }
-        float ht[R];
-#pragma unroll
-        for (int rr = 0; rr < R; ++rr) {
-            ht[rr] = rr < nr ? h[(size_t)(row0 + rr) * 128 + t] : 0.f;
-            float hd = ht[rr] * dh[rr];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                hd += __shfl_xor_sync(FULL, hd, o);
-            if (lane == 0)
-                red[rr][warp] = hd;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int rr = 0; rr < R; ++rr) {
-            const float hd = red[rr][0] + red[rr][1] + red[rr][2] + red[rr][3];
-            const float nrm = rr < nr ? norm[row0 + rr] : 0.f;
-            dH[rr][t] = nrm > 0.f ? (dh[rr] - ht[rr] * hd) / nrm : 0.f;
-        }
-        for (int rr = 0; rr < nr; ++rr) {
-            const int row = row0 + rr;
-            const float nrm = norm[row];
-            // this patch's BAD responses and dL/dr (loads in flight meanwhile)
-            float rb[QB], drb[QB];
-#pragma unroll
-            for (int q = 0; q < QB; ++q) {
-                rb[q] = r_bad[(size_t)row * KB + q * 128 + t];
-                drb[q] = dr_bad[(size_t)row * KB + q * 128 + t];
-            }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int e = t + q * 128;
-                P[e >> 5][e & 31] = pn[q];
-            }
-            for (int e = t; e < 33 * 33; e += 128)
-                (&D[0][0])[e] = 0.f;
-            if (rr + 1 < nr) {
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    pn[q] = __ldg(patches + (size_t)(row + 1) * 1024 + t + q * 128);
-            }
-            __syncthreads();
-            // per-pixel adjoint of the votes: thread t owns one pixel row of one cell
-            const int i = L.i;
-            const int iu = max(i - 1, 0), id = min(i + 1, 31);
-            const int cell = t >> 3;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int j = L.j0 + q;
-                const int jl = max(j - 1, 0), jr = min(j + 1, 31);
-                const float gx = 0.5f * (P[i][jr] - P[i][jl]);
-                const float gy = 0.5f * (P[id][j] - P[iu][j]);
-                const float m2 = gx * gx + gy * gy;
-                float dgx = 0.f, dgy = 0.f;
-                if (m2 > 0.f && nrm > 0.f) {
-                    // 1/|g| and 1/|g|^2 from one reciprocal square root; the bin
-                    // pair from the forward's orient_bin, exact at multiples of 45
-                    // degrees (frequent on flat-sided patches), where the
-                    // histogram's derivative jumps
-                    const float im = rsqrtf(m2);
-                    const float m = m2 * im;
-                    float w1;
-                    int b0 = dev::orient_bin(gx, gy, w1);
-                    // on a bin edge the derivative in the angle is one-sided: take
-                    // the floor side (the bin that starts at the edge, w1 = 0), as
-                    // the exact definition floor(q) does; the votes are the same
-                    if (w1 >= 1.0f) {
-                        b0 = (b0 + 1) & 7;
-                        w1 = 0.0f;
-                    }
-                    const int b1 = (b0 + 1) & 7;
-                    const float d0 = dH[rr][cell * 8 + b0], d1 = dH[rr][cell * 8 + b1];
-                    const float g = L.g[q];
-                    const float dmag = g * ((1.f - w1) * d0 + w1 * d1);
-                    const float dphi = g * m * (d1 - d0) * 1.27323954473516268615f;
-                    const float im2 = im * im;
-                    dgx = dmag * gx * im - dphi * gy * im2;
-                    dgy = dmag * gy * im + dphi * gx * im2;
-                }
-                gxs[i][j] = dgx;
-                gys[i][j] = dgy;
-            }
-            // BAD: dtheta and the box adjoints of this patch (z = (theta - f) / (255 T))
-#pragma unroll
-            for (int q = 0; q < QB; ++q) {
-                const int k = q * 128 + t;
-                const float dz = drb[q] * (1.f - rb[q] * rb[q]);
-                kahan_add(dth[q], dthc[q], dz * inv_scale);
-                if (dz == 0.f)
-                    continue;
-                const int s = __ldg(side + k);
-                const float g = -dz * inv_scale / (float)(s * s);
-                const short4 b = __ldg(box + k);
-#pragma unroll
-                for (int bx = 0; bx < 2; ++bx) {
-                    const int x0 = bx ? b.z : b.x, y0 = bx ? b.w : b.y;
-                    const float sg = bx ? -g : g;
-                    const int xa = min(max(x0, 0), 32), xb = min(max(x0 + s, 0), 32);
-                    const int ya = min(max(y0, 0), 32), yb = min(max(y0 + s, 0), 32);
-                    if (xa < xb && ya < yb) {
-                        atomicAdd(&D[ya][xa], sg);
-                        atomicAdd(&D[ya][xb], -sg);
-                        atomicAdd(&D[yb][xa], -sg);
-                        atomicAdd(&D[yb][xb], sg);
-                    }
-                }
-            }
-            __syncthreads();
-            if (t < 32) {  // prefix along x of row t
-                float acc = 0.f;
-                for (int x = 0; x < 32; ++x) {
-                    acc += D[t][x];
-                    D[t][x] = acc;
-                }
-            }
-            __syncthreads();
-            if (t < 32) {  // prefix along y of column t
-                float acc = 0.f;
-                for (int y = 0; y < 32; ++y) {
-                    acc += D[y][t];
-                    D[y][t] = acc;
-                }
-            }
-            __syncthreads();
-            // gather: gx(i,c) reads columns jr(c) (+) and jl(c) (-); gy likewise for
-            // rows; the patch gradient is the BAD part plus half the HashSIFT sum
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int e = t + q * 128;
-                const int y = e >> 5, x = e & 31;
-                float v = 0.f;
-                if (x >= 1) v += gxs[y][x - 1];      // jr(x-1) = x
-                if (x == 31) v += gxs[y][31];        // jr(31) = 31
-                if (x <= 30) v -= gxs[y][x + 1];     // jl(x+1) = x
-                if (x == 0) v -= gxs[y][0];          // jl(0) = 0
-                if (y >= 1) v += gys[y - 1][x];
-                if (y == 31) v += gys[31][x];
-                if (y <= 30) v -= gys[y + 1][x];
-                if (y == 0) v -= gys[0][x];
-                dpatches[(size_t)row * 1024 + e] = D[y][x] + 0.5f * v;
-            }
+            if (x >= 1) v += gxs[y][x - 1];      // jr(x-1) = x
+            if (x == 31) v += gxs[y][31];        // jr(31) = 31
+            if (x <= 30) v -= gxs[y][x + 1];     // jl(x+1) = x
+            if (x == 0) v -= gxs[y][0];          // jl(0) = 0
+            if (y >= 1) v += gys[y - 1][x];
+            if (y == 31) v += gys[31][x];
+            if (y <= 30) v -= gys[y + 1][x];
+            if (y == 0) v -= gys[0][x];
+            dpatches[(size_t)row * 1024 + e] = D[y][x] + 0.5f * v;
         }
     }
 #pragma unroll
@@ -682,9 +826,10 @@ bd_status bd_train_create(bd_ctx *ctx, const bd_bad_params *bad, int hs_bits, in
     if (e == cudaSuccess) e = cudaMalloc(&tr->dr_bad, sizeof(float) * R * tr->kb);
     if (e == cudaSuccess) e = cudaMalloc(&tr->dr_hs, sizeof(float) * R * tr->kh);
     if (e == cudaSuccess) e = cudaMalloc(&tr->Wt, sizeof(float) * 128 * tr->kh);
+    if (e == cudaSuccess) e = cudaMalloc(&tr->dH, sizeof(float) * R * 128);
     if (e == cudaSuccess) e = cudaMalloc(&tr->loss_acc, sizeof(double) * (2 + tr->kb + tr->kh));
     tr->max_hubs = n / (kHubMin + 1) + 1;
-    const size_t hub_words = 2 * (size_t)tr->max_hubs * (size_t)std::max(tr->kb, tr->kh);
+    const size_t hub_words = 2 * (size_t)tr->max_hubs * kHubRep * (size_t)std::max(tr->kb, tr->kh);
     if (e == cudaSuccess) e = cudaMalloc(&tr->hub, sizeof(int) * 2 * (size_t)n);
     if (e == cudaSuccess) e = cudaMemset(tr->hub, 0, sizeof(int) * 2 * (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc(&tr->n_hubs, sizeof(int) * 2);
@@ -712,7 +857,7 @@ void bd_train_destroy(bd_train *tr)
     for (void *p : {(void *)tr->r_bad, (void *)tr->r_hs, (void *)tr->h, (void *)tr->norm,
                     (void *)tr->bits_bad, (void *)tr->bits_hs, (void *)tr->tc_scratch,
                     (void *)tr->keys, (void *)tr->arrivals, (void *)tr->mining, (void *)tr->dr_bad,
-                    (void *)tr->dr_hs, (void *)tr->Wt, (void *)tr->loss_acc, (void *)tr->hub,
+                    (void *)tr->dr_hs, (void *)tr->Wt, (void *)tr->dH, (void *)tr->loss_acc, (void *)tr->hub,
                     (void *)tr->n_hubs, (void *)tr->hub_acc})
         if (p)
             cudaFree(p);
@@ -739,10 +884,10 @@ bd_status bd_train_forward(bd_ctx *ctx, bd_train *tr, const float *patches, cons
     cudaError_t e = cudaSuccess;
     // relaxed BAD
     if (tr->kb == 256)
-        train_bad_fwd_kernel<8><<<grid_rows((rows + 3) / 4, sm, 4), 128, 0, st>>>(
+        train_bad_fwd_kernel<8><<<grid_rows((rows + 3) / 4, sm, 5), 128, 0, st>>>(
             patches, rows, bp->d_patch_box, bp->d_patch_side, theta, inv_scale, tr->r_bad, tr->bits_bad);
     else
-        train_bad_fwd_kernel<16><<<grid_rows((rows + 3) / 4, sm, 3), 128, 0, st>>>(
+        train_bad_fwd_kernel<16><<<grid_rows((rows + 3) / 4, sm, 5), 128, 0, st>>>(
             patches, rows, bp->d_patch_box, bp->d_patch_side, theta, inv_scale, tr->r_bad, tr->bits_bad);
     trace_kernel(st, "train_bad_fwd");
     // relaxed HashSIFT
@@ -849,7 +994,7 @@ bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, con
             const float tau = d == 0 ? tr->tau_bad : tr->tau_hs;
             const int32_t *ns = tr->mining + (size_t)(2 * d) * n, *xs = ns + n;
             const int *hub = tr->hub + (size_t)d * n;
-            long long *hacc = tr->hub_acc + (size_t)d * tr->max_hubs * (size_t)std::max(tr->kb, tr->kh);
+            long long *hacc = tr->hub_acc + (size_t)d * tr->max_hubs * kHubRep * (size_t)std::max(tr->kb, tr->kh);
             if (K == 256)
                 train_loss_kernel<256><<<blocks, 256, 0, st>>>(r, n, ns, xs, tau, grad_loss + d, nullptr,
                                                                drp, hub, hacc);
@@ -866,12 +1011,14 @@ bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, con
         dim3 g2((rows + DW_ROWS - 1) / DW_ROWS, tr->kh / 64);
         train_hs_dw_kernel<<<g2, 256, 0, st>>>(rows, tr->kh, tr->h, tr->r_hs, tr->dr_hs, inv_t, dW, db_acc);
         trace_kernel(st, "train_hs_dw");
+        train_dh_kernel<<<(rows + DH_M - 1) / DH_M, 256, 0, st>>>(rows, tr->kh, tr->Wt, tr->h, tr->norm,
+                                                                  tr->r_hs, tr->dr_hs, inv_t, tr->dH);
+        trace_kernel(st, "train_dh");
         {
-            auto kern = tr->kb == 256 ? (tr->kh == 256 ? train_bwd_kernel<256, 256> : train_bwd_kernel<256, 512>)
-                                      : (tr->kh == 256 ? train_bwd_kernel<512, 256> : train_bwd_kernel<512, 512>);
-            kern<<<grid_rows(rows, sm, 8), 128, 0, st>>>(patches, rows, tr->Wt, tr->h, tr->norm, tr->r_hs,
-                                                        tr->dr_hs, inv_t, bp->d_patch_box, bp->d_patch_side,
-                                                        tr->r_bad, tr->dr_bad, inv_scale, dth_acc, dpatches);
+            auto kern = tr->kb == 256 ? train_bwd_kernel<256> : train_bwd_kernel<512>;
+            kern<<<grid_rows(rows, sm, 8), 128, 0, st>>>(patches, rows, tr->dH, bp->d_patch_box,
+                                                        bp->d_patch_side, tr->r_bad, tr->dr_bad, inv_scale,
+                                                        dth_acc, dpatches);
             trace_kernel(st, "train_bwd");
         }
         train_grad_finish_kernel<<<(tr->kb + tr->kh + 255) / 256, 256, 0, st>>>(dth_acc, tr->kb, tr->kh,
@@ -879,7 +1026,7 @@ bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, con
         trace_kernel(st, "train_grad_finish");
         e = cudaGetLastError();
     }
-    note_launches(10);
+    note_launches(11);
     (void)R;
     if (prev >= 0 && prev != ctx->device)
         cudaSetDevice(prev);
