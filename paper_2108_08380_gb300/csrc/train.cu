@@ -54,6 +54,7 @@ struct bd_train {
     double *loss_acc = nullptr;  // [2] losses, then [Kb] dtheta and [Kh] db accumulators
     int *hub = nullptr;            // [2][n] times mined (zero between steps), then hub index or -1
     int *n_hubs = nullptr;         // [2]
+    int *hub_list = nullptr;       // [2][max_hubs] the hubs' negatives
     long long *hub_acc = nullptr;  // [2][max_hubs][kHubRep][Kmax]: hubs' sum of r x 2^40, zero between steps
     int max_hubs = 0;
     void *tc_scratch = nullptr;       // FP8 codes and partials of the top-2 searches
@@ -319,52 +320,56 @@ __global__ void train_hub_count_kernel(const int32_t *__restrict__ mining, int n
         atomicAdd(hub + key, __popc(same));
 }
 
-// The count becomes the hub index (in order of arrival) or -1.
-__global__ void train_hub_assign_kernel(int n, int *__restrict__ hub, int *__restrict__ n_hubs)
+// The count becomes the hub index (in order of arrival) or -1; the hub's
+// negative goes into the hub list.
+__global__ void train_hub_assign_kernel(int n, int *__restrict__ hub, int *__restrict__ n_hubs,
+                                        int *__restrict__ hub_list, int max_hubs)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < 2 * n) {
         const int d = i / n;
-        hub[i] = hub[i] > kHubMin ? atomicAdd(n_hubs + d, 1) : -1;
+        int hb = -1;
+        if (hub[i] > kHubMin) {
+            hb = atomicAdd(n_hubs + d, 1);
+            hub_list[d * max_hubs + hb] = i - d * n;
+        }
+        hub[i] = hb;
     }
 }
 
-// Hub rows of dL/dr = w (sum of r 2^40) 2^-40: lane l of a warp takes
-// negative (d, j) = 32 w + l, resets its mark to a zero count for the next
-// step's mining, and the warp converts the rows of its hubs together (lanes
-// over the columns); the accumulator is cleared.
-__global__ void train_hub_finish_kernel(int n, int kb, int kh, int *__restrict__ hub,
-                                        long long *__restrict__ hub_acc, int max_hubs,
-                                        const float *__restrict__ gw, float *__restrict__ dr_bad,
-                                        float *__restrict__ dr_hs)
+// Hub rows of dL/dr = w (sum of r 2^40) 2^-40: CTA (h, d) converts hub h of
+// descriptor d (threads over the columns, the kHubRep copies summed in
+// integers) and clears its accumulator; the grid also resets the marks to
+// zero counts for the next step's mining.
+__global__ void __launch_bounds__(256) train_hub_finish_kernel(int n, int kb, int kh, int *__restrict__ hub,
+                                                               const int *__restrict__ hub_list,
+                                                               const int *__restrict__ n_hubs,
+                                                               long long *__restrict__ hub_acc, int max_hubs,
+                                                               const float *__restrict__ gw,
+                                                               float *__restrict__ dr_bad,
+                                                               float *__restrict__ dr_hs)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
-    int hb = -1;
-    if (i < 2 * n) {
-        hb = hub[i];
+    const int d = blockIdx.y, h = blockIdx.x, t = threadIdx.x;
+    for (int i = (blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + t; i < 2 * n;
+         i += gridDim.x * gridDim.y * blockDim.x)
         hub[i] = 0;
-    }
-    const int kmax = kb > kh ? kb : kh;
-    for (unsigned m = __ballot_sync(FULL, hb >= 0); m; m &= m - 1) {
-        const int src = __ffs(m) - 1;
-        const int ii = i - lane + src;
-        const int h = __shfl_sync(FULL, hb, src);
-        const int d = ii / n, j = ii % n;
-        const int K = d == 0 ? kb : kh;
-        // descriptor d's hubs start at d max_hubs kHubRep kmax, each kHubRep
-        // copies of K entries (as train_loss writes them)
-        long long *acc = hub_acc + ((size_t)d * max_hubs * kmax + (size_t)h * K) * kHubRep;
-        float *row = d == 0 ? dr_bad + (size_t)(2 * n + j) * kb : dr_hs + (size_t)(2 * n + j) * kh;
-        const float w = gw[d];
-        for (int k = lane; k < K; k += 32) {
-            long long sum = 0;
+    if (h >= n_hubs[d])
+        return;
+    const int j = hub_list[d * max_hubs + h];
+    const int K = d == 0 ? kb : kh, kmax = kb > kh ? kb : kh;
+    // descriptor d's hubs start at d max_hubs kHubRep kmax, each kHubRep
+    // copies of K entries (as train_loss writes them)
+    long long *acc = hub_acc + ((size_t)d * max_hubs * kmax + (size_t)h * K) * kHubRep;
+    float *row = d == 0 ? dr_bad + (size_t)(2 * n + j) * kb : dr_hs + (size_t)(2 * n + j) * kh;
+    const float w = gw[d];
+    for (int k = t; k < K; k += blockDim.x) {
+        long long sum = 0;
 #pragma unroll
-            for (int c = 0; c < kHubRep; ++c) {
-                sum += acc[(size_t)c * K + k];
-                acc[(size_t)c * K + k] = 0;
-            }
-            row[k] = w * (float)((double)sum * 0x1p-40);
+        for (int c = 0; c < kHubRep; ++c) {
+            sum += acc[(size_t)c * K + k];
+            acc[(size_t)c * K + k] = 0;
         }
+        row[k] = w * (float)((double)sum * 0x1p-40);
     }
 }
 
@@ -506,17 +511,16 @@ __global__ void __launch_bounds__(256) train_dh_kernel(int rows, int K, const fl
         for (int b = 0; b < 8; ++b)
             acc[a][b] = 0.f;
     constexpr int DQ = DH_M * DH_K / 256, WQ = DH_K * 128 / 256;
-    float dq[DQ], wq[WQ];
+    // raw (r, dr) pairs and W values, loaded a chunk ahead (dm is formed when
+    // they are stored, so that the loads stay in flight during the FMAs)
+    float rq[DQ], dq[DQ], wq[WQ];
     auto load = [&](int k0) {
 #pragma unroll
         for (int q = 0; q < DQ; ++q) {
             const int e = t + 256 * q, row = m0 + e / DH_K, k = k0 + e % DH_K;
-            float v = 0.f;
-            if (row < rows) {
-                const float rv = r[(size_t)row * K + k];
-                v = dr[(size_t)row * K + k] * (1.f - rv * rv) * inv_t;
-            }
-            dq[q] = v;
+            const bool in = row < rows;
+            rq[q] = in ? r[(size_t)row * K + k] : 0.f;
+            dq[q] = in ? dr[(size_t)row * K + k] : 0.f;
         }
 #pragma unroll
         for (int q = 0; q < WQ; ++q) {
@@ -530,7 +534,7 @@ __global__ void __launch_bounds__(256) train_dh_kernel(int rows, int K, const fl
 #pragma unroll
         for (int q = 0; q < DQ; ++q) {
             const int e = t + 256 * q;
-            Ds[e % DH_K][e / DH_K] = dq[q];
+            Ds[e % DH_K][e / DH_K] = dq[q] * (1.f - rq[q] * rq[q]) * inv_t;
         }
 #pragma unroll
         for (int q = 0; q < WQ; ++q) {
@@ -589,34 +593,45 @@ __global__ void __launch_bounds__(256) train_dh_kernel(int rows, int K, const fl
     }
 }
 
-// Patch gradient of both losses and dtheta, written once per patch: the
-// HashSIFT histogram adjoint per pixel (recomputed from the patch, with the
-// patch's dH from train_dh_kernel) and the BAD box adjoint (a 2-D difference
-// array in shared memory, 4 corner updates per box, then 2-D prefix sums by
-// warp scans) meet in one store, BAD + 0.5 * (HashSIFT gather).  The next
+// Patch gradient of both losses and dtheta, written once per patch.  Warp w
+// owns pixel rows 8w .. 8w + 7 of the patch; lane 8c + r takes row 8w + r,
+// columns 8c .. 8c + 7 (the histogram's thread layout).  The patch comes in
+// and its gradient goes out through shared memory with coalesced global
+// accesses.  The HashSIFT adjoint per pixel (recomputed from the patch, with
+// the patch's dH from train_dh_kernel) reads its gradient stencil from the
+// staged patch; the adjoint of the central differences gathers by lane
+// shuffles, with the warps' first and last rows through shared memory.  The
+// BAD box adjoint is a 2-D difference array in shared memory (the corner
+// updates that fall inside the patch, then prefix sums along x and y).  Both
+// meet in one value per pixel, BAD + 0.5 * (HashSIFT gather).  The next
 // patch's pixels and dH are in flight while the current patch is processed.
 // dtheta columns are summed per thread with compensated additions over its
 // rows and meet in the FP64 accumulators.
 template <int KB>
-__global__ void __launch_bounds__(128, 8) train_bwd_kernel(
+__global__ void __launch_bounds__(128, 7) train_bwd_kernel(
     const float *__restrict__ patches, int rows, const float *__restrict__ dHg,
     const short4 *__restrict__ box, const int *__restrict__ side, const float *__restrict__ r_bad,
     const float *__restrict__ dr_bad, float inv_scale, double *__restrict__ dtheta_acc,
     float *__restrict__ dpatches)
 {
     constexpr int QB = KB / 128;  // BAD bits per thread per patch
-    __shared__ float P[32][33];
-    __shared__ float gxs[32][33], gys[32][33];
-    __shared__ float D[33][33];
+    __shared__ __align__(16) float D[32][36];
+    __shared__ __align__(16) float P[32][36];                 // the patch
+    __shared__ __align__(16) float O[32][36];                 // the previous patch's gradient
+    __shared__ __align__(16) float gtop[4][32], gbot[4][32];  // dgy of rows 8w, 8w + 7
+    __shared__ float ctot[4][32];                             // column sums of rows 8w .. 8w + 7
     __shared__ float dH[128];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int r = lane & 7, c = lane >> 3;
+    const int i = warp * 8 + r, j0 = c * 8;  // this thread's row and first column
     const dev::HistLane L = dev::hist_lane(t);
     float dth[QB], dthc[QB];
 #pragma unroll
     for (int q = 0; q < QB; ++q)
         dth[q] = dthc[q] = 0.f;
-    float pn[8], hn = 0.f;
-    int row = blockIdx.x;
+    float pn[8];
+    float hn = 0.f;
+    int row = blockIdx.x, prev = -1;
     if (row < rows) {
 #pragma unroll
         for (int q = 0; q < 8; ++q)
@@ -632,34 +647,52 @@ __global__ void __launch_bounds__(128, 8) train_bwd_kernel(
             drb[q] = dr_bad[(size_t)row * KB + q * 128 + t];
         }
         __syncthreads();
+        // the previous patch's gradient out (coalesced), this patch's pixels in
+        if (prev >= 0) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = t + q * 128;
+                dpatches[(size_t)prev * 1024 + e] = O[e >> 5][e & 31];
+            }
+        }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int e = t + q * 128;
             P[e >> 5][e & 31] = pn[q];
         }
         dH[t] = hn;
-        for (int e = t; e < 33 * 33; e += 128)
-            (&D[0][0])[e] = 0.f;
-        const int next = row + gridDim.x;
-        if (next < rows) {
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                pn[q] = __ldg(patches + (size_t)next * 1024 + t + q * 128);
-            hn = dHg[(size_t)next * 128 + t];
-        }
+        for (int e = t; e < 32 * 36 / 4; e += 128)
+            reinterpret_cast<float4 *>(&D[0][0])[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
-        // per-pixel adjoint of the votes: thread t owns one pixel row of one cell
-        const int i = L.i;
-        const int iu = max(i - 1, 0), id = min(i + 1, 31);
+        // this thread's pixels and the stencil's neighbours: rows i -/+ 1 and
+        // columns j0 - 1, j0 + 8, clamped to the patch
+        float px[8], up[8], dn[8];
+        {
+            const int iu = max(i - 1, 0), id = min(i + 1, 31);
+            const float4 a = *reinterpret_cast<const float4 *>(&P[i][j0]);
+            const float4 b = *reinterpret_cast<const float4 *>(&P[i][j0 + 4]);
+            const float4 ua = *reinterpret_cast<const float4 *>(&P[iu][j0]);
+            const float4 ub = *reinterpret_cast<const float4 *>(&P[iu][j0 + 4]);
+            const float4 da = *reinterpret_cast<const float4 *>(&P[id][j0]);
+            const float4 db = *reinterpret_cast<const float4 *>(&P[id][j0 + 4]);
+            px[0] = a.x; px[1] = a.y; px[2] = a.z; px[3] = a.w;
+            px[4] = b.x; px[5] = b.y; px[6] = b.z; px[7] = b.w;
+            up[0] = ua.x; up[1] = ua.y; up[2] = ua.z; up[3] = ua.w;
+            up[4] = ub.x; up[5] = ub.y; up[6] = ub.z; up[7] = ub.w;
+            dn[0] = da.x; dn[1] = da.y; dn[2] = da.z; dn[3] = da.w;
+            dn[4] = db.x; dn[5] = db.y; dn[6] = db.z; dn[7] = db.w;
+        }
+        const float left = P[i][max(j0 - 1, 0)], right = P[i][min(j0 + 8, 31)];
+        // per-pixel adjoint of the votes
         const int cell = t >> 3;
+        float dgx[8], dgy[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int j = L.j0 + q;
-            const int jl = max(j - 1, 0), jr = min(j + 1, 31);
-            const float gx = 0.5f * (P[i][jr] - P[i][jl]);
-            const float gy = 0.5f * (P[id][j] - P[iu][j]);
+            const float pl = q > 0 ? px[q - 1] : left, pr = q < 7 ? px[q + 1] : right;
+            const float gx = 0.5f * (pr - pl);
+            const float gy = 0.5f * (dn[q] - up[q]);
             const float m2 = gx * gx + gy * gy;
-            float dgx = 0.f, dgy = 0.f;
+            dgx[q] = dgy[q] = 0.f;
             if (m2 > 0.f) {
                 // 1/|g| and 1/|g|^2 from one reciprocal square root; the bin
                 // pair from the forward's orient_bin, exact at multiples of 45
@@ -682,11 +715,25 @@ __global__ void __launch_bounds__(128, 8) train_bwd_kernel(
                 const float dmag = g * ((1.f - w1) * d0 + w1 * d1);
                 const float dphi = g * m * (d1 - d0) * 1.27323954473516268615f;
                 const float im2 = im * im;
-                dgx = dmag * gx * im - dphi * gy * im2;
-                dgy = dmag * gy * im + dphi * gx * im2;
+                dgx[q] = dmag * gx * im - dphi * gy * im2;
+                dgy[q] = dmag * gy * im + dphi * gx * im2;
             }
-            gxs[i][j] = dgx;
-            gys[i][j] = dgy;
+        }
+        // the next patch's pixels and dH, in flight from here
+        const int next = row + gridDim.x;
+        if (next < rows) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                pn[q] = __ldg(patches + (size_t)next * 1024 + t + q * 128);
+            hn = dHg[(size_t)next * 128 + t];
+        }
+        if (r == 0) {
+            *reinterpret_cast<float4 *>(&gtop[warp][j0]) = make_float4(dgy[0], dgy[1], dgy[2], dgy[3]);
+            *reinterpret_cast<float4 *>(&gtop[warp][j0 + 4]) = make_float4(dgy[4], dgy[5], dgy[6], dgy[7]);
+        }
+        if (r == 7) {
+            *reinterpret_cast<float4 *>(&gbot[warp][j0]) = make_float4(dgy[0], dgy[1], dgy[2], dgy[3]);
+            *reinterpret_cast<float4 *>(&gbot[warp][j0 + 4]) = make_float4(dgy[4], dgy[5], dgy[6], dgy[7]);
         }
         // BAD: dtheta and the box adjoints of this patch (z = (theta - f) / (255 T))
 #pragma unroll
@@ -705,70 +752,114 @@ __global__ void __launch_bounds__(128, 8) train_bwd_kernel(
                 const float sg = bx ? -g : g;
                 const int xa = min(max(x0, 0), 32), xb = min(max(x0 + s, 0), 32);
                 const int ya = min(max(y0, 0), 32), yb = min(max(y0 + s, 0), 32);
+                // corners on row or column 32 lie outside the prefix sums' range
                 if (xa < xb && ya < yb) {
                     atomicAdd(&D[ya][xa], sg);
-                    atomicAdd(&D[ya][xb], -sg);
-                    atomicAdd(&D[yb][xa], -sg);
-                    atomicAdd(&D[yb][xb], sg);
+                    if (xb < 32)
+                        atomicAdd(&D[ya][xb], -sg);
+                    if (yb < 32) {
+                        atomicAdd(&D[yb][xa], -sg);
+                        if (xb < 32)
+                            atomicAdd(&D[yb][xb], sg);
+                    }
                 }
             }
         }
         __syncthreads();
-        // prefix sums of the 32 x 32 corner: along x (warp w rows 8w .. 8w + 7,
-        // lane = x), then along y (warp w columns 8w .. 8w + 7, lane = y);
-        // row 32 and column 32 only hold the boxes' far corners
+        // prefix sums of the 32 x 32 difference array.  Along x: thread (y, u) = (t / 4, t % 4)
+        // sums columns 8u .. 8u + 7 of row y in order, the four segments of
+        // the row meet by a scan over their lanes.
         {
-            float v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                v[u] = D[warp * 8 + u][lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1)
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const float x = __shfl_up_sync(FULL, v[u], o);
-                    if (lane >= o)
-                        v[u] += x;
-                }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                D[warp * 8 + u][lane] = v[u];
+            const int y = t >> 2, u = t & 3;
+            float4 a = *reinterpret_cast<const float4 *>(&D[y][8 * u]);
+            float4 b = *reinterpret_cast<const float4 *>(&D[y][8 * u + 4]);
+            a.y += a.x; a.z += a.y; a.w += a.z;
+            b.x += a.w; b.y += b.x; b.z += b.y; b.w += b.z;
+            float inc = b.w;
+            float o = __shfl_up_sync(FULL, inc, 1);
+            if (u >= 1) inc += o;
+            o = __shfl_up_sync(FULL, inc, 2);
+            if (u >= 2) inc += o;
+            float ex = __shfl_up_sync(FULL, inc, 1);
+            if (u == 0)
+                ex = 0.f;
+            a.x += ex; a.y += ex; a.z += ex; a.w += ex;
+            b.x += ex; b.y += ex; b.z += ex; b.w += ex;
+            *reinterpret_cast<float4 *>(&D[y][8 * u]) = a;
+            *reinterpret_cast<float4 *>(&D[y][8 * u + 4]) = b;
         }
         __syncthreads();
+        // along y: warp w sums rows 8w .. 8w + 7 of column lane in order, then
+        // adds the column sums of the warps above
+        float cv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            cv[u] = D[warp * 8 + u][lane];
+#pragma unroll
+        for (int u = 1; u < 8; ++u)
+            cv[u] += cv[u - 1];
+        ctot[warp][lane] = cv[7];
+        __syncthreads();
         {
-            float v[8];
+            float carry = 0.f;
+            for (int w = 0; w < warp; ++w)
+                carry += ctot[w][lane];
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-                v[u] = D[lane][warp * 8 + u];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1)
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const float x = __shfl_up_sync(FULL, v[u], o);
-                    if (lane >= o)
-                        v[u] += x;
-                }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                D[lane][warp * 8 + u] = v[u];
+                D[warp * 8 + u][lane] = cv[u] + carry;
         }
         __syncthreads();
-        // gather: gx(i,c) reads columns jr(c) (+) and jl(c) (-); gy likewise for
-        // rows; the patch gradient is the BAD part plus half the HashSIFT sum
+        // gather: gx(i, x) reads columns jr(x) (+) and jl(x) (-), gy likewise
+        // for rows: pixel (y, x) collects dgx(y, x - 1), dgx(y, 31) at x = 31,
+        // -dgx(y, x + 1), -dgx(y, 0) at x = 0, and the same in y; the patch
+        // gradient is the BAD part plus half the HashSIFT sum
+        float gl = __shfl_up_sync(FULL, dgx[7], 8), gr = __shfl_down_sync(FULL, dgx[0], 8);
+        float gu[8], gd[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            gu[q] = __shfl_up_sync(FULL, dgy[q], 1);
+            gd[q] = __shfl_down_sync(FULL, dgy[q], 1);
+        }
+        if (r == 0 && warp > 0) {
+            const float4 a = *reinterpret_cast<const float4 *>(&gbot[warp - 1][j0]);
+            const float4 b = *reinterpret_cast<const float4 *>(&gbot[warp - 1][j0 + 4]);
+            gu[0] = a.x; gu[1] = a.y; gu[2] = a.z; gu[3] = a.w;
+            gu[4] = b.x; gu[5] = b.y; gu[6] = b.z; gu[7] = b.w;
+        }
+        if (r == 7 && warp < 3) {
+            const float4 a = *reinterpret_cast<const float4 *>(&gtop[warp + 1][j0]);
+            const float4 b = *reinterpret_cast<const float4 *>(&gtop[warp + 1][j0 + 4]);
+            gd[0] = a.x; gd[1] = a.y; gd[2] = a.z; gd[3] = a.w;
+            gd[4] = b.x; gd[5] = b.y; gd[6] = b.z; gd[7] = b.w;
+        }
+        const float4 da = *reinterpret_cast<const float4 *>(&D[i][j0]);
+        const float4 db = *reinterpret_cast<const float4 *>(&D[i][j0 + 4]);
+        const float dv[8] = {da.x, da.y, da.z, da.w, db.x, db.y, db.z, db.w};
+        float o8[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int x = j0 + q;
+            float v = 0.f;
+            if (x >= 1) v += q > 0 ? dgx[q - 1] : gl;  // jr(x-1) = x
+            if (x == 31) v += dgx[7];                  // jr(31) = 31
+            if (x <= 30) v -= q < 7 ? dgx[q + 1] : gr; // jl(x+1) = x
+            if (x == 0) v -= dgx[0];                   // jl(0) = 0
+            if (i >= 1) v += gu[q];
+            if (i == 31) v += dgy[q];
+            if (i <= 30) v -= gd[q];
+            if (i == 0) v -= dgy[q];
+            o8[q] = dv[q] + 0.5f * v;
+        }
+        *reinterpret_cast<float4 *>(&O[i][j0]) = make_float4(o8[0], o8[1], o8[2], o8[3]);
+        *reinterpret_cast<float4 *>(&O[i][j0 + 4]) = make_float4(o8[4], o8[5], o8[6], o8[7]);
+        prev = row;
+    }
+    __syncthreads();
+    if (prev >= 0) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int e = t + q * 128;
-            const int y = e >> 5, x = e & 31;
-            float v = 0.f;
-            if (x >= 1) v += gxs[y][x - 1];      // jr(x-1) = x
-            if (x == 31) v += gxs[y][31];        // jr(31) = 31
-            if (x <= 30) v -= gxs[y][x + 1];     // jl(x+1) = x
-            if (x == 0) v -= gxs[y][0];          // jl(0) = 0
-            if (y >= 1) v += gys[y - 1][x];
-            if (y == 31) v += gys[31][x];
-            if (y <= 30) v -= gys[y + 1][x];
-            if (y == 0) v -= gys[0][x];
-            dpatches[(size_t)row * 1024 + e] = D[y][x] + 0.5f * v;
+            dpatches[(size_t)prev * 1024 + e] = O[e >> 5][e & 31];
         }
     }
 #pragma unroll
@@ -833,6 +924,7 @@ bd_status bd_train_create(bd_ctx *ctx, const bd_bad_params *bad, int hs_bits, in
     if (e == cudaSuccess) e = cudaMalloc(&tr->hub, sizeof(int) * 2 * (size_t)n);
     if (e == cudaSuccess) e = cudaMemset(tr->hub, 0, sizeof(int) * 2 * (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc(&tr->n_hubs, sizeof(int) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&tr->hub_list, sizeof(int) * 2 * (size_t)tr->max_hubs);
     if (e == cudaSuccess) e = cudaMalloc(&tr->hub_acc, sizeof(long long) * hub_words);
     if (e == cudaSuccess) e = cudaMemset(tr->hub_acc, 0, sizeof(long long) * hub_words);
     if (prev >= 0 && prev != ctx->device)
@@ -858,7 +950,7 @@ void bd_train_destroy(bd_train *tr)
                     (void *)tr->bits_bad, (void *)tr->bits_hs, (void *)tr->tc_scratch,
                     (void *)tr->keys, (void *)tr->arrivals, (void *)tr->mining, (void *)tr->dr_bad,
                     (void *)tr->dr_hs, (void *)tr->Wt, (void *)tr->dH, (void *)tr->loss_acc, (void *)tr->hub,
-                    (void *)tr->n_hubs, (void *)tr->hub_acc})
+                    (void *)tr->n_hubs, (void *)tr->hub_list, (void *)tr->hub_acc})
         if (p)
             cudaFree(p);
     if (prev >= 0 && prev != tr->ctx->device)
@@ -976,7 +1068,8 @@ bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, con
     if (e == cudaSuccess) {
         train_hub_count_kernel<<<(2 * n + 255) / 256, 256, 0, st>>>(tr->mining, n, tr->hub);
         trace_kernel(st, "train_hub_count");
-        train_hub_assign_kernel<<<(2 * n + 255) / 256, 256, 0, st>>>(n, tr->hub, tr->n_hubs);
+        train_hub_assign_kernel<<<(2 * n + 255) / 256, 256, 0, st>>>(n, tr->hub, tr->n_hubs, tr->hub_list,
+                                                                    tr->max_hubs);
         trace_kernel(st, "train_hub_assign");
         e = cudaGetLastError();
     }
@@ -1003,8 +1096,9 @@ bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, con
                                                                drp, hub, hacc);
             trace_kernel(st, "train_dr");
         }
-        train_hub_finish_kernel<<<(2 * n + 255) / 256, 256, 0, st>>>(
-            n, tr->kb, tr->kh, tr->hub, tr->hub_acc, tr->max_hubs, grad_loss, tr->dr_bad, tr->dr_hs);
+        train_hub_finish_kernel<<<dim3(tr->max_hubs, 2), 256, 0, st>>>(
+            n, tr->kb, tr->kh, tr->hub, tr->hub_list, tr->n_hubs, tr->hub_acc, tr->max_hubs, grad_loss,
+            tr->dr_bad, tr->dr_hs);
         trace_kernel(st, "train_hub_finish");
         // HashSIFT: dW and db; then both patch gradients and dtheta in one pass
         transpose_w_kernel<<<(128 * tr->kh + 255) / 256, 256, 0, st>>>(W, tr->kh, tr->Wt);
@@ -1016,7 +1110,7 @@ bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, con
         trace_kernel(st, "train_dh");
         {
             auto kern = tr->kb == 256 ? train_bwd_kernel<256> : train_bwd_kernel<512>;
-            kern<<<grid_rows(rows, sm, 8), 128, 0, st>>>(patches, rows, tr->dH, bp->d_patch_box,
+            kern<<<grid_rows(rows, sm, 7), 128, 0, st>>>(patches, rows, tr->dH, bp->d_patch_box,
                                                         bp->d_patch_side, tr->r_bad, tr->dr_bad, inv_scale,
                                                         dth_acc, dpatches);
             trace_kernel(st, "train_bwd");
