@@ -399,89 +399,86 @@ __global__ void transpose_w_kernel(const float *__restrict__ W, int K, float *__
     }
 }
 
-// dW = H^T dM and db = colsum(dM), dM = dr (1 - r^2) / T; rows split across
-// CTAs, 32 rows at a time through shared memory, the next 32 rows' loads in
-// flight (registers) while the current ones are multiplied.
-constexpr int DW_ROWS = 1024;
-__global__ void __launch_bounds__(256) train_hs_dw_kernel(int rows, int K, const float *__restrict__ h,
-                                                          const float *__restrict__ r,
-                                                          const float *__restrict__ dr, float inv_t,
-                                                          float *__restrict__ dW,
-                                                          double *__restrict__ db_acc)
+// dW = H^T dM and db = colsum(dM), dM = dr (1 - r^2) / T.  CTA (x, y) takes
+// rows [x R, x R + R) (R a multiple of DW_CHUNK) and columns 128 y .. 128 y +
+// 127 of dW: 8 x 8 outputs per thread (dims 4 tq .. 4 tq + 3 and 64 + 4 tq ..,
+// k likewise with tk, so that a warp's 16-byte shared loads are contiguous),
+// DW_CHUNK rows at a time through shared memory with the next rows' loads in
+// flight, each output one fmaf chain over the CTA's rows in order; the CTAs'
+// sums meet in FP32 atomics.
+constexpr int DW_CHUNK = 8;
+__global__ void __launch_bounds__(256, 2) train_hs_dw_kernel(int rows, int K, int R,
+                                                             const float *__restrict__ h,
+                                                             const float *__restrict__ r,
+                                                             const float *__restrict__ dr, float inv_t,
+                                                             float *__restrict__ dW,
+                                                             double *__restrict__ db_acc)
 {
-    __shared__ __align__(16) float Hs[32][128 + 4];
-    __shared__ __align__(16) float Ms[32][64];
-    const int t = threadIdx.x;
-    // 32 x 8 threads: 4 q x 8 k outputs each, k = 4 tk .. 4 tk + 3 and
-    // 32 + 4 tk .. 32 + 4 tk + 3 (a warp's 16-byte shared loads contiguous)
-    const int tq = t >> 3, tk = t & 7;
-    const int k0 = blockIdx.y * 64;
-    const int r0 = blockIdx.x * DW_ROWS, r1 = min(rows, r0 + DW_ROWS);
-    float acc[4][8];
+    __shared__ __align__(16) float Hs[DW_CHUNK][128];
+    __shared__ __align__(16) float Ms[DW_CHUNK][128];
+    const int t = threadIdx.x, tq = t >> 4, tk = t & 15;
+    const int k0 = blockIdx.y * 128;
+    const int r0 = blockIdx.x * R, r1 = min(rows, r0 + R);
+    float acc[8][8];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b)
             acc[a][b] = 0.f;
     float dbs = 0.f, dbc = 0.f;
-    // this thread's share of a 32-row chunk: H entries t + 256 e (16), dM
-    // entries t + 256 e (8) as (r, dr) pairs
-    float hv_n[16], rv_n[8], dv_n[8];
+    // this thread's share of a chunk: entries t + 256 e of H and of the
+    // (r, dr) pairs
+    constexpr int E = DW_CHUNK * 128 / 256;
+    float hv_n[E], rv_n[E], dv_n[E];
     auto fetch = [&](int base) {
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const int idx = t + 256 * e, rr = idx >> 7, q = idx & 127;
-            hv_n[e] = base + rr < r1 ? h[(size_t)(base + rr) * 128 + q] : 0.f;
-        }
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int idx = t + 256 * e, rr = idx >> 6, k = idx & 63;
+        for (int e = 0; e < E; ++e) {
+            const int idx = t + 256 * e, rr = idx >> 7, c = idx & 127;
             const bool in = base + rr < r1;
-            rv_n[e] = in ? r[(size_t)(base + rr) * K + k0 + k] : 0.f;
-            dv_n[e] = in ? dr[(size_t)(base + rr) * K + k0 + k] : 0.f;
+            hv_n[e] = in ? h[(size_t)(base + rr) * 128 + c] : 0.f;
+            rv_n[e] = in ? r[(size_t)(base + rr) * K + k0 + c] : 0.f;
+            dv_n[e] = in ? dr[(size_t)(base + rr) * K + k0 + c] : 0.f;
         }
     };
     if (r0 < r1)
         fetch(r0);
-    for (int base = r0; base < r1; base += 32) {
+    for (int base = r0; base < r1; base += DW_CHUNK) {
         __syncthreads();
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
+        for (int e = 0; e < E; ++e) {
             const int idx = t + 256 * e;
             Hs[idx >> 7][idx & 127] = hv_n[e];
-        }
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int idx = t + 256 * e;
-            Ms[idx >> 6][idx & 63] = dv_n[e] * (1.f - rv_n[e] * rv_n[e]) * inv_t;
+            Ms[idx >> 7][idx & 127] = dv_n[e] * (1.f - rv_n[e] * rv_n[e]) * inv_t;
         }
         __syncthreads();
-        if (base + 32 < r1)
-            fetch(base + 32);
+        if (base + DW_CHUNK < r1)
+            fetch(base + DW_CHUNK);
 #pragma unroll 4
-        for (int rr = 0; rr < 32; ++rr) {
-            const float4 h4 = *reinterpret_cast<const float4 *>(&Hs[rr][tq * 4]);
+        for (int rr = 0; rr < DW_CHUNK; ++rr) {
+            const float4 h0 = *reinterpret_cast<const float4 *>(&Hs[rr][tq * 4]);
+            const float4 h1 = *reinterpret_cast<const float4 *>(&Hs[rr][64 + tq * 4]);
             const float4 m0 = *reinterpret_cast<const float4 *>(&Ms[rr][tk * 4]);
-            const float4 m1 = *reinterpret_cast<const float4 *>(&Ms[rr][32 + tk * 4]);
-            const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
+            const float4 m1 = *reinterpret_cast<const float4 *>(&Ms[rr][64 + tk * 4]);
+            const float hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
             const float mv[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 8; ++a)
 #pragma unroll
                 for (int b = 0; b < 8; ++b)
                     acc[a][b] = fmaf(hv[a], mv[b], acc[a][b]);
         }
-        if (t < 64)
-            for (int rr = 0; rr < 32; ++rr)
+        if (t < 128)
+            for (int rr = 0; rr < DW_CHUNK; ++rr)
                 kahan_add(dbs, dbc, Ms[rr][t]);
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 8; ++a) {
+        const int q = a < 4 ? tq * 4 + a : 64 + tq * 4 + a - 4;
 #pragma unroll
         for (int b = 0; b < 8; ++b)
-            atomicAdd(dW + (size_t)(tq * 4 + a) * K + k0 + (b < 4 ? tk * 4 + b : 32 + tk * 4 + b - 4),
-                      acc[a][b]);
-    if (t < 64)
+            atomicAdd(dW + (size_t)q * K + k0 + (b < 4 ? tk * 4 + b : 64 + tk * 4 + b - 4), acc[a][b]);
+    }
+    if (t < 128)
         atomicAdd(db_acc + k0 + t, (double)dbs - (double)dbc);
 }
 
@@ -615,7 +612,7 @@ __global__ void __launch_bounds__(128, 7) train_bwd_kernel(
     float *__restrict__ dpatches)
 {
     constexpr int QB = KB / 128;  // BAD bits per thread per patch
-    __shared__ __align__(16) float D[32][36];
+    __shared__ float D[32][33];  // odd row stride: the box corners spread over the banks
     __shared__ __align__(16) float P[32][36];                 // the patch
     __shared__ __align__(16) float O[32][36];                 // the previous patch's gradient
     __shared__ __align__(16) float gtop[4][32], gbot[4][32];  // dgy of rows 8w, 8w + 7
@@ -661,8 +658,8 @@ __global__ void __launch_bounds__(128, 7) train_bwd_kernel(
             P[e >> 5][e & 31] = pn[q];
         }
         dH[t] = hn;
-        for (int e = t; e < 32 * 36 / 4; e += 128)
-            reinterpret_cast<float4 *>(&D[0][0])[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int e = t; e < 32 * 33; e += 128)
+            (&D[0][0])[e] = 0.f;
         __syncthreads();
         // this thread's pixels and the stencil's neighbours: rows i -/+ 1 and
         // columns j0 - 1, j0 + 8, clamped to the patch
@@ -771,11 +768,14 @@ __global__ void __launch_bounds__(128, 7) train_bwd_kernel(
         // the row meet by a scan over their lanes.
         {
             const int y = t >> 2, u = t & 3;
-            float4 a = *reinterpret_cast<const float4 *>(&D[y][8 * u]);
-            float4 b = *reinterpret_cast<const float4 *>(&D[y][8 * u + 4]);
-            a.y += a.x; a.z += a.y; a.w += a.z;
-            b.x += a.w; b.y += b.x; b.z += b.y; b.w += b.z;
-            float inc = b.w;
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                v[q] = D[y][8 * u + q];
+#pragma unroll
+            for (int q = 1; q < 8; ++q)
+                v[q] += v[q - 1];
+            float inc = v[7];
             float o = __shfl_up_sync(FULL, inc, 1);
             if (u >= 1) inc += o;
             o = __shfl_up_sync(FULL, inc, 2);
@@ -783,10 +783,9 @@ __global__ void __launch_bounds__(128, 7) train_bwd_kernel(
             float ex = __shfl_up_sync(FULL, inc, 1);
             if (u == 0)
                 ex = 0.f;
-            a.x += ex; a.y += ex; a.z += ex; a.w += ex;
-            b.x += ex; b.y += ex; b.z += ex; b.w += ex;
-            *reinterpret_cast<float4 *>(&D[y][8 * u]) = a;
-            *reinterpret_cast<float4 *>(&D[y][8 * u + 4]) = b;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                D[y][8 * u + q] = v[q] + ex;
         }
         __syncthreads();
         // along y: warp w sums rows 8w .. 8w + 7 of column lane in order, then
@@ -832,9 +831,10 @@ __global__ void __launch_bounds__(128, 7) train_bwd_kernel(
             gd[0] = a.x; gd[1] = a.y; gd[2] = a.z; gd[3] = a.w;
             gd[4] = b.x; gd[5] = b.y; gd[6] = b.z; gd[7] = b.w;
         }
-        const float4 da = *reinterpret_cast<const float4 *>(&D[i][j0]);
-        const float4 db = *reinterpret_cast<const float4 *>(&D[i][j0 + 4]);
-        const float dv[8] = {da.x, da.y, da.z, da.w, db.x, db.y, db.z, db.w};
+        float dv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            dv[q] = D[i][j0 + q];
         float o8[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -1102,8 +1102,15 @@ bd_status bd_train_backward(bd_ctx *ctx, bd_train *tr, const float *patches, con
         trace_kernel(st, "train_hub_finish");
         // HashSIFT: dW and db; then both patch gradients and dtheta in one pass
         transpose_w_kernel<<<(128 * tr->kh + 255) / 256, 256, 0, st>>>(W, tr->kh, tr->Wt);
-        dim3 g2((rows + DW_ROWS - 1) / DW_ROWS, tr->kh / 64);
-        train_hs_dw_kernel<<<g2, 256, 0, st>>>(rows, tr->kh, tr->h, tr->r_hs, tr->dr_hs, inv_t, dW, db_acc);
+        {
+            // one wave: 2 CTAs per SM over the K / 128 column tiles
+            const int ktiles = tr->kh / 128;
+            const int nx = std::max(1, 2 * sm / ktiles);
+            const int R = ((rows + nx - 1) / nx + DW_CHUNK - 1) / DW_CHUNK * DW_CHUNK;
+            dim3 g2((rows + R - 1) / R, ktiles);
+            train_hs_dw_kernel<<<g2, 256, 0, st>>>(rows, tr->kh, R, tr->h, tr->r_hs, tr->dr_hs, inv_t, dW,
+                                                   db_acc);
+        }
         trace_kernel(st, "train_hs_dw");
         train_dh_kernel<<<(rows + DH_M - 1) / DH_M, 256, 0, st>>>(rows, tr->kh, tr->Wt, tr->h, tr->norm,
                                                                   tr->r_hs, tr->dr_hs, inv_t, tr->dH);
