@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) hs_proj_fp32_kernel(const float *__restri
             float v[8];
 #pragma unroll
             for (int b = 0; b < 8; ++b)
-                v[b] = tanhf((acc[a][b] + bv[b]) * inv_t);
+                v[b] = dev::tanh_relaxed((acc[a][b] + bv[b]) * inv_t);
             float *rr = relaxed + (size_t)row * K + n0;
             *reinterpret_cast<float4 *>(rr + tx * 4) = make_float4(v[0], v[1], v[2], v[3]);
             *reinterpret_cast<float4 *>(rr + 64 + tx * 4) = make_float4(v[4], v[5], v[6], v[7]);

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(128) train_bad_fwd_kernel(const float *__restr
             const long long d = sat_box64(Sw, b.x, b.y, s) - sat_box64(Sw, b.z, b.w, s);
             const bool bit = d <= thr[k];  // f = d 2^-32 / s^2 <= theta, exactly
             const float f = (float)d * fscale[k];
-            r[(size_t)row * K + k] = tanhf((__ldg(theta + k) - f) * inv_scale);
+            r[(size_t)row * K + k] = dev::tanh_relaxed((__ldg(theta + k) - f) * inv_scale);
             const uint32_t word = __ballot_sync(FULL, bit);
             if (lane == 0)
                 bits[(size_t)row * NW + j] = word;
