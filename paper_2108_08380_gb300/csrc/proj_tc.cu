@@ -34,7 +34,12 @@
 // block j - 1 overlap.  When the histogram producer has already written the
 // rows in that operand image (the batched kernel does, as it finishes each
 // histogram), one thread copies each block's 64 KB stage with bulk copies
-// instead, and the zero-row flags come with it: no conversion remains.  Every mbarrier wait is bounded; a wait that gives up
+// instead, and the zero-row flags come with it: no conversion remains.  The
+// other six converter warps then take over the re-check: the epilogue warps
+// hand the block's words and band bits over in shared memory (two buffers),
+// and those warps re-check the bits while the epilogue goes on with the next
+// block, then store the words (a block with more than RLCAP band bits keeps
+// the rest for the epilogue warps' own re-check).  Every mbarrier wait is bounded; a wait that gives up
 // raises BD_FLAG_TIMEOUT and stops every role at its next block; the CTA
 // then waits (bounded) for the MMAs it issued and the W loads before it
 // frees TMEM and returns.
@@ -56,6 +61,8 @@ constexpr int LCAP = 256;        // band bits an epilogue warp re-checks per rou
 constexpr int NEPI = 8;          // epilogue warps: TMEM lane quadrant warp mod 4, 64 columns each
 constexpr int ECOLS = BN * 4 / NEPI;  // columns per epilogue warp
 constexpr int NTH = 32 * (1 + NCONV + NEPI);
+constexpr int NRES = NCONV - 1;  // with the pre-split operand image: warps 2 .. NCONV re-check
+constexpr int RLCAP = 1024;      // band bits of one block handed to them (two buffers)
 constexpr int STAGES = 2;        // A operand stages
 constexpr int ACCS = 2;          // TMEM accumulators of BN columns
 // W (head K0, head K1, tail K0, tail K1) + STAGES x A (same four tiles)
@@ -80,6 +87,60 @@ __device__ __forceinline__ void split4(const float4 &a, uint2 &hi, uint2 &lo)
     lo = make_uint2(*reinterpret_cast<const uint32_t *>(&l0), *reinterpret_cast<const uint32_t *>(&l1));
 }
 
+// Chunk q (terms 32 q .. 32 q + 31, one fmaf chain from zero) of the FP32
+// margin of keypoint row kp for bit n0 + ec: the histogram row from global
+// memory (band_rows, issued first so that several rows are in flight), W from
+// the head tile in shared memory when W is exactly BF16, else the FP32 W^T
+// row (L2).
+__device__ __forceinline__ void band_rows(const float *__restrict__ hist32, size_t kp, int q, float4 (&fv)[8])
+{
+    const float4 *fr = reinterpret_cast<const float4 *>(hist32 + kp * kHistDim) + 8 * q;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        fv[i] = __ldg(fr + i);
+}
+
+__device__ __forceinline__ float band_dot(const float4 (&fv)[8], const float *__restrict__ Wt32,
+                                          const uint8_t *sW, int w_has_lo, int n0, int ec, int q)
+{
+    float w[32];
+    if (!w_has_lo) {
+        // W is exactly BF16: its head tile in shared memory is W
+        // (row ec, K values 32 q .. 32 q + 31: chunks 4 (q & 1) .. + 3)
+        const uint8_t *wrow = sW + (q >> 1) * TILE + ec * 128;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int c = 4 * (q & 1) + i;
+            const uint4 u = *reinterpret_cast<const uint4 *>(wrow + ((c ^ (ec & 7)) << 4));
+            const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                w[8 * i + 2 * e] = __uint_as_float(uw[e] << 16);
+                w[8 * i + 2 * e + 1] = __uint_as_float(uw[e] & 0xffff0000u);
+            }
+        }
+    } else {
+        const float4 *wr = reinterpret_cast<const float4 *>(Wt32 + (size_t)(n0 + ec) * kHistDim) + 8 * q;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float4 x = __ldg(wr + i);
+            w[4 * i] = x.x;
+            w[4 * i + 1] = x.y;
+            w[4 * i + 2] = x.z;
+            w[4 * i + 3] = x.w;
+        }
+    }
+    float part = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        part = fmaf(fv[i].x, w[4 * i], part);
+        part = fmaf(fv[i].y, w[4 * i + 1], part);
+        part = fmaf(fv[i].z, w[4 * i + 2], part);
+        part = fmaf(fv[i].w, w[4 * i + 3], part);
+    }
+    return part;
+}
+
 __global__ void __launch_bounds__(NTH, 1) hs_proj_tc_kernel(
     const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int w_has_lo,
     const float *__restrict__ hist32, const float *__restrict__ Wt32,
@@ -102,11 +163,20 @@ __global__ void __launch_bounds__(NTH, 1) hs_proj_tc_kernel(
     __shared__ uint8_t nz_s[NZSLOTS][BM];            // row has a nonzero histogram entry
     __shared__ uint16_t list_s[NEPI][LCAP];            // band bits: row in warp << 7 | column
     __shared__ uint32_t words_s[NEPI][32][ECOLS / 32]; // the warp's output words
+    // with the pre-split image: block j's band bits (row << 7 | column) and
+    // output words, buffer j % 2, the bits' count and the re-checking warps
+    // done with them
+    __shared__ uint32_t rl_s[2][RLCAP];
+    __shared__ __align__(16) uint32_t wb_s[2][BM][BN / 32];
+    __shared__ unsigned int rl_cnt[2], rl_done[2];
+    __shared__ uint64_t bar_lfull[2], bar_lempty[2];
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int chunk = blockIdx.x / cpc, part = blockIdx.x % cpc;
     const int n0 = chunk * BN;
     const int bb0 = (int)((long long)nblocks * part / cpc);
+    // band bits handed to the re-checking warps (entries keypoint << 7 | column)
+    const bool handoff = a16 != nullptr && n < (1 << 24);
     const int nb = (int)((long long)nblocks * (part + 1) / cpc) - bb0;
 
     if (t == 0) {
@@ -122,6 +192,12 @@ __global__ void __launch_bounds__(NTH, 1) hs_proj_tc_kernel(
         }
         for (int z = 0; z < NZSLOTS; ++z)
             dev::mbar_init(&bar_nz[z], NCONV);  // lane 0 of each converter warp
+        for (int b = 0; b < 2; ++b) {
+            dev::mbar_init(&bar_lfull[b], NEPI);   // lane 0 of each epilogue warp
+            dev::mbar_init(&bar_lempty[b], NRES);  // lane 0 of each re-checking warp
+            rl_cnt[b] = 0u;
+            rl_done[b] = 0u;
+        }
         dev::fence_mbar_init();
         abort_s = 0;
         issued_s = 0;
@@ -215,6 +291,89 @@ __global__ void __launch_bounds__(NTH, 1) hs_proj_tc_kernel(
                 for (int q = 0; q < 4; ++q)
                     dev::bulk_load(dst + q * TILE, src + q * TILE, TILE, &bar_afull[s]);
             }
+        } else if (warp >= 2 && handoff) {
+            // ---- FP32 re-check of the band bits the epilogue handed over ----
+            // block j's list (buffer j % 2): 16 bits per pass and warp, 4 lanes
+            // per bit, in the FP32 projection kernel's order, the bit set or
+            // cleared in the block's words in shared memory; the last warp
+            // done with a block stores its words and clears the list's count
+            // before the epilogue may fill that buffer again
+            const int rw = warp - 2, g = lane >> 2, q = lane & 3;
+            unsigned long long rescued = 0;
+            for (int j = 0; j < nb; ++j) {
+                const int b = j & 1;
+                if (__any_sync(0xffffffffu, *(volatile int *)&abort_s != 0))
+                    break;
+                if (!__all_sync(0xffffffffu, dev::mbar_wait_bounded(&bar_lfull[b], (uint32_t)(j >> 1) & 1u))) {
+                    give_up();
+                    break;
+                }
+                const unsigned int cnt = *(volatile unsigned int *)&rl_cnt[b];
+                const unsigned int ne = cnt < (unsigned int)RLCAP ? cnt : (unsigned int)RLCAP;
+                const int m0 = (bb0 + j) * BM;
+                // two bits per lane group and pass: both rows' loads in flight
+#pragma unroll 1
+                for (unsigned int e0 = (unsigned int)rw * 16u; e0 < ne; e0 += NRES * 16u) {
+                    uint32_t v[2];
+                    float4 fv[2][8];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const unsigned int e = e0 + 8u * (unsigned int)u + (unsigned int)g;
+                        v[u] = e < ne ? rl_s[b][e] : 0xffffffffu;
+                        if (v[u] != 0xffffffffu)
+                            band_rows(hist32, (size_t)m0 + (v[u] >> 7), q, fv[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const bool act = v[u] != 0xffffffffu;
+                        const int r = (int)(v[u] >> 7), ec = (int)(v[u] & 127u);
+                        const float part = act ? band_dot(fv[u], Wt32, sW, w_has_lo, n0, ec, q) : 0.0f;
+                        const float c1 = __shfl_down_sync(0xffffffffu, part, 1);
+                        const float c2 = __shfl_down_sync(0xffffffffu, part, 2);
+                        const float c3 = __shfl_down_sync(0xffffffffu, part, 3);
+                        if (act && q == 0) {
+                            const float m32 = ((part + c1) + c2) + c3 + bias_s[ec];
+                            uint32_t *w = &wb_s[b][r][ec >> 5];
+                            const uint32_t bit = 1u << (ec & 31);
+                            if (m32 > 0.0f)
+                                atomicOr(w, bit);
+                            else
+                                atomicAnd(w, ~bit);
+                            ++rescued;
+                        }
+                    }
+                }
+                __syncwarp();
+                __threadfence_block();
+                unsigned int done = 0;
+                if (lane == 0)
+                    done = atomicAdd(&rl_done[b], 1u);
+                done = __shfl_sync(0xffffffffu, done, 0);
+                if (done == (unsigned int)NRES - 1u) {
+                    // the other warps' corrections are in: store the block's words
+                    __threadfence_block();
+                    for (int r = lane; r < BM; r += 32) {
+                        const int kp = m0 + r;
+                        if (kp < n)
+                            *reinterpret_cast<uint4 *>(out + (size_t)kp * (K / 32) + n0 / 32) =
+                                *reinterpret_cast<const uint4 *>(&wb_s[b][r][0]);
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        rl_cnt[b] = 0u;
+                        rl_done[b] = 0u;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0)
+                    dev::mbar_arrive(&bar_lempty[b]);
+                __syncwarp();
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                rescued += __shfl_xor_sync(0xffffffffu, rescued, o);
+            if (lane == 0 && rescued)
+                atomicAdd(&status->rescued, rescued);
         }
         __syncwarp();
     } else if (warp <= NCONV) {
@@ -320,6 +479,45 @@ __global__ void __launch_bounds__(NTH, 1) hs_proj_tc_kernel(
             }
             dev::tc_fence_before();
             dev::mbar_arrive(&bar_accempty[a]);
+            // with the pre-split image, the band bits go to the re-checking
+            // warps (buffer j % 2, free once they are done with block j - 2);
+            // a warp whose bits no longer fit marks the slots it reserved
+            // unused and re-checks its bits itself below
+            const int lb = j & 1;
+            if (handoff) {
+                if (!__all_sync(0xffffffffu, dev::mbar_wait_bounded(&bar_lempty[lb],
+                                                                   ((uint32_t)(j >> 1) & 1u) ^ 1u))) {
+                    give_up();
+                    break;
+                }
+                const uint32_t cnt = __popc(near[0]) + __popc(near[1]);
+                uint32_t incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o)
+                        incl += u;
+                }
+                const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                if (total) {
+                    uint32_t base = 0;
+                    if (lane == 0)
+                        base = atomicAdd(&rl_cnt[lb], total);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (base + total <= (uint32_t)RLCAP) {
+                        uint32_t e = base + incl - cnt;
+#pragma unroll
+                        for (int cc = 0; cc < ECOLS / 32; ++cc) {
+                            for (uint32_t m = near[cc]; m; m &= m - 1, ++e)
+                                rl_s[lb][e] = ((uint32_t)row << 7) | (uint32_t)(c0 + cc * 32 + __ffs(m) - 1);
+                            near[cc] = 0u;
+                        }
+                    } else {
+                        for (uint32_t sl = base + lane; sl < (uint32_t)RLCAP && sl < base + total; sl += 32)
+                            rl_s[lb][sl] = 0xffffffffu;
+                    }
+                }
+            }
             // rounds: the lanes whose bits fit (a prefix of the warp) list
             // them; then 8 bits per pass, 4 lanes per bit (32-term chunk q of
             // the margin each, all loads in flight), combined in the FP32
@@ -357,47 +555,9 @@ __global__ void __launch_bounds__(NTH, 1) hs_proj_tc_kernel(
                     const int er = (int)(v >> 7), ec = (int)(v & 127u);
                     float part = 0.0f;
                     if (act) {
-                        const float4 *fr = reinterpret_cast<const float4 *>(
-                                               hist32 + (size_t)(m0 + qd * 32 + er) * kHistDim) + 8 * q;
                         float4 fv[8];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            fv[i] = __ldg(fr + i);
-                        float w[32];
-                        if (!w_has_lo) {
-                            // W is exactly BF16: its head tile in shared memory is W
-                            // (row ec, K values 32 q .. 32 q + 31: chunks 4 (q & 1) .. + 3)
-                            const uint8_t *wrow = sW + (q >> 1) * TILE + ec * 128;
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                const int c = 4 * (q & 1) + i;
-                                const uint4 u = *reinterpret_cast<const uint4 *>(wrow + ((c ^ (ec & 7)) << 4));
-                                const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    w[8 * i + 2 * e] = __uint_as_float(uw[e] << 16);
-                                    w[8 * i + 2 * e + 1] = __uint_as_float(uw[e] & 0xffff0000u);
-                                }
-                            }
-                        } else {
-                            const float4 *wr = reinterpret_cast<const float4 *>(
-                                                   Wt32 + (size_t)(n0 + ec) * kHistDim) + 8 * q;
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                const float4 x = __ldg(wr + i);
-                                w[4 * i] = x.x;
-                                w[4 * i + 1] = x.y;
-                                w[4 * i + 2] = x.z;
-                                w[4 * i + 3] = x.w;
-                            }
-                        }
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            part = fmaf(fv[i].x, w[4 * i], part);
-                            part = fmaf(fv[i].y, w[4 * i + 1], part);
-                            part = fmaf(fv[i].z, w[4 * i + 2], part);
-                            part = fmaf(fv[i].w, w[4 * i + 3], part);
-                        }
+                        band_rows(hist32, (size_t)(m0 + qd * 32 + er), q, fv);
+                        part = band_dot(fv, Wt32, sW, w_has_lo, n0, ec, q);
                     }
                     const float c1 = __shfl_down_sync(0xffffffffu, part, 1);
                     const float c2 = __shfl_down_sync(0xffffffffu, part, 2);
@@ -414,7 +574,15 @@ __global__ void __launch_bounds__(NTH, 1) hs_proj_tc_kernel(
                 rescued += total;  // counted on every lane; lane 0's copy is added below
                 __syncwarp();
             }
-            if (kp < n) {
+            if (handoff) {
+                // the block's words go to the re-checking warps with the list
+#pragma unroll
+                for (int cc = 0; cc < ECOLS / 32; ++cc)
+                    wb_s[lb][row][c0 / 32 + cc] = wds[lane][cc];
+                __syncwarp();
+                if (lane == 0)
+                    dev::mbar_arrive(&bar_lfull[lb]);
+            } else if (kp < n) {
                 uint32_t *dst = out + (size_t)kp * (K / 32) + (n0 + c0) / 32;
 #pragma unroll
                 for (int cc = 0; cc < ECOLS / 32; ++cc)

@@ -427,3 +427,42 @@ def test_wait_limit_runs_out_then_next_call_is_exact(gpu_ctx, graph):
             assert torch.equal(got, exp)
     b.set_matches([])
     b.close()
+
+
+@pytest.mark.parametrize("band", [1e-3, 0.05, 1e9])
+def test_deferred_band_recheck_equals_in_place(gpu_ctx, band):
+    """With the batch kernel's pre-split operand image, the tcgen05
+    projection hands each block's band bits to otherwise idle warps for the
+    FP32 re-check; the bits and the number of re-checked bits equal the
+    per-image calls, whose epilogue re-checks its own bits.  At band 1e9
+    every bit of a non-zero row is in the band, far past the hand-off's room,
+    so most of them take the epilogue's own re-check.  Two launches in a row
+    check that the hand-off's counters start from zero again."""
+    import torch
+    rng = np.random.default_rng(77)
+    sizes, counts = [(1280, 720), (800, 600), (640, 480)], [6000, 3000, 1500]
+    imgs = [synth.make_image(w, h, rng) for (w, h) in sizes]
+    kps = np.concatenate([synth.make_keypoints(c, w, h, rng, border=-10.0, scales=(1.0,), angle_bins=None)
+                          for (w, h), c in zip(sizes, counts)])
+    offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    hs = synth.make_hashsift_params(256, rng, bf16=True)
+    hp = gpu_ctx.hs_params(hs, band=band)
+    dimgs = [_dev(im) for im in imgs]
+    n = len(kps)
+    dk = _dev(kps)
+    ref, ref_cnt = [], 0
+    gpu_ctx.rescued_count(reset=True)
+    for i, im in enumerate(imgs):
+        ref.append(_u32(gpu_ctx.hashsift_describe(hp, dimgs[i], _dev(kps[offs[i]:offs[i + 1]]))))
+    ref = np.concatenate(ref)
+    ref_cnt = gpu_ctx.rescued_count(reset=True)
+    b = gpu_ctx.batch(None, hp, dimgs, offs)
+    b.set_config(8, 4, 2, 4, 0, 0, 0)
+    for graph in (False, True):
+        oh = torch.full((n, 8), -1, dtype=torch.int32, device="cuda")
+        b.describe(dimgs, dk, None, oh, graph=graph)
+        assert gpu_ctx.sync_status() == 0
+        assert np.array_equal(_u32(oh), ref)
+        assert gpu_ctx.rescued_count(reset=True) == ref_cnt
+    assert ref_cnt > 0
+    b.close()
