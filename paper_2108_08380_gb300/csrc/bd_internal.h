@@ -172,9 +172,12 @@ cudaError_t prepare_hs_proj_tc();
 // a16 (optional): the histograms already split into the BF16 operand image
 // (split_offset), with nz[k] != 0 for rows that are not all zero; the kernel
 // then copies each block's operands instead of converting the FP32 rows
+// relaxed (optional, [n][K] FP32): also writes tanh(m inv_t) of each margin
+// m as the tensor cores give it (the training path's relaxed responses).
 cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const float *hist, int n, uint32_t *out,
                               DeviceStatus *status, cudaStream_t st, const bd_keypoint *kps,
-                              const uint8_t *a16 = nullptr, const uint8_t *nz = nullptr);
+                              const uint8_t *a16 = nullptr, const uint8_t *nz = nullptr,
+                              float *relaxed = nullptr, float inv_t = 1.0f);
 
 size_t match_scratch_bytes(int nq, int nt, int nbits, int sm_count);
 // tensor-core matching: scratch for the FP8 codes and split partials
@@ -259,6 +262,17 @@ namespace dev {
 
 // griddepcontrol (sm_90+): wait for the previous grid of the stream to
 // complete and its memory to be visible; allow the next grid to launch.
+// Relaxed response tanh(x) of the training path from its definition,
+// (1 - u) / (1 + u) with u = e^(-2|x|) in (0, 1] and the sign of x: one
+// exponential and one fast division.  The error is absolute (u's relative
+// error, about 2^-21, times 2u / (1 + u)^2 <= 1/2: below 5e-7), far inside the
+// training tolerances; near 0 it does not keep tanh(x) ~ x relatively.
+__device__ __forceinline__ float tanh_relaxed(float x)
+{
+    const float u = __expf(-2.0f * fabsf(x));
+    return copysignf(__fdividef(1.0f - u, 1.0f + u), x);
+}
+
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void griddep_launch_dependents()
 {

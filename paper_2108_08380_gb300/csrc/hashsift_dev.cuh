@@ -140,17 +140,6 @@ __device__ __forceinline__ int orient_bin(float gx, float gy, float &w1)
     return 4 * sy + 2 * t + odd;
 }
 
-// Relaxed response tanh(x) of the training path from its definition,
-// (1 - u) / (1 + u) with u = e^(-2|x|) in (0, 1] and the sign of x: one
-// exponential and one fast division.  The error is absolute (u's relative
-// error, about 2^-21, times 2u / (1 + u)^2 <= 1/2: below 5e-7), far inside the
-// training tolerances; near 0 it does not keep tanh(x) ~ x relatively.
-__device__ __forceinline__ float tanh_relaxed(float x)
-{
-    const float u = __expf(-2.0f * fabsf(x));
-    return copysignf(__fdividef(1.0f - u, 1.0f + u), x);
-}
-
 // Per-thread constants of the 128-thread histogram layout used by the
 // training backward (thread t: cell t/8, pixel row t%8 of it): pixel row i,
 // first column j0 and the separable Gaussian weights gi * gj[q] (sigma = 16).

@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(NTH, 1) hs_proj_tc_kernel(
     const float *__restrict__ bias, const float *__restrict__ band,
     const bd_keypoint *__restrict__ kps, int n, int K, uint32_t *__restrict__ out,
     DeviceStatus *status, int nblocks, int cpc, const uint8_t *__restrict__ a16,
-    const uint8_t *__restrict__ nzg)
+    const uint8_t *__restrict__ nzg, float *__restrict__ relaxed, float inv_t)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
@@ -479,6 +479,20 @@ __global__ void __launch_bounds__(NTH, 1) hs_proj_tc_kernel(
             }
             dev::tc_fence_before();
             dev::mbar_arrive(&bar_accempty[a]);
+            if (relaxed && kp < n) {
+                // relaxed responses tanh(m / T) of these margins (training path)
+                float4 *dst = reinterpret_cast<float4 *>(relaxed + (size_t)kp * K + n0 + c0);
+#pragma unroll
+                for (int i = 0; i < ECOLS / 4; ++i) {
+                    const float4 bv = *reinterpret_cast<const float4 *>(&bias_s[c0 + 4 * i]);
+                    float4 o;
+                    o.x = dev::tanh_relaxed((__uint_as_float(r[4 * i]) + bv.x) * inv_t);
+                    o.y = dev::tanh_relaxed((__uint_as_float(r[4 * i + 1]) + bv.y) * inv_t);
+                    o.z = dev::tanh_relaxed((__uint_as_float(r[4 * i + 2]) + bv.z) * inv_t);
+                    o.w = dev::tanh_relaxed((__uint_as_float(r[4 * i + 3]) + bv.w) * inv_t);
+                    dst[i] = o;
+                }
+            }
             // with the pre-split image, the band bits go to the re-checking
             // warps (buffer j % 2, free once they are done with block j - 2);
             // a warp whose bits no longer fit marks the slots it reserved
@@ -620,7 +634,7 @@ cudaError_t prepare_hs_proj_tc()
 
 cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const float *hist, int n, uint32_t *out,
                               DeviceStatus *status, cudaStream_t st, const bd_keypoint *kps,
-                              const uint8_t *a16, const uint8_t *nz)
+                              const uint8_t *a16, const uint8_t *nz, float *relaxed, float inv_t)
 {
     if (n <= 0)
         return cudaSuccess;
@@ -642,7 +656,7 @@ cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const float *hist, int n, u
                                st, p->tmap_w_hi, p->tmap_w_lo, p->w_has_lo ? 1 : 0, hist,
                                (const float *)p->d_Wt, (const float *)p->d_bias,
                                (const float *)p->d_band, kps, n, p->nbits, out, status, nblocks, cpc,
-                               a16, nz);
+                               a16, nz, relaxed, inv_t);
     if (e != cudaSuccess)
         return e;
     trace_kernel(st, "hs_proj_tc");

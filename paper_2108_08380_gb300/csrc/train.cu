@@ -7,8 +7,12 @@
 //     fixed point (value x 2^32, exact for |v| >= 2^-9), so box sums are exact
 //     integer sums and the hard bit [f <= theta] is the exact comparison
 //     D <= floor(theta s^2 2^32); r = tanh((theta - f)/(255 T)) in FP32;
-//   - relaxed HashSIFT: the patch histogram kernel, then the FP32 projection
-//     with r = tanh((W^T h + b)/T) and hard bits [m > 0];
+//   - relaxed HashSIFT: the patch histogram kernel, then the projection on
+//     the tensor cores (W split into BF16 head and tail each step; three
+//     MMAs, margins within about 4e-6 of FP32 at these sizes) with
+//     r = tanh((W^T h + b)/T) from those margins, and hard bits [m > 0] equal
+//     to the FP32 projection's (the bits within the rescue band 2^-13 ||W_k||
+//     are recomputed in FP32);
 //   - mining on hard codes: for anchor i the negative j != i with the smallest
 //     min(Hamming(a_i,n_j), Hamming(p_i,n_j)) (= the largest similarity
 //     K - 2 Hamming, Sec. III-A), lowest j on ties, from two exact
@@ -51,6 +55,9 @@ struct bd_train {
     int32_t *mining = nullptr;  // [4][n]
     float *dr_bad = nullptr, *dr_hs = nullptr, *Wt = nullptr;
     float *dH = nullptr;         // [rows][128] adjoint of the normalised histograms
+    // the tcgen05 projection's view of this step's W and b: W^T in FP32 and
+    // as BF16 head and tail (their TMA maps encoded once), the per-bit band
+    bd_hs_params hp;
     double *loss_acc = nullptr;  // [2] losses, then [Kb] dtheta and [Kh] db accumulators
     int *hub = nullptr;            // [2][n] times mined (zero between steps), then hub index or -1
     int *n_hubs = nullptr;         // [2]
@@ -388,6 +395,34 @@ __global__ void train_grad_finish_kernel(const double *__restrict__ acc, int kb,
         dtheta[i] = (float)acc[i];
     else if (i < kb + kh)
         db[i - kb] = (float)acc[i];
+}
+
+// This step's W (128 x K, row-major) for the tcgen05 projection: W^T in FP32,
+// its BF16 head and tail (W = hi + lo + O(2^-16 |W|)), and the rescue band
+// 2^-13 ||W_k||_2 per bit (the bound the projection's FP32 re-check needs
+// for normalised histograms).  One CTA of 128 threads per bit.
+__global__ void __launch_bounds__(128) train_w_split_kernel(const float *__restrict__ W, int K,
+                                                            float *__restrict__ Wt,
+                                                            __nv_bfloat16 *__restrict__ hi,
+                                                            __nv_bfloat16 *__restrict__ lo,
+                                                            float *__restrict__ band)
+{
+    __shared__ float part[4];
+    const int k = blockIdx.x, i = threadIdx.x;
+    const float v = W[(size_t)i * K + k];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    Wt[(size_t)k * 128 + i] = v;
+    hi[(size_t)k * 128 + i] = h;
+    lo[(size_t)k * 128 + i] = __float2bfloat16_rn(v - __bfloat162float(h));
+    float ss = v * v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        ss += __shfl_xor_sync(FULL, ss, o);
+    if ((i & 31) == 0)
+        part[i >> 5] = ss;
+    __syncthreads();
+    if (i == 0)
+        band[k] = 0x1p-13f * sqrtf(part[0] + part[1] + part[2] + part[3]);
 }
 
 __global__ void transpose_w_kernel(const float *__restrict__ W, int K, float *__restrict__ Wt)
@@ -918,6 +953,25 @@ bd_status bd_train_create(bd_ctx *ctx, const bd_bad_params *bad, int hs_bits, in
     if (e == cudaSuccess) e = cudaMalloc(&tr->dr_hs, sizeof(float) * R * tr->kh);
     if (e == cudaSuccess) e = cudaMalloc(&tr->Wt, sizeof(float) * 128 * tr->kh);
     if (e == cudaSuccess) e = cudaMalloc(&tr->dH, sizeof(float) * R * 128);
+    {
+        bd_hs_params *hp = &tr->hp;
+        hp->ctx = ctx;
+        hp->nbits = tr->kh;
+        hp->precision = BD_HS_BF16_RESCUE;
+        hp->w_has_lo = true;
+        if (e == cudaSuccess) e = cudaMalloc(&hp->d_Wt, sizeof(float) * 128 * tr->kh);
+        if (e == cudaSuccess) e = cudaMalloc(&hp->d_Wt16_hi, sizeof(__nv_bfloat16) * 128 * tr->kh);
+        if (e == cudaSuccess) e = cudaMalloc(&hp->d_Wt16_lo, sizeof(__nv_bfloat16) * 128 * tr->kh);
+        if (e == cudaSuccess) e = cudaMalloc(&hp->d_band, sizeof(float) * tr->kh);
+        if (e == cudaSuccess) {
+            hp->tmap_ok = encode_tmap_2d_bf16(&hp->tmap_w_hi, hp->d_Wt16_hi, 128, (uint64_t)tr->kh, 256, 64, 128) &&
+                          encode_tmap_2d_bf16(&hp->tmap_w_lo, hp->d_Wt16_lo, 128, (uint64_t)tr->kh, 256, 64, 128);
+            if (!hp->tmap_ok)
+                e = cudaErrorInvalidValue;
+        }
+        if (e == cudaSuccess)
+            e = prepare_hs_proj_tc();
+    }
     if (e == cudaSuccess) e = cudaMalloc(&tr->loss_acc, sizeof(double) * (2 + tr->kb + tr->kh));
     tr->max_hubs = n / (kHubMin + 1) + 1;
     const size_t hub_words = 2 * (size_t)tr->max_hubs * kHubRep * (size_t)std::max(tr->kb, tr->kh);
@@ -949,7 +1003,9 @@ void bd_train_destroy(bd_train *tr)
     for (void *p : {(void *)tr->r_bad, (void *)tr->r_hs, (void *)tr->h, (void *)tr->norm,
                     (void *)tr->bits_bad, (void *)tr->bits_hs, (void *)tr->tc_scratch,
                     (void *)tr->keys, (void *)tr->arrivals, (void *)tr->mining, (void *)tr->dr_bad,
-                    (void *)tr->dr_hs, (void *)tr->Wt, (void *)tr->dH, (void *)tr->loss_acc, (void *)tr->hub,
+                    (void *)tr->dr_hs, (void *)tr->Wt, (void *)tr->dH, (void *)tr->hp.d_Wt,
+                    (void *)tr->hp.d_Wt16_hi, (void *)tr->hp.d_Wt16_lo, (void *)tr->hp.d_band,
+                    (void *)tr->loss_acc, (void *)tr->hub,
                     (void *)tr->n_hubs, (void *)tr->hub_list, (void *)tr->hub_acc})
         if (p)
             cudaFree(p);
@@ -984,8 +1040,18 @@ bd_status bd_train_forward(bd_ctx *ctx, bd_train *tr, const float *patches, cons
     trace_kernel(st, "train_bad_fwd");
     // relaxed HashSIFT
     e = launch_hs_hist_patches(patches, rows, tr->h, st, sm, tr->norm);
-    if (e == cudaSuccess)
-        e = launch_hs_proj_fp32_raw(W, b, tr->kh, tr->h, rows, tr->bits_hs, tr->r_hs, 1.0f / tr->T, st);
+    if (e == cudaSuccess) {
+        bd_hs_params *hp = &tr->hp;
+        train_w_split_kernel<<<tr->kh, 128, 0, st>>>(W, tr->kh, hp->d_Wt, hp->d_Wt16_hi, hp->d_Wt16_lo,
+                                                     hp->d_band);
+        trace_kernel(st, "train_w_split");
+        note_launches(1);
+        hp->d_bias = const_cast<float *>(b);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = launch_hs_proj_tc(hp, tr->h, rows, tr->bits_hs, ctx->status, st, nullptr, nullptr, nullptr,
+                                  tr->r_hs, 1.0f / tr->T);
+    }
     // mining on hard codes, or the given mining
     if (e == cudaSuccess && fixed_mining) {
         e = cudaMemcpyAsync(tr->mining, fixed_mining, sizeof(int32_t) * 4 * (size_t)n,
