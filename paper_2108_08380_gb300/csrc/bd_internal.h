@@ -171,7 +171,7 @@ cudaError_t launch_hs_proj_fp32_raw(const float *W, const float *bias, int K, co
 cudaError_t prepare_hs_proj_tc();
 // a16 (optional): the histograms already split into the BF16 operand image
 // (split_offset), with nz[k] != 0 for rows that are not all zero; the kernel
-// then copies each block's operands instead of converting the FP32 rows
+// then copies each block's operands instead of converting the FP32 rows.
 // relaxed (optional, [n][K] FP32): also writes tanh(m inv_t) of each margin
 // m as the tensor cores give it (the training path's relaxed responses).
 cudaError_t launch_hs_proj_tc(const bd_hs_params *p, const float *hist, int n, uint32_t *out,

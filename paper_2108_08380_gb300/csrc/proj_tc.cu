@@ -39,7 +39,8 @@
 // hand the block's words and band bits over in shared memory (two buffers),
 // and those warps re-check the bits while the epilogue goes on with the next
 // block, then store the words (a block with more than RLCAP band bits keeps
-// the rest for the epilogue warps' own re-check).  Every mbarrier wait is bounded; a wait that gives up
+// the rest for the epilogue warps' own re-check); from 16384 keypoints, where
+// each CTA has several blocks.  Every mbarrier wait is bounded; a wait that gives up
 // raises BD_FLAG_TIMEOUT and stops every role at its next block; the CTA
 // then waits (bounded) for the MMAs it issued and the W loads before it
 // frees TMEM and returns.
@@ -175,8 +176,9 @@ __global__ void __launch_bounds__(NTH, 1) hs_proj_tc_kernel(
     const int chunk = blockIdx.x / cpc, part = blockIdx.x % cpc;
     const int n0 = chunk * BN;
     const int bb0 = (int)((long long)nblocks * part / cpc);
-    // band bits handed to the re-checking warps (entries keypoint << 7 | column)
-    const bool handoff = a16 != nullptr && n < (1 << 24);
+    // band bits handed to the re-checking warps when the CTAs have several
+    // blocks to overlap (below that the hand-off only adds latency)
+    const bool handoff = a16 != nullptr && n >= 16384;
     const int nb = (int)((long long)nblocks * (part + 1) / cpc) - bb0;
 
     if (t == 0) {

@@ -431,16 +431,16 @@ def test_wait_limit_runs_out_then_next_call_is_exact(gpu_ctx, graph):
 
 @pytest.mark.parametrize("band", [1e-3, 0.05, 1e9])
 def test_deferred_band_recheck_equals_in_place(gpu_ctx, band):
-    """With the batch kernel's pre-split operand image, the tcgen05
-    projection hands each block's band bits to otherwise idle warps for the
-    FP32 re-check; the bits and the number of re-checked bits equal the
+    """With the batch kernel's pre-split operand image and 16384 keypoints or
+    more, the tcgen05 projection hands each block's band bits to otherwise
+    idle warps for the FP32 re-check; the bits and the number of re-checked bits equal the
     per-image calls, whose epilogue re-checks its own bits.  At band 1e9
     every bit of a non-zero row is in the band, far past the hand-off's room,
     so most of them take the epilogue's own re-check.  Two launches in a row
     check that the hand-off's counters start from zero again."""
     import torch
     rng = np.random.default_rng(77)
-    sizes, counts = [(1280, 720), (800, 600), (640, 480)], [6000, 3000, 1500]
+    sizes, counts = [(1280, 720), (800, 600), (640, 480)], [9000, 5000, 3000]
     imgs = [synth.make_image(w, h, rng) for (w, h) in sizes]
     kps = np.concatenate([synth.make_keypoints(c, w, h, rng, border=-10.0, scales=(1.0,), angle_bins=None)
                           for (w, h), c in zip(sizes, counts)])
