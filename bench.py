@@ -1185,16 +1185,16 @@ KERNEL_SOURCES = {
     "select_threshold": ["select.cu", "bd_internal.h"],
 }
 NCU_TRAFFIC = {
-    "plain": {"describe_batch/batch_persistent": (906752 + 0, "7822e209d42bd1fa")},
-    "large": {"describe_batch/batch_persistent": (45923840 + 66588416, "7822e209d42bd1fa"),
-              "describe_batch/hs_proj_tc": (31296768 + 1792, "f8872d2ab9ab7240"),
-              "match_bad/match_tc": (10284288, "0fe87184717ac856"),
-              "match_hashsift/match_tc": (20522496, "0fe87184717ac856")},
-    "select": {"select/select_keys": (201405696 + 342221568, "4be65b3b887320bd"),
-               "select/select_threshold": (394175488 + 3300096, "4be65b3b887320bd")},
-    "train": {"match_tc": (33592832 + 0, "0fe87184717ac856")},
-    "batch": {"describe_batch/batch_persistent": (286831360 + 406895872, "7822e209d42bd1fa"),
-              "describe_batch/hs_proj_tc": (162736384 + 10219776, "f8872d2ab9ab7240")},
+    "plain": {"describe_batch/batch_persistent": (879104 + 0, "cff0e4bf9f62b959")},
+    "large": {"describe_batch/batch_persistent": (37529088 + 60882176, "cff0e4bf9f62b959"),
+              "describe_batch/hs_proj_tc": (31311616 + 4352, "66fba9f1b9577e54"),
+              "match_bad/match_tc": (10279168 + 0, "c21743c215d3f9df"),
+              "match_hashsift/match_tc": (20523520 + 0, "c21743c215d3f9df")},
+    "select": {"select/select_keys": (201393664 + 342133504, "9efd42f6a99863ab"),
+               "select/select_threshold": (394337024 + 3256320, "9efd42f6a99863ab")},
+    "train": {"match_tc": (33593344 + 0, "c21743c215d3f9df")},
+    "batch": {"describe_batch/batch_persistent": (286708224 + 406824704, "cff0e4bf9f62b959"),
+              "describe_batch/hs_proj_tc": (162755072 + 9899776, "66fba9f1b9577e54")},
 }
 
 
