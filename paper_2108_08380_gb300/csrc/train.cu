@@ -3,11 +3,13 @@
 //
 // Rows of the patch tensor: [0,n) anchors, [n,2n) positives, [2n,3n) negatives.
 //  forward
-//   - relaxed BAD: one warp per patch builds its summed-area table in 64-bit
+//   - one pass over the patches (one warp per patch): the HashSIFT
+//     histogram, then the relaxed BAD responses;
+//   - relaxed BAD: the warp builds the patch's summed-area table in 64-bit
 //     fixed point (value x 2^32, exact for |v| >= 2^-9), so box sums are exact
 //     integer sums and the hard bit [f <= theta] is the exact comparison
 //     D <= floor(theta s^2 2^32); r = tanh((theta - f)/(255 T)) in FP32;
-//   - relaxed HashSIFT: the patch histogram kernel, then the projection on
+//   - relaxed HashSIFT: the histogram from that pass, then the projection on
 //     the tensor cores (W split into BF16 head and tail each step; three
 //     MMAs, margins within about 4e-6 of FP32 at these sizes) with
 //     r = tanh((W^T h + b)/T) from those margins, and hard bits [m > 0] equal
@@ -89,21 +91,32 @@ __device__ __forceinline__ long long sat_box64(const long long (*S)[33], int x0,
     return S[yb][xb] - S[ya][xb] - S[yb][xa] + S[ya][xa];
 }
 
-// Relaxed BAD forward, one warp per patch (four per CTA, no CTA barrier in the
-// patch loop).  Each CTA first turns the thresholds into their fixed-point
-// bounds floor(theta_k s_k^2 2^32) and scales 2^-32 / s_k^2.  The warp's
-// 33 x 33 fixed-point table is its only per-patch shared memory (five CTAs
-// per SM).
+// Relaxed forward of both descriptors, one warp per patch (four per CTA, no
+// CTA barrier in the patch loop); lane x holds column x of the patch in
+// registers (the patch is read once, coalesced).
+//  - HashSIFT: the orientation histogram, each row voted as the patch
+//    histogram kernel votes it (same values, same order: the same histogram
+//    and norm), into the warp's lane-private bins;
+//  - BAD: then, over the same shared memory, the patch's 33 x 33 summed-area
+//    table in 64-bit fixed point (column sums in registers, row sums in
+//    shared memory: integer sums, the same table in any order), the box
+//    differences D, the exact bit D <= floor(theta s^2 2^32) and r.
+// Each CTA first turns the thresholds into their fixed-point bounds
+// floor(theta_k s_k^2 2^32) and scales 2^-32 / s_k^2.  About 9 KB of shared
+// memory per warp: five CTAs per SM.
 template <int NW>
-__global__ void __launch_bounds__(128) train_bad_fwd_kernel(const float *__restrict__ patches, int rows,
-                                                            const short4 *__restrict__ box,
-                                                            const int *__restrict__ side,
-                                                            const float *__restrict__ theta,
-                                                            float inv_scale, float *__restrict__ r,
-                                                            uint32_t *__restrict__ bits)
+__global__ void __launch_bounds__(128) train_fwd_kernel(const float *__restrict__ patches, int rows,
+                                                        const short4 *__restrict__ box,
+                                                        const int *__restrict__ side,
+                                                        const float *__restrict__ theta,
+                                                        float inv_scale, float *__restrict__ r,
+                                                        uint32_t *__restrict__ bits,
+                                                        float *__restrict__ hist,
+                                                        float *__restrict__ norm)
 {
     constexpr int K = NW * 32;
-    __shared__ long long S[4][33][33];
+    static_assert(sizeof(dev::WarpHist) >= sizeof(long long) * 33 * 33, "the table fits the histogram area");
+    __shared__ dev::WarpHist H[4];
     __shared__ long long thr[K];
     __shared__ float fscale[K];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -114,21 +127,37 @@ __global__ void __launch_bounds__(128) train_bad_fwd_kernel(const float *__restr
         fscale[k] = (float)(1.0 / (s2 * kFix));
     }
     __syncthreads();
-    long long (*Sw)[33] = S[warp];
-    // the table's zero row and column stay zero
-    Sw[0][lane + 1] = 0;
-    Sw[lane + 1][0] = 0;
-    if (lane == 0)
-        Sw[0][0] = 0;
+    dev::WarpHist &S = H[warp];
+    long long (*Sw)[33] = reinterpret_cast<long long (*)[33]>(&S);
+    const float g_half = 0.5f * dev::gauss16(lane);
     for (int row = blockIdx.x * 4 + warp; row < rows; row += gridDim.x * 4) {
         const float *p = patches + (size_t)row * 1024;
-        // column x = lane: the patch's column from global memory (a warp's
-        // loads coalesced), its prefix sums down y in fixed point
         float v[32];
 #pragma unroll
         for (int y = 0; y < 32; ++y)
             v[y] = __ldg(p + y * 32 + lane);
+        __syncwarp();  // the previous patch's table reads are done
+        // HashSIFT: rows 0 .. 31 down this lane's column, row -1 and row 32
+        // replicated
+        dev::priv_zero_warp(S, lane);
         __syncwarp();
+        {
+            float up = v[0], here = v[0];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const float down = v[i < 31 ? i + 1 : 31];
+                dev::vote_px(S, lane, i, up, here, down, g_half);
+                up = here;
+                here = down;
+            }
+        }
+        __syncwarp();
+        dev::warp_finish(S, lane, true, hist, (size_t)row, norm, 0);
+        // BAD: the table over the histogram's shared memory
+        Sw[0][lane + 1] = 0;
+        Sw[lane + 1][0] = 0;
+        if (lane == 0)
+            Sw[0][0] = 0;
         {
             long long acc = 0;
 #pragma unroll
@@ -138,8 +167,7 @@ __global__ void __launch_bounds__(128) train_bad_fwd_kernel(const float *__restr
             }
         }
         __syncwarp();
-        // row y = lane + 1: prefix sums along x (integer sums: the same table
-        // in any order)
+        // row y = lane + 1: prefix sums along x
         {
             long long acc = 0;
 #pragma unroll 8
@@ -1030,16 +1058,18 @@ bd_status bd_train_forward(bd_ctx *ctx, bd_train *tr, const float *patches, cons
     const float inv_scale = 1.0f / (255.0f * tr->T);
     const bd_bad_params *bp = tr->bad;
     cudaError_t e = cudaSuccess;
-    // relaxed BAD
+    // relaxed BAD and the HashSIFT histograms in one pass over the patches
     if (tr->kb == 256)
-        train_bad_fwd_kernel<8><<<grid_rows((rows + 3) / 4, sm, 5), 128, 0, st>>>(
-            patches, rows, bp->d_patch_box, bp->d_patch_side, theta, inv_scale, tr->r_bad, tr->bits_bad);
+        train_fwd_kernel<8><<<grid_rows((rows + 3) / 4, sm, 5), 128, 0, st>>>(
+            patches, rows, bp->d_patch_box, bp->d_patch_side, theta, inv_scale, tr->r_bad, tr->bits_bad,
+            tr->h, tr->norm);
     else
-        train_bad_fwd_kernel<16><<<grid_rows((rows + 3) / 4, sm, 5), 128, 0, st>>>(
-            patches, rows, bp->d_patch_box, bp->d_patch_side, theta, inv_scale, tr->r_bad, tr->bits_bad);
-    trace_kernel(st, "train_bad_fwd");
-    // relaxed HashSIFT
-    e = launch_hs_hist_patches(patches, rows, tr->h, st, sm, tr->norm);
+        train_fwd_kernel<16><<<grid_rows((rows + 3) / 4, sm, 5), 128, 0, st>>>(
+            patches, rows, bp->d_patch_box, bp->d_patch_side, theta, inv_scale, tr->r_bad, tr->bits_bad,
+            tr->h, tr->norm);
+    trace_kernel(st, "train_fwd");
+    e = cudaGetLastError();
+    // relaxed HashSIFT projection
     if (e == cudaSuccess) {
         bd_hs_params *hp = &tr->hp;
         train_w_split_kernel<<<tr->kh, 128, 0, st>>>(W, tr->kh, hp->d_Wt, hp->d_Wt16_hi, hp->d_Wt16_lo,
