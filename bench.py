@@ -1185,16 +1185,16 @@ KERNEL_SOURCES = {
     "select_threshold": ["select.cu", "bd_internal.h"],
 }
 NCU_TRAFFIC = {
-    "plain": {"describe_batch/batch_persistent": (879104 + 0, "cff0e4bf9f62b959")},
-    "large": {"describe_batch/batch_persistent": (37529088 + 60882176, "cff0e4bf9f62b959"),
-              "describe_batch/hs_proj_tc": (31311616 + 4352, "66fba9f1b9577e54"),
-              "match_bad/match_tc": (10279168 + 0, "c21743c215d3f9df"),
-              "match_hashsift/match_tc": (20523520 + 0, "c21743c215d3f9df")},
-    "select": {"select/select_keys": (201393664 + 342133504, "9efd42f6a99863ab"),
-               "select/select_threshold": (394337024 + 3256320, "9efd42f6a99863ab")},
-    "train": {"match_tc": (33593344 + 0, "c21743c215d3f9df")},
-    "batch": {"describe_batch/batch_persistent": (286708224 + 406824704, "cff0e4bf9f62b959"),
-              "describe_batch/hs_proj_tc": (162755072 + 9899776, "66fba9f1b9577e54")},
+    "plain": {"describe_batch/batch_persistent": (879104 + 0, "db55869e06217044")},
+    "large": {"describe_batch/batch_persistent": (37529088 + 60882176, "db55869e06217044"),
+              "describe_batch/hs_proj_tc": (31311616 + 4352, "96a7fcb4409a3282"),
+              "match_bad/match_tc": (10279168 + 0, "55492dad1bd91d4d"),
+              "match_hashsift/match_tc": (20523520 + 0, "55492dad1bd91d4d")},
+    "select": {"select/select_keys": (201393664 + 342133504, "bb9218d805732253"),
+               "select/select_threshold": (394337024 + 3256320, "bb9218d805732253")},
+    "train": {"match_tc": (33593344 + 0, "55492dad1bd91d4d")},
+    "batch": {"describe_batch/batch_persistent": (286708224 + 406824704, "db55869e06217044"),
+              "describe_batch/hs_proj_tc": (162755072 + 9899776, "96a7fcb4409a3282")},
 }
 
 

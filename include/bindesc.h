@@ -429,7 +429,11 @@ void bd_train_destroy(bd_train *tr);
  * when it is the more similar one.  loss (device, 2 floats) receives
  * L = sum_i [tau - r(a_i).r(p_i) + r(x*_i).r(n*_i)]_+ for BAD and HashSIFT;
  * mining_out (device, nullable) receives [4][n] int32: n*_bad, swap_bad,
- * n*_hs, swap_hs; fixed_mining (device, nullable) replaces the mining. */
+ * n*_hs, swap_hs; fixed_mining (device, nullable) replaces the mining.
+ * The HashSIFT margins come from the tensor cores (W split into a BF16 head
+ * and tail each call, three products per term: within a few 1e-6 of the FP32
+ * sum for unit histograms and ||W_k|| near 1); the hard HashSIFT codes equal
+ * the FP32 projection's (bits within 2^-13 ||W_k|| are recomputed in FP32). */
 bd_status bd_train_forward(bd_ctx *ctx, bd_train *tr, const float *patches, const float *theta,
                            const float *W, const float *b, const int32_t *fixed_mining,
                            float *loss, int32_t *mining_out);

@@ -34,7 +34,8 @@
 //     each, summed at the end), converted and scaled by the loss weight at
 //     the end (which also clears it); the others keep FP32 atomics;
 //   - BAD: dtheta column sums, and the box adjoint as a 2-D difference array
-//     per patch (4 corner updates per box, then a 2-D prefix sum);
+//     per patch (the corner updates that fall inside the patch, then 2-D
+//     prefix sums);
 //   - the column sums over all 3n rows (dtheta, db) cancel heavily (anchors
 //     and positives pull one way, negatives the other), so each thread sums
 //     its rows with compensated (Kahan) FP32 additions and the partial sums
