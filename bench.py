@@ -1185,16 +1185,16 @@ KERNEL_SOURCES = {
     "select_threshold": ["select.cu", "bd_internal.h"],
 }
 NCU_TRAFFIC = {
-    "plain": {"describe_batch/batch_persistent": (879104 + 0, "db55869e06217044")},
-    "large": {"describe_batch/batch_persistent": (37529088 + 60882176, "db55869e06217044"),
-              "describe_batch/hs_proj_tc": (31311616 + 4352, "96a7fcb4409a3282"),
-              "match_bad/match_tc": (10279168 + 0, "55492dad1bd91d4d"),
-              "match_hashsift/match_tc": (20523520 + 0, "55492dad1bd91d4d")},
-    "select": {"select/select_keys": (201393664 + 342133504, "bb9218d805732253"),
-               "select/select_threshold": (394337024 + 3256320, "bb9218d805732253")},
-    "train": {"match_tc": (33593344 + 0, "55492dad1bd91d4d")},
-    "batch": {"describe_batch/batch_persistent": (286708224 + 406824704, "db55869e06217044"),
-              "describe_batch/hs_proj_tc": (162755072 + 9899776, "96a7fcb4409a3282")},
+    "plain": {"describe_batch/batch_persistent": (879104 + 0, "076afb1061f29035")},
+    "large": {"describe_batch/batch_persistent": (37529088 + 60882176, "076afb1061f29035"),
+              "describe_batch/hs_proj_tc": (31311616 + 4352, "be87799083a5e228"),
+              "match_bad/match_tc": (10279168 + 0, "59f3d684ac6a76a3"),
+              "match_hashsift/match_tc": (20523520 + 0, "59f3d684ac6a76a3")},
+    "select": {"select/select_keys": (201393664 + 342133504, "8d33f0ff71a1e5ba"),
+               "select/select_threshold": (394337024 + 3256320, "8d33f0ff71a1e5ba")},
+    "train": {"match_tc": (33593344 + 0, "59f3d684ac6a76a3")},
+    "batch": {"describe_batch/batch_persistent": (286708224 + 406824704, "076afb1061f29035"),
+              "describe_batch/hs_proj_tc": (162755072 + 9899776, "be87799083a5e228")},
 }
 
 

@@ -163,10 +163,6 @@ cudaError_t launch_hs_hist_image(const bd_hs_params *p, const uint8_t *img, int 
                                  int sm_count);
 cudaError_t launch_hs_proj_fp32(const bd_hs_params *p, const float *hist, int n, uint32_t *out,
                                 cudaStream_t st, const bd_keypoint *kps);
-// FP32 projection with any W [128][K] / bias; relaxed (nullable) gets tanh(m * inv_t)
-cudaError_t launch_hs_proj_fp32_raw(const float *W, const float *bias, int K, const float *hist,
-                                    int n, uint32_t *out, float *relaxed, float inv_t,
-                                    cudaStream_t st);
 // raises the projection kernel's dynamic shared-memory limit (per device, at set-up)
 cudaError_t prepare_hs_proj_tc();
 // a16 (optional): the histograms already split into the BF16 operand image

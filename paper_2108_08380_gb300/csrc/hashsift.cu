@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(NT) hs_warp_kernel(const uint8_t *__restrict__
 // re-check evaluates the same expression, so both paths give the same bits.
 // Tile: 64 keypoints x 128 bits per CTA, 4 x 8 outputs per thread: rows
 // 4 ty .. 4 ty + 3, columns 4 tx .. 4 tx + 3 and 64 + 4 tx .. 64 + 4 tx + 3, so
-// that a warp's 16-byte shared loads and relaxed-response stores are
-// contiguous; the two threads of a byte combine their nibbles by a shuffle.
+// that a warp's 16-byte shared loads are contiguous; the two threads of a
+// byte combine their nibbles by a shuffle.
 // ---------------------------------------------------------------------------
 constexpr int PBM = 64, PBN = 128, PBK = 32;
 
@@ -112,9 +112,7 @@ __global__ void __launch_bounds__(256) hs_proj_fp32_kernel(const float *__restri
                                                            const float *__restrict__ W, int K,
                                                            const float *__restrict__ bias,
                                                            const bd_keypoint *__restrict__ kps,
-                                                           uint8_t *__restrict__ out,
-                                                           float *__restrict__ relaxed,
-                                                           float inv_t)
+                                                           uint8_t *__restrict__ out)
 {
     __shared__ __align__(16) float Hs[PBK][PBM + 4];
     __shared__ __align__(16) float Ws[PBK][PBN];
@@ -208,15 +206,6 @@ __global__ void __launch_bounds__(256) hs_proj_fp32_kernel(const float *__restri
             o[tx >> 1] = (uint8_t)(lo | (lo_p << 4));
             o[8 + (tx >> 1)] = (uint8_t)(hi | (hi_p << 4));
         }
-        if (relaxed && in) {
-            float v[8];
-#pragma unroll
-            for (int b = 0; b < 8; ++b)
-                v[b] = dev::tanh_relaxed((acc[a][b] + bv[b]) * inv_t);
-            float *rr = relaxed + (size_t)row * K + n0;
-            *reinterpret_cast<float4 *>(rr + tx * 4) = make_float4(v[0], v[1], v[2], v[3]);
-            *reinterpret_cast<float4 *>(rr + 64 + tx * 4) = make_float4(v[4], v[5], v[6], v[7]);
-        }
     }
 }
 
@@ -272,24 +261,12 @@ cudaError_t launch_hs_hist_image(const bd_hs_params *p, const uint8_t *img, int 
 }
 
 
-cudaError_t launch_hs_proj_fp32_raw(const float *W, const float *bias, int K, const float *hist,
-                                    int n, uint32_t *out, float *relaxed, float inv_t,
-                                    cudaStream_t st)
-{
-    dim3 grid((n + PBM - 1) / PBM, K / PBN);
-    hs_proj_fp32_kernel<<<grid, 256, 0, st>>>(hist, n, W, K, bias, nullptr,
-                                              reinterpret_cast<uint8_t *>(out), relaxed, inv_t);
-    trace_kernel(st, "hs_proj_fp32_relaxed");
-    note_launches(1);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_hs_proj_fp32(const bd_hs_params *p, const float *hist, int n, uint32_t *out,
                                 cudaStream_t st, const bd_keypoint *kps)
 {
     dim3 grid((n + PBM - 1) / PBM, p->nbits / PBN);
     hs_proj_fp32_kernel<<<grid, 256, 0, st>>>(hist, n, p->d_W, p->nbits, p->d_bias, kps,
-                                              reinterpret_cast<uint8_t *>(out), nullptr, 1.0f);
+                                              reinterpret_cast<uint8_t *>(out));
     trace_kernel(st, "hs_proj_fp32");
     note_launches(1);
     return cudaGetLastError();
