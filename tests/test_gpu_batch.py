@@ -430,7 +430,7 @@ def test_wait_limit_runs_out_then_next_call_is_exact(gpu_ctx, graph):
 
 
 @pytest.mark.parametrize("band", [1e-3, 0.05, 1e9])
-def test_deferred_band_recheck_equals_in_place(gpu_ctx, band):
+def test_projection_recheck_handoff_equals_in_place(gpu_ctx, band):
     """With the batch kernel's pre-split operand image and 16384 keypoints or
     more, the tcgen05 projection hands each block's band bits to otherwise
     idle warps for the FP32 re-check; the bits and the number of re-checked bits equal the
