@@ -14,6 +14,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import atexit
 import weakref
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -163,8 +164,25 @@ def _np_ptr(a):
     return ctypes.c_void_p(a.ctypes.data)
 
 
+_live_contexts = weakref.WeakSet()
+_exit_hook = []
+
+
+def _close_live_contexts():
+    """At interpreter exit, closes every context still open (and the plans
+    and parameter sets made from it) while the CUDA runtime is still up."""
+    for c in list(_live_contexts):
+        try:
+            c.close()
+        except Exception:
+            pass
+
+
 class Context:
-    """Owns a bd_ctx on one CUDA device; calls enqueue on the current torch stream."""
+    """Owns a bd_ctx on one CUDA device; calls enqueue on the current torch stream.
+    Contexts still open at interpreter exit are closed by an exit handler
+    registered after CUDA is initialised (exit handlers run last-in, first-out,
+    so it runs before the runtime's own)."""
 
     def __init__(self, device: int = 0, stream=None):
         import torch
@@ -178,6 +196,10 @@ class Context:
         self.handle = h
         self._explicit_stream = stream is not None
         self._children = weakref.WeakSet()
+        _live_contexts.add(self)
+        if not _exit_hook:
+            atexit.register(_close_live_contexts)
+            _exit_hook.append(True)
 
     def _adopt(self, child):
         self._children.add(child)
